@@ -1,0 +1,241 @@
+/*
+ * rcbf.h — C ABI of the GB300 row-column / TOBE beamformer hot path.
+ *
+ * The library implements the data-parallel core of the realtime beamformer of
+ * Palamar et al., "An Open Source Realtime GPU Beamformer for Row-Column and
+ * TOBE Arrays" (arXiv 2512.11086):
+ *
+ *   decode   Hadamard aperture decode of FORCES / HERCULES acquisitions
+ *            (§THEORY "Synthetic Aperture Imaging"; §OPTIMIZATIONS "Decoding"):
+ *            a matrix product across the transmit axis.
+ *   das      synthetic-aperture delay-and-sum, Eq. (1), with the constant-F#
+ *            receive apodization of Eq. (2) and the Hanning window of Eq. (3)
+ *            (§OPTIMIZATIONS "DAS").
+ *   backward the adjoint of das with respect to the RF samples, the speed of
+ *            sound and the per-channel apodization weights (Eq. (1)
+ *            differentiated; the paper has no adjoint, it serves
+ *            speed-of-sound autofocus).
+ *   batch    many frames of uneven size in one persistent launch
+ *            (§METHODS "Data Processing": several pre-uploaded parameter sets).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Layouts. Encoded RF is int16 [n_tx][n_ch][n_samples], samples fastest
+ *    (n_tx = acquisitions = Hadamard order). Decoded RF has the same shape;
+ *    row i is the decoded transmit element i. A complex decoded RF (RCBF_CF32)
+ *    is two planes [2][n_tx][n_ch][n_samples] (real, then imaginary).
+ *    Images are float32 [nz][ny][nx], x fastest; a complex image is two such
+ *    planes (real, then imaginary).
+ *  * Memory. Every data pointer passed to decode / das / backward / batch is
+ *    a DEVICE pointer owned by the caller; the library never frees it. It must
+ *    be 16-byte aligned. A plan owns the device tables it creates in
+ *    rcbf_plan (decode matrix fragments) and frees them in rcbf_destroy.
+ *  * Streams. `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream). Work is enqueued asynchronously; no entry point except
+ *    rcbf_plan, rcbf_batch_create and rcbf_batch_status synchronises the host.
+ *  * Errors. Every int-returning entry point returns 0 on success or a
+ *    negative RCBF_E* code. Arguments are validated on the host before any
+ *    launch; on error nothing is enqueued. rcbf_last_error() returns a
+ *    thread-local, human-readable message for the last failure on the calling
+ *    thread.
+ *  * Geometry. All lengths in metres, times in seconds, rates in Hz. The array
+ *    frame has z along the array normal and its origin at the centre of the
+ *    array: transmit element i (a line element) sits at lateral coordinate
+ *    (i - (n_tx-1)/2) * tx_pitch, receive element j at
+ *    (j - (n_ch-1)/2) * rx_pitch, both at z = 0. A row element spans x, so
+ *    its lateral coordinate is y; a column element spans y, so its lateral
+ *    coordinate is x. The paper's corner-element origin is one translation
+ *    away, expressible through xdc_transform.
+ *  * Delays. For a voxel at array-frame position q and line elements with
+ *    lateral coordinates e_i (transmit) and e_j (receive):
+ *        d_tx = sqrt((lat_tx(q) - e_i)^2 + q_z^2)
+ *        d_rx = sqrt((lat_rx(q) - e_j)^2 + q_z^2)
+ *        s_ij = ((d_tx + d_rx) / c - t0) * fs          (fractional sample)
+ *    and DAS reads the decoded trace r_ij at s_ij by linear interpolation,
+ *    with r_ij[n] = 0 for n outside [0, n_samples-1].
+ */
+#ifndef RCBF_H
+#define RCBF_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define RCBF_OK             0
+#define RCBF_EINVAL        -1  /* bad argument: NULL, zero size, misaligned, inconsistent */
+#define RCBF_EUNSUPPORTED  -2  /* dtype / mode / size combination not built */
+#define RCBF_ECUDA         -3  /* CUDA runtime or launch error (message in rcbf_last_error) */
+#define RCBF_ENOMEM        -4  /* device allocation failed */
+#define RCBF_ETIMEOUT      -5  /* a bounded device-side wait expired (batch only) */
+
+/* ---- enumerations -------------------------------------------------------- */
+enum rcbf_dtype {
+    RCBF_I16  = 0,   /* int16 (encoded RF only) */
+    RCBF_I32  = 1,   /* int32: exact decode sum H^T S, unscaled */
+    RCBF_F32  = 2,   /* float32: (H^T S) / N, exact for N a power of two */
+    RCBF_F16  = 3,   /* float16: (H^T S) / N rounded once to nearest-even */
+    RCBF_CF32 = 4    /* complex float32 as two planes (DAS input only) */
+};
+
+enum rcbf_acq_kind {
+    RCBF_FORCES   = 0,  /* Hadamard-encoded transmit aperture */
+    RCBF_HERCULES = 1   /* Hadamard-encoded receive rows; same separable delays */
+};
+
+enum rcbf_orientation {
+    RCBF_ROWS    = 0,   /* line elements span x: lateral coordinate is y */
+    RCBF_COLUMNS = 1    /* line elements span y: lateral coordinate is x */
+};
+
+enum rcbf_interp { RCBF_LINEAR = 0 };
+
+enum rcbf_decode_variant {
+    RCBF_DECODE_MMA_I8  = 0,  /* split-byte int8 tensor-core GEMM (mma.sync s8/u8), exact */
+    RCBF_DECODE_PLAIN   = 1   /* plain CUDA-core form: one thread per output, int32 sums */
+};
+
+enum rcbf_das_variant {
+    RCBF_DAS_TILED = 0,  /* voxel tiles, per-tile FP64 reference delays, shared-memory windows */
+    RCBF_DAS_PLAIN = 1   /* plain FP32 form: one thread per voxel, FP32 delays, global loads */
+};
+
+/* ---- parameter block ------------------------------------------------------
+ * Caller-owned; rcbf_plan copies it. Zero-initialise and fill what you use:
+ * an all-zero xdc_transform / voxel_transform means "not given". */
+typedef struct rcbf_params {
+    uint32_t n_tx;            /* decoded transmits (rows of RF) */
+    uint32_t n_ch;            /* receive channels */
+    uint32_t n_samples;       /* samples per (transmit, channel) trace */
+    uint32_t hadamard_order;  /* 0: RF is not encoded (decode unavailable); else == n_tx */
+    uint32_t acq_kind;        /* enum rcbf_acq_kind (informational: delays are identical) */
+    uint32_t tx_orientation;  /* enum rcbf_orientation of the transmit line elements */
+    uint32_t rx_orientation;  /* enum rcbf_orientation of the receive line elements */
+    uint32_t decoded_dtype;   /* enum rcbf_dtype: decode output and DAS input
+                                 (RCBF_I32, RCBF_F32, RCBF_F16, RCBF_CF32) */
+    uint32_t interp;          /* enum rcbf_interp */
+    uint32_t decode_variant;  /* enum rcbf_decode_variant */
+    uint32_t das_variant;     /* enum rcbf_das_variant */
+    uint32_t out_dims[3];     /* nx, ny, nz (>= 1 each) */
+    uint32_t tile[3];         /* DAS voxel tile (bx, by, bz); all 0 = choose automatically.
+                                 bx*by*bz must be 1024 when given. */
+    uint32_t reserved;
+    double   fs;              /* sampling rate [Hz] */
+    double   c;               /* speed of sound [m/s] (DAS may override per call) */
+    double   t0;              /* time of sample 0 relative to emission [s] */
+    double   fc;              /* centre frequency [Hz] (informational) */
+    double   tx_pitch;        /* transmit element pitch [m] */
+    double   rx_pitch;        /* receive element pitch [m] */
+    double   xdc_transform[16]; /* row-major 4x4 affine, world -> array frame; zeros = identity */
+    double   out_min[3];      /* world position of voxel (0,0,0) [m] */
+    double   out_max[3];      /* world position of voxel (nx-1,ny-1,nz-1) [m] (inclusive linspace) */
+    double   voxel_transform[16]; /* row-major 4x4 affine, voxel index -> world; zeros = use out_min/out_max */
+    double   f_number;        /* F# of Eq. (2); 0 disables the window (all weights 1) */
+    const int8_t* decode_matrix; /* optional HOST pointer to an n_tx x n_tx +-1 matrix H,
+                                    row-major H[k][i] (k = acquisition, i = decoded element),
+                                    copied by rcbf_plan; NULL = Sylvester H[k][i] = (-1)^popcount(k&i) */
+} rcbf_params;
+
+typedef struct rcbf_plan_s*  rcbf_plan_t;
+typedef struct rcbf_batch_s* rcbf_batch_t;
+
+/* rcbf_plan — validate `params`, copy it, build the device decode tables and
+ * pick the DAS tile. Allocates a few KB of device memory on the current
+ * device; synchronises once. Decode requires hadamard_order == n_tx with
+ * n_tx a multiple of 32 in [32, 256] (any +-1 matrix if decode_matrix is
+ * given, else n_tx a power of two). Errors: RCBF_EINVAL (NULL, zero sizes,
+ * non-power-of-two order without a matrix, entries not +-1, tile product),
+ * RCBF_EUNSUPPORTED (dtype / variant), RCBF_ENOMEM, RCBF_ECUDA.
+ * Passage: §METHODS "Data Processing" (data description, array geometry,
+ * image region and resolution) and Fig. "das_dispatch" (voxel-index affine). */
+int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan);
+
+/* rcbf_destroy — free the plan's device tables. NULL is accepted. Must not be
+ * called while work using the plan is still pending on a stream. */
+void rcbf_destroy(rcbf_plan_t plan);
+
+/* rcbf_decode — D = H^T S over the transmit axis (§THEORY "Synthetic Aperture
+ * Imaging": decoded data behaves as one transmit per element; §OPTIMIZATIONS
+ * "Decoding": a matrix product across transmits).
+ *   rf       device int16 [n_tx][n_ch][n_samples] (encoded acquisitions k)
+ *   decoded  device [n_tx][n_ch][n_samples] of params.decoded_dtype:
+ *            RCBF_I32 = D exactly; RCBF_F32 = D / N exactly (|D| < 2^24 always
+ *            holds for int16 input and N <= 256); RCBF_F16 = D / N rounded once.
+ * Exact for every int16 input (integer arithmetic throughout).
+ * n_samples must be a multiple of 8. Errors: RCBF_EINVAL (NULL, misaligned,
+ * plan without Hadamard order), RCBF_EUNSUPPORTED (CF32 output), RCBF_ECUDA. */
+int rcbf_decode(rcbf_plan_t plan, const int16_t* rf, void* decoded, void* stream);
+
+/* rcbf_das — delay-and-sum of Eq. (1) with a_tx = 1 and receive apodization
+ *   a_j(v) = w_j * W(F# * |lat_rx(v) - e_j| / |z(v)|)   (Eq. (2), Eq. (3), W(u)=cos^2(pi u) for |u|<0.5)
+ * (a_j = w_j when f_number == 0):
+ *   image(v) = sum_i sum_j a_j(v) * lerp(r_ij, s_ij(v)).
+ *   decoded  device decoded RF of params.decoded_dtype (RCBF_I32 data is
+ *            scaled by 1/n_tx; RCBF_CF32 gives a complex image)
+ *   apod     device float32 [n_ch] per-channel weights w_j, or NULL (all 1)
+ *   c        speed of sound for this call; <= 0 uses params.c
+ *   image    device float32 [nz][ny][nx] (x2 planes for RCBF_CF32), overwritten
+ * Accumulation is FP32. Errors: RCBF_EINVAL, RCBF_EUNSUPPORTED, RCBF_ECUDA. */
+int rcbf_das(rcbf_plan_t plan, const void* decoded, const float* apod, float c,
+             float* image, void* stream);
+
+/* rcbf_das_backward — adjoint of rcbf_das (Eq. (1) differentiated) for an
+ * upstream gradient G = dL/dimage:
+ *   grad_rf[i][j][n]  = sum_v a_j(v) G(v) * lerp-weight of sample n at s_ij(v)
+ *   grad_c            = sum_v sum_ij a_j(v) G(v) * (r_ij[n+1]-r_ij[n]) * ds_ij/dc,
+ *                       ds_ij/dc = -(d_tx + d_rx) * fs / c^2
+ *   grad_apod[j]      = sum_v sum_i (a_j(v)/w_j) G(v) * lerp(r_ij, s_ij(v))
+ * (complex data: the real and imaginary planes contribute independently).
+ *   decoded    device RF as for rcbf_das (RCBF_F32 or RCBF_CF32 only)
+ *   grad_image device float32 image-shaped (x2 planes for complex)
+ *   grad_rf    device float32 RF-shaped, overwritten; NULL = not computed
+ *   grad_c     device float32 scalar, overwritten; NULL = not computed
+ *   grad_apod  device float32 [n_ch], overwritten; NULL = not computed
+ * Delays are recomputed per voxel tile, never stored. Sums use float atomics,
+ * so their order (and the last bits) vary between runs.
+ * Errors: RCBF_EINVAL, RCBF_EUNSUPPORTED (dtype), RCBF_ECUDA. */
+int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, float c,
+                      const float* grad_image, float* grad_rf, float* grad_c,
+                      float* grad_apod, void* stream);
+
+/* rcbf_batch_create — bind n_frames (plan, buffers) triples into one batch
+ * that a single persistent kernel processes: for every frame with a
+ * Hadamard order, decode rf[f] into decoded[f], then DAS decoded[f] into
+ * images[f] (frames with hadamard_order == 0 skip the decode and read
+ * decoded[f] directly). Plans may differ in every size; all must use
+ * decoded_dtype RCBF_F32 or RCBF_F16 and the tiled DAS. The plans must outlive
+ * the batch. Pointer arrays are HOST arrays of DEVICE pointers, copied.
+ * Passage: §METHODS "Data Processing" (pre-uploaded parameter sets) and
+ * §OPTIMIZATIONS "Data Transfer" (frames kept in flight).
+ * Allocates the device work list; synchronises once. */
+int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames,
+                      const int16_t* const* rf, void* const* decoded,
+                      float* const* images, rcbf_batch_t* out_batch);
+
+/* rcbf_batch_run — enqueue the whole batch as one persistent launch (plus a
+ * small reset kernel) on `stream`. Contains no host synchronisation and no
+ * allocation, so it can be captured in a CUDA graph. The persistent kernel's
+ * waits on per-frame decode completion are bounded; on expiry it records
+ * RCBF_ETIMEOUT in the batch's device status word (see rcbf_batch_status). */
+int rcbf_batch_run(rcbf_batch_t batch, void* stream);
+
+/* rcbf_batch_status — synchronise `stream` and return the device status word
+ * of the last run: RCBF_OK or RCBF_ETIMEOUT. */
+int rcbf_batch_status(rcbf_batch_t batch, void* stream);
+
+/* rcbf_batch_destroy — free the batch's device work list. NULL is accepted. */
+void rcbf_batch_destroy(rcbf_batch_t batch);
+
+/* rcbf_last_error — message for the last failure on this thread ("" if none). */
+const char* rcbf_last_error(void);
+
+/* rcbf_version — library version string. */
+const char* rcbf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RCBF_H */

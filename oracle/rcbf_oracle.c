@@ -1,0 +1,246 @@
+/*
+ * rcbf_oracle.c — plain, slow FP64 CPU oracle of the beamformer hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the library, its kernels or its Python
+ * binding may include, link or call this file; only the tests, the smoke
+ * check and the benchmark's CPU-baseline leg use it. It shares no header,
+ * table or helper with the CUDA path.
+ *
+ * Every function writes out the paper's definition directly, loop by loop,
+ * in double precision (int64 for the decode), with no blocking, fusion or
+ * reordering beyond the definition:
+ *
+ *   oracle_hadamard  Sylvester Hadamard matrix H[k][i] = (-1)^popcount(k & i).
+ *   oracle_decode    D[i][c] = sum_k H[k][i] * S[k][c]          (§THEORY
+ *                    "Synthetic Aperture Imaging": decoding is a matrix
+ *                    product across transmits; after decoding, row i behaves
+ *                    as a transmit on element i).
+ *   oracle_das       HR(v) = sum_i a_tx sum_j a_j(v) r_ij(ToF_ij(v))  Eq. (1),
+ *                    a_tx = 1, a_j(v) = w_j W(F# |lat_rx(v) - e_j| / |z(v)|)
+ *                    Eq. (2), W(u) = cos^2(pi u) for |u| < 0.5, else 0  Eq. (3);
+ *                    r_ij read at fractional sample s = (ToF - t0) fs by linear
+ *                    interpolation with zero outside the record.
+ *   oracle_das_grad  the derivatives of oracle_das with respect to the RF
+ *                    samples, the speed of sound c and the weights w_j.
+ *
+ * Geometry (the readings used by the whole project): line elements centred
+ * on the origin, e_i = (i - (n-1)/2) pitch at z = 0; a row element's lateral
+ * coordinate is y, a column element's is x; the distance from a point q to a
+ * line element is sqrt((lat(q) - e)^2 + q_z^2). Voxel positions come from an
+ * inclusive linspace (or a 4x4 voxel-index affine), then a 4x4 world-to-array
+ * affine.
+ *
+ * Window reading: the window is non-zero exactly when F# |lat - e_j| < 0.5 |z|
+ * (|u| < 0.5 written without a division), so a voxel at z = 0 gets weight 0.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct oracle_geom {
+    int64_t n_tx, n_ch, n_samples;
+    int64_t tx_orientation, rx_orientation;  /* 0 rows (lateral y), 1 columns (lateral x) */
+    int64_t dims[3];                          /* nx, ny, nz */
+    int64_t has_voxel_transform, has_xdc_transform;
+    double fs, c, t0;
+    double tx_pitch, rx_pitch;
+    double f_number;
+    double out_min[3], out_max[3];
+    double voxel_transform[16];               /* row-major, index -> world */
+    double xdc_transform[16];                 /* row-major, world -> array */
+} oracle_geom;
+
+int oracle_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ---------------------------------------------------------------- decode */
+
+void oracle_hadamard(int64_t n, int8_t* H) {
+    for (int64_t k = 0; k < n; ++k)
+        for (int64_t i = 0; i < n; ++i)
+            H[k * n + i] = (__builtin_popcountll((unsigned long long)(k & i)) & 1) ? -1 : 1;
+}
+
+/* D[i][c] = sum_k H[k][i] S[k][c]; S is [n][n_cols] int16, D is [n][n_cols] int64. */
+void oracle_decode(int64_t n, int64_t n_cols, const int16_t* S, const int8_t* H, int64_t* D) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t* out = D + i * n_cols;
+        for (int64_t c = 0; c < n_cols; ++c) out[c] = 0;
+        for (int64_t k = 0; k < n; ++k) {
+            const int64_t h = (int64_t)H[k * n + i];
+            const int16_t* row = S + k * n_cols;
+            for (int64_t c = 0; c < n_cols; ++c) out[c] += h * (int64_t)row[c];
+        }
+    }
+}
+
+/* ------------------------------------------------------------- geometry */
+
+static void voxel_position(const oracle_geom* g, int64_t v, double q[3]) {
+    const int64_t nx = g->dims[0], ny = g->dims[1];
+    const int64_t ix = v % nx, iy = (v / nx) % ny, iz = v / (nx * ny);
+    const double idx[3] = {(double)ix, (double)iy, (double)iz};
+    double p[3];
+    if (g->has_voxel_transform) {
+        for (int r = 0; r < 3; ++r) {
+            const double* m = g->voxel_transform + 4 * r;
+            p[r] = m[0] * idx[0] + m[1] * idx[1] + m[2] * idx[2] + m[3];
+        }
+    } else {
+        for (int d = 0; d < 3; ++d) {
+            if (g->dims[d] > 1)
+                p[d] = g->out_min[d] + idx[d] * (g->out_max[d] - g->out_min[d]) / (double)(g->dims[d] - 1);
+            else
+                p[d] = g->out_min[d];
+        }
+    }
+    if (g->has_xdc_transform) {
+        for (int r = 0; r < 3; ++r) {
+            const double* m = g->xdc_transform + 4 * r;
+            q[r] = m[0] * p[0] + m[1] * p[1] + m[2] * p[2] + m[3];
+        }
+    } else {
+        q[0] = p[0]; q[1] = p[1]; q[2] = p[2];
+    }
+}
+
+static double lateral(const double q[3], int64_t orientation) {
+    return orientation == 0 ? q[1] : q[0];
+}
+
+static double element_position(int64_t index, int64_t count, double pitch) {
+    return ((double)index - (double)(count - 1) / 2.0) * pitch;
+}
+
+/* Eq. (3) evaluated at u = F# |delta| / |z|, with the support test written
+ * as F# |delta| < 0.5 |z|. */
+static double window_weight(double f_number, double delta, double z) {
+    if (f_number <= 0.0) return 1.0;
+    const double a = f_number * fabs(delta);
+    if (!(a < 0.5 * fabs(z))) return 0.0;
+    const double cs = cos(M_PI * a / fabs(z));
+    return cs * cs;
+}
+
+/* r at fractional sample s: (1-f) r[n] + f r[n+1], n = floor(s), zero outside. */
+static double sample_linear(const double* trace, int64_t n_s, double s) {
+    const double fl = floor(s);
+    const double f = s - fl;
+    const int64_t n = (int64_t)fl;
+    const double a = (n >= 0 && n < n_s) ? trace[n] : 0.0;
+    const double b = (n + 1 >= 0 && n + 1 < n_s) ? trace[n + 1] : 0.0;
+    return (1.0 - f) * a + f * b;
+}
+
+/* ------------------------------------------------------------------ DAS */
+
+/* rf: [n_planes][n_tx][n_ch][n_s] doubles; w: [n_ch] or NULL; c > 0.
+ * vox: n_vox voxel linear indices (z-major, x fastest) or NULL for all voxels
+ * (then n_vox must equal nx*ny*nz). out: [n_planes][n_vox]. */
+void oracle_das(const oracle_geom* g, const double* rf, int64_t n_planes, const double* w,
+                double c, int64_t n_vox, const int64_t* vox, double* out) {
+    const int64_t n_tx = g->n_tx, n_ch = g->n_ch, n_s = g->n_samples;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < n_vox; ++t) {
+        const int64_t v = vox ? vox[t] : t;
+        double q[3];
+        voxel_position(g, v, q);
+        const double lat_tx = lateral(q, g->tx_orientation);
+        const double lat_rx = lateral(q, g->rx_orientation);
+        for (int64_t p = 0; p < n_planes; ++p) {
+            double acc = 0.0;
+            for (int64_t i = 0; i < n_tx; ++i) {
+                const double dx_t = lat_tx - element_position(i, n_tx, g->tx_pitch);
+                const double d_tx = sqrt(dx_t * dx_t + q[2] * q[2]);
+                for (int64_t j = 0; j < n_ch; ++j) {
+                    const double dx_r = lat_rx - element_position(j, n_ch, g->rx_pitch);
+                    const double d_rx = sqrt(dx_r * dx_r + q[2] * q[2]);
+                    const double a = (w ? w[j] : 1.0) * window_weight(g->f_number, dx_r, q[2]);
+                    if (a == 0.0) continue;
+                    const double tof = (d_tx + d_rx) / c;
+                    const double s = (tof - g->t0) * g->fs;
+                    const double* trace = rf + ((p * n_tx + i) * n_ch + j) * n_s;
+                    acc += a * sample_linear(trace, n_s, s);
+                }
+            }
+            out[p * n_vox + t] = acc;
+        }
+    }
+}
+
+/* Gradients of L with dL/dHR = G (G: [n_planes][nx*ny*nz], all voxels):
+ *   grad_rf[p][i][j][n] = sum_v a_j(v) G_p(v) dlerp/dr[n]
+ *   grad_c              = sum_p sum_v sum_ij a_j(v) G_p(v) (r[n+1] - r[n]) ds/dc,
+ *                         ds/dc = -(d_tx + d_rx) fs / c^2
+ *   grad_w[j]           = sum_p sum_v sum_i W_j(v) G_p(v) lerp(r_ij, s)
+ * with n = floor(s) (the right derivative at integer s). Any output may be NULL.
+ * Parallel over transmits: each thread owns grad_rf rows of its transmits. */
+void oracle_das_grad(const oracle_geom* g, const double* rf, int64_t n_planes, const double* w,
+                     double c, const double* G, double* grad_rf, double* grad_c, double* grad_w) {
+    const int64_t n_tx = g->n_tx, n_ch = g->n_ch, n_s = g->n_samples;
+    const int64_t n_vox = g->dims[0] * g->dims[1] * g->dims[2];
+    if (grad_rf) memset(grad_rf, 0, sizeof(double) * (size_t)(n_planes * n_tx * n_ch * n_s));
+    double gc_total = 0.0;
+    double* gw_total = (double*)calloc((size_t)n_ch, sizeof(double));
+#pragma omp parallel
+    {
+        double gc = 0.0;
+        double* gw = (double*)calloc((size_t)n_ch, sizeof(double));
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t i = 0; i < n_tx; ++i) {
+            for (int64_t v = 0; v < n_vox; ++v) {
+                double q[3];
+                voxel_position(g, v, q);
+                const double lat_tx = lateral(q, g->tx_orientation);
+                const double lat_rx = lateral(q, g->rx_orientation);
+                const double dx_t = lat_tx - element_position(i, n_tx, g->tx_pitch);
+                const double d_tx = sqrt(dx_t * dx_t + q[2] * q[2]);
+                for (int64_t j = 0; j < n_ch; ++j) {
+                    const double dx_r = lat_rx - element_position(j, n_ch, g->rx_pitch);
+                    const double d_rx = sqrt(dx_r * dx_r + q[2] * q[2]);
+                    const double W = window_weight(g->f_number, dx_r, q[2]);
+                    if (W == 0.0) continue;
+                    const double a = (w ? w[j] : 1.0) * W;
+                    const double s = ((d_tx + d_rx) / c - g->t0) * g->fs;
+                    const double dsdc = -(d_tx + d_rx) * g->fs / (c * c);
+                    const double fl = floor(s);
+                    const double f = s - fl;
+                    const int64_t n = (int64_t)fl;
+                    for (int64_t p = 0; p < n_planes; ++p) {
+                        const double Gv = G[p * n_vox + v];
+                        if (Gv == 0.0) continue;
+                        const int64_t base = ((p * n_tx + i) * n_ch + j) * n_s;
+                        const double* trace = rf + base;
+                        const double r0 = (n >= 0 && n < n_s) ? trace[n] : 0.0;
+                        const double r1 = (n + 1 >= 0 && n + 1 < n_s) ? trace[n + 1] : 0.0;
+                        if (grad_rf) {
+                            if (n >= 0 && n < n_s) grad_rf[base + n] += a * Gv * (1.0 - f);
+                            if (n + 1 >= 0 && n + 1 < n_s) grad_rf[base + n + 1] += a * Gv * f;
+                        }
+                        gc += a * Gv * (r1 - r0) * dsdc;
+                        gw[j] += W * Gv * ((1.0 - f) * r0 + f * r1);
+                    }
+                }
+            }
+        }
+#pragma omp critical
+        {
+            gc_total += gc;
+            for (int64_t j = 0; j < n_ch; ++j) gw_total[j] += gw[j];
+        }
+        free(gw);
+    }
+    if (grad_c) *grad_c = gc_total;
+    if (grad_w) for (int64_t j = 0; j < n_ch; ++j) grad_w[j] = gw_total[j];
+    free(gw_total);
+}

@@ -1,0 +1,293 @@
+"""Pins of the FP64 CPU oracle against facts that do not come from the oracle
+itself: textbook Hadamard values and identities, hand-computed times of
+flight, closed forms of the DAS sum for constant and ramp data, symmetry,
+exact linearity, brute force, and the adjoint identity. CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import twin
+import synth
+from synth import Geometry, MM, ROWS, COLUMNS
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_rows(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append([float(v) for v in line.split()])
+    return rows
+
+
+# ------------------------------------------------------------- Hadamard
+
+def test_hadamard_h4_golden():
+    expect = np.array(_golden_rows("hadamard_sylvester_h4.txt"), dtype=np.int8)
+    np.testing.assert_array_equal(oracle.hadamard(4), expect)
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 8, 16, 32, 64, 128, 256])
+def test_hadamard_orthogonal(n):
+    H = oracle.hadamard(n).astype(np.int64)
+    np.testing.assert_array_equal(H @ H.T, n * np.eye(n, dtype=np.int64))
+    np.testing.assert_array_equal(H, H.T)                     # Sylvester H is symmetric
+    assert set(np.unique(H)) <= {-1, 1}
+
+
+@pytest.mark.parametrize("n", [2, 8, 64, 256])
+def test_hadamard_matches_kronecker_construction(n):
+    # the popcount form and the doubling construction are the same matrix
+    np.testing.assert_array_equal(oracle.hadamard(n).astype(np.int64), synth.sylvester_kron(n))
+
+
+# --------------------------------------------------------------- decode
+
+@pytest.mark.parametrize("n,cols", [(32, 1), (32, 1000), (64, 777), (128, 4096), (256, 96)])
+def test_decode_brute_force(n, cols):
+    rng = np.random.default_rng(n * 7 + cols)
+    S = rng.integers(-32768, 32768, size=(n, cols)).astype(np.int16)
+    D = oracle.decode(S)
+    H = synth.sylvester_kron(n)
+    np.testing.assert_array_equal(D, H.T @ S.astype(np.int64))
+
+
+def test_decode_twin_tiny():
+    rng = np.random.default_rng(3)
+    S = rng.integers(-32768, 32768, size=(8, 5)).astype(np.int16)
+    np.testing.assert_array_equal(oracle.decode(S), np.array(twin.decode(S.astype(int).tolist())))
+
+
+@pytest.mark.parametrize("n", [32, 64, 128, 256])
+def test_decode_round_trip_recovers_unencoded(n):
+    # integer un-encoded data r small enough that the encoded s = H r fits
+    # int16; decoding must return n * r bit-exactly (H^T H = n I)
+    rng = np.random.default_rng(n)
+    lim = 32767 // n
+    r = rng.integers(-lim, lim + 1, size=(n, 3, 50)).astype(np.int64)
+    H = synth.sylvester_kron(n)
+    s = np.einsum("ki,ics->kcs", H, r)
+    assert np.abs(s).max() <= 32767
+    D = oracle.decode(s.astype(np.int16))
+    np.testing.assert_array_equal(D, n * r)
+
+
+def test_decode_custom_matrix():
+    # any +-1 matrix: a column-sign-flipped, row-permuted Sylvester matrix
+    rng = np.random.default_rng(11)
+    H = synth.sylvester_kron(32)[rng.permutation(32)] * rng.choice([-1, 1], 32)[None, :]
+    S = rng.integers(-32768, 32768, size=(32, 100)).astype(np.int16)
+    D = oracle.decode(S, H.astype(np.int8))
+    np.testing.assert_array_equal(D, H.T @ S.astype(np.int64))
+
+
+def test_decoded_dtype_rounding():
+    n = 128
+    D = np.array([2049 * n, 2051 * n, -2049 * n, 3 * n + 64, 2**22, -(2**22)], dtype=np.int64)
+    f16 = oracle.decoded_as(D, n, "f16").astype(np.float64)
+    # float16 keeps 11 significant bits: 2049 and 2051 are ties -> nearest even
+    np.testing.assert_array_equal(f16[:3], [2048.0, 2052.0, -2048.0])
+    assert f16[3] == 3.5
+    f32 = oracle.decoded_as(D, n, "f32").astype(np.float64)
+    np.testing.assert_array_equal(f32 * n, D.astype(np.float64))   # exact
+    np.testing.assert_array_equal(oracle.decoded_as(D, n, "i32"), D.astype(np.int32))
+
+
+# ------------------------------------------------------------------ DAS
+
+def _point_geom(x, y, z, t0=0.0, n_s=1000):
+    return Geometry(n_tx=1, n_ch=1, n_samples=n_s, fs=10e6, c=1500.0, t0=t0,
+                    tx_orientation=ROWS, rx_orientation=COLUMNS,
+                    out_dims=(1, 1, 1), out_min=(x, y, z), out_max=(x, y, z))
+
+
+def test_hand_computed_time_of_flight():
+    for x, y, z, t0_us, expect in _golden_rows("pythagorean_tof.txt"):
+        g = _point_geom(x * MM, y * MM, z * MM, t0=t0_us * 1e-6)
+        ramp = np.arange(g.n_samples, dtype=np.float64).reshape(1, 1, -1)
+        img = oracle.das(g, ramp)
+        assert img.ravel()[0] == pytest.approx(expect, rel=0, abs=1e-9)
+
+
+def test_orientation_swap_uses_the_other_coordinate():
+    # transmit on columns (lateral x) and receive on rows (lateral y): the
+    # 3-4-5 voxel (x=3, y=0, z=4) now has d_tx = 5, d_rx = 4 -> still s = 60,
+    # while (x=3, y=3, z=4) gives 5 + 5 = 10 mm -> s = 66.67
+    g = _point_geom(3 * MM, 3 * MM, 4 * MM)
+    g.tx_orientation, g.rx_orientation = COLUMNS, ROWS
+    ramp = np.arange(g.n_samples, dtype=np.float64).reshape(1, 1, -1)
+    assert oracle.das(g, ramp).ravel()[0] == pytest.approx(10e-3 / 1500 * 10e6, abs=1e-9)
+
+
+def test_fractional_sample_weights():
+    # s = 60 + 1/4 -> weights 3/4 on sample 60 and 1/4 on sample 61
+    g = _point_geom(3 * MM, 0.0, 4 * MM, t0=-0.025e-6)
+    for n, expect in ((60, 0.75), (61, 0.25), (59, 0.0), (62, 0.0)):
+        r = np.zeros((1, 1, g.n_samples))
+        r[0, 0, n] = 1.0
+        assert oracle.das(g, r).ravel()[0] == pytest.approx(expect, abs=1e-12)
+
+
+def test_zero_outside_record():
+    g = _point_geom(3 * MM, 0.0, 4 * MM, n_s=60)   # s = 60 is one past the last sample
+    r = np.ones((1, 1, 60))
+    assert oracle.das(g, r).ravel()[0] == 0.0
+    g = _point_geom(3 * MM, 0.0, 4 * MM, t0=6.05e-6, n_s=10)   # s = -0.5: half of r[0]
+    assert oracle.das(g, np.ones((1, 1, 10))).ravel()[0] == pytest.approx(0.5, abs=1e-12)
+
+
+def _small_geom(n_tx=4, n_ch=4, n_s=256, dims=(5, 1, 6), fnum=0.0):
+    return Geometry(n_tx=n_tx, n_ch=n_ch, n_samples=n_s, fs=30e6, c=1540.0,
+                    out_dims=dims, out_min=(-1 * MM, 0.0, 2 * MM), out_max=(1 * MM, 0.0, 4 * MM),
+                    f_number=fnum)
+
+
+def test_constant_rf_closed_form():
+    g = _small_geom()
+    img = oracle.das(g, np.ones((g.n_tx, g.n_ch, g.n_samples)))
+    np.testing.assert_allclose(img, g.n_tx * g.n_ch, rtol=0, atol=1e-12)
+
+
+def test_constant_rf_hanning_closed_form():
+    # receive columns at x = -0.5 mm and +0.5 mm (pitch 1 mm, 2 channels),
+    # voxel at x = 0, z = 1 mm, F# = 0.5: u = 0.5 * 0.5 / 1 = 0.25 ->
+    # W = cos^2(pi/4) = 1/2 per channel; two channels, one transmit -> 1.0
+    g = Geometry(n_tx=1, n_ch=2, n_samples=400, fs=30e6, c=1540.0,
+                 rx_pitch=1 * MM, out_dims=(1, 1, 1), out_min=(0.0, 0.0, 1 * MM),
+                 out_max=(0.0, 0.0, 1 * MM), f_number=0.5)
+    assert oracle.das(g, np.ones((1, 2, 400))).ravel()[0] == pytest.approx(1.0, abs=1e-12)
+    g.f_number = 1.0      # u = 0.5: outside the window
+    assert oracle.das(g, np.ones((1, 2, 400))).ravel()[0] == 0.0
+    # per-channel weights multiply the window
+    g.f_number = 0.5
+    assert oracle.das(g, np.ones((1, 2, 400)), w=np.array([3.0, -1.0])).ravel()[0] == \
+        pytest.approx(1.0, abs=1e-12)
+
+
+def test_twin_matches_oracle_on_tiny_grid():
+    g = _small_geom(fnum=0.7)
+    rng = np.random.default_rng(5)
+    rf = rng.normal(size=(g.n_tx, g.n_ch, g.n_samples))
+    w = rng.uniform(0.5, 1.5, g.n_ch)
+    a = oracle.das(g, rf, w=w, c=1500.0).ravel()
+    b = np.array(twin.das(g, rf, w=w, c=1500.0))
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-12 * np.abs(b).max())
+
+
+def test_listed_voxels_match_full_image():
+    g = _small_geom(dims=(7, 3, 5))
+    rng = np.random.default_rng(6)
+    rf = rng.normal(size=(g.n_tx, g.n_ch, g.n_samples))
+    full = oracle.das(g, rf).ravel()
+    vox = np.array([0, 3, 17, 50, 104])
+    np.testing.assert_array_equal(oracle.das(g, rf, voxels=vox), full[vox])
+
+
+def test_linearity_and_complex_planes():
+    g = _small_geom()
+    rng = np.random.default_rng(7)
+    r1 = rng.normal(size=(g.n_tx, g.n_ch, g.n_samples))
+    r2 = rng.normal(size=(g.n_tx, g.n_ch, g.n_samples))
+    lhs = oracle.das(g, 2.0 * r1 - 3.0 * r2)
+    rhs = 2.0 * oracle.das(g, r1) - 3.0 * oracle.das(g, r2)
+    np.testing.assert_allclose(lhs, rhs, rtol=1e-12, atol=1e-12)
+    cimg = oracle.das(g, r1 + 1j * r2)
+    np.testing.assert_allclose(cimg.real, oracle.das(g, r1), rtol=1e-15)
+    np.testing.assert_allclose(cimg.imag, oracle.das(g, r2), rtol=1e-15)
+
+
+def _scatterer_on_node(orientation_swap=False):
+    g = Geometry(n_tx=32, n_ch=32, n_samples=1024, hadamard_order=32,
+                 out_dims=(41, 1, 41), out_min=(-2 * MM, 0.0, 8 * MM),
+                 out_max=(2 * MM, 0.0, 12 * MM))
+    node = (27, 0, 13)         # x = 0.7 mm, z = 9.3 mm
+    p = [g.out_min[d] + node[d] * (g.out_max[d] - g.out_min[d]) / max(g.out_dims[d] - 1, 1)
+         for d in range(3)]
+    frame = synth.make_frame(g, seed=0, n_scatterers=1, box_x=(p[0], p[0]),
+                             box_z=(p[2], p[2]), noise_frac=0.0)
+    return g, node, frame
+
+
+def test_point_scatterer_peaks_at_its_voxel():
+    g, node, frame = _scatterer_on_node()
+    D = oracle.decode(frame.rf)
+    r = oracle.decoded_as(D, g.n_tx, "f32").astype(np.float64)
+    env = np.abs(oracle.das(g, r))
+    iz, iy, ix = np.unravel_index(np.argmax(env), env.shape)
+    assert (ix, iy, iz) == node
+
+
+def test_mirror_symmetry_about_x0():
+    # a scatterer on the axis gives receive data symmetric under j -> n-1-j;
+    # on a grid symmetric about x = 0 the image is then mirror symmetric
+    g = Geometry(n_tx=8, n_ch=8, n_samples=512, out_dims=(9, 1, 7),
+                 out_min=(-1 * MM, 0.0, 4 * MM), out_max=(1 * MM, 0.0, 6 * MM))
+    frame = synth.make_frame(g, seed=0, n_scatterers=1, box_x=(0.0, 0.0),
+                             box_z=(5 * MM, 5 * MM), noise_frac=0.0)
+    r = frame.decoded.astype(np.float64)
+    np.testing.assert_allclose(r, r[:, ::-1, :], atol=1e-6)
+    img = oracle.das(g, r)
+    np.testing.assert_allclose(img, img[:, :, ::-1], rtol=1e-9, atol=1e-9 * np.abs(img).max())
+
+
+# ------------------------------------------------------------- gradients
+
+def test_adjoint_dot_product_identity():
+    # <DAS(r), G> == <r, DAS^T(G)>: the RF gradient is the exact adjoint
+    g = _small_geom(fnum=0.8)
+    rng = np.random.default_rng(8)
+    r = rng.normal(size=(g.n_tx, g.n_ch, g.n_samples))
+    G = rng.normal(size=(g.out_dims[2], g.out_dims[1], g.out_dims[0]))
+    w = rng.uniform(0.5, 1.5, g.n_ch)
+    lhs = float(np.sum(oracle.das(g, r, w=w) * G))
+    grad_rf, _, _ = oracle.das_grad(g, r, G, w=w)
+    rhs = float(np.sum(r * grad_rf))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_apodization_gradient_is_exact_for_linear_loss():
+    # L = <DAS(r; w), G> is linear in w, so dL/dw_j = <DAS(r; e_j), G>
+    g = _small_geom(fnum=0.6)
+    rng = np.random.default_rng(9)
+    r = rng.normal(size=(g.n_tx, g.n_ch, g.n_samples))
+    G = rng.normal(size=(g.out_dims[2], 1, g.out_dims[0]))
+    _, _, gw = oracle.das_grad(g, r, G, w=rng.uniform(0.5, 1.5, g.n_ch))
+    for j in range(g.n_ch):
+        e = np.zeros(g.n_ch)
+        e[j] = 1.0
+        assert gw[j] == pytest.approx(float(np.sum(oracle.das(g, r, w=e) * G)), rel=1e-12, abs=1e-12)
+
+
+def test_speed_of_sound_gradient_matches_small_step_difference():
+    # a step of 1e-9 relative moves no sample across an integer here, so the
+    # central difference of the piecewise-linear interpolant is exact up to
+    # rounding
+    g = _small_geom()
+    rng = np.random.default_rng(10)
+    r = rng.normal(size=(g.n_tx, g.n_ch, g.n_samples))
+    G = rng.normal(size=(g.out_dims[2], 1, g.out_dims[0]))
+    c = 1530.0
+    _, gc, _ = oracle.das_grad(g, r, G, c=c, want_rf=False)
+    h = c * 1e-9
+    fd = (np.sum(oracle.das(g, r, c=c + h) * G) - np.sum(oracle.das(g, r, c=c - h) * G)) / (2 * h)
+    assert gc == pytest.approx(fd, rel=1e-5)
+
+
+def test_complex_gradient_planes():
+    g = _small_geom()
+    rng = np.random.default_rng(12)
+    r = rng.normal(size=(g.n_tx, g.n_ch, g.n_samples)) + 1j * rng.normal(size=(g.n_tx, g.n_ch, g.n_samples))
+    G = rng.normal(size=(g.out_dims[2], 1, g.out_dims[0])) + 1j * rng.normal(size=(g.out_dims[2], 1, g.out_dims[0]))
+    grc, gcc, gwc = oracle.das_grad(g, r, G)
+    gr_re, gc_re, gw_re = oracle.das_grad(g, r.real, G.real)
+    gr_im, gc_im, gw_im = oracle.das_grad(g, r.imag, G.imag)
+    np.testing.assert_allclose(grc.real, gr_re, atol=1e-12)
+    np.testing.assert_allclose(grc.imag, gr_im, atol=1e-12)
+    assert gcc == pytest.approx(gc_re + gc_im, rel=1e-12)
+    np.testing.assert_allclose(gwc, gw_re + gw_im, rtol=1e-12)
