@@ -120,8 +120,10 @@ typedef struct rcbf_params {
     uint32_t decode_variant;  /* enum rcbf_decode_variant */
     uint32_t das_variant;     /* enum rcbf_das_variant */
     uint32_t out_dims[3];     /* nx, ny, nz (>= 1 each) */
-    uint32_t tile[3];         /* DAS voxel tile (bx, by, bz); all 0 = choose automatically.
-                                 bx*by*bz must be 1024 when given. */
+    uint32_t tile[3];         /* DAS voxel tile (bu, bv, bw); all 0 = choose automatically.
+                                 bu (32, 64 or 128) runs along the image axis parallel to the
+                                 transmit line elements (x for rows, y for columns), bv along
+                                 the other lateral image axis, bw along z; bu*bv*bw = 1024. */
     uint32_t reserved;
     double   fs;              /* sampling rate [Hz] */
     double   c;               /* speed of sound [m/s] (DAS may override per call) */

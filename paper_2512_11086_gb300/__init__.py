@@ -1,0 +1,257 @@
+"""GB300 row-column / TOBE beamformer hot path: Python binding of librcbf.so.
+
+This module only marshals arguments for the C ABI declared in
+``include/rcbf.h``: every step of the path (decode, DAS, its adjoint, the
+batched persistent launch) runs in the library's CUDA kernels. PyTorch
+provides device memory and the current CUDA stream. There is no CPU fallback:
+if the compiled library is missing, importing the binding raises.
+
+Names follow the paper (Palamar et al., arXiv 2512.11086): ``decode`` is the
+Hadamard aperture decode (§THEORY "Synthetic Aperture Imaging",
+§OPTIMIZATIONS "Decoding"), ``das`` the delay-and-sum of Eq. (1) with the
+receive apodization of Eq. (2)-(3) (§OPTIMIZATIONS "DAS").
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librcbf.so")
+
+# ---- constants mirrored from rcbf.h
+OK, EINVAL, EUNSUPPORTED, ECUDA, ENOMEM, ETIMEOUT = 0, -1, -2, -3, -4, -5
+I16, I32, F32, F16, CF32 = 0, 1, 2, 3, 4
+FORCES, HERCULES = 0, 1
+ROWS, COLUMNS = 0, 1
+LINEAR = 0
+DECODE_MMA_I8, DECODE_PLAIN = 0, 1
+DAS_TILED, DAS_PLAIN = 0, 1
+
+_DTYPE_NAMES = {"i32": I32, "f32": F32, "f16": F16, "cf32": CF32}
+
+
+class RcbfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("rcbf error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    """ctypes mirror of ``rcbf_params`` (field order and types as in rcbf.h)."""
+    _fields_ = [
+        ("n_tx", ctypes.c_uint32), ("n_ch", ctypes.c_uint32), ("n_samples", ctypes.c_uint32),
+        ("hadamard_order", ctypes.c_uint32), ("acq_kind", ctypes.c_uint32),
+        ("tx_orientation", ctypes.c_uint32), ("rx_orientation", ctypes.c_uint32),
+        ("decoded_dtype", ctypes.c_uint32), ("interp", ctypes.c_uint32),
+        ("decode_variant", ctypes.c_uint32), ("das_variant", ctypes.c_uint32),
+        ("out_dims", ctypes.c_uint32 * 3), ("tile", ctypes.c_uint32 * 3), ("reserved", ctypes.c_uint32),
+        ("fs", ctypes.c_double), ("c", ctypes.c_double), ("t0", ctypes.c_double), ("fc", ctypes.c_double),
+        ("tx_pitch", ctypes.c_double), ("rx_pitch", ctypes.c_double),
+        ("xdc_transform", ctypes.c_double * 16),
+        ("out_min", ctypes.c_double * 3), ("out_max", ctypes.c_double * 3),
+        ("voxel_transform", ctypes.c_double * 16),
+        ("f_number", ctypes.c_double),
+        ("decode_matrix", ctypes.c_void_p),
+    ]
+
+
+# symbol -> (restype, argtypes); every function rcbf.h declares
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "rcbf_plan": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(_P)]),
+    "rcbf_destroy": (None, [_P]),
+    "rcbf_decode": (ctypes.c_int, [_P, _P, _P, _P]),
+    "rcbf_das": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, _P, _P]),
+    "rcbf_das_backward": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, _P, _P, _P, _P, _P]),
+    "rcbf_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_uint32, ctypes.POINTER(_P),
+                                         ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "rcbf_batch_run": (ctypes.c_int, [_P, _P]),
+    "rcbf_batch_status": (ctypes.c_int, [_P, _P]),
+    "rcbf_batch_destroy": (None, [_P]),
+    "rcbf_last_error": (ctypes.c_char_p, []),
+    "rcbf_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load librcbf.so (build it first with ``paper_2512_11086_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("librcbf.so is not built (%s); run __graft_entry__.build() or "
+                          "python paper_2512_11086_gb300/build.py" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != OK:
+        raise RcbfError(code, load_library().rcbf_last_error().decode())
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def make_params(g, decoded_dtype="f32", decode_variant=DECODE_MMA_I8, das_variant=DAS_TILED,
+                tile=None, f_number=None, xdc_transform=None, voxel_transform=None) -> Params:
+    """Parameter block from any object with the geometry attributes (n_tx,
+    n_ch, n_samples, fs, c, t0, fc, pitches, orientations, hadamard_order,
+    out_dims, out_min, out_max, f_number)."""
+    p = Params()
+    p.n_tx, p.n_ch, p.n_samples = int(g.n_tx), int(g.n_ch), int(g.n_samples)
+    p.hadamard_order = int(getattr(g, "hadamard_order", 0))
+    p.acq_kind = int(getattr(g, "acq_kind", FORCES))
+    p.tx_orientation, p.rx_orientation = int(g.tx_orientation), int(g.rx_orientation)
+    p.decoded_dtype = _DTYPE_NAMES[decoded_dtype] if isinstance(decoded_dtype, str) else int(decoded_dtype)
+    p.interp = LINEAR
+    p.decode_variant, p.das_variant = int(decode_variant), int(das_variant)
+    for d in range(3):
+        p.out_dims[d] = int(g.out_dims[d])
+        p.out_min[d] = float(g.out_min[d])
+        p.out_max[d] = float(g.out_max[d])
+    if tile is not None:
+        for d in range(3):
+            p.tile[d] = int(tile[d])
+    p.fs, p.c, p.t0, p.fc = float(g.fs), float(g.c), float(g.t0), float(getattr(g, "fc", 0.0))
+    p.tx_pitch, p.rx_pitch = float(g.tx_pitch), float(g.rx_pitch)
+    p.f_number = float(g.f_number if f_number is None else f_number)
+    if xdc_transform is not None:
+        for k, v in enumerate([float(x) for row in xdc_transform for x in row]):
+            p.xdc_transform[k] = v
+    if voxel_transform is not None:
+        for k, v in enumerate([float(x) for row in voxel_transform for x in row]):
+            p.voxel_transform[k] = v
+    return p
+
+
+class Plan:
+    """Owns an ``rcbf_plan_t``. Device buffers are torch CUDA tensors."""
+
+    def __init__(self, params: Params, decode_matrix=None):
+        lib = load_library()
+        self._keep = None
+        if decode_matrix is not None:
+            import numpy as np
+            m = np.ascontiguousarray(decode_matrix, dtype=np.int8)
+            self._keep = m
+            params.decode_matrix = m.ctypes.data
+        h = ctypes.c_void_p()
+        _check(lib.rcbf_plan(ctypes.byref(params), ctypes.byref(h)))
+        params.decode_matrix = None
+        self.handle = h
+        self.params = params
+
+    # sizes
+    @property
+    def rf_shape(self):
+        p = self.params
+        return (p.n_tx, p.n_ch, p.n_samples)
+
+    @property
+    def image_shape(self):
+        p = self.params
+        return (p.out_dims[2], p.out_dims[1], p.out_dims[0])
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().rcbf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def decoded_torch_dtype(self):
+        import torch
+        return {I32: torch.int32, F32: torch.float32, F16: torch.float16, CF32: torch.float32}[
+            self.params.decoded_dtype]
+
+    def decode(self, rf, out=None, stream=None):
+        """rcbf_decode: int16 [n_tx][n_ch][n_s] CUDA tensor -> decoded tensor."""
+        import torch
+        if out is None:
+            out = torch.empty(self.rf_shape, dtype=self.decoded_torch_dtype(), device=rf.device)
+        _check(load_library().rcbf_decode(self.handle, _ptr(rf), _ptr(out), _stream(stream)))
+        return out
+
+    def das(self, decoded, apod=None, c: float = 0.0, out=None, stream=None):
+        """rcbf_das: decoded RF -> float32 image [nz][ny][nx] (two planes for complex)."""
+        import torch
+        if out is None:
+            shape = self.image_shape
+            if self.params.decoded_dtype == CF32:
+                shape = (2,) + shape
+            out = torch.empty(shape, dtype=torch.float32, device=decoded.device)
+        _check(load_library().rcbf_das(self.handle, _ptr(decoded), _ptr(apod), ctypes.c_float(c),
+                                       _ptr(out), _stream(stream)))
+        return out
+
+    def das_backward(self, decoded, grad_image, apod=None, c: float = 0.0, want_rf=True,
+                     want_c=True, want_apod=True, stream=None):
+        """rcbf_das_backward: (grad_rf, grad_c, grad_apod) for dL/dimage."""
+        import torch
+        dev = decoded.device
+        grad_rf = torch.empty_like(decoded, dtype=torch.float32) if want_rf else None
+        grad_c = torch.empty((), dtype=torch.float32, device=dev) if want_c else None
+        grad_apod = torch.empty(self.params.n_ch, dtype=torch.float32, device=dev) if want_apod else None
+        _check(load_library().rcbf_das_backward(self.handle, _ptr(decoded), _ptr(apod), ctypes.c_float(c),
+                                                _ptr(grad_image), _ptr(grad_rf), _ptr(grad_c),
+                                                _ptr(grad_apod), _stream(stream)))
+        return grad_rf, grad_c, grad_apod
+
+
+class Batch:
+    """Owns an ``rcbf_batch_t``: frames bound to fixed device buffers, run as
+    one persistent launch (capturable in a CUDA graph)."""
+
+    def __init__(self, plans: Sequence[Plan], rf, decoded, images):
+        lib = load_library()
+        n = len(plans)
+        P = ctypes.c_void_p
+        self._plans = list(plans)
+        self._bufs = (list(rf), list(decoded), list(images))
+        arr = lambda xs: (P * n)(*[P(0 if x is None else x.data_ptr()) for x in xs])
+        hp = (P * n)(*[p.handle for p in plans])
+        h = P()
+        _check(lib.rcbf_batch_create(hp, n, arr(rf), arr(decoded), arr(images), ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(load_library().rcbf_batch_run(self.handle, _stream(stream)))
+
+    def status(self, stream=None) -> int:
+        return int(load_library().rcbf_batch_status(self.handle, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().rcbf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def version() -> str:
+    return load_library().rcbf_version().decode()

@@ -1,0 +1,364 @@
+// api.cu — the C ABI of include/rcbf.h: argument validation, plan
+// construction (geometry affine, decode fragments, DAS tile choice), error
+// reporting and dispatch to the kernels. Every check happens on the host
+// before a launch; on error nothing is enqueued.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace rcbf {
+
+namespace {
+thread_local std::string g_last_error;
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3u) == 0; }
+bool is_pow2(uint32_t n) { return n && !(n & (n - 1)); }
+bool all_zero(const double* m, int n) {
+    for (int k = 0; k < n; ++k) if (m[k] != 0.0) return false;
+    return true;
+}
+}  // namespace
+
+int set_error(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int check_launch(const char* what) {
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) return RCBF_OK;
+    return set_error(e == cudaErrorMemoryAllocation ? RCBF_ENOMEM : RCBF_ECUDA,
+                     std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+namespace {
+
+// A = H^T fragments of mma.m16n8k32 (row-major A, int8) in the k order that
+// ldmatrix.trans + byte permutes give the B fragments: fragment position p of
+// a k32 chunk holds acquisition 16*(p>>4) + 8*((p&3)>>1) + 2*((p>>2)&3) + (p&1).
+std::vector<uint32_t> build_afrag(const std::vector<int8_t>& H, int n) {
+    const int MT = n / 16, KC = n / 32;
+    std::vector<uint32_t> out((size_t)MT * KC * 32 * 4);
+    for (int mt = 0; mt < MT; ++mt)
+        for (int kc = 0; kc < KC; ++kc)
+            for (int lane = 0; lane < 32; ++lane) {
+                const int g = lane >> 2, t = lane & 3;
+                for (int r = 0; r < 4; ++r) {
+                    uint32_t word = 0;
+                    for (int m = 0; m < 4; ++m) {
+                        const int row = mt * 16 + g + ((r & 1) ? 8 : 0);
+                        const int pos = ((r >= 2) ? 16 : 0) + 4 * t + m;
+                        const int kk = 16 * (pos >> 4) + 8 * ((pos & 3) >> 1) + 2 * ((pos >> 2) & 3) + (pos & 1);
+                        const int k = kc * 32 + kk;
+                        const int8_t v = H[(size_t)k * n + row];    // A[row][k] = H[k][row]
+                        word |= (uint32_t)(uint8_t)v << (8 * m);
+                    }
+                    out[(((size_t)mt * KC + kc) * 32 + lane) * 4 + r] = word;
+                }
+            }
+    return out;
+}
+
+void mat_mul_3x4(const double* X /*4x4*/, const double* M /*4x4*/, double* G /*3x4*/) {
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 4; ++c) {
+            double s = 0;
+            for (int k = 0; k < 4; ++k) s += X[r * 4 + k] * M[k * 4 + c];
+            G[r * 4 + c] = s;
+        }
+}
+
+// Tile radius in the (lateral, z) plane of an element family: the largest
+// distance from the tile centre to a tile corner (distances to a line element
+// are 1-Lipschitz in that plane, so this bounds every delay offset).
+double tile_radius(const double* G, int lat_axis, int ua, int va, int bu, int bv, int bw) {
+    double best = 0;
+    for (int sx = -1; sx <= 1; sx += 2)
+        for (int sy = -1; sy <= 1; sy += 2)
+            for (int sz = -1; sz <= 1; sz += 2) {
+                const double du = sx * 0.5 * (bu - 1), dv = sy * 0.5 * (bv - 1), dw = sz * 0.5 * (bw - 1);
+                const double dl = G[lat_axis * 4 + ua] * du + G[lat_axis * 4 + va] * dv + G[lat_axis * 4 + 2] * dw;
+                const double dz = G[2 * 4 + ua] * du + G[2 * 4 + va] * dv + G[2 * 4 + 2] * dw;
+                best = std::fmax(best, std::sqrt(dl * dl + dz * dz));
+            }
+    return best;
+}
+
+int validate(const rcbf_params* p) {
+    if (!p) return set_error(RCBF_EINVAL, "rcbf_plan: params is NULL");
+    if (p->n_tx < 1 || p->n_tx > (uint32_t)kMaxOrder)
+        return set_error(RCBF_EINVAL, "rcbf_plan: n_tx must be in [1, 256]");
+    if (p->n_ch < 1 || p->n_ch > (uint32_t)kMaxChannels)
+        return set_error(RCBF_EINVAL, "rcbf_plan: n_ch must be in [1, 256]");
+    if (p->n_samples < 8 || p->n_samples % 8)
+        return set_error(RCBF_EINVAL, "rcbf_plan: n_samples must be a positive multiple of 8");
+    if (p->n_samples > (1u << 24))
+        return set_error(RCBF_EINVAL, "rcbf_plan: n_samples too large");
+    for (int d = 0; d < 3; ++d)
+        if (p->out_dims[d] < 1) return set_error(RCBF_EINVAL, "rcbf_plan: out_dims must be >= 1");
+    if ((double)p->out_dims[0] * p->out_dims[1] * p->out_dims[2] > 2147483647.0)
+        return set_error(RCBF_EINVAL, "rcbf_plan: too many voxels");
+    if (!(p->fs > 0) || !(p->c > 0)) return set_error(RCBF_EINVAL, "rcbf_plan: fs and c must be > 0");
+    if (!(p->f_number >= 0)) return set_error(RCBF_EINVAL, "rcbf_plan: f_number must be >= 0");
+    if (p->tx_orientation > 1 || p->rx_orientation > 1)
+        return set_error(RCBF_EINVAL, "rcbf_plan: orientation must be RCBF_ROWS or RCBF_COLUMNS");
+    if (p->acq_kind > 1) return set_error(RCBF_EINVAL, "rcbf_plan: unknown acq_kind");
+    if (p->interp != RCBF_LINEAR) return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: only linear interpolation is built");
+    if (p->decoded_dtype != RCBF_I32 && p->decoded_dtype != RCBF_F32 && p->decoded_dtype != RCBF_F16 &&
+        p->decoded_dtype != RCBF_CF32)
+        return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: decoded_dtype must be RCBF_I32, RCBF_F32, RCBF_F16 or RCBF_CF32");
+    if (p->decode_variant > RCBF_DECODE_PLAIN || p->das_variant > RCBF_DAS_PLAIN)
+        return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: unknown variant");
+    if (p->hadamard_order) {
+        if (p->hadamard_order != p->n_tx)
+            return set_error(RCBF_EINVAL, "rcbf_plan: hadamard_order must equal n_tx");
+        if (p->decoded_dtype == RCBF_CF32)
+            return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: complex data cannot be Hadamard-decoded");
+        if (!p->decode_matrix && !is_pow2(p->n_tx))
+            return set_error(RCBF_EINVAL, "rcbf_plan: a Sylvester order must be a power of two");
+        if (p->decode_variant == RCBF_DECODE_MMA_I8 && !(p->n_tx == 32 || p->n_tx == 64 || p->n_tx == 128 || p->n_tx == 256))
+            return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: the tensor-core decode needs n_tx in {32, 64, 128, 256}");
+        if (p->decode_variant == RCBF_DECODE_PLAIN && p->n_tx % 16)
+            return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: the plain decode needs n_tx a multiple of 16");
+        if (p->decode_matrix)
+            for (uint32_t q = 0; q < p->n_tx * p->n_tx; ++q)
+                if (p->decode_matrix[q] != 1 && p->decode_matrix[q] != -1)
+                    return set_error(RCBF_EINVAL, "rcbf_plan: decode_matrix entries must be +1 or -1");
+    }
+    const bool tile_given = p->tile[0] || p->tile[1] || p->tile[2];
+    if (tile_given) {
+        if (!(p->tile[0] == 32 || p->tile[0] == 64 || p->tile[0] == 128) ||
+            p->tile[1] < 1 || p->tile[2] < 1 || p->tile[0] * p->tile[1] * p->tile[2] != (uint32_t)kTileVoxels)
+            return set_error(RCBF_EINVAL, "rcbf_plan: tile must be (32|64|128, a, b) with product 1024");
+    }
+    return RCBF_OK;
+}
+
+}  // namespace
+}  // namespace rcbf
+
+using namespace rcbf;
+
+extern "C" {
+
+const char* rcbf_last_error(void) { return g_last_error.c_str(); }
+
+const char* rcbf_version(void) { return "rcbf 0.1 (sm_103a)"; }
+
+int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
+    g_last_error.clear();
+    if (!out_plan) return set_error(RCBF_EINVAL, "rcbf_plan: out_plan is NULL");
+    *out_plan = nullptr;
+    int rc = validate(params);
+    if (rc != RCBF_OK) return rc;
+
+    rcbf_plan_s* plan = new rcbf_plan_s();
+    PlanHost& h = plan->h;
+    h.p = *params;
+    h.p.decode_matrix = nullptr;   // the matrix is copied, never referenced later
+    const rcbf_params& p = h.p;
+
+    // ---- geometry: voxel index -> world (M), world -> array (X), G = X M
+    double M[16] = {0}, X[16] = {0}, G[12];
+    if (!all_zero(p.voxel_transform, 16)) {
+        std::memcpy(M, p.voxel_transform, sizeof(M));
+    } else {
+        for (int d = 0; d < 3; ++d) {
+            const double step = p.out_dims[d] > 1 ? (p.out_max[d] - p.out_min[d]) / (double)(p.out_dims[d] - 1) : 0.0;
+            M[d * 4 + d] = step;
+            M[d * 4 + 3] = p.out_min[d];
+        }
+        M[15] = 1.0;
+    }
+    if (!all_zero(p.xdc_transform, 16)) std::memcpy(X, p.xdc_transform, sizeof(X));
+    else { X[0] = X[5] = X[10] = X[15] = 1.0; }
+    mat_mul_3x4(X, M, G);
+
+    const int tx_axis = p.tx_orientation == RCBF_ROWS ? 1 : 0;
+    const int rx_axis = p.rx_orientation == RCBF_ROWS ? 1 : 0;
+    // lane axis u: an index axis along which neither the transmit lateral
+    // coordinate nor z changes (then the transmit delay depends on tile rows only)
+    auto tx_invariant = [&](int ax) {
+        const double scale = std::fabs(G[ax]) + std::fabs(G[4 + ax]) + std::fabs(G[8 + ax]);
+        return std::fabs(G[tx_axis * 4 + ax]) <= 1e-12 * scale && std::fabs(G[8 + ax]) <= 1e-12 * scale;
+    };
+    int ua = -1;
+    for (int ax = 0; ax < 2 && ua < 0; ++ax) if (tx_invariant(ax) && p.out_dims[ax] > 1) ua = ax;
+    for (int ax = 0; ax < 2 && ua < 0; ++ax) if (tx_invariant(ax)) ua = ax;
+    h.tiled_ok = ua >= 0 && p.n_ch % kCJ == 0 && p.n_tx % (p.decoded_dtype == RCBF_CF32 ? 4 : kCI) == 0;
+    if (ua < 0) ua = 0;
+    const int va = 1 - ua;
+    h.swap_uv = ua == 1;
+
+    DasArgs& a = h.das;
+    std::memset(&a, 0, sizeof(a));
+    for (int d = 0; d < 3; ++d) {
+        a.q0[d] = G[d * 4 + 3];
+        a.Gu[d] = G[d * 4 + ua];
+        a.Gv[d] = G[d * 4 + va];
+        a.Gw[d] = G[d * 4 + 2];
+    }
+    const long long strides[3] = {1, (long long)p.out_dims[0], (long long)p.out_dims[0] * p.out_dims[1]};
+    a.n_u = (int)p.out_dims[ua];
+    a.n_v = (int)p.out_dims[va];
+    a.n_w = (int)p.out_dims[2];
+    a.out_su = strides[ua];
+    a.out_sv = strides[va];
+    a.out_sw = strides[2];
+    a.n_tx = (int)p.n_tx;
+    a.n_ch = (int)p.n_ch;
+    a.n_s = (int)p.n_samples;
+    a.tx_axis = tx_axis;
+    a.rx_axis = rx_axis;
+    a.tx_pitch = p.tx_pitch;
+    a.rx_pitch = p.rx_pitch;
+    a.tx_e0 = -0.5 * (double)(p.n_tx - 1) * p.tx_pitch;
+    a.rx_e0 = -0.5 * (double)(p.n_ch - 1) * p.rx_pitch;
+    a.fs = p.fs;
+    a.f_number = (float)p.f_number;
+    a.dtype = (int)p.decoded_dtype;
+    a.scale = p.decoded_dtype == RCBF_I32 ? 1.0f / (float)p.n_tx : 1.0f;
+    a.plane_stride = (long long)p.n_tx * p.n_ch * p.n_samples;
+    a.image_plane = (long long)p.out_dims[0] * p.out_dims[1] * p.out_dims[2];
+
+    // ---- DAS tile: given, or the shape with the smallest window at the plan's c
+    auto radius_sum = [&](int bu, int bv, int bw) {
+        return tile_radius(G, tx_axis, ua, va, bu, bv, bw) + tile_radius(G, rx_axis, ua, va, bu, bv, bw);
+    };
+    int best_bu = 64, best_bv = 1, best_bw = 16;
+    if (p.tile[0]) {
+        best_bu = (int)p.tile[0];
+        // the given tile is in image axes (x, y, z); the lane axis is u
+        best_bv = (int)(ua == 0 ? p.tile[1] : p.tile[1]);
+        best_bw = (int)p.tile[2];
+    } else {
+        double best = 1e300;
+        const int bus[3] = {128, 64, 32};
+        for (int bi = 0; bi < 3; ++bi) {
+            const int bu = bus[bi];
+            const int rows = kTileVoxels / bu;
+            for (int bv = 1; bv <= rows; bv *= 2) {
+                const int bw = rows / bv;
+                if (bv > 1 && a.n_v == 1) continue;
+                const double r = radius_sum(bu, bv, bw);
+                if (r < best * (1.0 - 1e-9)) { best = r; best_bu = bu; best_bv = bv; best_bw = bw; }
+            }
+        }
+    }
+    h.vu = best_bu / 32;
+    a.bu = best_bu;
+    a.bv = best_bv;
+    a.bw = best_bw;
+    a.tiles_u = (a.n_u + a.bu - 1) / a.bu;
+    a.tiles_v = (a.n_v + a.bv - 1) / a.bv;
+    a.tiles_w = (a.n_w + a.bw - 1) / a.bw;
+    h.r_alpha_m = tile_radius(G, tx_axis, ua, va, a.bu, a.bv, a.bw);
+    h.r_beta_m = tile_radius(G, rx_axis, ua, va, a.bu, a.bv, a.bw);
+
+    // ---- device tables
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&h.n_sms, cudaDevAttrMultiProcessorCount, dev);
+    auto fail = [&](int code, const std::string& msg) {
+        rcbf_destroy(plan);
+        return set_error(code, msg);
+    };
+    if (cudaMalloc(&h.d_status, sizeof(int)) != cudaSuccess) return fail(RCBF_ENOMEM, "rcbf_plan: cudaMalloc status");
+    if (cudaMemset(h.d_status, 0, sizeof(int)) != cudaSuccess) return fail(RCBF_ECUDA, "rcbf_plan: cudaMemset");
+    a.status = h.d_status;
+    if (p.hadamard_order) {
+        const int n = (int)p.n_tx;
+        std::vector<int8_t> H((size_t)n * n);
+        if (params->decode_matrix) std::memcpy(H.data(), params->decode_matrix, H.size());
+        else
+            for (int k = 0; k < n; ++k)
+                for (int i = 0; i < n; ++i) H[(size_t)k * n + i] = (__builtin_popcount((unsigned)(k & i)) & 1) ? -1 : 1;
+        if (cudaMalloc(&h.d_hmat, H.size()) != cudaSuccess) return fail(RCBF_ENOMEM, "rcbf_plan: cudaMalloc H");
+        if (cudaMemcpy(h.d_hmat, H.data(), H.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(RCBF_ECUDA, "rcbf_plan: copy H");
+        if (n % 32 == 0) {
+            const std::vector<uint32_t> fr = build_afrag(H, n);
+            if (cudaMalloc(&h.d_afrag, fr.size() * 4) != cudaSuccess) return fail(RCBF_ENOMEM, "rcbf_plan: cudaMalloc fragments");
+            if (cudaMemcpy(h.d_afrag, fr.data(), fr.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(RCBF_ECUDA, "rcbf_plan: copy fragments");
+        }
+        if ((rc = configure_decode(h)) != RCBF_OK) { std::string m = g_last_error; rcbf_destroy(plan); return set_error(rc, m); }
+    }
+    if ((rc = configure_das(h)) != RCBF_OK) { std::string m = g_last_error; rcbf_destroy(plan); return set_error(rc, m); }
+    *out_plan = plan;
+    return RCBF_OK;
+}
+
+void rcbf_destroy(rcbf_plan_t plan) {
+    if (!plan) return;
+    PlanHost& h = plan->h;
+    if (h.d_afrag) cudaFree(h.d_afrag);
+    if (h.d_hmat) cudaFree(h.d_hmat);
+    if (h.d_status) cudaFree(h.d_status);
+    delete plan;
+}
+
+int rcbf_decode(rcbf_plan_t plan, const int16_t* rf, void* decoded, void* stream) {
+    if (!plan) return set_error(RCBF_EINVAL, "rcbf_decode: plan is NULL");
+    const PlanHost& h = plan->h;
+    if (!h.p.hadamard_order) return set_error(RCBF_EINVAL, "rcbf_decode: the plan has no Hadamard order");
+    if (!rf || !decoded) return set_error(RCBF_EINVAL, "rcbf_decode: NULL buffer");
+    if (!aligned16(rf) || !aligned16(decoded)) return set_error(RCBF_EINVAL, "rcbf_decode: buffers must be 16-byte aligned");
+    return launch_decode(h, rf, decoded, static_cast<cudaStream_t>(stream));
+}
+
+int rcbf_das(rcbf_plan_t plan, const void* decoded, const float* apod, float c, float* image, void* stream) {
+    if (!plan) return set_error(RCBF_EINVAL, "rcbf_das: plan is NULL");
+    const PlanHost& h = plan->h;
+    if (!decoded || !image) return set_error(RCBF_EINVAL, "rcbf_das: NULL buffer");
+    if (!aligned16(decoded) || !aligned4(image) || (apod && !aligned4(apod)))
+        return set_error(RCBF_EINVAL, "rcbf_das: decoded must be 16-byte aligned, image and apod 4-byte aligned");
+    const double cc = c > 0.f ? (double)c : h.p.c;
+    DasArgs a;
+    std::string why;
+    const bool tiled = h.p.das_variant == RCBF_DAS_TILED;
+    if (tiled && !h.tiled_ok)
+        return set_error(RCBF_EUNSUPPORTED, "rcbf_das: the tiled form needs n_ch % 8 == 0, n_tx % 8 == 0 "
+                                            "(4 for complex) and an image axis parallel to the transmit elements");
+    int rc = das_prepare(h, cc, &a, &why);
+    if (tiled && rc != RCBF_OK) return set_error(rc, why);
+    a.rf = decoded;
+    a.apod = apod;
+    a.image = image;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return tiled ? launch_das(h, a, s) : launch_das_plain(h, a, s);
+}
+
+int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, float c,
+                      const float* grad_image, float* grad_rf, float* grad_c, float* grad_apod, void* stream) {
+    (void)decoded; (void)apod; (void)c; (void)grad_image; (void)grad_rf; (void)grad_c;
+    (void)grad_apod; (void)stream;
+    if (!plan) return set_error(RCBF_EINVAL, "rcbf_das_backward: plan is NULL");
+    return set_error(RCBF_EUNSUPPORTED, "rcbf_das_backward: not built yet");
+}
+
+int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t* const* rf,
+                      void* const* decoded, float* const* images, rcbf_batch_t* out_batch) {
+    (void)plans; (void)n_frames; (void)rf; (void)decoded; (void)images;
+    if (out_batch) *out_batch = nullptr;
+    return set_error(RCBF_EUNSUPPORTED, "rcbf_batch_create: not built yet");
+}
+
+int rcbf_batch_run(rcbf_batch_t batch, void* stream) {
+    (void)stream;
+    if (!batch) return set_error(RCBF_EINVAL, "rcbf_batch_run: batch is NULL");
+    return set_error(RCBF_EUNSUPPORTED, "rcbf_batch_run: not built yet");
+}
+
+int rcbf_batch_status(rcbf_batch_t batch, void* stream) {
+    (void)batch; (void)stream;
+    return set_error(RCBF_EUNSUPPORTED, "rcbf_batch_status: not built yet");
+}
+
+void rcbf_batch_destroy(rcbf_batch_t batch) { (void)batch; }
+
+}  // extern "C"

@@ -1,0 +1,151 @@
+// das.cu — DAS dispatch, the plain FP32 form, and per-call window set-up.
+//
+// The plain form is the direct reading of Eq. (1)-(3) on the GPU: one thread
+// per voxel, FP32 voxel position and distances (the transmit distances of the
+// voxel cached per thread), fractional sample s = (d_tx + d_rx) fs / c - t0 fs,
+// floor / fraction, two global loads through the read-only cache and a
+// linear interpolation with zero outside the record.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace rcbf {
+
+template <int VU> int configure_das_vu(int ws, bool cplx, int* per_sm);
+template <int VU> int launch_das_vu(const DasArgs& a, int ws, bool cplx, bool apod, cudaStream_t s);
+
+namespace {
+
+template <int DT>
+__device__ __forceinline__ float plain_load(const void* rf, long long idx, float scale) {
+    if (DT == RCBF_F16) return __half2float(__ldg(static_cast<const __half*>(rf) + idx));
+    if (DT == RCBF_I32) return (float)__ldg(static_cast<const int*>(rf) + idx) * scale;
+    return __ldg(static_cast<const float*>(rf) + idx);
+}
+
+template <int DT, bool CPLX>
+__global__ void __launch_bounds__(128)
+das_plain_kernel(DasArgs a) {
+    const long long n_vox = (long long)a.n_u * a.n_v * a.n_w;
+    const long long vox = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (vox >= n_vox) return;
+    const int iu = (int)(vox % a.n_u);
+    const int iv = (int)((vox / a.n_u) % a.n_v);
+    const int iw = (int)(vox / ((long long)a.n_u * a.n_v));
+    float q[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        q[d] = (float)a.q0[d] + (float)a.Gu[d] * iu + (float)a.Gv[d] * iv + (float)a.Gw[d] * iw;
+    const float lat_tx = q[a.tx_axis], lat_rx = q[a.rx_axis], z = q[2];
+    const float fsc = (float)a.fs_over_c, t0fs = (float)a.t0fs;
+    float dtx[kMaxOrder];
+    for (int i = 0; i < a.n_tx; ++i) {
+        const float dx = lat_tx - ((float)a.tx_e0 + i * (float)a.tx_pitch);
+        dtx[i] = sqrtf(dx * dx + z * z);
+    }
+    float acc = 0.f, acci = 0.f;
+    for (int j = 0; j < a.n_ch; ++j) {
+        const float dx = lat_rx - ((float)a.rx_e0 + j * (float)a.rx_pitch);
+        const float drx = sqrtf(dx * dx + z * z);
+        float w = a.apod ? __ldg(a.apod + j) : 1.0f;
+        if (a.f_number > 0.f) {
+            const float al = a.f_number * fabsf(dx), az = fabsf(z);
+            if (al < 0.5f * az) { const float cs = cospif(al / az); w *= cs * cs; }
+            else w = 0.f;
+        }
+        if (w == 0.f) continue;
+        for (int i = 0; i < a.n_tx; ++i) {
+            const float s = (dtx[i] + drx) * fsc - t0fs;
+            const float fl = floorf(s);
+            const float f = s - fl;
+            const int n = (int)fl;
+            const long long base = ((long long)i * a.n_ch + j) * a.n_s;
+            const bool in0 = n >= 0 && n < a.n_s, in1 = n + 1 >= 0 && n + 1 < a.n_s;
+            const float r0 = in0 ? plain_load<DT>(a.rf, base + n, a.scale) : 0.f;
+            const float r1 = in1 ? plain_load<DT>(a.rf, base + n + 1, a.scale) : 0.f;
+            acc += w * ((1.0f - f) * r0 + f * r1);
+            if (CPLX) {
+                const float i0 = in0 ? plain_load<DT>(a.rf, a.plane_stride + base + n, a.scale) : 0.f;
+                const float i1 = in1 ? plain_load<DT>(a.rf, a.plane_stride + base + n + 1, a.scale) : 0.f;
+                acci += w * ((1.0f - f) * i0 + f * i1);
+            }
+        }
+    }
+    const long long o = (long long)iw * a.out_sw + (long long)iv * a.out_sv + (long long)iu * a.out_su;
+    a.image[o] = acc;
+    if (CPLX) a.image[a.image_plane + o] = acci;
+}
+
+}  // namespace
+
+int launch_das_plain(const PlanHost& h, const DasArgs& a, cudaStream_t s) {
+    (void)h;
+    const long long n_vox = (long long)a.n_u * a.n_v * a.n_w;
+    const unsigned grid = (unsigned)((n_vox + 127) / 128);
+    switch (a.dtype) {
+        case RCBF_F32: das_plain_kernel<RCBF_F32, false><<<grid, 128, 0, s>>>(a); break;
+        case RCBF_F16: das_plain_kernel<RCBF_F16, false><<<grid, 128, 0, s>>>(a); break;
+        case RCBF_I32: das_plain_kernel<RCBF_I32, false><<<grid, 128, 0, s>>>(a); break;
+        case RCBF_CF32: das_plain_kernel<RCBF_F32, true><<<grid, 128, 0, s>>>(a); break;
+        default: return set_error(RCBF_EUNSUPPORTED, "das: unsupported decoded dtype");
+    }
+    return check_launch("das_plain_kernel");
+}
+
+// Window geometry of one call. With R the tile radius in samples (transmit
+// plus receive plane), every voxel of a tile reads trace (i, j) inside
+// [K_i + K_j + lo, K_i + K_j + lo + W]: alpha, beta lie within R_a, R_b of
+// their references and the references' fractional parts are in [0, 1).
+int das_prepare(const PlanHost& h, double c, DasArgs* a, std::string* why) {
+    *a = h.das;
+    a->c = c;
+    a->fs_over_c = h.p.fs / c;
+    a->t0fs = h.p.t0 * h.p.fs;
+    const double R = (h.r_alpha_m + h.r_beta_m) * a->fs_over_c;
+    a->lo = (int)std::floor(-R) - 1;
+    a->W = (int)std::floor(4.0 + 2.0 * R + 0.01) + 1;
+    a->H = a->W / 2;
+    a->raw_samples = ((a->W + 8 + 7) / 8) * 8;
+    // alpha and beta are clamped to reference +- reach in the kernel; the
+    // 0.004-sample slack per side stays inside the 0.01 slack of W, so every
+    // interval index lands in [0, W-1] whatever the input (NaN included)
+    a->reach_a = (float)(h.r_alpha_m * a->fs_over_c + 0.004);
+    a->reach_b = (float)(h.r_beta_m * a->fs_over_c + 0.004);
+    if (a->W > 128) {
+        if (why) *why = "das: the voxel tile spans more than 128 samples at this speed of sound; choose a smaller tile";
+        return RCBF_EUNSUPPORTED;
+    }
+    return RCBF_OK;
+}
+
+static int stride_class(int W) { return W <= 64 ? 64 : 128; }
+
+int launch_das(const PlanHost& h, const DasArgs& a, cudaStream_t s) {
+    const int ws = stride_class(a.W);
+    const bool cplx = a.dtype == RCBF_CF32;
+    const bool apod = a.apod != nullptr || a.f_number > 0.f;
+    switch (h.vu) {
+        case 1: return launch_das_vu<1>(a, ws, cplx, apod, s);
+        case 2: return launch_das_vu<2>(a, ws, cplx, apod, s);
+        default: return launch_das_vu<4>(a, ws, cplx, apod, s);
+    }
+}
+
+int configure_das(PlanHost& h) {
+    if (h.p.das_variant == RCBF_DAS_PLAIN || !h.tiled_ok) return RCBF_OK;
+    const bool cplx = h.p.decoded_dtype == RCBF_CF32;
+    for (int c = 0; c < 2; ++c) {
+        const int ws = c == 0 ? 64 : 128;
+        int rc, n = 0;
+        switch (h.vu) {
+            case 1: rc = configure_das_vu<1>(ws, cplx, &n); break;
+            case 2: rc = configure_das_vu<2>(ws, cplx, &n); break;
+            default: rc = configure_das_vu<4>(ws, cplx, &n); break;
+        }
+        if (rc != RCBF_OK) return rc;
+        h.das_blocks_per_sm[c] = n;
+    }
+    return RCBF_OK;
+}
+
+}  // namespace rcbf

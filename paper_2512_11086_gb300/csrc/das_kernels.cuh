@@ -1,0 +1,70 @@
+// das_kernels.cuh — the tiled DAS kernel (one tile per CTA) and its host
+// launcher / configuration, instantiated per voxels-per-thread class in
+// das_vu1.cu, das_vu2.cu and das_vu4.cu so they compile in parallel.
+#pragma once
+
+#include "das_tile.cuh"
+
+namespace rcbf {
+
+template <int VU, int WS, bool CPLX, bool APOD>
+__global__ void __launch_bounds__(kDasThreads, (WS <= 64) ? 2 : 1)
+das_tiled_kernel(DasArgs a) {
+    using C = DasCfg<VU, WS, CPLX>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const uint32_t bar0 = smem_u32(smem + C::OFF_BAR);
+    if (threadIdx.x == 0) {
+        mbar_init(bar0, C::COPIES);
+        mbar_init(bar0 + 8, C::COPIES);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    DasPipe pipe{0u};
+    if (!das_tile<VU, WS, CPLX, APOD>(a, blockIdx.x, smem, pipe) && threadIdx.x == 0)
+        atomicOr(a.status, kStatusWaitExpired);
+}
+
+template <int VU, int WS, bool CPLX, bool APOD>
+int das_cfg_one(int* per_sm) {
+    using C = DasCfg<VU, WS, CPLX>;
+    auto k = das_tiled_kernel<VU, WS, CPLX, APOD>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess)
+        return check_launch("das: set shared memory");
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kDasThreads, C::SMEM) != cudaSuccess)
+        return check_launch("das: occupancy");
+    if (per_sm) *per_sm = n;
+    return RCBF_OK;
+}
+
+template <int VU>
+int configure_das_vu(int ws, bool cplx, int* per_sm) {
+    int rc;
+#define RCBF_CFG(WSV, CP)                                                        \
+    if ((rc = das_cfg_one<VU, WSV, CP, false>(per_sm)) != RCBF_OK) return rc;   \
+    if ((rc = das_cfg_one<VU, WSV, CP, true>(nullptr)) != RCBF_OK) return rc;
+    if (ws == 64 && !cplx) { RCBF_CFG(64, false) }
+    else if (ws == 64 && cplx) { RCBF_CFG(64, true) }
+    else if (ws == 128 && !cplx) { RCBF_CFG(128, false) }
+    else { RCBF_CFG(128, true) }
+#undef RCBF_CFG
+    return RCBF_OK;
+}
+
+template <int VU>
+int launch_das_vu(const DasArgs& a, int ws, bool cplx, bool apod, cudaStream_t s) {
+    const unsigned grid = (unsigned)a.tiles_u * a.tiles_v * a.tiles_w;
+#define RCBF_LAUNCH(WSV, CP, AP)                                                                   \
+    das_tiled_kernel<VU, WSV, CP, AP><<<grid, kDasThreads, DasCfg<VU, WSV, CP>::SMEM, s>>>(a);    \
+    return check_launch("das_tiled_kernel");
+    if (ws == 64) {
+        if (cplx) { if (apod) { RCBF_LAUNCH(64, true, true) } else { RCBF_LAUNCH(64, true, false) } }
+        else { if (apod) { RCBF_LAUNCH(64, false, true) } else { RCBF_LAUNCH(64, false, false) } }
+    } else {
+        if (cplx) { if (apod) { RCBF_LAUNCH(128, true, true) } else { RCBF_LAUNCH(128, true, false) } }
+        else { if (apod) { RCBF_LAUNCH(128, false, true) } else { RCBF_LAUNCH(128, false, false) } }
+    }
+#undef RCBF_LAUNCH
+}
+
+}  // namespace rcbf

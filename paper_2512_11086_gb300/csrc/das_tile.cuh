@@ -1,0 +1,329 @@
+// das_tile.cuh — one voxel tile of the delay-and-sum of Eq. (1)
+// (§THEORY "Synthetic Aperture Imaging"; §OPTIMIZATIONS "DAS").
+//
+// A CTA of 256 threads beamforms a tile of 1024 voxels, 4 per thread, and
+// walks the (transmit, channel) plane in stages of CI x CJ windows.
+//
+// Delays. For the tile centre q_ref the FP64 reference distance of every
+// element is split into an integer sample K and a fractional remainder; a
+// voxel's delay to element e is then
+//   K_e + rho_e + (d_e(v) - d_e(ref)) * fs / c,
+//   d_e(v) - d_e(ref) = (dL (2L + dL) + dZ (2Z + dZ)) / (d_e(v) + d_e(ref))
+// evaluated in FP32 (no cancellation: dL, dZ are the voxel's offsets from
+// q_ref, L = lat(q_ref) - e, Z = z(q_ref)). The separable row-column delay
+// s_ij = A_i + B_j (transmit line i, receive line j) needs one such term per
+// (voxel, transmit) and per (voxel, channel), never per (voxel, i, j).
+//
+// Windows. Every (i, j) trace is read only inside the window
+// [K_i + K_j + lo, K_i + K_j + lo + W] that the tile can reach (W from the
+// tile radius, a 1-Lipschitz bound of the distances). The 1-D TMA bulk engine
+// copies each window into shared memory, where it is rewritten as W line
+// pieces (c_n, slope_n): r(x) = c_n + u * slope_n on sample interval n, u
+// being the window-centred position. The inner loop per voxel and (i, j) is
+// then: u = alpha_i + beta_j; t = u + 2^23 + H (the integer part of t is the
+// interval n); one 8-byte shared load; one FMA for the interpolated sample;
+// one add (or FMA with the apodization weight a_j(v) of Eq. (2)-(3)).
+#pragma once
+
+#include <type_traits>
+
+#include "internal.cuh"
+
+namespace rcbf {
+
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, N>(f);
+    }
+}
+
+template <int VU, int WS, bool CPLX>
+struct DasCfg {
+    static constexpr int VR = 4 / VU;              // tile rows per thread
+    static constexpr int ROWS = 8 * VR;            // tile rows (one warp covers VR rows)
+    static constexpr int BU = 32 * VU;             // tile extent along u
+    static constexpr int CI = CPLX ? 4 : 8;        // transmits per stage
+    static constexpr int CJ = 8;                   // channels per stage
+    static constexpr int NWIN = CI * CJ;           // windows per stage
+    static constexpr int COPIES = 64;              // bulk copies per stage (windows x planes)
+    static constexpr int PAIR_BYTES = CPLX ? 16 : 8;
+    static constexpr int RAWS = WS + 8;            // raw samples per window plane (max)
+    static constexpr int RAW_WIN_BYTES = RAWS * 4 * (CPLX ? 2 : 1);
+    static constexpr int OFF_TX = 0;                               // float4[kMaxOrder]
+    static constexpr int OFF_RX = OFF_TX + kMaxOrder * 16;         // float4[kMaxChannels]
+    static constexpr int OFF_ALPHA = OFF_RX + kMaxChannels * 16;   // float[CI][ROWS]
+    static constexpr int OFF_WOFF = OFF_ALPHA + CI * ROWS * 4;     // int[2][NWIN]
+    static constexpr int OFF_BAR = OFF_WOFF + 2 * NWIN * 4;        // uint64[2]
+    static constexpr int OFF_PAIRS = ((OFF_BAR + 16 + 127) / 128) * 128;
+    static constexpr int OFF_RAW = OFF_PAIRS + NWIN * WS * PAIR_BYTES;
+    static constexpr int SMEM = OFF_RAW + 2 * NWIN * RAW_WIN_BYTES;
+    static_assert(CI * ROWS <= kDasThreads, "alpha table needs one thread per entry");
+    static_assert(NWIN * (CPLX ? 2 : 1) == COPIES, "one issuing thread per copy");
+};
+
+template <int OFF>
+__device__ __forceinline__ float2 lds_f2(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0,%1}, [%2+%3];" : "=f"(v.x), "=f"(v.y) : "r"(addr), "n"(OFF));
+    return v;
+}
+template <int OFF>
+__device__ __forceinline__ float4 lds_f4(uint32_t addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4+%5];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr), "n"(OFF));
+    return v;
+}
+
+// Eq. (3) window at u = F# |lat| / |z|, support test F# |lat| < 0.5 |z|.
+__device__ __forceinline__ float hann_weight(float f_number, float lat, float z) {
+    const float al = f_number * fabsf(lat), az = fabsf(z);
+    if (!(al < 0.5f * az)) return 0.0f;
+    const float cs = cospif(al / az);
+    return cs * cs;
+}
+
+__device__ __forceinline__ float load_sample(const unsigned char* raw, int dtype, int n, float scale) {
+    if (dtype == RCBF_F16) return __half2float(reinterpret_cast<const __half*>(raw)[n]);
+    if (dtype == RCBF_I32) return (float)reinterpret_cast<const int*>(raw)[n] * scale;
+    return reinterpret_cast<const float*>(raw)[n];
+}
+
+// Persistent state of a CTA running DAS tiles (mbarrier phases).
+struct DasPipe {
+    uint32_t phase;   // bit b: parity of the next phase of mbarrier b
+};
+
+// Returns false when a bounded wait expired (the CTA must stop; the caller
+// records the status).
+template <int VU, int WS, bool CPLX, bool APOD>
+__device__ __forceinline__ bool das_tile(const DasArgs& a, int tile, unsigned char* smem, DasPipe& pipe) {
+    using C = DasCfg<VU, WS, CPLX>;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float4* s_tx = reinterpret_cast<float4*>(smem + C::OFF_TX);
+    float4* s_rx = reinterpret_cast<float4*>(smem + C::OFF_RX);
+    float* s_alpha = reinterpret_cast<float*>(smem + C::OFF_ALPHA);
+    int* s_woff = reinterpret_cast<int*>(smem + C::OFF_WOFF);
+    const uint32_t bar0 = smem_u32(smem + C::OFF_BAR);
+    const uint32_t pairs_u32 = smem_u32(smem + C::OFF_PAIRS);
+    unsigned char* raw = smem + C::OFF_RAW;
+    const int es = (a.dtype == RCBF_F16) ? 2 : 4;
+
+    // ---- tile position and FP64 reference delays
+    const int tu = tile % a.tiles_u;
+    const int tv = (tile / a.tiles_u) % a.tiles_v;
+    const int tw = tile / (a.tiles_u * a.tiles_v);
+    const int u0 = tu * C::BU, v0 = tv * a.bv, w0 = tw * a.bw;
+    const double cu = u0 + 0.5 * (C::BU - 1), cv = v0 + 0.5 * (a.bv - 1), cw = w0 + 0.5 * (a.bw - 1);
+    const double qx = a.q0[0] + a.Gu[0] * cu + a.Gv[0] * cv + a.Gw[0] * cw;
+    const double qy = a.q0[1] + a.Gu[1] * cu + a.Gv[1] * cv + a.Gw[1] * cw;
+    const double zr = a.q0[2] + a.Gu[2] * cu + a.Gv[2] * cv + a.Gw[2] * cw;
+    const double lat_tx_ref = a.tx_axis ? qy : qx, lat_rx_ref = a.rx_axis ? qy : qx;
+    for (int e = tid; e < a.n_tx + a.n_ch; e += kDasThreads) {
+        if (e < a.n_tx) {
+            const double L = lat_tx_ref - (a.tx_e0 + e * a.tx_pitch);
+            const double d = sqrt(L * L + zr * zr);
+            const double A = d * a.fs_over_c - a.t0fs;
+            const double K = floor(A);
+            // remainder with the window offset, the half-sample shift of the
+            // rounding trick and the window centring folded in
+            const float rho = (float)(A - K - (double)a.lo - 0.5 - (double)a.H);
+            s_tx[e] = make_float4((float)L, (float)d, rho, __int_as_float((int)K));
+        } else {
+            const int j = e - a.n_tx;
+            const double L = lat_rx_ref - (a.rx_e0 + j * a.rx_pitch);
+            const double d = sqrt(L * L + zr * zr);
+            const double B = d * a.fs_over_c;
+            const double K = floor(B);
+            s_rx[j] = make_float4((float)L, (float)d, (float)(B - K), __int_as_float((int)K));
+        }
+    }
+
+    // ---- this thread's voxels: offsets from the reference, in FP32 (exact
+    // half-integer index offsets times the FP32 voxel steps)
+    const float Zf = (float)zr;
+    const float fsc = (float)a.fs_over_c;
+    const float gur = (float)(a.rx_axis ? a.Gu[1] : a.Gu[0]);
+    const float gvr = (float)(a.rx_axis ? a.Gv[1] : a.Gv[0]);
+    const float gwr = (float)(a.rx_axis ? a.Gw[1] : a.Gw[0]);
+    const float guz = (float)a.Gu[2], gvz = (float)a.Gv[2], gwz = (float)a.Gw[2];
+    auto voxel_offsets = [&](int k, float& dlr, float& dz) {
+        const int ku = k % VU, kr = k / VU;
+        const int row = warp * C::VR + kr;
+        const float du = (float)(lane + 32 * ku) - 0.5f * (C::BU - 1);
+        const float dv = (float)(row % a.bv) - 0.5f * (a.bv - 1);
+        const float dw = (float)(row / a.bv) - 0.5f * (a.bw - 1);
+        dlr = gur * du + gvr * dv + gwr * dw;
+        dz = guz * du + gvz * dv + gwz * dw;
+    };
+    __syncthreads();   // reference tables ready
+
+    const int n_ic = a.n_tx / C::CI, n_jc = a.n_ch / C::CJ;
+    const int NS = n_ic * n_jc;
+
+    // ---- producer: one thread per bulk copy (window, plane)
+    auto issue = [&](int s, int b) {
+        if (tid < C::COPIES) {
+            const int win = CPLX ? (tid >> 1) : tid;
+            const int plane = CPLX ? (tid & 1) : 0;
+            const int ii = win / C::CJ, jj = win % C::CJ;
+            const int jc = s / n_ic, ic = s % n_ic;
+            const int i = ic * C::CI + ii, j = jc * C::CJ + jj;
+            const int S0 = __float_as_int(s_tx[i].w) + __float_as_int(s_rx[j].w) + a.lo;
+            const int A = S0 & ~7;
+            if (plane == 0) s_woff[b * C::NWIN + win] = S0 - A;
+            const int lo_s = max(A, 0);
+            const int hi_s = min(A + a.raw_samples, a.n_s);
+            unsigned char* dst = raw + (b * C::NWIN + win) * C::RAW_WIN_BYTES + plane * C::RAWS * 4;
+            const int pre = (min(lo_s, A + a.raw_samples) - A) * es;       // bytes of zeros before
+            const int body = hi_s > lo_s ? (hi_s - lo_s) * es : 0;
+            const int total = a.raw_samples * es;
+            for (int o = 0; o < pre; o += 16) *reinterpret_cast<uint4*>(dst + o) = make_uint4(0, 0, 0, 0);
+            for (int o = pre + body; o < total; o += 16) *reinterpret_cast<uint4*>(dst + o) = make_uint4(0, 0, 0, 0);
+            fence_proxy_async_smem();
+            const uint32_t bar = bar0 + 8 * b;
+            mbar_arrive_expect_tx(bar, (uint32_t)body);
+            if (body > 0) {
+                const char* src = static_cast<const char*>(a.rf) +
+                    ((long long)plane * a.plane_stride + ((long long)i * a.n_ch + j) * a.n_s + lo_s) * es;
+                bulk_g2s(smem_u32(dst + pre), src, (uint32_t)body, bar);
+            }
+        }
+    };
+
+    issue(0, 0);
+    if (NS > 1) issue(1, 1);
+    __syncthreads();   // window offsets and zero fills of the first two stages visible
+
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float acci[4] = {0.f, 0.f, 0.f, 0.f};
+    float beta[4][C::CJ];
+    float apw[4][C::CJ];
+    const float magic = 8388608.0f + (float)a.H;     // 2^23 + H
+    constexpr int SHIFT = CPLX ? 4 : 3;
+    const uint32_t pbase = pairs_u32 - (0x4B000000u << SHIFT);
+
+    for (int s = 0; s < NS; ++s) {
+        const int jc = s / n_ic, ic = s % n_ic;
+        const int b = s & 1;
+        if (ic == 0) {
+            // per-voxel receive terms (and apodization) for this channel chunk
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float dlr, dz;
+                voxel_offsets(k, dlr, dz);
+                const float Zv = Zf + dz;
+#pragma unroll
+                for (int jj = 0; jj < C::CJ; ++jj) {
+                    const int j = jc * C::CJ + jj;
+                    const float4 rx = s_rx[j];
+                    const float Lv = rx.x + dlr;
+                    const float d = sqrtf(Lv * Lv + Zv * Zv);
+                    const float num = dlr * (2.0f * rx.x + dlr) + dz * (2.0f * Zf + dz);
+                    const float bt = rx.z + __fdividef(num, d + rx.y) * fsc;
+                    beta[k][jj] = fminf(fmaxf(bt, rx.z - a.reach_b), rx.z + a.reach_b);
+                    if (APOD) {
+                        const float wj = a.apod ? __ldg(a.apod + j) : 1.0f;
+                        apw[k][jj] = a.f_number > 0.f ? wj * hann_weight(a.f_number, Lv, Zv) : wj;
+                    }
+                }
+            }
+        }
+        const bool ok = mbar_wait_parity(bar0 + 8 * b, (pipe.phase >> b) & 1u);
+        pipe.phase ^= 1u << b;
+
+        // ---- raw window -> line pieces (c_n, slope_n)
+        const unsigned char* rawb = raw + b * C::NWIN * C::RAW_WIN_BYTES;
+        const float hp = 0.5f + (float)a.H;
+        for (int win = warp; win < C::NWIN; win += kDasThreads / 32) {
+            const int off = s_woff[b * C::NWIN + win];
+            const unsigned char* rw0 = rawb + win * C::RAW_WIN_BYTES;
+            unsigned char* pw = smem + C::OFF_PAIRS + win * WS * C::PAIR_BYTES;
+            for (int n = lane; n < a.W; n += 32) {
+                const float r0 = load_sample(rw0, a.dtype, off + n, a.scale);
+                const float r1 = load_sample(rw0, a.dtype, off + n + 1, a.scale);
+                const float sl = r1 - r0;
+                const float cn = fmaf(hp - (float)n, sl, r0);
+                if (CPLX) {
+                    const unsigned char* rw1 = rw0 + C::RAWS * 4;
+                    const float i0 = load_sample(rw1, a.dtype, off + n, a.scale);
+                    const float i1 = load_sample(rw1, a.dtype, off + n + 1, a.scale);
+                    const float si = i1 - i0;
+                    reinterpret_cast<float4*>(pw)[n] = make_float4(cn, sl, fmaf(hp - (float)n, si, i0), si);
+                } else {
+                    reinterpret_cast<float2*>(pw)[n] = make_float2(cn, sl);
+                }
+            }
+        }
+        // ---- transmit terms of this stage for every tile row (alpha depends on row only)
+        if (tid < C::CI * C::ROWS) {
+            const int ii = tid / C::ROWS, row = tid % C::ROWS;
+            const int rv = row % a.bv, rw = row / a.bv;
+            const float dv = (float)rv - 0.5f * (a.bv - 1);
+            const float dw = (float)rw - 0.5f * (a.bw - 1);
+            const float dL = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]) * dv + (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]) * dw;
+            const float dz = (float)a.Gv[2] * dv + (float)a.Gw[2] * dw;
+            const float4 tx = s_tx[ic * C::CI + ii];
+            const float Lv = tx.x + dL, Zv = Zf + dz;
+            const float d = sqrtf(Lv * Lv + Zv * Zv);
+            const float num = dL * (2.0f * tx.x + dL) + dz * (2.0f * Zf + dz);
+            const float al = tx.z + __fdividef(num, d + tx.y) * fsc;
+            s_alpha[ii * C::ROWS + row] = fminf(fmaxf(al, tx.z - a.reach_a), tx.z + a.reach_a);
+        }
+        if (__syncthreads_or(!ok)) {
+            // a window never arrived: give this CTA's copies still in flight a
+            // bounded chance to land, then stop
+            if (!ok) mbar_wait_parity(bar0 + 8 * b, ((pipe.phase >> b) & 1u) ^ 1u);
+            if (s + 1 < NS) mbar_wait_parity(bar0 + 8 * (b ^ 1), (pipe.phase >> (b ^ 1)) & 1u);
+            return false;
+        }
+        if (s + 2 < NS) issue(s + 2, b);
+
+        // ---- the sum: 4 voxels x CI transmits x CJ channels
+        static_for<0, C::CI>([&](auto iic) {
+            constexpr int ii = decltype(iic)::value;
+            float al[C::VR];
+#pragma unroll
+            for (int kr = 0; kr < C::VR; ++kr) al[kr] = s_alpha[ii * C::ROWS + warp * C::VR + kr];
+            static_for<0, C::CJ>([&](auto jjc) {
+                constexpr int jj = decltype(jjc)::value;
+                constexpr int OFF = (ii * C::CJ + jj) * WS * C::PAIR_BYTES;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float u = al[k / VU] + beta[k][jj];
+                    const float t = u + magic;
+                    const uint32_t addr = (__float_as_uint(t) << SHIFT) + pbase;
+                    if (CPLX) {
+                        const float4 p = lds_f4<OFF>(addr);
+                        const float vr = fmaf(u, p.y, p.x), vi = fmaf(u, p.w, p.z);
+                        if (APOD) { acc[k] = fmaf(apw[k][jj], vr, acc[k]); acci[k] = fmaf(apw[k][jj], vi, acci[k]); }
+                        else { acc[k] += vr; acci[k] += vi; }
+                    } else {
+                        const float2 p = lds_f2<OFF>(addr);
+                        const float v = fmaf(u, p.y, p.x);
+                        if (APOD) acc[k] = fmaf(apw[k][jj], v, acc[k]);
+                        else acc[k] += v;
+                    }
+                }
+            });
+        });
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int ku = k % VU, kr = k / VU;
+        const int row = warp * C::VR + kr;
+        const int iu = u0 + lane + 32 * ku, iv = v0 + row % a.bv, iw = w0 + row / a.bv;
+        if (iu < a.n_u && iv < a.n_v && iw < a.n_w) {
+            const long long o = (long long)iw * a.out_sw + (long long)iv * a.out_sv + (long long)iu * a.out_su;
+            a.image[o] = acc[k];
+            if (CPLX) a.image[a.image_plane + o] = acci[k];
+        }
+    }
+    return true;
+}
+
+}  // namespace rcbf

@@ -1,0 +1,160 @@
+// internal.cuh — plan layout, kernel argument blocks and PTX helpers shared
+// by the library's translation units (decode, DAS, adjoint, batch, API).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+#include <string>
+
+#include "rcbf.h"
+
+namespace rcbf {
+
+// ---------------------------------------------------------------- limits
+constexpr int kMaxOrder = 256;        // largest Hadamard order / transmit count
+constexpr int kMaxChannels = 256;     // receive channels per plan
+constexpr int kDasThreads = 256;      // threads of a DAS tile CTA
+constexpr int kTileVoxels = 1024;     // voxels of a DAS tile (4 per thread)
+constexpr int kCI = 8;                // transmits per staged chunk
+constexpr int kCJ = 8;                // channels per staged chunk
+constexpr int kDecodeThreads = 256;
+constexpr int kDecodeCols = 128;      // columns (channel x sample) per decode tile
+constexpr uint32_t kWaitLimit = 1u << 26;   // bounded mbarrier polls before giving up
+
+// Status bits written by kernels into a plan's device status word.
+constexpr int kStatusWaitExpired = 1;
+
+// ------------------------------------------------------ DAS argument block
+// Voxel index space is reordered so that u is the fast (lane) axis:
+// u = x normally, u = y when the image has nx == 1 and ny > 1.
+struct DasArgs {
+    double q0[3];          // array-frame position of voxel (0,0,0)
+    double Gu[3], Gv[3], Gw[3];   // array-frame step per index along u, v, w
+    int n_u, n_v, n_w;
+    long long out_su, out_sv, out_sw;   // image strides (floats) along u, v, w
+    int tiles_u, tiles_v, tiles_w;
+    int bu, bv, bw;        // tile extents (bu = 32*VU, bv*bw = 8*VR)
+    int n_tx, n_ch, n_s;
+    int tx_axis, rx_axis;  // lateral coordinate of an element: 0 -> q.x, 1 -> q.y
+    double tx_e0, tx_pitch, rx_e0, rx_pitch;   // e_i = e0 + i*pitch
+    double fs_over_c;      // samples per metre of path
+    double t0fs;           // t0 * fs (samples)
+    double c;              // speed of sound of this call
+    double fs;
+    float f_number;
+    int W;                 // pairs per window actually used (<= compiled stride)
+    int lo;                // window start offset in samples (<= 0)
+    int H;                 // W / 2: centring of the per-window line intercepts
+    int raw_samples;       // raw samples staged per window (multiple of 8)
+    float reach_a, reach_b;// tile reach of the transmit / receive delays in samples (+ slack)
+    int dtype;             // rcbf_dtype of the decoded RF
+    float scale;           // 1/N for RCBF_I32 input, else 1
+    long long plane_stride;// elements between real and imaginary planes (complex)
+    const void* rf;
+    const float* apod;     // per-channel weights or nullptr
+    float* image;
+    long long image_plane; // floats between image planes (complex)
+    int* status;
+    // adjoint outputs (backward only)
+    const float* grad_image;
+    float* grad_rf;
+    float* grad_c;
+    float* grad_apod;
+};
+
+struct DecodeArgs {
+    const int16_t* rf;
+    void* out;
+    const uint32_t* afrag;  // A = H^T fragments, permuted for the ldmatrix.trans B order
+    const int8_t* hmat;     // H[k][i] row-major (plain variant)
+    long long n_cols;       // n_ch * n_samples
+    int n;                  // order
+    int dtype;              // RCBF_I32 / RCBF_F32 / RCBF_F16
+    float inv_n;
+};
+
+// ----------------------------------------------------------------- plan
+struct PlanHost {
+    rcbf_params p;
+    DasArgs das;            // geometry part filled at plan time
+    double r_alpha_m;       // tile radius in the (lateral_tx, z) plane [m]
+    double r_beta_m;        // tile radius in the (lateral_rx, z) plane [m]
+    int vu;                 // voxels per thread along u (1, 2, 4)
+    bool swap_uv;           // u = y
+    bool tiled_ok;          // geometry and sizes admit the tiled DAS
+    uint32_t* d_afrag;      // device A fragments
+    int8_t* d_hmat;         // device H (plain decode)
+    int* d_status;          // device status word
+    int n_sms;              // SMs of the plan's device
+    int decode_blocks_per_sm;
+    int das_blocks_per_sm[2];   // by window stride class (64, 128)
+};
+
+}  // namespace rcbf
+
+struct rcbf_plan_s {
+    rcbf::PlanHost h;
+};
+
+namespace rcbf {
+
+// Thread-local error message helpers (api.cu).
+int set_error(int code, const std::string& msg);
+int check_launch(const char* what);
+
+// Window geometry of a DAS call at speed of sound c (host side).
+int das_prepare(const PlanHost& h, double c, DasArgs* a, std::string* why);
+
+// Kernel launchers (one per translation unit).
+int launch_decode(const PlanHost& h, const int16_t* rf, void* out, cudaStream_t s);
+int launch_das(const PlanHost& h, const DasArgs& a, cudaStream_t s);
+int launch_das_plain(const PlanHost& h, const DasArgs& a, cudaStream_t s);
+int launch_das_backward(const PlanHost& h, const DasArgs& a, cudaStream_t s);
+int configure_decode(PlanHost& h);
+int configure_das(PlanHost& h);
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(bar), "r"(bytes) : "memory");
+}
+
+// Bounded wait on an mbarrier phase; returns false if the poll budget ran out.
+__device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 1-D bulk copy global -> shared (TMA engine), completion on an mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+}  // namespace rcbf
