@@ -1,0 +1,352 @@
+"""Benchmark of the row-column / TOBE beamformer hot path on GB300.
+
+Workload: the FORCES full-aperture B-scan (128 Hadamard-encoded transmits x
+128 channels x 4096 int16 samples, 512 x 1024 image, 8.59e9 voxel-channel-
+transmit sums per frame), synthetic point-scatterer data. One step = one
+frame through the whole path: Hadamard decode (split-byte int8 tensor cores,
+FP16-stored output) and tiled DAS (FP32 accumulation).
+
+Reported: value = whole-job DAS sums/s over the full step (decode included),
+frames/s, per-kernel CUDA-event times, the roofline of the dominant (DAS)
+kernel and of the decode, the plain FP32 form on the same GPU, an end-to-end
+figure through the C ABI with host buffers, clocks during the timed region,
+and the FP64 CPU oracle timed on a bounded sample (N = 1, rank 0).
+
+--impl reference times the FP64 CPU oracle itself (the reference arm) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "DAS G voxel·chan·tx sums/s & frames/s vs plain FP32 at <=1e-4 rel-L2"
+UNIT = "Gsums/s"
+WORKLOAD = "FORCES 2D full aperture: 128 tx (H128) x 128 ch x 4096 int16 samples -> 512x1024 FP32 image"
+RING = 3           # input frames rotated so no step finds its input in L2
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)),
+                "src": "of measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "of fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(float(r[2]) for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    dist.init_process_group("nccl")
+    return rank, ws, local
+
+
+def cpu_baseline(frame, target_s: float = 15.0):
+    """The FP64 oracle as it stands, on a bounded sample of the frame: the
+    decode of a slice of columns and the DAS of a random voxel subset, both
+    the same fraction phi of the frame, sized to about target_s seconds.
+    Returns (Gsums/s, details)."""
+    import oracle
+    g = frame.geometry
+    cores = oracle.threads()
+    exact = _exact_decoded(frame)          # inputs of the DAS sample (not timed)
+    rng = np.random.default_rng(0)
+    flat = frame.rf.reshape(g.n_tx, -1)
+    nv = 256
+    while True:
+        vox = np.sort(rng.choice(g.n_vox, size=nv, replace=False)).astype(np.int64)
+        ncol = max(8, int(round(nv / g.n_vox * flat.shape[1])))
+        t0 = time.perf_counter()
+        oracle.decode(flat[:, :ncol])
+        oracle.das(g, exact, voxels=vox)
+        t = time.perf_counter() - t0
+        if t >= 0.5 * target_s or nv >= g.n_vox:
+            break
+        nv = min(g.n_vox, int(nv * max(2.0, target_s / max(t, 1e-3))))
+    value = nv * g.n_tx * g.n_ch / t / 1e9
+    return value, {"cores": cores, "seconds": t,
+                   "sample": "%d of %d voxels (%.4f of the frame) plus the same fraction of the decode "
+                             "columns: %.1f s of oracle time" % (nv, g.n_vox, nv / g.n_vox, t)}
+
+
+_EXACT = {}
+
+
+def _exact_decoded(frame):
+    key = id(frame)
+    if key not in _EXACT:
+        import oracle
+        D = oracle.decode(frame.rf)
+        _EXACT[key] = D.astype(np.float64) / frame.geometry.n_tx
+    return _EXACT[key]
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle timed on the host cores."""
+    rank, ws, _ = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    frame = synth.full_bscan(seed=2)
+    g = frame.geometry
+    oracle.build()
+    cores = oracle.threads()
+    exact = _exact_decoded(frame)
+    rng = np.random.default_rng(1)
+    nv = 2048                                  # voxels per step (a bounded sample)
+    phi = nv / g.n_vox
+    ncol = int(round(phi * g.n_ch * g.n_samples))
+    times = []
+    for step in range(args.warmup + args.steps):
+        vox = np.sort(rng.choice(g.n_vox, size=nv, replace=False)).astype(np.int64)
+        t0 = time.perf_counter()
+        oracle.decode(frame.rf.reshape(g.n_tx, -1)[:, :ncol])
+        oracle.das(g, exact, voxels=vox)
+        t1 = time.perf_counter()
+        if step >= args.warmup:
+            times.append(t1 - t0)
+    per = float(np.mean(times))
+    value = nv * g.n_tx * g.n_ch / per / 1e9
+    sample = "%d random voxels (%.5f of the frame) and the same fraction of decode columns per step" % (nv, phi)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "frames_per_s": value * 1e9 / g.sums,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    rank, ws, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2512_11086_gb300 import build as rbuild
+    if rank == 0:
+        rbuild.build()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    import paper_2512_11086_gb300 as rc
+    import synth
+
+    frame = synth.full_bscan(seed=2)
+    g = frame.geometry
+    sums = g.sums
+    tuned = rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=rc.DECODE_MMA_I8,
+                                   das_variant=rc.DAS_TILED))
+    plain = rc.Plan(rc.make_params(g, decoded_dtype="f32", decode_variant=rc.DECODE_PLAIN,
+                                   das_variant=rc.DAS_PLAIN))
+    rf_host = torch.from_numpy(frame.rf)
+    rf = [rf_host.to(dev) for _ in range(RING)]
+    dec16 = [torch.empty(g.n_tx, g.n_ch, g.n_samples, dtype=torch.float16, device=dev) for _ in range(RING)]
+    img = torch.empty(tuned.image_shape, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if ws == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- tuned form: warm-up, then K timed steps with per-kernel events
+    for s in range(args.warmup):
+        tuned.das(tuned.decode(rf[s % RING], out=dec16[s % RING]), out=img)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    for s in range(args.steps):
+        b = s % RING
+        ev[s][0].record(stream)
+        tuned.decode(rf[b], out=dec16[b])
+        ev[s][1].record(stream)
+        tuned.das(dec16[b], out=img)
+        ev[s][2].record(stream)
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(start.elapsed_time(end))
+    ms_step = total_ms / args.steps
+    t_dec = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    t_das = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    value = sums * args.steps * ws / (total_ms * 1e-3) / 1e9
+
+    # ---- plain FP32 form on the same GPU (same frame, same timing)
+    dec32 = torch.empty(g.n_tx, g.n_ch, g.n_samples, dtype=torch.float32, device=dev)
+    plain_steps = max(3, min(args.steps, 10))
+    for s in range(3):
+        plain.das(plain.decode(rf[s % RING], out=dec32), out=img)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for s in range(plain_steps):
+        plain.das(plain.decode(rf[s % RING], out=dec32), out=img)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = max_over_ranks(p0.elapsed_time(p1)) / plain_steps
+    plain_value = sums / (plain_ms * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    pinned = [rf_host.pin_memory() for _ in range(RING)]
+    img_host = torch.empty(tuned.image_shape, dtype=torch.float32).pin_memory()
+    for s in range(3):
+        rf[0].copy_(pinned[s % RING], non_blocking=True)
+        tuned.das(tuned.decode(rf[0], out=dec16[0]), out=img)
+        img_host.copy_(img, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for s in range(args.steps):
+        b = s % RING
+        rf[b].copy_(pinned[b], non_blocking=True)
+        tuned.das(tuned.decode(rf[b], out=dec16[b]), out=img)
+        img_host.copy_(img, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
+    e2e_value = sums * ws / (e2e_ms * 1e-3) / 1e9
+
+    # ---- roofline: DAS (dominant) against the FP32 ALU peak; decode against HBM
+    peaks = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    ops_per_sum = 5   # add (A_i + B_j), floor, fraction, interpolation FMA, accumulate
+    alu_peak = sms * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12   # FP32 lane-ops/s in T
+    das_achieved = ops_per_sum * sums / (t_das * 1e-3) / 1e12
+    dec_bytes = g.n_tx * g.n_ch * g.n_samples * (2 + 2)       # int16 in + FP16 out
+    dec_achieved = dec_bytes / (t_dec * 1e-3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": ws, "decoded_storage": "f16",
+                   "decode": "split-byte int8 mma.sync (exact)", "das": "tiled, TMA windows, FP32",
+                   "l2": "inputs rotate over %d frames (%d MB int16 each, %d MB total > 129 MB L2)"
+                         % (RING, rf_host.numel() * 2 >> 20, RING * rf_host.numel() * 2 >> 20),
+                   "parallelism": "independent frames per GPU" if ws > 1 else "1 GPU"},
+        "frames_per_s": 1e3 / ms_step * ws,
+        "kernel_ms": {"decode": t_dec, "das": t_das},
+        "das_only_gsums_per_s": sums / (t_das * 1e-3) / 1e9,
+        "plain_fp32": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_ms,
+                       "speedup_of_tuned": value / plain_value},
+        "roofline": {"bound": "alu", "achieved": das_achieved, "peak": alu_peak, "unit": "TOP/s",
+                     "frac": das_achieved / alu_peak, "traffic": None,
+                     "kernel": "das_tiled_kernel", "peak_src": "%d SMs x 128 FP32 lanes x %.0f MHz"
+                     % (sms, peaks["sm_max_mhz"]), "ops_per_sum": ops_per_sum},
+        "roofline_decode": {"bound": "hbm", "achieved": dec_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": dec_achieved / peaks["hbm_gbs"], "traffic": None,
+                            "kernel": "decode_mma_kernel", "peak_src": peaks["src"]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(rf_host.numel() * 2),
+                "d2h_bytes_per_step": int(img_host.numel() * 4), "ms_per_step": e2e_ms},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, det = cpu_baseline(frame)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
+                                "sample": det["sample"]}
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

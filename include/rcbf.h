@@ -180,7 +180,12 @@ int rcbf_decode(rcbf_plan_t plan, const int16_t* rf, void* decoded, void* stream
  *   apod     device float32 [n_ch] per-channel weights w_j, or NULL (all 1)
  *   c        speed of sound for this call; <= 0 uses params.c
  *   image    device float32 [nz][ny][nx] (x2 planes for RCBF_CF32), overwritten
- * Accumulation is FP32. Errors: RCBF_EINVAL, RCBF_EUNSUPPORTED, RCBF_ECUDA. */
+ * Accumulation is FP32. The tiled form (params.das_variant = RCBF_DAS_TILED)
+ * needs n_tx % 8 == 0 (4 for complex), n_ch % 8 == 0, an image axis parallel
+ * to the transmit line elements, and voxel tiles that reach at most 128
+ * samples of a trace (any grid finer than about a quarter of the pulse
+ * length); a grid too coarse for that runs the plain form instead.
+ * Errors: RCBF_EINVAL, RCBF_EUNSUPPORTED, RCBF_ECUDA. */
 int rcbf_das(rcbf_plan_t plan, const void* decoded, const float* apod, float c,
              float* image, void* stream);
 

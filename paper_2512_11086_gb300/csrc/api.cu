@@ -324,13 +324,14 @@ int rcbf_das(rcbf_plan_t plan, const void* decoded, const float* apod, float c, 
     if (tiled && !h.tiled_ok)
         return set_error(RCBF_EUNSUPPORTED, "rcbf_das: the tiled form needs n_ch % 8 == 0, n_tx % 8 == 0 "
                                             "(4 for complex) and an image axis parallel to the transmit elements");
-    int rc = das_prepare(h, cc, &a, &why);
-    if (tiled && rc != RCBF_OK) return set_error(rc, why);
+    // a grid so coarse that a 1024-voxel tile reaches more than 128 samples
+    // of a trace runs the plain GPU form (same result within the bound)
+    const bool fits = das_prepare(h, cc, &a, &why) == RCBF_OK;
     a.rf = decoded;
     a.apod = apod;
     a.image = image;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    return tiled ? launch_das(h, a, s) : launch_das_plain(h, a, s);
+    return tiled && fits ? launch_das(h, a, s) : launch_das_plain(h, a, s);
 }
 
 int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, float c,

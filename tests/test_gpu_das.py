@@ -65,14 +65,33 @@ def test_tiny_bscan_full_image(variant):
     assert _report("tiny v%d" % variant, got, want) <= TOL
 
 
+def _dense_tiny():
+    # the tiny acquisition on a grid fine enough for every tile shape to stay
+    # within the tiled kernel's 128-sample window
+    fr = frame("tiny")
+    g = synth.tiny_bscan_geometry()
+    g.out_dims = (128, 1, 512)
+    return fr, g
+
+
 @pytest.mark.parametrize("tile", [(32, 1, 32), (64, 1, 16), (128, 1, 8)])
 def test_tiny_bscan_every_tile_shape(tile):
-    fr = frame("tiny")
-    g = fr.geometry
+    fr, g = _dense_tiny()
     _, exact = _decoded_exact(fr)
-    want = oracle.das(g, exact)
-    got = _gpu_image(g, exact.astype(np.float32), tile=tile)
+    vox = sample_voxels(g.out_dims, 6000, seed=5)
+    want = oracle.das(g, exact, voxels=vox)
+    got = _gpu_image(g, exact.astype(np.float32), tile=tile).ravel()[vox]
     assert _report("tiny tile %s" % (tile,), got, want) <= TOL
+
+
+def test_coarse_grid_runs_plain_form():
+    # 1024-voxel tiles of this grid reach more than 128 samples: the library
+    # runs the plain GPU form, still within the bound
+    g = synth.Geometry(n_tx=16, n_ch=16, n_samples=512, out_dims=(40, 12, 20),
+                       out_min=(-1.5 * MM, -1 * MM, 3 * MM), out_max=(1.5 * MM, 1 * MM, 9 * MM))
+    r = np.random.default_rng(31).normal(size=(16, 16, 512))
+    got = _gpu_image(g, r.astype(np.float32))
+    assert _report("coarse volume", got, oracle.das(g, r)) <= TOL
 
 
 def test_full_bscan_sampled_voxels_f32():
@@ -147,8 +166,8 @@ def test_speed_of_sound_override():
 
 
 def test_complex_input():
-    g = synth.Geometry(n_tx=32, n_ch=32, n_samples=1024, out_dims=(96, 1, 80),
-                       out_min=(-3 * MM, 0.0, 4 * MM), out_max=(3 * MM, 0.0, 20 * MM))
+    g = synth.Geometry(n_tx=32, n_ch=32, n_samples=1024, out_dims=(128, 1, 256),
+                       out_min=(-3 * MM, 0.0, 4 * MM), out_max=(3 * MM, 0.0, 14 * MM))
     fr = synth.make_frame(g, seed=9, n_scatterers=6, analytic=True, noise_frac=0.0)
     r = fr.decoded.astype(np.complex128)
     want = oracle.das(g, r)
@@ -160,10 +179,10 @@ def test_complex_input():
 def test_ragged_tiles_and_record_edges():
     # image sizes that are not tile multiples, and a time origin that puts
     # part of every window before sample 0 or past the end of the record
-    for t0 in (-8e-6, 0.0, 30e-6):
-        g = synth.Geometry(n_tx=32, n_ch=16, n_samples=1024, t0=t0, out_dims=(70, 1, 45),
+    for k, t0 in enumerate((-8e-6, 0.0, 30e-6)):
+        g = synth.Geometry(n_tx=32, n_ch=16, n_samples=1024, t0=t0, out_dims=(70, 1, 450),
                            out_min=(-2 * MM, 0.0, 2 * MM), out_max=(2 * MM, 0.0, 28 * MM))
-        rng = np.random.default_rng(int(t0 * 1e7) + 50)
+        rng = np.random.default_rng(50 + k)
         r = rng.normal(size=(g.n_tx, g.n_ch, g.n_samples))
         want = oracle.das(g, r)
         got = _gpu_image(g, r.astype(np.float32))
@@ -174,8 +193,8 @@ def test_cross_plane_orientation_swap():
     # second plane of a cross-plane pair: columns transmit, rows receive,
     # image in the y-z plane (nx = 1)
     g = synth.Geometry(n_tx=32, n_ch=32, n_samples=1024, tx_orientation=synth.COLUMNS,
-                       rx_orientation=synth.ROWS, hadamard_order=32, out_dims=(1, 100, 90),
-                       out_min=(0.0, -3 * MM, 4 * MM), out_max=(0.0, 3 * MM, 22 * MM))
+                       rx_orientation=synth.ROWS, hadamard_order=32, out_dims=(1, 128, 256),
+                       out_min=(0.0, -3 * MM, 4 * MM), out_max=(0.0, 3 * MM, 16 * MM))
     fr = synth.make_frame(g, seed=21, n_scatterers=5, box_y=(-2 * MM, 2 * MM))
     D = oracle.decode(fr.rf)
     exact = D.astype(np.float64) / g.n_tx
@@ -185,20 +204,19 @@ def test_cross_plane_orientation_swap():
 
 
 def test_small_volume_every_row_split():
-    g = synth.Geometry(n_tx=16, n_ch=16, n_samples=512, out_dims=(40, 12, 20),
-                       out_min=(-1.5 * MM, -1 * MM, 3 * MM), out_max=(1.5 * MM, 1 * MM, 9 * MM))
-    rng = np.random.default_rng(31)
-    r = rng.normal(size=(16, 16, 512))
+    g = synth.Geometry(n_tx=16, n_ch=16, n_samples=512, out_dims=(70, 16, 48),
+                       out_min=(-1.5 * MM, -0.5 * MM, 3 * MM), out_max=(1.5 * MM, 0.5 * MM, 4.5 * MM))
+    r = np.random.default_rng(31).normal(size=(16, 16, 512))
     want = oracle.das(g, r)
-    for tile in [(32, 4, 8), (32, 1, 32), (64, 2, 8), (128, 2, 4)]:
+    for tile in [(32, 4, 8), (32, 1, 32), (64, 2, 8), (64, 16, 1), (128, 1, 8)]:
         got = _gpu_image(g, r.astype(np.float32), tile=tile)
         assert _report("volume tile %s" % (tile,), got, want) <= TOL
 
 
 def test_point_scatterer_peak_matches_oracle():
-    g = synth.Geometry(n_tx=32, n_ch=32, n_samples=1024, hadamard_order=32, out_dims=(41, 1, 41),
+    g = synth.Geometry(n_tx=32, n_ch=32, n_samples=1024, hadamard_order=32, out_dims=(81, 1, 81),
                        out_min=(-2 * MM, 0.0, 8 * MM), out_max=(2 * MM, 0.0, 12 * MM))
-    node = (27, 0, 13)
+    node = (54, 0, 26)
     p = [g.out_min[d] + node[d] * (g.out_max[d] - g.out_min[d]) / max(g.out_dims[d] - 1, 1) for d in range(3)]
     fr = synth.make_frame(g, seed=0, n_scatterers=1, box_x=(p[0], p[0]), box_z=(p[2], p[2]), noise_frac=0.0)
     plan = rc.Plan(rc.make_params(g, decoded_dtype="f32"))
