@@ -280,6 +280,20 @@ def main():
     plain_ms = max_over_ranks(p0.elapsed_time(p1)) / plain_steps
     plain_value = sums / (plain_ms * 1e-3) / 1e9
 
+    # ---- the exact byte-split FP16 tensor-core decode, same output, same frames
+    f16dec = rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=rc.DECODE_MMA_F16,
+                                    das_variant=rc.DAS_TILED))
+    for s in range(3):
+        f16dec.decode(rf[s % RING], out=dec16[s % RING])
+    torch.cuda.synchronize()
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q0.record(stream)
+    for s in range(args.steps):
+        f16dec.decode(rf[s % RING], out=dec16[s % RING])
+    q1.record(stream)
+    torch.cuda.synchronize()
+    t_dec_f16 = q0.elapsed_time(q1) / args.steps
+
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     pinned = [rf_host.pin_memory() for _ in range(RING)]
     img_host = torch.empty(tuned.image_shape, dtype=torch.float32).pin_memory()
@@ -301,6 +315,7 @@ def main():
     e2e_ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
     e2e_value = sums * ws / (e2e_ms * 1e-3) / 1e9
 
+    info = tuned.info()
     # ---- roofline: DAS (dominant) against the FP32 ALU peak; decode against HBM
     peaks = _peaks()
     props = torch.cuda.get_device_properties(dev)
@@ -321,7 +336,7 @@ def main():
                          % (RING, rf_host.numel() * 2 >> 20, RING * rf_host.numel() * 2 >> 20),
                    "parallelism": "independent frames per GPU" if ws > 1 else "1 GPU"},
         "frames_per_s": 1e3 / ms_step * ws,
-        "kernel_ms": {"decode": t_dec, "das": t_das},
+        "kernel_ms": {"decode": t_dec, "das": t_das, "decode_f16_mma_alternative": t_dec_f16},
         "das_only_gsums_per_s": sums / (t_das * 1e-3) / 1e9,
         "plain_fp32": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_ms,
                        "speedup_of_tuned": value / plain_value},
@@ -334,7 +349,8 @@ def main():
                             "kernel": "decode_mma_kernel", "peak_src": peaks["src"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(rf_host.numel() * 2),
                 "d2h_bytes_per_step": int(img_host.numel() * 4), "ms_per_step": e2e_ms},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (info["decode_launches"] + info["das_launches"]) * args.steps,
+        "plan": info,
         "clocks": clk,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

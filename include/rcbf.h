@@ -95,7 +95,9 @@ enum rcbf_interp { RCBF_LINEAR = 0 };
 
 enum rcbf_decode_variant {
     RCBF_DECODE_MMA_I8  = 0,  /* split-byte int8 tensor-core GEMM (mma.sync s8/u8), exact */
-    RCBF_DECODE_PLAIN   = 1   /* plain CUDA-core form: one thread per output, int32 sums */
+    RCBF_DECODE_PLAIN   = 1,  /* plain CUDA-core form: one thread per output, int32 sums */
+    RCBF_DECODE_MMA_F16 = 2   /* split-byte FP16 tensor-core GEMM (bytes and +-1 exact in
+                                 FP16, FP32 accumulation exact below 2^24), exact */
 };
 
 enum rcbf_das_variant {
@@ -154,6 +156,21 @@ typedef struct rcbf_batch_s* rcbf_batch_t;
  * Passage: §METHODS "Data Processing" (data description, array geometry,
  * image region and resolution) and Fig. "das_dispatch" (voxel-index affine). */
 int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan);
+
+/* What a plan chose, for callers that size, schedule or count work. */
+typedef struct rcbf_plan_info {
+    uint32_t tile[3];          /* DAS voxel tile (bu, bv, bw) */
+    uint32_t tiled;            /* 1 if rcbf_das runs the tiled form at params.c, 0 if the plain form */
+    uint32_t window;           /* samples per (transmit, channel) window of a tile at params.c */
+    uint32_t n_split;          /* channels of a tile split over this many work units (1 = none) */
+    uint32_t das_launches;     /* kernels one rcbf_das call enqueues at params.c */
+    uint32_t decode_launches;  /* kernels one rcbf_decode call enqueues (0 without Hadamard order) */
+    uint64_t workspace_bytes;  /* device memory the plan owns */
+} rcbf_plan_info;
+
+/* rcbf_plan_query — describe a plan (host only, no CUDA call).
+ * Errors: RCBF_EINVAL (NULL plan or info). */
+int rcbf_plan_query(rcbf_plan_t plan, rcbf_plan_info* info);
 
 /* rcbf_destroy — free the plan's device tables. NULL is accepted. Must not be
  * called while work using the plan is still pending on a stream. */

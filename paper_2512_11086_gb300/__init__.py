@@ -26,7 +26,7 @@ I16, I32, F32, F16, CF32 = 0, 1, 2, 3, 4
 FORCES, HERCULES = 0, 1
 ROWS, COLUMNS = 0, 1
 LINEAR = 0
-DECODE_MMA_I8, DECODE_PLAIN = 0, 1
+DECODE_MMA_I8, DECODE_PLAIN, DECODE_MMA_F16 = 0, 1, 2
 DAS_TILED, DAS_PLAIN = 0, 1
 
 _DTYPE_NAMES = {"i32": I32, "f32": F32, "f16": F16, "cf32": CF32}
@@ -57,11 +57,21 @@ class Params(ctypes.Structure):
     ]
 
 
+class PlanInfo(ctypes.Structure):
+    """ctypes mirror of ``rcbf_plan_info``."""
+    _fields_ = [
+        ("tile", ctypes.c_uint32 * 3), ("tiled", ctypes.c_uint32), ("window", ctypes.c_uint32),
+        ("n_split", ctypes.c_uint32), ("das_launches", ctypes.c_uint32),
+        ("decode_launches", ctypes.c_uint32), ("workspace_bytes", ctypes.c_uint64),
+    ]
+
+
 # symbol -> (restype, argtypes); every function rcbf.h declares
 _P = ctypes.c_void_p
 SIGNATURES = {
     "rcbf_plan": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(_P)]),
     "rcbf_destroy": (None, [_P]),
+    "rcbf_plan_query": (ctypes.c_int, [_P, ctypes.POINTER(PlanInfo)]),
     "rcbf_decode": (ctypes.c_int, [_P, _P, _P, _P]),
     "rcbf_das": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, _P, _P]),
     "rcbf_das_backward": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, _P, _P, _P, _P, _P]),
@@ -179,6 +189,14 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def info(self) -> dict:
+        """rcbf_plan_query as a dict."""
+        pi = PlanInfo()
+        _check(load_library().rcbf_plan_query(self.handle, ctypes.byref(pi)))
+        return {"tile": tuple(pi.tile), "tiled": bool(pi.tiled), "window": pi.window,
+                "n_split": pi.n_split, "das_launches": pi.das_launches,
+                "decode_launches": pi.decode_launches, "workspace_bytes": pi.workspace_bytes}
 
     def decoded_torch_dtype(self):
         import torch

@@ -2,6 +2,7 @@
 // construction (geometry affine, decode fragments, DAS tile choice), error
 // reporting and dispatch to the kernels. Every check happens on the host
 // before a launch; on error nothing is enqueued.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -63,6 +64,30 @@ std::vector<uint32_t> build_afrag(const std::vector<int8_t>& H, int n) {
     return out;
 }
 
+// A = H^T fragments of mma.m16n8k16 (row-major A, FP16 +-1): register r of
+// lane (g, t) holds rows g (+8 for r odd) and k pair 2t, 2t+1 (+8 for r >= 2).
+std::vector<uint32_t> build_afrag16(const std::vector<int8_t>& H, int n) {
+    const int MT = n / 16, KC = n / 16;
+    std::vector<uint32_t> out((size_t)MT * KC * 32 * 4);
+    for (int mt = 0; mt < MT; ++mt)
+        for (int kc = 0; kc < KC; ++kc)
+            for (int lane = 0; lane < 32; ++lane) {
+                const int g = lane >> 2, t = lane & 3;
+                for (int r = 0; r < 4; ++r) {
+                    const int row = mt * 16 + g + ((r & 1) ? 8 : 0);
+                    const int k0 = kc * 16 + 2 * t + ((r >= 2) ? 8 : 0);
+                    uint32_t word = 0;
+                    for (int e = 0; e < 2; ++e) {
+                        const int8_t v = H[(size_t)(k0 + e) * n + row];
+                        const uint32_t bits = v > 0 ? 0x3C00u : 0xBC00u;   // FP16 +1 / -1
+                        word |= bits << (16 * e);
+                    }
+                    out[(((size_t)mt * KC + kc) * 32 + lane) * 4 + r] = word;
+                }
+            }
+    return out;
+}
+
 void mat_mul_3x4(const double* X /*4x4*/, const double* M /*4x4*/, double* G /*3x4*/) {
     for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 4; ++c) {
@@ -111,7 +136,7 @@ int validate(const rcbf_params* p) {
     if (p->decoded_dtype != RCBF_I32 && p->decoded_dtype != RCBF_F32 && p->decoded_dtype != RCBF_F16 &&
         p->decoded_dtype != RCBF_CF32)
         return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: decoded_dtype must be RCBF_I32, RCBF_F32, RCBF_F16 or RCBF_CF32");
-    if (p->decode_variant > RCBF_DECODE_PLAIN || p->das_variant > RCBF_DAS_PLAIN)
+    if (p->decode_variant > RCBF_DECODE_MMA_F16 || p->das_variant > RCBF_DAS_PLAIN)
         return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: unknown variant");
     if (p->hadamard_order) {
         if (p->hadamard_order != p->n_tx)
@@ -120,7 +145,7 @@ int validate(const rcbf_params* p) {
             return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: complex data cannot be Hadamard-decoded");
         if (!p->decode_matrix && !is_pow2(p->n_tx))
             return set_error(RCBF_EINVAL, "rcbf_plan: a Sylvester order must be a power of two");
-        if (p->decode_variant == RCBF_DECODE_MMA_I8 && !(p->n_tx == 32 || p->n_tx == 64 || p->n_tx == 128 || p->n_tx == 256))
+        if (p->decode_variant != RCBF_DECODE_PLAIN && !(p->n_tx == 32 || p->n_tx == 64 || p->n_tx == 128 || p->n_tx == 256))
             return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: the tensor-core decode needs n_tx in {32, 64, 128, 256}");
         if (p->decode_variant == RCBF_DECODE_PLAIN && p->n_tx % 16)
             return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: the plain decode needs n_tx a multiple of 16");
@@ -232,11 +257,15 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
     int best_bu = 64, best_bv = 1, best_bw = 16;
     if (p.tile[0]) {
         best_bu = (int)p.tile[0];
-        // the given tile is in image axes (x, y, z); the lane axis is u
-        best_bv = (int)(ua == 0 ? p.tile[1] : p.tile[1]);
+        best_bv = (int)p.tile[1];
         best_bw = (int)p.tile[2];
     } else {
-        double best = 1e300;
+        // window length (in samples) of a shape at the plan's speed of sound;
+        // prefer shapes whose windows fit the 64-interval class, then more
+        // voxels per thread along u (fewer transmit-term loads per sum),
+        // then the shorter window
+        const double spm = p.fs / p.c;
+        double best_key = 1e300;
         const int bus[3] = {128, 64, 32};
         for (int bi = 0; bi < 3; ++bi) {
             const int bu = bus[bi];
@@ -244,8 +273,9 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
             for (int bv = 1; bv <= rows; bv *= 2) {
                 const int bw = rows / bv;
                 if (bv > 1 && a.n_v == 1) continue;
-                const double r = radius_sum(bu, bv, bw);
-                if (r < best * (1.0 - 1e-9)) { best = r; best_bu = bu; best_bv = bv; best_bw = bw; }
+                const double W = std::floor(4.0 + 2.0 * radius_sum(bu, bv, bw) * spm + 0.01) + 1.0;
+                const double key = (W <= 64 ? 0.0 : 1e6) + (W <= 64 ? (128 - bu) * 100.0 : 0.0) + W;
+                if (key < best_key) { best_key = key; best_bu = bu; best_bv = bv; best_bw = bw; }
             }
         }
     }
@@ -285,11 +315,56 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
             if (cudaMalloc(&h.d_afrag, fr.size() * 4) != cudaSuccess) return fail(RCBF_ENOMEM, "rcbf_plan: cudaMalloc fragments");
             if (cudaMemcpy(h.d_afrag, fr.data(), fr.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
                 return fail(RCBF_ECUDA, "rcbf_plan: copy fragments");
+            const std::vector<uint32_t> f16 = build_afrag16(H, n);
+            if (cudaMalloc(&h.d_afrag16, f16.size() * 4) != cudaSuccess) return fail(RCBF_ENOMEM, "rcbf_plan: cudaMalloc fragments");
+            if (cudaMemcpy(h.d_afrag16, f16.data(), f16.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(RCBF_ECUDA, "rcbf_plan: copy fragments");
+            std::vector<int> hs(n, 0);
+            for (int k = 0; k < n; ++k)
+                for (int i = 0; i < n; ++i) hs[i] += H[(size_t)k * n + i];
+            if (cudaMalloc(&h.d_hsum, hs.size() * 4) != cudaSuccess) return fail(RCBF_ENOMEM, "rcbf_plan: cudaMalloc sums");
+            if (cudaMemcpy(h.d_hsum, hs.data(), hs.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(RCBF_ECUDA, "rcbf_plan: copy sums");
         }
         if ((rc = configure_decode(h)) != RCBF_OK) { std::string m = g_last_error; rcbf_destroy(plan); return set_error(rc, m); }
     }
     if ((rc = configure_das(h)) != RCBF_OK) { std::string m = g_last_error; rcbf_destroy(plan); return set_error(rc, m); }
+    {
+        const int sp = std::max(h.n_split[0], h.n_split[1]);
+        if (sp > 1) {
+            h.partial_floats = (size_t)sp * a.image_plane * (p.decoded_dtype == RCBF_CF32 ? 2 : 1);
+            if (cudaMalloc(&h.d_partial, h.partial_floats * sizeof(float)) != cudaSuccess)
+                return fail(RCBF_ENOMEM, "rcbf_plan: cudaMalloc partial images");
+        }
+    }
     *out_plan = plan;
+    return RCBF_OK;
+}
+
+int rcbf_plan_query(rcbf_plan_t plan, rcbf_plan_info* info) {
+    if (!plan || !info) return set_error(RCBF_EINVAL, "rcbf_plan_query: NULL argument");
+    const PlanHost& h = plan->h;
+    std::memset(info, 0, sizeof(*info));
+    info->tile[0] = (uint32_t)h.das.bu;
+    info->tile[1] = (uint32_t)h.das.bv;
+    info->tile[2] = (uint32_t)h.das.bw;
+    DasArgs a;
+    std::string why;
+    const bool fits = das_prepare(h, h.p.c, &a, &why) == RCBF_OK;
+    const bool tiled = h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok && fits;
+    info->tiled = tiled ? 1u : 0u;
+    info->window = (uint32_t)a.W;
+    const int sp = tiled ? std::max(1, h.n_split[a.W <= 64 ? 0 : 1]) : 1;
+    info->n_split = (uint32_t)sp;
+    info->das_launches = sp > 1 ? 2u : 1u;
+    info->decode_launches = h.p.hadamard_order ? 1u : 0u;
+    uint64_t bytes = sizeof(int) + h.partial_floats * sizeof(float);
+    if (h.p.hadamard_order) {
+        const uint64_t n = h.p.n_tx;
+        bytes += n * n + n * sizeof(int);
+        if (n % 32 == 0) bytes += 2 * (n / 16) * (n / 32) * 32 * 16 + (n / 16) * (n / 16) * 32 * 16 / 2;
+    }
+    info->workspace_bytes = bytes;
     return RCBF_OK;
 }
 
@@ -298,7 +373,10 @@ void rcbf_destroy(rcbf_plan_t plan) {
     PlanHost& h = plan->h;
     if (h.d_afrag) cudaFree(h.d_afrag);
     if (h.d_hmat) cudaFree(h.d_hmat);
+    if (h.d_afrag16) cudaFree(h.d_afrag16);
+    if (h.d_hsum) cudaFree(h.d_hsum);
     if (h.d_status) cudaFree(h.d_status);
+    if (h.d_partial) cudaFree(h.d_partial);
     delete plan;
 }
 

@@ -5,6 +5,7 @@
 // voxel cached per thread), fractional sample s = (d_tx + d_rx) fs / c - t0 fs,
 // floor / fraction, two global loads through the read-only cache and a
 // linear interpolation with zero outside the record.
+#include <algorithm>
 #include <cmath>
 
 #include "internal.cuh"
@@ -76,6 +77,18 @@ das_plain_kernel(DasArgs a) {
     if (CPLX) a.image[a.image_plane + o] = acci;
 }
 
+// Sum of the channel-split partial images in split order (deterministic).
+__global__ void __launch_bounds__(256)
+das_reduce_kernel(const float* __restrict__ partial, float* __restrict__ image, long long n,
+                  long long stride, int n_split) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float acc = partial[i];
+        for (int k = 1; k < n_split; ++k) acc += partial[(long long)k * stride + i];
+        image[i] = acc;
+    }
+}
+
 }  // namespace
 
 int launch_das_plain(const PlanHost& h, const DasArgs& a, cudaStream_t s) {
@@ -120,15 +133,26 @@ int das_prepare(const PlanHost& h, double c, DasArgs* a, std::string* why) {
 
 static int stride_class(int W) { return W <= 64 ? 64 : 128; }
 
-int launch_das(const PlanHost& h, const DasArgs& a, cudaStream_t s) {
+int launch_das(const PlanHost& h, const DasArgs& a_in, cudaStream_t s) {
+    DasArgs a = a_in;
     const int ws = stride_class(a.W);
     const bool cplx = a.dtype == RCBF_CF32;
     const bool apod = a.apod != nullptr || a.f_number > 0.f;
+    a.n_split = std::max(1, h.n_split[ws == 64 ? 0 : 1]);
+    a.partial = h.d_partial;
+    a.partial_stride = a.image_plane * (cplx ? 2 : 1);
+    int rc;
     switch (h.vu) {
-        case 1: return launch_das_vu<1>(a, ws, cplx, apod, s);
-        case 2: return launch_das_vu<2>(a, ws, cplx, apod, s);
-        default: return launch_das_vu<4>(a, ws, cplx, apod, s);
+        case 1: rc = launch_das_vu<1>(a, ws, cplx, apod, s); break;
+        case 2: rc = launch_das_vu<2>(a, ws, cplx, apod, s); break;
+        default: rc = launch_das_vu<4>(a, ws, cplx, apod, s); break;
     }
+    if (rc != RCBF_OK || a.n_split == 1) return rc;
+    const long long n = a.partial_stride;
+    long long blocks = (n + 255) / 256;
+    if (blocks > (long long)h.n_sms * 8) blocks = (long long)h.n_sms * 8;
+    das_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(a.partial, a.image, n, a.partial_stride, a.n_split);
+    return check_launch("das_reduce_kernel");
 }
 
 int configure_das(PlanHost& h) {
@@ -144,6 +168,22 @@ int configure_das(PlanHost& h) {
         }
         if (rc != RCBF_OK) return rc;
         h.das_blocks_per_sm[c] = n;
+        // channel split: the smallest power of two (dividing the channel
+        // chunks) whose work units fill the resident CTA slots to >= 95 %
+        const long long tiles = (long long)h.das.tiles_u * h.das.tiles_v * h.das.tiles_w;
+        const long long slots = (long long)h.n_sms * (n > 0 ? n : 1);
+        const int chunks = (int)h.p.n_ch / kCJ;
+        int best = 1;
+        double best_eff = 0;
+        for (int sp = 1; sp <= chunks && sp <= 16; sp *= 2) {
+            if (chunks % sp) break;
+            const long long units = tiles * sp;
+            const long long waves = (units + slots - 1) / slots;
+            const double eff = (double)units / (double)(waves * slots);
+            if (eff > best_eff + 1e-9) { best_eff = eff; best = sp; }
+            if (eff >= 0.95) break;
+        }
+        h.n_split[c] = best;
     }
     return RCBF_OK;
 }

@@ -8,7 +8,7 @@
 namespace rcbf {
 
 template <int VU, int WS, bool CPLX, bool APOD>
-__global__ void __launch_bounds__(kDasThreads, (WS <= 64) ? 2 : 1)
+__global__ void __launch_bounds__(kDasThreads, 2)
 das_tiled_kernel(DasArgs a) {
     using C = DasCfg<VU, WS, CPLX>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -20,7 +20,7 @@ das_tiled_kernel(DasArgs a) {
     }
     __syncthreads();
     DasPipe pipe{0u};
-    if (!das_tile<VU, WS, CPLX, APOD>(a, blockIdx.x, smem, pipe) && threadIdx.x == 0)
+    if (!das_unit<VU, WS, CPLX, APOD>(a, blockIdx.x, smem, pipe) && threadIdx.x == 0)
         atomicOr(a.status, kStatusWaitExpired);
 }
 
@@ -53,7 +53,7 @@ int configure_das_vu(int ws, bool cplx, int* per_sm) {
 
 template <int VU>
 int launch_das_vu(const DasArgs& a, int ws, bool cplx, bool apod, cudaStream_t s) {
-    const unsigned grid = (unsigned)a.tiles_u * a.tiles_v * a.tiles_w;
+    const unsigned grid = (unsigned)a.tiles_u * a.tiles_v * a.tiles_w * a.n_split;
 #define RCBF_LAUNCH(WSV, CP, AP)                                                                   \
     das_tiled_kernel<VU, WSV, CP, AP><<<grid, kDasThreads, DasCfg<VU, WSV, CP>::SMEM, s>>>(a);    \
     return check_launch("das_tiled_kernel");

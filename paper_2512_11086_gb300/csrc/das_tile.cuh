@@ -1,8 +1,12 @@
-// das_tile.cuh — one voxel tile of the delay-and-sum of Eq. (1)
-// (§THEORY "Synthetic Aperture Imaging"; §OPTIMIZATIONS "DAS").
+// das_tile.cuh — one work unit (a voxel tile x a range of receive channels)
+// of the delay-and-sum of Eq. (1) (§THEORY "Synthetic Aperture Imaging";
+// §OPTIMIZATIONS "DAS").
 //
 // A CTA of 256 threads beamforms a tile of 1024 voxels, 4 per thread, and
-// walks the (transmit, channel) plane in stages of CI x CJ windows.
+// walks its part of the (transmit, channel) plane in stages of CI x CJ
+// windows. A plan may split the channels of a tile over several units (to
+// fill every SM); each unit then writes a partial image and a reduce kernel
+// adds the partials in a fixed order.
 //
 // Delays. For the tile centre q_ref the FP64 reference distance of every
 // element is split into an integer sample K and a fractional remainder; a
@@ -20,9 +24,14 @@
 // copies each window into shared memory, where it is rewritten as W line
 // pieces (c_n, slope_n): r(x) = c_n + u * slope_n on sample interval n, u
 // being the window-centred position. The inner loop per voxel and (i, j) is
-// then: u = alpha_i + beta_j; t = u + 2^23 + H (the integer part of t is the
+// then: u = alpha_i + beta_j; t = u + 2^23 + H (the low bits of t are the
 // interval n); one 8-byte shared load; one FMA for the interpolated sample;
 // one add (or FMA with the apodization weight a_j(v) of Eq. (2)-(3)).
+//
+// Pipeline (one CTA barrier per stage): during stage s every warp first
+// rewrites the raw windows of stage s+1 (landed by TMA two stages earlier)
+// into the second line-piece buffer, then sums stage s from the first; after
+// the barrier the raw buffer just rewritten is refilled with stage s+3.
 #pragma once
 
 #include <type_traits>
@@ -44,23 +53,26 @@ struct DasCfg {
     static constexpr int VR = 4 / VU;              // tile rows per thread
     static constexpr int ROWS = 8 * VR;            // tile rows (one warp covers VR rows)
     static constexpr int BU = 32 * VU;             // tile extent along u
-    static constexpr int CI = CPLX ? 4 : 8;        // transmits per stage
+    // transmits per stage: every variant stages 32 KB of line pieces
+    static constexpr int CI = (CPLX ? 4 : 8) / (WS > 64 ? 2 : 1);
     static constexpr int CJ = 8;                   // channels per stage
     static constexpr int NWIN = CI * CJ;           // windows per stage
-    static constexpr int COPIES = 64;              // bulk copies per stage (windows x planes)
+    static constexpr int COPIES = NWIN * (CPLX ? 2 : 1);   // bulk copies per stage (windows x planes)
     static constexpr int PAIR_BYTES = CPLX ? 16 : 8;
     static constexpr int RAWS = WS + 8;            // raw samples per window plane (max)
     static constexpr int RAW_WIN_BYTES = RAWS * 4 * (CPLX ? 2 : 1);
-    static constexpr int OFF_TX = 0;                               // float4[kMaxOrder]
-    static constexpr int OFF_RX = OFF_TX + kMaxOrder * 16;         // float4[kMaxChannels]
-    static constexpr int OFF_ALPHA = OFF_RX + kMaxChannels * 16;   // float[CI][ROWS]
-    static constexpr int OFF_WOFF = OFF_ALPHA + CI * ROWS * 4;     // int[2][NWIN]
-    static constexpr int OFF_BAR = OFF_WOFF + 2 * NWIN * 4;        // uint64[2]
-    static constexpr int OFF_PAIRS = ((OFF_BAR + 16 + 127) / 128) * 128;
-    static constexpr int OFF_RAW = OFF_PAIRS + NWIN * WS * PAIR_BYTES;
-    static constexpr int SMEM = OFF_RAW + 2 * NWIN * RAW_WIN_BYTES;
+    static constexpr int PAIR_BUF = NWIN * WS * PAIR_BYTES;
+    static constexpr int OFF_PAIRS = 0;                                // 2 line-piece buffers
+    static constexpr int OFF_RAW = OFF_PAIRS + 2 * PAIR_BUF;           // 2 raw window buffers
+    static constexpr int OFF_TX = OFF_RAW + 2 * NWIN * RAW_WIN_BYTES;  // float4[kMaxOrder]
+    static constexpr int OFF_RX = OFF_TX + kMaxOrder * 16;             // float4[kMaxChannels]
+    static constexpr int OFF_ALPHA = OFF_RX + kMaxChannels * 16;       // float[2][CI][ROWS]
+    static constexpr int OFF_WOFF = OFF_ALPHA + 2 * CI * ROWS * 4;     // int[2][NWIN]
+    static constexpr int OFF_BAR = OFF_WOFF + 2 * NWIN * 4;            // uint64[2]
+    static constexpr int SMEM = OFF_BAR + 16;
     static_assert(CI * ROWS <= kDasThreads, "alpha table needs one thread per entry");
-    static_assert(NWIN * (CPLX ? 2 : 1) == COPIES, "one issuing thread per copy");
+    static_assert(COPIES <= kDasThreads, "one issuing thread per copy");
+    static_assert(OFF_RAW % 128 == 0 && OFF_TX % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
 };
 
 template <int OFF>
@@ -85,21 +97,50 @@ __device__ __forceinline__ float hann_weight(float f_number, float lat, float z)
     return cs * cs;
 }
 
-__device__ __forceinline__ float load_sample(const unsigned char* raw, int dtype, int n, float scale) {
-    if (dtype == RCBF_F16) return __half2float(reinterpret_cast<const __half*>(raw)[n]);
-    if (dtype == RCBF_I32) return (float)reinterpret_cast<const int*>(raw)[n] * scale;
-    return reinterpret_cast<const float*>(raw)[n];
+template <class T> __device__ __forceinline__ float to_f32(T v, float scale);
+template <> __device__ __forceinline__ float to_f32<float>(float v, float) { return v; }
+template <> __device__ __forceinline__ float to_f32<__half>(__half v, float) { return __half2float(v); }
+template <> __device__ __forceinline__ float to_f32<int>(int v, float scale) { return (float)v * scale; }
+
+// Raw windows of one stage -> line pieces. Lane l of a warp rewrites the
+// intervals 2l and 2l+1 (three raw samples, one 16-byte store), so a warp
+// covers 64 intervals per pass.
+template <class T, bool CPLX, int WS, int NWIN, int RAWS, int RAW_WIN_BYTES>
+__device__ __forceinline__ void rewrite_windows(const unsigned char* rawb, const int* woff,
+                                                unsigned char* pairs, int W, float hp, float scale,
+                                                int warp, int lane) {
+    for (int win = warp; win < NWIN; win += kDasThreads / 32) {
+        const int off = woff[win];
+        const T* r = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES) + off;
+        const T* ri = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES + RAWS * 4) + off;
+        for (int n = 2 * lane; n < W; n += 64) {
+            const float r0 = to_f32<T>(r[n], scale), r1 = to_f32<T>(r[n + 1], scale);
+            const float r2 = to_f32<T>(r[n + 2], scale);
+            const float s0 = r1 - r0, s1 = r2 - r1;
+            const float c0 = fmaf(hp - (float)n, s0, r0), c1 = fmaf(hp - (float)(n + 1), s1, r1);
+            if (CPLX) {
+                const float i0 = to_f32<T>(ri[n], scale), i1 = to_f32<T>(ri[n + 1], scale);
+                const float i2 = to_f32<T>(ri[n + 2], scale);
+                const float t0 = i1 - i0, t1 = i2 - i1;
+                float4* p = reinterpret_cast<float4*>(pairs + (size_t)(win * WS + n) * 16);
+                p[0] = make_float4(c0, s0, fmaf(hp - (float)n, t0, i0), t0);
+                p[1] = make_float4(c1, s1, fmaf(hp - (float)(n + 1), t1, i1), t1);
+            } else {
+                *reinterpret_cast<float4*>(pairs + (size_t)(win * WS + n) * 8) = make_float4(c0, s0, c1, s1);
+            }
+        }
+    }
 }
 
-// Persistent state of a CTA running DAS tiles (mbarrier phases).
+// Persistent state of a CTA running DAS units (mbarrier phases).
 struct DasPipe {
     uint32_t phase;   // bit b: parity of the next phase of mbarrier b
 };
 
-// Returns false when a bounded wait expired (the CTA must stop; the caller
-// records the status).
+// One work unit. Returns false when a bounded wait expired (the CTA must
+// stop; the caller records the status).
 template <int VU, int WS, bool CPLX, bool APOD>
-__device__ __forceinline__ bool das_tile(const DasArgs& a, int tile, unsigned char* smem, DasPipe& pipe) {
+__device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned char* smem, DasPipe& pipe) {
     using C = DasCfg<VU, WS, CPLX>;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float4* s_tx = reinterpret_cast<float4*>(smem + C::OFF_TX);
@@ -111,6 +152,15 @@ __device__ __forceinline__ bool das_tile(const DasArgs& a, int tile, unsigned ch
     unsigned char* raw = smem + C::OFF_RAW;
     const int es = (a.dtype == RCBF_F16) ? 2 : 4;
 
+    // ---- unit -> (tile, channel split)
+    const int n_tiles = a.tiles_u * a.tiles_v * a.tiles_w;
+    const int tile = unit % n_tiles;
+    const int split = unit / n_tiles;
+    const int n_ic = a.n_tx / C::CI;
+    const int js = (a.n_ch / C::CJ) / a.n_split;     // channel chunks of this unit
+    const int jc0 = split * js;
+    const int NS = n_ic * js;
+
     // ---- tile position and FP64 reference delays
     const int tu = tile % a.tiles_u;
     const int tv = (tile / a.tiles_u) % a.tiles_v;
@@ -121,7 +171,8 @@ __device__ __forceinline__ bool das_tile(const DasArgs& a, int tile, unsigned ch
     const double qy = a.q0[1] + a.Gu[1] * cu + a.Gv[1] * cv + a.Gw[1] * cw;
     const double zr = a.q0[2] + a.Gu[2] * cu + a.Gv[2] * cv + a.Gw[2] * cw;
     const double lat_tx_ref = a.tx_axis ? qy : qx, lat_rx_ref = a.rx_axis ? qy : qx;
-    for (int e = tid; e < a.n_tx + a.n_ch; e += kDasThreads) {
+    const int j_lo = jc0 * C::CJ, n_rx = js * C::CJ;
+    for (int e = tid; e < a.n_tx + n_rx; e += kDasThreads) {
         if (e < a.n_tx) {
             const double L = lat_tx_ref - (a.tx_e0 + e * a.tx_pitch);
             const double d = sqrt(L * L + zr * zr);
@@ -132,7 +183,7 @@ __device__ __forceinline__ bool das_tile(const DasArgs& a, int tile, unsigned ch
             const float rho = (float)(A - K - (double)a.lo - 0.5 - (double)a.H);
             s_tx[e] = make_float4((float)L, (float)d, rho, __int_as_float((int)K));
         } else {
-            const int j = e - a.n_tx;
+            const int j = j_lo + e - a.n_tx;
             const double L = lat_rx_ref - (a.rx_e0 + j * a.rx_pitch);
             const double d = sqrt(L * L + zr * zr);
             const double B = d * a.fs_over_c;
@@ -141,8 +192,8 @@ __device__ __forceinline__ bool das_tile(const DasArgs& a, int tile, unsigned ch
         }
     }
 
-    // ---- this thread's voxels: offsets from the reference, in FP32 (exact
-    // half-integer index offsets times the FP32 voxel steps)
+    // ---- voxel offsets from the reference in FP32 (exact half-integer index
+    // offsets times the FP32 voxel steps)
     const float Zf = (float)zr;
     const float fsc = (float)a.fs_over_c;
     const float gur = (float)(a.rx_axis ? a.Gu[1] : a.Gu[0]);
@@ -160,17 +211,13 @@ __device__ __forceinline__ bool das_tile(const DasArgs& a, int tile, unsigned ch
     };
     __syncthreads();   // reference tables ready
 
-    const int n_ic = a.n_tx / C::CI, n_jc = a.n_ch / C::CJ;
-    const int NS = n_ic * n_jc;
-
-    // ---- producer: one thread per bulk copy (window, plane)
+    // ---- producer: one thread per bulk copy (window, plane) into raw buffer b
     auto issue = [&](int s, int b) {
         if (tid < C::COPIES) {
             const int win = CPLX ? (tid >> 1) : tid;
             const int plane = CPLX ? (tid & 1) : 0;
             const int ii = win / C::CJ, jj = win % C::CJ;
-            const int jc = s / n_ic, ic = s % n_ic;
-            const int i = ic * C::CI + ii, j = jc * C::CJ + jj;
+            const int i = (s % n_ic) * C::CI + ii, j = (jc0 + s / n_ic) * C::CJ + jj;
             const int S0 = __float_as_int(s_tx[i].w) + __float_as_int(s_rx[j].w) + a.lo;
             const int A = S0 & ~7;
             if (plane == 0) s_woff[b * C::NWIN + win] = S0 - A;
@@ -193,9 +240,50 @@ __device__ __forceinline__ bool das_tile(const DasArgs& a, int tile, unsigned ch
         }
     };
 
+    // ---- stage preparation: wait for its raw windows, rewrite them into line
+    // pieces (buffer pb) and tabulate its transmit terms (alpha buffer pb)
+    const float hp = 0.5f + (float)a.H;
+    auto prepare = [&](int s, int pb) -> bool {
+        const int b = s & 1;
+        const bool ok = mbar_wait_parity(bar0 + 8 * b, (pipe.phase >> b) & 1u);
+        pipe.phase ^= 1u << b;
+        const unsigned char* rawb = raw + b * C::NWIN * C::RAW_WIN_BYTES;
+        unsigned char* pairs = smem + C::OFF_PAIRS + pb * C::PAIR_BUF;
+        const int* woff = s_woff + b * C::NWIN;
+        if (a.dtype == RCBF_F16)
+            rewrite_windows<__half, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
+        else if (a.dtype == RCBF_I32)
+            rewrite_windows<int, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
+        else
+            rewrite_windows<float, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
+        if (tid < C::CI * C::ROWS) {
+            // transmit terms of this stage for every tile row (alpha depends on the row only)
+            const int ii = tid / C::ROWS, row = tid % C::ROWS;
+            const float dv = (float)(row % a.bv) - 0.5f * (a.bv - 1);
+            const float dw = (float)(row / a.bv) - 0.5f * (a.bw - 1);
+            const float dL = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]) * dv + (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]) * dw;
+            const float dz = (float)a.Gv[2] * dv + (float)a.Gw[2] * dw;
+            const float4 tx = s_tx[(s % n_ic) * C::CI + ii];
+            const float Lv = tx.x + dL, Zv = Zf + dz;
+            const float d = sqrtf(Lv * Lv + Zv * Zv);
+            const float num = dL * (2.0f * tx.x + dL) + dz * (2.0f * Zf + dz);
+            const float al = tx.z + __fdividef(num, d + tx.y) * fsc;
+            s_alpha[pb * C::CI * C::ROWS + ii * C::ROWS + row] = fminf(fmaxf(al, tx.z - a.reach_a), tx.z + a.reach_a);
+        }
+        return ok;
+    };
+
+    // ---- prologue
     issue(0, 0);
     if (NS > 1) issue(1, 1);
     __syncthreads();   // window offsets and zero fills of the first two stages visible
+    bool ok = prepare(0, 0);
+    if (__syncthreads_or(!ok)) {
+        if (!ok) mbar_wait_parity(bar0, (pipe.phase & 1u) ^ 1u);
+        if (NS > 1) mbar_wait_parity(bar0 + 8, (pipe.phase >> 1) & 1u);
+        return false;
+    }
+    if (NS > 2) issue(2, 0);
 
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     float acci[4] = {0.f, 0.f, 0.f, 0.f};
@@ -203,11 +291,10 @@ __device__ __forceinline__ bool das_tile(const DasArgs& a, int tile, unsigned ch
     float apw[4][C::CJ];
     const float magic = 8388608.0f + (float)a.H;     // 2^23 + H
     constexpr int SHIFT = CPLX ? 4 : 3;
-    const uint32_t pbase = pairs_u32 - (0x4B000000u << SHIFT);
 
     for (int s = 0; s < NS; ++s) {
-        const int jc = s / n_ic, ic = s % n_ic;
-        const int b = s & 1;
+        const int ic = s % n_ic, jc = jc0 + s / n_ic;
+        const int pb = s & 1;
         if (ic == 0) {
             // per-voxel receive terms (and apodization) for this channel chunk
 #pragma unroll
@@ -231,62 +318,16 @@ __device__ __forceinline__ bool das_tile(const DasArgs& a, int tile, unsigned ch
                 }
             }
         }
-        const bool ok = mbar_wait_parity(bar0 + 8 * b, (pipe.phase >> b) & 1u);
-        pipe.phase ^= 1u << b;
+        if (s + 1 < NS) ok = prepare(s + 1, pb ^ 1);
 
-        // ---- raw window -> line pieces (c_n, slope_n)
-        const unsigned char* rawb = raw + b * C::NWIN * C::RAW_WIN_BYTES;
-        const float hp = 0.5f + (float)a.H;
-        for (int win = warp; win < C::NWIN; win += kDasThreads / 32) {
-            const int off = s_woff[b * C::NWIN + win];
-            const unsigned char* rw0 = rawb + win * C::RAW_WIN_BYTES;
-            unsigned char* pw = smem + C::OFF_PAIRS + win * WS * C::PAIR_BYTES;
-            for (int n = lane; n < a.W; n += 32) {
-                const float r0 = load_sample(rw0, a.dtype, off + n, a.scale);
-                const float r1 = load_sample(rw0, a.dtype, off + n + 1, a.scale);
-                const float sl = r1 - r0;
-                const float cn = fmaf(hp - (float)n, sl, r0);
-                if (CPLX) {
-                    const unsigned char* rw1 = rw0 + C::RAWS * 4;
-                    const float i0 = load_sample(rw1, a.dtype, off + n, a.scale);
-                    const float i1 = load_sample(rw1, a.dtype, off + n + 1, a.scale);
-                    const float si = i1 - i0;
-                    reinterpret_cast<float4*>(pw)[n] = make_float4(cn, sl, fmaf(hp - (float)n, si, i0), si);
-                } else {
-                    reinterpret_cast<float2*>(pw)[n] = make_float2(cn, sl);
-                }
-            }
-        }
-        // ---- transmit terms of this stage for every tile row (alpha depends on row only)
-        if (tid < C::CI * C::ROWS) {
-            const int ii = tid / C::ROWS, row = tid % C::ROWS;
-            const int rv = row % a.bv, rw = row / a.bv;
-            const float dv = (float)rv - 0.5f * (a.bv - 1);
-            const float dw = (float)rw - 0.5f * (a.bw - 1);
-            const float dL = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]) * dv + (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]) * dw;
-            const float dz = (float)a.Gv[2] * dv + (float)a.Gw[2] * dw;
-            const float4 tx = s_tx[ic * C::CI + ii];
-            const float Lv = tx.x + dL, Zv = Zf + dz;
-            const float d = sqrtf(Lv * Lv + Zv * Zv);
-            const float num = dL * (2.0f * tx.x + dL) + dz * (2.0f * Zf + dz);
-            const float al = tx.z + __fdividef(num, d + tx.y) * fsc;
-            s_alpha[ii * C::ROWS + row] = fminf(fmaxf(al, tx.z - a.reach_a), tx.z + a.reach_a);
-        }
-        if (__syncthreads_or(!ok)) {
-            // a window never arrived: give this CTA's copies still in flight a
-            // bounded chance to land, then stop
-            if (!ok) mbar_wait_parity(bar0 + 8 * b, ((pipe.phase >> b) & 1u) ^ 1u);
-            if (s + 1 < NS) mbar_wait_parity(bar0 + 8 * (b ^ 1), (pipe.phase >> (b ^ 1)) & 1u);
-            return false;
-        }
-        if (s + 2 < NS) issue(s + 2, b);
-
-        // ---- the sum: 4 voxels x CI transmits x CJ channels
+        // ---- the sum: 4 voxels x CI transmits x CJ channels from buffer pb
+        const uint32_t pbase = pairs_u32 + pb * C::PAIR_BUF - (0x4B000000u << SHIFT);
+        const float* alb = s_alpha + pb * C::CI * C::ROWS + warp * C::VR;
         static_for<0, C::CI>([&](auto iic) {
             constexpr int ii = decltype(iic)::value;
             float al[C::VR];
 #pragma unroll
-            for (int kr = 0; kr < C::VR; ++kr) al[kr] = s_alpha[ii * C::ROWS + warp * C::VR + kr];
+            for (int kr = 0; kr < C::VR; ++kr) al[kr] = alb[ii * C::ROWS + kr];
             static_for<0, C::CJ>([&](auto jjc) {
                 constexpr int jj = decltype(jjc)::value;
                 constexpr int OFF = (ii * C::CJ + jj) * WS * C::PAIR_BYTES;
@@ -309,9 +350,19 @@ __device__ __forceinline__ bool das_tile(const DasArgs& a, int tile, unsigned ch
                 }
             });
         });
-        __syncthreads();
+        if (__syncthreads_or(!ok)) {
+            // a window never arrived: give this CTA's copies still in flight a
+            // bounded chance to land, then stop
+            const int b = (s + 1) & 1;
+            if (!ok) mbar_wait_parity(bar0 + 8 * b, ((pipe.phase >> b) & 1u) ^ 1u);
+            if (s + 2 < NS) mbar_wait_parity(bar0 + 8 * (b ^ 1), (pipe.phase >> (b ^ 1)) & 1u);
+            return false;
+        }
+        if (s + 3 < NS) issue(s + 3, (s + 1) & 1);
     }
 
+    // ---- store the tile (or this unit's partial of it)
+    float* out = a.n_split > 1 ? a.partial + (long long)split * a.partial_stride : a.image;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int ku = k % VU, kr = k / VU;
@@ -319,8 +370,8 @@ __device__ __forceinline__ bool das_tile(const DasArgs& a, int tile, unsigned ch
         const int iu = u0 + lane + 32 * ku, iv = v0 + row % a.bv, iw = w0 + row / a.bv;
         if (iu < a.n_u && iv < a.n_v && iw < a.n_w) {
             const long long o = (long long)iw * a.out_sw + (long long)iv * a.out_sv + (long long)iu * a.out_su;
-            a.image[o] = acc[k];
-            if (CPLX) a.image[a.image_plane + o] = acci[k];
+            out[o] = acc[k];
+            if (CPLX) out[a.image_plane + o] = acci[k];
         }
     }
     return true;

@@ -48,6 +48,9 @@ struct DasArgs {
     int H;                 // W / 2: centring of the per-window line intercepts
     int raw_samples;       // raw samples staged per window (multiple of 8)
     float reach_a, reach_b;// tile reach of the transmit / receive delays in samples (+ slack)
+    int n_split;           // channel split of every tile (units = tiles x n_split)
+    float* partial;        // [n_split][planes][voxels] partial images (n_split > 1)
+    long long partial_stride;  // floats between splits
     int dtype;             // rcbf_dtype of the decoded RF
     float scale;           // 1/N for RCBF_I32 input, else 1
     long long plane_stride;// elements between real and imaginary planes (complex)
@@ -68,6 +71,8 @@ struct DecodeArgs {
     void* out;
     const uint32_t* afrag;  // A = H^T fragments, permuted for the ldmatrix.trans B order
     const int8_t* hmat;     // H[k][i] row-major (plain variant)
+    const uint32_t* afrag16;// A = H^T fragments of the FP16 form (natural k order)
+    const int* hsum;        // h_i = sum_k H[k][i] (FP16 form correction)
     long long n_cols;       // n_ch * n_samples
     int n;                  // order
     int dtype;              // RCBF_I32 / RCBF_F32 / RCBF_F16
@@ -85,10 +90,15 @@ struct PlanHost {
     bool tiled_ok;          // geometry and sizes admit the tiled DAS
     uint32_t* d_afrag;      // device A fragments
     int8_t* d_hmat;         // device H (plain decode)
+    uint32_t* d_afrag16;    // device A fragments, FP16 form
+    int* d_hsum;            // device column sums of H
     int* d_status;          // device status word
     int n_sms;              // SMs of the plan's device
     int decode_blocks_per_sm;
     int das_blocks_per_sm[2];   // by window stride class (64, 128)
+    int n_split[2];         // channel split by window stride class
+    float* d_partial;       // DAS partial images (channel split), plan-owned
+    size_t partial_floats;
 };
 
 }  // namespace rcbf

@@ -109,6 +109,7 @@ def test_null_arguments_rejected(lib):
     assert lib.rcbf_das(None, None, None, ctypes.c_float(0), None, None) == rc.EINVAL
     assert lib.rcbf_das_backward(None, None, None, ctypes.c_float(0), None, None, None, None, None) == rc.EINVAL
     assert lib.rcbf_batch_run(None, None) == rc.EINVAL
+    assert lib.rcbf_plan_query(None, None) == rc.EINVAL
     lib.rcbf_destroy(None)
     lib.rcbf_batch_destroy(None)
 

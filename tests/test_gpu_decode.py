@@ -42,7 +42,10 @@ def _assert_bit_exact(got, D, n, dtype):
         np.testing.assert_array_equal(got, want)
 
 
-@pytest.mark.parametrize("variant", [rc.DECODE_MMA_I8, rc.DECODE_PLAIN])
+VARIANTS = [rc.DECODE_MMA_I8, rc.DECODE_MMA_F16, rc.DECODE_PLAIN]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("dtype", ["i32", "f32", "f16"])
 @pytest.mark.parametrize("n,n_ch,n_s", [(32, 32, 1024), (64, 5, 136), (128, 3, 1000), (256, 3, 520),
                                         (32, 1, 8), (128, 1, 24)])
@@ -54,31 +57,34 @@ def test_decode_random_full_int16_range(variant, dtype, n, n_ch, n_s):
     _assert_bit_exact(_run(g, rf, dtype, variant), oracle.decode(rf), n, dtype)
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("dtype", ["i32", "f32", "f16"])
-def test_decode_extreme_values(dtype):
+def test_decode_extreme_values(variant, dtype):
     # every acquisition at -32768 or +32767: the largest |D| = n * 32768
     n = 256
     rf = np.full((n, 2, 64), -32768, dtype=np.int16)
     rf[::2, 0, :] = 32767
     g = _geom(n, 2, 64)
-    _assert_bit_exact(_run(g, rf, dtype, rc.DECODE_MMA_I8), oracle.decode(rf), n, dtype)
+    _assert_bit_exact(_run(g, rf, dtype, variant), oracle.decode(rf), n, dtype)
 
 
+@pytest.mark.parametrize("variant", [rc.DECODE_MMA_I8, rc.DECODE_MMA_F16])
 @pytest.mark.parametrize("name", ["tiny", "bscan", "volume"])
 @pytest.mark.parametrize("dtype", ["f32", "f16"])
-def test_decode_workloads(name, dtype):
+def test_decode_workloads(variant, name, dtype):
     fr = frame(name)
     g = fr.geometry
-    _assert_bit_exact(_run(g, fr.rf, dtype, rc.DECODE_MMA_I8), oracle.decode(fr.rf), g.n_tx, dtype)
+    _assert_bit_exact(_run(g, fr.rf, dtype, variant), oracle.decode(fr.rf), g.n_tx, dtype)
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("n", [32, 64, 128, 256])
-def test_decode_round_trip(n):
+def test_decode_round_trip(variant, n):
     rng = np.random.default_rng(100 + n)
     lim = 32767 // n
     r = rng.integers(-lim, lim + 1, size=(n, 4, 256)).astype(np.int64)
     s = np.einsum("ki,ics->kcs", synth.sylvester_kron(n), r).astype(np.int16)
-    got = _run(_geom(n, 4, 256), s, "i32", rc.DECODE_MMA_I8)
+    got = _run(_geom(n, 4, 256), s, "i32", variant)
     np.testing.assert_array_equal(got, (n * r).astype(np.int32))
 
 
@@ -87,7 +93,7 @@ def test_decode_custom_matrix():
     rng = np.random.default_rng(7)
     H = (synth.sylvester_kron(n)[rng.permutation(n)] * rng.choice([-1, 1], n)[None, :]).astype(np.int8)
     rf = synth.random_int_rf(n, 3, 128, seed=8)
-    for variant in (rc.DECODE_MMA_I8, rc.DECODE_PLAIN):
+    for variant in VARIANTS:
         plan = rc.Plan(rc.make_params(_geom(n, 3, 128), decoded_dtype="i32", decode_variant=variant),
                        decode_matrix=H)
         got = plan.decode(torch.from_numpy(rf).cuda()).cpu().numpy()
