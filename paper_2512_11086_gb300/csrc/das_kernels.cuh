@@ -12,13 +12,7 @@ __global__ void __launch_bounds__(kDasThreads, 2)
 das_tiled_kernel(DasArgs a) {
     using C = DasCfg<VU, WS, CPLX>;
     extern __shared__ __align__(128) unsigned char smem[];
-    const uint32_t bar0 = smem_u32(smem + C::OFF_BAR);
-    if (threadIdx.x == 0) {
-        mbar_init(bar0, C::COPIES);
-        mbar_init(bar0 + 8, C::COPIES);
-        fence_mbar_init();
-    }
-    __syncthreads();
+    das_pipe_init<C::COPIES>(smem + C::OFF_BAR, reinterpret_cast<volatile int*>(smem + C::OFF_ABORT));
     DasPipe pipe{0u};
     if (!das_unit<VU, WS, CPLX, APOD>(a, blockIdx.x, smem, pipe) && threadIdx.x == 0)
         atomicOr(a.status, kStatusWaitExpired);

@@ -28,10 +28,13 @@
 // interval n); one 8-byte shared load; one FMA for the interpolated sample;
 // one add (or FMA with the apodization weight a_j(v) of Eq. (2)-(3)).
 //
-// Pipeline (one CTA barrier per stage): during stage s every warp first
-// rewrites the raw windows of stage s+1 (landed by TMA two stages earlier)
-// into the second line-piece buffer, then sums stage s from the first; after
-// the barrier the raw buffer just rewritten is refilled with stage s+3.
+// Pipeline (no CTA-wide barrier per stage): two raw-window buffers and two
+// line-piece buffers, each with a "full" and an "empty" mbarrier. In stage s a
+// thread (i) if it issues copies, waits until the raw buffer of stage s is
+// drained and refills it with stage s+2, (ii) rewrites its share of the raw
+// windows of stage s+1 once they have landed and the line-piece buffer is
+// free, (iii) sums stage s once every share of it is written. Warps drift
+// apart by up to a stage instead of meeting at a barrier each stage.
 #pragma once
 
 #include <type_traits>
@@ -68,8 +71,9 @@ struct DasCfg {
     static constexpr int OFF_RX = OFF_TX + kMaxOrder * 16;             // float4[kMaxChannels]
     static constexpr int OFF_ALPHA = OFF_RX + kMaxChannels * 16;       // float[2][CI][ROWS]
     static constexpr int OFF_WOFF = OFF_ALPHA + 2 * CI * ROWS * 4;     // int[2][NWIN]
-    static constexpr int OFF_BAR = OFF_WOFF + 2 * NWIN * 4;            // uint64[2]
-    static constexpr int SMEM = OFF_BAR + 16;
+    static constexpr int OFF_BAR = OFF_WOFF + 2 * NWIN * 4;            // uint64[8]: raw full/empty, pieces full/empty
+    static constexpr int OFF_ABORT = OFF_BAR + 64;                     // int: a bounded wait expired
+    static constexpr int SMEM = OFF_ABORT + 16;
     static_assert(CI * ROWS <= kDasThreads, "alpha table needs one thread per entry");
     static_assert(COPIES <= kDasThreads, "one issuing thread per copy");
     static_assert(OFF_RAW % 128 == 0 && OFF_TX % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
@@ -132,10 +136,34 @@ __device__ __forceinline__ void rewrite_windows(const unsigned char* rawb, const
     }
 }
 
-// Persistent state of a CTA running DAS units (mbarrier phases).
+// mbarrier slots (8 bytes each) of a DAS CTA.
+enum : int { kRawFull = 0, kRawEmpty = 2, kPieceFull = 4, kPieceEmpty = 6 };
+
+// Per-thread state of a CTA running DAS units: bit k is the parity of the
+// next phase this thread waits for on mbarrier slot k.
 struct DasPipe {
-    uint32_t phase;   // bit b: parity of the next phase of mbarrier b
+    uint32_t phase;
 };
+
+// Initialise the CTA's mbarriers (thread 0) and pre-complete the first phase
+// of every "empty" barrier so that the first fill of each buffer needs no
+// special case. Ends with a CTA barrier.
+template <int COPIES>
+__device__ __forceinline__ void das_pipe_init(unsigned char* bar_base, volatile int* abort) {
+    const uint32_t bar0 = smem_u32(bar_base);
+    if (threadIdx.x == 0) {
+        mbar_init(bar0 + 8 * (kRawFull + 0), COPIES);
+        mbar_init(bar0 + 8 * (kRawFull + 1), COPIES);
+        for (int k = kRawEmpty; k < 8; ++k) mbar_init(bar0 + 8 * k, kDasThreads);
+        *abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    mbar_arrive(bar0 + 8 * (kRawEmpty + 0));
+    mbar_arrive(bar0 + 8 * (kRawEmpty + 1));
+    mbar_arrive(bar0 + 8 * (kPieceEmpty + 0));
+    mbar_arrive(bar0 + 8 * (kPieceEmpty + 1));
+}
 
 // One work unit. Returns false when a bounded wait expired (the CTA must
 // stop; the caller records the status).
@@ -172,6 +200,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     const double zr = a.q0[2] + a.Gu[2] * cu + a.Gv[2] * cv + a.Gw[2] * cw;
     const double lat_tx_ref = a.tx_axis ? qy : qx, lat_rx_ref = a.rx_axis ? qy : qx;
     const int j_lo = jc0 * C::CJ, n_rx = js * C::CJ;
+    __syncthreads();   // the previous unit of this CTA no longer reads the tables
     for (int e = tid; e < a.n_tx + n_rx; e += kDasThreads) {
         if (e < a.n_tx) {
             const double L = lat_tx_ref - (a.tx_e0 + e * a.tx_pitch);
@@ -211,44 +240,55 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     };
     __syncthreads();   // reference tables ready
 
-    // ---- producer: one thread per bulk copy (window, plane) into raw buffer b
-    auto issue = [&](int s, int b) {
-        if (tid < C::COPIES) {
-            const int win = CPLX ? (tid >> 1) : tid;
-            const int plane = CPLX ? (tid & 1) : 0;
-            const int ii = win / C::CJ, jj = win % C::CJ;
-            const int i = (s % n_ic) * C::CI + ii, j = (jc0 + s / n_ic) * C::CJ + jj;
-            const int S0 = __float_as_int(s_tx[i].w) + __float_as_int(s_rx[j].w) + a.lo;
-            const int A = S0 & ~7;
-            if (plane == 0) s_woff[b * C::NWIN + win] = S0 - A;
-            const int lo_s = max(A, 0);
-            const int hi_s = min(A + a.raw_samples, a.n_s);
-            unsigned char* dst = raw + (b * C::NWIN + win) * C::RAW_WIN_BYTES + plane * C::RAWS * 4;
-            const int pre = (min(lo_s, A + a.raw_samples) - A) * es;       // bytes of zeros before
-            const int body = hi_s > lo_s ? (hi_s - lo_s) * es : 0;
-            const int total = a.raw_samples * es;
-            for (int o = 0; o < pre; o += 16) *reinterpret_cast<uint4*>(dst + o) = make_uint4(0, 0, 0, 0);
-            for (int o = pre + body; o < total; o += 16) *reinterpret_cast<uint4*>(dst + o) = make_uint4(0, 0, 0, 0);
-            fence_proxy_async_smem();
-            const uint32_t bar = bar0 + 8 * b;
-            mbar_arrive_expect_tx(bar, (uint32_t)body);
-            if (body > 0) {
-                const char* src = static_cast<const char*>(a.rf) +
-                    ((long long)plane * a.plane_stride + ((long long)i * a.n_ch + j) * a.n_s + lo_s) * es;
-                bulk_g2s(smem_u32(dst + pre), src, (uint32_t)body, bar);
-            }
-        }
+    volatile int* abort = reinterpret_cast<volatile int*>(smem + C::OFF_ABORT);
+    auto wait = [&](int slot) -> bool {
+        if (!mbar_wait_or_abort(bar0 + 8 * slot, (pipe.phase >> slot) & 1u, abort)) return false;
+        pipe.phase ^= 1u << slot;
+        return true;
     };
 
-    // ---- stage preparation: wait for its raw windows, rewrite them into line
-    // pieces (buffer pb) and tabulate its transmit terms (alpha buffer pb)
-    const float hp = 0.5f + (float)a.H;
-    auto prepare = [&](int s, int pb) -> bool {
+    // ---- producer: one thread per bulk copy (window, plane) of stage s into
+    // raw buffer s & 1, once every thread has rewritten that buffer's previous stage
+    auto issue = [&](int s) -> bool {
+        if (tid >= C::COPIES) return true;
         const int b = s & 1;
-        const bool ok = mbar_wait_parity(bar0 + 8 * b, (pipe.phase >> b) & 1u);
-        pipe.phase ^= 1u << b;
+        if (!wait(kRawEmpty + b)) return false;
+        const int win = CPLX ? (tid >> 1) : tid;
+        const int plane = CPLX ? (tid & 1) : 0;
+        const int ii = win / C::CJ, jj = win % C::CJ;
+        const int i = (s % n_ic) * C::CI + ii, j = (jc0 + s / n_ic) * C::CJ + jj;
+        const int S0 = __float_as_int(s_tx[i].w) + __float_as_int(s_rx[j].w) + a.lo;
+        const int A = S0 & ~7;
+        if (plane == 0) s_woff[b * C::NWIN + win] = S0 - A;
+        const int lo_s = max(A, 0);
+        const int hi_s = min(A + a.raw_samples, a.n_s);
+        unsigned char* dst = raw + (b * C::NWIN + win) * C::RAW_WIN_BYTES + plane * C::RAWS * 4;
+        const int pre = (min(lo_s, A + a.raw_samples) - A) * es;       // bytes of zeros before
+        const int body = hi_s > lo_s ? (hi_s - lo_s) * es : 0;
+        const int total = a.raw_samples * es;
+        for (int o = 0; o < pre; o += 16) *reinterpret_cast<uint4*>(dst + o) = make_uint4(0, 0, 0, 0);
+        for (int o = pre + body; o < total; o += 16) *reinterpret_cast<uint4*>(dst + o) = make_uint4(0, 0, 0, 0);
+        fence_proxy_async_smem();
+        const uint32_t bar = bar0 + 8 * (kRawFull + b);
+        mbar_arrive_expect_tx(bar, (uint32_t)body);
+        if (body > 0) {
+            const char* src = static_cast<const char*>(a.rf) +
+                ((long long)plane * a.plane_stride + ((long long)i * a.n_ch + j) * a.n_s + lo_s) * es;
+            bulk_g2s(smem_u32(dst + pre), src, (uint32_t)body, bar);
+        }
+        return true;
+    };
+
+    // ---- stage preparation: once its raw windows have landed and the
+    // line-piece buffer is free, rewrite this thread's share of the windows
+    // and of the transmit-term table, then release both buffers
+    const float hp = 0.5f + (float)a.H;
+    auto prepare = [&](int s) -> bool {
+        const int b = s & 1;
+        if (!wait(kRawFull + b)) return false;
+        if (!wait(kPieceEmpty + b)) return false;
         const unsigned char* rawb = raw + b * C::NWIN * C::RAW_WIN_BYTES;
-        unsigned char* pairs = smem + C::OFF_PAIRS + pb * C::PAIR_BUF;
+        unsigned char* pairs = smem + C::OFF_PAIRS + b * C::PAIR_BUF;
         const int* woff = s_woff + b * C::NWIN;
         if (a.dtype == RCBF_F16)
             rewrite_windows<__half, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
@@ -268,22 +308,12 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             const float d = sqrtf(Lv * Lv + Zv * Zv);
             const float num = dL * (2.0f * tx.x + dL) + dz * (2.0f * Zf + dz);
             const float al = tx.z + __fdividef(num, d + tx.y) * fsc;
-            s_alpha[pb * C::CI * C::ROWS + ii * C::ROWS + row] = fminf(fmaxf(al, tx.z - a.reach_a), tx.z + a.reach_a);
+            s_alpha[b * C::CI * C::ROWS + ii * C::ROWS + row] = fminf(fmaxf(al, tx.z - a.reach_a), tx.z + a.reach_a);
         }
-        return ok;
+        mbar_arrive(bar0 + 8 * (kRawEmpty + b));
+        mbar_arrive(bar0 + 8 * (kPieceFull + b));
+        return true;
     };
-
-    // ---- prologue
-    issue(0, 0);
-    if (NS > 1) issue(1, 1);
-    __syncthreads();   // window offsets and zero fills of the first two stages visible
-    bool ok = prepare(0, 0);
-    if (__syncthreads_or(!ok)) {
-        if (!ok) mbar_wait_parity(bar0, (pipe.phase & 1u) ^ 1u);
-        if (NS > 1) mbar_wait_parity(bar0 + 8, (pipe.phase >> 1) & 1u);
-        return false;
-    }
-    if (NS > 2) issue(2, 0);
 
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     float acci[4] = {0.f, 0.f, 0.f, 0.f};
@@ -292,9 +322,16 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     const float magic = 8388608.0f + (float)a.H;     // 2^23 + H
     constexpr int SHIFT = CPLX ? 4 : 3;
 
-    for (int s = 0; s < NS; ++s) {
+    // ---- prologue: stages 0 and 1 in flight, stage 0 rewritten
+    bool ok = issue(0);
+    if (ok && NS > 1) ok = issue(1);
+    if (ok) ok = prepare(0);
+    int issued = NS > 1 ? 1 : 0;      // last stage this thread's copies were requested for
+    int landed = 0;                   // last stage whose raw windows this thread waited for
+
+    for (int s = 0; ok && s < NS; ++s) {
         const int ic = s % n_ic, jc = jc0 + s / n_ic;
-        const int pb = s & 1;
+        const int b = s & 1;
         if (ic == 0) {
             // per-voxel receive terms (and apodization) for this channel chunk
 #pragma unroll
@@ -318,24 +355,27 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
                 }
             }
         }
-        if (s + 1 < NS) ok = prepare(s + 1, pb ^ 1);
+        if (s + 2 < NS) { if (!(ok = issue(s + 2))) break; issued = s + 2; }
+        if (s + 1 < NS) { if (!(ok = prepare(s + 1))) break; landed = s + 1; }
+        if (!(ok = wait(kPieceFull + b))) break;
 
-        // ---- the sum: 4 voxels x CI transmits x CJ channels from buffer pb
-        const uint32_t pbase = pairs_u32 + pb * C::PAIR_BUF - (0x4B000000u << SHIFT);
-        const float* alb = s_alpha + pb * C::CI * C::ROWS + warp * C::VR;
-        static_for<0, C::CI>([&](auto iic) {
-            constexpr int ii = decltype(iic)::value;
+        // ---- the sum: 4 voxels x CI transmits x CJ channels from buffer b
+        const uint32_t pbase = pairs_u32 + b * C::PAIR_BUF - (0x4B000000u << SHIFT);
+        const float* alb = s_alpha + b * C::CI * C::ROWS + warp * C::VR;
+#pragma unroll 1
+        for (int ii = 0; ii < C::CI; ++ii) {
             float al[C::VR];
 #pragma unroll
             for (int kr = 0; kr < C::VR; ++kr) al[kr] = alb[ii * C::ROWS + kr];
+            const uint32_t pb_ii = pbase + ii * (C::CJ * WS * C::PAIR_BYTES);
             static_for<0, C::CJ>([&](auto jjc) {
                 constexpr int jj = decltype(jjc)::value;
-                constexpr int OFF = (ii * C::CJ + jj) * WS * C::PAIR_BYTES;
+                constexpr int OFF = jj * WS * C::PAIR_BYTES;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const float u = al[k / VU] + beta[k][jj];
                     const float t = u + magic;
-                    const uint32_t addr = (__float_as_uint(t) << SHIFT) + pbase;
+                    const uint32_t addr = (__float_as_uint(t) << SHIFT) + pb_ii;
                     if (CPLX) {
                         const float4 p = lds_f4<OFF>(addr);
                         const float vr = fmaf(u, p.y, p.x), vi = fmaf(u, p.w, p.z);
@@ -349,16 +389,18 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
                     }
                 }
             });
-        });
-        if (__syncthreads_or(!ok)) {
-            // a window never arrived: give this CTA's copies still in flight a
-            // bounded chance to land, then stop
-            const int b = (s + 1) & 1;
-            if (!ok) mbar_wait_parity(bar0 + 8 * b, ((pipe.phase >> b) & 1u) ^ 1u);
-            if (s + 2 < NS) mbar_wait_parity(bar0 + 8 * (b ^ 1), (pipe.phase >> (b ^ 1)) & 1u);
-            return false;
         }
-        if (s + 3 < NS) issue(s + 3, (s + 1) & 1);
+        mbar_arrive(bar0 + 8 * (kPieceEmpty + b));
+    }
+    if (!ok) {
+        // a bounded wait expired somewhere in the CTA: give the copies this
+        // thread still expects a bounded chance to land, then stop
+        for (int k = landed + 1; k <= issued; ++k) {
+            const int slot = kRawFull + (k & 1);
+            mbar_wait_parity(bar0 + 8 * slot, (pipe.phase >> slot) & 1u);
+            pipe.phase ^= 1u << slot;
+        }
+        return false;
     }
 
     // ---- store the tile (or this unit's partial of it)

@@ -20,7 +20,7 @@ constexpr int kCI = 8;                // transmits per staged chunk
 constexpr int kCJ = 8;                // channels per staged chunk
 constexpr int kDecodeThreads = 256;
 constexpr int kDecodeCols = 128;      // columns (channel x sample) per decode tile
-constexpr uint32_t kWaitLimit = 1u << 26;   // bounded mbarrier polls before giving up
+constexpr long long kWaitCycles = 2000000000LL;   // bounded mbarrier waits: about one second of SM clock
 
 // Status bits written by kernels into a plan's device status word.
 constexpr int kStatusWaitExpired = 1;
@@ -138,9 +138,16 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
                  :: "r"(bar), "r"(bytes) : "memory");
 }
 
-// Bounded wait on an mbarrier phase; returns false if the poll budget ran out.
-__device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity) {
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" :: "r"(bar) : "memory");
+}
+
+// Bounded wait on an mbarrier phase that also gives up when another thread
+// of the CTA has raised the abort flag; raises it itself when its own time
+// budget (about a second) runs out. Returns false on abort.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort) {
+    const long long t0 = clock64();
+    for (uint32_t it = 0;; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -148,8 +155,19 @@ __device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity) 
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done) : "r"(bar), "r"(parity) : "memory");
         if (done) return true;
+        if ((it & 15u) == 15u) {
+            if (*abort) return false;
+            if (clock64() - t0 > kWaitCycles) break;
+        }
     }
+    *abort = 1;
     return false;
+}
+
+// Bounded wait on an mbarrier phase; returns false after about a second.
+__device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity) {
+    volatile int never = 0;
+    return mbar_wait_or_abort(bar, parity, &never);
 }
 
 // 1-D bulk copy global -> shared (TMA engine), completion on an mbarrier.
