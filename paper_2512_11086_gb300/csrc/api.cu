@@ -261,9 +261,9 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
         best_bw = (int)p.tile[2];
     } else {
         // window length (in samples) of a shape at the plan's speed of sound;
-        // prefer shapes whose windows fit the 64-interval class, then more
-        // voxels per thread along u (fewer transmit-term loads per sum),
-        // then the shorter window
+        // prefer the smallest window class (48, 64, 128 intervals: larger
+        // stages), then more voxels per thread along u (fewer transmit-term
+        // loads per sum), then the shorter window
         const double spm = p.fs / p.c;
         double best_key = 1e300;
         const int bus[3] = {128, 64, 32};
@@ -274,7 +274,8 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
                 const int bw = rows / bv;
                 if (bv > 1 && a.n_v == 1) continue;
                 const double W = std::floor(4.0 + 2.0 * radius_sum(bu, bv, bw) * spm + 0.01) + 1.0;
-                const double key = (W <= 64 ? 0.0 : 1e6) + (W <= 64 ? (128 - bu) * 100.0 : 0.0) + W;
+                const double cls = W <= 48 ? 0.0 : W <= 64 ? 1.0 : W <= 128 ? 2.0 : 3.0;
+                const double key = cls * 1e6 + (cls < 2 ? (128 - bu) * 100.0 : 0.0) + W;
                 if (key < best_key) { best_key = key; best_bu = bu; best_bv = bv; best_bw = bw; }
             }
         }
@@ -330,7 +331,7 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
     }
     if ((rc = configure_das(h)) != RCBF_OK) { std::string m = g_last_error; rcbf_destroy(plan); return set_error(rc, m); }
     {
-        const int sp = std::max(h.n_split[0], h.n_split[1]);
+        const int sp = std::max(h.n_split[0], std::max(h.n_split[1], h.n_split[2]));
         if (sp > 1) {
             h.partial_floats = (size_t)sp * a.image_plane * (p.decoded_dtype == RCBF_CF32 ? 2 : 1);
             if (cudaMalloc(&h.d_partial, h.partial_floats * sizeof(float)) != cudaSuccess)
@@ -354,7 +355,7 @@ int rcbf_plan_query(rcbf_plan_t plan, rcbf_plan_info* info) {
     const bool tiled = h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok && fits;
     info->tiled = tiled ? 1u : 0u;
     info->window = (uint32_t)a.W;
-    const int sp = tiled ? std::max(1, h.n_split[a.W <= 64 ? 0 : 1]) : 1;
+    const int sp = tiled ? std::max(1, h.n_split[das_class_index(a.W)]) : 1;
     info->n_split = (uint32_t)sp;
     info->das_launches = sp > 1 ? 2u : 1u;
     info->decode_launches = h.p.hadamard_order ? 1u : 0u;

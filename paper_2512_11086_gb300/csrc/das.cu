@@ -131,14 +131,17 @@ int das_prepare(const PlanHost& h, double c, DasArgs* a, std::string* why) {
     return RCBF_OK;
 }
 
-static int stride_class(int W) { return W <= 64 ? 64 : 128; }
+static int stride_class(int W) { return W <= 48 ? 48 : W <= 64 ? 64 : 128; }
+static int class_index(int ws) { return ws == 48 ? 0 : ws == 64 ? 1 : 2; }
+
+int das_class_index(int W) { return class_index(stride_class(W)); }
 
 int launch_das(const PlanHost& h, const DasArgs& a_in, cudaStream_t s) {
     DasArgs a = a_in;
     const int ws = stride_class(a.W);
     const bool cplx = a.dtype == RCBF_CF32;
     const bool apod = a.apod != nullptr || a.f_number > 0.f;
-    a.n_split = std::max(1, h.n_split[ws == 64 ? 0 : 1]);
+    a.n_split = std::max(1, h.n_split[class_index(ws)]);
     a.partial = h.d_partial;
     a.partial_stride = a.image_plane * (cplx ? 2 : 1);
     int rc;
@@ -158,8 +161,8 @@ int launch_das(const PlanHost& h, const DasArgs& a_in, cudaStream_t s) {
 int configure_das(PlanHost& h) {
     if (h.p.das_variant == RCBF_DAS_PLAIN || !h.tiled_ok) return RCBF_OK;
     const bool cplx = h.p.decoded_dtype == RCBF_CF32;
-    for (int c = 0; c < 2; ++c) {
-        const int ws = c == 0 ? 64 : 128;
+    for (int c = 0; c < 3; ++c) {
+        const int ws = c == 0 ? 48 : c == 1 ? 64 : 128;
         int rc, n = 0;
         switch (h.vu) {
             case 1: rc = configure_das_vu<1>(ws, cplx, &n); break;

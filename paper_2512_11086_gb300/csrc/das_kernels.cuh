@@ -37,10 +37,9 @@ int configure_das_vu(int ws, bool cplx, int* per_sm) {
 #define RCBF_CFG(WSV, CP)                                                        \
     if ((rc = das_cfg_one<VU, WSV, CP, false>(per_sm)) != RCBF_OK) return rc;   \
     if ((rc = das_cfg_one<VU, WSV, CP, true>(nullptr)) != RCBF_OK) return rc;
-    if (ws == 64 && !cplx) { RCBF_CFG(64, false) }
-    else if (ws == 64 && cplx) { RCBF_CFG(64, true) }
-    else if (ws == 128 && !cplx) { RCBF_CFG(128, false) }
-    else { RCBF_CFG(128, true) }
+    if (ws == 48) { if (cplx) { RCBF_CFG(48, true) } else { RCBF_CFG(48, false) } }
+    else if (ws == 64) { if (cplx) { RCBF_CFG(64, true) } else { RCBF_CFG(64, false) } }
+    else { if (cplx) { RCBF_CFG(128, true) } else { RCBF_CFG(128, false) } }
 #undef RCBF_CFG
     return RCBF_OK;
 }
@@ -51,13 +50,13 @@ int launch_das_vu(const DasArgs& a, int ws, bool cplx, bool apod, cudaStream_t s
 #define RCBF_LAUNCH(WSV, CP, AP)                                                                   \
     das_tiled_kernel<VU, WSV, CP, AP><<<grid, kDasThreads, DasCfg<VU, WSV, CP>::SMEM, s>>>(a);    \
     return check_launch("das_tiled_kernel");
-    if (ws == 64) {
-        if (cplx) { if (apod) { RCBF_LAUNCH(64, true, true) } else { RCBF_LAUNCH(64, true, false) } }
-        else { if (apod) { RCBF_LAUNCH(64, false, true) } else { RCBF_LAUNCH(64, false, false) } }
-    } else {
-        if (cplx) { if (apod) { RCBF_LAUNCH(128, true, true) } else { RCBF_LAUNCH(128, true, false) } }
-        else { if (apod) { RCBF_LAUNCH(128, false, true) } else { RCBF_LAUNCH(128, false, false) } }
-    }
+#define RCBF_WS(WSV)                                                                               \
+    if (cplx) { if (apod) { RCBF_LAUNCH(WSV, true, true) } else { RCBF_LAUNCH(WSV, true, false) } } \
+    else { if (apod) { RCBF_LAUNCH(WSV, false, true) } else { RCBF_LAUNCH(WSV, false, false) } }
+    if (ws == 48) { RCBF_WS(48) }
+    else if (ws == 64) { RCBF_WS(64) }
+    else { RCBF_WS(128) }
+#undef RCBF_WS
 #undef RCBF_LAUNCH
 }
 

@@ -28,13 +28,13 @@
 // interval n); one 8-byte shared load; one FMA for the interpolated sample;
 // one add (or FMA with the apodization weight a_j(v) of Eq. (2)-(3)).
 //
-// Pipeline (no CTA-wide barrier per stage): two raw-window buffers and two
+// Pipeline (no CTA-wide barrier per stage): two raw-window buffers and three
 // line-piece buffers, each with a "full" and an "empty" mbarrier. In stage s a
 // thread (i) if it issues copies, waits until the raw buffer of stage s is
 // drained and refills it with stage s+2, (ii) rewrites its share of the raw
-// windows of stage s+1 once they have landed and the line-piece buffer is
-// free, (iii) sums stage s once every share of it is written. Warps drift
-// apart by up to a stage instead of meeting at a barrier each stage.
+// windows of stage s+1 once they have landed and the line-piece buffer of
+// stage s-2 is free, (iii) sums stage s once every share of it is written.
+// Warps drift apart by up to a stage instead of meeting at a barrier.
 #pragma once
 
 #include <type_traits>
@@ -56,27 +56,31 @@ struct DasCfg {
     static constexpr int VR = 4 / VU;              // tile rows per thread
     static constexpr int ROWS = 8 * VR;            // tile rows (one warp covers VR rows)
     static constexpr int BU = 32 * VU;             // tile extent along u
-    // transmits per stage: every variant stages 32 KB of line pieces
-    static constexpr int CI = (CPLX ? 4 : 8) / (WS > 64 ? 2 : 1);
+    // transmits per stage, so that three line-piece buffers and two raw
+    // buffers fit two CTAs per SM for every window class
+    static constexpr int CI = (WS <= 48 ? 8 : WS <= 64 ? 4 : 2) / (CPLX ? 2 : 1);
     static constexpr int CJ = 8;                   // channels per stage
     static constexpr int NWIN = CI * CJ;           // windows per stage
     static constexpr int COPIES = NWIN * (CPLX ? 2 : 1);   // bulk copies per stage (windows x planes)
+    static constexpr int NB = 3;                   // line-piece buffers
     static constexpr int PAIR_BYTES = CPLX ? 16 : 8;
     static constexpr int RAWS = WS + 8;            // raw samples per window plane (max)
     static constexpr int RAW_WIN_BYTES = RAWS * 4 * (CPLX ? 2 : 1);
     static constexpr int PAIR_BUF = NWIN * WS * PAIR_BYTES;
-    static constexpr int OFF_PAIRS = 0;                                // 2 line-piece buffers
-    static constexpr int OFF_RAW = OFF_PAIRS + 2 * PAIR_BUF;           // 2 raw window buffers
+    static constexpr int ALPHA_N = CI * ROWS;      // transmit terms per stage
+    static constexpr int OFF_PAIRS = 0;                                // NB line-piece buffers
+    static constexpr int OFF_RAW = OFF_PAIRS + NB * PAIR_BUF;          // 2 raw window buffers
     static constexpr int OFF_TX = OFF_RAW + 2 * NWIN * RAW_WIN_BYTES;  // float4[kMaxOrder]
     static constexpr int OFF_RX = OFF_TX + kMaxOrder * 16;             // float4[kMaxChannels]
-    static constexpr int OFF_ALPHA = OFF_RX + kMaxChannels * 16;       // float[2][CI][ROWS]
-    static constexpr int OFF_WOFF = OFF_ALPHA + 2 * CI * ROWS * 4;     // int[2][NWIN]
-    static constexpr int OFF_BAR = OFF_WOFF + 2 * NWIN * 4;            // uint64[8]: raw full/empty, pieces full/empty
-    static constexpr int OFF_ABORT = OFF_BAR + 64;                     // int: a bounded wait expired
+    static constexpr int OFF_ALPHA = OFF_RX + kMaxChannels * 16;       // float[NB][CI][ROWS]
+    static constexpr int OFF_WOFF = OFF_ALPHA + NB * ALPHA_N * 4;      // int[2][NWIN]
+    static constexpr int OFF_BAR = OFF_WOFF + 2 * NWIN * 4;            // uint64[10]
+    static constexpr int OFF_ABORT = OFF_BAR + 80;                     // int: a bounded wait expired
     static constexpr int SMEM = OFF_ABORT + 16;
-    static_assert(CI * ROWS <= kDasThreads, "alpha table needs one thread per entry");
-    static_assert(COPIES <= kDasThreads, "one issuing thread per copy");
+    static_assert(ALPHA_N <= kDasThreads && kDasThreads % ALPHA_N == 0, "alpha table spread over the CTA");
+    static_assert(COPIES <= kDasThreads && kDasThreads % COPIES == 0, "one issuing thread per copy");
     static_assert(OFF_RAW % 128 == 0 && OFF_TX % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+    static_assert(2 * SMEM + 2048 <= 232448, "two CTAs per SM");
 };
 
 template <int OFF>
@@ -136,8 +140,9 @@ __device__ __forceinline__ void rewrite_windows(const unsigned char* rawb, const
     }
 }
 
-// mbarrier slots (8 bytes each) of a DAS CTA.
-enum : int { kRawFull = 0, kRawEmpty = 2, kPieceFull = 4, kPieceEmpty = 6 };
+// mbarrier slots (8 bytes each) of a DAS CTA: raw-window buffers (2) and
+// line-piece buffers (3), each with a "full" and an "empty" barrier.
+enum : int { kRawFull = 0, kRawEmpty = 2, kPieceFull = 4, kPieceEmpty = 7, kNumBars = 10 };
 
 // Per-thread state of a CTA running DAS units: bit k is the parity of the
 // next phase this thread waits for on mbarrier slot k.
@@ -154,15 +159,13 @@ __device__ __forceinline__ void das_pipe_init(unsigned char* bar_base, volatile 
     if (threadIdx.x == 0) {
         mbar_init(bar0 + 8 * (kRawFull + 0), COPIES);
         mbar_init(bar0 + 8 * (kRawFull + 1), COPIES);
-        for (int k = kRawEmpty; k < 8; ++k) mbar_init(bar0 + 8 * k, kDasThreads);
+        for (int k = kRawEmpty; k < kNumBars; ++k) mbar_init(bar0 + 8 * k, kDasThreads);
         *abort = 0;
         fence_mbar_init();
     }
     __syncthreads();
-    mbar_arrive(bar0 + 8 * (kRawEmpty + 0));
-    mbar_arrive(bar0 + 8 * (kRawEmpty + 1));
-    mbar_arrive(bar0 + 8 * (kPieceEmpty + 0));
-    mbar_arrive(bar0 + 8 * (kPieceEmpty + 1));
+    for (int k = 0; k < 2; ++k) mbar_arrive(bar0 + 8 * (kRawEmpty + k));
+    for (int k = 0; k < 3; ++k) mbar_arrive(bar0 + 8 * (kPieceEmpty + k));
 }
 
 // One work unit. Returns false when a bounded wait expired (the CTA must
@@ -249,12 +252,14 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
 
     // ---- producer: one thread per bulk copy (window, plane) of stage s into
     // raw buffer s & 1, once every thread has rewritten that buffer's previous stage
+    constexpr int ISTRIDE = kDasThreads / C::COPIES;
     auto issue = [&](int s) -> bool {
-        if (tid >= C::COPIES) return true;
+        if (tid % ISTRIDE) return true;
+        const int copy = tid / ISTRIDE;
         const int b = s & 1;
         if (!wait(kRawEmpty + b)) return false;
-        const int win = CPLX ? (tid >> 1) : tid;
-        const int plane = CPLX ? (tid & 1) : 0;
+        const int win = CPLX ? (copy >> 1) : copy;
+        const int plane = CPLX ? (copy & 1) : 0;
         const int ii = win / C::CJ, jj = win % C::CJ;
         const int i = (s % n_ic) * C::CI + ii, j = (jc0 + s / n_ic) * C::CJ + jj;
         const int S0 = __float_as_int(s_tx[i].w) + __float_as_int(s_rx[j].w) + a.lo;
@@ -283,12 +288,13 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     // line-piece buffer is free, rewrite this thread's share of the windows
     // and of the transmit-term table, then release both buffers
     const float hp = 0.5f + (float)a.H;
+    constexpr int ASTRIDE = kDasThreads / C::ALPHA_N;
     auto prepare = [&](int s) -> bool {
-        const int b = s & 1;
+        const int b = s & 1, pb = s % C::NB;
         if (!wait(kRawFull + b)) return false;
-        if (!wait(kPieceEmpty + b)) return false;
+        if (!wait(kPieceEmpty + pb)) return false;
         const unsigned char* rawb = raw + b * C::NWIN * C::RAW_WIN_BYTES;
-        unsigned char* pairs = smem + C::OFF_PAIRS + b * C::PAIR_BUF;
+        unsigned char* pairs = smem + C::OFF_PAIRS + pb * C::PAIR_BUF;
         const int* woff = s_woff + b * C::NWIN;
         if (a.dtype == RCBF_F16)
             rewrite_windows<__half, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
@@ -296,9 +302,10 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             rewrite_windows<int, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
         else
             rewrite_windows<float, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
-        if (tid < C::CI * C::ROWS) {
+        if (tid % ASTRIDE == 0) {
             // transmit terms of this stage for every tile row (alpha depends on the row only)
-            const int ii = tid / C::ROWS, row = tid % C::ROWS;
+            const int e = tid / ASTRIDE;
+            const int ii = e / C::ROWS, row = e % C::ROWS;
             const float dv = (float)(row % a.bv) - 0.5f * (a.bv - 1);
             const float dw = (float)(row / a.bv) - 0.5f * (a.bw - 1);
             const float dL = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]) * dv + (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]) * dw;
@@ -308,10 +315,10 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             const float d = sqrtf(Lv * Lv + Zv * Zv);
             const float num = dL * (2.0f * tx.x + dL) + dz * (2.0f * Zf + dz);
             const float al = tx.z + __fdividef(num, d + tx.y) * fsc;
-            s_alpha[b * C::CI * C::ROWS + ii * C::ROWS + row] = fminf(fmaxf(al, tx.z - a.reach_a), tx.z + a.reach_a);
+            s_alpha[pb * C::ALPHA_N + ii * C::ROWS + row] = fminf(fmaxf(al, tx.z - a.reach_a), tx.z + a.reach_a);
         }
         mbar_arrive(bar0 + 8 * (kRawEmpty + b));
-        mbar_arrive(bar0 + 8 * (kPieceFull + b));
+        mbar_arrive(bar0 + 8 * (kPieceFull + pb));
         return true;
     };
 
@@ -331,7 +338,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
 
     for (int s = 0; ok && s < NS; ++s) {
         const int ic = s % n_ic, jc = jc0 + s / n_ic;
-        const int b = s & 1;
+        const int pb = s % C::NB;
         if (ic == 0) {
             // per-voxel receive terms (and apodization) for this channel chunk
 #pragma unroll
@@ -357,11 +364,11 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
         }
         if (s + 2 < NS) { if (!(ok = issue(s + 2))) break; issued = s + 2; }
         if (s + 1 < NS) { if (!(ok = prepare(s + 1))) break; landed = s + 1; }
-        if (!(ok = wait(kPieceFull + b))) break;
+        if (!(ok = wait(kPieceFull + pb))) break;
 
-        // ---- the sum: 4 voxels x CI transmits x CJ channels from buffer b
-        const uint32_t pbase = pairs_u32 + b * C::PAIR_BUF - (0x4B000000u << SHIFT);
-        const float* alb = s_alpha + b * C::CI * C::ROWS + warp * C::VR;
+        // ---- the sum: 4 voxels x CI transmits x CJ channels from buffer pb
+        const uint32_t pbase = pairs_u32 + pb * C::PAIR_BUF - (0x4B000000u << SHIFT);
+        const float* alb = s_alpha + pb * C::ALPHA_N + warp * C::VR;
 #pragma unroll 1
         for (int ii = 0; ii < C::CI; ++ii) {
             float al[C::VR];
@@ -390,7 +397,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
                 }
             });
         }
-        mbar_arrive(bar0 + 8 * (kPieceEmpty + b));
+        mbar_arrive(bar0 + 8 * (kPieceEmpty + pb));
     }
     if (!ok) {
         // a bounded wait expired somewhere in the CTA: give the copies this

@@ -95,8 +95,8 @@ struct PlanHost {
     int* d_status;          // device status word
     int n_sms;              // SMs of the plan's device
     int decode_blocks_per_sm;
-    int das_blocks_per_sm[2];   // by window stride class (64, 128)
-    int n_split[2];         // channel split by window stride class
+    int das_blocks_per_sm[3];   // by window stride class (48, 64, 128)
+    int n_split[3];         // channel split by window stride class
     float* d_partial;       // DAS partial images (channel split), plan-owned
     size_t partial_floats;
 };
@@ -122,6 +122,7 @@ int launch_das(const PlanHost& h, const DasArgs& a, cudaStream_t s);
 int launch_das_plain(const PlanHost& h, const DasArgs& a, cudaStream_t s);
 int launch_das_backward(const PlanHost& h, const DasArgs& a, cudaStream_t s);
 int configure_decode(PlanHost& h);
+int das_class_index(int W);
 int configure_das(PlanHost& h);
 
 // ------------------------------------------------------------ PTX helpers
