@@ -77,8 +77,8 @@ struct DasCfg {
     static constexpr int OFF_BAR = OFF_WOFF + 2 * NWIN * 4;            // uint64[10]
     static constexpr int OFF_ABORT = OFF_BAR + 80;                     // int: a bounded wait expired
     static constexpr int SMEM = OFF_ABORT + 16;
-    static_assert(ALPHA_N <= kDasThreads && kDasThreads % ALPHA_N == 0, "alpha table spread over the CTA");
-    static_assert(COPIES <= kDasThreads && kDasThreads % COPIES == 0, "one issuing thread per copy");
+    static_assert(ALPHA_N <= kDasThreads, "one thread per transmit term");
+    static_assert(COPIES <= kDasThreads, "one issuing thread per copy");
     static_assert(OFF_RAW % 128 == 0 && OFF_TX % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
     static_assert(2 * SMEM + 2048 <= 232448, "two CTAs per SM");
 };
@@ -95,6 +95,27 @@ __device__ __forceinline__ float4 lds_f4(uint32_t addr) {
     asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4+%5];"
                  : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr), "n"(OFF));
     return v;
+}
+
+// Packed FP32 pairs (sm_100+ f32x2 arithmetic): two voxels per instruction.
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x pk(float lo, float hi) {
+    f2x r;
+    asm("mov.b64 %0, {%1,%2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(f2x v, float& lo, float& hi) {
+    asm("mov.b64 {%0,%1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+    f2x r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+    f2x r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
 }
 
 // Eq. (3) window at u = F# |lat| / |z|, support test F# |lat| < 0.5 |z|.
@@ -252,10 +273,9 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
 
     // ---- producer: one thread per bulk copy (window, plane) of stage s into
     // raw buffer s & 1, once every thread has rewritten that buffer's previous stage
-    constexpr int ISTRIDE = kDasThreads / C::COPIES;
     auto issue = [&](int s) -> bool {
-        if (tid % ISTRIDE) return true;
-        const int copy = tid / ISTRIDE;
+        if (tid >= C::COPIES) return true;
+        const int copy = tid;
         const int b = s & 1;
         if (!wait(kRawEmpty + b)) return false;
         const int win = CPLX ? (copy >> 1) : copy;
@@ -288,7 +308,6 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     // line-piece buffer is free, rewrite this thread's share of the windows
     // and of the transmit-term table, then release both buffers
     const float hp = 0.5f + (float)a.H;
-    constexpr int ASTRIDE = kDasThreads / C::ALPHA_N;
     auto prepare = [&](int s) -> bool {
         const int b = s & 1, pb = s % C::NB;
         if (!wait(kRawFull + b)) return false;
@@ -302,10 +321,9 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             rewrite_windows<int, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
         else
             rewrite_windows<float, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
-        if (tid % ASTRIDE == 0) {
+        if (tid < C::ALPHA_N) {
             // transmit terms of this stage for every tile row (alpha depends on the row only)
-            const int e = tid / ASTRIDE;
-            const int ii = e / C::ROWS, row = e % C::ROWS;
+            const int ii = tid / C::ROWS, row = tid % C::ROWS;
             const float dv = (float)(row % a.bv) - 0.5f * (a.bv - 1);
             const float dw = (float)(row / a.bv) - 0.5f * (a.bw - 1);
             const float dL = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]) * dv + (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]) * dw;
@@ -322,11 +340,14 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
         return true;
     };
 
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    // voxel pairs (k, k+1) are packed in f32x2 registers: receive terms,
+    // weights and accumulators
+    f2x acc2[2] = {0ull, 0ull};
     float acci[4] = {0.f, 0.f, 0.f, 0.f};
-    float beta[4][C::CJ];
-    float apw[4][C::CJ];
+    f2x beta2[2][C::CJ];
+    f2x apw2[2][C::CJ];
     const float magic = 8388608.0f + (float)a.H;     // 2^23 + H
+    const f2x magic2 = pk(magic, magic);
     constexpr int SHIFT = CPLX ? 4 : 3;
 
     // ---- prologue: stages 0 and 1 in flight, stage 0 rewritten
@@ -342,23 +363,27 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
         if (ic == 0) {
             // per-voxel receive terms (and apodization) for this channel chunk
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float dlr, dz;
-                voxel_offsets(k, dlr, dz);
-                const float Zv = Zf + dz;
+            for (int kp = 0; kp < 2; ++kp) {
+                float dlr[2], dz[2];
+                voxel_offsets(2 * kp, dlr[0], dz[0]);
+                voxel_offsets(2 * kp + 1, dlr[1], dz[1]);
 #pragma unroll
                 for (int jj = 0; jj < C::CJ; ++jj) {
                     const int j = jc * C::CJ + jj;
                     const float4 rx = s_rx[j];
-                    const float Lv = rx.x + dlr;
-                    const float d = sqrtf(Lv * Lv + Zv * Zv);
-                    const float num = dlr * (2.0f * rx.x + dlr) + dz * (2.0f * Zf + dz);
-                    const float bt = rx.z + __fdividef(num, d + rx.y) * fsc;
-                    beta[k][jj] = fminf(fmaxf(bt, rx.z - a.reach_b), rx.z + a.reach_b);
-                    if (APOD) {
-                        const float wj = a.apod ? __ldg(a.apod + j) : 1.0f;
-                        apw[k][jj] = a.f_number > 0.f ? wj * hann_weight(a.f_number, Lv, Zv) : wj;
+                    const float wj = APOD && a.apod ? __ldg(a.apod + j) : 1.0f;
+                    float bt[2], aw[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const float Lv = rx.x + dlr[h], Zv = Zf + dz[h];
+                        const float d = sqrtf(Lv * Lv + Zv * Zv);
+                        const float num = dlr[h] * (2.0f * rx.x + dlr[h]) + dz[h] * (2.0f * Zf + dz[h]);
+                        const float b0 = rx.z + __fdividef(num, d + rx.y) * fsc;
+                        bt[h] = fminf(fmaxf(b0, rx.z - a.reach_b), rx.z + a.reach_b);
+                        aw[h] = a.f_number > 0.f ? wj * hann_weight(a.f_number, Lv, Zv) : wj;
                     }
+                    beta2[kp][jj] = pk(bt[0], bt[1]);
+                    if (APOD) apw2[kp][jj] = pk(aw[0], aw[1]);
                 }
             }
         }
@@ -374,25 +399,42 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             float al[C::VR];
 #pragma unroll
             for (int kr = 0; kr < C::VR; ++kr) al[kr] = alb[ii * C::ROWS + kr];
+            const f2x al2[2] = {pk(al[0 / VU], al[1 / VU]), pk(al[2 / VU], al[3 / VU])};
             const uint32_t pb_ii = pbase + ii * (C::CJ * WS * C::PAIR_BYTES);
             static_for<0, C::CJ>([&](auto jjc) {
                 constexpr int jj = decltype(jjc)::value;
                 constexpr int OFF = jj * WS * C::PAIR_BYTES;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float u = al[k / VU] + beta[k][jj];
-                    const float t = u + magic;
-                    const uint32_t addr = (__float_as_uint(t) << SHIFT) + pb_ii;
+                for (int kp = 0; kp < 2; ++kp) {
+                    const f2x u2 = add2(al2[kp], beta2[kp][jj]);
+                    const f2x t2 = add2(u2, magic2);
+                    float u[2], t[2];
+                    upk(u2, u[0], u[1]);
+                    upk(t2, t[0], t[1]);
                     if (CPLX) {
-                        const float4 p = lds_f4<OFF>(addr);
-                        const float vr = fmaf(u, p.y, p.x), vi = fmaf(u, p.w, p.z);
-                        if (APOD) { acc[k] = fmaf(apw[k][jj], vr, acc[k]); acci[k] = fmaf(apw[k][jj], vi, acci[k]); }
-                        else { acc[k] += vr; acci[k] += vi; }
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int k = 2 * kp + h;
+                            const uint32_t addr = (__float_as_uint(t[h]) << SHIFT) + pb_ii;
+                            const float4 p = lds_f4<OFF>(addr);
+                            const float vr = fmaf(u[h], p.y, p.x), vi = fmaf(u[h], p.w, p.z);
+                            float ar, ai;
+                            upk(acc2[kp], ar, ai);
+                            float wr = 1.f, wi = 1.f;
+                            if (APOD) upk(apw2[kp][jj], wr, wi);
+                            const float w = h == 0 ? wr : wi;
+                            if (h == 0) ar = APOD ? fmaf(w, vr, ar) : ar + vr;
+                            else ai = APOD ? fmaf(w, vr, ai) : ai + vr;
+                            acc2[kp] = pk(ar, ai);
+                            acci[k] = APOD ? fmaf(w, vi, acci[k]) : acci[k] + vi;
+                        }
                     } else {
-                        const float2 p = lds_f2<OFF>(addr);
-                        const float v = fmaf(u, p.y, p.x);
-                        if (APOD) acc[k] = fmaf(apw[k][jj], v, acc[k]);
-                        else acc[k] += v;
+                        const uint32_t ad0 = (__float_as_uint(t[0]) << SHIFT) + pb_ii;
+                        const uint32_t ad1 = (__float_as_uint(t[1]) << SHIFT) + pb_ii;
+                        const float2 p0 = lds_f2<OFF>(ad0);
+                        const float2 p1 = lds_f2<OFF>(ad1);
+                        const f2x v2 = pk(fmaf(u[0], p0.y, p0.x), fmaf(u[1], p1.y, p1.x));
+                        acc2[kp] = APOD ? fma2(apw2[kp][jj], v2, acc2[kp]) : add2(acc2[kp], v2);
                     }
                 }
             });
@@ -412,6 +454,9 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
 
     // ---- store the tile (or this unit's partial of it)
     float* out = a.n_split > 1 ? a.partial + (long long)split * a.partial_stride : a.image;
+    float acc[4];
+    upk(acc2[0], acc[0], acc[1]);
+    upk(acc2[1], acc[2], acc[3]);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int ku = k % VU, kr = k / VU;
