@@ -273,9 +273,11 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
 
     // ---- producer: one thread per bulk copy (window, plane) of stage s into
     // raw buffer s & 1, once every thread has rewritten that buffer's previous stage
+    // the copy-issuing and transmit-term roles rotate over the warps from
+    // stage to stage, so that no warp carries the extra work every stage
     auto issue = [&](int s) -> bool {
-        if (tid >= C::COPIES) return true;
-        const int copy = tid;
+        const int copy = (tid + kDasThreads - (s * C::COPIES) % kDasThreads) % kDasThreads;
+        if (copy >= C::COPIES) return true;
         const int b = s & 1;
         if (!wait(kRawEmpty + b)) return false;
         const int win = CPLX ? (copy >> 1) : copy;
@@ -321,9 +323,10 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             rewrite_windows<int, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
         else
             rewrite_windows<float, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
-        if (tid < C::ALPHA_N) {
+        const int ae = (tid + kDasThreads - (s * C::ALPHA_N + kDasThreads / 2) % kDasThreads) % kDasThreads;
+        if (ae < C::ALPHA_N) {
             // transmit terms of this stage for every tile row (alpha depends on the row only)
-            const int ii = tid / C::ROWS, row = tid % C::ROWS;
+            const int ii = ae / C::ROWS, row = ae % C::ROWS;
             const float dv = (float)(row % a.bv) - 0.5f * (a.bv - 1);
             const float dw = (float)(row / a.bv) - 0.5f * (a.bw - 1);
             const float dL = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]) * dv + (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]) * dw;
