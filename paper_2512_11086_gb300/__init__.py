@@ -273,3 +273,51 @@ class Batch:
 
 def version() -> str:
     return load_library().rcbf_version().decode()
+
+
+def _make_das_function():
+    import torch
+
+    class DASFunction(torch.autograd.Function):
+        """Differentiable DAS: image = rcbf_das(decoded, apod, c). The backward
+        pass calls rcbf_das_backward (the hand-written adjoint kernel) for the
+        gradients with respect to the decoded RF, the per-channel apodization
+        weights and the speed of sound. decoded: float32 [n_tx][n_ch][n_s]
+        (or [2][...] planes for a complex plan); apod: float32 [n_ch]; c:
+        float32 scalar tensor."""
+
+        @staticmethod
+        def forward(ctx, decoded, apod, c, plan):
+            ctx.plan = plan
+            ctx.save_for_backward(decoded, apod, c)
+            return plan.das(decoded.contiguous(), apod=apod.contiguous(), c=float(c.item()))
+
+        @staticmethod
+        def backward(ctx, grad_image):
+            decoded, apod, c = ctx.saved_tensors
+            plan = ctx.plan
+            g_rf, g_c, g_w = plan.das_backward(decoded.contiguous(), grad_image.contiguous(),
+                                               apod=apod.contiguous(), c=float(c.item()),
+                                               want_rf=ctx.needs_input_grad[0],
+                                               want_apod=ctx.needs_input_grad[1],
+                                               want_c=ctx.needs_input_grad[2])
+            return g_rf, g_w, (g_c.reshape(c.shape) if g_c is not None else None), None
+
+    return DASFunction
+
+
+_DAS_FUNCTION = None
+
+
+def das_autograd(plan: Plan, decoded, apod, c):
+    """image = DAS(decoded; apod, c) with gradients through the adjoint kernel."""
+    global _DAS_FUNCTION
+    if _DAS_FUNCTION is None:
+        _DAS_FUNCTION = _make_das_function()
+    return _DAS_FUNCTION.apply(decoded, apod, c, plan)
+
+
+def envelope_loss(image):
+    """Autofocus loss: minus the summed squared envelope, -sum |I|^2 (image as
+    two planes [2][...] for a complex plan, or one real plane)."""
+    return -(image * image).sum()

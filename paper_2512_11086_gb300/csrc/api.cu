@@ -415,10 +415,34 @@ int rcbf_das(rcbf_plan_t plan, const void* decoded, const float* apod, float c, 
 
 int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, float c,
                       const float* grad_image, float* grad_rf, float* grad_c, float* grad_apod, void* stream) {
-    (void)decoded; (void)apod; (void)c; (void)grad_image; (void)grad_rf; (void)grad_c;
-    (void)grad_apod; (void)stream;
     if (!plan) return set_error(RCBF_EINVAL, "rcbf_das_backward: plan is NULL");
-    return set_error(RCBF_EUNSUPPORTED, "rcbf_das_backward: not built yet");
+    const PlanHost& h = plan->h;
+    if (!decoded || !grad_image) return set_error(RCBF_EINVAL, "rcbf_das_backward: NULL buffer");
+    if (!aligned16(decoded) || !aligned4(grad_image) || (grad_rf && !aligned4(grad_rf)) ||
+        (grad_c && !aligned4(grad_c)) || (grad_apod && !aligned4(grad_apod)) || (apod && !aligned4(apod)))
+        return set_error(RCBF_EINVAL, "rcbf_das_backward: decoded must be 16-byte aligned, float buffers 4-byte aligned");
+    if (h.p.decoded_dtype != RCBF_F32 && h.p.decoded_dtype != RCBF_CF32)
+        return set_error(RCBF_EUNSUPPORTED, "rcbf_das_backward: decoded_dtype must be RCBF_F32 or RCBF_CF32");
+    const double cc = c > 0.f ? (double)c : h.p.c;
+    DasArgs a;
+    std::string why;
+    const bool fits = das_prepare(h, cc, &a, &why) == RCBF_OK;
+    const bool tiled = h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok && fits;
+    a.rf = decoded;
+    a.apod = apod;
+    a.grad_image = grad_image;
+    a.grad_rf = grad_rf;
+    a.grad_c = grad_c;
+    a.grad_apod = grad_apod;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int planes = h.p.decoded_dtype == RCBF_CF32 ? 2 : 1;
+    if (grad_rf && cudaMemsetAsync(grad_rf, 0, (size_t)a.plane_stride * planes * sizeof(float), s) != cudaSuccess)
+        return check_launch("rcbf_das_backward: clear grad_rf");
+    if (grad_c && cudaMemsetAsync(grad_c, 0, sizeof(float), s) != cudaSuccess)
+        return check_launch("rcbf_das_backward: clear grad_c");
+    if (grad_apod && cudaMemsetAsync(grad_apod, 0, (size_t)h.p.n_ch * sizeof(float), s) != cudaSuccess)
+        return check_launch("rcbf_das_backward: clear grad_apod");
+    return launch_das_backward(h, a, tiled, s);
 }
 
 int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t* const* rf,

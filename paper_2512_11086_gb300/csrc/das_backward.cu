@@ -1,0 +1,423 @@
+// das_backward.cu — adjoint of the delay-and-sum of Eq. (1) for an upstream
+// gradient G = dL/dimage: gradients with respect to the decoded RF samples,
+// the speed of sound c and the per-channel apodization weights w_j. The paper
+// has no adjoint; it is Eq. (1) differentiated for speed-of-sound autofocus.
+//
+// With s = s_ij(v), n = floor(s), f = s - n and a_j(v) = w_j W_j(v):
+//   dL/dr_ij[n]   += a_j(v) G(v) (1 - f),   dL/dr_ij[n+1] += a_j(v) G(v) f
+//   dL/dc         += a_j(v) G(v) (r[n+1] - r[n]) ds/dc,   ds/dc = -(d_tx + d_rx) fs / c^2
+//                                                               = -(s + t0 fs) / c
+//   dL/dw_j       += W_j(v) G(v) lerp(r_ij, s)
+// (complex data: the two planes contribute independently).
+//
+// Tiled form: the forward's voxel tiles, per-tile FP64 reference delays,
+// TMA windows and line pieces (c_n, slope_n). Per stage each window gets a
+// shared-memory accumulator; the transposed interpolation weights go there by
+// shared atomics and the window is then added into dL/dr with global atomics
+// (windows of neighbouring tiles overlap). Delays are recomputed per tile,
+// never stored. The plain form is one thread per voxel with global atomics.
+#include <algorithm>
+
+#include "das_tile.cuh"
+
+namespace rcbf {
+
+namespace {
+
+constexpr int kBwdCI = 4;          // transmits per backward stage
+constexpr int kBwdCJ = 4;          // channels per backward stage
+constexpr int kBwdWS = 128;        // window intervals (every W <= 128)
+
+template <int VU, bool CPLX>
+struct BwdCfg {
+    static constexpr int VR = 4 / VU;
+    static constexpr int ROWS = 8 * VR;
+    static constexpr int BU = 32 * VU;
+    static constexpr int NWIN = kBwdCI * kBwdCJ;
+    static constexpr int PLANES = CPLX ? 2 : 1;
+    static constexpr int COPIES = NWIN * PLANES;
+    static constexpr int PAIR_BYTES = 8 * PLANES;
+    static constexpr int RAWS = kBwdWS + 8;
+    static constexpr int RAW_WIN_BYTES = RAWS * 4 * PLANES;
+    static constexpr int GW = kBwdWS + 2;            // accumulator samples per window plane
+    static constexpr int OFF_PAIRS = 0;
+    static constexpr int OFF_RAW = OFF_PAIRS + NWIN * kBwdWS * PAIR_BYTES;
+    static constexpr int OFF_GRAD = OFF_RAW + 2 * NWIN * RAW_WIN_BYTES;
+    static constexpr int OFF_TX = OFF_GRAD + NWIN * GW * 4 * PLANES;
+    static constexpr int OFF_RX = OFF_TX + kMaxOrder * 16;
+    static constexpr int OFF_ALPHA = OFF_RX + kMaxChannels * 16;
+    static constexpr int OFF_WIN = OFF_ALPHA + kBwdCI * ROWS * 4;      // int S0[2][NWIN], int off[2][NWIN]
+    static constexpr int OFF_GW = OFF_WIN + 4 * NWIN * 4;              // float[kMaxChannels]
+    static constexpr int OFF_RED = OFF_GW + kMaxChannels * 4;          // float[8]
+    static constexpr int OFF_BAR = OFF_RED + 32;                       // uint64[2]
+    static constexpr int SMEM = OFF_BAR + 16;
+    static_assert(OFF_RAW % 128 == 0 && OFF_GRAD % 16 == 0 && OFF_TX % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+};
+
+template <int VU, bool CPLX>
+__global__ void __launch_bounds__(kDasThreads, 2)
+das_bwd_kernel(DasArgs a) {
+    using C = BwdCfg<VU, CPLX>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float4* s_tx = reinterpret_cast<float4*>(smem + C::OFF_TX);
+    float4* s_rx = reinterpret_cast<float4*>(smem + C::OFF_RX);
+    float* s_alpha = reinterpret_cast<float*>(smem + C::OFF_ALPHA);
+    int* s_S0 = reinterpret_cast<int*>(smem + C::OFF_WIN);
+    int* s_off = s_S0 + 2 * C::NWIN;
+    float* s_gw = reinterpret_cast<float*>(smem + C::OFF_GW);
+    float* s_red = reinterpret_cast<float*>(smem + C::OFF_RED);
+    float* gwin = reinterpret_cast<float*>(smem + C::OFF_GRAD);
+    unsigned char* raw = smem + C::OFF_RAW;
+    const uint32_t bar0 = smem_u32(smem + C::OFF_BAR);
+    const uint32_t pairs_u32 = smem_u32(smem + C::OFF_PAIRS);
+
+    if (tid == 0) {
+        mbar_init(bar0, C::COPIES);
+        mbar_init(bar0 + 8, C::COPIES);
+        fence_mbar_init();
+    }
+    for (int q = tid; q < C::NWIN * C::GW * C::PLANES; q += kDasThreads) gwin[q] = 0.f;
+    for (int q = tid; q < kMaxChannels; q += kDasThreads) s_gw[q] = 0.f;
+
+    // ---- unit -> (tile, channel split)
+    const int n_tiles = a.tiles_u * a.tiles_v * a.tiles_w;
+    const int tile = blockIdx.x % n_tiles;
+    const int split = blockIdx.x / n_tiles;
+    const int n_ic = a.n_tx / kBwdCI;
+    const int js = (a.n_ch / kBwdCJ) / a.n_split;
+    const int jc0 = split * js;
+    const int NS = n_ic * js;
+
+    const int tu = tile % a.tiles_u, tv = (tile / a.tiles_u) % a.tiles_v, tw = tile / (a.tiles_u * a.tiles_v);
+    const int u0 = tu * C::BU, v0 = tv * a.bv, w0 = tw * a.bw;
+    const double cu = u0 + 0.5 * (C::BU - 1), cv = v0 + 0.5 * (a.bv - 1), cw = w0 + 0.5 * (a.bw - 1);
+    const double qx = a.q0[0] + a.Gu[0] * cu + a.Gv[0] * cv + a.Gw[0] * cw;
+    const double qy = a.q0[1] + a.Gu[1] * cu + a.Gv[1] * cv + a.Gw[1] * cw;
+    const double zr = a.q0[2] + a.Gu[2] * cu + a.Gv[2] * cv + a.Gw[2] * cw;
+    const double lat_tx_ref = a.tx_axis ? qy : qx, lat_rx_ref = a.rx_axis ? qy : qx;
+    const int j_lo = jc0 * kBwdCJ, n_rx = js * kBwdCJ;
+    for (int e = tid; e < a.n_tx + n_rx; e += kDasThreads) {
+        if (e < a.n_tx) {
+            const double L = lat_tx_ref - (a.tx_e0 + e * a.tx_pitch);
+            const double d = sqrt(L * L + zr * zr);
+            const double A = d * a.fs_over_c - a.t0fs;
+            const double K = floor(A);
+            s_tx[e] = make_float4((float)L, (float)d, (float)(A - K - (double)a.lo - 0.5 - (double)a.H),
+                                  __int_as_float((int)K));
+        } else {
+            const int j = j_lo + e - a.n_tx;
+            const double L = lat_rx_ref - (a.rx_e0 + j * a.rx_pitch);
+            const double d = sqrt(L * L + zr * zr);
+            const double B = d * a.fs_over_c;
+            const double K = floor(B);
+            s_rx[j] = make_float4((float)L, (float)d, (float)(B - K), __int_as_float((int)K));
+        }
+    }
+
+    // this thread's voxels: offsets, validity and upstream gradient
+    const float Zf = (float)zr, fsc = (float)a.fs_over_c;
+    float dlr[4], dz[4], g_re[4], g_im[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int ku = k % VU, kr = k / VU;
+        const int row = warp * C::VR + kr;
+        const int rv = row % a.bv, rw = row / a.bv;
+        const float du = (float)(lane + 32 * ku) - 0.5f * (C::BU - 1);
+        const float dv = (float)rv - 0.5f * (a.bv - 1);
+        const float dw = (float)rw - 0.5f * (a.bw - 1);
+        dlr[k] = (float)(a.rx_axis ? a.Gu[1] : a.Gu[0]) * du + (float)(a.rx_axis ? a.Gv[1] : a.Gv[0]) * dv +
+                 (float)(a.rx_axis ? a.Gw[1] : a.Gw[0]) * dw;
+        dz[k] = (float)a.Gu[2] * du + (float)a.Gv[2] * dv + (float)a.Gw[2] * dw;
+        const int iu = u0 + lane + 32 * ku, iv = v0 + rv, iw = w0 + rw;
+        const bool in = iu < a.n_u && iv < a.n_v && iw < a.n_w;
+        const long long o = (long long)iw * a.out_sw + (long long)iv * a.out_sv + (long long)iu * a.out_su;
+        g_re[k] = in ? a.grad_image[o] : 0.f;        // voxels outside the image carry no gradient
+        g_im[k] = (in && CPLX) ? a.grad_image[a.image_plane + o] : 0.f;
+    }
+    __syncthreads();
+
+    const int es = 4;
+    auto issue = [&](int s) {
+        if (tid >= C::COPIES) return;
+        const int b = s & 1;
+        const int win = CPLX ? (tid >> 1) : tid;
+        const int plane = CPLX ? (tid & 1) : 0;
+        const int ii = win / kBwdCJ, jj = win % kBwdCJ;
+        const int i = (s % n_ic) * kBwdCI + ii, j = (jc0 + s / n_ic) * kBwdCJ + jj;
+        const int S0 = __float_as_int(s_tx[i].w) + __float_as_int(s_rx[j].w) + a.lo;
+        const int A = S0 & ~7;
+        if (plane == 0) { s_off[b * C::NWIN + win] = S0 - A; s_S0[b * C::NWIN + win] = S0; }
+        const int lo_s = max(A, 0), hi_s = min(A + a.raw_samples, a.n_s);
+        unsigned char* dst = raw + (b * C::NWIN + win) * C::RAW_WIN_BYTES + plane * C::RAWS * 4;
+        const int pre = (min(lo_s, A + a.raw_samples) - A) * es;
+        const int body = hi_s > lo_s ? (hi_s - lo_s) * es : 0;
+        const int total = a.raw_samples * es;
+        for (int o = 0; o < pre; o += 16) *reinterpret_cast<uint4*>(dst + o) = make_uint4(0, 0, 0, 0);
+        for (int o = pre + body; o < total; o += 16) *reinterpret_cast<uint4*>(dst + o) = make_uint4(0, 0, 0, 0);
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar0 + 8 * b, (uint32_t)body);
+        if (body > 0) {
+            const char* src = static_cast<const char*>(a.rf) +
+                ((long long)plane * a.plane_stride + ((long long)i * a.n_ch + j) * a.n_s + lo_s) * es;
+            bulk_g2s(smem_u32(dst + pre), src, (uint32_t)body, bar0 + 8 * b);
+        }
+    };
+
+    issue(0);
+    if (NS > 1) issue(1);
+    __syncthreads();
+
+    const float magic = 8388608.0f + (float)a.H;
+    const float hp = 0.5f + (float)a.H;
+    constexpr int SHIFT = CPLX ? 4 : 3;
+    float beta[4][kBwdCJ], ag[4][kBwdCJ], agi[4][kBwdCJ], win_w[4][kBwdCJ], pj[4][kBwdCJ];
+    float gc = 0.f;
+    bool ok = true;
+    uint32_t phase = 0;
+
+    for (int s = 0; s < NS; ++s) {
+        const int ic = s % n_ic, jc = jc0 + s / n_ic;
+        const int b = s & 1;
+        if (ic == 0) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float Zv = Zf + dz[k];
+#pragma unroll
+                for (int jj = 0; jj < kBwdCJ; ++jj) {
+                    const int j = jc * kBwdCJ + jj;
+                    const float4 rx = s_rx[j];
+                    const float Lv = rx.x + dlr[k];
+                    const float d = sqrtf(Lv * Lv + Zv * Zv);
+                    const float num = dlr[k] * (2.0f * rx.x + dlr[k]) + dz[k] * (2.0f * Zf + dz[k]);
+                    const float bt = rx.z + __fdividef(num, d + rx.y) * fsc;
+                    beta[k][jj] = fminf(fmaxf(bt, rx.z - a.reach_b), rx.z + a.reach_b);
+                    const float W = a.f_number > 0.f ? hann_weight(a.f_number, Lv, Zv) : 1.0f;
+                    const float wj = a.apod ? __ldg(a.apod + j) : 1.0f;
+                    win_w[k][jj] = W;
+                    ag[k][jj] = wj * W * g_re[k];
+                    agi[k][jj] = wj * W * g_im[k];
+                    pj[k][jj] = 0.f;
+                }
+            }
+        }
+        // ---- wait for this stage's windows and rewrite them as line pieces
+        ok = mbar_wait_parity(bar0 + 8 * b, (phase >> b) & 1u) && ok;
+        phase ^= 1u << b;
+        {
+            const unsigned char* rawb = raw + b * C::NWIN * C::RAW_WIN_BYTES;
+            unsigned char* pairs = smem + C::OFF_PAIRS;
+            rewrite_windows<float, CPLX, kBwdWS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(
+                rawb, s_off + b * C::NWIN, pairs, a.W, hp, 1.0f, warp, lane);
+        }
+        if (tid < kBwdCI * C::ROWS) {
+            const int ii = tid / C::ROWS, row = tid % C::ROWS;
+            const float dv = (float)(row % a.bv) - 0.5f * (a.bv - 1);
+            const float dw = (float)(row / a.bv) - 0.5f * (a.bw - 1);
+            const float dL = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]) * dv + (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]) * dw;
+            const float dzz = (float)a.Gv[2] * dv + (float)a.Gw[2] * dw;
+            const float4 tx = s_tx[ic * kBwdCI + ii];
+            const float Lv = tx.x + dL, Zv = Zf + dzz;
+            const float d = sqrtf(Lv * Lv + Zv * Zv);
+            const float num = dL * (2.0f * tx.x + dL) + dzz * (2.0f * Zf + dzz);
+            const float al = tx.z + __fdividef(num, d + tx.y) * fsc;
+            s_alpha[ii * C::ROWS + row] = fminf(fmaxf(al, tx.z - a.reach_a), tx.z + a.reach_a);
+        }
+        if (__syncthreads_or(!ok)) {
+            if (s + 1 < NS) mbar_wait_parity(bar0 + 8 * (b ^ 1), (phase >> (b ^ 1)) & 1u);
+            if (tid == 0) atomicOr(a.status, kStatusWaitExpired);
+            return;
+        }
+
+        // ---- transposed interpolation into the window accumulators
+        const uint32_t pbase = pairs_u32 - (0x4B000000u << SHIFT);
+#pragma unroll
+        for (int ii = 0; ii < kBwdCI; ++ii) {
+#pragma unroll
+            for (int jj = 0; jj < kBwdCJ; ++jj) {
+                const int win = ii * kBwdCJ + jj;
+                // absolute sample position of u is S0 + u + 0.5 + H; add t0 fs
+                const float cwin = (float)s_S0[b * C::NWIN + win] + hp + (float)a.t0fs;
+                float* gw0 = gwin + win * C::GW;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int kr = k / VU;
+                    const float u = s_alpha[ii * C::ROWS + warp * C::VR + kr] + beta[k][jj];
+                    const float t = u + magic;
+                    const int n = (int)(__float_as_uint(t) - 0x4B000000u);
+                    const uint32_t addr = (__float_as_uint(t) << SHIFT) + pbase + win * kBwdWS * C::PAIR_BYTES;
+                    const float f = u + hp - (float)n;          // fraction within interval n
+                    float cr, sr, ci = 0.f, si = 0.f;
+                    if (CPLX) {
+                        float4 p;
+                        asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                                     : "=f"(p.x), "=f"(p.y), "=f"(p.z), "=f"(p.w) : "r"(addr));
+                        cr = p.x; sr = p.y; ci = p.z; si = p.w;
+                    } else {
+                        float2 p;
+                        asm volatile("ld.shared.v2.f32 {%0,%1}, [%2];" : "=f"(p.x), "=f"(p.y) : "r"(addr));
+                        cr = p.x; sr = p.y;
+                    }
+                    const float gr = ag[k][jj];
+                    atomicAdd(gw0 + n, gr * (1.0f - f));
+                    atomicAdd(gw0 + n + 1, gr * f);
+                    float dsum = gr * sr;
+                    pj[k][jj] += g_re[k] * fmaf(u, sr, cr);
+                    if (CPLX) {
+                        const float gi = agi[k][jj];
+                        float* gw1 = gw0 + C::NWIN * C::GW;
+                        atomicAdd(gw1 + n, gi * (1.0f - f));
+                        atomicAdd(gw1 + n + 1, gi * f);
+                        dsum = fmaf(gi, si, dsum);
+                        pj[k][jj] += g_im[k] * fmaf(u, si, ci);
+                    }
+                    gc = fmaf(dsum, u + cwin, gc);
+                }
+            }
+        }
+        if (ic == n_ic - 1) {
+            // this channel chunk is complete: dL/dw_j partials of the CTA
+#pragma unroll
+            for (int jj = 0; jj < kBwdCJ; ++jj) {
+                float v = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) v += win_w[k][jj] * pj[k][jj];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) atomicAdd(s_gw + jc * kBwdCJ + jj, v);
+            }
+        }
+        __syncthreads();
+        // ---- window accumulators -> dL/dr (global atomics), then clear them
+        for (int q = tid; q < C::NWIN * C::PLANES * (kBwdWS + 1); q += kDasThreads) {
+            const int n = q % (kBwdWS + 1);
+            const int wp = q / (kBwdWS + 1);
+            const int win = wp % C::NWIN, plane = wp / C::NWIN;
+            if (n > a.W) continue;
+            float* cell = gwin + (plane * C::NWIN + win) * C::GW + n;
+            const float v = *cell;
+            if (v == 0.f) continue;
+            *cell = 0.f;
+            const int S = s_S0[b * C::NWIN + win] + n;
+            if (S < 0 || S >= a.n_s) continue;
+            const int ii = win / kBwdCJ, jj = win % kBwdCJ;
+            const int i = ic * kBwdCI + ii, j = jc * kBwdCJ + jj;
+            if (a.grad_rf)
+                atomicAdd(a.grad_rf + (long long)plane * a.plane_stride + ((long long)i * a.n_ch + j) * a.n_s + S, v);
+        }
+        __syncthreads();
+        // the window starts of stage s are no longer read: refill its raw buffer
+        if (s + 2 < NS) issue(s + 2);
+    }
+
+    // ---- dL/dc and dL/dw partials of this unit
+    if (a.grad_c) {
+        float v = gc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_red[warp] = v;
+        __syncthreads();
+        if (tid == 0) {
+            float t = 0.f;
+            for (int w = 0; w < kDasThreads / 32; ++w) t += s_red[w];
+            atomicAdd(a.grad_c, -t / (float)a.c);
+        }
+    }
+    if (a.grad_apod) {
+        __syncthreads();
+        for (int j = j_lo + tid; j < j_lo + n_rx; j += kDasThreads)
+            if (s_gw[j] != 0.f) atomicAdd(a.grad_apod + j, s_gw[j]);
+    }
+}
+
+// Plain form: one thread per voxel, FP32 distances, global atomics.
+template <bool CPLX>
+__global__ void __launch_bounds__(128)
+das_bwd_plain_kernel(DasArgs a) {
+    const long long n_vox = (long long)a.n_u * a.n_v * a.n_w;
+    const long long vox = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (vox >= n_vox) return;
+    const int iu = (int)(vox % a.n_u), iv = (int)((vox / a.n_u) % a.n_v), iw = (int)(vox / ((long long)a.n_u * a.n_v));
+    const float qx = (float)a.q0[0] + (float)a.Gu[0] * iu + (float)a.Gv[0] * iv + (float)a.Gw[0] * iw;
+    const float qy = (float)a.q0[1] + (float)a.Gu[1] * iu + (float)a.Gv[1] * iv + (float)a.Gw[1] * iw;
+    const float z = (float)a.q0[2] + (float)a.Gu[2] * iu + (float)a.Gv[2] * iv + (float)a.Gw[2] * iw;
+    const float lat_tx = a.tx_axis ? qy : qx, lat_rx = a.rx_axis ? qy : qx;
+    const long long o = (long long)iw * a.out_sw + (long long)iv * a.out_sv + (long long)iu * a.out_su;
+    const float gre = a.grad_image[o], gim = CPLX ? a.grad_image[a.image_plane + o] : 0.f;
+    const float fsc = (float)a.fs_over_c, t0fs = (float)a.t0fs, inv_c = 1.0f / (float)a.c;
+    const float* rf = static_cast<const float*>(a.rf);
+    float gc = 0.f;
+    for (int j = 0; j < a.n_ch; ++j) {
+        const float dxr = lat_rx - ((float)a.rx_e0 + j * (float)a.rx_pitch);
+        const float drx = sqrtf(dxr * dxr + z * z);
+        const float W = a.f_number > 0.f ? hann_weight(a.f_number, dxr, z) : 1.0f;
+        if (W == 0.f) continue;
+        const float a_j = (a.apod ? __ldg(a.apod + j) : 1.0f) * W;
+        float gw = 0.f;
+        for (int i = 0; i < a.n_tx; ++i) {
+            const float dxt = lat_tx - ((float)a.tx_e0 + i * (float)a.tx_pitch);
+            const float dtx = sqrtf(dxt * dxt + z * z);
+            const float s = (dtx + drx) * fsc - t0fs;
+            const float fl = floorf(s);
+            const float f = s - fl;
+            const int n = (int)fl;
+            const long long base = ((long long)i * a.n_ch + j) * a.n_s;
+            const bool in0 = n >= 0 && n < a.n_s, in1 = n + 1 >= 0 && n + 1 < a.n_s;
+            for (int p = 0; p < (CPLX ? 2 : 1); ++p) {
+                const float g = p ? gim : gre;
+                const long long pb = p * a.plane_stride + base;
+                const float r0 = in0 ? __ldg(rf + pb + n) : 0.f;
+                const float r1 = in1 ? __ldg(rf + pb + n + 1) : 0.f;
+                if (a.grad_rf && g != 0.f) {
+                    if (in0) atomicAdd(a.grad_rf + pb + n, a_j * g * (1.0f - f));
+                    if (in1) atomicAdd(a.grad_rf + pb + n + 1, a_j * g * f);
+                }
+                gc += a_j * g * (r1 - r0) * (s + t0fs);
+                gw += g * ((1.0f - f) * r0 + f * r1);
+            }
+        }
+        if (a.grad_apod && gw != 0.f) atomicAdd(a.grad_apod + j, W * gw);
+    }
+    if (a.grad_c) {
+        float v = gc;
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0) atomicAdd(a.grad_c, -v * inv_c);
+    }
+}
+
+template <int VU, bool CPLX>
+int launch_bwd_tiled(const PlanHost& h, DasArgs a, cudaStream_t s) {
+    using C = BwdCfg<VU, CPLX>;
+    auto k = das_bwd_kernel<VU, CPLX>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess)
+        return check_launch("das_backward: set shared memory");
+    // channel split: enough units for two CTAs per SM
+    const long long tiles = (long long)a.tiles_u * a.tiles_v * a.tiles_w;
+    const int chunks = a.n_ch / kBwdCJ;
+    int sp = 1;
+    while (tiles * sp < 2LL * h.n_sms && sp * 2 <= chunks && chunks % (sp * 2) == 0) sp *= 2;
+    a.n_split = sp;
+    const unsigned grid = (unsigned)(tiles * sp);
+    k<<<grid, kDasThreads, C::SMEM, s>>>(a);
+    return check_launch("das_bwd_kernel");
+}
+
+}  // namespace
+
+int launch_das_backward(const PlanHost& h, const DasArgs& a, bool tiled, cudaStream_t s) {
+    const bool cplx = a.dtype == RCBF_CF32;
+    if (!tiled) {
+        const long long n_vox = (long long)a.n_u * a.n_v * a.n_w;
+        const unsigned grid = (unsigned)((n_vox + 127) / 128);
+        if (cplx) das_bwd_plain_kernel<true><<<grid, 128, 0, s>>>(a);
+        else das_bwd_plain_kernel<false><<<grid, 128, 0, s>>>(a);
+        return check_launch("das_bwd_plain_kernel");
+    }
+    switch (h.vu) {
+        case 1: return cplx ? launch_bwd_tiled<1, true>(h, a, s) : launch_bwd_tiled<1, false>(h, a, s);
+        case 2: return cplx ? launch_bwd_tiled<2, true>(h, a, s) : launch_bwd_tiled<2, false>(h, a, s);
+        default: return cplx ? launch_bwd_tiled<4, true>(h, a, s) : launch_bwd_tiled<4, false>(h, a, s);
+    }
+}
+
+}  // namespace rcbf

@@ -13,7 +13,7 @@ das_tiled_kernel(DasArgs a) {
     using C = DasCfg<VU, WS, CPLX>;
     extern __shared__ __align__(128) unsigned char smem[];
     das_pipe_init<C::COPIES>(smem + C::OFF_BAR, reinterpret_cast<volatile int*>(smem + C::OFF_ABORT));
-    DasPipe pipe{0u};
+    DasPipe pipe{0u};   // stage counter of this CTA
     if (!das_unit<VU, WS, CPLX, APOD>(a, blockIdx.x, smem, pipe) && threadIdx.x == 0)
         atomicOr(a.status, kStatusWaitExpired);
 }

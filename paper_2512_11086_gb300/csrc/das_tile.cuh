@@ -165,10 +165,14 @@ __device__ __forceinline__ void rewrite_windows(const unsigned char* rawb, const
 // line-piece buffers (3), each with a "full" and an "empty" barrier.
 enum : int { kRawFull = 0, kRawEmpty = 2, kPieceFull = 4, kPieceEmpty = 7, kNumBars = 10 };
 
-// Per-thread state of a CTA running DAS units: bit k is the parity of the
-// next phase this thread waits for on mbarrier slot k.
+// State of a CTA running DAS units: the number of stages it ran before the
+// current unit. Every barrier phase follows from the CTA-wide stage index
+// k = base + s: raw buffers (two) complete phase k/2 for stage k, line-piece
+// buffers (three) phase k/3, and each "empty" barrier starts with one
+// pre-completed phase. So any thread may wait on any phase without keeping
+// its own phase bits.
 struct DasPipe {
-    uint32_t phase;
+    uint32_t base;
 };
 
 // Initialise the CTA's mbarriers (thread 0) and pre-complete the first phase
@@ -265,21 +269,23 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     __syncthreads();   // reference tables ready
 
     volatile int* abort = reinterpret_cast<volatile int*>(smem + C::OFF_ABORT);
-    auto wait = [&](int slot) -> bool {
-        if (!mbar_wait_or_abort(bar0 + 8 * slot, (pipe.phase >> slot) & 1u, abort)) return false;
-        pipe.phase ^= 1u << slot;
-        return true;
+    auto wait = [&](int slot, uint32_t phase) -> bool {
+        return mbar_wait_or_abort(bar0 + 8 * slot, phase & 1u, abort);
     };
+    auto raw_phase = [&](int s) -> uint32_t { return (pipe.base + (uint32_t)s) >> 1; };
+    auto piece_phase = [&](int s) -> uint32_t { return (pipe.base + (uint32_t)s) / 3u; };
+    auto raw_buf = [&](int s) -> int { return (int)((pipe.base + (uint32_t)s) & 1u); };
+    auto piece_buf = [&](int s) -> int { return (int)((pipe.base + (uint32_t)s) % 3u); };
 
     // ---- producer: one thread per bulk copy (window, plane) of stage s into
-    // raw buffer s & 1, once every thread has rewritten that buffer's previous stage
+    // the raw buffer of stage s, once every thread has rewritten that buffer's previous stage
     // the copy-issuing and transmit-term roles rotate over the warps from
     // stage to stage, so that no warp carries the extra work every stage
     auto issue = [&](int s) -> bool {
         const int copy = (tid + kDasThreads - (s * C::COPIES) % kDasThreads) % kDasThreads;
         if (copy >= C::COPIES) return true;
-        const int b = s & 1;
-        if (!wait(kRawEmpty + b)) return false;
+        const int b = raw_buf(s);
+        if (!wait(kRawEmpty + b, raw_phase(s))) return false;
         const int win = CPLX ? (copy >> 1) : copy;
         const int plane = CPLX ? (copy & 1) : 0;
         const int ii = win / C::CJ, jj = win % C::CJ;
@@ -311,9 +317,9 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     // and of the transmit-term table, then release both buffers
     const float hp = 0.5f + (float)a.H;
     auto prepare = [&](int s) -> bool {
-        const int b = s & 1, pb = s % C::NB;
-        if (!wait(kRawFull + b)) return false;
-        if (!wait(kPieceEmpty + pb)) return false;
+        const int b = raw_buf(s), pb = piece_buf(s);
+        if (!wait(kRawFull + b, raw_phase(s))) return false;
+        if (!wait(kPieceEmpty + pb, piece_phase(s))) return false;
         const unsigned char* rawb = raw + b * C::NWIN * C::RAW_WIN_BYTES;
         unsigned char* pairs = smem + C::OFF_PAIRS + pb * C::PAIR_BUF;
         const int* woff = s_woff + b * C::NWIN;
@@ -362,7 +368,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
 
     for (int s = 0; ok && s < NS; ++s) {
         const int ic = s % n_ic, jc = jc0 + s / n_ic;
-        const int pb = s % C::NB;
+        const int pb = piece_buf(s);
         if (ic == 0) {
             // per-voxel receive terms (and apodization) for this channel chunk
 #pragma unroll
@@ -392,7 +398,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
         }
         if (s + 2 < NS) { if (!(ok = issue(s + 2))) break; issued = s + 2; }
         if (s + 1 < NS) { if (!(ok = prepare(s + 1))) break; landed = s + 1; }
-        if (!(ok = wait(kPieceFull + pb))) break;
+        if (!(ok = wait(kPieceFull + pb, piece_phase(s)))) break;
 
         // ---- the sum: 4 voxels x CI transmits x CJ channels from buffer pb
         const uint32_t pbase = pairs_u32 + pb * C::PAIR_BUF - (0x4B000000u << SHIFT);
@@ -447,13 +453,11 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     if (!ok) {
         // a bounded wait expired somewhere in the CTA: give the copies this
         // thread still expects a bounded chance to land, then stop
-        for (int k = landed + 1; k <= issued; ++k) {
-            const int slot = kRawFull + (k & 1);
-            mbar_wait_parity(bar0 + 8 * slot, (pipe.phase >> slot) & 1u);
-            pipe.phase ^= 1u << slot;
-        }
+        for (int k = landed + 1; k <= issued; ++k)
+            mbar_wait_parity(bar0 + 8 * (kRawFull + raw_buf(k)), raw_phase(k) & 1u);
         return false;
     }
+    pipe.base += (uint32_t)NS;
 
     // ---- store the tile (or this unit's partial of it)
     float* out = a.n_split > 1 ? a.partial + (long long)split * a.partial_stride : a.image;

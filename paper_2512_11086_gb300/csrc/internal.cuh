@@ -120,7 +120,7 @@ int das_prepare(const PlanHost& h, double c, DasArgs* a, std::string* why);
 int launch_decode(const PlanHost& h, const int16_t* rf, void* out, cudaStream_t s);
 int launch_das(const PlanHost& h, const DasArgs& a, cudaStream_t s);
 int launch_das_plain(const PlanHost& h, const DasArgs& a, cudaStream_t s);
-int launch_das_backward(const PlanHost& h, const DasArgs& a, cudaStream_t s);
+int launch_das_backward(const PlanHost& h, const DasArgs& a, bool tiled, cudaStream_t s);
 int configure_decode(PlanHost& h);
 int das_class_index(int W);
 int configure_das(PlanHost& h);
