@@ -253,6 +253,26 @@ int rcbf_batch_status(rcbf_batch_t batch, void* stream);
 /* rcbf_batch_destroy — free the batch's device work list. NULL is accepted. */
 void rcbf_batch_destroy(rcbf_batch_t batch);
 
+/* rcbf_das_noalloc — rcbf_das without a plan, for callers that must not
+ * allocate device memory: code that owns every device allocation through its
+ * own pool, real-time loops that forbid allocation after start-up, or a
+ * stream capture that may not allocate. rcbf_plan allocates (decode tables,
+ * a status word, the channel-split partial images), so those callers cannot
+ * make a plan. This entry point takes the parameter block itself, validates
+ * and sets up the geometry on the host, and calls no cudaMalloc, cudaFree or
+ * other allocating routine. The scratch the DAS kernels need (the partial
+ * images of a channel-split tile pass and the status word) is a fixed,
+ * file-scope device array of 16 MiB, which every GPU that loads the library
+ * holds until the process exits. There is no counterpart in the paper.
+ *   params, decoded, apod, c, image, stream: as for rcbf_plan + rcbf_das.
+ * The first call on a device looks up that device's address of the array;
+ * make it before any stream capture. All calls share the one array: calls
+ * whose work overlaps on the GPU (other streams, other host threads) race on
+ * it, so serialise them. Errors: as rcbf_plan and rcbf_das, and RCBF_EINVAL
+ * when the partial images would exceed the 16 MiB array. */
+int rcbf_das_noalloc(const rcbf_params* params, const void* decoded, const float* apod, float c,
+                     float* image, void* stream);
+
 /* rcbf_last_error — message for the last failure on this thread ("" if none). */
 const char* rcbf_last_error(void);
 

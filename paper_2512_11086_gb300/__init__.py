@@ -80,6 +80,7 @@ SIGNATURES = {
     "rcbf_batch_run": (ctypes.c_int, [_P, _P]),
     "rcbf_batch_status": (ctypes.c_int, [_P, _P]),
     "rcbf_batch_destroy": (None, [_P]),
+    "rcbf_das_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _P, _P, ctypes.c_float, _P, _P]),
     "rcbf_last_error": (ctypes.c_char_p, []),
     "rcbf_version": (ctypes.c_char_p, []),
 }

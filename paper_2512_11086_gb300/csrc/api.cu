@@ -163,30 +163,10 @@ int validate(const rcbf_params* p) {
     return RCBF_OK;
 }
 
-}  // namespace
-}  // namespace rcbf
-
-using namespace rcbf;
-
-extern "C" {
-
-const char* rcbf_last_error(void) { return g_last_error.c_str(); }
-
-const char* rcbf_version(void) { return "rcbf 0.1 (sm_103a)"; }
-
-int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
-    g_last_error.clear();
-    if (!out_plan) return set_error(RCBF_EINVAL, "rcbf_plan: out_plan is NULL");
-    *out_plan = nullptr;
-    int rc = validate(params);
-    if (rc != RCBF_OK) return rc;
-
-    rcbf_plan_s* plan = new rcbf_plan_s();
-    PlanHost& h = plan->h;
-    h.p = *params;
-    h.p.decode_matrix = nullptr;   // the matrix is copied, never referenced later
+// Geometry of a plan (host only, no CUDA call, no allocation): the voxel-index
+// to array-frame affine, the lane axis, the DAS argument block and the tile.
+void setup_geometry(PlanHost& h) {
     const rcbf_params& p = h.p;
-
     // ---- geometry: voxel index -> world (M), world -> array (X), G = X M
     double M[16] = {0}, X[16] = {0}, G[12];
     if (!all_zero(p.voxel_transform, 16)) {
@@ -289,6 +269,39 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
     a.tiles_w = (a.n_w + a.bw - 1) / a.bw;
     h.r_alpha_m = tile_radius(G, tx_axis, ua, va, a.bu, a.bv, a.bw);
     h.r_beta_m = tile_radius(G, rx_axis, ua, va, a.bu, a.bv, a.bw);
+
+}
+
+}  // namespace
+
+int plan_validate(const rcbf_params* p) { return validate(p); }
+void plan_geometry(PlanHost& h) { setup_geometry(h); }
+
+}  // namespace rcbf
+
+using namespace rcbf;
+
+extern "C" {
+
+const char* rcbf_last_error(void) { return g_last_error.c_str(); }
+
+const char* rcbf_version(void) { return "rcbf 0.1 (sm_103a)"; }
+
+int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
+    g_last_error.clear();
+    if (!out_plan) return set_error(RCBF_EINVAL, "rcbf_plan: out_plan is NULL");
+    *out_plan = nullptr;
+    int rc = validate(params);
+    if (rc != RCBF_OK) return rc;
+
+    rcbf_plan_s* plan = new rcbf_plan_s();
+    PlanHost& h = plan->h;
+    h.p = *params;
+    h.p.decode_matrix = nullptr;   // the matrix is copied, never referenced later
+    const rcbf_params& p = h.p;
+
+    setup_geometry(h);
+    DasArgs& a = h.das;
 
     // ---- device tables
     int dev = 0;

@@ -113,6 +113,11 @@ namespace rcbf {
 int set_error(int code, const std::string& msg);
 int check_launch(const char* what);
 
+// Host-side plan pieces (api.cu): argument validation and the geometry /
+// tile set-up of a plan, neither of which touches the device.
+int plan_validate(const rcbf_params* p);
+void plan_geometry(PlanHost& h);
+
 // Window geometry of a DAS call at speed of sound c (host side).
 int das_prepare(const PlanHost& h, double c, DasArgs* a, std::string* why);
 

@@ -1,0 +1,58 @@
+"""rcbf_das_noalloc: the delay-and-sum entry point for callers that must not
+allocate device memory (allocation owned by a host framework's pool, real-time
+loops, stream captures that may not allocate). It takes the parameter block
+instead of a plan and keeps its scratch (the channel-split partial images) in
+a fixed 16 MiB device array of the library. Its images must equal those of the
+planned rcbf_das on the same inputs, call after call."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests._frames import frame, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2512_11086_gb300 as rc  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_11086_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _noalloc(params, decoded, out, c=0.0):
+    lib = rc.load_library()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    code = lib.rcbf_das_noalloc(ctypes.byref(params), ctypes.c_void_p(decoded.data_ptr()), None,
+                                ctypes.c_float(c), ctypes.c_void_p(out.data_ptr()), stream)
+    assert code == rc.OK, lib.rcbf_last_error()
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("name", ["tiny", "bscan"])
+def test_noalloc_matches_planned_das_on_two_calls(name):
+    fr = frame(name)
+    g = fr.geometry
+    params = rc.make_params(g, decoded_dtype="f32")
+    plan = rc.Plan(rc.make_params(g, decoded_dtype="f32"))
+    assert plan.info()["n_split"] > 1        # the partial-image scratch is in use
+    D = oracle.decode(fr.rf)
+    dec = torch.from_numpy((D.astype(np.float64) / g.n_tx).astype(np.float32)).cuda()
+    out = torch.empty(plan.image_shape, dtype=torch.float32, device="cuda")
+    # first call, then a second one on other inputs (speed of sound, scaled data)
+    for c, scale in ((0.0, 1.0), (1500.0, -0.5)):
+        d = dec * scale
+        want = plan.das(d, c=c).cpu().numpy()
+        got = _noalloc(params, d, out, c=c)
+        err = rel_l2(got, want)
+        print("%s c=%g: rel-L2 vs rcbf_das %.2e" % (name, c, err))
+        assert err <= 1e-4
