@@ -227,14 +227,20 @@ int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, 
 
 /* rcbf_batch_create — bind n_frames (plan, buffers) triples into one batch
  * that a single persistent kernel processes: for every frame with a
- * Hadamard order, decode rf[f] into decoded[f], then DAS decoded[f] into
- * images[f] (frames with hadamard_order == 0 skip the decode and read
- * decoded[f] directly). Plans may differ in every size; all must use
- * decoded_dtype RCBF_F32 or RCBF_F16 and the tiled DAS. The plans must outlive
- * the batch. Pointer arrays are HOST arrays of DEVICE pointers, copied.
+ * Hadamard order, decode rf[f] into decoded[f] (with the plan's tensor-core
+ * decode form), then DAS decoded[f] into images[f] (frames with
+ * hadamard_order == 0 skip the decode and read decoded[f] directly). Plans
+ * may differ in transmit count, samples, grid and orientation; all must use
+ * decoded_dtype RCBF_F32 or RCBF_F16, the tiled DAS with no F# window, and
+ * the same tile extent along u (tile[0]). Each frame is beamformed at its
+ * plan's speed of sound, without channel weights. The plans must outlive the
+ * batch. Pointer arrays are HOST arrays of DEVICE pointers, copied; rf may be
+ * NULL when no frame is encoded.
  * Passage: §METHODS "Data Processing" (pre-uploaded parameter sets) and
  * §OPTIMIZATIONS "Data Transfer" (frames kept in flight).
- * Allocates the device work list; synchronises once. */
+ * Allocates the device work list; synchronises once. Errors: RCBF_EINVAL,
+ * RCBF_EUNSUPPORTED (dtype, variant, F#, window longer than 128 samples),
+ * RCBF_ENOMEM, RCBF_ECUDA. */
 int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames,
                       const int16_t* const* rf, void* const* decoded,
                       float* const* images, rcbf_batch_t* out_batch);
@@ -249,6 +255,14 @@ int rcbf_batch_run(rcbf_batch_t batch, void* stream);
 /* rcbf_batch_status — synchronise `stream` and return the device status word
  * of the last run: RCBF_OK or RCBF_ETIMEOUT. */
 int rcbf_batch_status(rcbf_batch_t batch, void* stream);
+
+/* rcbf_batch_set_wait — bound of a DAS item's wait for its frame's decode
+ * (default one second; at most ten), and a test hook: withhold_frame >= 0
+ * makes that frame's decode completion count unreachable, so that its DAS
+ * items wait out the bound and the run reports RCBF_ETIMEOUT through
+ * rcbf_batch_status while the context stays usable; -1 disables the hook.
+ * Host only. Errors: RCBF_EINVAL (NULL batch, wait_ns == 0, frame out of range). */
+int rcbf_batch_set_wait(rcbf_batch_t batch, uint64_t wait_ns, int32_t withhold_frame);
 
 /* rcbf_batch_destroy — free the batch's device work list. NULL is accepted. */
 void rcbf_batch_destroy(rcbf_batch_t batch);

@@ -79,6 +79,7 @@ SIGNATURES = {
                                          ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "rcbf_batch_run": (ctypes.c_int, [_P, _P]),
     "rcbf_batch_status": (ctypes.c_int, [_P, _P]),
+    "rcbf_batch_set_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int32]),
     "rcbf_batch_destroy": (None, [_P]),
     "rcbf_das_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _P, _P, ctypes.c_float, _P, _P]),
     "rcbf_last_error": (ctypes.c_char_p, []),
@@ -247,18 +248,25 @@ class Batch:
         n = len(plans)
         P = ctypes.c_void_p
         self._plans = list(plans)
-        self._bufs = (list(rf), list(decoded), list(images))
+        self._bufs = (None if rf is None else list(rf), list(decoded), list(images))
         arr = lambda xs: (P * n)(*[P(0 if x is None else x.data_ptr()) for x in xs])
         hp = (P * n)(*[p.handle for p in plans])
         h = P()
-        _check(lib.rcbf_batch_create(hp, n, arr(rf), arr(decoded), arr(images), ctypes.byref(h)))
+        rf_arr = arr(rf) if rf is not None else None
+        _check(lib.rcbf_batch_create(hp, n, rf_arr, arr(decoded), arr(images), ctypes.byref(h)))
         self.handle = h
 
     def run(self, stream=None):
         _check(load_library().rcbf_batch_run(self.handle, _stream(stream)))
 
     def status(self, stream=None) -> int:
+        """Synchronise the stream and return OK or ETIMEOUT (no exception)."""
         return int(load_library().rcbf_batch_status(self.handle, _stream(stream)))
+
+    def set_wait(self, wait_ns: int, withhold_frame: int = -1):
+        """rcbf_batch_set_wait: bound of the per-frame decode wait; the
+        withhold_frame test hook makes one frame's wait expire."""
+        _check(load_library().rcbf_batch_set_wait(self.handle, int(wait_ns), int(withhold_frame)))
 
     def close(self):
         if getattr(self, "handle", None):

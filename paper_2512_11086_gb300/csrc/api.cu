@@ -458,24 +458,5 @@ int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, 
     return launch_das_backward(h, a, tiled, s);
 }
 
-int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t* const* rf,
-                      void* const* decoded, float* const* images, rcbf_batch_t* out_batch) {
-    (void)plans; (void)n_frames; (void)rf; (void)decoded; (void)images;
-    if (out_batch) *out_batch = nullptr;
-    return set_error(RCBF_EUNSUPPORTED, "rcbf_batch_create: not built yet");
-}
-
-int rcbf_batch_run(rcbf_batch_t batch, void* stream) {
-    (void)stream;
-    if (!batch) return set_error(RCBF_EINVAL, "rcbf_batch_run: batch is NULL");
-    return set_error(RCBF_EUNSUPPORTED, "rcbf_batch_run: not built yet");
-}
-
-int rcbf_batch_status(rcbf_batch_t batch, void* stream) {
-    (void)batch; (void)stream;
-    return set_error(RCBF_EUNSUPPORTED, "rcbf_batch_status: not built yet");
-}
-
-void rcbf_batch_destroy(rcbf_batch_t batch) { (void)batch; }
 
 }  // extern "C"

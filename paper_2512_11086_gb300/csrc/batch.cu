@@ -1,0 +1,191 @@
+// batch.cu — host side of the batched stream (rcbf_batch_*): one persistent
+// launch decodes and beamforms many frames of uneven size (§METHODS "Data
+// Processing": several pre-uploaded parameter sets, each frame with its own
+// acquisition and image description).
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "batch_kernel.cuh"
+
+namespace rcbf {
+template <int VU> int batch_configure_vu(int ws, int* per_sm, size_t* smem);
+template <int VU> int batch_launch_vu(int ws, unsigned grid, size_t smem, const int4* items, int n_items,
+                                      const BatchFrame* frames, int* counters, long long wait_ns, int withhold,
+                                      cudaStream_t s);
+}  // namespace rcbf
+
+struct rcbf_batch_s {
+    int n_frames = 0;
+    int n_items = 0;
+    int vu = 2;
+    int ws = 64;
+    unsigned grid = 1;
+    size_t smem = 0;
+    long long wait_ns = 1000000000LL;   // bounded wait of a DAS item on its frame's decode
+    int withhold = -1;                  // test hook: a frame whose decode never completes
+    int4* d_items = nullptr;
+    rcbf::BatchFrame* d_frames = nullptr;
+    int* d_counters = nullptr;
+};
+
+using namespace rcbf;
+
+namespace {
+
+int batch_fail(rcbf_batch_s* b, int code, const std::string& msg) {
+    rcbf_batch_destroy(b);
+    return set_error(code, msg);
+}
+
+int class_of(int W) { return W <= 48 ? 48 : W <= 64 ? 64 : 128; }
+
+}  // namespace
+
+extern "C" {
+
+int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t* const* rf,
+                      void* const* decoded, float* const* images, rcbf_batch_t* out_batch) {
+    if (!out_batch) return set_error(RCBF_EINVAL, "rcbf_batch_create: out_batch is NULL");
+    *out_batch = nullptr;
+    if (!plans || !decoded || !images || n_frames == 0)
+        return set_error(RCBF_EINVAL, "rcbf_batch_create: NULL array or zero frames");
+    const int bu = plans[0] ? plans[0]->h.das.bu : 0;
+    std::vector<BatchFrame> frames(n_frames);
+    int ws = 48;
+    for (uint32_t f = 0; f < n_frames; ++f) {
+        const rcbf_plan_t p = plans[f];
+        const std::string at = "rcbf_batch_create: frame " + std::to_string(f) + ": ";
+        if (!p) return set_error(RCBF_EINVAL, at + "NULL plan");
+        const PlanHost& h = p->h;
+        if (h.p.decoded_dtype != RCBF_F16 && h.p.decoded_dtype != RCBF_F32)
+            return set_error(RCBF_EUNSUPPORTED, at + "decoded_dtype must be RCBF_F16 or RCBF_F32");
+        if (h.p.das_variant != RCBF_DAS_TILED || !h.tiled_ok)
+            return set_error(RCBF_EUNSUPPORTED, at + "the plan must use the tiled DAS");
+        if (h.p.f_number > 0.0) return set_error(RCBF_EUNSUPPORTED, at + "batch frames use no F# window");
+        if (h.das.bu != bu) return set_error(RCBF_EINVAL, at + "all plans of a batch need the same tile extent along u");
+        if (!decoded[f] || !images[f] || (h.p.hadamard_order && (!rf || !rf[f])))
+            return set_error(RCBF_EINVAL, at + "NULL buffer");
+        if ((reinterpret_cast<uintptr_t>(decoded[f]) & 15u) || (reinterpret_cast<uintptr_t>(images[f]) & 3u) ||
+            (h.p.hadamard_order && (reinterpret_cast<uintptr_t>(rf[f]) & 15u)))
+            return set_error(RCBF_EINVAL, at + "misaligned buffer");
+        BatchFrame& fr = frames[f];
+        std::memset(&fr, 0, sizeof(fr));
+        std::string why;
+        if (das_prepare(h, h.p.c, &fr.das, &why) != RCBF_OK) return set_error(RCBF_EUNSUPPORTED, at + why);
+        fr.das.rf = decoded[f];
+        fr.das.image = images[f];
+        fr.das.apod = nullptr;
+        fr.das.n_split = 1;
+        fr.das.partial = nullptr;
+        ws = std::max(ws, class_of(fr.das.W));
+        fr.out_dtype = (int)h.p.decoded_dtype;
+        fr.order = (int)h.p.n_tx;
+        if (h.p.hadamard_order) {
+            fr.n_decode = (int)(((long long)h.p.n_ch * h.p.n_samples + kDecodeCols - 1) / kDecodeCols);
+            fr.decode_f16 = h.p.decode_variant == RCBF_DECODE_MMA_F16 ? 1 : 0;
+            DecodeArgs& d = fr.dec;
+            d.rf = rf[f];
+            d.out = decoded[f];
+            d.afrag = h.d_afrag;
+            d.afrag16 = h.d_afrag16;
+            d.hsum = h.d_hsum;
+            d.hmat = h.d_hmat;
+            d.n_cols = (long long)h.p.n_ch * h.p.n_samples;
+            d.n = (int)h.p.n_tx;
+            d.dtype = (int)h.p.decoded_dtype;
+            d.inv_n = 1.0f / (float)h.p.n_tx;
+            if (!h.d_afrag) return set_error(RCBF_EUNSUPPORTED, at + "the tensor-core decode needs n_tx in {32, 64, 128, 256}");
+        }
+    }
+    // item list: decode of frame f+1 ahead of the DAS of frame f
+    std::vector<int4> items;
+    auto push_decode = [&](int f) {
+        for (int t = 0; t < frames[f].n_decode; ++t) items.push_back(make_int4(kItemDecode, f, t, 0));
+    };
+    auto push_das = [&](int f) {
+        const DasArgs& a = frames[f].das;
+        const int units = a.tiles_u * a.tiles_v * a.tiles_w;
+        for (int u = 0; u < units; ++u) items.push_back(make_int4(kItemDas, f, u, 0));
+    };
+    push_decode(0);
+    for (uint32_t f = 0; f < n_frames; ++f) {
+        if (f + 1 < n_frames) push_decode((int)f + 1);
+        push_das((int)f);
+    }
+    for (uint32_t f = 0; f < n_frames; ++f) frames[f].das.status = nullptr;   // set below
+
+    rcbf_batch_s* b = new rcbf_batch_s();
+    b->n_frames = (int)n_frames;
+    b->n_items = (int)items.size();
+    b->vu = bu / 32;
+    b->ws = ws;
+    if (cudaMalloc(&b->d_items, items.size() * sizeof(int4)) != cudaSuccess ||
+        cudaMalloc(&b->d_frames, frames.size() * sizeof(BatchFrame)) != cudaSuccess ||
+        cudaMalloc(&b->d_counters, (kBatchDone + n_frames) * sizeof(int)) != cudaSuccess)
+        return batch_fail(b, RCBF_ENOMEM, "rcbf_batch_create: cudaMalloc");
+    for (auto& fr : frames) fr.das.status = b->d_counters + kBatchStatus;
+    if (cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(b->d_frames, frames.data(), frames.size() * sizeof(BatchFrame), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->d_counters, 0, (kBatchDone + n_frames) * sizeof(int)) != cudaSuccess)
+        return batch_fail(b, RCBF_ECUDA, "rcbf_batch_create: copy work list");
+    int per_sm = 1, rc;
+    switch (b->vu) {
+        case 1: rc = batch_configure_vu<1>(ws, &per_sm, &b->smem); break;
+        case 2: rc = batch_configure_vu<2>(ws, &per_sm, &b->smem); break;
+        default: rc = batch_configure_vu<4>(ws, &per_sm, &b->smem); break;
+    }
+    if (rc != RCBF_OK) { const std::string m = rcbf_last_error(); return batch_fail(b, rc, m); }
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->grid = (unsigned)std::min<long long>((long long)sms * per_sm, (long long)items.size());
+    *out_batch = b;
+    return RCBF_OK;
+}
+
+int rcbf_batch_run(rcbf_batch_t batch, void* stream) {
+    if (!batch) return set_error(RCBF_EINVAL, "rcbf_batch_run: batch is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(batch->d_counters, 0, (kBatchDone + batch->n_frames) * sizeof(int), s) != cudaSuccess)
+        return check_launch("rcbf_batch_run: reset counters");
+    switch (batch->vu) {
+        case 1: return batch_launch_vu<1>(batch->ws, batch->grid, batch->smem, batch->d_items, batch->n_items,
+                                          batch->d_frames, batch->d_counters, batch->wait_ns, batch->withhold, s);
+        case 2: return batch_launch_vu<2>(batch->ws, batch->grid, batch->smem, batch->d_items, batch->n_items,
+                                          batch->d_frames, batch->d_counters, batch->wait_ns, batch->withhold, s);
+        default: return batch_launch_vu<4>(batch->ws, batch->grid, batch->smem, batch->d_items, batch->n_items,
+                                           batch->d_frames, batch->d_counters, batch->wait_ns, batch->withhold, s);
+    }
+}
+
+int rcbf_batch_status(rcbf_batch_t batch, void* stream) {
+    if (!batch) return set_error(RCBF_EINVAL, "rcbf_batch_status: batch is NULL");
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return check_launch("rcbf_batch_status: synchronize");
+    int st = 0;
+    if (cudaMemcpy(&st, batch->d_counters + kBatchStatus, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return check_launch("rcbf_batch_status: read status");
+    if (st) return set_error(RCBF_ETIMEOUT, "rcbf_batch_status: a bounded device wait expired");
+    return RCBF_OK;
+}
+
+int rcbf_batch_set_wait(rcbf_batch_t batch, uint64_t wait_ns, int32_t withhold_frame) {
+    if (!batch) return set_error(RCBF_EINVAL, "rcbf_batch_set_wait: batch is NULL");
+    if (wait_ns == 0 || withhold_frame < -1 || withhold_frame >= batch->n_frames)
+        return set_error(RCBF_EINVAL, "rcbf_batch_set_wait: wait_ns must be > 0 and withhold_frame in [-1, n_frames)");
+    batch->wait_ns = (long long)std::min<uint64_t>(wait_ns, (uint64_t)10000000000ULL);
+    batch->withhold = withhold_frame;
+    return RCBF_OK;
+}
+
+void rcbf_batch_destroy(rcbf_batch_t batch) {
+    if (!batch) return;
+    if (batch->d_items) cudaFree(batch->d_items);
+    if (batch->d_frames) cudaFree(batch->d_frames);
+    if (batch->d_counters) cudaFree(batch->d_counters);
+    delete batch;
+}
+
+}  // extern "C"

@@ -1,0 +1,162 @@
+// batch_kernel.cuh — many frames of uneven size in one persistent launch
+// (§METHODS "Data Processing": several pre-uploaded parameter sets;
+// §OPTIMIZATIONS "Data Transfer": frames kept in flight).
+//
+// Work items are decode tiles (128 columns of one frame) and DAS units (one
+// voxel tile of one frame). Resident CTAs take items in list order through an
+// atomic ticket. The host orders the list so that the decode of frame f+1
+// precedes the DAS of frame f, and a DAS item waits (bounded by a time limit)
+// until every decode item of its frame has completed. Every item it waits for
+// holds a smaller ticket and never waits itself, so the waits always end
+// unless a frame's completion count is made unreachable on purpose (the
+// host-side test hook of rcbf_batch_set_wait), in which case the wait expires
+// and the status word records it.
+#pragma once
+
+#include "das_tile.cuh"
+#include "decode_tile.cuh"
+
+namespace rcbf {
+
+struct BatchFrame {
+    DasArgs das;        // DAS of the frame (rf = its decoded buffer, image = its image)
+    DecodeArgs dec;     // decode of the frame (valid when n_decode > 0)
+    int n_decode;       // decode items of the frame (0: the frame is not encoded)
+    int decode_f16;     // 1: split-byte FP16 form, 0: split-byte int8 form
+    int order;          // Hadamard order
+    int out_dtype;      // RCBF_F16 or RCBF_F32
+};
+
+enum : int { kItemDecode = 0, kItemDas = 1 };
+enum : int { kBatchTicket = 0, kBatchStatus = 1, kBatchDone = 2 };   // counter slots
+
+template <int VU, int WS>
+struct BatchCfg {
+    using D = DasCfg<VU, WS, false>;
+    static constexpr int OFF_ARGS = ((D::SMEM + 15) / 16) * 16;
+    static constexpr int SMEM_DAS = OFF_ARGS + (int)((sizeof(DasArgs) + 15) / 16) * 16;
+    static constexpr int SMEM_DEC = DecodeCfg<256>::STAGE_BYTES;     // one staged tile of the largest order
+    static constexpr int SMEM = SMEM_DAS > SMEM_DEC ? SMEM_DAS : SMEM_DEC;
+    static_assert(SMEM_DEC <= D::OFF_BAR, "a decode tile must not overlap the DAS mbarriers");
+};
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <int N, int DT>
+__device__ __forceinline__ void batch_decode_n(const BatchFrame& f, long long tile, unsigned char* smem) {
+    if (f.decode_f16) decode_one_tile<N, DT, true>(f.dec, tile, smem);
+    else decode_one_tile<N, DT, false>(f.dec, tile, smem);
+}
+
+template <int DT>
+__device__ __forceinline__ void batch_decode_dt(const BatchFrame& f, long long tile, unsigned char* smem) {
+    switch (f.order) {
+        case 32: batch_decode_n<32, DT>(f, tile, smem); break;
+        case 64: batch_decode_n<64, DT>(f, tile, smem); break;
+        case 128: batch_decode_n<128, DT>(f, tile, smem); break;
+        default: batch_decode_n<256, DT>(f, tile, smem); break;
+    }
+}
+
+template <int VU, int WS>
+__global__ void __launch_bounds__(kDasThreads, 2)
+batch_kernel(const int4* __restrict__ items, int n_items, const BatchFrame* __restrict__ frames,
+             int* counters, long long wait_ns, int withhold) {
+    using C = BatchCfg<VU, WS>;
+    using D = typename C::D;
+    extern __shared__ __align__(128) unsigned char smem[];
+    DasArgs* s_args = reinterpret_cast<DasArgs*>(smem + C::OFF_ARGS);
+    __shared__ int s_item, s_ok;
+    das_pipe_init<D::COPIES>(smem + D::OFF_BAR, reinterpret_cast<volatile int*>(smem + D::OFF_ABORT));
+    DasPipe pipe{0u};
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counters + kBatchTicket, 1);
+        __syncthreads();
+        const int t = s_item;
+        if (t >= n_items) break;
+        const int4 it = items[t];
+        const BatchFrame& fr = frames[it.y];
+        if (it.x == kItemDecode) {
+            if (fr.out_dtype == RCBF_F16) batch_decode_dt<RCBF_F16>(fr, it.z, smem);
+            else batch_decode_dt<RCBF_F32>(fr, it.z, smem);
+            if (threadIdx.x == 0) {
+                __threadfence();                                   // release the decoded tile
+                atomicAdd(counters + kBatchDone + it.y, 1);
+            }
+        } else {
+            if (threadIdx.x == 0) {
+                int ok = 1;
+                const int need = fr.n_decode + (it.y == withhold ? 1 : 0);
+                if (need > 0) {
+                    const unsigned long long t0 = global_ns();
+                    while (ld_acquire(counters + kBatchDone + it.y) < need) {
+                        if (global_ns() - t0 > (unsigned long long)wait_ns) {
+                            ok = 0;
+                            atomicOr(counters + kBatchStatus, kStatusWaitExpired);
+                            break;
+                        }
+                        __nanosleep(200);
+                    }
+                }
+                s_ok = ok;
+            }
+            __syncthreads();
+            if (s_ok) {
+                // the frame's DAS arguments, then order the acquired decode
+                // output before the TMA (async proxy) reads of it
+                const int4* src = reinterpret_cast<const int4*>(&fr.das);
+                int4* dst = reinterpret_cast<int4*>(s_args);
+                for (int q = threadIdx.x; q < (int)(sizeof(DasArgs) / 16); q += kDasThreads) dst[q] = src[q];
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                __syncthreads();
+                const bool ok = das_unit<VU, WS, false, false>(*s_args, it.z, smem, pipe);
+                if (__syncthreads_or(!ok)) {
+                    if (threadIdx.x == 0) atomicOr(counters + kBatchStatus, kStatusWaitExpired);
+                    break;
+                }
+            }
+        }
+        __syncthreads();   // s_item, s_args and the staging buffers are reused
+    }
+}
+
+template <int VU, int WS>
+int batch_configure(int* per_sm, size_t* smem) {
+    using C = BatchCfg<VU, WS>;
+    auto k = batch_kernel<VU, WS>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess)
+        return check_launch("batch: set shared memory");
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kDasThreads, C::SMEM) != cudaSuccess)
+        return check_launch("batch: occupancy");
+    *per_sm = n < 1 ? 1 : n;
+    *smem = C::SMEM;
+    return RCBF_OK;
+}
+
+template <int VU>
+int batch_configure_vu(int ws, int* per_sm, size_t* smem) {
+    if (ws == 48) return batch_configure<VU, 48>(per_sm, smem);
+    if (ws == 64) return batch_configure<VU, 64>(per_sm, smem);
+    return batch_configure<VU, 128>(per_sm, smem);
+}
+
+template <int VU>
+int batch_launch_vu(int ws, unsigned grid, size_t smem, const int4* items, int n_items, const BatchFrame* frames,
+                    int* counters, long long wait_ns, int withhold, cudaStream_t s) {
+    if (ws == 48) batch_kernel<VU, 48><<<grid, kDasThreads, smem, s>>>(items, n_items, frames, counters, wait_ns, withhold);
+    else if (ws == 64) batch_kernel<VU, 64><<<grid, kDasThreads, smem, s>>>(items, n_items, frames, counters, wait_ns, withhold);
+    else batch_kernel<VU, 128><<<grid, kDasThreads, smem, s>>>(items, n_items, frames, counters, wait_ns, withhold);
+    return check_launch("batch_kernel");
+}
+
+}  // namespace rcbf

@@ -1,0 +1,8 @@
+// batch_vu1.cu — persistent batch kernel instantiations with 1 voxel(s) per thread along u.
+#include "batch_kernel.cuh"
+
+namespace rcbf {
+template int batch_configure_vu<1>(int, int*, size_t*);
+template int batch_launch_vu<1>(int, unsigned, size_t, const int4*, int, const BatchFrame*, int*, long long, int,
+                                 cudaStream_t);
+}  // namespace rcbf

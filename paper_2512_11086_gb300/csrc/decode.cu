@@ -16,71 +16,11 @@
 // one column, which two byte permutes turn into the hi / lo B fragments. The
 // B fragment's k order is therefore a fixed permutation of the acquisitions;
 // the A = H^T fragments are built on the host in the same permuted order.
-#include "internal.cuh"
+#include "decode_tile.cuh"
 
 namespace rcbf {
 
 namespace {
-
-constexpr int kRowPitch = kDecodeCols * 2 + 16;   // bytes per staged row (padding kills ldmatrix conflicts)
-
-template <int N> struct DecodeCfg {
-    static constexpr int MG = N / 32;              // warp groups along M (2 m16 tiles each)
-    static constexpr int NG = 8 / MG;              // warp groups along N
-    static constexpr int NT = (kDecodeCols / 8) / NG;   // n8 tiles per warp
-    static constexpr int KC = N / 32;              // k32 chunks
-    static constexpr int STAGES = (N >= 256) ? 2 : 3;
-    static constexpr int STAGE_BYTES = N * kRowPitch;
-    static constexpr int SMEM = STAGES * STAGE_BYTES;
-    static constexpr int CHUNKS = N * (kDecodeCols / 8);          // 16-byte chunks per stage
-    static constexpr int CHUNKS_PER_THREAD = CHUNKS / kDecodeThreads;
-};
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
-    const int n = valid ? 16 : 0;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(dst), "l"(src), "r"(n) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int K> __device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" :: "n"(K) : "memory");
-}
-
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
-}
-
-__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
-    uint32_t d;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
-    return d;
-}
-
-__device__ __forceinline__ void mma_s8s8(int (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-                 : "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-__device__ __forceinline__ void mma_s8u8(int (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.s8.u8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-                 : "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-template <int DT>
-__device__ __forceinline__ void store_pair(void* out, long long idx, int d0, int d1, float inv_n) {
-    if (DT == RCBF_I32) {
-        *reinterpret_cast<int2*>(static_cast<int*>(out) + idx) = make_int2(d0, d1);
-    } else if (DT == RCBF_F32) {
-        // |d| < 2^24, so the conversion is exact and the power-of-two scale too
-        *reinterpret_cast<float2*>(static_cast<float*>(out) + idx) =
-            make_float2(__int2float_rn(d0) * inv_n, __int2float_rn(d1) * inv_n);
-    } else {
-        // one rounding of the exact value d / n
-        *reinterpret_cast<__half2*>(static_cast<__half*>(out) + idx) =
-            __floats2half2_rn(__int2float_rn(d0) * inv_n, __int2float_rn(d1) * inv_n);
-    }
-}
 
 template <int N, int DT>
 __global__ void __launch_bounds__(kDecodeThreads, 1)
@@ -169,12 +109,6 @@ decode_mma_kernel(DecodeArgs a) {
         }
     }
     cp_async_wait<0>();
-}
-
-__device__ __forceinline__ void mma_f16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 // Byte-split FP16 form. The sample is offset to unsigned, u = v + 32768 =

@@ -110,6 +110,11 @@ def test_null_arguments_rejected(lib):
     assert lib.rcbf_das_backward(None, None, None, ctypes.c_float(0), None, None, None, None, None) == rc.EINVAL
     assert lib.rcbf_batch_run(None, None) == rc.EINVAL
     assert lib.rcbf_plan_query(None, None) == rc.EINVAL
+    assert lib.rcbf_batch_status(None, None) == rc.EINVAL
+    assert lib.rcbf_batch_set_wait(None, 1000, -1) == rc.EINVAL
+    h = ctypes.c_void_p()
+    assert lib.rcbf_batch_create(None, 0, None, None, None, ctypes.byref(h)) == rc.EINVAL
+    assert lib.rcbf_batch_create(None, 1, None, None, None, None) == rc.EINVAL
     lib.rcbf_destroy(None)
     lib.rcbf_batch_destroy(None)
 
