@@ -18,7 +18,7 @@
 
 namespace rcbf {
 
-struct BatchFrame {
+struct alignas(16) BatchFrame {
     DasArgs das;        // DAS of the frame (rf = its decoded buffer, image = its image)
     DecodeArgs dec;     // decode of the frame (valid when n_decode > 0)
     int n_decode;       // decode items of the frame (0: the frame is not encoded)
@@ -26,6 +26,9 @@ struct BatchFrame {
     int order;          // Hadamard order
     int out_dtype;      // RCBF_F16 or RCBF_F32
 };
+
+static_assert(sizeof(DasArgs) % 8 == 0, "DasArgs is copied in 8-byte words");
+static_assert(alignof(BatchFrame) >= 16 && sizeof(BatchFrame) % 16 == 0, "frame descriptors stay 16-byte aligned");
 
 enum : int { kItemDecode = 0, kItemDas = 1 };
 enum : int { kBatchTicket = 0, kBatchStatus = 1, kBatchDone = 2 };   // counter slots
@@ -113,9 +116,9 @@ batch_kernel(const int4* __restrict__ items, int n_items, const BatchFrame* __re
             if (s_ok) {
                 // the frame's DAS arguments, then order the acquired decode
                 // output before the TMA (async proxy) reads of it
-                const int4* src = reinterpret_cast<const int4*>(&fr.das);
-                int4* dst = reinterpret_cast<int4*>(s_args);
-                for (int q = threadIdx.x; q < (int)(sizeof(DasArgs) / 16); q += kDasThreads) dst[q] = src[q];
+                const long long* src = reinterpret_cast<const long long*>(&fr.das);
+                long long* dst = reinterpret_cast<long long*>(s_args);
+                for (int q = threadIdx.x; q < (int)(sizeof(DasArgs) / 8); q += kDasThreads) dst[q] = src[q];
                 asm volatile("fence.proxy.async.global;" ::: "memory");
                 __syncthreads();
                 const bool ok = das_unit<VU, WS, false, false>(*s_args, it.z, smem, pipe);
