@@ -3,14 +3,17 @@
 Workload: the FORCES full-aperture B-scan (128 Hadamard-encoded transmits x
 128 channels x 4096 int16 samples, 512 x 1024 image, 8.59e9 voxel-channel-
 transmit sums per frame), synthetic point-scatterer data. One step = one
-frame through the whole path: Hadamard decode (split-byte int8 tensor cores,
-FP16-stored output) and tiled DAS (FP32 accumulation).
+batch of B frames (default 4) through the whole path in one persistent
+launch replayed from a CUDA graph: Hadamard decode (split-byte int8 tensor
+cores, FP16-stored output) and tiled DAS (FP32 accumulation), voxel tile
+from the autotuner.
 
 Reported: value = whole-job DAS sums/s over the full step (decode included),
-frames/s, per-kernel CUDA-event times, the roofline of the dominant (DAS)
-kernel and of the decode, the plain FP32 form on the same GPU, an end-to-end
-figure through the C ABI with host buffers, clocks during the timed region,
-and the FP64 CPU oracle timed on a bounded sample (N = 1, rank 0).
+frames/s, the same form unbatched (per-kernel CUDA-event times), the plain
+FP32 form on the same GPU, the roofline of the dominant kernel and of the
+decode, an end-to-end figure through the C ABI with host buffers, clocks
+during the timed region, and the FP64 CPU oracle timed on a bounded sample
+(N = 1, rank 0).
 
 --impl reference times the FP64 CPU oracle itself (the reference arm) on a
 bounded sample of the same workload.
@@ -35,7 +38,6 @@ import numpy as np  # noqa: E402
 METRIC = "DAS G voxel·chan·tx sums/s & frames/s vs plain FP32 at <=1e-4 rel-L2"
 UNIT = "Gsums/s"
 WORKLOAD = "FORCES 2D full aperture: 128 tx (H128) x 128 ch x 4096 int16 samples -> 512x1024 FP32 image"
-RING = 3           # input frames rotated so no step finds its input in L2
 
 
 def _peaks():
@@ -183,11 +185,17 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--batch", type=int, default=4, help="frames per step (one persistent launch)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -208,19 +216,13 @@ def main():
         import torch.distributed as dist
         dist.barrier()
     import paper_2512_11086_gb300 as rc
+    from paper_2512_11086_gb300 import tune
     import synth
 
+    B = max(1, args.batch)
     frame = synth.full_bscan(seed=2)
     g = frame.geometry
     sums = g.sums
-    tuned = rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=rc.DECODE_MMA_I8,
-                                   das_variant=rc.DAS_TILED))
-    plain = rc.Plan(rc.make_params(g, decoded_dtype="f32", decode_variant=rc.DECODE_PLAIN,
-                                   das_variant=rc.DAS_PLAIN))
-    rf_host = torch.from_numpy(frame.rf)
-    rf = [rf_host.to(dev) for _ in range(RING)]
-    dec16 = [torch.empty(g.n_tx, g.n_ch, g.n_samples, dtype=torch.float16, device=dev) for _ in range(RING)]
-    img = torch.empty(tuned.image_shape, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -236,120 +238,164 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    # ---- tuned form: warm-up, then K timed steps with per-kernel events
-    for s in range(args.warmup):
-        tuned.das(tuned.decode(rf[s % RING], out=dec16[s % RING]), out=img)
+    # ---- the batched, precision-tuned form: B frames per step, split-byte int8
+    # tensor-core decode to FP16, tiled FP32 DAS, one persistent launch replayed
+    # from a CUDA graph; the voxel tile comes from the autotuner
+    tile = tune.tune_tile(g, "f16")
+    tuned = rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=rc.DECODE_MMA_I8,
+                                   das_variant=rc.DAS_TILED, tile=tile))
+    rf_host = torch.from_numpy(frame.rf)
+    rf = [rf_host.to(dev) for _ in range(B)]
+    dec16 = [torch.empty(g.n_tx, g.n_ch, g.n_samples, dtype=torch.float16, device=dev) for _ in range(B)]
+    imgs = [torch.empty(tuned.image_shape, dtype=torch.float32, device=dev) for _ in range(B)]
+    batch = rc.Batch([tuned] * B, rf, dec16, imgs)
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        batch.run(stream=side)
+    stream.wait_stream(side)
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.run()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    if batch.status() != rc.OK:
+        raise RuntimeError("batch status %d after warm-up" % batch.status())
+    ev = _events(args.steps + 1)
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
     torch.cuda.synchronize()
-    start.record(stream)
+    ev[0].record(stream)
     for s in range(args.steps):
-        b = s % RING
-        ev[s][0].record(stream)
-        tuned.decode(rf[b], out=dec16[b])
-        ev[s][1].record(stream)
-        tuned.das(dec16[b], out=img)
-        ev[s][2].record(stream)
-    end.record(stream)
+        graph.replay()
+        ev[s + 1].record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    total_ms = max_over_ranks(start.elapsed_time(end))
+    total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]))
     ms_step = total_ms / args.steps
-    t_dec = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
-    t_das = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
-    value = sums * args.steps * ws / (total_ms * 1e-3) / 1e9
+    t_batch = float(np.mean([ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]))
+    value = B * sums * args.steps * ws / (total_ms * 1e-3) / 1e9
+    if batch.status() != rc.OK:
+        raise RuntimeError("batch status %d after the timed steps" % batch.status())
 
-    # ---- plain FP32 form on the same GPU (same frame, same timing)
-    dec32 = torch.empty(g.n_tx, g.n_ch, g.n_samples, dtype=torch.float32, device=dev)
-    plain_steps = max(3, min(args.steps, 10))
+    # ---- the same form unbatched: decode and DAS launched per frame
+    ub_steps = max(3, min(args.steps, 10))
     for s in range(3):
-        plain.das(plain.decode(rf[s % RING], out=dec32), out=img)
+        tuned.das(tuned.decode(rf[s % B], out=dec16[s % B]), out=imgs[0])
     torch.cuda.synchronize()
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ue = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(ub_steps)]
+    for s in range(ub_steps):
+        ue[s][0].record(stream)
+        tuned.decode(rf[s % B], out=dec16[s % B])
+        ue[s][1].record(stream)
+        tuned.das(dec16[s % B], out=imgs[0])
+        ue[s][2].record(stream)
+    torch.cuda.synchronize()
+    t_dec = float(np.mean([e[0].elapsed_time(e[1]) for e in ue]))
+    t_das = float(np.mean([e[1].elapsed_time(e[2]) for e in ue]))
+
+    # ---- the exact byte-split FP16 tensor-core decode, same output
+    f16dec = rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=rc.DECODE_MMA_F16,
+                                    das_variant=rc.DAS_TILED, tile=tile))
+    for s in range(3):
+        f16dec.decode(rf[s % B], out=dec16[s % B])
+    q0, q1 = _events(2)
+    torch.cuda.synchronize()
+    q0.record(stream)
+    for s in range(ub_steps):
+        f16dec.decode(rf[s % B], out=dec16[s % B])
+    q1.record(stream)
+    torch.cuda.synchronize()
+    t_dec_f16 = q0.elapsed_time(q1) / ub_steps
+
+    # ---- plain FP32 form on the same GPU (same frames, same timing)
+    plain = rc.Plan(rc.make_params(g, decoded_dtype="f32", decode_variant=rc.DECODE_PLAIN,
+                                   das_variant=rc.DAS_PLAIN))
+    dec32 = torch.empty(g.n_tx, g.n_ch, g.n_samples, dtype=torch.float32, device=dev)
+    plain_steps = max(3, min(args.steps, 6))
+    for s in range(2):
+        plain.das(plain.decode(rf[s % B], out=dec32), out=imgs[0])
+    p0, p1 = _events(2)
+    torch.cuda.synchronize()
     p0.record(stream)
     for s in range(plain_steps):
-        plain.das(plain.decode(rf[s % RING], out=dec32), out=img)
+        plain.das(plain.decode(rf[s % B], out=dec32), out=imgs[0])
     p1.record(stream)
     torch.cuda.synchronize()
     plain_ms = max_over_ranks(p0.elapsed_time(p1)) / plain_steps
     plain_value = sums / (plain_ms * 1e-3) / 1e9
 
-    # ---- the exact byte-split FP16 tensor-core decode, same output, same frames
-    f16dec = rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=rc.DECODE_MMA_F16,
-                                    das_variant=rc.DAS_TILED))
-    for s in range(3):
-        f16dec.decode(rf[s % RING], out=dec16[s % RING])
-    torch.cuda.synchronize()
-    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    q0.record(stream)
-    for s in range(args.steps):
-        f16dec.decode(rf[s % RING], out=dec16[s % RING])
-    q1.record(stream)
-    torch.cuda.synchronize()
-    t_dec_f16 = q0.elapsed_time(q1) / args.steps
+    # ---- end to end through the C ABI with host buffers: every step copies
+    # the B encoded frames from pinned host memory, replays the batch and
+    # reads the B images back
+    pinned = [rf_host.pin_memory() for _ in range(B)]
+    img_host = [torch.empty(tuned.image_shape, dtype=torch.float32).pin_memory() for _ in range(B)]
 
-    # ---- end to end through the C ABI with host buffers (pinned), copies timed
-    pinned = [rf_host.pin_memory() for _ in range(RING)]
-    img_host = torch.empty(tuned.image_shape, dtype=torch.float32).pin_memory()
-    for s in range(3):
-        rf[0].copy_(pinned[s % RING], non_blocking=True)
-        tuned.das(tuned.decode(rf[0], out=dec16[0]), out=img)
-        img_host.copy_(img, non_blocking=True)
+    def e2e_step():
+        for b in range(B):
+            rf[b].copy_(pinned[b], non_blocking=True)
+        graph.replay()
+        for b in range(B):
+            img_host[b].copy_(imgs[b], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, e1 = _events(2)
     barrier()
     e0.record(stream)
-    for s in range(args.steps):
-        b = s % RING
-        rf[b].copy_(pinned[b], non_blocking=True)
-        tuned.das(tuned.decode(rf[b], out=dec16[b]), out=img)
-        img_host.copy_(img, non_blocking=True)
+    for _ in range(args.steps):
+        e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1)) / args.steps
-    e2e_value = sums * ws / (e2e_ms * 1e-3) / 1e9
+    e2e_value = B * sums * ws / (e2e_ms * 1e-3) / 1e9
 
-    info = tuned.info()
-    # ---- roofline: DAS (dominant) against the FP32 ALU peak; decode against HBM
+    # ---- roofline: the dominant kernel (the persistent batch kernel) against
+    # the FP32 ALU peak; the decode against HBM
     peaks = _peaks()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     ops_per_sum = 5   # add (A_i + B_j), floor, fraction, interpolation FMA, accumulate
     alu_peak = sms * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12   # FP32 lane-ops/s in T
-    das_achieved = ops_per_sum * sums / (t_das * 1e-3) / 1e12
+    achieved = ops_per_sum * B * sums / (t_batch * 1e-3) / 1e12
     dec_bytes = g.n_tx * g.n_ch * g.n_samples * (2 + 2)       # int16 in + FP16 out
-    dec_achieved = dec_bytes / (t_dec * 1e-3) / 1e9
+    info = tuned.info()
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "global_batch": ws, "decoded_storage": "f16",
-                   "decode": "split-byte int8 mma.sync (exact)", "das": "tiled, TMA windows, FP32",
-                   "l2": "inputs rotate over %d frames (%d MB int16 each, %d MB total > 129 MB L2)"
-                         % (RING, rf_host.numel() * 2 >> 20, RING * rf_host.numel() * 2 >> 20),
+        "config": {"workload": WORKLOAD, "frames_per_step": B, "global_batch": B * ws,
+                   "form": "batched persistent launch (CUDA graph): split-byte int8 mma.sync decode "
+                           "(exact) to FP16, tiled TMA-window DAS in FP32",
+                   "tile": list(tile),
+                   "l2": "inputs larger than L2: %d frames of %d MB int16 RF + %d MB FP16 decoded per step "
+                         "(129 MB L2)" % (B, rf_host.numel() * 2 >> 20, rf_host.numel() * 2 >> 20),
                    "parallelism": "independent frames per GPU" if ws > 1 else "1 GPU"},
-        "frames_per_s": 1e3 / ms_step * ws,
-        "kernel_ms": {"decode": t_dec, "das": t_das, "decode_f16_mma_alternative": t_dec_f16},
-        "das_only_gsums_per_s": sums / (t_das * 1e-3) / 1e9,
-        "plain_fp32": {"value": plain_value, "unit": UNIT, "ms_per_step": plain_ms,
-                       "speedup_of_tuned": value / plain_value},
-        "roofline": {"bound": "alu", "achieved": das_achieved, "peak": alu_peak, "unit": "TOP/s",
-                     "frac": das_achieved / alu_peak, "traffic": None,
-                     "kernel": "das_tiled_kernel", "peak_src": "%d SMs x 128 FP32 lanes x %.0f MHz"
-                     % (sms, peaks["sm_max_mhz"]), "ops_per_sum": ops_per_sum},
-        "roofline_decode": {"bound": "hbm", "achieved": dec_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                            "frac": dec_achieved / peaks["hbm_gbs"], "traffic": None,
-                            "kernel": "decode_mma_kernel", "peak_src": peaks["src"]},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(rf_host.numel() * 2),
-                "d2h_bytes_per_step": int(img_host.numel() * 4), "ms_per_step": e2e_ms},
-        "gpu_launches": (info["decode_launches"] + info["das_launches"]) * args.steps,
+        "frames_per_s": B * ws * 1e3 / ms_step,
+        "kernel_ms": {"batch_kernel_per_step": t_batch, "unbatched_decode": t_dec, "unbatched_das": t_das,
+                      "decode_f16_mma_alternative": t_dec_f16},
+        "unbatched": {"value": sums / ((t_dec + t_das) * 1e-3) / 1e9, "unit": UNIT,
+                      "das_only": sums / (t_das * 1e-3) / 1e9},
+        "plain_fp32": {"value": plain_value, "unit": UNIT, "ms_per_frame": plain_ms,
+                       "speedup_of_tuned": value / ws / plain_value},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TOP/s",
+                     "frac": achieved / alu_peak, "traffic": None, "kernel": "batch_kernel",
+                     "peak_src": "%d SMs x 128 FP32 lanes x %.0f MHz" % (sms, peaks["sm_max_mhz"]),
+                     "ops_per_sum": ops_per_sum},
+        "roofline_decode": {"bound": "hbm", "achieved": dec_bytes / (t_dec * 1e-3) / 1e9,
+                            "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": dec_bytes / (t_dec * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
+                            "kernel": "decode_mma_kernel (unbatched)", "peak_src": peaks["src"]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(B * rf_host.numel() * 2),
+                "d2h_bytes_per_step": int(B * img_host[0].numel() * 4), "ms_per_step": e2e_ms},
+        "gpu_launches": args.steps,
         "plan": info,
         "clocks": clk,
     }
