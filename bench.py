@@ -50,6 +50,29 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "src": "of fallback"}
 
 
+def recorded_traffic(kernel: str, frames_per_launch: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, only
+    while the kernel's sources still hash to the value recorded with it."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    for line in lines:
+        if not line.startswith("TRAFFIC %s " % kernel):
+            continue
+        fields = dict(f.split("=", 1) for f in line.split()[2:])
+        if int(fields.get("frames_per_launch", -1)) != frames_per_launch:
+            return None
+        h = hashlib.sha1()
+        for f in fields["files"].split(","):
+            with open(os.path.join(ROOT, "paper_2512_11086_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+        return int(fields["bytes_per_launch"]) if h.hexdigest()[:16] == fields["sources"] else None
+    return None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -386,7 +409,8 @@ def main():
         "plain_fp32": {"value": plain_value, "unit": UNIT, "ms_per_frame": plain_ms,
                        "speedup_of_tuned": value / ws / plain_value},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TOP/s",
-                     "frac": achieved / alu_peak, "traffic": None, "kernel": "batch_kernel",
+                     "frac": achieved / alu_peak, "traffic": recorded_traffic("batch_kernel", B),
+                     "kernel": "batch_kernel",
                      "peak_src": "%d SMs x 128 FP32 lanes x %.0f MHz" % (sms, peaks["sm_max_mhz"]),
                      "ops_per_sum": ops_per_sum},
         "roofline_decode": {"bound": "hbm", "achieved": dec_bytes / (t_dec * 1e-3) / 1e9,
