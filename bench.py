@@ -117,6 +117,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def aggregate(local_ms: float, local_units: float, device=None):
+    """Whole-job figures of a weak-scaling run: the slowest rank's time and
+    the units all ranks processed (each rank beamforms its own frames; the
+    only collective is this bookkeeping, never the data path)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return local_ms, local_units
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([local_units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
@@ -298,10 +313,10 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    total_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]))
+    total_ms, job_sums = aggregate(ev[0].elapsed_time(ev[-1]), float(B * sums * args.steps), device=dev)
     ms_step = total_ms / args.steps
     t_batch = float(np.mean([ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]))
-    value = B * sums * args.steps * ws / (total_ms * 1e-3) / 1e9
+    value = job_sums / (total_ms * 1e-3) / 1e9
     if batch.status() != rc.OK:
         raise RuntimeError("batch status %d after the timed steps" % batch.status())
 
