@@ -223,6 +223,97 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+OTHER_WORKLOADS = {
+    "volume": "HERCULES volume: 128 tx x 128 ch x 2048 int16 samples -> 128x128x256 FP32 voxels",
+    "stream": "realtime stream: 64 frames of uneven size (32/64/128 tx, 2048-4096 samples, 256x512 to "
+              "512x1024 grids, 16 cross-plane pairs) in one persistent launch",
+    "autofocus": "differentiable DAS: complex 128 tx x 128 ch x 2048 decoded RF -> 256x512 image, "
+                 "forward + adjoint (dRF, dc, dw) per step",
+}
+
+
+def run_other_workload(args):
+    """The volume, stream and autofocus configurations, timed like the
+    headline (CUDA events, warm-up, clocks) but reported on their own line."""
+    import torch
+    import paper_2512_11086_gb300 as rc
+    from paper_2512_11086_gb300 import build as rbuild, tune
+    import synth
+    rbuild.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    extra = {}
+    if args.workload in ("volume", "stream"):
+        if args.workload == "volume":
+            fr = synth.hercules_volume(3)
+            frames = [fr] * max(1, args.batch)
+            tiles = [tune.tune_tile(fr.geometry, "f16")] * len(frames)
+            extra["frames_per_step"] = len(frames)
+        else:
+            geos = synth.stream_geometries()
+            cache = {}
+            frames = []
+            for g, seed, box in geos:
+                key = (g.n_tx, g.n_samples, g.out_dims, g.tx_orientation)
+                if key not in cache:                      # one synthetic content per frame class
+                    cache[key] = synth.make_frame(g, seed, 16, **box)
+                frames.append(cache[key])
+            tiles = tune.tune_stream([f.geometry for f in frames], "f16")
+            extra["frames_per_step"] = len(frames)
+            extra["content"] = "frames of one class share synthetic content (distinct buffers)"
+        plans, rf, dec, img = [], [], [], []
+        for fr, t in zip(frames, tiles):
+            g = fr.geometry
+            plans.append(rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=rc.DECODE_MMA_I8, tile=t)))
+            rf.append(torch.from_numpy(fr.rf).to(dev))
+            dec.append(torch.empty(g.n_tx, g.n_ch, g.n_samples, dtype=torch.float16, device=dev))
+            img.append(torch.empty(g.out_dims[2], g.out_dims[1], g.out_dims[0], device=dev))
+        batch = rc.Batch(plans, rf, dec, img)
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            batch.run(stream=side)
+        stream.wait_stream(side)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            batch.run()
+        step = graph.replay
+        sums = sum(f.geometry.sums for f in frames)
+        extra["tiles"] = sorted({tuple(t) for t in tiles})
+    else:
+        fr = synth.autofocus(5)
+        g = fr.geometry
+        plan = rc.Plan(rc.make_params(g, decoded_dtype="cf32", tile=tune.tune_tile(g, "f32")))
+        d = torch.from_numpy(np.stack([fr.decoded.real, fr.decoded.imag]).astype(np.float32)).to(dev)
+        w = torch.ones(g.n_ch, device=dev)
+        out = torch.empty((2,) + plan.image_shape, device=dev)
+
+        def step():
+            im = plan.das(d, apod=w, c=1540.0, out=out)
+            plan.das_backward(d, -2.0 * im, apod=w, c=1540.0)
+        sums = g.sums
+        extra["sums"] = "complex voxel x channel x transmit sums (two real planes each)"
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = _events(2)
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    line = {"metric": METRIC, "value": sums / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict({"workload": OTHER_WORKLOADS[args.workload]}, **extra), "clocks": clk}
+    print(json.dumps(line))
+
+
 def _events(n):
     import torch
     return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
@@ -236,11 +327,16 @@ def main():
     ap.add_argument("--batch", type=int, default=4, help="frames per step (one persistent launch)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="bscan", choices=["bscan"] + sorted(OTHER_WORKLOADS),
+                    help="bscan (the headline) or another configuration on its own line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "bscan":
+        run_other_workload(args)
         return
 
     import torch
