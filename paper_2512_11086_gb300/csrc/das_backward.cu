@@ -16,6 +16,15 @@
 // shared atomics and the window is then added into dL/dr with global atomics
 // (windows of neighbouring tiles overlap). Delays are recomputed per tile,
 // never stored. The plain form is one thread per voxel with global atomics.
+//
+// The window accumulators are 32-bit fixed point. Shared-memory float atomics
+// retry per conflicting lane, and neighbouring voxels along the lane axis
+// often hit the same sample; integer atomics do not retry, and integer sums do
+// not depend on order. Per channel chunk the scale is 2^e with
+// 1024 * B * 2^e < 2^30, B = max|w_j| over the chunk times max|G| over the tile
+// (an upper bound of |a_j G|): a cell collects at most one term per voxel of
+// the 1024-voxel tile, so it cannot overflow, and a term is rounded to
+// 2^-e <= 2^-19 * B (a relative 2e-6 of the largest possible term).
 #include <algorithm>
 
 #include "das_tile.cuh"
@@ -49,7 +58,8 @@ struct BwdCfg {
     static constexpr int OFF_WIN = OFF_ALPHA + kBwdCI * ROWS * 4;      // int S0[2][NWIN], int off[2][NWIN]
     static constexpr int OFF_GW = OFF_WIN + 4 * NWIN * 4;              // float[kMaxChannels]
     static constexpr int OFF_RED = OFF_GW + kMaxChannels * 4;          // float[8]
-    static constexpr int OFF_BAR = OFF_RED + 32;                       // uint64[2]
+    static constexpr int OFF_MAX = OFF_RED + 32;                       // float[8]: per-warp max|G|
+    static constexpr int OFF_BAR = OFF_MAX + 32;                       // uint64[2]
     static constexpr int SMEM = OFF_BAR + 16;
     static_assert(OFF_RAW % 128 == 0 && OFF_GRAD % 16 == 0 && OFF_TX % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
 };
@@ -67,7 +77,8 @@ das_bwd_kernel(DasArgs a) {
     int* s_off = s_S0 + 2 * C::NWIN;
     float* s_gw = reinterpret_cast<float*>(smem + C::OFF_GW);
     float* s_red = reinterpret_cast<float*>(smem + C::OFF_RED);
-    float* gwin = reinterpret_cast<float*>(smem + C::OFF_GRAD);
+    int* gwin = reinterpret_cast<int*>(smem + C::OFF_GRAD);
+    float* s_max = reinterpret_cast<float*>(smem + C::OFF_MAX);
     unsigned char* raw = smem + C::OFF_RAW;
     const uint32_t bar0 = smem_u32(smem + C::OFF_BAR);
     const uint32_t pairs_u32 = smem_u32(smem + C::OFF_PAIRS);
@@ -77,7 +88,7 @@ das_bwd_kernel(DasArgs a) {
         mbar_init(bar0 + 8, C::COPIES);
         fence_mbar_init();
     }
-    for (int q = tid; q < C::NWIN * C::GW * C::PLANES; q += kDasThreads) gwin[q] = 0.f;
+    for (int q = tid; q < C::NWIN * C::GW * C::PLANES; q += kDasThreads) gwin[q] = 0;
     for (int q = tid; q < kMaxChannels; q += kDasThreads) s_gw[q] = 0.f;
 
     // ---- unit -> (tile, channel split)
@@ -135,7 +146,15 @@ das_bwd_kernel(DasArgs a) {
         g_re[k] = in ? a.grad_image[o] : 0.f;        // voxels outside the image carry no gradient
         g_im[k] = (in && CPLX) ? a.grad_image[a.image_plane + o] : 0.f;
     }
+    float g_max = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) g_max = fmaxf(g_max, fmaxf(fabsf(g_re[k]), fabsf(g_im[k])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) g_max = fmaxf(g_max, __shfl_xor_sync(0xffffffffu, g_max, o));
+    if (lane == 0) s_max[warp] = g_max;
     __syncthreads();
+#pragma unroll
+    for (int w = 0; w < kDasThreads / 32; ++w) g_max = fmaxf(g_max, s_max[w]);
 
     const int es = 4;
     auto issue = [&](int s) {
@@ -175,11 +194,13 @@ das_bwd_kernel(DasArgs a) {
     float gc = 0.f;
     bool ok = true;
     uint32_t phase = 0;
+    float scale = 1.f, inv_scale = 1.f;     // fixed-point scale of the window accumulators
 
     for (int s = 0; s < NS; ++s) {
         const int ic = s % n_ic, jc = jc0 + s / n_ic;
         const int b = s & 1;
         if (ic == 0) {
+            float wmax = 0.f;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const float Zv = Zf + dz[k];
@@ -194,12 +215,19 @@ das_bwd_kernel(DasArgs a) {
                     beta[k][jj] = fminf(fmaxf(bt, rx.z - a.reach_b), rx.z + a.reach_b);
                     const float W = a.f_number > 0.f ? hann_weight(a.f_number, Lv, Zv) : 1.0f;
                     const float wj = a.apod ? __ldg(a.apod + j) : 1.0f;
+                    wmax = fmaxf(wmax, fabsf(wj));
                     win_w[k][jj] = W;
                     ag[k][jj] = wj * W * g_re[k];
                     agi[k][jj] = wj * W * g_im[k];
                     pj[k][jj] = 0.f;
                 }
             }
+            // |a_j G| <= max|w_j| * max|G| (the window weight is at most 1)
+            int ex = 0;
+            frexpf(wmax * g_max, &ex);          // the bound is < 2^ex
+            const int e = min(max(20 - ex, -120), 120);
+            scale = ldexpf(1.0f, e);
+            inv_scale = ldexpf(1.0f, -e);
         }
         // ---- wait for this stage's windows and rewrite them as line pieces
         ok = mbar_wait_parity(bar0 + 8 * b, (phase >> b) & 1u) && ok;
@@ -231,14 +259,14 @@ das_bwd_kernel(DasArgs a) {
 
         // ---- transposed interpolation into the window accumulators
         const uint32_t pbase = pairs_u32 - (0x4B000000u << SHIFT);
-#pragma unroll
+#pragma unroll 1
         for (int ii = 0; ii < kBwdCI; ++ii) {
 #pragma unroll
             for (int jj = 0; jj < kBwdCJ; ++jj) {
                 const int win = ii * kBwdCJ + jj;
                 // absolute sample position of u is S0 + u + 0.5 + H; add t0 fs
                 const float cwin = (float)s_S0[b * C::NWIN + win] + hp + (float)a.t0fs;
-                float* gw0 = gwin + win * C::GW;
+                int* gw0 = gwin + win * C::GW;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int kr = k / VU;
@@ -259,15 +287,17 @@ das_bwd_kernel(DasArgs a) {
                         cr = p.x; sr = p.y;
                     }
                     const float gr = ag[k][jj];
-                    atomicAdd(gw0 + n, gr * (1.0f - f));
-                    atomicAdd(gw0 + n + 1, gr * f);
+                    const float gs = gr * scale;
+                    atomicAdd(gw0 + n, __float2int_rn(gs - gs * f));
+                    atomicAdd(gw0 + n + 1, __float2int_rn(gs * f));
                     float dsum = gr * sr;
                     pj[k][jj] += g_re[k] * fmaf(u, sr, cr);
                     if (CPLX) {
                         const float gi = agi[k][jj];
-                        float* gw1 = gw0 + C::NWIN * C::GW;
-                        atomicAdd(gw1 + n, gi * (1.0f - f));
-                        atomicAdd(gw1 + n + 1, gi * f);
+                        const float gis = gi * scale;
+                        int* gw1 = gw0 + C::NWIN * C::GW;
+                        atomicAdd(gw1 + n, __float2int_rn(gis - gis * f));
+                        atomicAdd(gw1 + n + 1, __float2int_rn(gis * f));
                         dsum = fmaf(gi, si, dsum);
                         pj[k][jj] += g_im[k] * fmaf(u, si, ci);
                     }
@@ -294,10 +324,11 @@ das_bwd_kernel(DasArgs a) {
             const int wp = q / (kBwdWS + 1);
             const int win = wp % C::NWIN, plane = wp / C::NWIN;
             if (n > a.W) continue;
-            float* cell = gwin + (plane * C::NWIN + win) * C::GW + n;
-            const float v = *cell;
-            if (v == 0.f) continue;
-            *cell = 0.f;
+            int* cell = gwin + (plane * C::NWIN + win) * C::GW + n;
+            const int acc = *cell;
+            if (acc == 0) continue;
+            *cell = 0;
+            const float v = (float)acc * inv_scale;
             const int S = s_S0[b * C::NWIN + win] + n;
             if (S < 0 || S >= a.n_s) continue;
             const int ii = win / kBwdCJ, jj = win % kBwdCJ;
