@@ -166,6 +166,9 @@ typedef struct rcbf_plan_info {
     uint32_t das_launches;     /* kernels one rcbf_das call enqueues at params.c */
     uint32_t decode_launches;  /* kernels one rcbf_decode call enqueues (0 without Hadamard order) */
     uint64_t workspace_bytes;  /* device memory the plan owns */
+    uint32_t bwd_tile[3];      /* voxel tile rcbf_das_backward uses at params.c */
+    uint32_t bwd_mode;         /* rcbf_das_backward at params.c: 0 plain form, 1 tiled with lanes along the
+                                  tile's u axis, 2 tiled with lanes over z (tile 32 x bv x bw, bv * bw = 32) */
 } rcbf_plan_info;
 
 /* rcbf_plan_query — describe a plan (host only, no CUDA call).
@@ -218,8 +221,13 @@ int rcbf_das(rcbf_plan_t plan, const void* decoded, const float* apod, float c,
  *   grad_rf    device float32 RF-shaped, overwritten; NULL = not computed
  *   grad_c     device float32 scalar, overwritten; NULL = not computed
  *   grad_apod  device float32 [n_ch], overwritten; NULL = not computed
- * Delays are recomputed per voxel tile, never stored. Sums use float atomics,
- * so their order (and the last bits) vary between runs.
+ * Delays are recomputed per voxel tile, never stored. The tiled form sums a
+ * tile's terms per (transmit, channel) window in 32-bit fixed point (scale
+ * 2^e chosen so a window cannot overflow; a term is rounded to about 2e-6 of
+ * max|w| max|G|) and adds windows into grad_rf, grad_c and grad_apod with
+ * float atomics, so the order of those sums (and their last bits) varies
+ * between runs. A 16-byte aligned grad_rf takes four-float reductions; any
+ * 4-byte aligned one is accepted. rcbf_plan_query reports the tile used.
  * Errors: RCBF_EINVAL, RCBF_EUNSUPPORTED (dtype), RCBF_ECUDA. */
 int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, float c,
                       const float* grad_image, float* grad_rf, float* grad_c,

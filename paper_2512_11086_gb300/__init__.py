@@ -63,6 +63,7 @@ class PlanInfo(ctypes.Structure):
         ("tile", ctypes.c_uint32 * 3), ("tiled", ctypes.c_uint32), ("window", ctypes.c_uint32),
         ("n_split", ctypes.c_uint32), ("das_launches", ctypes.c_uint32),
         ("decode_launches", ctypes.c_uint32), ("workspace_bytes", ctypes.c_uint64),
+        ("bwd_tile", ctypes.c_uint32 * 3), ("bwd_mode", ctypes.c_uint32),
     ]
 
 
@@ -198,7 +199,8 @@ class Plan:
         _check(load_library().rcbf_plan_query(self.handle, ctypes.byref(pi)))
         return {"tile": tuple(pi.tile), "tiled": bool(pi.tiled), "window": pi.window,
                 "n_split": pi.n_split, "das_launches": pi.das_launches,
-                "decode_launches": pi.decode_launches, "workspace_bytes": pi.workspace_bytes}
+                "decode_launches": pi.decode_launches, "workspace_bytes": pi.workspace_bytes,
+                "bwd_tile": tuple(pi.bwd_tile), "bwd_mode": pi.bwd_mode}
 
     def decoded_torch_dtype(self):
         import torch
@@ -226,11 +228,17 @@ class Plan:
         return out
 
     def das_backward(self, decoded, grad_image, apod=None, c: float = 0.0, want_rf=True,
-                     want_c=True, want_apod=True, stream=None):
-        """rcbf_das_backward: (grad_rf, grad_c, grad_apod) for dL/dimage."""
+                     want_c=True, want_apod=True, stream=None, out_rf=None):
+        """rcbf_das_backward: (grad_rf, grad_c, grad_apod) for dL/dimage
+        (grad_rf written into ``out_rf`` when given: float32, decoded's shape)."""
         import torch
         dev = decoded.device
-        grad_rf = torch.empty_like(decoded, dtype=torch.float32) if want_rf else None
+        if out_rf is not None:
+            if out_rf.dtype != torch.float32 or tuple(out_rf.shape) != tuple(decoded.shape) or not out_rf.is_contiguous():
+                raise ValueError("out_rf must be a contiguous float32 tensor of decoded's shape")
+            grad_rf = out_rf
+        else:
+            grad_rf = torch.empty_like(decoded, dtype=torch.float32) if want_rf else None
         grad_c = torch.empty((), dtype=torch.float32, device=dev) if want_c else None
         grad_apod = torch.empty(self.params.n_ch, dtype=torch.float32, device=dev) if want_apod else None
         _check(load_library().rcbf_das_backward(self.handle, _ptr(decoded), _ptr(apod), ctypes.c_float(c),

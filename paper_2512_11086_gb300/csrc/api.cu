@@ -270,6 +270,24 @@ void setup_geometry(PlanHost& h) {
     h.r_alpha_m = tile_radius(G, tx_axis, ua, va, a.bu, a.bv, a.bw);
     h.r_beta_m = tile_radius(G, rx_axis, ua, va, a.bu, a.bv, a.bw);
 
+    // adjoint tile: 32 voxels along u by 32 rows, lanes over the rows with z
+    // fastest; the most z-rows whose window stays within 128 samples
+    h.bwd_bv = h.bwd_bw = 0;
+    h.bwd_r_alpha_m = h.bwd_r_beta_m = 0.0;
+    for (int bv = 1; bv <= 4; bv *= 2) {
+        const int bw = 32 / bv;
+        if (bv > 1 && a.n_v == 1) break;
+        const double ra = tile_radius(G, tx_axis, ua, va, 32, bv, bw);
+        const double rb = tile_radius(G, rx_axis, ua, va, 32, bv, bw);
+        if (std::floor(4.0 + 2.0 * (ra + rb) * p.fs / p.c + 0.01) + 1.0 <= 128.0) {
+            h.bwd_bv = bv;
+            h.bwd_bw = bw;
+            h.bwd_r_alpha_m = ra;
+            h.bwd_r_beta_m = rb;
+            break;
+        }
+    }
+
 }
 
 }  // namespace
@@ -379,6 +397,19 @@ int rcbf_plan_query(rcbf_plan_t plan, rcbf_plan_info* info) {
         if (n % 32 == 0) bytes += 2 * (n / 16) * (n / 32) * 32 * 16 + (n / 16) * (n / 16) * 32 * 16 / 2;
     }
     info->workspace_bytes = bytes;
+    int mode = 0;
+    DasArgs b = a;
+    if (h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok) {
+        if (h.bwd_bv > 0 && das_prepare_tile(h, h.p.c, 32, h.bwd_bv, h.bwd_bw, h.bwd_r_alpha_m, h.bwd_r_beta_m, &b,
+                                             &why) == RCBF_OK)
+            mode = 2;
+        else if (fits)
+            mode = 1;
+    }
+    info->bwd_mode = (uint32_t)mode;
+    info->bwd_tile[0] = mode == 2 ? 32u : (uint32_t)h.das.bu;
+    info->bwd_tile[1] = mode == 2 ? (uint32_t)h.bwd_bv : (uint32_t)h.das.bv;
+    info->bwd_tile[2] = mode == 2 ? (uint32_t)h.bwd_bw : (uint32_t)h.das.bw;
     return RCBF_OK;
 }
 
@@ -439,8 +470,17 @@ int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, 
     const double cc = c > 0.f ? (double)c : h.p.c;
     DasArgs a;
     std::string why;
-    const bool fits = das_prepare(h, cc, &a, &why) == RCBF_OK;
-    const bool tiled = h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok && fits;
+    // the adjoint's own tile (lanes over z) where its window fits at this
+    // speed of sound, else the plan's tile, else the plain form
+    int mode = 0;
+    if (h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok) {
+        if (h.bwd_bv > 0 && das_prepare_tile(h, cc, 32, h.bwd_bv, h.bwd_bw, h.bwd_r_alpha_m, h.bwd_r_beta_m, &a,
+                                             &why) == RCBF_OK)
+            mode = 2;
+        else if (das_prepare(h, cc, &a, &why) == RCBF_OK)
+            mode = 1;
+    }
+    if (mode == 0) das_prepare(h, cc, &a, &why);
     a.rf = decoded;
     a.apod = apod;
     a.grad_image = grad_image;
@@ -455,7 +495,7 @@ int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, 
         return check_launch("rcbf_das_backward: clear grad_c");
     if (grad_apod && cudaMemsetAsync(grad_apod, 0, (size_t)h.p.n_ch * sizeof(float), s) != cudaSuccess)
         return check_launch("rcbf_das_backward: clear grad_apod");
-    return launch_das_backward(h, a, tiled, s);
+    return launch_das_backward(h, a, mode, s);
 }
 
 

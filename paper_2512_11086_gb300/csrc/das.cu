@@ -110,11 +110,22 @@ int launch_das_plain(const PlanHost& h, const DasArgs& a, cudaStream_t s) {
 // [K_i + K_j + lo, K_i + K_j + lo + W]: alpha, beta lie within R_a, R_b of
 // their references and the references' fractional parts are in [0, 1).
 int das_prepare(const PlanHost& h, double c, DasArgs* a, std::string* why) {
+    return das_prepare_tile(h, c, h.das.bu, h.das.bv, h.das.bw, h.r_alpha_m, h.r_beta_m, a, why);
+}
+
+int das_prepare_tile(const PlanHost& h, double c, int bu, int bv, int bw, double r_alpha_m, double r_beta_m,
+                     DasArgs* a, std::string* why) {
     *a = h.das;
+    a->bu = bu;
+    a->bv = bv;
+    a->bw = bw;
+    a->tiles_u = (a->n_u + bu - 1) / bu;
+    a->tiles_v = (a->n_v + bv - 1) / bv;
+    a->tiles_w = (a->n_w + bw - 1) / bw;
     a->c = c;
     a->fs_over_c = h.p.fs / c;
     a->t0fs = h.p.t0 * h.p.fs;
-    const double R = (h.r_alpha_m + h.r_beta_m) * a->fs_over_c;
+    const double R = (r_alpha_m + r_beta_m) * a->fs_over_c;
     a->lo = (int)std::floor(-R) - 1;
     a->W = (int)std::floor(4.0 + 2.0 * R + 0.01) + 1;
     a->H = a->W / 2;
@@ -122,8 +133,8 @@ int das_prepare(const PlanHost& h, double c, DasArgs* a, std::string* why) {
     // alpha and beta are clamped to reference +- reach in the kernel; the
     // 0.004-sample slack per side stays inside the 0.01 slack of W, so every
     // interval index lands in [0, W-1] whatever the input (NaN included)
-    a->reach_a = (float)(h.r_alpha_m * a->fs_over_c + 0.004);
-    a->reach_b = (float)(h.r_beta_m * a->fs_over_c + 0.004);
+    a->reach_a = (float)(r_alpha_m * a->fs_over_c + 0.004);
+    a->reach_b = (float)(r_beta_m * a->fs_over_c + 0.004);
     if (a->W > 128) {
         if (why) *why = "das: the voxel tile spans more than 128 samples at this speed of sound; choose a smaller tile";
         return RCBF_EUNSUPPORTED;

@@ -37,6 +37,11 @@ constexpr int kBwdCI = 4;          // transmits per backward stage
 constexpr int kBwdCJ = 4;          // channels per backward stage
 constexpr int kBwdWS = 128;        // window intervals (every W <= 128)
 
+// ZL: lanes on tile rows (the z-major row index), each thread four
+// consecutive voxels along u. Along z the delay grows by a sizeable fraction
+// of a sample per voxel, so the 32 lanes of a warp rarely meet on one sample
+// and the shared atomics rarely serialise; with lanes along u (ZL false) the
+// lanes near a receive element's axis share a sample.
 template <int VU, bool CPLX>
 struct BwdCfg {
     static constexpr int VR = 4 / VU;
@@ -64,10 +69,16 @@ struct BwdCfg {
     static_assert(OFF_RAW % 128 == 0 && OFF_GRAD % 16 == 0 && OFF_TX % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
 };
 
-template <int VU, bool CPLX>
+// FN: receive F# window active (a per-voxel weight W_j(v)); VEC_RED: dL/dr
+// is 16-byte aligned, so window cells go out as four-float reductions.
+template <int VU, bool CPLX, bool ZL, bool FN, bool VEC_RED>
 __global__ void __launch_bounds__(kDasThreads, 2)
 das_bwd_kernel(DasArgs a) {
     using C = BwdCfg<VU, CPLX>;
+    static_assert(!ZL || VU == 1, "lanes on rows need 32 rows of 32 voxels");
+    // tile row -> (v, w): z-fastest when lanes run over rows
+    auto row_v = [&](int row) { return ZL ? row / a.bw : row % a.bv; };
+    auto row_w = [&](int row) { return ZL ? row % a.bw : row / a.bv; };
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float4* s_tx = reinterpret_cast<float4*>(smem + C::OFF_TX);
@@ -131,16 +142,16 @@ das_bwd_kernel(DasArgs a) {
     float dlr[4], dz[4], g_re[4], g_im[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const int ku = k % VU, kr = k / VU;
-        const int row = warp * C::VR + kr;
-        const int rv = row % a.bv, rw = row / a.bv;
-        const float du = (float)(lane + 32 * ku) - 0.5f * (C::BU - 1);
+        const int uu = ZL ? 4 * warp + k : lane + 32 * (k % VU);
+        const int row = ZL ? lane : warp * C::VR + k / VU;
+        const int rv = row_v(row), rw = row_w(row);
+        const float du = (float)uu - 0.5f * (C::BU - 1);
         const float dv = (float)rv - 0.5f * (a.bv - 1);
         const float dw = (float)rw - 0.5f * (a.bw - 1);
         dlr[k] = (float)(a.rx_axis ? a.Gu[1] : a.Gu[0]) * du + (float)(a.rx_axis ? a.Gv[1] : a.Gv[0]) * dv +
                  (float)(a.rx_axis ? a.Gw[1] : a.Gw[0]) * dw;
         dz[k] = (float)a.Gu[2] * du + (float)a.Gv[2] * dv + (float)a.Gw[2] * dw;
-        const int iu = u0 + lane + 32 * ku, iv = v0 + rv, iw = w0 + rw;
+        const int iu = u0 + uu, iv = v0 + rv, iw = w0 + rw;
         const bool in = iu < a.n_u && iv < a.n_v && iw < a.n_w;
         const long long o = (long long)iw * a.out_sw + (long long)iv * a.out_sv + (long long)iu * a.out_su;
         g_re[k] = in ? a.grad_image[o] : 0.f;        // voxels outside the image carry no gradient
@@ -190,11 +201,13 @@ das_bwd_kernel(DasArgs a) {
     const float magic = 8388608.0f + (float)a.H;
     const float hp = 0.5f + (float)a.H;
     constexpr int SHIFT = CPLX ? 4 : 3;
-    float beta[4][kBwdCJ], ag[4][kBwdCJ], agi[4][kBwdCJ], win_w[4][kBwdCJ], pj[4][kBwdCJ];
+    // per channel of the chunk: w_j and w_j * scale; per (voxel, channel): beta
+    // and (F# window) W_j(v); dL/dw_j and dL/dc partials per channel
+    float beta[4][kBwdCJ], win_w[FN ? 4 : 1][kBwdCJ], wj[kBwdCJ], ws[kBwdCJ], pj[kBwdCJ], gcj[kBwdCJ];
     float gc = 0.f;
     bool ok = true;
     uint32_t phase = 0;
-    float scale = 1.f, inv_scale = 1.f;     // fixed-point scale of the window accumulators
+    float inv_scale = 1.f;                  // fixed-point scale of the window accumulators
 
     for (int s = 0; s < NS; ++s) {
         const int ic = s % n_ic, jc = jc0 + s / n_ic;
@@ -202,32 +215,34 @@ das_bwd_kernel(DasArgs a) {
         if (ic == 0) {
             float wmax = 0.f;
 #pragma unroll
+            for (int jj = 0; jj < kBwdCJ; ++jj) {
+                wj[jj] = a.apod ? __ldg(a.apod + jc * kBwdCJ + jj) : 1.0f;
+                wmax = fmaxf(wmax, fabsf(wj[jj]));
+                pj[jj] = 0.f;
+                gcj[jj] = 0.f;
+            }
+#pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const float Zv = Zf + dz[k];
 #pragma unroll
                 for (int jj = 0; jj < kBwdCJ; ++jj) {
-                    const int j = jc * kBwdCJ + jj;
-                    const float4 rx = s_rx[j];
+                    const float4 rx = s_rx[jc * kBwdCJ + jj];
                     const float Lv = rx.x + dlr[k];
                     const float d = sqrtf(Lv * Lv + Zv * Zv);
                     const float num = dlr[k] * (2.0f * rx.x + dlr[k]) + dz[k] * (2.0f * Zf + dz[k]);
                     const float bt = rx.z + __fdividef(num, d + rx.y) * fsc;
                     beta[k][jj] = fminf(fmaxf(bt, rx.z - a.reach_b), rx.z + a.reach_b);
-                    const float W = a.f_number > 0.f ? hann_weight(a.f_number, Lv, Zv) : 1.0f;
-                    const float wj = a.apod ? __ldg(a.apod + j) : 1.0f;
-                    wmax = fmaxf(wmax, fabsf(wj));
-                    win_w[k][jj] = W;
-                    ag[k][jj] = wj * W * g_re[k];
-                    agi[k][jj] = wj * W * g_im[k];
-                    pj[k][jj] = 0.f;
+                    if (FN) win_w[FN ? k : 0][jj] = hann_weight(a.f_number, Lv, Zv);
                 }
             }
             // |a_j G| <= max|w_j| * max|G| (the window weight is at most 1)
             int ex = 0;
             frexpf(wmax * g_max, &ex);          // the bound is < 2^ex
             const int e = min(max(20 - ex, -120), 120);
-            scale = ldexpf(1.0f, e);
+            const float scale = ldexpf(1.0f, e);
             inv_scale = ldexpf(1.0f, -e);
+#pragma unroll
+            for (int jj = 0; jj < kBwdCJ; ++jj) ws[jj] = wj[jj] * scale;
         }
         // ---- wait for this stage's windows and rewrite them as line pieces
         ok = mbar_wait_parity(bar0 + 8 * b, (phase >> b) & 1u) && ok;
@@ -240,8 +255,8 @@ das_bwd_kernel(DasArgs a) {
         }
         if (tid < kBwdCI * C::ROWS) {
             const int ii = tid / C::ROWS, row = tid % C::ROWS;
-            const float dv = (float)(row % a.bv) - 0.5f * (a.bv - 1);
-            const float dw = (float)(row / a.bv) - 0.5f * (a.bw - 1);
+            const float dv = (float)row_v(row) - 0.5f * (a.bv - 1);
+            const float dw = (float)row_w(row) - 0.5f * (a.bw - 1);
             const float dL = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]) * dv + (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]) * dw;
             const float dzz = (float)a.Gv[2] * dv + (float)a.Gw[2] * dw;
             const float4 tx = s_tx[ic * kBwdCI + ii];
@@ -259,8 +274,13 @@ das_bwd_kernel(DasArgs a) {
 
         // ---- transposed interpolation into the window accumulators
         const uint32_t pbase = pairs_u32 - (0x4B000000u << SHIFT);
+        // x + 1.5 * 2^23 holds round(x) in its low mantissa bits for |x| < 2^22
+        // (every fixed-point term is below 2^20 in magnitude)
+        constexpr float kQ = 12582912.0f;
+        constexpr uint32_t kQbits = 0x4B400000u;
 #pragma unroll 1
         for (int ii = 0; ii < kBwdCI; ++ii) {
+            const float al_row = ZL ? s_alpha[ii * C::ROWS + lane] : 0.f;
 #pragma unroll
             for (int jj = 0; jj < kBwdCJ; ++jj) {
                 const int win = ii * kBwdCJ + jj;
@@ -269,12 +289,12 @@ das_bwd_kernel(DasArgs a) {
                 int* gw0 = gwin + win * C::GW;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const int kr = k / VU;
-                    const float u = s_alpha[ii * C::ROWS + warp * C::VR + kr] + beta[k][jj];
+                    const float al = ZL ? al_row : s_alpha[ii * C::ROWS + warp * C::VR + k / VU];
+                    const float u = al + beta[k][jj];
                     const float t = u + magic;
                     const int n = (int)(__float_as_uint(t) - 0x4B000000u);
                     const uint32_t addr = (__float_as_uint(t) << SHIFT) + pbase + win * kBwdWS * C::PAIR_BYTES;
-                    const float f = u + hp - (float)n;          // fraction within interval n
+                    const float f = (u + hp) - (t - 8388608.0f);       // fraction within interval n
                     float cr, sr, ci = 0.f, si = 0.f;
                     if (CPLX) {
                         float4 p;
@@ -286,55 +306,80 @@ das_bwd_kernel(DasArgs a) {
                         asm volatile("ld.shared.v2.f32 {%0,%1}, [%2];" : "=f"(p.x), "=f"(p.y) : "r"(addr));
                         cr = p.x; sr = p.y;
                     }
-                    const float gr = ag[k][jj];
-                    const float gs = gr * scale;
-                    atomicAdd(gw0 + n, __float2int_rn(gs - gs * f));
-                    atomicAdd(gw0 + n + 1, __float2int_rn(gs * f));
-                    float dsum = gr * sr;
-                    pj[k][jj] += g_re[k] * fmaf(u, sr, cr);
+                    const float wk = FN ? ws[jj] * win_w[FN ? k : 0][jj] : ws[jj];
+                    const float gs = g_re[k] * wk;
+                    const float hi = fmaf(gs, f, kQ);                 // kQ + round(gs f)
+                    const float lo = fmaf(-gs, f, gs + kQ);           // kQ + round(round(gs) - gs f)
+                    atomicAdd(gw0 + n, (int)(__float_as_uint(lo) - kQbits));
+                    atomicAdd(gw0 + n + 1, (int)(__float_as_uint(hi) - kQbits));
+                    float dsum = g_re[k] * sr;
+                    float lerp = g_re[k] * fmaf(u, sr, cr);
                     if (CPLX) {
-                        const float gi = agi[k][jj];
-                        const float gis = gi * scale;
+                        const float gis = g_im[k] * wk;
+                        const float hii = fmaf(gis, f, kQ);
+                        const float loi = fmaf(-gis, f, gis + kQ);
                         int* gw1 = gw0 + C::NWIN * C::GW;
-                        atomicAdd(gw1 + n, __float2int_rn(gis - gis * f));
-                        atomicAdd(gw1 + n + 1, __float2int_rn(gis * f));
-                        dsum = fmaf(gi, si, dsum);
-                        pj[k][jj] += g_im[k] * fmaf(u, si, ci);
+                        atomicAdd(gw1 + n, (int)(__float_as_uint(loi) - kQbits));
+                        atomicAdd(gw1 + n + 1, (int)(__float_as_uint(hii) - kQbits));
+                        dsum = fmaf(g_im[k], si, dsum);
+                        lerp = fmaf(g_im[k], fmaf(u, si, ci), lerp);
                     }
-                    gc = fmaf(dsum, u + cwin, gc);
+                    if (FN) {
+                        dsum *= win_w[FN ? k : 0][jj];
+                        lerp *= win_w[FN ? k : 0][jj];
+                    }
+                    pj[jj] += lerp;
+                    gcj[jj] = fmaf(dsum, u + cwin, gcj[jj]);
                 }
             }
         }
         if (ic == n_ic - 1) {
-            // this channel chunk is complete: dL/dw_j partials of the CTA
+            // this channel chunk is complete: dL/dc and dL/dw_j partials
 #pragma unroll
             for (int jj = 0; jj < kBwdCJ; ++jj) {
-                float v = 0.f;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) v += win_w[k][jj] * pj[k][jj];
+                gc = fmaf(wj[jj], gcj[jj], gc);
+                float v = pj[jj];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if (lane == 0) atomicAdd(s_gw + jc * kBwdCJ + jj, v);
             }
         }
         __syncthreads();
-        // ---- window accumulators -> dL/dr (global atomics), then clear them
-        for (int q = tid; q < C::NWIN * C::PLANES * (kBwdWS + 1); q += kDasThreads) {
-            const int n = q % (kBwdWS + 1);
-            const int wp = q / (kBwdWS + 1);
+        // ---- window accumulators -> dL/dr, then clear them. Cells go out in
+        // groups of four samples starting at a multiple of 4 (window starts
+        // are A + off with A a multiple of 8; traces are multiples of 8 long,
+        // so a group lies wholly inside or wholly outside its trace).
+        constexpr int kGroups = (7 + kBwdWS + 1 + 3) / 4;
+        for (int q = tid; q < C::NWIN * C::PLANES * kGroups; q += kDasThreads) {
+            const int g = q % kGroups, wp = q / kGroups;
             const int win = wp % C::NWIN, plane = wp / C::NWIN;
-            if (n > a.W) continue;
-            int* cell = gwin + (plane * C::NWIN + win) * C::GW + n;
-            const int acc = *cell;
-            if (acc == 0) continue;
-            *cell = 0;
-            const float v = (float)acc * inv_scale;
-            const int S = s_S0[b * C::NWIN + win] + n;
-            if (S < 0 || S >= a.n_s) continue;
+            const int off = s_off[b * C::NWIN + win];
+            const int n0 = 4 * g - off;
+            if (n0 > a.W) continue;
+            int* cells = gwin + (plane * C::NWIN + win) * C::GW;
+            int c4[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int n = n0 + e;
+                const bool in = n >= 0 && n <= a.W;
+                c4[e] = in ? cells[n] : 0;
+                if (in && c4[e] != 0) cells[n] = 0;
+            }
+            if ((c4[0] | c4[1] | c4[2] | c4[3]) == 0) continue;
+            const int S = s_S0[b * C::NWIN + win] - off + 4 * g;
+            if (S < 0 || S >= a.n_s || !a.grad_rf) continue;
             const int ii = win / kBwdCJ, jj = win % kBwdCJ;
             const int i = ic * kBwdCI + ii, j = jc * kBwdCJ + jj;
-            if (a.grad_rf)
-                atomicAdd(a.grad_rf + (long long)plane * a.plane_stride + ((long long)i * a.n_ch + j) * a.n_s + S, v);
+            float* dst = a.grad_rf + (long long)plane * a.plane_stride + ((long long)i * a.n_ch + j) * a.n_s + S;
+            if (VEC_RED) {
+                asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};"
+                             :: "l"(dst), "f"((float)c4[0] * inv_scale), "f"((float)c4[1] * inv_scale),
+                                "f"((float)c4[2] * inv_scale), "f"((float)c4[3] * inv_scale) : "memory");
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (c4[e] != 0) atomicAdd(dst + e, (float)c4[e] * inv_scale);
+            }
         }
         __syncthreads();
         // the window starts of stage s are no longer read: refill its raw buffer
@@ -416,10 +461,10 @@ das_bwd_plain_kernel(DasArgs a) {
     }
 }
 
-template <int VU, bool CPLX>
-int launch_bwd_tiled(const PlanHost& h, DasArgs a, cudaStream_t s) {
+template <int VU, bool CPLX, bool ZL, bool FN, bool VEC_RED>
+int launch_bwd_tiled_v(const PlanHost& h, DasArgs a, cudaStream_t s) {
     using C = BwdCfg<VU, CPLX>;
-    auto k = das_bwd_kernel<VU, CPLX>;
+    auto k = das_bwd_kernel<VU, CPLX, ZL, FN, VEC_RED>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess)
         return check_launch("das_backward: set shared memory");
     // channel split: enough units for two CTAs per SM
@@ -433,21 +478,35 @@ int launch_bwd_tiled(const PlanHost& h, DasArgs a, cudaStream_t s) {
     return check_launch("das_bwd_kernel");
 }
 
+template <int VU, bool CPLX, bool ZL>
+int launch_bwd_tiled(const PlanHost& h, const DasArgs& a, cudaStream_t s) {
+    const bool fn = a.f_number > 0.f;
+    const bool vec = (reinterpret_cast<uintptr_t>(a.grad_rf) & 15u) == 0;
+    if (fn) return vec ? launch_bwd_tiled_v<VU, CPLX, ZL, true, true>(h, a, s)
+                       : launch_bwd_tiled_v<VU, CPLX, ZL, true, false>(h, a, s);
+    return vec ? launch_bwd_tiled_v<VU, CPLX, ZL, false, true>(h, a, s)
+               : launch_bwd_tiled_v<VU, CPLX, ZL, false, false>(h, a, s);
+}
+
 }  // namespace
 
-int launch_das_backward(const PlanHost& h, const DasArgs& a, bool tiled, cudaStream_t s) {
+int launch_das_backward(const PlanHost& h, const DasArgs& a, int mode, cudaStream_t s) {
     const bool cplx = a.dtype == RCBF_CF32;
-    if (!tiled) {
+    if (mode == 0) {
         const long long n_vox = (long long)a.n_u * a.n_v * a.n_w;
         const unsigned grid = (unsigned)((n_vox + 127) / 128);
         if (cplx) das_bwd_plain_kernel<true><<<grid, 128, 0, s>>>(a);
         else das_bwd_plain_kernel<false><<<grid, 128, 0, s>>>(a);
         return check_launch("das_bwd_plain_kernel");
     }
+    if (mode == 2) {
+        if (a.bu != 32) return set_error(RCBF_EINVAL, "das_backward: the adjoint tile needs 32 voxels along u");
+        return cplx ? launch_bwd_tiled<1, true, true>(h, a, s) : launch_bwd_tiled<1, false, true>(h, a, s);
+    }
     switch (h.vu) {
-        case 1: return cplx ? launch_bwd_tiled<1, true>(h, a, s) : launch_bwd_tiled<1, false>(h, a, s);
-        case 2: return cplx ? launch_bwd_tiled<2, true>(h, a, s) : launch_bwd_tiled<2, false>(h, a, s);
-        default: return cplx ? launch_bwd_tiled<4, true>(h, a, s) : launch_bwd_tiled<4, false>(h, a, s);
+        case 1: return cplx ? launch_bwd_tiled<1, true, false>(h, a, s) : launch_bwd_tiled<1, false, false>(h, a, s);
+        case 2: return cplx ? launch_bwd_tiled<2, true, false>(h, a, s) : launch_bwd_tiled<2, false, false>(h, a, s);
+        default: return cplx ? launch_bwd_tiled<4, true, false>(h, a, s) : launch_bwd_tiled<4, false, false>(h, a, s);
     }
 }
 

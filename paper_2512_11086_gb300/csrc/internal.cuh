@@ -99,6 +99,10 @@ struct PlanHost {
     int n_split[3];         // channel split by window stride class
     float* d_partial;       // DAS partial images (channel split), plan-owned
     size_t partial_floats;
+    // adjoint tile with lanes over z: 32 voxels along u by bwd_bv x bwd_bw
+    // rows (bwd_bv = 0: no such tile keeps the window within 128 samples)
+    int bwd_bv, bwd_bw;
+    double bwd_r_alpha_m, bwd_r_beta_m;
 };
 
 }  // namespace rcbf
@@ -120,12 +124,17 @@ void plan_geometry(PlanHost& h);
 
 // Window geometry of a DAS call at speed of sound c (host side).
 int das_prepare(const PlanHost& h, double c, DasArgs* a, std::string* why);
+// das_prepare for another tile (bu, bv, bw) with its radii [m]
+int das_prepare_tile(const PlanHost& h, double c, int bu, int bv, int bw, double r_alpha_m, double r_beta_m,
+                     DasArgs* a, std::string* why);
 
 // Kernel launchers (one per translation unit).
 int launch_decode(const PlanHost& h, const int16_t* rf, void* out, cudaStream_t s);
 int launch_das(const PlanHost& h, const DasArgs& a, cudaStream_t s);
 int launch_das_plain(const PlanHost& h, const DasArgs& a, cudaStream_t s);
-int launch_das_backward(const PlanHost& h, const DasArgs& a, bool tiled, cudaStream_t s);
+// mode: 0 plain, 1 tiled with the plan's tile (lanes along u), 2 tiled with
+// the adjoint tile (lanes over z; a.bu must be 32)
+int launch_das_backward(const PlanHost& h, const DasArgs& a, int mode, cudaStream_t s);
 int configure_decode(PlanHost& h);
 int das_class_index(int W);
 int configure_das(PlanHost& h);

@@ -58,6 +58,20 @@ def test_params_layout_matches_header(tmp_path):
     assert got == want
 
 
+def test_plan_info_layout_matches_header(tmp_path):
+    src = tmp_path / "info.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "rcbf.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu\\n\", sizeof(rcbf_plan_info),"
+        " offsetof(rcbf_plan_info, workspace_bytes), offsetof(rcbf_plan_info, bwd_tile),"
+        " offsetof(rcbf_plan_info, bwd_mode)); return 0;}\n")
+    exe = tmp_path / "info"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    I = rc.PlanInfo
+    assert got == [ctypes.sizeof(I), I.workspace_bytes.offset, I.bwd_tile.offset, I.bwd_mode.offset]
+
+
 def _good_params():
     import synth
     return rc.make_params(synth.tiny_bscan_geometry(), decoded_dtype="f32")

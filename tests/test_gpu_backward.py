@@ -104,6 +104,75 @@ def test_gradients_match_oracle(variant, cplx):
     assert e_rf <= 1e-4 and e_w <= 1e-4 and e_c <= tol_c
 
 
+def _coarse_z(cplx):
+    # 10 um lateral, 150 um axial spacing: 32 z-rows of the adjoint's own tile
+    # reach more than 128 samples, the plan's tile (long along x) does not
+    g = synth.Geometry(n_tx=16, n_ch=16, n_samples=1024, out_dims=(128, 1, 64), f_number=0.0,
+                       out_min=(-0.64 * MM, 0.0, 3 * MM), out_max=(0.63 * MM, 0.0, 12.45 * MM))
+    rng = np.random.default_rng(91 + cplx)
+    r = rng.normal(size=(16, 16, 1024)) + (1j * rng.normal(size=(16, 16, 1024)) if cplx else 0)
+    G = rng.normal(size=(64, 1, 128)) + (1j * rng.normal(size=(64, 1, 128)) if cplx else 0)
+    return g, r, G, rng.uniform(0.5, 1.5, 16)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("case", ["z_lanes", "u_lanes", "z_lanes_unaligned_grad_rf", "z_lanes_fnumber"])
+def test_adjoint_lane_mappings_and_flush_forms(case, cplx):
+    # the adjoint's two tiled lane mappings (lanes over z with its own tile;
+    # lanes along u with the plan's tile) and both flush forms (four-float
+    # reductions into a 16-byte aligned grad_rf, scalar atomics otherwise)
+    if case == "u_lanes":
+        g, r, G, w = _coarse_z(cplx)
+    else:
+        g, r, G, w = _small(fnum=0.7 if case == "z_lanes_fnumber" else 0.0, cplx=cplx)
+    plan = rc.Plan(rc.make_params(g, decoded_dtype="cf32" if cplx else "f32"))
+    info = plan.info()
+    assert info["bwd_mode"] == (1 if case == "u_lanes" else 2), info
+    if info["bwd_mode"] == 2:
+        assert info["bwd_tile"][0] == 32 and info["bwd_tile"][1] * info["bwd_tile"][2] == 32
+    dr = _to_dev(r)
+    out = None
+    if case == "z_lanes_unaligned_grad_rf":
+        buf = torch.zeros(dr.numel() + 1, device="cuda")
+        out = buf[1:].view(dr.shape)                 # 4-byte but not 16-byte aligned
+        assert out.data_ptr() % 16 != 0
+    grf, gc, gw = plan.das_backward(dr, _to_dev(G), apod=_to_dev(w), c=1500.0, out_rf=out)
+    want_rf, want_c, want_w = oracle.das_grad(g, r, G, w=w, c=1500.0)
+    e_rf = rel_l2(_from_dev(grf, cplx), want_rf)
+    e_w = rel_l2(gw.cpu().numpy(), want_w)
+    print("%s cplx=%s tile %s: rf %.2e  w %.2e" % (case, cplx, info["bwd_tile"], e_rf, e_w))
+    assert e_rf <= 1e-4 and e_w <= 1e-4
+    if out is not None:
+        assert float(buf[0].item()) == 0.0           # nothing written before the view
+
+
+def test_adjoint_fixed_point_range_extremes():
+    # one 32 x 32 voxel block (one adjoint tile) carries gradients 1e6 times
+    # larger than the rest. The fixed-point scale is set per tile, so trace
+    # samples that only the other tiles reach keep their own relative accuracy.
+    g, r, G, w = _small()
+    plan = rc.Plan(rc.make_params(g, decoded_dtype="f32"))
+    assert plan.info()["bwd_tile"] == (32, 1, 32)
+    big = np.zeros_like(G)
+    big[:32, :, :32] = G[:32, :, :32] * 1e6
+    G = G.copy()
+    G[:32, :, :32] = big[:32, :, :32]
+    grf, _, gw = plan.das_backward(_to_dev(r), _to_dev(G), apod=_to_dev(w))
+    want_rf, _, want_w = oracle.das_grad(g, r, G, w=w)
+    got = grf.cpu().numpy()
+    assert rel_l2(got, want_rf) <= 1e-4
+    assert rel_l2(gw.cpu().numpy(), want_w) <= 1e-4
+    only_small = oracle.das_grad(g, r, big, w=w)[0] == 0.0
+    assert only_small.mean() > 0.3
+    e_small = rel_l2(got[only_small], want_rf[only_small])
+    print("samples reached by the small tiles only: %.1f %%, rel-L2 %.2e" % (100 * only_small.mean(), e_small))
+    assert e_small <= 1e-4
+    # an all-zero gradient (scale from a zero bound)
+    grf0, gc0, gw0 = plan.das_backward(_to_dev(r), _to_dev(np.zeros_like(G)), apod=_to_dev(w))
+    assert float(grf0.abs().max().item()) == 0.0 and float(gc0.item()) == 0.0
+    assert float(gw0.abs().max().item()) == 0.0
+
+
 def test_grad_outputs_are_optional():
     g, r, G, w = _small()
     plan = rc.Plan(rc.make_params(g, decoded_dtype="f32"))
