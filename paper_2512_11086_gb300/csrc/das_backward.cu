@@ -7,24 +7,26 @@
 //   dL/dr_ij[n]   += a_j(v) G(v) (1 - f),   dL/dr_ij[n+1] += a_j(v) G(v) f
 //   dL/dc         += a_j(v) G(v) (r[n+1] - r[n]) ds/dc,   ds/dc = -(d_tx + d_rx) fs / c^2
 //                                                               = -(s + t0 fs) / c
-//   dL/dw_j       += W_j(v) G(v) lerp(r_ij, s)
+//   dL/dw_j       += W_j(v) G(v) lerp(r_ij, s) = sum_n r_ij[n] (dL/dr_ij[n]) / w_j
 // (complex data: the two planes contribute independently).
 //
-// Tiled form: the forward's voxel tiles, per-tile FP64 reference delays,
-// TMA windows and line pieces (c_n, slope_n). Per stage each window gets a
-// shared-memory accumulator; the transposed interpolation weights go there by
-// shared atomics and the window is then added into dL/dr with global atomics
-// (windows of neighbouring tiles overlap). Delays are recomputed per tile,
-// never stored. The plain form is one thread per voxel with global atomics.
+// Tiled form: per-tile FP64 reference delays and TMA windows as in the
+// forward. Per stage each (transmit, channel) window gets a shared-memory
+// accumulator c_ij[n] = sum_v W_j(v) G(v) (lerp weight of sample n); the
+// window is then added into dL/dr_ij = w_j c_ij with global atomics (windows
+// of neighbouring tiles overlap), and sum_n r_ij[n] c_ij[n] into dL/dw_j, so
+// the per-voxel work is the two accumulator updates plus the slope term of
+// dL/dc (the windows are staged as slopes only). Delays are recomputed per
+// tile, never stored. The plain form is one thread per voxel with global
+// atomics.
 //
 // The window accumulators are 32-bit fixed point. Shared-memory float atomics
 // retry per conflicting lane, and neighbouring voxels along the lane axis
 // often hit the same sample; integer atomics do not retry, and integer sums do
-// not depend on order. Per channel chunk the scale is 2^e with
-// 1024 * B * 2^e < 2^30, B = max|w_j| over the chunk times max|G| over the tile
-// (an upper bound of |a_j G|): a cell collects at most one term per voxel of
-// the 1024-voxel tile, so it cannot overflow, and a term is rounded to
-// 2^-e <= 2^-19 * B (a relative 2e-6 of the largest possible term).
+// not depend on order. The scale is 2^e with 1024 * max|G| * 2^e < 2^30 over
+// the tile (W_j <= 1): a cell collects at most one term per voxel of the
+// 1024-voxel tile, so it cannot overflow, and a term is rounded to
+// 2^-e <= 2^-19 max|G| (a relative 2e-6 of the largest term of the tile).
 #include <algorithm>
 
 #include "das_tile.cuh"
@@ -36,6 +38,7 @@ namespace {
 constexpr int kBwdCI = 4;          // transmits per backward stage
 constexpr int kBwdCJ = 4;          // channels per backward stage
 constexpr int kBwdWS = 128;        // window intervals (every W <= 128)
+constexpr int kBwdGroups = (7 + kBwdWS + 1 + 3) / 4;   // 4-sample groups a window's cells can touch
 
 // ZL: lanes on tile rows (the z-major row index), each thread four
 // consecutive voxels along u. Along z the delay grows by a sizeable fraction
@@ -50,12 +53,12 @@ struct BwdCfg {
     static constexpr int NWIN = kBwdCI * kBwdCJ;
     static constexpr int PLANES = CPLX ? 2 : 1;
     static constexpr int COPIES = NWIN * PLANES;
-    static constexpr int PAIR_BYTES = 8 * PLANES;
+    static constexpr int SLOPE_BYTES = 4 * PLANES;   // slope per interval (and plane)
     static constexpr int RAWS = kBwdWS + 8;
     static constexpr int RAW_WIN_BYTES = RAWS * 4 * PLANES;
     static constexpr int GW = kBwdWS + 2;            // accumulator samples per window plane
-    static constexpr int OFF_PAIRS = 0;
-    static constexpr int OFF_RAW = OFF_PAIRS + NWIN * kBwdWS * PAIR_BYTES;
+    static constexpr int OFF_SLOPES = 0;
+    static constexpr int OFF_RAW = OFF_SLOPES + NWIN * kBwdWS * SLOPE_BYTES;
     static constexpr int OFF_GRAD = OFF_RAW + 2 * NWIN * RAW_WIN_BYTES;
     static constexpr int OFF_TX = OFF_GRAD + NWIN * GW * 4 * PLANES;
     static constexpr int OFF_RX = OFF_TX + kMaxOrder * 16;
@@ -68,6 +71,28 @@ struct BwdCfg {
     static constexpr int SMEM = OFF_BAR + 16;
     static_assert(OFF_RAW % 128 == 0 && OFF_GRAD % 16 == 0 && OFF_TX % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
 };
+
+// Raw windows of one stage -> slopes r[n+1] - r[n] of the intervals n < W
+// (both planes of a complex window interleaved). Lane l of a warp handles the
+// intervals 2l and 2l+1.
+template <bool CPLX, int NWIN, int RAWS, int RAW_WIN_BYTES>
+__device__ __forceinline__ void slope_windows(const unsigned char* rawb, const int* woff, float* slopes, int W,
+                                              int warp, int lane) {
+    for (int win = warp; win < NWIN; win += kDasThreads / 32) {
+        const int off = woff[win];
+        const float* r = reinterpret_cast<const float*>(rawb + win * RAW_WIN_BYTES) + off;
+        const float* ri = reinterpret_cast<const float*>(rawb + win * RAW_WIN_BYTES + RAWS * 4) + off;
+        for (int n = 2 * lane; n < W; n += 64) {
+            const float r0 = r[n], r1 = r[n + 1], r2 = r[n + 2];
+            if (CPLX) {
+                const float i0 = ri[n], i1 = ri[n + 1], i2 = ri[n + 2];
+                *reinterpret_cast<float4*>(slopes + 2 * (win * kBwdWS + n)) = make_float4(r1 - r0, i1 - i0, r2 - r1, i2 - i1);
+            } else {
+                *reinterpret_cast<float2*>(slopes + win * kBwdWS + n) = make_float2(r1 - r0, r2 - r1);
+            }
+        }
+    }
+}
 
 // FN: receive F# window active (a per-voxel weight W_j(v)); VEC_RED: dL/dr
 // is 16-byte aligned, so window cells go out as four-float reductions.
@@ -90,9 +115,9 @@ das_bwd_kernel(DasArgs a) {
     float* s_red = reinterpret_cast<float*>(smem + C::OFF_RED);
     int* gwin = reinterpret_cast<int*>(smem + C::OFF_GRAD);
     float* s_max = reinterpret_cast<float*>(smem + C::OFF_MAX);
+    float* slopes = reinterpret_cast<float*>(smem + C::OFF_SLOPES);
     unsigned char* raw = smem + C::OFF_RAW;
     const uint32_t bar0 = smem_u32(smem + C::OFF_BAR);
-    const uint32_t pairs_u32 = smem_u32(smem + C::OFF_PAIRS);
 
     if (tid == 0) {
         mbar_init(bar0, C::COPIES);
@@ -137,9 +162,9 @@ das_bwd_kernel(DasArgs a) {
         }
     }
 
-    // this thread's voxels: offsets, validity and upstream gradient
+    // this thread's voxels: offsets, validity and the scaled upstream gradient
     const float Zf = (float)zr, fsc = (float)a.fs_over_c;
-    float dlr[4], dz[4], g_re[4], g_im[4];
+    float dlr[4], dz[4], gs_re[4], gs_im[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int uu = ZL ? 4 * warp + k : lane + 32 * (k % VU);
@@ -154,18 +179,31 @@ das_bwd_kernel(DasArgs a) {
         const int iu = u0 + uu, iv = v0 + rv, iw = w0 + rw;
         const bool in = iu < a.n_u && iv < a.n_v && iw < a.n_w;
         const long long o = (long long)iw * a.out_sw + (long long)iv * a.out_sv + (long long)iu * a.out_su;
-        g_re[k] = in ? a.grad_image[o] : 0.f;        // voxels outside the image carry no gradient
-        g_im[k] = (in && CPLX) ? a.grad_image[a.image_plane + o] : 0.f;
+        gs_re[k] = in ? a.grad_image[o] : 0.f;       // voxels outside the image carry no gradient
+        gs_im[k] = (in && CPLX) ? a.grad_image[a.image_plane + o] : 0.f;
     }
     float g_max = 0.f;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) g_max = fmaxf(g_max, fmaxf(fabsf(g_re[k]), fabsf(g_im[k])));
+    for (int k = 0; k < 4; ++k) g_max = fmaxf(g_max, fmaxf(fabsf(gs_re[k]), fabsf(gs_im[k])));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) g_max = fmaxf(g_max, __shfl_xor_sync(0xffffffffu, g_max, o));
     if (lane == 0) s_max[warp] = g_max;
     __syncthreads();
 #pragma unroll
     for (int w = 0; w < kDasThreads / 32; ++w) g_max = fmaxf(g_max, s_max[w]);
+    float inv_scale;
+    {
+        int ex = 0;
+        frexpf(g_max, &ex);                 // max|G| < 2^ex
+        const int e = min(max(20 - ex, -120), 120);
+        const float scale = ldexpf(1.0f, e);
+        inv_scale = ldexpf(1.0f, -e);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            gs_re[k] *= scale;
+            gs_im[k] *= scale;
+        }
+    }
 
     const int es = 4;
     auto issue = [&](int s) {
@@ -198,28 +236,24 @@ das_bwd_kernel(DasArgs a) {
     if (NS > 1) issue(1);
     __syncthreads();
 
-    const float magic = 8388608.0f + (float)a.H;
     const float hp = 0.5f + (float)a.H;
-    constexpr int SHIFT = CPLX ? 4 : 3;
-    // per channel of the chunk: w_j and w_j * scale; per (voxel, channel): beta
-    // and (F# window) W_j(v); dL/dw_j and dL/dc partials per channel
-    float beta[4][kBwdCJ], win_w[FN ? 4 : 1][kBwdCJ], wj[kBwdCJ], ws[kBwdCJ], pj[kBwdCJ], gcj[kBwdCJ];
+    constexpr int SHIFT = CPLX ? 3 : 2;
+    // per channel of the chunk: w_j; per (voxel, channel): beta + 0.5 + H and
+    // (F# window) W_j(v); dL/dc partials per channel, dL/dw partials per channel
+    float betah[4][kBwdCJ], win_w[FN ? 4 : 1][kBwdCJ], wj[kBwdCJ], gcj[kBwdCJ], pw[kBwdCJ];
     float gc = 0.f;
     bool ok = true;
     uint32_t phase = 0;
-    float inv_scale = 1.f;                  // fixed-point scale of the window accumulators
 
     for (int s = 0; s < NS; ++s) {
         const int ic = s % n_ic, jc = jc0 + s / n_ic;
         const int b = s & 1;
         if (ic == 0) {
-            float wmax = 0.f;
 #pragma unroll
             for (int jj = 0; jj < kBwdCJ; ++jj) {
                 wj[jj] = a.apod ? __ldg(a.apod + jc * kBwdCJ + jj) : 1.0f;
-                wmax = fmaxf(wmax, fabsf(wj[jj]));
-                pj[jj] = 0.f;
                 gcj[jj] = 0.f;
+                pw[jj] = 0.f;
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -231,28 +265,16 @@ das_bwd_kernel(DasArgs a) {
                     const float d = sqrtf(Lv * Lv + Zv * Zv);
                     const float num = dlr[k] * (2.0f * rx.x + dlr[k]) + dz[k] * (2.0f * Zf + dz[k]);
                     const float bt = rx.z + __fdividef(num, d + rx.y) * fsc;
-                    beta[k][jj] = fminf(fmaxf(bt, rx.z - a.reach_b), rx.z + a.reach_b);
+                    betah[k][jj] = fminf(fmaxf(bt, rx.z - a.reach_b), rx.z + a.reach_b) + hp;
                     if (FN) win_w[FN ? k : 0][jj] = hann_weight(a.f_number, Lv, Zv);
                 }
             }
-            // |a_j G| <= max|w_j| * max|G| (the window weight is at most 1)
-            int ex = 0;
-            frexpf(wmax * g_max, &ex);          // the bound is < 2^ex
-            const int e = min(max(20 - ex, -120), 120);
-            const float scale = ldexpf(1.0f, e);
-            inv_scale = ldexpf(1.0f, -e);
-#pragma unroll
-            for (int jj = 0; jj < kBwdCJ; ++jj) ws[jj] = wj[jj] * scale;
         }
-        // ---- wait for this stage's windows and rewrite them as line pieces
+        // ---- wait for this stage's windows and take their slopes
         ok = mbar_wait_parity(bar0 + 8 * b, (phase >> b) & 1u) && ok;
         phase ^= 1u << b;
-        {
-            const unsigned char* rawb = raw + b * C::NWIN * C::RAW_WIN_BYTES;
-            unsigned char* pairs = smem + C::OFF_PAIRS;
-            rewrite_windows<float, CPLX, kBwdWS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(
-                rawb, s_off + b * C::NWIN, pairs, a.W, hp, 1.0f, warp, lane);
-        }
+        slope_windows<CPLX, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(raw + b * C::NWIN * C::RAW_WIN_BYTES,
+                                                               s_off + b * C::NWIN, slopes, a.W, warp, lane);
         if (tid < kBwdCI * C::ROWS) {
             const int ii = tid / C::ROWS, row = tid % C::ROWS;
             const float dv = (float)row_v(row) - 0.5f * (a.bv - 1);
@@ -272,8 +294,11 @@ das_bwd_kernel(DasArgs a) {
             return;
         }
 
-        // ---- transposed interpolation into the window accumulators
-        const uint32_t pbase = pairs_u32 - (0x4B000000u << SHIFT);
+        // ---- transposed interpolation into the window accumulators. With
+        // uh = u + 0.5 + H (u the window-relative delay), the interval is
+        // n = round(uh - 0.5) and the fraction f = uh - n: t = uh + 2^23 - 0.5
+        // holds n in its low mantissa bits.
+        const uint32_t sbase = smem_u32(slopes) - (0x4B000000u << SHIFT);
         // x + 1.5 * 2^23 holds round(x) in its low mantissa bits for |x| < 2^22
         // (every fixed-point term is below 2^20 in magnitude)
         constexpr float kQ = 12582912.0f;
@@ -284,74 +309,53 @@ das_bwd_kernel(DasArgs a) {
 #pragma unroll
             for (int jj = 0; jj < kBwdCJ; ++jj) {
                 const int win = ii * kBwdCJ + jj;
-                // absolute sample position of u is S0 + u + 0.5 + H; add t0 fs
-                const float cwin = (float)s_S0[b * C::NWIN + win] + hp + (float)a.t0fs;
+                // absolute sample position of uh is S0 + uh; add t0 fs
+                const float cwin = (float)s_S0[b * C::NWIN + win] + (float)a.t0fs;
                 int* gw0 = gwin + win * C::GW;
+                const uint32_t wbase = sbase + win * kBwdWS * C::SLOPE_BYTES;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const float al = ZL ? al_row : s_alpha[ii * C::ROWS + warp * C::VR + k / VU];
-                    const float u = al + beta[k][jj];
-                    const float t = u + magic;
+                    const float uh = al + betah[k][jj];
+                    const float t = uh + 8388607.5f;
                     const int n = (int)(__float_as_uint(t) - 0x4B000000u);
-                    const uint32_t addr = (__float_as_uint(t) << SHIFT) + pbase + win * kBwdWS * C::PAIR_BYTES;
-                    const float f = (u + hp) - (t - 8388608.0f);       // fraction within interval n
-                    float cr, sr, ci = 0.f, si = 0.f;
+                    const float f = uh - (t - 8388608.0f);
+                    const uint32_t addr = (__float_as_uint(t) << SHIFT) + wbase;
+                    float sr, si = 0.f;
                     if (CPLX) {
-                        float4 p;
-                        asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
-                                     : "=f"(p.x), "=f"(p.y), "=f"(p.z), "=f"(p.w) : "r"(addr));
-                        cr = p.x; sr = p.y; ci = p.z; si = p.w;
-                    } else {
                         float2 p;
                         asm volatile("ld.shared.v2.f32 {%0,%1}, [%2];" : "=f"(p.x), "=f"(p.y) : "r"(addr));
-                        cr = p.x; sr = p.y;
+                        sr = p.x; si = p.y;
+                    } else {
+                        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(sr) : "r"(addr));
                     }
-                    const float wk = FN ? ws[jj] * win_w[FN ? k : 0][jj] : ws[jj];
-                    const float gs = g_re[k] * wk;
-                    const float hi = fmaf(gs, f, kQ);                 // kQ + round(gs f)
-                    const float lo = fmaf(-gs, f, gs + kQ);           // kQ + round(round(gs) - gs f)
+                    const float gr = FN ? gs_re[k] * win_w[FN ? k : 0][jj] : gs_re[k];
+                    const float hi = fmaf(gr, f, kQ);                 // kQ + round(g f)
+                    const float lo = fmaf(-gr, f, gr + kQ);           // kQ + round(round(g) - g f)
                     atomicAdd(gw0 + n, (int)(__float_as_uint(lo) - kQbits));
                     atomicAdd(gw0 + n + 1, (int)(__float_as_uint(hi) - kQbits));
-                    float dsum = g_re[k] * sr;
-                    float lerp = g_re[k] * fmaf(u, sr, cr);
+                    float dsum = gr * sr;
                     if (CPLX) {
-                        const float gis = g_im[k] * wk;
-                        const float hii = fmaf(gis, f, kQ);
-                        const float loi = fmaf(-gis, f, gis + kQ);
+                        const float gi = FN ? gs_im[k] * win_w[FN ? k : 0][jj] : gs_im[k];
+                        const float hii = fmaf(gi, f, kQ);
+                        const float loi = fmaf(-gi, f, gi + kQ);
                         int* gw1 = gw0 + C::NWIN * C::GW;
                         atomicAdd(gw1 + n, (int)(__float_as_uint(loi) - kQbits));
                         atomicAdd(gw1 + n + 1, (int)(__float_as_uint(hii) - kQbits));
-                        dsum = fmaf(g_im[k], si, dsum);
-                        lerp = fmaf(g_im[k], fmaf(u, si, ci), lerp);
+                        dsum = fmaf(gi, si, dsum);
                     }
-                    if (FN) {
-                        dsum *= win_w[FN ? k : 0][jj];
-                        lerp *= win_w[FN ? k : 0][jj];
-                    }
-                    pj[jj] += lerp;
-                    gcj[jj] = fmaf(dsum, u + cwin, gcj[jj]);
+                    gcj[jj] = fmaf(dsum, uh + cwin, gcj[jj]);
                 }
             }
         }
-        if (ic == n_ic - 1) {
-            // this channel chunk is complete: dL/dc and dL/dw_j partials
-#pragma unroll
-            for (int jj = 0; jj < kBwdCJ; ++jj) {
-                gc = fmaf(wj[jj], gcj[jj], gc);
-                float v = pj[jj];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) atomicAdd(s_gw + jc * kBwdCJ + jj, v);
-            }
-        }
         __syncthreads();
-        // ---- window accumulators -> dL/dr, then clear them. Cells go out in
-        // groups of four samples starting at a multiple of 4 (window starts
-        // are A + off with A a multiple of 8; traces are multiples of 8 long,
-        // so a group lies wholly inside or wholly outside its trace).
-        constexpr int kGroups = (7 + kBwdWS + 1 + 3) / 4;
-        for (int q = tid; q < C::NWIN * C::PLANES * kGroups; q += kDasThreads) {
-            const int g = q % kGroups, wp = q / kGroups;
+        // ---- window accumulators -> dL/dr = w_j c and dL/dw_j += sum_n r[n] c[n];
+        // then clear them. Cells go out in groups of four samples starting at a
+        // multiple of 4 (window starts are A + off with A a multiple of 8;
+        // traces are multiples of 8 long, so a group lies wholly inside or
+        // wholly outside its trace).
+        for (int q = tid; q < C::NWIN * C::PLANES * kBwdGroups; q += kDasThreads) {
+            const int g = q % kBwdGroups, wp = q / kBwdGroups;
             const int win = wp % C::NWIN, plane = wp / C::NWIN;
             const int off = s_off[b * C::NWIN + win];
             const int n0 = 4 * g - off;
@@ -366,19 +370,44 @@ das_bwd_kernel(DasArgs a) {
                 if (in && c4[e] != 0) cells[n] = 0;
             }
             if ((c4[0] | c4[1] | c4[2] | c4[3]) == 0) continue;
+            const int jj = win % kBwdCJ;
+            // raw sample of cell n is at window index off + n = 4g + e
+            const float4 rv = *reinterpret_cast<const float4*>(
+                raw + (b * C::NWIN + win) * C::RAW_WIN_BYTES + plane * C::RAWS * 4 + 16 * g);
+            const float pr = (float)c4[0] * rv.x + (float)c4[1] * rv.y + (float)c4[2] * rv.z + (float)c4[3] * rv.w;
+            float w_sel = 1.f;
+#pragma unroll
+            for (int t = 0; t < kBwdCJ; ++t) {
+                if (t == jj) {
+                    pw[t] += pr;
+                    w_sel = wj[t];
+                }
+            }
             const int S = s_S0[b * C::NWIN + win] - off + 4 * g;
             if (S < 0 || S >= a.n_s || !a.grad_rf) continue;
-            const int ii = win / kBwdCJ, jj = win % kBwdCJ;
+            const int ii = win / kBwdCJ;
             const int i = ic * kBwdCI + ii, j = jc * kBwdCJ + jj;
             float* dst = a.grad_rf + (long long)plane * a.plane_stride + ((long long)i * a.n_ch + j) * a.n_s + S;
+            const float m = w_sel * inv_scale;
             if (VEC_RED) {
                 asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};"
-                             :: "l"(dst), "f"((float)c4[0] * inv_scale), "f"((float)c4[1] * inv_scale),
-                                "f"((float)c4[2] * inv_scale), "f"((float)c4[3] * inv_scale) : "memory");
+                             :: "l"(dst), "f"((float)c4[0] * m), "f"((float)c4[1] * m),
+                                "f"((float)c4[2] * m), "f"((float)c4[3] * m) : "memory");
             } else {
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    if (c4[e] != 0) atomicAdd(dst + e, (float)c4[e] * inv_scale);
+                    if (c4[e] != 0) atomicAdd(dst + e, (float)c4[e] * m);
+            }
+        }
+        if (ic == n_ic - 1) {
+            // this channel chunk is complete: dL/dc and dL/dw_j partials
+#pragma unroll
+            for (int jj = 0; jj < kBwdCJ; ++jj) {
+                gc = fmaf(wj[jj], gcj[jj], gc);
+                float v = pw[jj];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0 && v != 0.f) atomicAdd(s_gw + jc * kBwdCJ + jj, v * inv_scale);
             }
         }
         __syncthreads();
@@ -388,7 +417,7 @@ das_bwd_kernel(DasArgs a) {
 
     // ---- dL/dc and dL/dw partials of this unit
     if (a.grad_c) {
-        float v = gc;
+        float v = gc * inv_scale;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) s_red[warp] = v;
