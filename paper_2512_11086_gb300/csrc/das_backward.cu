@@ -11,22 +11,28 @@
 // (complex data: the two planes contribute independently).
 //
 // Tiled form: per-tile FP64 reference delays and TMA windows as in the
-// forward. Per stage each (transmit, channel) window gets a shared-memory
-// accumulator c_ij[n] = sum_v W_j(v) G(v) (lerp weight of sample n); the
-// window is then added into dL/dr_ij = w_j c_ij with global atomics (windows
-// of neighbouring tiles overlap), and sum_n r_ij[n] c_ij[n] into dL/dw_j, so
-// the per-voxel work is the two accumulator updates plus the slope term of
-// dL/dc (the windows are staged as slopes only). Delays are recomputed per
-// tile, never stored. The plain form is one thread per voxel with global
+// forward. Per stage each (transmit, channel) window gets two shared-memory
+// accumulators over the intervals n of the window: G0[n] = sum g and
+// G1[n] = sum g f over the voxels v whose delay falls in interval n, with
+// g = W_j(v) G(v) and f the fraction within the interval. Everything else is
+// exact arithmetic on them once the stage is done:
+//   c[n] = G0[n] - G1[n] + G1[n-1]                (lerp weights of sample n)
+//   dL/dr_ij[n] = w_j c[n],   dL/dw_j += sum_n r[n] c[n],
+//   dL/dc (before -w_j / c) += sum_n (r[n+1] - r[n]) ((n + S0 + t0 fs) G0[n] + G1[n])
+// (S0 + n + f is the voxel's absolute sample position). So a voxel costs two
+// accumulator updates per plane and nothing else. Windows of neighbouring
+// tiles overlap, so dL/dr is added with global atomics. Delays are recomputed
+// per tile, never stored. The plain form is one thread per voxel with global
 // atomics.
 //
 // The window accumulators are 32-bit fixed point. Shared-memory float atomics
 // retry per conflicting lane, and neighbouring voxels along the lane axis
 // often hit the same sample; integer atomics do not retry, and integer sums do
 // not depend on order. The scale is 2^e with 1024 * max|G| * 2^e < 2^30 over
-// the tile (W_j <= 1): a cell collects at most one term per voxel of the
-// 1024-voxel tile, so it cannot overflow, and a term is rounded to
-// 2^-e <= 2^-19 max|G| (a relative 2e-6 of the largest term of the tile).
+// the tile (W_j <= 1 and 0 <= f <= 1): an accumulator collects at most one
+// term per voxel of the 1024-voxel tile, so it cannot overflow, and a term is
+// rounded to 2^-e <= 2^-19 max|G| (a relative 2e-6 of the largest term of the
+// tile). c[n] is formed in 64-bit integers.
 #include <algorithm>
 
 #include "das_tile.cuh"
@@ -53,14 +59,13 @@ struct BwdCfg {
     static constexpr int NWIN = kBwdCI * kBwdCJ;
     static constexpr int PLANES = CPLX ? 2 : 1;
     static constexpr int COPIES = NWIN * PLANES;
-    static constexpr int SLOPE_BYTES = 4 * PLANES;   // slope per interval (and plane)
     static constexpr int RAWS = kBwdWS + 8;
     static constexpr int RAW_WIN_BYTES = RAWS * 4 * PLANES;
-    static constexpr int GW = kBwdWS + 2;            // accumulator samples per window plane
-    static constexpr int OFF_SLOPES = 0;
-    static constexpr int OFF_RAW = OFF_SLOPES + NWIN * kBwdWS * SLOPE_BYTES;
-    static constexpr int OFF_GRAD = OFF_RAW + 2 * NWIN * RAW_WIN_BYTES;
-    static constexpr int OFF_TX = OFF_GRAD + NWIN * GW * 4 * PLANES;
+    static constexpr int GW = kBwdWS + 2;            // accumulator intervals per window plane (stride)
+    static constexpr int ACC_INTS = NWIN * PLANES * GW;   // one accumulator (G0 or G1)
+    static constexpr int OFF_RAW = 0;
+    static constexpr int OFF_GRAD = OFF_RAW + 2 * NWIN * RAW_WIN_BYTES;   // int G0[ACC_INTS], G1[ACC_INTS]
+    static constexpr int OFF_TX = OFF_GRAD + 2 * ACC_INTS * 4;
     static constexpr int OFF_RX = OFF_TX + kMaxOrder * 16;
     static constexpr int OFF_ALPHA = OFF_RX + kMaxChannels * 16;
     static constexpr int OFF_WIN = OFF_ALPHA + kBwdCI * ROWS * 4;      // int S0[2][NWIN], int off[2][NWIN]
@@ -69,30 +74,9 @@ struct BwdCfg {
     static constexpr int OFF_MAX = OFF_RED + 32;                       // float[8]: per-warp max|G|
     static constexpr int OFF_BAR = OFF_MAX + 32;                       // uint64[2]
     static constexpr int SMEM = OFF_BAR + 16;
-    static_assert(OFF_RAW % 128 == 0 && OFF_GRAD % 16 == 0 && OFF_TX % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+    static_assert(OFF_RAW % 128 == 0 && OFF_GRAD % 16 == 0 && ACC_INTS % 4 == 0 && OFF_TX % 16 == 0 &&
+                  OFF_BAR % 8 == 0, "alignment");
 };
-
-// Raw windows of one stage -> slopes r[n+1] - r[n] of the intervals n < W
-// (both planes of a complex window interleaved). Lane l of a warp handles the
-// intervals 2l and 2l+1.
-template <bool CPLX, int NWIN, int RAWS, int RAW_WIN_BYTES>
-__device__ __forceinline__ void slope_windows(const unsigned char* rawb, const int* woff, float* slopes, int W,
-                                              int warp, int lane) {
-    for (int win = warp; win < NWIN; win += kDasThreads / 32) {
-        const int off = woff[win];
-        const float* r = reinterpret_cast<const float*>(rawb + win * RAW_WIN_BYTES) + off;
-        const float* ri = reinterpret_cast<const float*>(rawb + win * RAW_WIN_BYTES + RAWS * 4) + off;
-        for (int n = 2 * lane; n < W; n += 64) {
-            const float r0 = r[n], r1 = r[n + 1], r2 = r[n + 2];
-            if (CPLX) {
-                const float i0 = ri[n], i1 = ri[n + 1], i2 = ri[n + 2];
-                *reinterpret_cast<float4*>(slopes + 2 * (win * kBwdWS + n)) = make_float4(r1 - r0, i1 - i0, r2 - r1, i2 - i1);
-            } else {
-                *reinterpret_cast<float2*>(slopes + win * kBwdWS + n) = make_float2(r1 - r0, r2 - r1);
-            }
-        }
-    }
-}
 
 // FN: receive F# window active (a per-voxel weight W_j(v)); VEC_RED: dL/dr
 // is 16-byte aligned, so window cells go out as four-float reductions.
@@ -115,7 +99,6 @@ das_bwd_kernel(DasArgs a) {
     float* s_red = reinterpret_cast<float*>(smem + C::OFF_RED);
     int* gwin = reinterpret_cast<int*>(smem + C::OFF_GRAD);
     float* s_max = reinterpret_cast<float*>(smem + C::OFF_MAX);
-    float* slopes = reinterpret_cast<float*>(smem + C::OFF_SLOPES);
     unsigned char* raw = smem + C::OFF_RAW;
     const uint32_t bar0 = smem_u32(smem + C::OFF_BAR);
 
@@ -124,7 +107,7 @@ das_bwd_kernel(DasArgs a) {
         mbar_init(bar0 + 8, C::COPIES);
         fence_mbar_init();
     }
-    for (int q = tid; q < C::NWIN * C::GW * C::PLANES; q += kDasThreads) gwin[q] = 0;
+    for (int q = tid; q < 2 * C::ACC_INTS; q += kDasThreads) gwin[q] = 0;
     for (int q = tid; q < kMaxChannels; q += kDasThreads) s_gw[q] = 0.f;
 
     // ---- unit -> (tile, channel split)
@@ -191,7 +174,12 @@ das_bwd_kernel(DasArgs a) {
     __syncthreads();
 #pragma unroll
     for (int w = 0; w < kDasThreads / 32; ++w) g_max = fmaxf(g_max, s_max[w]);
+    // x + 1.5 * 2^23 holds round(x) in its low mantissa bits for |x| < 2^22
+    // (every fixed-point term is below 2^20 in magnitude)
+    constexpr float kQ = 12582912.0f;
+    constexpr uint32_t kQbits = 0x4B400000u;
     float inv_scale;
+    int q_re[4], q_im[4];                   // round(scaled G): the G0 term without an F# window
     {
         int ex = 0;
         frexpf(g_max, &ex);                 // max|G| < 2^ex
@@ -202,6 +190,8 @@ das_bwd_kernel(DasArgs a) {
         for (int k = 0; k < 4; ++k) {
             gs_re[k] *= scale;
             gs_im[k] *= scale;
+            q_re[k] = (int)(__float_as_uint(gs_re[k] + kQ) - kQbits);
+            q_im[k] = (int)(__float_as_uint(gs_im[k] + kQ) - kQbits);
         }
     }
 
@@ -237,11 +227,10 @@ das_bwd_kernel(DasArgs a) {
     __syncthreads();
 
     const float hp = 0.5f + (float)a.H;
-    constexpr int SHIFT = CPLX ? 3 : 2;
-    // per channel of the chunk: w_j; per (voxel, channel): beta + 0.5 + H and
-    // (F# window) W_j(v); dL/dc partials per channel, dL/dw partials per channel
-    float betah[4][kBwdCJ], win_w[FN ? 4 : 1][kBwdCJ], wj[kBwdCJ], gcj[kBwdCJ], pw[kBwdCJ];
-    float gc = 0.f;
+    // per channel of the chunk: w_j and the dL/dw_j partial; per (voxel,
+    // channel): beta + 0.5 + H and (F# window) W_j(v)
+    float betah[4][kBwdCJ], win_w[FN ? 4 : 1][kBwdCJ], wj[kBwdCJ], pw[kBwdCJ];
+    float gc = 0.f;                         // dL/dc partial (times -c, scaled)
     bool ok = true;
     uint32_t phase = 0;
 
@@ -252,7 +241,6 @@ das_bwd_kernel(DasArgs a) {
 #pragma unroll
             for (int jj = 0; jj < kBwdCJ; ++jj) {
                 wj[jj] = a.apod ? __ldg(a.apod + jc * kBwdCJ + jj) : 1.0f;
-                gcj[jj] = 0.f;
                 pw[jj] = 0.f;
             }
 #pragma unroll
@@ -270,11 +258,9 @@ das_bwd_kernel(DasArgs a) {
                 }
             }
         }
-        // ---- wait for this stage's windows and take their slopes
+        // ---- wait for this stage's windows
         ok = mbar_wait_parity(bar0 + 8 * b, (phase >> b) & 1u) && ok;
         phase ^= 1u << b;
-        slope_windows<CPLX, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(raw + b * C::NWIN * C::RAW_WIN_BYTES,
-                                                               s_off + b * C::NWIN, slopes, a.W, warp, lane);
         if (tid < kBwdCI * C::ROWS) {
             const int ii = tid / C::ROWS, row = tid % C::ROWS;
             const float dv = (float)row_v(row) - 0.5f * (a.bv - 1);
@@ -294,87 +280,89 @@ das_bwd_kernel(DasArgs a) {
             return;
         }
 
-        // ---- transposed interpolation into the window accumulators. With
-        // uh = u + 0.5 + H (u the window-relative delay), the interval is
-        // n = round(uh - 0.5) and the fraction f = uh - n: t = uh + 2^23 - 0.5
-        // holds n in its low mantissa bits.
-        const uint32_t sbase = smem_u32(slopes) - (0x4B000000u << SHIFT);
-        // x + 1.5 * 2^23 holds round(x) in its low mantissa bits for |x| < 2^22
-        // (every fixed-point term is below 2^20 in magnitude)
-        constexpr float kQ = 12582912.0f;
-        constexpr uint32_t kQbits = 0x4B400000u;
+        // ---- interval sums G0, G1 of every window. With uh = u + 0.5 + H (u
+        // the window-relative delay), the interval is n = round(uh - 0.5) and
+        // the fraction f = uh - n: t = uh + 2^23 - 0.5 holds n in its low
+        // mantissa bits.
+        const uint32_t abase = smem_u32(gwin) - (0x4B000000u << 2);
 #pragma unroll 1
         for (int ii = 0; ii < kBwdCI; ++ii) {
             const float al_row = ZL ? s_alpha[ii * C::ROWS + lane] : 0.f;
 #pragma unroll
             for (int jj = 0; jj < kBwdCJ; ++jj) {
                 const int win = ii * kBwdCJ + jj;
-                // absolute sample position of uh is S0 + uh; add t0 fs
-                const float cwin = (float)s_S0[b * C::NWIN + win] + (float)a.t0fs;
-                int* gw0 = gwin + win * C::GW;
-                const uint32_t wbase = sbase + win * kBwdWS * C::SLOPE_BYTES;
+                const uint32_t wb0 = abase + 4u * (uint32_t)(win * C::GW);      // G0, plane 0
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const float al = ZL ? al_row : s_alpha[ii * C::ROWS + warp * C::VR + k / VU];
                     const float uh = al + betah[k][jj];
                     const float t = uh + 8388607.5f;
-                    const int n = (int)(__float_as_uint(t) - 0x4B000000u);
                     const float f = uh - (t - 8388608.0f);
-                    const uint32_t addr = (__float_as_uint(t) << SHIFT) + wbase;
-                    float sr, si = 0.f;
-                    if (CPLX) {
-                        float2 p;
-                        asm volatile("ld.shared.v2.f32 {%0,%1}, [%2];" : "=f"(p.x), "=f"(p.y) : "r"(addr));
-                        sr = p.x; si = p.y;
-                    } else {
-                        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(sr) : "r"(addr));
+                    const uint32_t g0 = (__float_as_uint(t) << 2) + wb0;
+                    constexpr uint32_t kG1 = 4u * C::ACC_INTS;                  // G1 after G0
+                    constexpr uint32_t kIm = 4u * C::NWIN * C::GW;              // plane 1 after plane 0
+                    float gr = gs_re[k];
+                    int qr = q_re[k];
+                    if (FN) {
+                        gr *= win_w[FN ? k : 0][jj];
+                        qr = (int)(__float_as_uint(gr + kQ) - kQbits);
                     }
-                    const float gr = FN ? gs_re[k] * win_w[FN ? k : 0][jj] : gs_re[k];
-                    const float hi = fmaf(gr, f, kQ);                 // kQ + round(g f)
-                    const float lo = fmaf(-gr, f, gr + kQ);           // kQ + round(round(g) - g f)
-                    atomicAdd(gw0 + n, (int)(__float_as_uint(lo) - kQbits));
-                    atomicAdd(gw0 + n + 1, (int)(__float_as_uint(hi) - kQbits));
-                    float dsum = gr * sr;
+                    const int q1 = (int)(__float_as_uint(fmaf(gr, f, kQ)) - kQbits);
+                    asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(g0), "r"(qr) : "memory");
+                    asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(g0 + kG1), "r"(q1) : "memory");
                     if (CPLX) {
-                        const float gi = FN ? gs_im[k] * win_w[FN ? k : 0][jj] : gs_im[k];
-                        const float hii = fmaf(gi, f, kQ);
-                        const float loi = fmaf(-gi, f, gi + kQ);
-                        int* gw1 = gw0 + C::NWIN * C::GW;
-                        atomicAdd(gw1 + n, (int)(__float_as_uint(loi) - kQbits));
-                        atomicAdd(gw1 + n + 1, (int)(__float_as_uint(hii) - kQbits));
-                        dsum = fmaf(gi, si, dsum);
+                        float gi = gs_im[k];
+                        int qi = q_im[k];
+                        if (FN) {
+                            gi *= win_w[FN ? k : 0][jj];
+                            qi = (int)(__float_as_uint(gi + kQ) - kQbits);
+                        }
+                        const int qi1 = (int)(__float_as_uint(fmaf(gi, f, kQ)) - kQbits);
+                        asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(g0 + kIm), "r"(qi) : "memory");
+                        asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(g0 + kIm + kG1), "r"(qi1) : "memory");
                     }
-                    gcj[jj] = fmaf(dsum, uh + cwin, gcj[jj]);
                 }
             }
         }
         __syncthreads();
-        // ---- window accumulators -> dL/dr = w_j c and dL/dw_j += sum_n r[n] c[n];
-        // then clear them. Cells go out in groups of four samples starting at a
-        // multiple of 4 (window starts are A + off with A a multiple of 8;
-        // traces are multiples of 8 long, so a group lies wholly inside or
-        // wholly outside its trace).
+        // ---- accumulators -> dL/dr = w_j c, dL/dw_j and dL/dc partials. Cells go
+        // out in groups of four samples starting at a multiple of 4 (window
+        // starts are A + off with A a multiple of 8; traces are multiples of 8
+        // long, so a group lies wholly inside or wholly outside its trace).
         for (int q = tid; q < C::NWIN * C::PLANES * kBwdGroups; q += kDasThreads) {
             const int g = q % kBwdGroups, wp = q / kBwdGroups;
             const int win = wp % C::NWIN, plane = wp / C::NWIN;
             const int off = s_off[b * C::NWIN + win];
             const int n0 = 4 * g - off;
             if (n0 > a.W) continue;
-            int* cells = gwin + (plane * C::NWIN + win) * C::GW;
-            int c4[4];
+            const int* G0 = gwin + (plane * C::NWIN + win) * C::GW;
+            const int* G1 = G0 + C::ACC_INTS;
+            // intervals n0-1 .. n0+3 (valid ones are 0 .. W-1)
+            int g0[4], g1[5];
+#pragma unroll
+            for (int e = 0; e < 5; ++e) {
+                const int n = n0 - 1 + e;
+                const bool in = n >= 0 && n < a.W;
+                g1[e] = in ? G1[n] : 0;
+                if (e > 0) g0[e - 1] = in ? G0[n] : 0;
+            }
+            if ((g0[0] | g0[1] | g0[2] | g0[3] | g1[0] | g1[1] | g1[2] | g1[3] | g1[4]) == 0) continue;
+            // raw sample of cell n is at window index off + n = 4g + e
+            const float* rw = reinterpret_cast<const float*>(raw + (b * C::NWIN + win) * C::RAW_WIN_BYTES +
+                                                             plane * C::RAWS * 4) + 4 * g;
+            const float4 r4 = *reinterpret_cast<const float4*>(rw);
+            const float r5 = (n0 + 3 < a.W) ? rw[4] : 0.f;     // right end of interval n0+3
+            const float rr[5] = {r4.x, r4.y, r4.z, r4.w, r5};
+            const float cwin = (float)s_S0[b * C::NWIN + win] + (float)a.t0fs + (float)n0;
+            float c4[4], pr = 0.f, pc = 0.f;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const int n = n0 + e;
-                const bool in = n >= 0 && n <= a.W;
-                c4[e] = in ? cells[n] : 0;
-                if (in && c4[e] != 0) cells[n] = 0;
+                c4[e] = (float)((long long)g0[e] - (long long)g1[e + 1] + (long long)g1[e]);
+                pr = fmaf(rr[e], c4[e], pr);
+                // interval n0+e: slope times position-weighted sum
+                pc = fmaf(rr[e + 1] - rr[e], fmaf((float)e + cwin, (float)g0[e], (float)g1[e + 1]), pc);
             }
-            if ((c4[0] | c4[1] | c4[2] | c4[3]) == 0) continue;
             const int jj = win % kBwdCJ;
-            // raw sample of cell n is at window index off + n = 4g + e
-            const float4 rv = *reinterpret_cast<const float4*>(
-                raw + (b * C::NWIN + win) * C::RAW_WIN_BYTES + plane * C::RAWS * 4 + 16 * g);
-            const float pr = (float)c4[0] * rv.x + (float)c4[1] * rv.y + (float)c4[2] * rv.z + (float)c4[3] * rv.w;
             float w_sel = 1.f;
 #pragma unroll
             for (int t = 0; t < kBwdCJ; ++t) {
@@ -383,6 +371,7 @@ das_bwd_kernel(DasArgs a) {
                     w_sel = wj[t];
                 }
             }
+            gc = fmaf(w_sel, pc, gc);
             const int S = s_S0[b * C::NWIN + win] - off + 4 * g;
             if (S < 0 || S >= a.n_s || !a.grad_rf) continue;
             const int ii = win / kBwdCJ;
@@ -391,19 +380,18 @@ das_bwd_kernel(DasArgs a) {
             const float m = w_sel * inv_scale;
             if (VEC_RED) {
                 asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};"
-                             :: "l"(dst), "f"((float)c4[0] * m), "f"((float)c4[1] * m),
-                                "f"((float)c4[2] * m), "f"((float)c4[3] * m) : "memory");
+                             :: "l"(dst), "f"(c4[0] * m), "f"(c4[1] * m), "f"(c4[2] * m), "f"(c4[3] * m)
+                             : "memory");
             } else {
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    if (c4[e] != 0) atomicAdd(dst + e, (float)c4[e] * m);
+                    if (c4[e] != 0.f) atomicAdd(dst + e, c4[e] * m);
             }
         }
         if (ic == n_ic - 1) {
             // this channel chunk is complete: dL/dc and dL/dw_j partials
 #pragma unroll
             for (int jj = 0; jj < kBwdCJ; ++jj) {
-                gc = fmaf(wj[jj], gcj[jj], gc);
                 float v = pw[jj];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -411,7 +399,11 @@ das_bwd_kernel(DasArgs a) {
             }
         }
         __syncthreads();
-        // the window starts of stage s are no longer read: refill its raw buffer
+        // clear the accumulators (read above, written again after the next
+        // stage's barrier); the window starts of stage s are no longer read:
+        // refill its raw buffer
+        for (int q = tid; q < 2 * C::ACC_INTS / 4; q += kDasThreads)
+            reinterpret_cast<int4*>(gwin)[q] = make_int4(0, 0, 0, 0);
         if (s + 2 < NS) issue(s + 2);
     }
 
