@@ -292,15 +292,63 @@ das_bwd_kernel(DasArgs a) {
             for (int jj = 0; jj < kBwdCJ; ++jj) {
                 const int win = ii * kBwdCJ + jj;
                 const uint32_t wb0 = abase + 4u * (uint32_t)(win * C::GW);      // G0, plane 0
+                // the four voxels' intervals (t holds the interval in its low bits)
+                uint32_t tb[4];
+                float fr[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const float al = ZL ? al_row : s_alpha[ii * C::ROWS + warp * C::VR + k / VU];
                     const float uh = al + betah[k][jj];
                     const float t = uh + 8388607.5f;
-                    const float f = uh - (t - 8388608.0f);
-                    const uint32_t g0 = (__float_as_uint(t) << 2) + wb0;
-                    constexpr uint32_t kG1 = 4u * C::ACC_INTS;                  // G1 after G0
-                    constexpr uint32_t kIm = 4u * C::NWIN * C::GW;              // plane 1 after plane 0
+                    tb[k] = __float_as_uint(t);
+                    fr[k] = uh - (t - 8388608.0f);
+                }
+                constexpr uint32_t kG1 = 4u * C::ACC_INTS;                  // G1 after G0
+                constexpr uint32_t kIm = 4u * C::NWIN * C::GW;              // plane 1 after plane 0
+                // With lanes over z a thread's four voxels are consecutive along
+                // u. Where the delay changes slowly along u they fall into at
+                // most two adjacent intervals in every lane: then per plane the
+                // interval sums go out as two or four reductions, not eight.
+                uint32_t span = 2;
+                uint32_t tmin = 0;
+                if (ZL) {
+                    tmin = min(min(tb[0], tb[1]), min(tb[2], tb[3]));
+                    span = __reduce_max_sync(0xffffffffu, max(max(tb[0], tb[1]), max(tb[2], tb[3])) - tmin);
+                }
+                if (ZL && span <= 1) {
+                    const uint32_t s0 = (tmin << 2) + wb0;
+#pragma unroll
+                    for (int p = 0; p < (CPLX ? 2 : 1); ++p) {
+                        int qs = 0, a1 = 0, g1 = 0, b1 = 0;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            float g = p ? gs_im[k] : gs_re[k];
+                            int q = p ? q_im[k] : q_re[k];
+                            if (FN) {
+                                g *= win_w[FN ? k : 0][jj];
+                                q = (int)(__float_as_uint(g + kQ) - kQbits);
+                            }
+                            const int q1 = (int)(__float_as_uint(fmaf(g, fr[k], kQ)) - kQbits);
+                            const int d = (int)(tb[k] - tmin);                  // 0 or 1
+                            qs += q;
+                            a1 += d * q;
+                            g1 += q1;
+                            b1 += d * q1;
+                        }
+                        const uint32_t sp0 = s0 + (p ? kIm : 0u);
+                        asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0), "r"(qs - a1) : "memory");
+                        asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0 + kG1), "r"(g1 - b1) : "memory");
+                        if (span == 1) {
+                            asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0 + 4u), "r"(a1) : "memory");
+                            asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0 + 4u + kG1), "r"(b1) : "memory");
+                        }
+                    }
+                    continue;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float f = fr[k];
+                    const uint32_t g0 = (tb[k] << 2) + wb0;
                     float gr = gs_re[k];
                     int qr = q_re[k];
                     if (FN) {
@@ -488,11 +536,23 @@ int launch_bwd_tiled_v(const PlanHost& h, DasArgs a, cudaStream_t s) {
     auto k = das_bwd_kernel<VU, CPLX, ZL, FN, VEC_RED>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess)
         return check_launch("das_backward: set shared memory");
-    // channel split: enough units for two CTAs per SM
+    // channel split: the smallest power of two (dividing the channel chunks)
+    // whose work units fill the resident CTA slots to >= 95 %
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kDasThreads, C::SMEM) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
     const long long tiles = (long long)a.tiles_u * a.tiles_v * a.tiles_w;
+    const long long slots = (long long)h.n_sms * per_sm;
     const int chunks = a.n_ch / kBwdCJ;
     int sp = 1;
-    while (tiles * sp < 2LL * h.n_sms && sp * 2 <= chunks && chunks % (sp * 2) == 0) sp *= 2;
+    double best_eff = 0.0;
+    for (int c = 1; c <= chunks && c <= 32; c *= 2) {
+        if (chunks % c) break;
+        const long long units = tiles * c;
+        const double eff = (double)units / (double)(((units + slots - 1) / slots) * slots);
+        if (eff > best_eff + 1e-9) { best_eff = eff; sp = c; }
+        if (eff >= 0.95) break;
+    }
     a.n_split = sp;
     const unsigned grid = (unsigned)(tiles * sp);
     k<<<grid, kDasThreads, C::SMEM, s>>>(a);
