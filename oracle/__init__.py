@@ -54,7 +54,10 @@ class _Geom(ctypes.Structure):
         ("f_number", ctypes.c_double),
         ("out_min", ctypes.c_double * 3), ("out_max", ctypes.c_double * 3),
         ("voxel_transform", ctypes.c_double * 16), ("xdc_transform", ctypes.c_double * 16),
+        ("interp", ctypes.c_int64),
     ]
+
+INTERP = {"linear": 0, "cubic": 1}
 
 
 def _load():
@@ -82,9 +85,11 @@ def _ptr(a: Optional[np.ndarray]):
 
 
 def geom_from(g, c: Optional[float] = None, f_number: Optional[float] = None,
-              voxel_transform=None, xdc_transform=None) -> _Geom:
-    """Oracle geometry from any object with the synth.Geometry attributes."""
+              voxel_transform=None, xdc_transform=None, interp: Optional[str] = None) -> _Geom:
+    """Oracle geometry from any object with the synth.Geometry attributes
+    (interp: 'linear' or 'cubic', default the geometry's own, else linear)."""
     s = _Geom()
+    s.interp = INTERP[interp if interp is not None else getattr(g, "interp", "linear")]
     s.n_tx, s.n_ch, s.n_samples = int(g.n_tx), int(g.n_ch), int(g.n_samples)
     s.tx_orientation, s.rx_orientation = int(g.tx_orientation), int(g.rx_orientation)
     for d in range(3):
@@ -172,6 +177,8 @@ def das_grad(g, rf: np.ndarray, G: np.ndarray, w: Optional[np.ndarray] = None,
     Gp = np.stack([G.real, G.imag]) if cplx else np.asarray(G)[None]
     Gp = np.ascontiguousarray(Gp.reshape(planes.shape[0], -1), dtype=np.float64)
     geom = geom_from(g, c=c, **geom_kw)
+    if geom.interp != 0:
+        raise NotImplementedError("the DAS gradients are defined for linear interpolation")
     grad_rf = np.empty_like(planes) if want_rf else None
     gc = np.zeros(1, dtype=np.float64)
     gw = np.zeros(g.n_ch, dtype=np.float64)

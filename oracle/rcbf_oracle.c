@@ -19,7 +19,8 @@
  *                    a_tx = 1, a_j(v) = w_j W(F# |lat_rx(v) - e_j| / |z(v)|)
  *                    Eq. (2), W(u) = cos^2(pi u) for |u| < 0.5, else 0  Eq. (3);
  *                    r_ij read at fractional sample s = (ToF - t0) fs by linear
- *                    interpolation with zero outside the record.
+ *                    or 4-point cubic Hermite interpolation (§THEORY
+ *                    "Interpolation & Sampling"), zero outside the record.
  *   oracle_das_grad  the derivatives of oracle_das with respect to the RF
  *                    samples, the speed of sound c and the weights w_j.
  *
@@ -52,6 +53,7 @@ typedef struct oracle_geom {
     double out_min[3], out_max[3];
     double voxel_transform[16];               /* row-major, index -> world */
     double xdc_transform[16];                 /* row-major, world -> array */
+    int64_t interp;                           /* 0 linear, 1 cubic Hermite */
 } oracle_geom;
 
 int oracle_threads(void) {
@@ -142,6 +144,29 @@ static double sample_linear(const double* trace, int64_t n_s, double s) {
     return (1.0 - f) * a + f * b;
 }
 
+static double sample_at(const double* trace, int64_t n_s, int64_t k) {
+    return (k >= 0 && k < n_s) ? trace[k] : 0.0;
+}
+
+/* 4-point cubic Hermite spline at fractional sample s (§THEORY
+ * "Interpolation & Sampling"): on [n, n+1], n = floor(s), f = s - n, the
+ * cubic with values r[n], r[n+1] and slopes m_k = (r[k+1] - r[k-1]) / 2 at
+ * both ends (central differences; the paper names the Hermite basis but not
+ * its tangents), in the Hermite basis h00 = 2f^3 - 3f^2 + 1,
+ * h10 = f^3 - 2f^2 + f, h01 = -2f^3 + 3f^2, h11 = f^3 - f^2; zero outside. */
+static double sample_cubic(const double* trace, int64_t n_s, double s) {
+    const double fl = floor(s);
+    const double f = s - fl;
+    const int64_t n = (int64_t)fl;
+    const double p0 = sample_at(trace, n_s, n - 1), p1 = sample_at(trace, n_s, n);
+    const double p2 = sample_at(trace, n_s, n + 1), p3 = sample_at(trace, n_s, n + 2);
+    const double m1 = 0.5 * (p2 - p0), m2 = 0.5 * (p3 - p1);
+    const double f2 = f * f, f3 = f2 * f;
+    const double h00 = 2.0 * f3 - 3.0 * f2 + 1.0, h10 = f3 - 2.0 * f2 + f;
+    const double h01 = -2.0 * f3 + 3.0 * f2, h11 = f3 - f2;
+    return h00 * p1 + h10 * m1 + h01 * p2 + h11 * m2;
+}
+
 /* ------------------------------------------------------------------ DAS */
 
 /* rf: [n_planes][n_tx][n_ch][n_s] doubles; w: [n_ch] or NULL; c > 0.
@@ -170,7 +195,7 @@ void oracle_das(const oracle_geom* g, const double* rf, int64_t n_planes, const 
                     const double tof = (d_tx + d_rx) / c;
                     const double s = (tof - g->t0) * g->fs;
                     const double* trace = rf + ((p * n_tx + i) * n_ch + j) * n_s;
-                    acc += a * sample_linear(trace, n_s, s);
+                    acc += a * (g->interp == 1 ? sample_cubic(trace, n_s, s) : sample_linear(trace, n_s, s));
                 }
             }
             out[p * n_vox + t] = acc;

@@ -73,6 +73,7 @@ class Geometry:
     out_min: Tuple[float, float, float] = (-2.5 * MM, 0.0, 4 * MM)
     out_max: Tuple[float, float, float] = (2.5 * MM, 0.0, 25 * MM)
     f_number: float = 0.0
+    interp: str = "linear"           # sample interpolation of the beamformer: linear or cubic
 
     @property
     def n_vox(self) -> int:

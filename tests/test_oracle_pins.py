@@ -142,6 +142,70 @@ def test_zero_outside_record():
     assert oracle.das(g, np.ones((1, 1, 10))).ravel()[0] == pytest.approx(0.5, abs=1e-12)
 
 
+# -------------------------------------------- cubic Hermite interpolation
+
+def test_cubic_weights_at_a_quarter_sample():
+    # s = 60 + 1/4. The 4-point cubic Hermite spline with central-difference
+    # slopes weights samples 59..62 by -(1/2) h10, h00 - (1/2) h11,
+    # h01 + (1/2) h10, (1/2) h11 at f = 1/4 (h00 = 27/32, h10 = 9/64,
+    # h01 = 5/32, h11 = -3/64): -9/128, 111/128, 29/128, -3/128
+    g = _point_geom(3 * MM, 0.0, 4 * MM, t0=-0.025e-6)
+    g.interp = "cubic"
+    for n, expect in ((59, -9 / 128), (60, 111 / 128), (61, 29 / 128), (62, -3 / 128), (58, 0.0), (63, 0.0)):
+        r = np.zeros((1, 1, g.n_samples))
+        r[0, 0, n] = 1.0
+        assert oracle.das(g, r).ravel()[0] == pytest.approx(expect, abs=1e-12)
+
+
+def test_cubic_interpolates_the_samples():
+    # s = 60 exactly (3-4-5 triangle): the spline passes through r[60]
+    g = _point_geom(3 * MM, 0.0, 4 * MM)
+    g.interp = "cubic"
+    r = np.random.default_rng(11).normal(size=(1, 1, g.n_samples))
+    assert oracle.das(g, r).ravel()[0] == pytest.approx(r[0, 0, 60], abs=1e-12)
+
+
+def test_cubic_reproduces_quadratics_at_hand_computed_delays():
+    # central-difference Hermite splines are exact for polynomials of degree
+    # <= 2: quadratic data returns the quadratic at the delay s of each
+    # hand-computed geometry
+    for x, y, z, t0_us, s in _golden_rows("pythagorean_tof.txt"):
+        g = _point_geom(x * MM, y * MM, z * MM, t0=t0_us * 1e-6)
+        g.interp = "cubic"
+        n = np.arange(g.n_samples, dtype=np.float64)
+        r = (0.3 * n * n - 2.0 * n + 5.0).reshape(1, 1, -1)
+        want = 0.3 * s * s - 2.0 * s + 5.0
+        assert oracle.das(g, r).ravel()[0] == pytest.approx(want, rel=1e-12, abs=1e-9)
+
+
+def test_cubic_matches_scipy_hermite_spline_including_record_ends():
+    # one transmit row and one receive column through the origin: a voxel at
+    # (0, 0, z) is z from both, so s = 2 z fs / c - t0 fs. The delays sweep
+    # the whole record and one sample past each end; the reference is scipy's
+    # CubicHermiteSpline through the zero-extended trace with central
+    # differences as the knot slopes.
+    interp = pytest.importorskip("scipy.interpolate")
+    n_s = 64
+    fs, c = 10e6, 1500.0
+    t0 = 2 * (1.0 * MM) / c + 3.0 / fs               # s = -3 at z = 1 mm
+    z1 = 0.5 * c * ((n_s + 2) / fs + t0)               # s = n_s + 2 at the far end
+    g = Geometry(n_tx=1, n_ch=1, n_samples=n_s, fs=fs, c=c, t0=t0, out_dims=(1, 1, 997),
+                 out_min=(0.0, 0.0, 1.0 * MM), out_max=(0.0, 0.0, z1), interp="cubic")
+    r = np.random.default_rng(12).normal(size=n_s)
+    img = oracle.das(g, r.reshape(1, 1, -1)).ravel()
+    z = np.linspace(1.0 * MM, z1, 997)
+    s = 2 * z * fs / c - t0 * fs
+    pad = 3
+    knots = np.arange(-pad, n_s + pad, dtype=np.float64)
+    vals = np.concatenate([np.zeros(pad), r, np.zeros(pad)])
+    slopes = np.zeros_like(vals)
+    slopes[1:-1] = 0.5 * (vals[2:] - vals[:-2])
+    spline = interp.CubicHermiteSpline(knots, vals, slopes)
+    want = spline(s)
+    assert s.min() < -2.5 and s.max() > n_s + 1.5
+    np.testing.assert_allclose(img, want, rtol=0, atol=1e-12)
+
+
 def _small_geom(n_tx=4, n_ch=4, n_s=256, dims=(5, 1, 6), fnum=0.0):
     return Geometry(n_tx=n_tx, n_ch=n_ch, n_samples=n_s, fs=30e6, c=1540.0,
                     out_dims=dims, out_min=(-1 * MM, 0.0, 2 * MM), out_max=(1 * MM, 0.0, 4 * MM),
