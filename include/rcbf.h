@@ -51,8 +51,13 @@
  *        d_tx = sqrt((lat_tx(q) - e_i)^2 + q_z^2)
  *        d_rx = sqrt((lat_rx(q) - e_j)^2 + q_z^2)
  *        s_ij = ((d_tx + d_rx) / c - t0) * fs          (fractional sample)
- *    and DAS reads the decoded trace r_ij at s_ij by linear interpolation,
- *    with r_ij[n] = 0 for n outside [0, n_samples-1].
+ *    and DAS reads the decoded trace r_ij at s_ij by linear interpolation or
+ *    by the 4-point cubic Hermite spline (§THEORY "Interpolation &
+ *    Sampling"), with r_ij[n] = 0 for n outside [0, n_samples-1].
+ *  * Cubic Hermite reading. On [n, n+1] (n = floor(s), f = s - n) the cubic
+ *    with values r[n], r[n+1] and slopes m_k = (r[k+1] - r[k-1]) / 2 at both
+ *    ends: the paper names the Hermite basis and 4 points but not the
+ *    tangents; central differences are the 4-point choice.
  */
 #ifndef RCBF_H
 #define RCBF_H
@@ -91,7 +96,10 @@ enum rcbf_orientation {
     RCBF_COLUMNS = 1    /* line elements span y: lateral coordinate is x */
 };
 
-enum rcbf_interp { RCBF_LINEAR = 0 };
+enum rcbf_interp {
+    RCBF_LINEAR = 0,    /* (1 - f) r[n] + f r[n+1] */
+    RCBF_CUBIC  = 1     /* 4-point cubic Hermite spline, central-difference slopes (rcbf_das only) */
+};
 
 enum rcbf_decode_variant {
     RCBF_DECODE_MMA_I8  = 0,  /* split-byte int8 tensor-core GEMM (mma.sync s8/u8), exact */

@@ -25,7 +25,8 @@ OK, EINVAL, EUNSUPPORTED, ECUDA, ENOMEM, ETIMEOUT = 0, -1, -2, -3, -4, -5
 I16, I32, F32, F16, CF32 = 0, 1, 2, 3, 4
 FORCES, HERCULES = 0, 1
 ROWS, COLUMNS = 0, 1
-LINEAR = 0
+LINEAR, CUBIC = 0, 1
+_INTERP_NAMES = {"linear": LINEAR, "cubic": CUBIC}
 DECODE_MMA_I8, DECODE_PLAIN, DECODE_MMA_F16 = 0, 1, 2
 DAS_TILED, DAS_PLAIN = 0, 1
 
@@ -123,17 +124,19 @@ def _ptr(t) -> ctypes.c_void_p:
 
 
 def make_params(g, decoded_dtype="f32", decode_variant=DECODE_MMA_I8, das_variant=DAS_TILED,
-                tile=None, f_number=None, xdc_transform=None, voxel_transform=None) -> Params:
+                tile=None, f_number=None, xdc_transform=None, voxel_transform=None, interp=None) -> Params:
     """Parameter block from any object with the geometry attributes (n_tx,
     n_ch, n_samples, fs, c, t0, fc, pitches, orientations, hadamard_order,
-    out_dims, out_min, out_max, f_number)."""
+    out_dims, out_min, out_max, f_number, optionally interp: 'linear' or
+    'cubic'; the interp argument overrides it)."""
     p = Params()
     p.n_tx, p.n_ch, p.n_samples = int(g.n_tx), int(g.n_ch), int(g.n_samples)
     p.hadamard_order = int(getattr(g, "hadamard_order", 0))
     p.acq_kind = int(getattr(g, "acq_kind", FORCES))
     p.tx_orientation, p.rx_orientation = int(g.tx_orientation), int(g.rx_orientation)
     p.decoded_dtype = _DTYPE_NAMES[decoded_dtype] if isinstance(decoded_dtype, str) else int(decoded_dtype)
-    p.interp = LINEAR
+    it = interp if interp is not None else getattr(g, "interp", "linear")
+    p.interp = _INTERP_NAMES[it] if isinstance(it, str) else int(it)
     p.decode_variant, p.das_variant = int(decode_variant), int(das_variant)
     for d in range(3):
         p.out_dims[d] = int(g.out_dims[d])

@@ -132,7 +132,8 @@ int validate(const rcbf_params* p) {
     if (p->tx_orientation > 1 || p->rx_orientation > 1)
         return set_error(RCBF_EINVAL, "rcbf_plan: orientation must be RCBF_ROWS or RCBF_COLUMNS");
     if (p->acq_kind > 1) return set_error(RCBF_EINVAL, "rcbf_plan: unknown acq_kind");
-    if (p->interp != RCBF_LINEAR) return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: only linear interpolation is built");
+    if (p->interp != RCBF_LINEAR && p->interp != RCBF_CUBIC)
+        return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: interp must be RCBF_LINEAR or RCBF_CUBIC");
     if (p->decoded_dtype != RCBF_I32 && p->decoded_dtype != RCBF_F32 && p->decoded_dtype != RCBF_F16 &&
         p->decoded_dtype != RCBF_CF32)
         return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: decoded_dtype must be RCBF_I32, RCBF_F32, RCBF_F16 or RCBF_CF32");
@@ -225,6 +226,7 @@ void setup_geometry(PlanHost& h) {
     a.rx_e0 = -0.5 * (double)(p.n_ch - 1) * p.rx_pitch;
     a.fs = p.fs;
     a.f_number = (float)p.f_number;
+    a.interp = (int)p.interp;
     a.dtype = (int)p.decoded_dtype;
     a.scale = p.decoded_dtype == RCBF_I32 ? 1.0f / (float)p.n_tx : 1.0f;
     a.plane_stride = (long long)p.n_tx * p.n_ch * p.n_samples;
@@ -467,6 +469,8 @@ int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, 
         return set_error(RCBF_EINVAL, "rcbf_das_backward: decoded must be 16-byte aligned, float buffers 4-byte aligned");
     if (h.p.decoded_dtype != RCBF_F32 && h.p.decoded_dtype != RCBF_CF32)
         return set_error(RCBF_EUNSUPPORTED, "rcbf_das_backward: decoded_dtype must be RCBF_F32 or RCBF_CF32");
+    if (h.p.interp != RCBF_LINEAR)
+        return set_error(RCBF_EUNSUPPORTED, "rcbf_das_backward: the adjoint is built for linear interpolation");
     const double cc = c > 0.f ? (double)c : h.p.c;
     DasArgs a;
     std::string why;

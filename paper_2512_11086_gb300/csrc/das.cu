@@ -3,8 +3,9 @@
 // The plain form is the direct reading of Eq. (1)-(3) on the GPU: one thread
 // per voxel, FP32 voxel position and distances (the transmit distances of the
 // voxel cached per thread), fractional sample s = (d_tx + d_rx) fs / c - t0 fs,
-// floor / fraction, two global loads through the read-only cache and a
-// linear interpolation with zero outside the record.
+// floor / fraction, and two global loads through the read-only cache for a
+// linear interpolation (four for the cubic Hermite spline), zero outside the
+// record.
 #include <algorithm>
 #include <cmath>
 
@@ -12,8 +13,8 @@
 
 namespace rcbf {
 
-template <int VU> int configure_das_vu(int ws, bool cplx, int* per_sm);
-template <int VU> int launch_das_vu(const DasArgs& a, int ws, bool cplx, bool apod, cudaStream_t s);
+template <int VU> int configure_das_vu(int ws, bool cplx, bool cubic, int* per_sm);
+template <int VU> int launch_das_vu(const DasArgs& a, int ws, bool cplx, bool apod, bool cubic, cudaStream_t s);
 
 namespace {
 
@@ -24,7 +25,24 @@ __device__ __forceinline__ float plain_load(const void* rf, long long idx, float
     return __ldg(static_cast<const float*>(rf) + idx);
 }
 
-template <int DT, bool CPLX>
+// Trace sample k (zero outside the record).
+template <int DT>
+__device__ __forceinline__ float plain_sample(const void* rf, long long base, int k, int n_s, float scale) {
+    return (k >= 0 && k < n_s) ? plain_load<DT>(rf, base + k, scale) : 0.f;
+}
+
+// Cubic Hermite value at fraction f of interval n: slopes are central
+// differences of the four samples k = n-1 .. n+2.
+template <int DT>
+__device__ __forceinline__ float plain_cubic(const void* rf, long long base, int n, float f, int n_s, float scale) {
+    const float p0 = plain_sample<DT>(rf, base, n - 1, n_s, scale), p1 = plain_sample<DT>(rf, base, n, n_s, scale);
+    const float p2 = plain_sample<DT>(rf, base, n + 1, n_s, scale), p3 = plain_sample<DT>(rf, base, n + 2, n_s, scale);
+    const float m1 = 0.5f * (p2 - p0), m2 = 0.5f * (p3 - p1), d = p2 - p1;
+    const float a2 = 3.0f * d - 2.0f * m1 - m2, a3 = -2.0f * d + m1 + m2;
+    return fmaf(fmaf(fmaf(a3, f, a2), f, m1), f, p1);
+}
+
+template <int DT, bool CPLX, bool CUBIC>
 __global__ void __launch_bounds__(128)
 das_plain_kernel(DasArgs a) {
     const long long n_vox = (long long)a.n_u * a.n_v * a.n_w;
@@ -61,6 +79,11 @@ das_plain_kernel(DasArgs a) {
             const float f = s - fl;
             const int n = (int)fl;
             const long long base = ((long long)i * a.n_ch + j) * a.n_s;
+            if (CUBIC) {
+                acc += w * plain_cubic<DT>(a.rf, base, n, f, a.n_s, a.scale);
+                if (CPLX) acci += w * plain_cubic<DT>(a.rf, a.plane_stride + base, n, f, a.n_s, a.scale);
+                continue;
+            }
             const bool in0 = n >= 0 && n < a.n_s, in1 = n + 1 >= 0 && n + 1 < a.n_s;
             const float r0 = in0 ? plain_load<DT>(a.rf, base + n, a.scale) : 0.f;
             const float r1 = in1 ? plain_load<DT>(a.rf, base + n + 1, a.scale) : 0.f;
@@ -95,13 +118,16 @@ int launch_das_plain(const PlanHost& h, const DasArgs& a, cudaStream_t s) {
     (void)h;
     const long long n_vox = (long long)a.n_u * a.n_v * a.n_w;
     const unsigned grid = (unsigned)((n_vox + 127) / 128);
-    switch (a.dtype) {
-        case RCBF_F32: das_plain_kernel<RCBF_F32, false><<<grid, 128, 0, s>>>(a); break;
-        case RCBF_F16: das_plain_kernel<RCBF_F16, false><<<grid, 128, 0, s>>>(a); break;
-        case RCBF_I32: das_plain_kernel<RCBF_I32, false><<<grid, 128, 0, s>>>(a); break;
-        case RCBF_CF32: das_plain_kernel<RCBF_F32, true><<<grid, 128, 0, s>>>(a); break;
-        default: return set_error(RCBF_EUNSUPPORTED, "das: unsupported decoded dtype");
+#define RCBF_PLAIN(CU)                                                                      \
+    switch (a.dtype) {                                                                      \
+        case RCBF_F32: das_plain_kernel<RCBF_F32, false, CU><<<grid, 128, 0, s>>>(a); break;  \
+        case RCBF_F16: das_plain_kernel<RCBF_F16, false, CU><<<grid, 128, 0, s>>>(a); break;  \
+        case RCBF_I32: das_plain_kernel<RCBF_I32, false, CU><<<grid, 128, 0, s>>>(a); break;  \
+        case RCBF_CF32: das_plain_kernel<RCBF_F32, true, CU><<<grid, 128, 0, s>>>(a); break;  \
+        default: return set_error(RCBF_EUNSUPPORTED, "das: unsupported decoded dtype");     \
     }
+    if (a.interp == RCBF_CUBIC) { RCBF_PLAIN(true) } else { RCBF_PLAIN(false) }
+#undef RCBF_PLAIN
     return check_launch("das_plain_kernel");
 }
 
@@ -135,8 +161,18 @@ int das_prepare_tile(const PlanHost& h, double c, int bu, int bv, int bw, double
     // interval index lands in [0, W-1] whatever the input (NaN included)
     a->reach_a = (float)(r_alpha_m * a->fs_over_c + 0.004);
     a->reach_b = (float)(r_beta_m * a->fs_over_c + 0.004);
+    if (a->interp == RCBF_CUBIC) {
+        // the 4-point stencil of interval n reaches one sample before the
+        // window start and two after its interval: copies start one sample
+        // early and carry two more
+        a->raw_samples = ((a->W + 10 + 7) / 8) * 8;
+    }
     if (a->W > 128) {
         if (why) *why = "das: the voxel tile spans more than 128 samples at this speed of sound; choose a smaller tile";
+        return RCBF_EUNSUPPORTED;
+    }
+    if (a->interp == RCBF_CUBIC && a->dtype == RCBF_CF32 && a->W > 64) {
+        if (why) *why = "das: complex cubic windows above 64 samples run the plain form";
         return RCBF_EUNSUPPORTED;
     }
     return RCBF_OK;
@@ -152,14 +188,15 @@ int launch_das(const PlanHost& h, const DasArgs& a_in, cudaStream_t s) {
     const int ws = stride_class(a.W);
     const bool cplx = a.dtype == RCBF_CF32;
     const bool apod = a.apod != nullptr || a.f_number > 0.f;
+    const bool cubic = a.interp == RCBF_CUBIC;
     a.n_split = std::max(1, h.n_split[class_index(ws)]);
     a.partial = h.d_partial;
     a.partial_stride = a.image_plane * (cplx ? 2 : 1);
     int rc;
     switch (h.vu) {
-        case 1: rc = launch_das_vu<1>(a, ws, cplx, apod, s); break;
-        case 2: rc = launch_das_vu<2>(a, ws, cplx, apod, s); break;
-        default: rc = launch_das_vu<4>(a, ws, cplx, apod, s); break;
+        case 1: rc = launch_das_vu<1>(a, ws, cplx, apod, cubic, s); break;
+        case 2: rc = launch_das_vu<2>(a, ws, cplx, apod, cubic, s); break;
+        default: rc = launch_das_vu<4>(a, ws, cplx, apod, cubic, s); break;
     }
     if (rc != RCBF_OK || a.n_split == 1) return rc;
     const long long n = a.partial_stride;
@@ -172,13 +209,19 @@ int launch_das(const PlanHost& h, const DasArgs& a_in, cudaStream_t s) {
 int configure_das(PlanHost& h) {
     if (h.p.das_variant == RCBF_DAS_PLAIN || !h.tiled_ok) return RCBF_OK;
     const bool cplx = h.p.decoded_dtype == RCBF_CF32;
+    const bool cubic = h.p.interp == RCBF_CUBIC;
     for (int c = 0; c < 3; ++c) {
         const int ws = c == 0 ? 48 : c == 1 ? 64 : 128;
         int rc, n = 0;
+        if (cubic && cplx && ws == 128) {          // runs the plain form
+            h.das_blocks_per_sm[c] = 0;
+            h.n_split[c] = 1;
+            continue;
+        }
         switch (h.vu) {
-            case 1: rc = configure_das_vu<1>(ws, cplx, &n); break;
-            case 2: rc = configure_das_vu<2>(ws, cplx, &n); break;
-            default: rc = configure_das_vu<4>(ws, cplx, &n); break;
+            case 1: rc = configure_das_vu<1>(ws, cplx, cubic, &n); break;
+            case 2: rc = configure_das_vu<2>(ws, cplx, cubic, &n); break;
+            default: rc = configure_das_vu<4>(ws, cplx, cubic, &n); break;
         }
         if (rc != RCBF_OK) return rc;
         h.das_blocks_per_sm[c] = n;

@@ -18,6 +18,13 @@
 // s_ij = A_i + B_j (transmit line i, receive line j) needs one such term per
 // (voxel, transmit) and per (voxel, channel), never per (voxel, i, j).
 //
+// Cubic Hermite (CUBIC): each window copy starts one sample earlier and the
+// pieces hold the interval's cubic in its local fraction f,
+//   r(f) = a0 + f (a1 + f (a2 + f a3)),  a0 = r[n], a1 = m_n,
+//   a2 = 3 (r[n+1] - r[n]) - 2 m_n - m_{n+1},  a3 = 2 (r[n] - r[n+1]) + m_n + m_{n+1},
+// with the central-difference slopes m_k = (r[k+1] - r[k-1]) / 2; the inner
+// loop takes f from the same rounding of t (one 16-byte load, three FMAs).
+//
 // Windows. Every (i, j) trace is read only inside the window
 // [K_i + K_j + lo, K_i + K_j + lo + W] that the tile can reach (W from the
 // tile radius, a 1-Lipschitz bound of the distances). The 1-D TMA bulk engine
@@ -51,20 +58,22 @@ __device__ __forceinline__ void static_for(F&& f) {
     }
 }
 
-template <int VU, int WS, bool CPLX>
+template <int VU, int WS, bool CPLX, bool CUBIC = false>
 struct DasCfg {
     static constexpr int VR = 4 / VU;              // tile rows per thread
     static constexpr int ROWS = 8 * VR;            // tile rows (one warp covers VR rows)
     static constexpr int BU = 32 * VU;             // tile extent along u
     // transmits per stage, so that three line-piece buffers and two raw
     // buffers fit two CTAs per SM for every window class
-    static constexpr int CI = (WS <= 48 ? 8 : WS <= 64 ? 4 : 2) / (CPLX ? 2 : 1);
+    static constexpr int CI_BASE = (WS <= 48 ? 8 : WS <= 64 ? 4 : 2) / (CPLX ? 2 : 1) / (CUBIC ? 2 : 1);
+    static constexpr int CI = CI_BASE > 0 ? CI_BASE : 1;
     static constexpr int CJ = 8;                   // channels per stage
     static constexpr int NWIN = CI * CJ;           // windows per stage
     static constexpr int COPIES = NWIN * (CPLX ? 2 : 1);   // bulk copies per stage (windows x planes)
     static constexpr int NB = 3;                   // line-piece buffers
-    static constexpr int PAIR_BYTES = CPLX ? 16 : 8;
-    static constexpr int RAWS = WS + 8;            // raw samples per window plane (max)
+    static constexpr int PAIR_BYTES = (CPLX ? 16 : 8) * (CUBIC ? 2 : 1);   // one piece (all planes)
+    static constexpr int SHIFT = CPLX ? (CUBIC ? 5 : 4) : (CUBIC ? 4 : 3);  // log2(PAIR_BYTES)
+    static constexpr int RAWS = WS + (CUBIC ? 16 : 8);   // raw samples per window plane (max)
     static constexpr int RAW_WIN_BYTES = RAWS * 4 * (CPLX ? 2 : 1);
     static constexpr int PAIR_BUF = NWIN * WS * PAIR_BYTES;
     static constexpr int ALPHA_N = CI * ROWS;      // transmit terms per stage
@@ -161,6 +170,44 @@ __device__ __forceinline__ void rewrite_windows(const unsigned char* rawb, const
     }
 }
 
+// Raw windows of one stage -> cubic Hermite pieces (coefficients of the
+// interval's cubic in its local fraction). The copy starts one sample before
+// the window, so interval n reads raw samples n .. n+3 (after the offset).
+// Lane l rewrites the intervals 2l and 2l+1 from five raw samples.
+template <class T, bool CPLX, int WS, int NWIN, int RAWS, int RAW_WIN_BYTES>
+__device__ __forceinline__ void rewrite_windows_cubic(const unsigned char* rawb, const int* woff,
+                                                      unsigned char* pairs, int W, float scale,
+                                                      int warp, int lane) {
+    auto coeffs = [](float p0, float p1, float p2, float p3) {
+        const float m1 = 0.5f * (p2 - p0), m2 = 0.5f * (p3 - p1);
+        const float d = p2 - p1;
+        return make_float4(p1, m1, fmaf(3.0f, d, -(2.0f * m1 + m2)), fmaf(-2.0f, d, m1 + m2));
+    };
+    for (int win = warp; win < NWIN; win += kDasThreads / 32) {
+        const int off = woff[win];
+        const T* r = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES) + off;
+        const T* ri = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES + RAWS * 4) + off;
+        for (int n = 2 * lane; n < W; n += 64) {
+            float q[5];
+#pragma unroll
+            for (int e = 0; e < 5; ++e) q[e] = to_f32<T>(r[n + e], scale);
+            float4* p = reinterpret_cast<float4*>(pairs + (size_t)(win * WS + n) * (CPLX ? 32 : 16));
+            if (CPLX) {
+                float qi[5];
+#pragma unroll
+                for (int e = 0; e < 5; ++e) qi[e] = to_f32<T>(ri[n + e], scale);
+                p[0] = coeffs(q[0], q[1], q[2], q[3]);
+                p[1] = coeffs(qi[0], qi[1], qi[2], qi[3]);
+                p[2] = coeffs(q[1], q[2], q[3], q[4]);
+                p[3] = coeffs(qi[1], qi[2], qi[3], qi[4]);
+            } else {
+                p[0] = coeffs(q[0], q[1], q[2], q[3]);
+                p[1] = coeffs(q[1], q[2], q[3], q[4]);
+            }
+        }
+    }
+}
+
 // mbarrier slots (8 bytes each) of a DAS CTA: raw-window buffers (2) and
 // line-piece buffers (3), each with a "full" and an "empty" barrier.
 enum : int { kRawFull = 0, kRawEmpty = 2, kPieceFull = 4, kPieceEmpty = 7, kNumBars = 10 };
@@ -195,9 +242,9 @@ __device__ __forceinline__ void das_pipe_init(unsigned char* bar_base, volatile 
 
 // One work unit. Returns false when a bounded wait expired (the CTA must
 // stop; the caller records the status).
-template <int VU, int WS, bool CPLX, bool APOD>
+template <int VU, int WS, bool CPLX, bool APOD, bool CUBIC = false>
 __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned char* smem, DasPipe& pipe) {
-    using C = DasCfg<VU, WS, CPLX>;
+    using C = DasCfg<VU, WS, CPLX, CUBIC>;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float4* s_tx = reinterpret_cast<float4*>(smem + C::OFF_TX);
     float4* s_rx = reinterpret_cast<float4*>(smem + C::OFF_RX);
@@ -290,7 +337,8 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
         const int plane = CPLX ? (copy & 1) : 0;
         const int ii = win / C::CJ, jj = win % C::CJ;
         const int i = (s % n_ic) * C::CI + ii, j = (jc0 + s / n_ic) * C::CJ + jj;
-        const int S0 = __float_as_int(s_tx[i].w) + __float_as_int(s_rx[j].w) + a.lo;
+        // first staged sample (cubic: one before the window, for the stencil)
+        const int S0 = __float_as_int(s_tx[i].w) + __float_as_int(s_rx[j].w) + a.lo - (CUBIC ? 1 : 0);
         const int A = S0 & ~7;
         if (plane == 0) s_woff[b * C::NWIN + win] = S0 - A;
         const int lo_s = max(A, 0);
@@ -323,7 +371,14 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
         const unsigned char* rawb = raw + b * C::NWIN * C::RAW_WIN_BYTES;
         unsigned char* pairs = smem + C::OFF_PAIRS + pb * C::PAIR_BUF;
         const int* woff = s_woff + b * C::NWIN;
-        if (a.dtype == RCBF_F16)
+        if (CUBIC) {
+            if (a.dtype == RCBF_F16)
+                rewrite_windows_cubic<__half, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, a.scale, warp, lane);
+            else if (a.dtype == RCBF_I32)
+                rewrite_windows_cubic<int, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, a.scale, warp, lane);
+            else
+                rewrite_windows_cubic<float, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, a.scale, warp, lane);
+        } else if (a.dtype == RCBF_F16)
             rewrite_windows<__half, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
         else if (a.dtype == RCBF_I32)
             rewrite_windows<int, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
@@ -355,9 +410,9 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     float acci[4] = {0.f, 0.f, 0.f, 0.f};
     f2x beta2[2][C::CJ];
     f2x apw2[2][C::CJ];
-    const float magic = 8388608.0f + (float)a.H;     // 2^23 + H
+    const float magic = CUBIC ? 8388607.5f : 8388608.0f + (float)a.H;     // 2^23 + H (cubic: on u + 0.5 + H)
     const f2x magic2 = pk(magic, magic);
-    constexpr int SHIFT = CPLX ? 4 : 3;
+    constexpr int SHIFT = C::SHIFT;
 
     // ---- prologue: stages 0 and 1 in flight, stage 0 rewritten
     bool ok = issue(0);
@@ -388,7 +443,8 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
                         const float d = sqrtf(Lv * Lv + Zv * Zv);
                         const float num = dlr[h] * (2.0f * rx.x + dlr[h]) + dz[h] * (2.0f * Zf + dz[h]);
                         const float b0 = rx.z + __fdividef(num, d + rx.y) * fsc;
-                        bt[h] = fminf(fmaxf(b0, rx.z - a.reach_b), rx.z + a.reach_b);
+                        // (cubic: + 0.5 + H, the position in interval units)
+                        bt[h] = fminf(fmaxf(b0, rx.z - a.reach_b), rx.z + a.reach_b) + (CUBIC ? hp : 0.0f);
                         aw[h] = a.f_number > 0.f ? wj * hann_weight(a.f_number, Lv, Zv) : wj;
                     }
                     beta2[kp][jj] = pk(bt[0], bt[1]);
@@ -420,7 +476,41 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
                     float u[2], t[2];
                     upk(u2, u[0], u[1]);
                     upk(t2, t[0], t[1]);
-                    if (CPLX) {
+                    if (CUBIC) {
+                        // u here is u + 0.5 + H: fraction f = u - (t - 2^23)
+                        const f2x f2 = fma2(add2(t2, pk(-8388608.0f, -8388608.0f)), pk(-1.0f, -1.0f), u2);
+                        float f[2];
+                        upk(f2, f[0], f[1]);
+                        float vr[2], vi[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const uint32_t addr = (__float_as_uint(t[h]) << SHIFT) + pb_ii;
+                            const float4 p = lds_f4<OFF>(addr);
+                            vr[h] = fmaf(fmaf(fmaf(p.w, f[h], p.z), f[h], p.y), f[h], p.x);
+                            if (CPLX) {
+                                const float4 q = lds_f4<OFF + 16>(addr);
+                                vi[h] = fmaf(fmaf(fmaf(q.w, f[h], q.z), f[h], q.y), f[h], q.x);
+                            }
+                        }
+                        if (CPLX) {
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const int k = 2 * kp + h;
+                                float ar, ai;
+                                upk(acc2[kp], ar, ai);
+                                float wr = 1.f, wi = 1.f;
+                                if (APOD) upk(apw2[kp][jj], wr, wi);
+                                const float w = h == 0 ? wr : wi;
+                                if (h == 0) ar = APOD ? fmaf(w, vr[h], ar) : ar + vr[h];
+                                else ai = APOD ? fmaf(w, vr[h], ai) : ai + vr[h];
+                                acc2[kp] = pk(ar, ai);
+                                acci[k] = APOD ? fmaf(w, vi[h], acci[k]) : acci[k] + vi[h];
+                            }
+                        } else {
+                            const f2x v2 = pk(vr[0], vr[1]);
+                            acc2[kp] = APOD ? fma2(apw2[kp][jj], v2, acc2[kp]) : add2(acc2[kp], v2);
+                        }
+                    } else if (CPLX) {
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             const int k = 2 * kp + h;

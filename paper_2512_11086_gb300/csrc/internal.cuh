@@ -43,6 +43,7 @@ struct DasArgs {
     double c;              // speed of sound of this call
     double fs;
     float f_number;
+    int interp;            // rcbf_interp
     int W;                 // pairs per window actually used (<= compiled stride)
     int lo;                // window start offset in samples (<= 0)
     int H;                 // W / 2: centring of the per-window line intercepts

@@ -77,9 +77,10 @@ def time_tiles(g, decoded_dtype: str = "f16", tiles: Optional[Sequence[Tile]] = 
     """Milliseconds per DAS call for each admissible tile (tiled form only)."""
     import torch
     tiles = list(tiles) if tiles is not None else candidate_tiles(g)
-    tdt = {"f16": torch.float16, "f32": torch.float32}[decoded_dtype]
-    dec = torch.randn(int(g.n_tx), int(g.n_ch), int(g.n_samples), device="cuda").to(tdt)
-    out = torch.empty(int(g.out_dims[2]), int(g.out_dims[1]), int(g.out_dims[0]), device="cuda")
+    tdt = {"f16": torch.float16, "f32": torch.float32, "cf32": torch.float32}[decoded_dtype]
+    planes = (2,) if decoded_dtype == "cf32" else ()       # complex data: two real planes
+    dec = torch.randn(planes + (int(g.n_tx), int(g.n_ch), int(g.n_samples)), device="cuda").to(tdt)
+    out = torch.empty(planes + (int(g.out_dims[2]), int(g.out_dims[1]), int(g.out_dims[0])), device="cuda")
     result: Dict[Tile, float] = {}
     for t in tiles:
         plan = Plan(make_params(g, decoded_dtype=decoded_dtype, das_variant=DAS_TILED, tile=t))
