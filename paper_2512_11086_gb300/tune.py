@@ -37,7 +37,7 @@ def geometry_key(g, decoded_dtype: str) -> str:
               tuple(round(float(v), 9) for v in g.out_min), tuple(round(float(v), 9) for v in g.out_max),
               int(g.tx_orientation), int(g.rx_orientation), round(float(g.fs), 3), round(float(g.c), 6),
               round(float(g.t0), 12), round(float(g.tx_pitch), 9), round(float(g.rx_pitch), 9),
-              round(float(g.f_number), 6), decoded_dtype)
+              round(float(g.f_number), 6), decoded_dtype, str(getattr(g, "interp", "linear")))
     return repr(fields)
 
 
