@@ -54,7 +54,7 @@ class _Geom(ctypes.Structure):
         ("f_number", ctypes.c_double),
         ("out_min", ctypes.c_double * 3), ("out_max", ctypes.c_double * 3),
         ("voxel_transform", ctypes.c_double * 16), ("xdc_transform", ctypes.c_double * 16),
-        ("interp", ctypes.c_int64),
+        ("interp", ctypes.c_int64), ("iq_freq", ctypes.c_double),
     ]
 
 INTERP = {"linear": 0, "cubic": 1}
@@ -71,6 +71,7 @@ def _load():
             lib.oracle_decode.argtypes = [I64, I64, P, P, P]
             lib.oracle_das.argtypes = [P, P, I64, P, ctypes.c_double, I64, P, P]
             lib.oracle_das_grad.argtypes = [P, P, I64, P, ctypes.c_double, P, P, P, P]
+            lib.oracle_demodulate.argtypes = [I64, I64, P, P, I64, I64, I64, I64, P]
             lib.oracle_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -85,10 +86,14 @@ def _ptr(a: Optional[np.ndarray]):
 
 
 def geom_from(g, c: Optional[float] = None, f_number: Optional[float] = None,
-              voxel_transform=None, xdc_transform=None, interp: Optional[str] = None) -> _Geom:
+              voxel_transform=None, xdc_transform=None, interp: Optional[str] = None,
+              iq_freq: Optional[float] = None) -> _Geom:
     """Oracle geometry from any object with the synth.Geometry attributes
-    (interp: 'linear' or 'cubic', default the geometry's own, else linear)."""
+    (interp: 'linear' or 'cubic', default the geometry's own, else linear;
+    iq_freq: demodulation frequency of baseband IQ data, default the
+    geometry's own, else 0 = RF data)."""
     s = _Geom()
+    s.iq_freq = float(iq_freq if iq_freq is not None else getattr(g, "iq_freq", 0.0))
     s.interp = INTERP[interp if interp is not None else getattr(g, "interp", "linear")]
     s.n_tx, s.n_ch, s.n_samples = int(g.n_tx), int(g.n_ch), int(g.n_samples)
     s.tx_orientation, s.rx_orientation = int(g.tx_orientation), int(g.rx_orientation)
@@ -177,8 +182,8 @@ def das_grad(g, rf: np.ndarray, G: np.ndarray, w: Optional[np.ndarray] = None,
     Gp = np.stack([G.real, G.imag]) if cplx else np.asarray(G)[None]
     Gp = np.ascontiguousarray(Gp.reshape(planes.shape[0], -1), dtype=np.float64)
     geom = geom_from(g, c=c, **geom_kw)
-    if geom.interp != 0:
-        raise NotImplementedError("the DAS gradients are defined for linear interpolation")
+    if geom.interp != 0 or geom.iq_freq > 0:
+        raise NotImplementedError("the DAS gradients are defined for linear interpolation of RF data")
     grad_rf = np.empty_like(planes) if want_rf else None
     gc = np.zeros(1, dtype=np.float64)
     gw = np.zeros(g.n_ch, dtype=np.float64)
@@ -188,3 +193,20 @@ def das_grad(g, rf: np.ndarray, G: np.ndarray, w: Optional[np.ndarray] = None,
     if grad_rf is not None:
         grad_rf = grad_rf[0] + 1j * grad_rf[1] if cplx else grad_rf[0]
     return grad_rf, float(gc[0]), gw
+
+
+# ------------------------------------------------------------ demodulation
+
+def demodulate(rf: np.ndarray, taps: np.ndarray, shift: int, decimation: int) -> np.ndarray:
+    """Eq. (demodulation) at quadrature sampling (f_d = f_s / 4) with int16
+    taps, a rounding right shift and decimation, in exact integers.
+    rf: int16 [..., n_in] -> int16 [2, ..., n_in // decimation] (I, Q)."""
+    rf = np.ascontiguousarray(rf, dtype=np.int16)
+    h = np.ascontiguousarray(taps, dtype=np.int16)
+    n_in = rf.shape[-1]
+    n_out = n_in // int(decimation)
+    n_traces = rf.size // n_in
+    out = np.empty((2,) + rf.shape[:-1] + (n_out,), dtype=np.int16)
+    _load().oracle_demodulate(n_traces, n_in, _ptr(rf), _ptr(h), h.size, int(shift), int(decimation), n_out,
+                              _ptr(out))
+    return out

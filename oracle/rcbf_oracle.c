@@ -23,6 +23,15 @@
  *                    "Interpolation & Sampling"), zero outside the record.
  *   oracle_das_grad  the derivatives of oracle_das with respect to the RF
  *                    samples, the speed of sound c and the weights w_j.
+ *   oracle_demodulate  IQ[n] = LPF{s[n] e^{-j 2 pi f_d n / f_s}} (§OPTIMIZATIONS
+ *                    "Filtering & Demodulation", Eq. (demodulation)) at
+ *                    quadrature sampling f_s = 4 f_d, with an integer FIR
+ *                    (int16 taps, a rounding right shift back to int16) and
+ *                    decimation, in exact integer arithmetic.
+ *   IQ beamforming   oracle_das with iq_freq = f_d > 0 reads the two planes as
+ *                    the baseband signal and multiplies each interpolated
+ *                    sample by e^{j 2 pi (f_d / f_s) s}, which restores the
+ *                    carrier that the index-based mixer removed.
  *
  * Geometry (the readings used by the whole project): line elements centred
  * on the origin, e_i = (i - (n-1)/2) pitch at z = 0; a row element's lateral
@@ -54,6 +63,7 @@ typedef struct oracle_geom {
     double voxel_transform[16];               /* row-major, index -> world */
     double xdc_transform[16];                 /* row-major, world -> array */
     int64_t interp;                           /* 0 linear, 1 cubic Hermite */
+    double iq_freq;                           /* 0: RF planes; > 0: baseband IQ demodulated at this frequency */
 } oracle_geom;
 
 int oracle_threads(void) {
@@ -175,6 +185,7 @@ static double sample_cubic(const double* trace, int64_t n_s, double s) {
 void oracle_das(const oracle_geom* g, const double* rf, int64_t n_planes, const double* w,
                 double c, int64_t n_vox, const int64_t* vox, double* out) {
     const int64_t n_tx = g->n_tx, n_ch = g->n_ch, n_s = g->n_samples;
+    const int iq = g->iq_freq > 0.0 && n_planes == 2;
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t t = 0; t < n_vox; ++t) {
         const int64_t v = vox ? vox[t] : t;
@@ -182,24 +193,34 @@ void oracle_das(const oracle_geom* g, const double* rf, int64_t n_planes, const 
         voxel_position(g, v, q);
         const double lat_tx = lateral(q, g->tx_orientation);
         const double lat_rx = lateral(q, g->rx_orientation);
-        for (int64_t p = 0; p < n_planes; ++p) {
-            double acc = 0.0;
-            for (int64_t i = 0; i < n_tx; ++i) {
-                const double dx_t = lat_tx - element_position(i, n_tx, g->tx_pitch);
-                const double d_tx = sqrt(dx_t * dx_t + q[2] * q[2]);
-                for (int64_t j = 0; j < n_ch; ++j) {
-                    const double dx_r = lat_rx - element_position(j, n_ch, g->rx_pitch);
-                    const double d_rx = sqrt(dx_r * dx_r + q[2] * q[2]);
-                    const double a = (w ? w[j] : 1.0) * window_weight(g->f_number, dx_r, q[2]);
-                    if (a == 0.0) continue;
-                    const double tof = (d_tx + d_rx) / c;
-                    const double s = (tof - g->t0) * g->fs;
+        double acc[2] = {0.0, 0.0};
+        for (int64_t i = 0; i < n_tx; ++i) {
+            const double dx_t = lat_tx - element_position(i, n_tx, g->tx_pitch);
+            const double d_tx = sqrt(dx_t * dx_t + q[2] * q[2]);
+            for (int64_t j = 0; j < n_ch; ++j) {
+                const double dx_r = lat_rx - element_position(j, n_ch, g->rx_pitch);
+                const double d_rx = sqrt(dx_r * dx_r + q[2] * q[2]);
+                const double a = (w ? w[j] : 1.0) * window_weight(g->f_number, dx_r, q[2]);
+                if (a == 0.0) continue;
+                const double tof = (d_tx + d_rx) / c;
+                const double s = (tof - g->t0) * g->fs;
+                double val[2] = {0.0, 0.0};
+                for (int64_t p = 0; p < n_planes; ++p) {
                     const double* trace = rf + ((p * n_tx + i) * n_ch + j) * n_s;
-                    acc += a * (g->interp == 1 ? sample_cubic(trace, n_s, s) : sample_linear(trace, n_s, s));
+                    val[p] = g->interp == 1 ? sample_cubic(trace, n_s, s) : sample_linear(trace, n_s, s);
+                }
+                if (iq) {
+                    /* (I + jQ) e^{j 2 pi (f_d / f_s) s} */
+                    const double ph = 2.0 * M_PI * (g->iq_freq / g->fs) * s;
+                    const double cr = cos(ph), sr = sin(ph);
+                    acc[0] += a * (val[0] * cr - val[1] * sr);
+                    acc[1] += a * (val[0] * sr + val[1] * cr);
+                } else {
+                    for (int64_t p = 0; p < n_planes; ++p) acc[p] += a * val[p];
                 }
             }
-            out[p * n_vox + t] = acc;
         }
+        for (int64_t p = 0; p < n_planes; ++p) out[p * n_vox + t] = acc[p];
     }
 }
 
@@ -268,4 +289,55 @@ void oracle_das_grad(const oracle_geom* g, const double* rf, int64_t n_planes, c
     if (grad_c) *grad_c = gc_total;
     if (grad_w) for (int64_t j = 0; j < n_ch; ++j) grad_w[j] = gw_total[j];
     free(gw_total);
+}
+
+/* ------------------------------------------------------------ demodulation */
+
+/* Round x / 2^shift to the nearest integer, ties to even. */
+static int64_t round_shift_even(int64_t x, int64_t shift) {
+    if (shift <= 0) return x;
+    const int64_t d = (int64_t)1 << shift;
+    int64_t q = x >= 0 ? x / d : -((-x + d - 1) / d);     /* floor(x / d) */
+    const int64_t rem = x - q * d;                          /* 0 <= rem < d */
+    if (2 * rem > d || (2 * rem == d && (q & 1))) q += 1;
+    return q;
+}
+
+/* Eq. (demodulation) at f_d = f_s / 4: e^{-j 2 pi n / 4} = cos(pi n / 2) - j sin(pi n / 2)
+ * is 1, -j, -1, j for n mod 4 = 0, 1, 2, 3. The LPF is the causal FIR
+ * y[n] = sum_k h[k] x[n - k] (x = 0 outside the record); decimation keeps
+ * n = m D. Each output component is rounded (ties to even) after a right
+ * shift and saturated to int16.
+ * s: [n_traces][n_in] int16; h: [n_taps] int16; out: [2][n_traces][n_out]
+ * (I plane, then Q plane), n_out * D <= n_in. */
+void oracle_demodulate(int64_t n_traces, int64_t n_in, const int16_t* s, const int16_t* h, int64_t n_taps,
+                       int64_t shift, int64_t decimation, int64_t n_out, int16_t* out) {
+#pragma omp parallel for schedule(static)
+    for (int64_t tr = 0; tr < n_traces; ++tr) {
+        const int16_t* x = s + tr * n_in;
+        for (int64_t m = 0; m < n_out; ++m) {
+            const int64_t n = m * decimation;
+            int64_t acc_i = 0, acc_q = 0;
+            for (int64_t k = 0; k < n_taps; ++k) {
+                const int64_t idx = n - k;
+                if (idx < 0 || idx >= n_in) continue;
+                const int64_t v = x[idx];
+                /* x[idx] e^{-j pi idx / 2} */
+                int64_t re = 0, im = 0;
+                switch (idx & 3) {
+                    case 0: re = v; break;
+                    case 1: im = -v; break;
+                    case 2: re = -v; break;
+                    default: im = v; break;
+                }
+                acc_i += (int64_t)h[k] * re;
+                acc_q += (int64_t)h[k] * im;
+            }
+            int64_t oi = round_shift_even(acc_i, shift), oq = round_shift_even(acc_q, shift);
+            oi = oi > 32767 ? 32767 : oi < -32768 ? -32768 : oi;
+            oq = oq > 32767 ? 32767 : oq < -32768 ? -32768 : oq;
+            out[tr * n_out + m] = (int16_t)oi;
+            out[(n_traces + tr) * n_out + m] = (int16_t)oq;
+        }
+    }
 }

@@ -74,6 +74,7 @@ class Geometry:
     out_max: Tuple[float, float, float] = (2.5 * MM, 0.0, 25 * MM)
     f_number: float = 0.0
     interp: str = "linear"           # sample interpolation of the beamformer: linear or cubic
+    iq_freq: float = 0.0             # > 0: the beamformed data is baseband IQ demodulated at this frequency
 
     @property
     def n_vox(self) -> int:

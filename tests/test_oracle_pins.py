@@ -206,6 +206,76 @@ def test_cubic_matches_scipy_hermite_spline_including_record_ends():
     np.testing.assert_allclose(img, want, rtol=0, atol=1e-12)
 
 
+# ------------------------------------------------- demodulation (Eq. demod)
+
+def test_demod_impulse_response_is_the_mixed_tap_sequence():
+    # an FIR's response to an impulse is its tap sequence; the quadrature mixer
+    # e^{-j pi n / 2} at n = 13 (13 mod 4 = 1) is -j; decimation by 2 keeps the
+    # outputs at n = 2 m, so output m sees tap 2 m - 13
+    h = np.array([3, -7, 11, 2, -5, 9, 1, -4, 6], dtype=np.int16)
+    s = np.zeros((1, 64), dtype=np.int16)
+    s[0, 13] = 8
+    iq = oracle.demodulate(s, h, shift=3, decimation=2)
+    assert iq.shape == (2, 1, 32)
+    for m in range(32):
+        k = 2 * m - 13
+        want = -int(h[k]) if 0 <= k < h.size else 0
+        assert iq[0, 0, m] == 0 and iq[1, 0, m] == want
+    s[0, 13], s[0, 12] = 0, 8                       # 12 mod 4 = 0: mixer 1 -> I plane
+    iq = oracle.demodulate(s, h, shift=3, decimation=2)
+    for m in range(32):
+        k = 2 * m - 12
+        assert iq[1, 0, m] == 0 and iq[0, 0, m] == (int(h[k]) if 0 <= k < h.size else 0)
+
+
+def test_demod_tone_at_the_demodulation_frequency_goes_to_baseband():
+    # s = A cos(pi n / 2) = A, 0, -A, 0, ...: mixed it is A at even n, 0 at odd
+    # n, so (once the filter is full) the output is A * (sum of the even taps)
+    # in I and 0 in Q; s = A sin(pi n / 2) mixes to -jA at odd n: -A * (sum of
+    # the odd taps) in Q
+    h = np.array([1, 2, 3, 4, 5, 4, 3, 2, 1], dtype=np.int16)
+    n = np.arange(200)
+    A = 100
+    cos_t = (A * np.round(np.cos(np.pi * n / 2))).astype(np.int16)[None]
+    sin_t = (A * np.round(np.sin(np.pi * n / 2))).astype(np.int16)[None]
+    even, odd = int(h[0::2].sum()), int(h[1::2].sum())
+    iq = oracle.demodulate(cos_t, h, shift=0, decimation=4)
+    assert np.all(iq[0, 0, 3:] == A * even) and np.all(iq[1, 0, :] == 0)
+    iq = oracle.demodulate(sin_t, h, shift=0, decimation=4)
+    assert np.all(iq[1, 0, 3:] == -A * odd) and np.all(iq[0, 0, :] == 0)
+
+
+def test_demod_rounding_ties_to_even_and_saturation():
+    # one tap of 1, shift 1: v / 2 rounded half to even (by hand)
+    vals = [3, 5, -3, -5, 7, 1, -1, 4]
+    want = [2, 2, -2, -2, 4, 0, 0, 2]
+    s = np.zeros((1, 4 * len(vals)), dtype=np.int16)
+    s[0, 0::4] = vals                               # n mod 4 = 0: mixer 1
+    iq = oracle.demodulate(s, np.array([1], dtype=np.int16), shift=1, decimation=4)
+    assert list(iq[0, 0]) == want
+    # a tap of 32767 with no shift saturates both ways
+    s[0, 0::4] = [2, -2, 1, -1, 0, 0, 0, 0]
+    iq = oracle.demodulate(s, np.array([32767], dtype=np.int16), shift=0, decimation=4)
+    assert list(iq[0, 0, :4]) == [32767, -32768, 32767, -32767]
+
+
+def test_iq_beamforming_restores_the_carrier_at_integer_delays():
+    # at an integer delay s the interpolants return the samples, and IQ
+    # beamforming multiplies (I + jQ)[s] by e^{j 2 pi (f_d / f_s) s}
+    rng = np.random.default_rng(14)
+    for x, y, z, t0_us, s_exact in _golden_rows("pythagorean_tof.txt"):
+        if abs(s_exact - round(s_exact)) > 1e-9:
+            continue
+        g = _point_geom(x * MM, y * MM, z * MM, t0=t0_us * 1e-6)
+        g.iq_freq = 2.5e6                             # f_d / f_s = 1/4
+        iq = rng.normal(size=(1, 1, g.n_samples)) + 1j * rng.normal(size=(1, 1, g.n_samples))
+        sn = int(round(s_exact))
+        want = iq[0, 0, sn] * np.exp(2j * np.pi * 0.25 * sn)
+        for interp in ("linear", "cubic"):
+            got = oracle.das(g, iq, interp=interp).ravel()[0]
+            assert abs(got - want) <= 1e-12 * max(1.0, abs(want))
+
+
 def _small_geom(n_tx=4, n_ch=4, n_s=256, dims=(5, 1, 6), fnum=0.0):
     return Geometry(n_tx=n_tx, n_ch=n_ch, n_samples=n_s, fs=30e6, c=1540.0,
                     out_dims=dims, out_min=(-1 * MM, 0.0, 2 * MM), out_max=(1 * MM, 0.0, 4 * MM),
