@@ -149,6 +149,20 @@ typedef struct rcbf_params {
     const int8_t* decode_matrix; /* optional HOST pointer to an n_tx x n_tx +-1 matrix H,
                                     row-major H[k][i] (k = acquisition, i = decoded element),
                                     copied by rcbf_plan; NULL = Sylvester H[k][i] = (-1)^popcount(k&i) */
+    /* Quadrature demodulation ahead of the decode (rcbf_demodulate, §OPTIMIZATIONS
+     * "Filtering & Demodulation"). 0 = none. With D = demod_decimation >= 1 the raw RF
+     * has n_samples * D samples per trace, sampled at 4 f_d; n_samples, fs and t0
+     * describe the demodulated data (fs = raw rate / D). A Hadamard-encoded plan with
+     * demodulation decodes the two int16 planes into RCBF_CF32. */
+    uint32_t demod_decimation;  /* D in [1, 16], or 0 */
+    uint32_t demod_n_taps;      /* FIR length, 1..1024 */
+    int32_t  demod_shift;       /* right shift (rounding ties to even) back to int16, 0..30 */
+    uint32_t reserved2;
+    const int16_t* demod_taps;  /* HOST pointer to the int16 taps h[0..n_taps-1], copied by rcbf_plan;
+                                   sum |h| <= 65535 (exact 32-bit accumulation) */
+    double   iq_freq;           /* > 0: the decoded data is baseband IQ demodulated at this frequency
+                                   (RCBF_CF32 only): rcbf_das multiplies each interpolated sample by
+                                   e^{j 2 pi (iq_freq / fs) s} (IQ beamforming). 0 = RF data. */
 } rcbf_params;
 
 typedef struct rcbf_plan_s*  rcbf_plan_t;
@@ -187,10 +201,24 @@ int rcbf_plan_query(rcbf_plan_t plan, rcbf_plan_info* info);
  * called while work using the plan is still pending on a stream. */
 void rcbf_destroy(rcbf_plan_t plan);
 
+/* rcbf_demodulate — Eq. (demodulation), IQ[n] = LPF{s[n] e^{-j 2 pi f_d n / f_s}}
+ * (§OPTIMIZATIONS "Filtering & Demodulation"), at quadrature sampling f_s = 4 f_d,
+ * where the mixer e^{-j pi n / 2} is 1, -j, -1, j for n mod 4 = 0..3. The LPF is
+ * the causal FIR y[n] = sum_k h[k] x[n - k] with the plan's int16 taps (x = 0
+ * outside the record), evaluated at n = m D (decimation); each component is
+ * shifted right by demod_shift with rounding ties to even and saturated to
+ * int16. Exact integer arithmetic, so the result is reproducible bit for bit.
+ *   rf  device int16 [n_tx][n_ch][n_samples * D] (raw traces, any encoding)
+ *   iq  device int16 [2][n_tx][n_ch][n_samples]: I plane, then Q plane
+ * Errors: RCBF_EINVAL (NULL, misaligned, plan without demodulation), RCBF_ECUDA. */
+int rcbf_demodulate(rcbf_plan_t plan, const int16_t* rf, int16_t* iq, void* stream);
+
 /* rcbf_decode — D = H^T S over the transmit axis (§THEORY "Synthetic Aperture
  * Imaging": decoded data behaves as one transmit per element; §OPTIMIZATIONS
  * "Decoding": a matrix product across transmits).
- *   rf       device int16 [n_tx][n_ch][n_samples] (encoded acquisitions k)
+ *   rf       device int16 [n_tx][n_ch][n_samples] (encoded acquisitions k), or
+ *            with demodulation the two int16 planes [2][n_tx][n_ch][n_samples]
+ *            that rcbf_demodulate writes (decoded as RCBF_CF32: each plane D / N)
  *   decoded  device [n_tx][n_ch][n_samples] of params.decoded_dtype:
  *            RCBF_I32 = D exactly; RCBF_F32 = D / N exactly (|D| < 2^24 always
  *            holds for int16 input and N <= 256); RCBF_F16 = D / N rounded once.
@@ -208,6 +236,9 @@ int rcbf_decode(rcbf_plan_t plan, const int16_t* rf, void* decoded, void* stream
  *   apod     device float32 [n_ch] per-channel weights w_j, or NULL (all 1)
  *   c        speed of sound for this call; <= 0 uses params.c
  *   image    device float32 [nz][ny][nx] (x2 planes for RCBF_CF32), overwritten
+ * IQ beamforming (params.iq_freq > 0, RCBF_CF32): the interpolated baseband
+ * sample is multiplied by e^{j 2 pi (iq_freq / fs) s} before the sum, which
+ * restores the carrier that the index-based demodulation mixer removed.
  * Accumulation is FP32. The tiled form (params.das_variant = RCBF_DAS_TILED)
  * needs n_tx % 8 == 0 (4 for complex), n_ch % 8 == 0, an image axis parallel
  * to the transmit line elements, and voxel tiles that reach at most 128
@@ -236,6 +267,8 @@ int rcbf_das(rcbf_plan_t plan, const void* decoded, const float* apod, float c,
  * float atomics, so the order of those sums (and their last bits) varies
  * between runs. A 16-byte aligned grad_rf takes four-float reductions; any
  * 4-byte aligned one is accepted. rcbf_plan_query reports the tile used.
+ * Built for RF data with linear interpolation: IQ or cubic plans return
+ * RCBF_EUNSUPPORTED.
  * Errors: RCBF_EINVAL, RCBF_EUNSUPPORTED (dtype), RCBF_ECUDA. */
 int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, float c,
                       const float* grad_image, float* grad_rf, float* grad_c,

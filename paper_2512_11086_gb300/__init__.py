@@ -55,6 +55,10 @@ class Params(ctypes.Structure):
         ("voxel_transform", ctypes.c_double * 16),
         ("f_number", ctypes.c_double),
         ("decode_matrix", ctypes.c_void_p),
+        ("demod_decimation", ctypes.c_uint32), ("demod_n_taps", ctypes.c_uint32),
+        ("demod_shift", ctypes.c_int32), ("reserved2", ctypes.c_uint32),
+        ("demod_taps", ctypes.c_void_p),
+        ("iq_freq", ctypes.c_double),
     ]
 
 
@@ -75,6 +79,7 @@ SIGNATURES = {
     "rcbf_destroy": (None, [_P]),
     "rcbf_plan_query": (ctypes.c_int, [_P, ctypes.POINTER(PlanInfo)]),
     "rcbf_decode": (ctypes.c_int, [_P, _P, _P, _P]),
+    "rcbf_demodulate": (ctypes.c_int, [_P, _P, _P, _P]),
     "rcbf_das": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, _P, _P]),
     "rcbf_das_backward": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, _P, _P, _P, _P, _P]),
     "rcbf_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_uint32, ctypes.POINTER(_P),
@@ -124,11 +129,14 @@ def _ptr(t) -> ctypes.c_void_p:
 
 
 def make_params(g, decoded_dtype="f32", decode_variant=DECODE_MMA_I8, das_variant=DAS_TILED,
-                tile=None, f_number=None, xdc_transform=None, voxel_transform=None, interp=None) -> Params:
+                tile=None, f_number=None, xdc_transform=None, voxel_transform=None, interp=None,
+                demod=None, iq_freq=None) -> Params:
     """Parameter block from any object with the geometry attributes (n_tx,
     n_ch, n_samples, fs, c, t0, fc, pitches, orientations, hadamard_order,
     out_dims, out_min, out_max, f_number, optionally interp: 'linear' or
-    'cubic'; the interp argument overrides it)."""
+    'cubic', iq_freq; the arguments override them). demod = (decimation,
+    int16 taps, shift) adds the quadrature demodulation stage; the geometry
+    then describes the demodulated data (n_samples, fs, t0)."""
     p = Params()
     p.n_tx, p.n_ch, p.n_samples = int(g.n_tx), int(g.n_ch), int(g.n_samples)
     p.hadamard_order = int(getattr(g, "hadamard_order", 0))
@@ -148,6 +156,14 @@ def make_params(g, decoded_dtype="f32", decode_variant=DECODE_MMA_I8, das_varian
     p.fs, p.c, p.t0, p.fc = float(g.fs), float(g.c), float(g.t0), float(getattr(g, "fc", 0.0))
     p.tx_pitch, p.rx_pitch = float(g.tx_pitch), float(g.rx_pitch)
     p.f_number = float(g.f_number if f_number is None else f_number)
+    p.iq_freq = float(iq_freq if iq_freq is not None else getattr(g, "iq_freq", 0.0))
+    if demod is not None:
+        import numpy as np
+        dec, taps, shift = demod
+        taps = np.ascontiguousarray(taps, dtype=np.int16)
+        p.demod_decimation, p.demod_n_taps, p.demod_shift = int(dec), int(taps.size), int(shift)
+        p.demod_taps = taps.ctypes.data
+        p._taps = taps          # kept alive until rcbf_plan copies it
     if xdc_transform is not None:
         for k, v in enumerate([float(x) for row in xdc_transform for x in row]):
             p.xdc_transform[k] = v
@@ -171,6 +187,7 @@ class Plan:
         h = ctypes.c_void_p()
         _check(lib.rcbf_plan(ctypes.byref(params), ctypes.byref(h)))
         params.decode_matrix = None
+        params.demod_taps = None
         self.handle = h
         self.params = params
 
@@ -210,11 +227,21 @@ class Plan:
         return {I32: torch.int32, F32: torch.float32, F16: torch.float16, CF32: torch.float32}[
             self.params.decoded_dtype]
 
-    def decode(self, rf, out=None, stream=None):
-        """rcbf_decode: int16 [n_tx][n_ch][n_s] CUDA tensor -> decoded tensor."""
+    def demodulate(self, rf, out=None, stream=None):
+        """rcbf_demodulate: raw int16 [n_tx][n_ch][n_s * D] -> int16 IQ planes [2][n_tx][n_ch][n_s]."""
         import torch
         if out is None:
-            out = torch.empty(self.rf_shape, dtype=self.decoded_torch_dtype(), device=rf.device)
+            out = torch.empty((2,) + self.rf_shape, dtype=torch.int16, device=rf.device)
+        _check(load_library().rcbf_demodulate(self.handle, _ptr(rf), _ptr(out), _stream(stream)))
+        return out
+
+    def decode(self, rf, out=None, stream=None):
+        """rcbf_decode: int16 [n_tx][n_ch][n_s] CUDA tensor (two planes after
+        demodulation) -> decoded tensor (two FP32 planes for RCBF_CF32)."""
+        import torch
+        if out is None:
+            shape = ((2,) if self.params.decoded_dtype == CF32 else ()) + self.rf_shape
+            out = torch.empty(shape, dtype=self.decoded_torch_dtype(), device=rf.device)
         _check(load_library().rcbf_decode(self.handle, _ptr(rf), _ptr(out), _stream(stream)))
         return out
 

@@ -4,6 +4,7 @@
 // before a launch; on error nothing is enqueued.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -142,8 +143,11 @@ int validate(const rcbf_params* p) {
     if (p->hadamard_order) {
         if (p->hadamard_order != p->n_tx)
             return set_error(RCBF_EINVAL, "rcbf_plan: hadamard_order must equal n_tx");
-        if (p->decoded_dtype == RCBF_CF32)
-            return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: complex data cannot be Hadamard-decoded");
+        if (p->decoded_dtype == RCBF_CF32 && p->demod_decimation == 0)
+            return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: complex data is Hadamard-decoded only after rcbf_demodulate "
+                                                "(demod_decimation > 0)");
+        if (p->demod_decimation && p->decoded_dtype != RCBF_CF32)
+            return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: demodulated data decodes to RCBF_CF32");
         if (!p->decode_matrix && !is_pow2(p->n_tx))
             return set_error(RCBF_EINVAL, "rcbf_plan: a Sylvester order must be a power of two");
         if (p->decode_variant != RCBF_DECODE_PLAIN && !(p->n_tx == 32 || p->n_tx == 64 || p->n_tx == 128 || p->n_tx == 256))
@@ -155,6 +159,21 @@ int validate(const rcbf_params* p) {
                 if (p->decode_matrix[q] != 1 && p->decode_matrix[q] != -1)
                     return set_error(RCBF_EINVAL, "rcbf_plan: decode_matrix entries must be +1 or -1");
     }
+    if (p->demod_decimation) {
+        if (p->demod_decimation > 16) return set_error(RCBF_EINVAL, "rcbf_plan: demod_decimation must be in [1, 16]");
+        if (!p->demod_taps || p->demod_n_taps < 1 || p->demod_n_taps > 1024)
+            return set_error(RCBF_EINVAL, "rcbf_plan: demodulation needs 1..1024 taps (demod_taps, demod_n_taps)");
+        if (p->demod_shift < 0 || p->demod_shift > 30)
+            return set_error(RCBF_EINVAL, "rcbf_plan: demod_shift must be in [0, 30]");
+        long long l1 = 0;
+        for (uint32_t k = 0; k < p->demod_n_taps; ++k) l1 += std::llabs((long long)p->demod_taps[k]);
+        if (l1 > 65535) return set_error(RCBF_EINVAL, "rcbf_plan: sum |taps| must be <= 65535");
+        if ((double)p->n_samples * p->demod_decimation > (double)(1u << 24))
+            return set_error(RCBF_EINVAL, "rcbf_plan: raw trace too long");
+    }
+    if (!(p->iq_freq >= 0.0)) return set_error(RCBF_EINVAL, "rcbf_plan: iq_freq must be >= 0");
+    if (p->iq_freq > 0.0 && p->decoded_dtype != RCBF_CF32)
+        return set_error(RCBF_EINVAL, "rcbf_plan: IQ beamforming (iq_freq > 0) needs RCBF_CF32 data");
     const bool tile_given = p->tile[0] || p->tile[1] || p->tile[2];
     if (tile_given) {
         if (!(p->tile[0] == 32 || p->tile[0] == 64 || p->tile[0] == 128) ||
@@ -226,6 +245,7 @@ void setup_geometry(PlanHost& h) {
     a.rx_e0 = -0.5 * (double)(p.n_ch - 1) * p.rx_pitch;
     a.fs = p.fs;
     a.f_number = (float)p.f_number;
+    a.iq_ratio = p.iq_freq / p.fs;
     a.interp = (int)p.interp;
     a.dtype = (int)p.decoded_dtype;
     a.scale = p.decoded_dtype == RCBF_I32 ? 1.0f / (float)p.n_tx : 1.0f;
@@ -318,6 +338,7 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
     PlanHost& h = plan->h;
     h.p = *params;
     h.p.decode_matrix = nullptr;   // the matrix is copied, never referenced later
+    h.p.demod_taps = nullptr;      // so are the taps
     const rcbf_params& p = h.p;
 
     setup_geometry(h);
@@ -334,6 +355,12 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
     if (cudaMalloc(&h.d_status, sizeof(int)) != cudaSuccess) return fail(RCBF_ENOMEM, "rcbf_plan: cudaMalloc status");
     if (cudaMemset(h.d_status, 0, sizeof(int)) != cudaSuccess) return fail(RCBF_ECUDA, "rcbf_plan: cudaMemset");
     a.status = h.d_status;
+    if (p.demod_decimation) {
+        const size_t bytes = (size_t)p.demod_n_taps * sizeof(int16_t);
+        if (cudaMalloc(&h.d_taps, bytes) != cudaSuccess) return fail(RCBF_ENOMEM, "rcbf_plan: cudaMalloc taps");
+        if (cudaMemcpy(h.d_taps, params->demod_taps, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(RCBF_ECUDA, "rcbf_plan: copy taps");
+    }
     if (p.hadamard_order) {
         const int n = (int)p.n_tx;
         std::vector<int8_t> H((size_t)n * n);
@@ -391,13 +418,14 @@ int rcbf_plan_query(rcbf_plan_t plan, rcbf_plan_info* info) {
     const int sp = tiled ? std::max(1, h.n_split[das_class_index(a.W)]) : 1;
     info->n_split = (uint32_t)sp;
     info->das_launches = sp > 1 ? 2u : 1u;
-    info->decode_launches = h.p.hadamard_order ? 1u : 0u;
+    info->decode_launches = h.p.hadamard_order ? (h.p.decoded_dtype == RCBF_CF32 ? 2u : 1u) : 0u;
     uint64_t bytes = sizeof(int) + h.partial_floats * sizeof(float);
     if (h.p.hadamard_order) {
         const uint64_t n = h.p.n_tx;
         bytes += n * n + n * sizeof(int);
         if (n % 32 == 0) bytes += 2 * (n / 16) * (n / 32) * 32 * 16 + (n / 16) * (n / 16) * 32 * 16 / 2;
     }
+    if (h.p.demod_decimation) bytes += (uint64_t)h.p.demod_n_taps * sizeof(int16_t);
     info->workspace_bytes = bytes;
     int mode = 0;
     DasArgs b = a;
@@ -424,7 +452,17 @@ void rcbf_destroy(rcbf_plan_t plan) {
     if (h.d_hsum) cudaFree(h.d_hsum);
     if (h.d_status) cudaFree(h.d_status);
     if (h.d_partial) cudaFree(h.d_partial);
+    if (h.d_taps) cudaFree(h.d_taps);
     delete plan;
+}
+
+int rcbf_demodulate(rcbf_plan_t plan, const int16_t* rf, int16_t* iq, void* stream) {
+    if (!plan) return set_error(RCBF_EINVAL, "rcbf_demodulate: plan is NULL");
+    const PlanHost& h = plan->h;
+    if (!h.p.demod_decimation) return set_error(RCBF_EINVAL, "rcbf_demodulate: the plan has no demodulation");
+    if (!rf || !iq) return set_error(RCBF_EINVAL, "rcbf_demodulate: NULL buffer");
+    if (!aligned16(rf) || !aligned16(iq)) return set_error(RCBF_EINVAL, "rcbf_demodulate: buffers must be 16-byte aligned");
+    return launch_demodulate(h, rf, iq, static_cast<cudaStream_t>(stream));
 }
 
 int rcbf_decode(rcbf_plan_t plan, const int16_t* rf, void* decoded, void* stream) {
@@ -469,8 +507,8 @@ int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, 
         return set_error(RCBF_EINVAL, "rcbf_das_backward: decoded must be 16-byte aligned, float buffers 4-byte aligned");
     if (h.p.decoded_dtype != RCBF_F32 && h.p.decoded_dtype != RCBF_CF32)
         return set_error(RCBF_EUNSUPPORTED, "rcbf_das_backward: decoded_dtype must be RCBF_F32 or RCBF_CF32");
-    if (h.p.interp != RCBF_LINEAR)
-        return set_error(RCBF_EUNSUPPORTED, "rcbf_das_backward: the adjoint is built for linear interpolation");
+    if (h.p.interp != RCBF_LINEAR || h.p.iq_freq > 0.0)
+        return set_error(RCBF_EUNSUPPORTED, "rcbf_das_backward: the adjoint is built for RF data with linear interpolation");
     const double cc = c > 0.f ? (double)c : h.p.c;
     DasArgs a;
     std::string why;

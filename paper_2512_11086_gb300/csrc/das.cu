@@ -13,8 +13,8 @@
 
 namespace rcbf {
 
-template <int VU> int configure_das_vu(int ws, bool cplx, bool cubic, int* per_sm);
-template <int VU> int launch_das_vu(const DasArgs& a, int ws, bool cplx, bool apod, bool cubic, cudaStream_t s);
+template <int VU> int configure_das_vu(int ws, bool cplx, bool cubic, bool iq, int* per_sm);
+template <int VU> int launch_das_vu(const DasArgs& a, int ws, bool cplx, bool apod, bool cubic, bool iq, cudaStream_t s);
 
 namespace {
 
@@ -42,7 +42,7 @@ __device__ __forceinline__ float plain_cubic(const void* rf, long long base, int
     return fmaf(fmaf(fmaf(a3, f, a2), f, m1), f, p1);
 }
 
-template <int DT, bool CPLX, bool CUBIC>
+template <int DT, bool CPLX, bool CUBIC, bool IQ>
 __global__ void __launch_bounds__(128)
 das_plain_kernel(DasArgs a) {
     const long long n_vox = (long long)a.n_u * a.n_v * a.n_w;
@@ -63,9 +63,19 @@ das_plain_kernel(DasArgs a) {
         dtx[i] = sqrtf(dx * dx + z * z);
     }
     float acc = 0.f, acci = 0.f;
+    // IQ phase r s = r fs/c d_tx + r fs/c d_rx - r t0 fs, each term reduced to
+    // a fraction of a cycle before the sum (the absolute terms reach ~10^2 cycles)
+    const float rk = (float)(a.iq_ratio * a.fs_over_c);
+    const double t0c = a.iq_ratio * a.t0fs;
+    const float ph_t0 = (float)(t0c - floor(t0c));
     for (int j = 0; j < a.n_ch; ++j) {
         const float dx = lat_rx - ((float)a.rx_e0 + j * (float)a.rx_pitch);
         const float drx = sqrtf(dx * dx + z * z);
+        float ph_rx = 0.f;
+        if (IQ) {
+            const float prx = rk * drx;
+            ph_rx = prx - rintf(prx) - ph_t0;
+        }
         float w = a.apod ? __ldg(a.apod + j) : 1.0f;
         if (a.f_number > 0.f) {
             const float al = a.f_number * fabsf(dx), az = fabsf(z);
@@ -79,20 +89,33 @@ das_plain_kernel(DasArgs a) {
             const float f = s - fl;
             const int n = (int)fl;
             const long long base = ((long long)i * a.n_ch + j) * a.n_s;
+            float vr, vi = 0.f;
             if (CUBIC) {
-                acc += w * plain_cubic<DT>(a.rf, base, n, f, a.n_s, a.scale);
-                if (CPLX) acci += w * plain_cubic<DT>(a.rf, a.plane_stride + base, n, f, a.n_s, a.scale);
-                continue;
+                vr = plain_cubic<DT>(a.rf, base, n, f, a.n_s, a.scale);
+                if (CPLX) vi = plain_cubic<DT>(a.rf, a.plane_stride + base, n, f, a.n_s, a.scale);
+            } else {
+                const bool in0 = n >= 0 && n < a.n_s, in1 = n + 1 >= 0 && n + 1 < a.n_s;
+                const float r0 = in0 ? plain_load<DT>(a.rf, base + n, a.scale) : 0.f;
+                const float r1 = in1 ? plain_load<DT>(a.rf, base + n + 1, a.scale) : 0.f;
+                vr = (1.0f - f) * r0 + f * r1;
+                if (CPLX) {
+                    const float i0 = in0 ? plain_load<DT>(a.rf, a.plane_stride + base + n, a.scale) : 0.f;
+                    const float i1 = in1 ? plain_load<DT>(a.rf, a.plane_stride + base + n + 1, a.scale) : 0.f;
+                    vi = (1.0f - f) * i0 + f * i1;
+                }
             }
-            const bool in0 = n >= 0 && n < a.n_s, in1 = n + 1 >= 0 && n + 1 < a.n_s;
-            const float r0 = in0 ? plain_load<DT>(a.rf, base + n, a.scale) : 0.f;
-            const float r1 = in1 ? plain_load<DT>(a.rf, base + n + 1, a.scale) : 0.f;
-            acc += w * ((1.0f - f) * r0 + f * r1);
-            if (CPLX) {
-                const float i0 = in0 ? plain_load<DT>(a.rf, a.plane_stride + base + n, a.scale) : 0.f;
-                const float i1 = in1 ? plain_load<DT>(a.rf, a.plane_stride + base + n + 1, a.scale) : 0.f;
-                acci += w * ((1.0f - f) * i0 + f * i1);
+            if (IQ) {
+                const float ptx = rk * dtx[i];
+                float x = (ptx - rintf(ptx)) + ph_rx;
+                x -= rintf(x);
+                float sn, cs;
+                __sincosf(6.28318530717958648f * x, &sn, &cs);
+                const float r0 = vr * cs - vi * sn;
+                vi = fmaf(vr, sn, vi * cs);
+                vr = r0;
             }
+            acc += w * vr;
+            if (CPLX) acci += w * vi;
         }
     }
     const long long o = (long long)iw * a.out_sw + (long long)iv * a.out_sv + (long long)iu * a.out_su;
@@ -118,13 +141,16 @@ int launch_das_plain(const PlanHost& h, const DasArgs& a, cudaStream_t s) {
     (void)h;
     const long long n_vox = (long long)a.n_u * a.n_v * a.n_w;
     const unsigned grid = (unsigned)((n_vox + 127) / 128);
-#define RCBF_PLAIN(CU)                                                                      \
-    switch (a.dtype) {                                                                      \
-        case RCBF_F32: das_plain_kernel<RCBF_F32, false, CU><<<grid, 128, 0, s>>>(a); break;  \
-        case RCBF_F16: das_plain_kernel<RCBF_F16, false, CU><<<grid, 128, 0, s>>>(a); break;  \
-        case RCBF_I32: das_plain_kernel<RCBF_I32, false, CU><<<grid, 128, 0, s>>>(a); break;  \
-        case RCBF_CF32: das_plain_kernel<RCBF_F32, true, CU><<<grid, 128, 0, s>>>(a); break;  \
-        default: return set_error(RCBF_EUNSUPPORTED, "das: unsupported decoded dtype");     \
+#define RCBF_PLAIN(CU)                                                                             \
+    switch (a.dtype) {                                                                             \
+        case RCBF_F32: das_plain_kernel<RCBF_F32, false, CU, false><<<grid, 128, 0, s>>>(a); break;  \
+        case RCBF_F16: das_plain_kernel<RCBF_F16, false, CU, false><<<grid, 128, 0, s>>>(a); break;  \
+        case RCBF_I32: das_plain_kernel<RCBF_I32, false, CU, false><<<grid, 128, 0, s>>>(a); break;  \
+        case RCBF_CF32:                                                                            \
+            if (a.iq_ratio > 0.0) das_plain_kernel<RCBF_F32, true, CU, true><<<grid, 128, 0, s>>>(a); \
+            else das_plain_kernel<RCBF_F32, true, CU, false><<<grid, 128, 0, s>>>(a);               \
+            break;                                                                                 \
+        default: return set_error(RCBF_EUNSUPPORTED, "das: unsupported decoded dtype");            \
     }
     if (a.interp == RCBF_CUBIC) { RCBF_PLAIN(true) } else { RCBF_PLAIN(false) }
 #undef RCBF_PLAIN
@@ -189,14 +215,15 @@ int launch_das(const PlanHost& h, const DasArgs& a_in, cudaStream_t s) {
     const bool cplx = a.dtype == RCBF_CF32;
     const bool apod = a.apod != nullptr || a.f_number > 0.f;
     const bool cubic = a.interp == RCBF_CUBIC;
+    const bool iq = cplx && a.iq_ratio > 0.0;
     a.n_split = std::max(1, h.n_split[class_index(ws)]);
     a.partial = h.d_partial;
     a.partial_stride = a.image_plane * (cplx ? 2 : 1);
     int rc;
     switch (h.vu) {
-        case 1: rc = launch_das_vu<1>(a, ws, cplx, apod, cubic, s); break;
-        case 2: rc = launch_das_vu<2>(a, ws, cplx, apod, cubic, s); break;
-        default: rc = launch_das_vu<4>(a, ws, cplx, apod, cubic, s); break;
+        case 1: rc = launch_das_vu<1>(a, ws, cplx, apod, cubic, iq, s); break;
+        case 2: rc = launch_das_vu<2>(a, ws, cplx, apod, cubic, iq, s); break;
+        default: rc = launch_das_vu<4>(a, ws, cplx, apod, cubic, iq, s); break;
     }
     if (rc != RCBF_OK || a.n_split == 1) return rc;
     const long long n = a.partial_stride;
@@ -210,6 +237,7 @@ int configure_das(PlanHost& h) {
     if (h.p.das_variant == RCBF_DAS_PLAIN || !h.tiled_ok) return RCBF_OK;
     const bool cplx = h.p.decoded_dtype == RCBF_CF32;
     const bool cubic = h.p.interp == RCBF_CUBIC;
+    const bool iq = cplx && h.p.iq_freq > 0.0;
     for (int c = 0; c < 3; ++c) {
         const int ws = c == 0 ? 48 : c == 1 ? 64 : 128;
         int rc, n = 0;
@@ -219,9 +247,9 @@ int configure_das(PlanHost& h) {
             continue;
         }
         switch (h.vu) {
-            case 1: rc = configure_das_vu<1>(ws, cplx, cubic, &n); break;
-            case 2: rc = configure_das_vu<2>(ws, cplx, cubic, &n); break;
-            default: rc = configure_das_vu<4>(ws, cplx, cubic, &n); break;
+            case 1: rc = configure_das_vu<1>(ws, cplx, cubic, iq, &n); break;
+            case 2: rc = configure_das_vu<2>(ws, cplx, cubic, iq, &n); break;
+            default: rc = configure_das_vu<4>(ws, cplx, cubic, iq, &n); break;
         }
         if (rc != RCBF_OK) return rc;
         h.das_blocks_per_sm[c] = n;

@@ -25,6 +25,13 @@
 // with the central-difference slopes m_k = (r[k+1] - r[k-1]) / 2; the inner
 // loop takes f from the same rounding of t (one 16-byte load, three FMAs).
 //
+// IQ beamforming (IQ, complex data demodulated at f_d): each interpolated
+// baseband sample is multiplied by e^{j 2 pi r s}, r = f_d / f_s, s the
+// absolute fractional sample. Per window the phase of its start, frac(r S0),
+// is taken in FP64 when the window is rewritten; per term the phase is
+// frac(that + r u) (u the window-relative position), and the rotation is one
+// sincos and a complex product.
+//
 // Windows. Every (i, j) trace is read only inside the window
 // [K_i + K_j + lo, K_i + K_j + lo + W] that the tile can reach (W from the
 // tile radius, a 1-Lipschitz bound of the distances). The 1-D TMA bulk engine
@@ -83,7 +90,8 @@ struct DasCfg {
     static constexpr int OFF_RX = OFF_TX + kMaxOrder * 16;             // float4[kMaxChannels]
     static constexpr int OFF_ALPHA = OFF_RX + kMaxChannels * 16;       // float[NB][CI][ROWS]
     static constexpr int OFF_WOFF = OFF_ALPHA + NB * ALPHA_N * 4;      // int[2][NWIN]
-    static constexpr int OFF_BAR = OFF_WOFF + 2 * NWIN * 4;            // uint64[10]
+    static constexpr int OFF_WPH = OFF_WOFF + 2 * NWIN * 4;            // float[NB][NWIN]: IQ window phases
+    static constexpr int OFF_BAR = ((OFF_WPH + NB * NWIN * 4 + 7) / 8) * 8;   // uint64[10]
     static constexpr int OFF_ABORT = OFF_BAR + 80;                     // int: a bounded wait expired
     static constexpr int SMEM = OFF_ABORT + 16;
     static_assert(ALPHA_N <= kDasThreads, "one thread per transmit term");
@@ -242,9 +250,11 @@ __device__ __forceinline__ void das_pipe_init(unsigned char* bar_base, volatile 
 
 // One work unit. Returns false when a bounded wait expired (the CTA must
 // stop; the caller records the status).
-template <int VU, int WS, bool CPLX, bool APOD, bool CUBIC = false>
+template <int VU, int WS, bool CPLX, bool APOD, bool CUBIC = false, bool IQ = false>
 __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned char* smem, DasPipe& pipe) {
     using C = DasCfg<VU, WS, CPLX, CUBIC>;
+    static_assert(!IQ || CPLX, "IQ beamforming reads two planes");
+    float* s_wph = reinterpret_cast<float*>(smem + C::OFF_WPH);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float4* s_tx = reinterpret_cast<float4*>(smem + C::OFF_TX);
     float4* s_rx = reinterpret_cast<float4*>(smem + C::OFF_RX);
@@ -384,6 +394,16 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             rewrite_windows<int, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
         else
             rewrite_windows<float, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
+        if (IQ && tid < C::NWIN) {
+            // phase (in cycles) of the window's reference position: the sample
+            // at u = 0 is S0 + 0.5 + H for linear pieces; cubic positions
+            // already include 0.5 + H
+            const int win = tid;
+            const int i = (s % n_ic) * C::CI + win / C::CJ, j = (jc0 + s / n_ic) * C::CJ + win % C::CJ;
+            const int S0 = __float_as_int(s_tx[i].w) + __float_as_int(s_rx[j].w) + a.lo;
+            const double x = a.iq_ratio * ((double)S0 + (CUBIC ? 0.0 : 0.5 + (double)a.H));
+            s_wph[pb * C::NWIN + win] = (float)(x - floor(x));
+        }
         const int ae = (tid + kDasThreads - (s * C::ALPHA_N + kDasThreads / 2) % kDasThreads) % kDasThreads;
         if (ae < C::ALPHA_N) {
             // transmit terms of this stage for every tile row (alpha depends on the row only)
@@ -413,6 +433,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     const float magic = CUBIC ? 8388607.5f : 8388608.0f + (float)a.H;     // 2^23 + H (cubic: on u + 0.5 + H)
     const f2x magic2 = pk(magic, magic);
     constexpr int SHIFT = C::SHIFT;
+    const float iqr = (float)a.iq_ratio;
 
     // ---- prologue: stages 0 and 1 in flight, stage 0 rewritten
     bool ok = issue(0);
@@ -469,6 +490,16 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             static_for<0, C::CJ>([&](auto jjc) {
                 constexpr int jj = decltype(jjc)::value;
                 constexpr int OFF = jj * WS * C::PAIR_BYTES;
+                const float phw = IQ ? s_wph[pb * C::NWIN + ii * C::CJ + jj] : 0.0f;
+                // e^{j 2 pi (phw + r u)} applied to (vr, vi)
+                auto iq_rotate = [&](float uu, float& vr, float& vi) {
+                    const float x = fmaf(iqr, uu, phw);
+                    float sn, cs;
+                    __sincosf(6.28318530717958648f * (x - rintf(x)), &sn, &cs);
+                    const float r0 = vr * cs - vi * sn;
+                    vi = fmaf(vr, sn, vi * cs);
+                    vr = r0;
+                };
 #pragma unroll
                 for (int kp = 0; kp < 2; ++kp) {
                     const f2x u2 = add2(al2[kp], beta2[kp][jj]);
@@ -491,6 +522,10 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
                                 const float4 q = lds_f4<OFF + 16>(addr);
                                 vi[h] = fmaf(fmaf(fmaf(q.w, f[h], q.z), f[h], q.y), f[h], q.x);
                             }
+                        }
+                        if (IQ) {
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) iq_rotate(u[h], vr[h], vi[h]);
                         }
                         if (CPLX) {
 #pragma unroll
@@ -516,7 +551,8 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
                             const int k = 2 * kp + h;
                             const uint32_t addr = (__float_as_uint(t[h]) << SHIFT) + pb_ii;
                             const float4 p = lds_f4<OFF>(addr);
-                            const float vr = fmaf(u[h], p.y, p.x), vi = fmaf(u[h], p.w, p.z);
+                            float vr = fmaf(u[h], p.y, p.x), vi = fmaf(u[h], p.w, p.z);
+                            if (IQ) iq_rotate(u[h], vr, vi);
                             float ar, ai;
                             upk(acc2[kp], ar, ai);
                             float wr = 1.f, wi = 1.f;

@@ -301,6 +301,17 @@ int launch_plain(const DecodeArgs& a, cudaStream_t s) {
 }  // namespace
 
 int launch_decode(const PlanHost& h, const int16_t* rf, void* out, cudaStream_t s) {
+    if (h.p.decoded_dtype == RCBF_CF32) {
+        // demodulated data: each int16 plane decodes to its FP32 plane (D / N)
+        PlanHost hp = h;
+        hp.p.decoded_dtype = RCBF_F32;
+        const long long plane = (long long)h.p.n_tx * h.p.n_ch * h.p.n_samples;
+        for (int p = 0; p < 2; ++p) {
+            const int rc = launch_decode(hp, rf + p * plane, static_cast<float*>(out) + p * plane, s);
+            if (rc != RCBF_OK) return rc;
+        }
+        return RCBF_OK;
+    }
     DecodeArgs a;
     a.rf = rf;
     a.out = out;
@@ -333,7 +344,7 @@ int configure_decode(PlanHost& h) {
     if (h.p.hadamard_order == 0 || h.p.decode_variant == RCBF_DECODE_PLAIN) return RCBF_OK;
     const int n = (int)h.p.n_tx;
     const bool f16 = h.p.decode_variant == RCBF_DECODE_MMA_F16;
-    switch (h.p.decoded_dtype) {
+    switch (h.p.decoded_dtype == RCBF_CF32 ? RCBF_F32 : h.p.decoded_dtype) {
         case RCBF_I32: return f16 ? configure_dt<RCBF_I32, true>(n, &h.decode_blocks_per_sm)
                                   : configure_dt<RCBF_I32, false>(n, &h.decode_blocks_per_sm);
         case RCBF_F32: return f16 ? configure_dt<RCBF_F32, true>(n, &h.decode_blocks_per_sm)

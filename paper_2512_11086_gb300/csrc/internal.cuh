@@ -42,6 +42,7 @@ struct DasArgs {
     double t0fs;           // t0 * fs (samples)
     double c;              // speed of sound of this call
     double fs;
+    double iq_ratio;       // iq_freq / fs: IQ beamforming phase per sample (0 = RF data)
     float f_number;
     int interp;            // rcbf_interp
     int W;                 // pairs per window actually used (<= compiled stride)
@@ -100,6 +101,7 @@ struct PlanHost {
     int n_split[3];         // channel split by window stride class
     float* d_partial;       // DAS partial images (channel split), plan-owned
     size_t partial_floats;
+    int16_t* d_taps;        // device demodulation FIR taps (demod_decimation > 0)
     // adjoint tile with lanes over z: 32 voxels along u by bwd_bv x bwd_bw
     // rows (bwd_bv = 0: no such tile keeps the window within 128 samples)
     int bwd_bv, bwd_bw;
@@ -131,6 +133,7 @@ int das_prepare_tile(const PlanHost& h, double c, int bu, int bv, int bw, double
 
 // Kernel launchers (one per translation unit).
 int launch_decode(const PlanHost& h, const int16_t* rf, void* out, cudaStream_t s);
+int launch_demodulate(const PlanHost& h, const int16_t* rf, int16_t* iq, cudaStream_t s);
 int launch_das(const PlanHost& h, const DasArgs& a, cudaStream_t s);
 int launch_das_plain(const PlanHost& h, const DasArgs& a, cudaStream_t s);
 // mode: 0 plain, 1 tiled with the plan's tile (lanes along u), 2 tiled with
