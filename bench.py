@@ -230,6 +230,8 @@ OTHER_WORKLOADS = {
               "512x1024 grids, 16 cross-plane pairs) in one persistent launch",
     "autofocus": "differentiable DAS: complex 128 tx x 128 ch x 2048 decoded RF -> 256x512 image, "
                  "forward + adjoint (dRF, dc, dw) per step",
+    "iq": "IQ pipeline: FORCES 128 tx x 128 ch x 4096 int16 at 4 f_d -> quadrature demodulation (166-tap "
+          "integer FIR, decimation 4) -> exact decode of both planes -> cubic IQ DAS to 512x1024 (complex)",
 }
 
 
@@ -282,6 +284,40 @@ def run_other_workload(args):
         step = graph.replay
         sums = sum(f.geometry.sums for f in frames)
         extra["tiles"] = sorted({tuple(t) for t in tiles})
+    elif args.workload == "iq":
+        fr = synth.full_bscan(2)
+        g_raw = fr.geometry
+        D, taps, shift = 4, synth.lowpass_taps(166, 0.12, shift=14), 14
+        gd = (taps.size - 1) / 2
+        g = dataclasses.replace(g_raw, n_samples=g_raw.n_samples // D, fs=g_raw.fs / D,
+                                t0=g_raw.t0 - gd / g_raw.fs, iq_freq=g_raw.fs / 4, interp="cubic")
+        plan = rc.Plan(rc.make_params(g, decoded_dtype="cf32", demod=(D, taps, shift)))
+        rf = torch.from_numpy(fr.rf).to(dev)
+        iq = torch.empty((2,) + plan.rf_shape, dtype=torch.int16, device=dev)
+        dec = torch.empty((2,) + plan.rf_shape, dtype=torch.float32, device=dev)
+        out = torch.empty((2,) + plan.image_shape, device=dev)
+
+        def step():
+            plan.demodulate(rf, out=iq)
+            plan.decode(iq, out=dec)
+            plan.das(dec, out=out)
+        sums = g.sums
+        for _ in range(3):
+            step()
+        ev = _events(4)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        plan.demodulate(rf, out=iq)
+        ev[1].record(stream)
+        plan.decode(iq, out=dec)
+        ev[2].record(stream)
+        plan.das(dec, out=out)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        extra["stage_ms"] = {"demodulate": ev[0].elapsed_time(ev[1]), "decode_two_planes": ev[1].elapsed_time(ev[2]),
+                             "iq_das_cubic": ev[2].elapsed_time(ev[3])}
+        extra["sums"] = "complex voxel x channel x transmit sums of the IQ DAS"
+        extra["plan"] = plan.info()
     else:
         fr = synth.autofocus(5)
         g = fr.geometry

@@ -7,10 +7,10 @@
 // for even n and imaginary for odd n: with e[n] = s[n] * (+1, -1, -1, +1)[n mod 4]
 // the I output sums the taps k with n - k even and the Q output the others.
 // A CTA stages the sign-mixed samples of one trace segment in shared memory
-// (kDemodOut outputs need kDemodOut * D + N_f samples, loaded and converted
-// once, zero outside the record: the paper's LDS reuse) and every thread
-// computes four outputs, sharing each tap load between them. Accumulation is
-// exact in 32 bits (sum |h| <= 65535 is checked at plan time).
+// (kDemodOut outputs need about kDemodOut * D + N_f samples, loaded and
+// converted once, zero outside the record: the paper's LDS reuse) and every
+// thread computes four outputs, sharing each tap load between them.
+// Accumulation is exact in 32 bits (sum |h| <= 65535 is checked at plan time).
 #include "internal.cuh"
 
 namespace rcbf {
@@ -32,18 +32,23 @@ __device__ __forceinline__ int16_t round_shift_sat(int acc, int shift) {
     return (int16_t)max(-32768, min(32767, q));
 }
 
+// Shared layout (polyphase): the staged samples e[p] (p from the segment's
+// first needed input) are stored as D rows, e_ph[p mod D][p / D], so that for
+// a tap k = a D + b the 32 threads of a warp (consecutive outputs, inputs D
+// apart) read consecutive words of one row: no bank conflicts.
 // grid: (traces, segments of kDemodOut outputs)
 __global__ void __launch_bounds__(kDemodThreads)
 demod_kernel(const int16_t* __restrict__ rf, int16_t* __restrict__ iq, const int16_t* __restrict__ taps,
-             int n_taps, int shift, int D, long long n_in, long long n_out, long long n_traces) {
+             int n_taps, int shift, int D, int Q, long long n_in, long long n_out, long long n_traces) {
     extern __shared__ int sm[];
     const int n_taps2 = (n_taps + 1) & ~1;                     // even, zero-padded
+    const int PD = (n_taps2 - 1 + D - 1) / D;                  // rows of history before the first output
     int* h = sm;                                               // [n_taps2]
-    int* e = sm + n_taps2;                                     // sign-mixed samples
+    int* e_ph = sm + n_taps2;                                  // [D][Q]
     const long long tr = blockIdx.x;
     const long long m0 = (long long)blockIdx.y * kDemodOut;
-    const long long base = m0 * D - (n_taps2 - 1);             // input index of e[0]
-    const int L = (kDemodOut - 1) * D + n_taps2;
+    const long long base = (m0 - PD) * D;                      // input index of e[0]
+    const int L = (kDemodOut + PD) * D;                        // staged samples, D * (rows used)
     const int16_t* x = rf + tr * n_in;
     for (int k = threadIdx.x; k < n_taps2; k += kDemodThreads) h[k] = k < n_taps ? (int)taps[k] : 0;
     for (int p = threadIdx.x; p < L; p += kDemodThreads) {
@@ -52,26 +57,34 @@ demod_kernel(const int16_t* __restrict__ rf, int16_t* __restrict__ iq, const int
         if (n >= 0 && n < n_in) {
             v = (int)x[n];
             const int r = (int)(n & 3);
-            if (r == 1 || r == 2) v = -v;
+            if (r == 1 || r == 2) v = -v;                      // mixer 1, -j, -1, j: real / imaginary sign
         }
-        e[p] = v;
+        e_ph[(p % D) * Q + p / D] = v;
     }
     __syncthreads();
-    // output m = m0 + t + 256 r reads e at (m - m0) D + (n_taps2 - 1) - k
+    // output m (local index mi = m - m0) and tap k = a D + b read
+    // e[(mi + PD) D - k] = e_ph[b ? D - b : 0][mi + PD - a - (b ? 1 : 0)]
     int acc_even[kDemodPer], acc_odd[kDemodPer];
-    int pos[kDemodPer];
 #pragma unroll
-    for (int r = 0; r < kDemodPer; ++r) {
-        acc_even[r] = 0;
-        acc_odd[r] = 0;
-        pos[r] = (threadIdx.x + kDemodThreads * r) * D + (n_taps2 - 1);
-    }
-    for (int k = 0; k < n_taps2; k += 2) {
-        const int h0 = h[k], h1 = h[k + 1];
+    for (int r = 0; r < kDemodPer; ++r) acc_even[r] = acc_odd[r] = 0;
+    const int astep = (D & 1) ? 2 : 1;                         // odd D: the parity of k alternates with a
+    for (int b = 0; b < D; ++b) {
+        const int* row = e_ph + (b ? D - b : 0) * Q + PD - (b ? 1 : 0) + threadIdx.x;
+        for (int a0 = 0; a0 < astep; ++a0) {
+            int acc[kDemodPer];
 #pragma unroll
-        for (int r = 0; r < kDemodPer; ++r) {
-            acc_even[r] += h0 * e[pos[r] - k];          // n - k with k even
-            acc_odd[r] += h1 * e[pos[r] - k - 1];       // k odd
+            for (int r = 0; r < kDemodPer; ++r) acc[r] = 0;
+            for (int a = a0; a * D + b < n_taps2; a += astep) {
+                const int hk = h[a * D + b];
+#pragma unroll
+                for (int r = 0; r < kDemodPer; ++r) acc[r] += hk * row[kDemodThreads * r - a];
+            }
+            const bool odd = ((a0 * D + b) & 1) != 0;         // parity of every k of this loop
+#pragma unroll
+            for (int r = 0; r < kDemodPer; ++r) {
+                acc_even[r] += odd ? 0 : acc[r];
+                acc_odd[r] += odd ? acc[r] : 0;
+            }
         }
     }
 #pragma unroll
@@ -94,11 +107,13 @@ int launch_demodulate(const PlanHost& h, const int16_t* rf, int16_t* iq, cudaStr
     const long long n_out = h.p.n_samples, n_in = n_out * D;
     const long long n_traces = (long long)h.p.n_tx * h.p.n_ch;
     const int n_taps2 = (n_taps + 1) & ~1;
-    const size_t smem = (size_t)(n_taps2 + (kDemodOut - 1) * D + n_taps2) * sizeof(int);
+    const int PD = (n_taps2 - 1 + D - 1) / D;
+    const int Q = (kDemodOut + PD) | 1;          // row length (odd: rows start in different banks)
+    const size_t smem = (size_t)(n_taps2 + D * Q) * sizeof(int);
     if (cudaFuncSetAttribute(demod_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return check_launch("demodulate: set shared memory");
     dim3 grid((unsigned)n_traces, (unsigned)((n_out + kDemodOut - 1) / kDemodOut));
-    demod_kernel<<<grid, kDemodThreads, smem, s>>>(rf, iq, h.d_taps, n_taps, (int)h.p.demod_shift, D, n_in,
+    demod_kernel<<<grid, kDemodThreads, smem, s>>>(rf, iq, h.d_taps, n_taps, (int)h.p.demod_shift, D, Q, n_in,
                                                     n_out, n_traces);
     return check_launch("demod_kernel");
 }

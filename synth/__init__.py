@@ -189,6 +189,15 @@ def make_frame(g: Geometry, seed: int, n_scatterers: int,
     return Frame(g, None, dec, sc, seed)
 
 
+def lowpass_taps(n_taps: int, cutoff: float, shift: int = 15) -> np.ndarray:
+    """Demodulation filter input: Hann-windowed sinc low-pass with cutoff in
+    cycles per raw sample, unit DC gain in Q(shift), rounded to int16."""
+    k = np.arange(n_taps) - (n_taps - 1) / 2
+    h = np.sinc(2 * cutoff * k) * np.hanning(n_taps + 2)[1:-1]
+    h = h / h.sum() * (1 << shift)
+    return np.round(h).astype(np.int16)
+
+
 # ---------------------------------------------------------------------------
 # Workloads of the paper's configurations (sizes as the build's configs state;
 # grid extents and unstated constants as read in the design notes).

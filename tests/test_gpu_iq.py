@@ -29,12 +29,7 @@ def _dev():
     torch.cuda.set_device(0)
 
 
-def _lowpass_taps(n_taps, cutoff, shift=15):
-    """Hann-windowed sinc low-pass, unit DC gain in Q(shift), int16."""
-    k = np.arange(n_taps) - (n_taps - 1) / 2
-    h = np.sinc(2 * cutoff * k) * np.hanning(n_taps + 2)[1:-1]
-    h = h / h.sum() * (1 << shift)
-    return np.round(h).astype(np.int16)
+_lowpass_taps = synth.lowpass_taps
 
 
 def _geom(n_tx, n_ch, n_s, **kw):
