@@ -167,6 +167,7 @@ typedef struct rcbf_params {
 
 typedef struct rcbf_plan_s*  rcbf_plan_t;
 typedef struct rcbf_batch_s* rcbf_batch_t;
+typedef struct rcbf_pipeline_s* rcbf_pipeline_t;
 
 /* rcbf_plan — validate `params`, copy it, build the device decode tables and
  * pick the DAS tile. Allocates a few KB of device memory on the current
@@ -315,6 +316,40 @@ int rcbf_batch_set_wait(rcbf_batch_t batch, uint64_t wait_ns, int32_t withhold_f
 
 /* rcbf_batch_destroy — free the batch's device work list. NULL is accepted. */
 void rcbf_batch_destroy(rcbf_batch_t batch);
+
+/* rcbf_pipeline_create — the upload ring of §OPTIMIZATIONS "Data Transfer"
+ * (several frames in flight so that uploads never stall the GPU):
+ * n_slots (2..8; the paper keeps 3) sets of device buffers for a batch of
+ * n_frames frames, each set bound to its own rcbf_batch (plans validated as
+ * for rcbf_batch_create) and captured once as a CUDA graph, plus three streams
+ * (host->device copies, compute, device->host copies). Allocates the buffers
+ * and synchronises once. The plans must outlive the pipeline.
+ * Errors: RCBF_EINVAL, RCBF_EUNSUPPORTED (as rcbf_batch_create), RCBF_ENOMEM, RCBF_ECUDA. */
+int rcbf_pipeline_create(const rcbf_plan_t* plans, uint32_t n_frames, uint32_t n_slots,
+                         rcbf_pipeline_t* out_pipeline);
+
+/* rcbf_pipeline_submit — one step through the next slot: copy each frame's
+ * input from host memory (encoded int16 RF [n_tx][n_ch][n_samples] for a plan
+ * with a Hadamard order, else the decoded data of the plan's dtype), run the
+ * batch, and copy each image [nz][ny][nx] back to host_images[f]. Returns
+ * once the work is enqueued; the copies of one step overlap the compute of
+ * the step before. Before reusing a slot the call waits on the host until
+ * that slot's previous step has finished (so at most n_slots steps are in
+ * flight) and folds its batch status into the pipeline's status. Host
+ * buffers (arrays of HOST pointers, one per frame) must stay valid and
+ * unchanged until the step completes; page-locked memory makes the copies
+ * asynchronous (pageable memory works but serialises them).
+ * Errors: RCBF_EINVAL, RCBF_ECUDA. */
+int rcbf_pipeline_submit(rcbf_pipeline_t pipeline, const void* const* host_inputs, float* const* host_images);
+
+/* rcbf_pipeline_wait — wait for every submitted step; RCBF_ETIMEOUT if the
+ * bounded per-frame wait of any step's batch expired since the last call
+ * (the status is then cleared). Errors: RCBF_EINVAL, RCBF_ECUDA, RCBF_ETIMEOUT. */
+int rcbf_pipeline_wait(rcbf_pipeline_t pipeline);
+
+/* rcbf_pipeline_destroy — wait for the pipeline, then free its buffers,
+ * batches, graphs, events and streams. NULL is accepted. */
+void rcbf_pipeline_destroy(rcbf_pipeline_t pipeline);
 
 /* rcbf_das_noalloc — rcbf_das without a plan, for callers that must not
  * allocate device memory: code that owns every device allocation through its

@@ -85,6 +85,10 @@ SIGNATURES = {
     "rcbf_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_uint32, ctypes.POINTER(_P),
                                          ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
     "rcbf_batch_run": (ctypes.c_int, [_P, _P]),
+    "rcbf_pipeline_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_P)]),
+    "rcbf_pipeline_submit": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "rcbf_pipeline_wait": (ctypes.c_int, [_P]),
+    "rcbf_pipeline_destroy": (None, [_P]),
     "rcbf_batch_status": (ctypes.c_int, [_P, _P]),
     "rcbf_batch_set_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int32]),
     "rcbf_batch_destroy": (None, [_P]),
@@ -275,6 +279,53 @@ class Plan:
                                                 _ptr(grad_image), _ptr(grad_rf), _ptr(grad_c),
                                                 _ptr(grad_apod), _stream(stream)))
         return grad_rf, grad_c, grad_apod
+
+
+class Pipeline:
+    """Owns an ``rcbf_pipeline_t``: the upload ring. ``submit`` takes per-frame
+    host tensors (inputs: int16 RF for encoded plans, else decoded data;
+    outputs: float32 images), enqueues upload, batch and read-back, and returns
+    at once; ``wait`` blocks until every submitted step is done."""
+
+    def __init__(self, plans: Sequence["Plan"], n_slots: int = 3):
+        lib = load_library()
+        n = len(plans)
+        self._plans = list(plans)
+        self._n = n
+        hp = (_P * n)(*[p.handle for p in plans])
+        h = _P()
+        _check(lib.rcbf_pipeline_create(hp, n, int(n_slots), ctypes.byref(h)))
+        self.handle = h
+        self._held = []            # host tensors of steps in flight
+
+    def submit(self, host_inputs, host_images):
+        if len(host_inputs) != self._n or len(host_images) != self._n:
+            raise ValueError("one input and one image per frame")
+        for t in list(host_inputs) + list(host_images):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError("host buffers must be contiguous CPU tensors")
+        ins = (_P * self._n)(*[_P(t.data_ptr()) for t in host_inputs])
+        outs = (_P * self._n)(*[_P(t.data_ptr()) for t in host_images])
+        self._held.append((list(host_inputs), list(host_images)))
+        _check(load_library().rcbf_pipeline_submit(self.handle, ins, outs))
+
+    def wait(self):
+        try:
+            _check(load_library().rcbf_pipeline_wait(self.handle))
+        finally:
+            self._held.clear()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().rcbf_pipeline_destroy(self.handle)
+            self.handle = None
+            self._held.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

@@ -43,6 +43,10 @@ int class_of(int W) { return W <= 48 ? 48 : W <= 64 ? 64 : 128; }
 
 }  // namespace
 
+namespace rcbf {
+int* batch_status_word(rcbf_batch_t batch) { return batch ? batch->d_counters + kBatchStatus : nullptr; }
+}  // namespace rcbf
+
 extern "C" {
 
 int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t* const* rf,

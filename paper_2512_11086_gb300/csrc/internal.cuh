@@ -133,6 +133,8 @@ int das_prepare_tile(const PlanHost& h, double c, int bu, int bv, int bw, double
 
 // Kernel launchers (one per translation unit).
 int launch_decode(const PlanHost& h, const int16_t* rf, void* out, cudaStream_t s);
+// Device address of a batch's status word (batch.cu).
+int* batch_status_word(rcbf_batch_t batch);
 int launch_demodulate(const PlanHost& h, const int16_t* rf, int16_t* iq, cudaStream_t s);
 int launch_das(const PlanHost& h, const DasArgs& a, cudaStream_t s);
 int launch_das_plain(const PlanHost& h, const DasArgs& a, cudaStream_t s);
