@@ -55,7 +55,10 @@ class _Geom(ctypes.Structure):
         ("out_min", ctypes.c_double * 3), ("out_max", ctypes.c_double * 3),
         ("voxel_transform", ctypes.c_double * 16), ("xdc_transform", ctypes.c_double * 16),
         ("interp", ctypes.c_int64), ("iq_freq", ctypes.c_double),
+        ("tx_wave", ctypes.c_int64), ("tx_focus", ctypes.c_double), ("tx_angles", ctypes.c_void_p),
     ]
+
+TX_WAVE = {"line": 0, "plane": 1, "vls": 2}
 
 INTERP = {"linear": 0, "cubic": 1}
 
@@ -94,6 +97,14 @@ def geom_from(g, c: Optional[float] = None, f_number: Optional[float] = None,
     geometry's own, else 0 = RF data)."""
     s = _Geom()
     s.iq_freq = float(iq_freq if iq_freq is not None else getattr(g, "iq_freq", 0.0))
+    s.tx_wave = TX_WAVE[getattr(g, "tx_wave", "line")]
+    s.tx_focus = float(getattr(g, "tx_focus", 0.0))
+    if s.tx_wave == 1:
+        ang = np.ascontiguousarray(getattr(g, "tx_angles"), dtype=np.float64)
+        if ang.size != int(g.n_tx):
+            raise ValueError("one plane-wave angle per transmit")
+        s._angles = ang                      # kept alive with the structure
+        s.tx_angles = ang.ctypes.data
     s.interp = INTERP[interp if interp is not None else getattr(g, "interp", "linear")]
     s.n_tx, s.n_ch, s.n_samples = int(g.n_tx), int(g.n_ch), int(g.n_samples)
     s.tx_orientation, s.rx_orientation = int(g.tx_orientation), int(g.rx_orientation)

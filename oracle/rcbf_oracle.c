@@ -40,6 +40,15 @@
  * inclusive linspace (or a 4x4 voxel-index affine), then a 4x4 world-to-array
  * affine.
  *
+ * Transmit waves (the row-column methods of §CAPABILITIES: FORCES, TPW,
+ * VLS): the transmit path of line (or wave) i to a point q is
+ *   line element     d_tx = sqrt((lat_tx(q) - e_i)^2 + q_z^2)
+ *   plane wave       d_tx = q_z cos(theta_i) + lat_tx(q) sin(theta_i)
+ *   virtual line     d_tx = f + sgn(q_z - f) sqrt((lat_tx(q) - e_i)^2 + (q_z - f)^2)
+ *                    (a line focus at depth f above line element i; sgn(0) = +1)
+ * and every one of them depends on (lat_tx, z) only, so s_ij = A_i + B_j
+ * stays separable.
+ *
  * Window reading: the window is non-zero exactly when F# |lat - e_j| < 0.5 |z|
  * (|u| < 0.5 written without a division), so a voxel at z = 0 gets weight 0.
  */
@@ -64,6 +73,9 @@ typedef struct oracle_geom {
     double xdc_transform[16];                 /* row-major, world -> array */
     int64_t interp;                           /* 0 linear, 1 cubic Hermite */
     double iq_freq;                           /* 0: RF planes; > 0: baseband IQ demodulated at this frequency */
+    int64_t tx_wave;                          /* 0 line elements, 1 plane waves, 2 virtual line sources */
+    double tx_focus;                          /* virtual line source depth f [m] */
+    const double* tx_angles;                  /* plane-wave angles theta_i [rad], n_tx of them */
 } oracle_geom;
 
 int oracle_threads(void) {
@@ -134,6 +146,20 @@ static double element_position(int64_t index, int64_t count, double pitch) {
     return ((double)index - (double)(count - 1) / 2.0) * pitch;
 }
 
+/* Transmit path of wave i to the point (lat_tx, z). */
+static double transmit_distance(const oracle_geom* g, int64_t i, double lat_tx, double z) {
+    if (g->tx_wave == 1) {
+        const double th = g->tx_angles[i];
+        return z * cos(th) + lat_tx * sin(th);
+    }
+    const double dx = lat_tx - element_position(i, g->n_tx, g->tx_pitch);
+    if (g->tx_wave == 2) {
+        const double dz = z - g->tx_focus;
+        return g->tx_focus + (dz >= 0.0 ? 1.0 : -1.0) * sqrt(dx * dx + dz * dz);
+    }
+    return sqrt(dx * dx + z * z);
+}
+
 /* Eq. (3) evaluated at u = F# |delta| / |z|, with the support test written
  * as F# |delta| < 0.5 |z|. */
 static double window_weight(double f_number, double delta, double z) {
@@ -195,8 +221,7 @@ void oracle_das(const oracle_geom* g, const double* rf, int64_t n_planes, const 
         const double lat_rx = lateral(q, g->rx_orientation);
         double acc[2] = {0.0, 0.0};
         for (int64_t i = 0; i < n_tx; ++i) {
-            const double dx_t = lat_tx - element_position(i, n_tx, g->tx_pitch);
-            const double d_tx = sqrt(dx_t * dx_t + q[2] * q[2]);
+            const double d_tx = transmit_distance(g, i, lat_tx, q[2]);
             for (int64_t j = 0; j < n_ch; ++j) {
                 const double dx_r = lat_rx - element_position(j, n_ch, g->rx_pitch);
                 const double d_rx = sqrt(dx_r * dx_r + q[2] * q[2]);
@@ -249,8 +274,7 @@ void oracle_das_grad(const oracle_geom* g, const double* rf, int64_t n_planes, c
                 voxel_position(g, v, q);
                 const double lat_tx = lateral(q, g->tx_orientation);
                 const double lat_rx = lateral(q, g->rx_orientation);
-                const double dx_t = lat_tx - element_position(i, n_tx, g->tx_pitch);
-                const double d_tx = sqrt(dx_t * dx_t + q[2] * q[2]);
+                const double d_tx = transmit_distance(g, i, lat_tx, q[2]);
                 for (int64_t j = 0; j < n_ch; ++j) {
                     const double dx_r = lat_rx - element_position(j, n_ch, g->rx_pitch);
                     const double d_rx = sqrt(dx_r * dx_r + q[2] * q[2]);

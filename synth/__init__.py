@@ -75,6 +75,9 @@ class Geometry:
     f_number: float = 0.0
     interp: str = "linear"           # sample interpolation of the beamformer: linear or cubic
     iq_freq: float = 0.0             # > 0: the beamformed data is baseband IQ demodulated at this frequency
+    tx_wave: str = "line"            # transmit wave of each transmit index: line, plane or vls
+    tx_angles: Tuple[float, ...] = ()    # plane-wave angles [rad], one per transmit
+    tx_focus: float = 0.0            # virtual line source depth [m]
 
     @property
     def n_vox(self) -> int:
@@ -102,6 +105,19 @@ def echo_sigma(fc: float) -> float:
     return 2.0 / (fc * 2.0 * math.sqrt(2.0 * math.log(2.0)))
 
 
+def _transmit_path(g: Geometry, e_tx: np.ndarray, lt: float, z: float) -> np.ndarray:
+    """Acquisition physics of each transmit wave: a line element radiates a
+    cylinder, a steered plane wave crosses the array at t = 0, a virtual line
+    source converges at depth f and diverges below it."""
+    if g.tx_wave == "plane":
+        th = np.asarray(g.tx_angles, dtype=np.float64)
+        return z * np.cos(th) + lt * np.sin(th)
+    if g.tx_wave == "vls":
+        dz = z - g.tx_focus
+        return g.tx_focus + (1.0 if dz >= 0 else -1.0) * np.sqrt((lt - e_tx) ** 2 + dz * dz)
+    return np.sqrt((lt - e_tx) ** 2 + z * z)
+
+
 def _accumulate_echoes(g: Geometry, scatterers: np.ndarray, c: float,
                        analytic: bool) -> np.ndarray:
     """Un-encoded traces r[i, j, n] (float64 or complex128) of unit-amplitude
@@ -118,7 +134,7 @@ def _accumulate_echoes(g: Geometry, scatterers: np.ndarray, c: float,
         lt = _lateral(p, g.tx_orientation)
         lr = _lateral(p, g.rx_orientation)
         z = p[2]
-        dist_tx = np.sqrt((lt - e_tx) ** 2 + z * z)          # [n_tx]
+        dist_tx = _transmit_path(g, e_tx, lt, z)             # [n_tx]
         dist_rx = np.sqrt((lr - e_rx) ** 2 + z * z)          # [n_ch]
         tau = (dist_tx[:, None] + dist_rx[None, :]) / c      # [n_tx, n_ch]
         centre = np.floor((tau - g.t0) * g.fs).astype(np.int64)

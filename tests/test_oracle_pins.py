@@ -142,6 +142,33 @@ def test_zero_outside_record():
     assert oracle.das(g, np.ones((1, 1, 10))).ravel()[0] == pytest.approx(0.5, abs=1e-12)
 
 
+# ------------------------------------------------------- transmit waves
+
+def test_transmit_waves_hand_computed_delays():
+    for x, y, z, wave, ang, focus, expect in _golden_rows("transmit_waves.txt"):
+        g = _point_geom(x * MM, y * MM, z * MM)
+        if int(wave) == 1:
+            g.tx_wave, g.tx_angles = "plane", (np.deg2rad(ang),)
+        else:
+            g.tx_wave, g.tx_focus = "vls", focus * MM
+        ramp = np.arange(g.n_samples, dtype=np.float64).reshape(1, 1, -1)
+        assert oracle.das(g, ramp).ravel()[0] == pytest.approx(expect, rel=0, abs=1e-9)
+
+
+def test_plane_wave_at_zero_angle_and_vls_on_axis_equal_depth():
+    # a 0-degree plane wave and a virtual line source directly above the point
+    # both travel exactly z on transmit (the line element too, on its axis)
+    rng = np.random.default_rng(15)
+    r = rng.normal(size=(1, 1, 1000))
+    g = _point_geom(2.5 * MM, 0.0, 7.0 * MM)
+    want = oracle.das(g, r).ravel()[0]
+    g.tx_wave, g.tx_angles = "plane", (0.0,)
+    assert oracle.das(g, r).ravel()[0] == pytest.approx(want, abs=1e-12)
+    for f in (3 * MM, 7 * MM, 11 * MM):
+        g.tx_wave, g.tx_focus = "vls", f
+        assert oracle.das(g, r).ravel()[0] == pytest.approx(want, abs=1e-12)
+
+
 # -------------------------------------------- cubic Hermite interpolation
 
 def test_cubic_weights_at_a_quarter_sample():
