@@ -96,6 +96,15 @@ enum rcbf_orientation {
     RCBF_COLUMNS = 1    /* line elements span y: lateral coordinate is x */
 };
 
+enum rcbf_tx_wave {
+    RCBF_TX_LINE  = 0,  /* line element i: d_tx = sqrt((lat_tx - e_i)^2 + z^2) */
+    RCBF_TX_PLANE = 1,  /* plane wave i: d_tx = z cos(a_i) + lat_tx sin(a_i) (crosses the array at t = 0) */
+    RCBF_TX_VLS   = 2   /* virtual line source above line i at depth f:
+                           d_tx = f + sgn(z - f) sqrt((lat_tx - e_i)^2 + (z - f)^2), sgn(0) = +1.
+                           Off axis the delay jumps at z = f, so an image whose depth range
+                           contains f runs the plain DAS form. */
+};
+
 enum rcbf_interp {
     RCBF_LINEAR = 0,    /* (1 - f) r[n] + f r[n+1] */
     RCBF_CUBIC  = 1     /* 4-point cubic Hermite spline, central-difference slopes (rcbf_das only) */
@@ -163,6 +172,13 @@ typedef struct rcbf_params {
     double   iq_freq;           /* > 0: the decoded data is baseband IQ demodulated at this frequency
                                    (RCBF_CF32 only): rcbf_das multiplies each interpolated sample by
                                    e^{j 2 pi (iq_freq / fs) s} (IQ beamforming). 0 = RF data. */
+    /* Transmit wave of each transmit index (§CAPABILITIES: FORCES / TPW / VLS row-column
+     * methods); every one keeps the delay separable (it depends on lat_tx and z only). */
+    uint32_t tx_wave;           /* enum rcbf_tx_wave */
+    uint32_t reserved3;
+    double   tx_focus;          /* RCBF_TX_VLS: depth f of the virtual line sources [m] */
+    const double* tx_angles;    /* RCBF_TX_PLANE: HOST pointer to n_tx steering angles [rad], |angle| < pi/2,
+                                   copied by rcbf_plan */
 } rcbf_params;
 
 typedef struct rcbf_plan_s*  rcbf_plan_t;

@@ -26,6 +26,8 @@ I16, I32, F32, F16, CF32 = 0, 1, 2, 3, 4
 FORCES, HERCULES = 0, 1
 ROWS, COLUMNS = 0, 1
 LINEAR, CUBIC = 0, 1
+TX_LINE, TX_PLANE, TX_VLS = 0, 1, 2
+_TX_WAVE_NAMES = {"line": TX_LINE, "plane": TX_PLANE, "vls": TX_VLS}
 _INTERP_NAMES = {"linear": LINEAR, "cubic": CUBIC}
 DECODE_MMA_I8, DECODE_PLAIN, DECODE_MMA_F16 = 0, 1, 2
 DAS_TILED, DAS_PLAIN = 0, 1
@@ -59,6 +61,8 @@ class Params(ctypes.Structure):
         ("demod_shift", ctypes.c_int32), ("reserved2", ctypes.c_uint32),
         ("demod_taps", ctypes.c_void_p),
         ("iq_freq", ctypes.c_double),
+        ("tx_wave", ctypes.c_uint32), ("reserved3", ctypes.c_uint32),
+        ("tx_focus", ctypes.c_double), ("tx_angles", ctypes.c_void_p),
     ]
 
 
@@ -161,6 +165,14 @@ def make_params(g, decoded_dtype="f32", decode_variant=DECODE_MMA_I8, das_varian
     p.tx_pitch, p.rx_pitch = float(g.tx_pitch), float(g.rx_pitch)
     p.f_number = float(g.f_number if f_number is None else f_number)
     p.iq_freq = float(iq_freq if iq_freq is not None else getattr(g, "iq_freq", 0.0))
+    wave = getattr(g, "tx_wave", "line")
+    p.tx_wave = _TX_WAVE_NAMES[wave] if isinstance(wave, str) else int(wave)
+    p.tx_focus = float(getattr(g, "tx_focus", 0.0))
+    if p.tx_wave == TX_PLANE:
+        import numpy as np
+        ang = np.ascontiguousarray(getattr(g, "tx_angles"), dtype=np.float64)
+        p.tx_angles = ang.ctypes.data
+        p._angles = ang         # kept alive until rcbf_plan copies it
     if demod is not None:
         import numpy as np
         dec, taps, shift = demod
@@ -192,6 +204,7 @@ class Plan:
         _check(lib.rcbf_plan(ctypes.byref(params), ctypes.byref(h)))
         params.decode_matrix = None
         params.demod_taps = None
+        params.tx_angles = None
         self.handle = h
         self.params = params
 

@@ -172,6 +172,15 @@ int validate(const rcbf_params* p) {
             return set_error(RCBF_EINVAL, "rcbf_plan: raw trace too long");
     }
     if (!(p->iq_freq >= 0.0)) return set_error(RCBF_EINVAL, "rcbf_plan: iq_freq must be >= 0");
+    if (p->tx_wave > RCBF_TX_VLS) return set_error(RCBF_EINVAL, "rcbf_plan: unknown tx_wave");
+    if (p->tx_wave == RCBF_TX_PLANE) {
+        if (!p->tx_angles) return set_error(RCBF_EINVAL, "rcbf_plan: plane waves need tx_angles");
+        for (uint32_t i = 0; i < p->n_tx; ++i)
+            if (!(std::fabs(p->tx_angles[i]) < 1.5707963267948966))
+                return set_error(RCBF_EINVAL, "rcbf_plan: plane-wave angles must satisfy |angle| < pi/2");
+    }
+    if (p->tx_wave == RCBF_TX_VLS && !std::isfinite(p->tx_focus))
+        return set_error(RCBF_EINVAL, "rcbf_plan: tx_focus must be finite");
     if (p->iq_freq > 0.0 && p->decoded_dtype != RCBF_CF32)
         return set_error(RCBF_EINVAL, "rcbf_plan: IQ beamforming (iq_freq > 0) needs RCBF_CF32 data");
     const bool tile_given = p->tile[0] || p->tile[1] || p->tile[2];
@@ -215,6 +224,22 @@ void setup_geometry(PlanHost& h) {
     for (int ax = 0; ax < 2 && ua < 0; ++ax) if (tx_invariant(ax) && p.out_dims[ax] > 1) ua = ax;
     for (int ax = 0; ax < 2 && ua < 0; ++ax) if (tx_invariant(ax)) ua = ax;
     h.tiled_ok = ua >= 0 && p.n_ch % kCJ == 0 && p.n_tx % (p.decoded_dtype == RCBF_CF32 ? 4 : kCI) == 0;
+    if (p.tx_wave == RCBF_TX_VLS) {
+        // off the line's axis the virtual-line-source delay jumps by 2 |lat - e|
+        // at the focal depth (converging above, diverging below), so tile
+        // windows from the 1-Lipschitz radius bound hold only when no voxel
+        // lies at that depth: a focal plane inside the image runs the plain form
+        double zmin = 1e300, zmax = -1e300;
+        for (int c = 0; c < 8; ++c) {
+            const double ix = (c & 1) ? (double)(p.out_dims[0] - 1) : 0.0;
+            const double iy = (c & 2) ? (double)(p.out_dims[1] - 1) : 0.0;
+            const double iz = (c & 4) ? (double)(p.out_dims[2] - 1) : 0.0;
+            const double z = G[8] * ix + G[9] * iy + G[10] * iz + G[11];
+            zmin = std::fmin(zmin, z);
+            zmax = std::fmax(zmax, z);
+        }
+        h.force_plain = p.tx_focus >= zmin && p.tx_focus <= zmax;
+    }
     if (ua < 0) ua = 0;
     const int va = 1 - ua;
     h.swap_uv = ua == 1;
@@ -246,6 +271,9 @@ void setup_geometry(PlanHost& h) {
     a.fs = p.fs;
     a.f_number = (float)p.f_number;
     a.iq_ratio = p.iq_freq / p.fs;
+    a.tx_wave = (int)p.tx_wave;
+    a.tx_focus = p.tx_focus;
+    a.tx_dir = nullptr;        // device directions, set by rcbf_plan
     a.interp = (int)p.interp;
     a.dtype = (int)p.decoded_dtype;
     a.scale = p.decoded_dtype == RCBF_I32 ? 1.0f / (float)p.n_tx : 1.0f;
@@ -339,6 +367,7 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
     h.p = *params;
     h.p.decode_matrix = nullptr;   // the matrix is copied, never referenced later
     h.p.demod_taps = nullptr;      // so are the taps
+    h.p.tx_angles = nullptr;       // and the plane-wave angles
     const rcbf_params& p = h.p;
 
     setup_geometry(h);
@@ -355,6 +384,16 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
     if (cudaMalloc(&h.d_status, sizeof(int)) != cudaSuccess) return fail(RCBF_ENOMEM, "rcbf_plan: cudaMalloc status");
     if (cudaMemset(h.d_status, 0, sizeof(int)) != cudaSuccess) return fail(RCBF_ECUDA, "rcbf_plan: cudaMemset");
     a.status = h.d_status;
+    if (p.tx_wave == RCBF_TX_PLANE) {
+        std::vector<float2> dir(p.n_tx);
+        for (uint32_t i = 0; i < p.n_tx; ++i)
+            dir[i] = make_float2((float)std::sin(params->tx_angles[i]), (float)std::cos(params->tx_angles[i]));
+        if (cudaMalloc(&h.d_tx_dir, dir.size() * sizeof(float2)) != cudaSuccess)
+            return fail(RCBF_ENOMEM, "rcbf_plan: cudaMalloc directions");
+        if (cudaMemcpy(h.d_tx_dir, dir.data(), dir.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(RCBF_ECUDA, "rcbf_plan: copy directions");
+        a.tx_dir = h.d_tx_dir;
+    }
     if (p.demod_decimation) {
         const size_t bytes = (size_t)p.demod_n_taps * sizeof(int16_t);
         if (cudaMalloc(&h.d_taps, bytes) != cudaSuccess) return fail(RCBF_ENOMEM, "rcbf_plan: cudaMalloc taps");
@@ -453,6 +492,7 @@ void rcbf_destroy(rcbf_plan_t plan) {
     if (h.d_status) cudaFree(h.d_status);
     if (h.d_partial) cudaFree(h.d_partial);
     if (h.d_taps) cudaFree(h.d_taps);
+    if (h.d_tx_dir) cudaFree(h.d_tx_dir);
     delete plan;
 }
 

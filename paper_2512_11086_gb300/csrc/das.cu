@@ -59,8 +59,7 @@ das_plain_kernel(DasArgs a) {
     const float fsc = (float)a.fs_over_c, t0fs = (float)a.t0fs;
     float dtx[kMaxOrder];
     for (int i = 0; i < a.n_tx; ++i) {
-        const float dx = lat_tx - ((float)a.tx_e0 + i * (float)a.tx_pitch);
-        dtx[i] = sqrtf(dx * dx + z * z);
+        dtx[i] = tx_distance_f32(a, i, lat_tx, z);
     }
     float acc = 0.f, acci = 0.f;
     // IQ phase r s = r fs/c d_tx + r fs/c d_rx - r t0 fs, each term reduced to
@@ -195,6 +194,10 @@ int das_prepare_tile(const PlanHost& h, double c, int bu, int bv, int bw, double
     }
     if (a->W > 128) {
         if (why) *why = "das: the voxel tile spans more than 128 samples at this speed of sound; choose a smaller tile";
+        return RCBF_EUNSUPPORTED;
+    }
+    if (h.force_plain) {
+        if (why) *why = "das: the virtual-line-source focal depth lies inside the image (delays jump there)";
         return RCBF_EUNSUPPORTED;
     }
     if (a->interp == RCBF_CUBIC && a->dtype == RCBF_CF32 && a->W > 64) {

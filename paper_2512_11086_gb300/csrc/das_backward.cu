@@ -129,11 +129,11 @@ das_bwd_kernel(DasArgs a) {
     const int j_lo = jc0 * kBwdCJ, n_rx = js * kBwdCJ;
     for (int e = tid; e < a.n_tx + n_rx; e += kDasThreads) {
         if (e < a.n_tx) {
-            const double L = lat_tx_ref - (a.tx_e0 + e * a.tx_pitch);
-            const double d = sqrt(L * L + zr * zr);
+            float tx0, tx1;
+            const double d = tx_ref_distance(a, e, lat_tx_ref, zr, &tx0, &tx1);
             const double A = d * a.fs_over_c - a.t0fs;
             const double K = floor(A);
-            s_tx[e] = make_float4((float)L, (float)d, (float)(A - K - (double)a.lo - 0.5 - (double)a.H),
+            s_tx[e] = make_float4(tx0, tx1, (float)(A - K - (double)a.lo - 0.5 - (double)a.H),
                                   __int_as_float((int)K));
         } else {
             const int j = j_lo + e - a.n_tx;
@@ -147,6 +147,7 @@ das_bwd_kernel(DasArgs a) {
 
     // this thread's voxels: offsets, validity and the scaled upstream gradient
     const float Zf = (float)zr, fsc = (float)a.fs_over_c;
+    const float Zfoc = (float)(zr - a.tx_focus);   // reference depth below the virtual line sources
     float dlr[4], dz[4], gs_re[4], gs_im[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -268,10 +269,7 @@ das_bwd_kernel(DasArgs a) {
             const float dL = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]) * dv + (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]) * dw;
             const float dzz = (float)a.Gv[2] * dv + (float)a.Gw[2] * dw;
             const float4 tx = s_tx[ic * kBwdCI + ii];
-            const float Lv = tx.x + dL, Zv = Zf + dzz;
-            const float d = sqrtf(Lv * Lv + Zv * Zv);
-            const float num = dL * (2.0f * tx.x + dL) + dzz * (2.0f * Zf + dzz);
-            const float al = tx.z + __fdividef(num, d + tx.y) * fsc;
+            const float al = tx_offset(a.tx_wave, tx, dL, dzz, Zf, Zfoc, fsc);
             s_alpha[ii * C::ROWS + row] = fminf(fmaxf(al, tx.z - a.reach_a), tx.z + a.reach_a);
         }
         if (__syncthreads_or(!ok)) {
@@ -500,8 +498,7 @@ das_bwd_plain_kernel(DasArgs a) {
         const float a_j = (a.apod ? __ldg(a.apod + j) : 1.0f) * W;
         float gw = 0.f;
         for (int i = 0; i < a.n_tx; ++i) {
-            const float dxt = lat_tx - ((float)a.tx_e0 + i * (float)a.tx_pitch);
-            const float dtx = sqrtf(dxt * dxt + z * z);
+            const float dtx = tx_distance_f32(a, i, lat_tx, z);
             const float s = (dtx + drx) * fsc - t0fs;
             const float fl = floorf(s);
             const float f = s - fl;

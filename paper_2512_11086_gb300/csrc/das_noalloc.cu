@@ -60,6 +60,8 @@ extern "C" int rcbf_das_noalloc(const rcbf_params* params, const void* decoded, 
                                 float* image, void* stream) {
     int rc = plan_validate(params);
     if (rc != RCBF_OK) return rc;
+    if (params->tx_wave == RCBF_TX_PLANE)
+        return set_error(RCBF_EUNSUPPORTED, "rcbf_das_noalloc: plane-wave directions need a plan (device table)");
     if (!decoded || !image) return set_error(RCBF_EINVAL, "rcbf_das_noalloc: NULL buffer");
     if ((reinterpret_cast<uintptr_t>(decoded) & 15u) || (reinterpret_cast<uintptr_t>(image) & 3u) ||
         (apod && (reinterpret_cast<uintptr_t>(apod) & 3u)))
@@ -68,6 +70,8 @@ extern "C" int rcbf_das_noalloc(const rcbf_params* params, const void* decoded, 
     PlanHost h{};
     h.p = *params;
     h.p.decode_matrix = nullptr;
+    h.p.demod_taps = nullptr;
+    h.p.tx_angles = nullptr;
     plan_geometry(h);
     int dev = 0;
     cudaGetDevice(&dev);

@@ -288,14 +288,14 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     __syncthreads();   // the previous unit of this CTA no longer reads the tables
     for (int e = tid; e < a.n_tx + n_rx; e += kDasThreads) {
         if (e < a.n_tx) {
-            const double L = lat_tx_ref - (a.tx_e0 + e * a.tx_pitch);
-            const double d = sqrt(L * L + zr * zr);
+            float tx0, tx1;
+            const double d = tx_ref_distance(a, e, lat_tx_ref, zr, &tx0, &tx1);
             const double A = d * a.fs_over_c - a.t0fs;
             const double K = floor(A);
             // remainder with the window offset, the half-sample shift of the
             // rounding trick and the window centring folded in
             const float rho = (float)(A - K - (double)a.lo - 0.5 - (double)a.H);
-            s_tx[e] = make_float4((float)L, (float)d, rho, __int_as_float((int)K));
+            s_tx[e] = make_float4(tx0, tx1, rho, __int_as_float((int)K));
         } else {
             const int j = j_lo + e - a.n_tx;
             const double L = lat_rx_ref - (a.rx_e0 + j * a.rx_pitch);
@@ -309,6 +309,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     // ---- voxel offsets from the reference in FP32 (exact half-integer index
     // offsets times the FP32 voxel steps)
     const float Zf = (float)zr;
+    const float Zfoc = (float)(zr - a.tx_focus);   // reference depth below the virtual line sources
     const float fsc = (float)a.fs_over_c;
     const float gur = (float)(a.rx_axis ? a.Gu[1] : a.Gu[0]);
     const float gvr = (float)(a.rx_axis ? a.Gv[1] : a.Gv[0]);
@@ -413,10 +414,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             const float dL = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]) * dv + (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]) * dw;
             const float dz = (float)a.Gv[2] * dv + (float)a.Gw[2] * dw;
             const float4 tx = s_tx[(s % n_ic) * C::CI + ii];
-            const float Lv = tx.x + dL, Zv = Zf + dz;
-            const float d = sqrtf(Lv * Lv + Zv * Zv);
-            const float num = dL * (2.0f * tx.x + dL) + dz * (2.0f * Zf + dz);
-            const float al = tx.z + __fdividef(num, d + tx.y) * fsc;
+            const float al = tx_offset(a.tx_wave, tx, dL, dz, Zf, Zfoc, fsc);
             s_alpha[pb * C::ALPHA_N + ii * C::ROWS + row] = fminf(fmaxf(al, tx.z - a.reach_a), tx.z + a.reach_a);
         }
         mbar_arrive(bar0 + 8 * (kRawEmpty + b));

@@ -43,6 +43,10 @@ struct DasArgs {
     double c;              // speed of sound of this call
     double fs;
     double iq_ratio;       // iq_freq / fs: IQ beamforming phase per sample (0 = RF data)
+    double tx_focus;       // virtual line source depth [m]
+    const float2* tx_dir;  // plane waves: (sin a_i, cos a_i) per transmit (device)
+    int tx_wave;           // rcbf_tx_wave
+    int pad_tx;
     float f_number;
     int interp;            // rcbf_interp
     int W;                 // pairs per window actually used (<= compiled stride)
@@ -102,6 +106,8 @@ struct PlanHost {
     float* d_partial;       // DAS partial images (channel split), plan-owned
     size_t partial_floats;
     int16_t* d_taps;        // device demodulation FIR taps (demod_decimation > 0)
+    float2* d_tx_dir;       // device plane-wave directions (tx_wave == RCBF_TX_PLANE)
+    bool force_plain;       // the geometry admits no tile windows (a VLS focal plane inside the image)
     // adjoint tile with lanes over z: 32 voxels along u by bwd_bv x bwd_bw
     // rows (bwd_bv = 0: no such tile keeps the window within 128 samples)
     int bwd_bv, bwd_bw;
@@ -146,6 +152,72 @@ int das_class_index(int W);
 int configure_das(PlanHost& h);
 
 // ------------------------------------------------------------ PTX helpers
+// ---- transmit waves (line element, plane wave, virtual line source): the
+// FP64 reference entry of transmit e at the tile reference point, and the FP32
+// offset of a voxel from it. Entry: (x, y, frac, K) with A = K + frac the
+// reference transmit delay in samples; x, y per wave:
+//   line   (L, d)                   L = lat_ref - e, d = sqrt(L^2 + Z^2)
+//   plane  (sin a, cos a)
+//   vls    (L, sgn * dv)            dv = sqrt(L^2 + (Z - f)^2), sgn = sign(Z - f)
+__device__ __forceinline__ double tx_ref_distance(const DasArgs& a, int e, double lat_ref, double zr, float* x,
+                                                  float* y) {
+    if (a.tx_wave == RCBF_TX_PLANE) {
+        const float2 sc = a.tx_dir[e];
+        *x = sc.x;
+        *y = sc.y;
+        return zr * (double)sc.y + lat_ref * (double)sc.x;
+    }
+    const double L = lat_ref - (a.tx_e0 + e * a.tx_pitch);
+    if (a.tx_wave == RCBF_TX_VLS) {
+        const double dz = zr - a.tx_focus;
+        const double dv = (dz >= 0.0 ? 1.0 : -1.0) * sqrt(L * L + dz * dz);
+        *x = (float)L;
+        *y = (float)dv;
+        return a.tx_focus + dv;
+    }
+    const double d = sqrt(L * L + zr * zr);
+    *x = (float)L;
+    *y = (float)d;
+    return d;
+}
+
+// Transmit delay of the voxel at offsets (dL, dZ) from the reference, in
+// samples relative to the entry's reference (before the window clamp).
+// Zf = z of the reference (FP32), Zfoc = reference z minus the focus depth.
+__device__ __forceinline__ float tx_offset(int wave, float4 tx, float dL, float dZ, float Zf, float Zfoc, float fsc) {
+    if (wave == RCBF_TX_PLANE) return tx.z + fmaf(dZ, tx.y, dL * tx.x) * fsc;
+    if (wave == RCBF_TX_VLS) {
+        // tiles never straddle the focal depth (such images run the plain
+        // form), so the voxel is on the reference's side: the same
+        // cancellation-free difference, signed like the reference
+        const float Lv = tx.x + dL, Zv = Zfoc + dZ;
+        const float dv = sqrtf(Lv * Lv + Zv * Zv);
+        const float num = dL * (2.0f * tx.x + dL) + dZ * (2.0f * Zfoc + dZ);
+        const float diff = __fdividef(num, dv + fabsf(tx.y));
+        return tx.z + (tx.y >= 0.f ? diff : -diff) * fsc;
+    }
+    // cancellation-free d(v) - d(ref) = (dL (2L + dL) + dZ (2Z + dZ)) / (d(v) + d(ref))
+    const float Lv = tx.x + dL, Zv = Zf + dZ;
+    const float d = sqrtf(Lv * Lv + Zv * Zv);
+    const float num = dL * (2.0f * tx.x + dL) + dZ * (2.0f * Zf + dZ);
+    return tx.z + __fdividef(num, d + tx.y) * fsc;
+}
+
+// FP32 transmit path of transmit i to (lat_tx, z) (the plain forms).
+__device__ __forceinline__ float tx_distance_f32(const DasArgs& a, int i, float lat_tx, float z) {
+    if (a.tx_wave == RCBF_TX_PLANE) {
+        const float2 sc = a.tx_dir[i];
+        return fmaf(z, sc.y, lat_tx * sc.x);
+    }
+    const float dx = lat_tx - ((float)a.tx_e0 + i * (float)a.tx_pitch);
+    if (a.tx_wave == RCBF_TX_VLS) {
+        const float f = (float)a.tx_focus, dz = z - f;
+        const float dv = sqrtf(dx * dx + dz * dz);
+        return f + (dz >= 0.f ? dv : -dv);
+    }
+    return sqrtf(dx * dx + z * z);
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
