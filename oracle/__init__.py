@@ -56,9 +56,10 @@ class _Geom(ctypes.Structure):
         ("voxel_transform", ctypes.c_double * 16), ("xdc_transform", ctypes.c_double * 16),
         ("interp", ctypes.c_int64), ("iq_freq", ctypes.c_double),
         ("tx_wave", ctypes.c_int64), ("tx_focus", ctypes.c_double), ("tx_angles", ctypes.c_void_p),
+        ("acq_kind", ctypes.c_int64),
     ]
 
-TX_WAVE = {"line": 0, "plane": 1, "vls": 2}
+TX_WAVE = {"line": 0, "plane": 1, "vls": 2, "point": 3}
 
 INTERP = {"linear": 0, "cubic": 1}
 
@@ -99,10 +100,11 @@ def geom_from(g, c: Optional[float] = None, f_number: Optional[float] = None,
     s.iq_freq = float(iq_freq if iq_freq is not None else getattr(g, "iq_freq", 0.0))
     s.tx_wave = TX_WAVE[getattr(g, "tx_wave", "line")]
     s.tx_focus = float(getattr(g, "tx_focus", 0.0))
+    s.acq_kind = int(getattr(g, "acq_kind", 0))
     if s.tx_wave == 1:
         ang = np.ascontiguousarray(getattr(g, "tx_angles"), dtype=np.float64)
-        if ang.size != int(g.n_tx):
-            raise ValueError("one plane-wave angle per transmit")
+        if ang.size != (1 if s.acq_kind == 2 else int(g.n_tx)):
+            raise ValueError("one plane-wave angle per transmit (one for a 2D receive aperture)")
         s._angles = ang                      # kept alive with the structure
         s.tx_angles = ang.ctypes.data
     s.interp = INTERP[interp if interp is not None else getattr(g, "interp", "linear")]
@@ -193,7 +195,7 @@ def das_grad(g, rf: np.ndarray, G: np.ndarray, w: Optional[np.ndarray] = None,
     Gp = np.stack([G.real, G.imag]) if cplx else np.asarray(G)[None]
     Gp = np.ascontiguousarray(Gp.reshape(planes.shape[0], -1), dtype=np.float64)
     geom = geom_from(g, c=c, **geom_kw)
-    if geom.interp != 0 or geom.iq_freq > 0:
+    if geom.interp != 0 or geom.iq_freq > 0 or geom.acq_kind == 2:
         raise NotImplementedError("the DAS gradients are defined for linear interpolation of RF data")
     grad_rf = np.empty_like(planes) if want_rf else None
     gc = np.zeros(1, dtype=np.float64)

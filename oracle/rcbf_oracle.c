@@ -49,6 +49,17 @@
  * and every one of them depends on (lat_tx, z) only, so s_ij = A_i + B_j
  * stays separable.
  *
+ * HERCULES with its 2D receive aperture (acq_kind 2; §THEORY: after decoding
+ * the data is that of a 2D matrix array receiving one plane or diverging
+ * wave): index i is the receive row at lateral e_i (rows' lateral axis),
+ * index j the column at e_j (columns' axis); for each (i, j) the receive path
+ * is the point distance sqrt((lat_rx - e_j)^2 + (lat_tx - e_i)^2 + z^2), and
+ * one transmit wave reaches the point after
+ *   plane wave       d_tx = z cos(a) + lat_tx sin(a)      (a = tx_angles[0])
+ *   diverging wave   d_tx = sqrt(x^2 + y^2 + (z - f)^2) + f   (virtual point at depth f < 0)
+ * so the delay is not a sum of a row term and a column term. The F# window of
+ * Eq. (2) is applied to the radial lateral distance to element (i, j).
+ *
  * Window reading: the window is non-zero exactly when F# |lat - e_j| < 0.5 |z|
  * (|u| < 0.5 written without a division), so a voxel at z = 0 gets weight 0.
  */
@@ -76,6 +87,7 @@ typedef struct oracle_geom {
     int64_t tx_wave;                          /* 0 line elements, 1 plane waves, 2 virtual line sources */
     double tx_focus;                          /* virtual line source depth f [m] */
     const double* tx_angles;                  /* plane-wave angles theta_i [rad], n_tx of them */
+    int64_t acq_kind;                         /* 2: HERCULES with a 2D receive aperture */
 } oracle_geom;
 
 int oracle_threads(void) {
@@ -203,6 +215,24 @@ static double sample_cubic(const double* trace, int64_t n_s, double s) {
     return h00 * p1 + h10 * m1 + h01 * p2 + h11 * m2;
 }
 
+/* HERCULES 2D: transmit path of the frame's one wave (tx_wave 1 plane,
+ * 3 diverging) to q, and the receive path to element (row i, column j). */
+static double hercules_transmit(const oracle_geom* g, const double q[3]) {
+    if (g->tx_wave == 1) {
+        const double a = g->tx_angles[0];
+        return q[2] * cos(a) + lateral(q, g->tx_orientation) * sin(a);
+    }
+    const double dz = q[2] - g->tx_focus;
+    return sqrt(q[0] * q[0] + q[1] * q[1] + dz * dz) + g->tx_focus;
+}
+
+static double hercules_receive(const oracle_geom* g, int64_t i, int64_t j, const double q[3], double* radial) {
+    const double dr = lateral(q, g->rx_orientation) - element_position(j, g->n_ch, g->rx_pitch);
+    const double dt = lateral(q, g->tx_orientation) - element_position(i, g->n_tx, g->tx_pitch);
+    *radial = sqrt(dr * dr + dt * dt);
+    return sqrt(dr * dr + dt * dt + q[2] * q[2]);
+}
+
 /* ------------------------------------------------------------------ DAS */
 
 /* rf: [n_planes][n_tx][n_ch][n_s] doubles; w: [n_ch] or NULL; c > 0.
@@ -220,12 +250,19 @@ void oracle_das(const oracle_geom* g, const double* rf, int64_t n_planes, const 
         const double lat_tx = lateral(q, g->tx_orientation);
         const double lat_rx = lateral(q, g->rx_orientation);
         double acc[2] = {0.0, 0.0};
+        const int h2d = g->acq_kind == 2;
+        const double d_wave = h2d ? hercules_transmit(g, q) : 0.0;
         for (int64_t i = 0; i < n_tx; ++i) {
-            const double d_tx = transmit_distance(g, i, lat_tx, q[2]);
+            const double d_tx = h2d ? d_wave : transmit_distance(g, i, lat_tx, q[2]);
             for (int64_t j = 0; j < n_ch; ++j) {
-                const double dx_r = lat_rx - element_position(j, n_ch, g->rx_pitch);
-                const double d_rx = sqrt(dx_r * dx_r + q[2] * q[2]);
-                const double a = (w ? w[j] : 1.0) * window_weight(g->f_number, dx_r, q[2]);
+                double d_rx, lat_off;
+                if (h2d) {
+                    d_rx = hercules_receive(g, i, j, q, &lat_off);
+                } else {
+                    lat_off = lat_rx - element_position(j, n_ch, g->rx_pitch);
+                    d_rx = sqrt(lat_off * lat_off + q[2] * q[2]);
+                }
+                const double a = (w ? w[j] : 1.0) * window_weight(g->f_number, lat_off, q[2]);
                 if (a == 0.0) continue;
                 const double tof = (d_tx + d_rx) / c;
                 const double s = (tof - g->t0) * g->fs;

@@ -38,7 +38,7 @@ import numpy as np
 MM = 1e-3
 
 ROWS, COLUMNS = 0, 1
-FORCES, HERCULES = 0, 1
+FORCES, HERCULES, HERCULES_2D = 0, 1, 2     # HERCULES_2D: decoded rows x columns = a 2D receive aperture
 
 
 def sylvester_kron(n: int) -> np.ndarray:
@@ -134,9 +134,19 @@ def _accumulate_echoes(g: Geometry, scatterers: np.ndarray, c: float,
         lt = _lateral(p, g.tx_orientation)
         lr = _lateral(p, g.rx_orientation)
         z = p[2]
-        dist_tx = _transmit_path(g, e_tx, lt, z)             # [n_tx]
-        dist_rx = np.sqrt((lr - e_rx) ** 2 + z * z)          # [n_ch]
-        tau = (dist_tx[:, None] + dist_rx[None, :]) / c      # [n_tx, n_ch]
+        if g.acq_kind == HERCULES_2D:
+            # one transmit wave; receive on the 2D aperture (row i, column j)
+            if g.tx_wave == "plane":
+                a = float(g.tx_angles[0])
+                d_wave = z * math.cos(a) + lt * math.sin(a)
+            else:
+                d_wave = math.sqrt(p[0] ** 2 + p[1] ** 2 + (z - g.tx_focus) ** 2) + g.tx_focus
+            rx2 = np.sqrt((lr - e_rx[None, :]) ** 2 + (lt - e_tx[:, None]) ** 2 + z * z)   # [n_tx, n_ch]
+            tau = (d_wave + rx2) / c
+        else:
+            dist_tx = _transmit_path(g, e_tx, lt, z)             # [n_tx]
+            dist_rx = np.sqrt((lr - e_rx) ** 2 + z * z)          # [n_ch]
+            tau = (dist_tx[:, None] + dist_rx[None, :]) / c      # [n_tx, n_ch]
         centre = np.floor((tau - g.t0) * g.fs).astype(np.int64)
         n = centre[:, :, None] + k[None, None, :]            # [n_tx, n_ch, K]
         t = g.t0 + n / g.fs - tau[:, :, None]

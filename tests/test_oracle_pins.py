@@ -169,6 +169,32 @@ def test_plane_wave_at_zero_angle_and_vls_on_axis_equal_depth():
         assert oracle.das(g, r).ravel()[0] == pytest.approx(want, abs=1e-12)
 
 
+def test_hercules_2d_receive_hand_computed_delays():
+    # one row (lateral y = 0) and one column (lateral x = 0); the point
+    # (x, y, z) = (3, 4, 12) mm is 13 mm from the 2D element (x_j, y_i) = (0, 0)
+    g = _point_geom(3 * MM, 4 * MM, 12 * MM)
+    g.acq_kind = synth.HERCULES_2D
+    ramp = np.arange(g.n_samples, dtype=np.float64).reshape(1, 1, -1)
+    g.tx_wave, g.tx_angles = "plane", (0.0,)        # d_tx = z = 12 -> 25 mm -> s = 166.666...
+    assert oracle.das(g, ramp).ravel()[0] == pytest.approx(25e-3 / 1500 * 10e6, abs=1e-9)
+    # a diverging wave from a virtual point at depth -5 mm on the axis:
+    # d_tx = sqrt(3^2 + 4^2 + 17^2) - 5 = 12.72004514666935 -> 25.72004514666935 mm
+    g.tx_wave, g.tx_focus = "point", -5 * MM
+    assert oracle.das(g, ramp).ravel()[0] == pytest.approx(171.4669676444623, abs=1e-9)
+
+
+def test_hercules_2d_with_one_row_on_the_image_plane_equals_the_separable_form():
+    # one receive row at lateral 0 and a B-scan in its plane (y = 0): the 2D
+    # element distance reduces to the line-element distance, so the image is
+    # that of the separable plane-wave form with one transmit
+    g = _small_geom(n_tx=1, n_ch=6, dims=(7, 1, 9))
+    g.tx_wave, g.tx_angles = "plane", (0.2,)
+    r = np.random.default_rng(16).normal(size=(1, 6, g.n_samples))
+    sep = oracle.das(g, r, w=np.linspace(0.5, 1.5, 6))
+    g.acq_kind = synth.HERCULES_2D
+    np.testing.assert_allclose(oracle.das(g, r, w=np.linspace(0.5, 1.5, 6)), sep, rtol=0, atol=1e-12)
+
+
 # -------------------------------------------- cubic Hermite interpolation
 
 def test_cubic_weights_at_a_quarter_sample():
