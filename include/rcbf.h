@@ -87,8 +87,13 @@ enum rcbf_dtype {
 };
 
 enum rcbf_acq_kind {
-    RCBF_FORCES   = 0,  /* Hadamard-encoded transmit aperture */
-    RCBF_HERCULES = 1   /* Hadamard-encoded receive rows; same separable delays */
+    RCBF_FORCES      = 0,  /* Hadamard-encoded transmit aperture */
+    RCBF_HERCULES    = 1,  /* Hadamard-encoded receive rows; same separable delays */
+    RCBF_HERCULES_2D = 2   /* decoded rows x columns as a 2D receive aperture for one transmit wave
+                              (tx_wave RCBF_TX_PLANE with tx_angles[0], or RCBF_TX_POINT): index i is
+                              the receive row at lateral e_i (tx_orientation's axis), j the column;
+                              d_rx = sqrt((lat_rx - e_j)^2 + (lat_tx - e_i)^2 + z^2), not separable;
+                              the F# window uses the radial lateral distance. Plain DAS form. */
 };
 
 enum rcbf_orientation {
@@ -99,10 +104,12 @@ enum rcbf_orientation {
 enum rcbf_tx_wave {
     RCBF_TX_LINE  = 0,  /* line element i: d_tx = sqrt((lat_tx - e_i)^2 + z^2) */
     RCBF_TX_PLANE = 1,  /* plane wave i: d_tx = z cos(a_i) + lat_tx sin(a_i) (crosses the array at t = 0) */
-    RCBF_TX_VLS   = 2   /* virtual line source above line i at depth f:
+    RCBF_TX_VLS   = 2,  /* virtual line source above line i at depth f:
                            d_tx = f + sgn(z - f) sqrt((lat_tx - e_i)^2 + (z - f)^2), sgn(0) = +1.
                            Off axis the delay jumps at z = f, so an image whose depth range
                            contains f runs the plain DAS form. */
+    RCBF_TX_POINT = 3   /* RCBF_HERCULES_2D only: diverging wave from a virtual point at depth f < 0 on the
+                           array axis: d_tx = sqrt(x^2 + y^2 + (z - f)^2) + f */
 };
 
 enum rcbf_interp {
@@ -130,7 +137,7 @@ typedef struct rcbf_params {
     uint32_t n_ch;            /* receive channels */
     uint32_t n_samples;       /* samples per (transmit, channel) trace */
     uint32_t hadamard_order;  /* 0: RF is not encoded (decode unavailable); else == n_tx */
-    uint32_t acq_kind;        /* enum rcbf_acq_kind (informational: delays are identical) */
+    uint32_t acq_kind;        /* enum rcbf_acq_kind (FORCES and HERCULES share separable delays) */
     uint32_t tx_orientation;  /* enum rcbf_orientation of the transmit line elements */
     uint32_t rx_orientation;  /* enum rcbf_orientation of the receive line elements */
     uint32_t decoded_dtype;   /* enum rcbf_dtype: decode output and DAS input

@@ -26,8 +26,9 @@ I16, I32, F32, F16, CF32 = 0, 1, 2, 3, 4
 FORCES, HERCULES = 0, 1
 ROWS, COLUMNS = 0, 1
 LINEAR, CUBIC = 0, 1
-TX_LINE, TX_PLANE, TX_VLS = 0, 1, 2
-_TX_WAVE_NAMES = {"line": TX_LINE, "plane": TX_PLANE, "vls": TX_VLS}
+TX_LINE, TX_PLANE, TX_VLS, TX_POINT = 0, 1, 2, 3
+_TX_WAVE_NAMES = {"line": TX_LINE, "plane": TX_PLANE, "vls": TX_VLS, "point": TX_POINT}
+HERCULES_2D = 2
 _INTERP_NAMES = {"linear": LINEAR, "cubic": CUBIC}
 DECODE_MMA_I8, DECODE_PLAIN, DECODE_MMA_F16 = 0, 1, 2
 DAS_TILED, DAS_PLAIN = 0, 1
@@ -171,6 +172,8 @@ def make_params(g, decoded_dtype="f32", decode_variant=DECODE_MMA_I8, das_varian
     if p.tx_wave == TX_PLANE:
         import numpy as np
         ang = np.ascontiguousarray(getattr(g, "tx_angles"), dtype=np.float64)
+        if ang.size < (1 if p.acq_kind == HERCULES_2D else p.n_tx):
+            raise ValueError("plane waves need one angle per transmit (one for a 2D receive aperture)")
         p.tx_angles = ang.ctypes.data
         p._angles = ang         # kept alive until rcbf_plan copies it
     if demod is not None:

@@ -132,7 +132,7 @@ int validate(const rcbf_params* p) {
     if (!(p->f_number >= 0)) return set_error(RCBF_EINVAL, "rcbf_plan: f_number must be >= 0");
     if (p->tx_orientation > 1 || p->rx_orientation > 1)
         return set_error(RCBF_EINVAL, "rcbf_plan: orientation must be RCBF_ROWS or RCBF_COLUMNS");
-    if (p->acq_kind > 1) return set_error(RCBF_EINVAL, "rcbf_plan: unknown acq_kind");
+    if (p->acq_kind > RCBF_HERCULES_2D) return set_error(RCBF_EINVAL, "rcbf_plan: unknown acq_kind");
     if (p->interp != RCBF_LINEAR && p->interp != RCBF_CUBIC)
         return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: interp must be RCBF_LINEAR or RCBF_CUBIC");
     if (p->decoded_dtype != RCBF_I32 && p->decoded_dtype != RCBF_F32 && p->decoded_dtype != RCBF_F16 &&
@@ -172,10 +172,15 @@ int validate(const rcbf_params* p) {
             return set_error(RCBF_EINVAL, "rcbf_plan: raw trace too long");
     }
     if (!(p->iq_freq >= 0.0)) return set_error(RCBF_EINVAL, "rcbf_plan: iq_freq must be >= 0");
-    if (p->tx_wave > RCBF_TX_VLS) return set_error(RCBF_EINVAL, "rcbf_plan: unknown tx_wave");
+    if (p->tx_wave > RCBF_TX_POINT) return set_error(RCBF_EINVAL, "rcbf_plan: unknown tx_wave");
+    const bool h2d = p->acq_kind == RCBF_HERCULES_2D;
+    if (h2d && p->tx_wave != RCBF_TX_PLANE && p->tx_wave != RCBF_TX_POINT)
+        return set_error(RCBF_EINVAL, "rcbf_plan: a 2D receive aperture takes one plane or diverging wave");
+    if (p->tx_wave == RCBF_TX_POINT && (!h2d || !(p->tx_focus < 0.0)))
+        return set_error(RCBF_EINVAL, "rcbf_plan: RCBF_TX_POINT is a virtual point behind a 2D aperture (tx_focus < 0)");
     if (p->tx_wave == RCBF_TX_PLANE) {
         if (!p->tx_angles) return set_error(RCBF_EINVAL, "rcbf_plan: plane waves need tx_angles");
-        for (uint32_t i = 0; i < p->n_tx; ++i)
+        for (uint32_t i = 0; i < (h2d ? 1u : p->n_tx); ++i)
             if (!(std::fabs(p->tx_angles[i]) < 1.5707963267948966))
                 return set_error(RCBF_EINVAL, "rcbf_plan: plane-wave angles must satisfy |angle| < pi/2");
     }
@@ -240,6 +245,7 @@ void setup_geometry(PlanHost& h) {
         }
         h.force_plain = p.tx_focus >= zmin && p.tx_focus <= zmax;
     }
+    if (p.acq_kind == RCBF_HERCULES_2D) h.force_plain = true;   // non-separable: the plain form
     if (ua < 0) ua = 0;
     const int va = 1 - ua;
     h.swap_uv = ua == 1;
@@ -272,6 +278,7 @@ void setup_geometry(PlanHost& h) {
     a.f_number = (float)p.f_number;
     a.iq_ratio = p.iq_freq / p.fs;
     a.tx_wave = (int)p.tx_wave;
+    a.acq_kind = (int)p.acq_kind;
     a.tx_focus = p.tx_focus;
     a.tx_dir = nullptr;        // device directions, set by rcbf_plan
     a.interp = (int)p.interp;
@@ -386,8 +393,10 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
     a.status = h.d_status;
     if (p.tx_wave == RCBF_TX_PLANE) {
         std::vector<float2> dir(p.n_tx);
-        for (uint32_t i = 0; i < p.n_tx; ++i)
-            dir[i] = make_float2((float)std::sin(params->tx_angles[i]), (float)std::cos(params->tx_angles[i]));
+        for (uint32_t i = 0; i < p.n_tx; ++i) {
+            const double ang = params->tx_angles[p.acq_kind == RCBF_HERCULES_2D ? 0 : i];   // 2D: one wave
+            dir[i] = make_float2((float)std::sin(ang), (float)std::cos(ang));
+        }
         if (cudaMalloc(&h.d_tx_dir, dir.size() * sizeof(float2)) != cudaSuccess)
             return fail(RCBF_ENOMEM, "rcbf_plan: cudaMalloc directions");
         if (cudaMemcpy(h.d_tx_dir, dir.data(), dir.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -547,8 +556,9 @@ int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, 
         return set_error(RCBF_EINVAL, "rcbf_das_backward: decoded must be 16-byte aligned, float buffers 4-byte aligned");
     if (h.p.decoded_dtype != RCBF_F32 && h.p.decoded_dtype != RCBF_CF32)
         return set_error(RCBF_EUNSUPPORTED, "rcbf_das_backward: decoded_dtype must be RCBF_F32 or RCBF_CF32");
-    if (h.p.interp != RCBF_LINEAR || h.p.iq_freq > 0.0)
-        return set_error(RCBF_EUNSUPPORTED, "rcbf_das_backward: the adjoint is built for RF data with linear interpolation");
+    if (h.p.interp != RCBF_LINEAR || h.p.iq_freq > 0.0 || h.p.acq_kind == RCBF_HERCULES_2D)
+        return set_error(RCBF_EUNSUPPORTED, "rcbf_das_backward: the adjoint is built for separable RF data with "
+                                            "linear interpolation");
     const double cc = c > 0.f ? (double)c : h.p.c;
     DasArgs a;
     std::string why;

@@ -42,6 +42,88 @@ __device__ __forceinline__ float plain_cubic(const void* rf, long long base, int
     return fmaf(fmaf(fmaf(a3, f, a2), f, m1), f, p1);
 }
 
+// Interpolated sample of trace (i, j) at fractional sample s (linear or cubic).
+template <int DT, bool CUBIC>
+__device__ __forceinline__ float plain_interp(const void* rf, long long base, float s, int n_s, float scale) {
+    const float fl = floorf(s);
+    const float f = s - fl;
+    const int n = (int)fl;
+    if (CUBIC) return plain_cubic<DT>(rf, base, n, f, n_s, scale);
+    const float r0 = plain_sample<DT>(rf, base, n, n_s, scale), r1 = plain_sample<DT>(rf, base, n + 1, n_s, scale);
+    return (1.0f - f) * r0 + f * r1;
+}
+
+// HERCULES with its 2D receive aperture: one transmit wave, a point-element
+// receive path per (row i, column j) (not separable), F# window on the radial
+// lateral distance. One thread per voxel, FP32.
+template <int DT, bool CPLX, bool CUBIC, bool IQ>
+__global__ void __launch_bounds__(128)
+das_plain_2d_kernel(DasArgs a) {
+    const long long n_vox = (long long)a.n_u * a.n_v * a.n_w;
+    const long long vox = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (vox >= n_vox) return;
+    const int iu = (int)(vox % a.n_u);
+    const int iv = (int)((vox / a.n_u) % a.n_v);
+    const int iw = (int)(vox / ((long long)a.n_u * a.n_v));
+    float q[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        q[d] = (float)a.q0[d] + (float)a.Gu[d] * iu + (float)a.Gv[d] * iv + (float)a.Gw[d] * iw;
+    const float lat_tx = q[a.tx_axis], lat_rx = q[a.rx_axis], z = q[2];
+    const float fsc = (float)a.fs_over_c, t0fs = (float)a.t0fs;
+    float d_wave;
+    if (a.tx_wave == RCBF_TX_PLANE) {
+        const float2 sc = a.tx_dir[0];
+        d_wave = fmaf(z, sc.y, lat_tx * sc.x);
+    } else {
+        const float f = (float)a.tx_focus, dz = z - f;
+        d_wave = sqrtf(q[0] * q[0] + q[1] * q[1] + dz * dz) + f;
+    }
+    const float rk = (float)(a.iq_ratio * a.fs_over_c);
+    const double t0c = a.iq_ratio * a.t0fs;
+    const float ph_t0 = (float)(t0c - floor(t0c));
+    float ph_tx = 0.f;
+    if (IQ) {
+        const float p = rk * d_wave;
+        ph_tx = p - rintf(p) - ph_t0;
+    }
+    float acc = 0.f, acci = 0.f;
+    for (int i = 0; i < a.n_tx; ++i) {
+        const float dt = lat_tx - ((float)a.tx_e0 + i * (float)a.tx_pitch);
+        for (int j = 0; j < a.n_ch; ++j) {
+            const float dr = lat_rx - ((float)a.rx_e0 + j * (float)a.rx_pitch);
+            const float r2 = dr * dr + dt * dt;
+            float w = a.apod ? __ldg(a.apod + j) : 1.0f;
+            if (a.f_number > 0.f) {
+                const float al = a.f_number * sqrtf(r2), az = fabsf(z);
+                if (al < 0.5f * az) { const float cs = cospif(al / az); w *= cs * cs; }
+                else w = 0.f;
+            }
+            if (w == 0.f) continue;
+            const float d_rx = sqrtf(r2 + z * z);
+            const float s = (d_wave + d_rx) * fsc - t0fs;
+            const long long base = ((long long)i * a.n_ch + j) * a.n_s;
+            float vr = plain_interp<DT, CUBIC>(a.rf, base, s, a.n_s, a.scale), vi = 0.f;
+            if (CPLX) vi = plain_interp<DT, CUBIC>(a.rf, a.plane_stride + base, s, a.n_s, a.scale);
+            if (IQ) {
+                const float prx = rk * d_rx;
+                float x = ph_tx + (prx - rintf(prx));
+                x -= rintf(x);
+                float sn, cs;
+                __sincosf(6.28318530717958648f * x, &sn, &cs);
+                const float r0 = vr * cs - vi * sn;
+                vi = fmaf(vr, sn, vi * cs);
+                vr = r0;
+            }
+            acc += w * vr;
+            if (CPLX) acci += w * vi;
+        }
+    }
+    const long long o = (long long)iw * a.out_sw + (long long)iv * a.out_sv + (long long)iu * a.out_su;
+    a.image[o] = acc;
+    if (CPLX) a.image[a.image_plane + o] = acci;
+}
+
 template <int DT, bool CPLX, bool CUBIC, bool IQ>
 __global__ void __launch_bounds__(128)
 das_plain_kernel(DasArgs a) {
@@ -140,18 +222,22 @@ int launch_das_plain(const PlanHost& h, const DasArgs& a, cudaStream_t s) {
     (void)h;
     const long long n_vox = (long long)a.n_u * a.n_v * a.n_w;
     const unsigned grid = (unsigned)((n_vox + 127) / 128);
-#define RCBF_PLAIN(CU)                                                                             \
-    switch (a.dtype) {                                                                             \
-        case RCBF_F32: das_plain_kernel<RCBF_F32, false, CU, false><<<grid, 128, 0, s>>>(a); break;  \
-        case RCBF_F16: das_plain_kernel<RCBF_F16, false, CU, false><<<grid, 128, 0, s>>>(a); break;  \
-        case RCBF_I32: das_plain_kernel<RCBF_I32, false, CU, false><<<grid, 128, 0, s>>>(a); break;  \
-        case RCBF_CF32:                                                                            \
-            if (a.iq_ratio > 0.0) das_plain_kernel<RCBF_F32, true, CU, true><<<grid, 128, 0, s>>>(a); \
-            else das_plain_kernel<RCBF_F32, true, CU, false><<<grid, 128, 0, s>>>(a);               \
-            break;                                                                                 \
-        default: return set_error(RCBF_EUNSUPPORTED, "das: unsupported decoded dtype");            \
+#define RCBF_PLAIN(K, CU)                                                                       \
+    switch (a.dtype) {                                                                          \
+        case RCBF_F32: K<RCBF_F32, false, CU, false><<<grid, 128, 0, s>>>(a); break;              \
+        case RCBF_F16: K<RCBF_F16, false, CU, false><<<grid, 128, 0, s>>>(a); break;              \
+        case RCBF_I32: K<RCBF_I32, false, CU, false><<<grid, 128, 0, s>>>(a); break;              \
+        case RCBF_CF32:                                                                         \
+            if (a.iq_ratio > 0.0) K<RCBF_F32, true, CU, true><<<grid, 128, 0, s>>>(a);            \
+            else K<RCBF_F32, true, CU, false><<<grid, 128, 0, s>>>(a);                            \
+            break;                                                                              \
+        default: return set_error(RCBF_EUNSUPPORTED, "das: unsupported decoded dtype");         \
     }
-    if (a.interp == RCBF_CUBIC) { RCBF_PLAIN(true) } else { RCBF_PLAIN(false) }
+    if (a.acq_kind == RCBF_HERCULES_2D) {
+        if (a.interp == RCBF_CUBIC) { RCBF_PLAIN(das_plain_2d_kernel, true) } else { RCBF_PLAIN(das_plain_2d_kernel, false) }
+        return check_launch("das_plain_2d_kernel");
+    }
+    if (a.interp == RCBF_CUBIC) { RCBF_PLAIN(das_plain_kernel, true) } else { RCBF_PLAIN(das_plain_kernel, false) }
 #undef RCBF_PLAIN
     return check_launch("das_plain_kernel");
 }
@@ -197,7 +283,9 @@ int das_prepare_tile(const PlanHost& h, double c, int bu, int bv, int bw, double
         return RCBF_EUNSUPPORTED;
     }
     if (h.force_plain) {
-        if (why) *why = "das: the virtual-line-source focal depth lies inside the image (delays jump there)";
+        if (why) *why = h.p.acq_kind == RCBF_HERCULES_2D
+                            ? "das: a 2D receive aperture (non-separable delays) runs the plain form"
+                            : "das: the virtual-line-source focal depth lies inside the image (delays jump there)";
         return RCBF_EUNSUPPORTED;
     }
     if (a->interp == RCBF_CUBIC && a->dtype == RCBF_CF32 && a->W > 64) {

@@ -46,7 +46,7 @@ struct DasArgs {
     double tx_focus;       // virtual line source depth [m]
     const float2* tx_dir;  // plane waves: (sin a_i, cos a_i) per transmit (device)
     int tx_wave;           // rcbf_tx_wave
-    int pad_tx;
+    int acq_kind;          // rcbf_acq_kind (RCBF_HERCULES_2D: non-separable receive)
     float f_number;
     int interp;            // rcbf_interp
     int W;                 // pairs per window actually used (<= compiled stride)

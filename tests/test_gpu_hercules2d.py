@@ -1,0 +1,109 @@
+"""HERCULES with its 2D receive aperture (non-separable delays) on the GPU
+against the FP64 oracle: volumes and cross-planes, plane and diverging
+transmit waves, linear and cubic interpolation, real and complex data with
+an F# window and weights, IQ beamforming, 3D focusing of a point scatterer,
+and the entry points that are built for separable delays only."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import MM, HERCULES_2D
+from tests._frames import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2512_11086_gb300 as rc  # noqa: E402
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2512_11086_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _geom(wave, dims=(24, 20, 40), **kw):
+    g = synth.Geometry(n_tx=16, n_ch=16, n_samples=1024, acq_kind=HERCULES_2D, out_dims=dims,
+                       out_min=(-1.5 * MM, -1.2 * MM, 4 * MM), out_max=(1.5 * MM, 1.2 * MM, 14 * MM), **kw)
+    g.tx_wave = wave
+    if wave == "plane":
+        g.tx_angles = (0.12,)
+    else:
+        g.tx_focus = -6 * MM
+    return g
+
+
+def _run(g, decoded, dtype="f32", variant=rc.DAS_PLAIN, interp="linear", apod=None, f_number=None):
+    plan = rc.Plan(rc.make_params(g, decoded_dtype=dtype, das_variant=variant, interp=interp, f_number=f_number))
+    if dtype == "cf32":
+        dec = torch.from_numpy(np.stack([decoded.real, decoded.imag]).astype(np.float32)).cuda()
+    else:
+        dec = torch.from_numpy(decoded.astype(np.float32)).cuda()
+    w = None if apod is None else torch.from_numpy(apod.astype(np.float32)).cuda()
+    img = plan.das(dec, apod=w).cpu().numpy().astype(np.float64)
+    return (img[0] + 1j * img[1] if dtype == "cf32" else img), plan.info()
+
+
+@pytest.mark.parametrize("wave", ["plane", "point"])
+@pytest.mark.parametrize("interp", ["linear", "cubic"])
+@pytest.mark.parametrize("dims", [(24, 20, 40), (48, 1, 64), (1, 40, 64)])
+def test_2d_aperture_matches_oracle(wave, interp, dims):
+    g = _geom(wave, dims=dims)
+    fr = synth.make_frame(g, seed=51, n_scatterers=4, box_x=(-1 * MM, 1 * MM), box_y=(-1 * MM, 1 * MM),
+                          box_z=(5 * MM, 13 * MM), noise_frac=0.0)
+    want = oracle.das(g, fr.decoded.astype(np.float64), interp=interp)
+    got, info = _run(g, fr.decoded, variant=rc.DAS_TILED, interp=interp)      # runs the plain form
+    assert not info["tiled"]
+    err = rel_l2(got, want)
+    print("2D aperture %s %s %s: rel-L2 %.3e" % (wave, interp, dims, err))
+    assert err <= TOL
+
+
+def test_2d_aperture_focuses_a_point_in_3d():
+    p = (0.375 * MM, -0.25 * MM, 9.0 * MM)          # on a grid node (x 15, y 10, z 20)
+    g = _geom("plane", dims=(25, 25, 41))
+    g.out_min, g.out_max = (-1.5 * MM, -1.5 * MM, 7 * MM), (1.5 * MM, 1.5 * MM, 11 * MM)
+    fr = synth.make_frame(g, seed=52, n_scatterers=1, box_x=(p[0], p[0]), box_y=(p[1], p[1]), box_z=(p[2], p[2]),
+                          noise_frac=0.0)
+    got, _ = _run(g, fr.decoded)
+    pk = np.unravel_index(np.argmax(np.abs(got)), got.shape)
+    assert pk == (20, 10, 15)                       # (z, y, x) node of the point
+
+
+@pytest.mark.parametrize("wave", ["plane", "point"])
+def test_complex_fnumber_weights_and_iq(wave):
+    g = _geom(wave)
+    fr = synth.make_frame(g, seed=53, n_scatterers=4, analytic=True, noise_frac=0.0, box_x=(-1 * MM, 1 * MM),
+                          box_y=(-1 * MM, 1 * MM), box_z=(5 * MM, 13 * MM))
+    r = fr.decoded.astype(np.complex128)
+    w = np.random.default_rng(5).uniform(0.5, 1.5, g.n_ch)
+    got, _ = _run(g, fr.decoded, dtype="cf32", apod=w, f_number=0.8)
+    assert rel_l2(got, oracle.das(g, r, w=w, f_number=0.8)) <= TOL
+    g.iq_freq = 2.5e6                               # IQ beamforming of the same samples
+    got, _ = _run(g, fr.decoded, dtype="cf32")
+    assert rel_l2(got, oracle.das(g, r)) <= TOL
+
+
+def test_separable_only_entry_points_reject_2d_aperture():
+    g = _geom("plane")
+    plan = rc.Plan(rc.make_params(g, decoded_dtype="f32"))
+    dec = torch.zeros(g.n_tx, g.n_ch, g.n_samples, device="cuda")
+    gi = torch.zeros(g.out_dims[2], g.out_dims[1], g.out_dims[0], device="cuda")
+    with pytest.raises(rc.RcbfError) as e:
+        plan.das_backward(dec, gi)
+    assert e.value.code == rc.EUNSUPPORTED
+    p16 = rc.Plan(rc.make_params(g, decoded_dtype="f16"))
+    with pytest.raises(rc.RcbfError) as e:
+        rc.Batch([p16], None, [dec.half()], [gi])
+    assert e.value.code == rc.EUNSUPPORTED
+    bad = _geom("point")
+    bad.tx_focus = 2 * MM                           # a diverging point must lie behind the array
+    with pytest.raises(rc.RcbfError) as e:
+        rc.Plan(rc.make_params(bad, decoded_dtype="f32"))
+    assert e.value.code == rc.EINVAL
