@@ -230,6 +230,8 @@ OTHER_WORKLOADS = {
               "512x1024 grids, 16 cross-plane pairs) in one persistent launch",
     "autofocus": "differentiable DAS: complex 128 tx x 128 ch x 2048 decoded RF -> 256x512 image, "
                  "forward + adjoint (dRF, dc, dw) per step",
+    "hercules2d": "HERCULES 2D receive aperture (non-separable delays, plain form): decoded 128 rows x 128 "
+                  "columns x 2048 samples, one plane wave -> 128x128x256 FP32 voxels",
     "iq": "IQ pipeline: FORCES 128 tx x 128 ch x 4096 int16 at 4 f_d -> quadrature demodulation (166-tap "
           "integer FIR, decimation 4) -> exact decode of both planes -> cubic IQ DAS to 512x1024 (complex)",
 }
@@ -284,6 +286,19 @@ def run_other_workload(args):
         step = graph.replay
         sums = sum(f.geometry.sums for f in frames)
         extra["tiles"] = sorted({tuple(t) for t in tiles})
+    elif args.workload == "hercules2d":
+        g = dataclasses.replace(synth.hercules_volume_geometry(), acq_kind=synth.HERCULES_2D, hadamard_order=0,
+                                tx_wave="plane", tx_angles=(0.0,))
+        plan = rc.Plan(rc.make_params(g, decoded_dtype="f16"))
+        rng = np.random.default_rng(7)
+        dec = torch.from_numpy(rng.normal(size=(g.n_tx, g.n_ch, g.n_samples)).astype(np.float16)).to(dev)
+        out = torch.empty(plan.image_shape, device=dev)
+
+        def step():
+            plan.das(dec, out=out)
+        sums = g.sums
+        extra["plan"] = plan.info()
+        extra["data"] = "seeded Gaussian decoded samples (timing only)"
     elif args.workload == "iq":
         fr = synth.full_bscan(2)
         g_raw = fr.geometry
