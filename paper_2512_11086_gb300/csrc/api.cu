@@ -439,7 +439,7 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
     }
     if ((rc = configure_das(h)) != RCBF_OK) { std::string m = g_last_error; rcbf_destroy(plan); return set_error(rc, m); }
     {
-        const int sp = std::max(h.n_split[0], std::max(h.n_split[1], h.n_split[2]));
+        const int sp = std::max(std::max(h.n_split[0], h.n_split[1]), std::max(h.n_split[2], h.n_split[3]));
         if (sp > 1) {
             h.partial_floats = (size_t)sp * a.image_plane * (p.decoded_dtype == RCBF_CF32 ? 2 : 1);
             if (cudaMalloc(&h.d_partial, h.partial_floats * sizeof(float)) != cudaSuccess)

@@ -39,7 +39,7 @@ int batch_fail(rcbf_batch_s* b, int code, const std::string& msg) {
     return set_error(code, msg);
 }
 
-int class_of(int W) { return W <= 48 ? 48 : W <= 64 ? 64 : 128; }
+int class_of(int W) { return W <= 48 ? 48 : W <= 64 ? 64 : W <= 96 ? 96 : 128; }
 
 }  // namespace
 

@@ -150,6 +150,7 @@ template <int VU>
 int batch_configure_vu(int ws, int* per_sm, size_t* smem) {
     if (ws == 48) return batch_configure<VU, 48>(per_sm, smem);
     if (ws == 64) return batch_configure<VU, 64>(per_sm, smem);
+    if (ws == 96) return batch_configure<VU, 96>(per_sm, smem);
     return batch_configure<VU, 128>(per_sm, smem);
 }
 
@@ -158,6 +159,7 @@ int batch_launch_vu(int ws, unsigned grid, size_t smem, const int4* items, int n
                     int* counters, long long wait_ns, int withhold, cudaStream_t s) {
     if (ws == 48) batch_kernel<VU, 48><<<grid, kDasThreads, smem, s>>>(items, n_items, frames, counters, wait_ns, withhold);
     else if (ws == 64) batch_kernel<VU, 64><<<grid, kDasThreads, smem, s>>>(items, n_items, frames, counters, wait_ns, withhold);
+    else if (ws == 96) batch_kernel<VU, 96><<<grid, kDasThreads, smem, s>>>(items, n_items, frames, counters, wait_ns, withhold);
     else batch_kernel<VU, 128><<<grid, kDasThreads, smem, s>>>(items, n_items, frames, counters, wait_ns, withhold);
     return check_launch("batch_kernel");
 }

@@ -13,8 +13,19 @@
 
 namespace rcbf {
 
-template <int VU> int configure_das_vu(int ws, bool cplx, bool cubic, bool iq, int* per_sm);
-template <int VU> int launch_das_vu(const DasArgs& a, int ws, bool cplx, bool apod, bool cubic, bool iq, cudaStream_t s);
+template <int VU, bool CPLX> int configure_das_vu(int ws, bool cubic, bool iq, int* per_sm);
+template <int VU, bool CPLX> int launch_das_vu(const DasArgs& a, int ws, bool apod, bool cubic, bool iq, cudaStream_t s);
+
+namespace {
+template <int VU>
+int configure_vu(int ws, bool cplx, bool cubic, bool iq, int* per_sm) {
+    return cplx ? configure_das_vu<VU, true>(ws, cubic, iq, per_sm) : configure_das_vu<VU, false>(ws, cubic, iq, per_sm);
+}
+template <int VU>
+int launch_vu(const DasArgs& a, int ws, bool cplx, bool apod, bool cubic, bool iq, cudaStream_t s) {
+    return cplx ? launch_das_vu<VU, true>(a, ws, apod, cubic, iq, s) : launch_das_vu<VU, false>(a, ws, apod, cubic, iq, s);
+}
+}  // namespace
 
 namespace {
 
@@ -295,8 +306,8 @@ int das_prepare_tile(const PlanHost& h, double c, int bu, int bv, int bw, double
     return RCBF_OK;
 }
 
-static int stride_class(int W) { return W <= 48 ? 48 : W <= 64 ? 64 : 128; }
-static int class_index(int ws) { return ws == 48 ? 0 : ws == 64 ? 1 : 2; }
+static int stride_class(int W) { return W <= 48 ? 48 : W <= 64 ? 64 : W <= 96 ? 96 : 128; }
+static int class_index(int ws) { return ws == 48 ? 0 : ws == 64 ? 1 : ws == 96 ? 2 : 3; }
 
 int das_class_index(int W) { return class_index(stride_class(W)); }
 
@@ -312,9 +323,9 @@ int launch_das(const PlanHost& h, const DasArgs& a_in, cudaStream_t s) {
     a.partial_stride = a.image_plane * (cplx ? 2 : 1);
     int rc;
     switch (h.vu) {
-        case 1: rc = launch_das_vu<1>(a, ws, cplx, apod, cubic, iq, s); break;
-        case 2: rc = launch_das_vu<2>(a, ws, cplx, apod, cubic, iq, s); break;
-        default: rc = launch_das_vu<4>(a, ws, cplx, apod, cubic, iq, s); break;
+        case 1: rc = launch_vu<1>(a, ws, cplx, apod, cubic, iq, s); break;
+        case 2: rc = launch_vu<2>(a, ws, cplx, apod, cubic, iq, s); break;
+        default: rc = launch_vu<4>(a, ws, cplx, apod, cubic, iq, s); break;
     }
     if (rc != RCBF_OK || a.n_split == 1) return rc;
     const long long n = a.partial_stride;
@@ -329,8 +340,8 @@ int configure_das(PlanHost& h) {
     const bool cplx = h.p.decoded_dtype == RCBF_CF32;
     const bool cubic = h.p.interp == RCBF_CUBIC;
     const bool iq = cplx && h.p.iq_freq > 0.0;
-    for (int c = 0; c < 3; ++c) {
-        const int ws = c == 0 ? 48 : c == 1 ? 64 : 128;
+    for (int c = 0; c < 4; ++c) {
+        const int ws = c == 0 ? 48 : c == 1 ? 64 : c == 2 ? 96 : 128;
         int rc, n = 0;
         if (cubic && cplx && ws == 128) {          // runs the plain form
             h.das_blocks_per_sm[c] = 0;
@@ -338,9 +349,9 @@ int configure_das(PlanHost& h) {
             continue;
         }
         switch (h.vu) {
-            case 1: rc = configure_das_vu<1>(ws, cplx, cubic, iq, &n); break;
-            case 2: rc = configure_das_vu<2>(ws, cplx, cubic, iq, &n); break;
-            default: rc = configure_das_vu<4>(ws, cplx, cubic, iq, &n); break;
+            case 1: rc = configure_vu<1>(ws, cplx, cubic, iq, &n); break;
+            case 2: rc = configure_vu<2>(ws, cplx, cubic, iq, &n); break;
+            default: rc = configure_vu<4>(ws, cplx, cubic, iq, &n); break;
         }
         if (rc != RCBF_OK) return rc;
         h.das_blocks_per_sm[c] = n;

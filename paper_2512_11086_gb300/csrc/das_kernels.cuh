@@ -1,6 +1,7 @@
 // das_kernels.cuh — the tiled DAS kernel (one tile per CTA) and its host
-// launcher / configuration, instantiated per voxels-per-thread class in
-// das_vu1.cu, das_vu2.cu and das_vu4.cu so they compile in parallel.
+// launcher / configuration, instantiated per voxels-per-thread class and
+// real / complex data in das_vu{1,2,4}_{real,cplx}.cu so they compile in
+// parallel.
 #pragma once
 
 #include "das_tile.cuh"
@@ -31,12 +32,14 @@ int das_cfg_one(int* per_sm) {
     return RCBF_OK;
 }
 
-// Instantiated forms: real or complex data, with or without weights, linear
-// or cubic pieces, and (complex only) IQ beamforming. Complex data with cubic
+// Instantiated forms: window classes of 48, 64, 96 and 128 intervals; real or
+// complex data, with or without weights, linear or cubic pieces, and (complex
+// only) IQ beamforming. Complex data with cubic
 // pieces has no 128-interval class (it would not fit two CTAs per SM); such
 // windows run the plain form.
-template <int VU>
-int configure_das_vu(int ws, bool cplx, bool cubic, bool iq, int* per_sm) {
+template <int VU, bool CPLX_T>
+int configure_das_vu(int ws, bool cubic, bool iq, int* per_sm) {
+    constexpr bool cplx = CPLX_T;
     int rc;
 #define RCBF_CFG(WSV, CP, CU, Q)                                                           \
     if ((rc = das_cfg_one<VU, WSV, CP, false, CU, Q>(per_sm)) != RCBF_OK) return rc;      \
@@ -44,14 +47,15 @@ int configure_das_vu(int ws, bool cplx, bool cubic, bool iq, int* per_sm) {
 #define RCBF_CFG_C(WSV, CU) \
     if (iq) { RCBF_CFG(WSV, true, CU, true) } else { RCBF_CFG(WSV, true, CU, false) }
 #define RCBF_CFG_WS(WSV)                                                                   \
-    if (cubic) { if (cplx) { RCBF_CFG_C(WSV, true) } else { RCBF_CFG(WSV, false, true, false) } } \
-    else { if (cplx) { RCBF_CFG_C(WSV, false) } else { RCBF_CFG(WSV, false, false, false) } }
+    if constexpr (CPLX_T) { if (cubic) { RCBF_CFG_C(WSV, true) } else { RCBF_CFG_C(WSV, false) } } \
+    else { if (cubic) { RCBF_CFG(WSV, false, true, false) } else { RCBF_CFG(WSV, false, false, false) } }
     if (ws == 48) { RCBF_CFG_WS(48) }
     else if (ws == 64) { RCBF_CFG_WS(64) }
+    else if (ws == 96) { RCBF_CFG_WS(96) }
     else {
         if (cubic && cplx) return set_error(RCBF_EUNSUPPORTED, "das: no complex cubic 128-interval class");
-        if (cubic) { RCBF_CFG(128, false, true, false) }
-        else { if (cplx) { RCBF_CFG_C(128, false) } else { RCBF_CFG(128, false, false, false) } }
+        if constexpr (CPLX_T) { RCBF_CFG_C(128, false) }
+        else { if (cubic) { RCBF_CFG(128, false, true, false) } else { RCBF_CFG(128, false, false, false) } }
     }
 #undef RCBF_CFG_WS
 #undef RCBF_CFG_C
@@ -59,8 +63,9 @@ int configure_das_vu(int ws, bool cplx, bool cubic, bool iq, int* per_sm) {
     return RCBF_OK;
 }
 
-template <int VU>
-int launch_das_vu(const DasArgs& a, int ws, bool cplx, bool apod, bool cubic, bool iq, cudaStream_t s) {
+template <int VU, bool CPLX_T>
+int launch_das_vu(const DasArgs& a, int ws, bool apod, bool cubic, bool iq, cudaStream_t s) {
+    constexpr bool cplx = CPLX_T;
     const unsigned grid = (unsigned)a.tiles_u * a.tiles_v * a.tiles_w * a.n_split;
 #define RCBF_LAUNCH(WSV, CP, AP, CU, Q)                                                                       \
     das_tiled_kernel<VU, WSV, CP, AP, CU, Q><<<grid, kDasThreads, DasCfg<VU, WSV, CP, CU>::SMEM, s>>>(a);    \
@@ -70,14 +75,15 @@ int launch_das_vu(const DasArgs& a, int ws, bool cplx, bool apod, bool cubic, bo
 #define RCBF_C(WSV, CU) \
     if (iq) { RCBF_AP(WSV, true, CU, true) } else { RCBF_AP(WSV, true, CU, false) }
 #define RCBF_WS(WSV)                                                                                  \
-    if (cubic) { if (cplx) { RCBF_C(WSV, true) } else { RCBF_AP(WSV, false, true, false) } }         \
-    else { if (cplx) { RCBF_C(WSV, false) } else { RCBF_AP(WSV, false, false, false) } }
+    if constexpr (CPLX_T) { if (cubic) { RCBF_C(WSV, true) } else { RCBF_C(WSV, false) } }            \
+    else { if (cubic) { RCBF_AP(WSV, false, true, false) } else { RCBF_AP(WSV, false, false, false) } }
     if (ws == 48) { RCBF_WS(48) }
     else if (ws == 64) { RCBF_WS(64) }
+    else if (ws == 96) { RCBF_WS(96) }
     else {
         if (cubic && cplx) return set_error(RCBF_EUNSUPPORTED, "das: no complex cubic 128-interval class");
-        if (cubic) { RCBF_AP(128, false, true, false) }
-        else { if (cplx) { RCBF_C(128, false) } else { RCBF_AP(128, false, false, false) } }
+        if constexpr (CPLX_T) { RCBF_C(128, false) }
+        else { if (cubic) { RCBF_AP(128, false, true, false) } else { RCBF_AP(128, false, false, false) } }
     }
 #undef RCBF_WS
 #undef RCBF_C

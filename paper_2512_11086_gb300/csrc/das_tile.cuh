@@ -72,7 +72,7 @@ struct DasCfg {
     static constexpr int BU = 32 * VU;             // tile extent along u
     // transmits per stage, so that three line-piece buffers and two raw
     // buffers fit two CTAs per SM for every window class
-    static constexpr int CI_BASE = (WS <= 48 ? 8 : WS <= 64 ? 4 : 2) / (CPLX ? 2 : 1) / (CUBIC ? 2 : 1);
+    static constexpr int CI_BASE = (WS <= 48 ? 8 : WS <= 96 ? 4 : 2) / (CPLX ? 2 : 1) / (CUBIC ? 2 : 1);
     static constexpr int CI = CI_BASE > 0 ? CI_BASE : 1;
     static constexpr int CJ = 8;                   // channels per stage
     static constexpr int NWIN = CI * CJ;           // windows per stage

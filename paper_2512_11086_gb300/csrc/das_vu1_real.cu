@@ -1,0 +1,7 @@
+// das_vu1_real.cu — tiled DAS instantiations with 1 voxel(s) per thread along u, real data.
+#include "das_kernels.cuh"
+
+namespace rcbf {
+template int configure_das_vu<1, false>(int, bool, bool, int*);
+template int launch_das_vu<1, false>(const DasArgs&, int, bool, bool, bool, cudaStream_t);
+}  // namespace rcbf

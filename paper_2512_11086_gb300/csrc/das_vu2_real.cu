@@ -1,0 +1,7 @@
+// das_vu2_real.cu — tiled DAS instantiations with 2 voxel(s) per thread along u, real data.
+#include "das_kernels.cuh"
+
+namespace rcbf {
+template int configure_das_vu<2, false>(int, bool, bool, int*);
+template int launch_das_vu<2, false>(const DasArgs&, int, bool, bool, bool, cudaStream_t);
+}  // namespace rcbf

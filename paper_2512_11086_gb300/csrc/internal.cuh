@@ -101,8 +101,8 @@ struct PlanHost {
     int* d_status;          // device status word
     int n_sms;              // SMs of the plan's device
     int decode_blocks_per_sm;
-    int das_blocks_per_sm[3];   // by window stride class (48, 64, 128)
-    int n_split[3];         // channel split by window stride class
+    int das_blocks_per_sm[4];   // by window stride class (48, 64, 96, 128)
+    int n_split[4];         // channel split by window stride class
     float* d_partial;       // DAS partial images (channel split), plan-owned
     size_t partial_floats;
     int16_t* d_taps;        // device demodulation FIR taps (demod_decimation > 0)
