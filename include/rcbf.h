@@ -186,6 +186,12 @@ typedef struct rcbf_params {
     double   tx_focus;          /* RCBF_TX_VLS: depth f of the virtual line sources [m] */
     const double* tx_angles;    /* RCBF_TX_PLANE: HOST pointer to n_tx steering angles [rad], |angle| < pi/2,
                                    copied by rcbf_plan */
+    /* Receive channels as a slice of a larger array (a channel-sharded frame: each GPU
+     * beamforms its slice and the partial images add, §8(e)-style one reduce-sum):
+     * channel j of this plan is element rx_channel_offset + j of rx_channels_total.
+     * 0 / 0 = the plan's channels are the whole array. */
+    uint32_t rx_channel_offset;
+    uint32_t rx_channels_total;
 } rcbf_params;
 
 typedef struct rcbf_plan_s*  rcbf_plan_t;

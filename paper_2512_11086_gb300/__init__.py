@@ -64,6 +64,7 @@ class Params(ctypes.Structure):
         ("iq_freq", ctypes.c_double),
         ("tx_wave", ctypes.c_uint32), ("reserved3", ctypes.c_uint32),
         ("tx_focus", ctypes.c_double), ("tx_angles", ctypes.c_void_p),
+        ("rx_channel_offset", ctypes.c_uint32), ("rx_channels_total", ctypes.c_uint32),
     ]
 
 

@@ -172,6 +172,11 @@ int validate(const rcbf_params* p) {
             return set_error(RCBF_EINVAL, "rcbf_plan: raw trace too long");
     }
     if (!(p->iq_freq >= 0.0)) return set_error(RCBF_EINVAL, "rcbf_plan: iq_freq must be >= 0");
+    if (p->rx_channels_total ? (uint64_t)p->rx_channel_offset + p->n_ch > p->rx_channels_total
+                             : p->rx_channel_offset != 0)
+        return set_error(RCBF_EINVAL, "rcbf_plan: the channel slice must lie inside rx_channels_total");
+    if (p->rx_channels_total && p->acq_kind == RCBF_HERCULES_2D)
+        return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: a 2D receive aperture is not sliced by channel");
     if (p->tx_wave > RCBF_TX_POINT) return set_error(RCBF_EINVAL, "rcbf_plan: unknown tx_wave");
     const bool h2d = p->acq_kind == RCBF_HERCULES_2D;
     if (h2d && p->tx_wave != RCBF_TX_PLANE && p->tx_wave != RCBF_TX_POINT)
@@ -273,7 +278,8 @@ void setup_geometry(PlanHost& h) {
     a.tx_pitch = p.tx_pitch;
     a.rx_pitch = p.rx_pitch;
     a.tx_e0 = -0.5 * (double)(p.n_tx - 1) * p.tx_pitch;
-    a.rx_e0 = -0.5 * (double)(p.n_ch - 1) * p.rx_pitch;
+    const uint32_t rx_total = p.rx_channels_total ? p.rx_channels_total : p.n_ch;
+    a.rx_e0 = (-0.5 * (double)(rx_total - 1) + (double)p.rx_channel_offset) * p.rx_pitch;
     a.fs = p.fs;
     a.f_number = (float)p.f_number;
     a.iq_ratio = p.iq_freq / p.fs;

@@ -100,3 +100,23 @@ def test_misaligned_buffers_are_rejected():
     with pytest.raises(rc.RcbfError) as e:
         plan.decode(rf.view(g.n_tx, g.n_ch, g.n_samples))
     assert e.value.code == rc.EINVAL
+
+
+def test_channel_shards_sum_to_the_frame():
+    # the per-GPU plans of a channel-sharded frame, run one after the other
+    # on one GPU: each sees only its slice of the decoded data, with the
+    # element positions of that slice in the whole array
+    from paper_2512_11086_gb300 import shard
+    g = synth.Geometry(n_tx=32, n_ch=48, n_samples=1024, out_dims=(96, 1, 160),
+                       out_min=(-2 * MM, 0.0, 4 * MM), out_max=(2 * MM, 0.0, 14 * MM))
+    fr = synth.make_frame(g, seed=65, n_scatterers=5, box_x=(-1.5 * MM, 1.5 * MM), box_z=(5 * MM, 13 * MM))
+    dec = torch.from_numpy(fr.decoded).cuda()
+    total = None
+    for rank in range(3):
+        off, cnt = shard.channel_slices(g.n_ch, 3)[rank]
+        plan = rc.Plan(shard.shard_params(g, rank, 3, decoded_dtype="f32"))
+        part = plan.das(dec[:, off:off + cnt].contiguous())
+        total = part if total is None else total + part
+    full = rc.Plan(rc.make_params(g, decoded_dtype="f32")).das(dec).cpu().numpy()
+    assert rel_l2(total.cpu().numpy(), full) <= 1e-5
+    assert rel_l2(total.cpu().numpy(), oracle.das(g, fr.decoded.astype(np.float64))) <= TOL
