@@ -66,8 +66,9 @@ __device__ __forceinline__ float plain_interp(const void* rf, long long base, fl
 
 // HERCULES with its 2D receive aperture: one transmit wave, a point-element
 // receive path per (row i, column j) (not separable), F# window on the radial
-// lateral distance. One thread per voxel, FP32.
-template <int DT, bool CPLX, bool CUBIC, bool IQ>
+// lateral distance (FN). One thread per voxel, FP32; the receive distance is
+// x * rsqrt(x) of the squared distance (x > 0 below the array).
+template <int DT, bool CPLX, bool CUBIC, bool IQ, bool FN>
 __global__ void __launch_bounds__(128)
 das_plain_2d_kernel(DasArgs a) {
     const long long n_vox = (long long)a.n_u * a.n_v * a.n_w;
@@ -101,17 +102,18 @@ das_plain_2d_kernel(DasArgs a) {
     float acc = 0.f, acci = 0.f;
     for (int i = 0; i < a.n_tx; ++i) {
         const float dt = lat_tx - ((float)a.tx_e0 + i * (float)a.tx_pitch);
+        const float p2 = dt * dt + z * z;
         for (int j = 0; j < a.n_ch; ++j) {
             const float dr = lat_rx - ((float)a.rx_e0 + j * (float)a.rx_pitch);
-            const float r2 = dr * dr + dt * dt;
             float w = a.apod ? __ldg(a.apod + j) : 1.0f;
-            if (a.f_number > 0.f) {
-                const float al = a.f_number * sqrtf(r2), az = fabsf(z);
+            if (FN) {
+                const float al = a.f_number * sqrtf(fmaf(dr, dr, dt * dt)), az = fabsf(z);
                 if (al < 0.5f * az) { const float cs = cospif(al / az); w *= cs * cs; }
                 else w = 0.f;
+                if (w == 0.f) continue;
             }
-            if (w == 0.f) continue;
-            const float d_rx = sqrtf(r2 + z * z);
+            const float x2 = fmaf(dr, dr, p2);
+            const float d_rx = x2 * rsqrtf(x2);
             const float s = (d_wave + d_rx) * fsc - t0fs;
             const long long base = ((long long)i * a.n_ch + j) * a.n_s;
             float vr = plain_interp<DT, CUBIC>(a.rf, base, s, a.n_s, a.scale), vi = 0.f;
@@ -233,22 +235,26 @@ int launch_das_plain(const PlanHost& h, const DasArgs& a, cudaStream_t s) {
     (void)h;
     const long long n_vox = (long long)a.n_u * a.n_v * a.n_w;
     const unsigned grid = (unsigned)((n_vox + 127) / 128);
-#define RCBF_PLAIN(K, CU)                                                                       \
+#define RCBF_PLAIN(K, CU, ...)                                                                  \
     switch (a.dtype) {                                                                          \
-        case RCBF_F32: K<RCBF_F32, false, CU, false><<<grid, 128, 0, s>>>(a); break;              \
-        case RCBF_F16: K<RCBF_F16, false, CU, false><<<grid, 128, 0, s>>>(a); break;              \
-        case RCBF_I32: K<RCBF_I32, false, CU, false><<<grid, 128, 0, s>>>(a); break;              \
+        case RCBF_F32: K<RCBF_F32, false, CU, false __VA_ARGS__><<<grid, 128, 0, s>>>(a); break;  \
+        case RCBF_F16: K<RCBF_F16, false, CU, false __VA_ARGS__><<<grid, 128, 0, s>>>(a); break;  \
+        case RCBF_I32: K<RCBF_I32, false, CU, false __VA_ARGS__><<<grid, 128, 0, s>>>(a); break;  \
         case RCBF_CF32:                                                                         \
-            if (a.iq_ratio > 0.0) K<RCBF_F32, true, CU, true><<<grid, 128, 0, s>>>(a);            \
-            else K<RCBF_F32, true, CU, false><<<grid, 128, 0, s>>>(a);                            \
+            if (a.iq_ratio > 0.0) K<RCBF_F32, true, CU, true __VA_ARGS__><<<grid, 128, 0, s>>>(a); \
+            else K<RCBF_F32, true, CU, false __VA_ARGS__><<<grid, 128, 0, s>>>(a);                 \
             break;                                                                              \
         default: return set_error(RCBF_EUNSUPPORTED, "das: unsupported decoded dtype");         \
     }
+#define RCBF_PLAIN_2D(CU)                                                                       \
+    if (a.f_number > 0.f) { RCBF_PLAIN(das_plain_2d_kernel, CU, , true) }                       \
+    else { RCBF_PLAIN(das_plain_2d_kernel, CU, , false) }
     if (a.acq_kind == RCBF_HERCULES_2D) {
-        if (a.interp == RCBF_CUBIC) { RCBF_PLAIN(das_plain_2d_kernel, true) } else { RCBF_PLAIN(das_plain_2d_kernel, false) }
+        if (a.interp == RCBF_CUBIC) { RCBF_PLAIN_2D(true) } else { RCBF_PLAIN_2D(false) }
         return check_launch("das_plain_2d_kernel");
     }
-    if (a.interp == RCBF_CUBIC) { RCBF_PLAIN(das_plain_kernel, true) } else { RCBF_PLAIN(das_plain_kernel, false) }
+    if (a.interp == RCBF_CUBIC) { RCBF_PLAIN(das_plain_kernel, true, ) } else { RCBF_PLAIN(das_plain_kernel, false, ) }
+#undef RCBF_PLAIN_2D
 #undef RCBF_PLAIN
     return check_launch("das_plain_kernel");
 }
