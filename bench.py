@@ -230,7 +230,7 @@ OTHER_WORKLOADS = {
               "512x1024 grids, 16 cross-plane pairs) in one persistent launch",
     "autofocus": "differentiable DAS: complex 128 tx x 128 ch x 2048 decoded RF -> 256x512 image, "
                  "forward + adjoint (dRF, dc, dw) per step",
-    "hercules2d": "HERCULES 2D receive aperture (non-separable delays, plain form): decoded 128 rows x 128 "
+    "hercules2d": "HERCULES 2D receive aperture (non-separable delays, tiled form): decoded FP16 128 rows x 128 "
                   "columns x 2048 samples, one plane wave -> 128x128x256 FP32 voxels",
     "iq": "IQ pipeline: FORCES 128 tx x 128 ch x 4096 int16 at 4 f_d -> quadrature demodulation (166-tap "
           "integer FIR, decimation 4) -> exact decode of both planes -> cubic IQ DAS to 512x1024 (complex)",

@@ -250,7 +250,13 @@ void setup_geometry(PlanHost& h) {
         }
         h.force_plain = p.tx_focus >= zmin && p.tx_focus <= zmax;
     }
-    if (p.acq_kind == RCBF_HERCULES_2D) h.force_plain = true;   // non-separable: the plain form
+    const bool h2d = p.acq_kind == RCBF_HERCULES_2D;
+    if (h2d) {
+        // the tiled 2D form takes no F# window (its weight is radial, per
+        // (i, j)), needs the rows and columns along different axes, and
+        // holds one voxel per thread along u
+        h.force_plain = p.f_number > 0.0 || tx_axis == rx_axis || (p.tile[0] && p.tile[0] != 32);
+    }
     if (ua < 0) ua = 0;
     const int va = 1 - ua;
     h.swap_uv = ua == 1;
@@ -297,8 +303,59 @@ void setup_geometry(PlanHost& h) {
     auto radius_sum = [&](int bu, int bv, int bw) {
         return tile_radius(G, tx_axis, ua, va, bu, bv, bw) + tile_radius(G, rx_axis, ua, va, bu, bv, bw);
     };
+    // 2D receive aperture: the receive path spans at most the tile's
+    // bounding-box diagonal; the transmit wave's path spans, over a tile's
+    // box, |cos a| 2 h_z + |sin a| 2 h_lat (plane) or the largest difference
+    // between the farthest corner and the nearest point from the virtual
+    // source (diverging wave, over every tile of the image)
+    auto half_ext = [&](int d, int bu, int bv, int bw) {
+        return 0.5 * (std::fabs(G[d * 4 + ua]) * (bu - 1) + std::fabs(G[d * 4 + va]) * (bv - 1) +
+                      std::fabs(G[d * 4 + 2]) * (bw - 1));
+    };
+    auto box_diag = [&](int bu, int bv, int bw) {
+        double e2 = 0.0;
+        for (int d = 0; d < 3; ++d) e2 += 4.0 * half_ext(d, bu, bv, bw) * half_ext(d, bu, bv, bw);
+        return std::sqrt(e2);
+    };
+    auto wave_spread = [&](int bu, int bv, int bw) {
+        const double hx = half_ext(0, bu, bv, bw), hy = half_ext(1, bu, bv, bw), hz = half_ext(2, bu, bv, bw);
+        if (p.tx_wave == RCBF_TX_PLANE) {
+            const double ang = h.tx_angle0;
+            const double cs = h.has_tx_angle0 ? std::fabs(std::cos(ang)) : 1.0;
+            const double sn = h.has_tx_angle0 ? std::fabs(std::sin(ang)) : 1.0;
+            return 2.0 * (cs * hz + sn * (tx_axis ? hy : hx));
+        }
+        const long long tu = ((long long)p.out_dims[ua] + bu - 1) / bu, tv = ((long long)p.out_dims[va] + bv - 1) / bv;
+        const long long tw = ((long long)p.out_dims[2] + bw - 1) / bw;
+        double spread = 0.0;
+        for (long long w = 0; w < tw; ++w)
+            for (long long v = 0; v < tv; ++v)
+                for (long long u = 0; u < tu; ++u) {
+                    const double cu = u * bu + 0.5 * (bu - 1), cv = v * bv + 0.5 * (bv - 1), cw = w * bw + 0.5 * (bw - 1);
+                    double q[3];
+                    for (int d = 0; d < 3; ++d) q[d] = G[d * 4 + 3] + G[d * 4 + ua] * cu + G[d * 4 + va] * cv + G[d * 4 + 2] * cw;
+                    const double zf = std::fabs(q[2] - p.tx_focus);
+                    const double nx = std::fmax(std::fabs(q[0]) - hx, 0.0), ny = std::fmax(std::fabs(q[1]) - hy, 0.0);
+                    const double nz = std::fmax(zf - hz, 0.0);
+                    const double fx = std::fabs(q[0]) + hx, fy = std::fabs(q[1]) + hy, fz = zf + hz;
+                    spread = std::fmax(spread, std::sqrt(fx * fx + fy * fy + fz * fz) - std::sqrt(nx * nx + ny * ny + nz * nz));
+                }
+        return spread;
+    };
     int best_bu = 64, best_bv = 1, best_bw = 16;
-    if (p.tile[0]) {
+    if (h2d && !p.tile[0]) {
+        const double spm = p.fs / p.c;
+        double best_key = 1e300;
+        best_bu = 32;
+        for (int bv = 1; bv <= 32; bv *= 2) {
+            const int bw = 32 / bv;
+            if (bv > 1 && a.n_v == 1) continue;
+            const double W = std::floor(4.0 + (box_diag(32, bv, bw) + wave_spread(32, bv, bw)) * spm + 0.02) + 1.0;
+            const double cls = W <= 64 ? 0.0 : W <= 96 ? 1.0 : W <= 128 ? 2.0 : 3.0;
+            const double key = cls * 1e6 + W;
+            if (key < best_key) { best_key = key; best_bv = bv; best_bw = bw; }
+        }
+    } else if (p.tile[0]) {
         best_bu = (int)p.tile[0];
         best_bv = (int)p.tile[1];
         best_bw = (int)p.tile[2];
@@ -332,6 +389,10 @@ void setup_geometry(PlanHost& h) {
     a.tiles_w = (a.n_w + a.bw - 1) / a.bw;
     h.r_alpha_m = tile_radius(G, tx_axis, ua, va, a.bu, a.bv, a.bw);
     h.r_beta_m = tile_radius(G, rx_axis, ua, va, a.bu, a.bv, a.bw);
+    if (h2d) {
+        h.r_alpha_m = wave_spread(a.bu, a.bv, a.bw);    // the 2D form's transmit spread [m]
+        h.r_beta_m = 0.0;
+    }
 
     // adjoint tile: 32 voxels along u by 32 rows, lanes over the rows with z
     // fastest; the most z-rows whose window stays within 128 samples
@@ -381,6 +442,8 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
     h.p.decode_matrix = nullptr;   // the matrix is copied, never referenced later
     h.p.demod_taps = nullptr;      // so are the taps
     h.p.tx_angles = nullptr;       // and the plane-wave angles
+    h.has_tx_angle0 = params->tx_angles != nullptr;
+    h.tx_angle0 = params->tx_angles ? params->tx_angles[0] : 0.0;
     const rcbf_params& p = h.p;
 
     setup_geometry(h);
@@ -469,7 +532,7 @@ int rcbf_plan_query(rcbf_plan_t plan, rcbf_plan_info* info) {
     const bool tiled = h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok && fits;
     info->tiled = tiled ? 1u : 0u;
     info->window = (uint32_t)a.W;
-    const int sp = tiled ? std::max(1, h.n_split[das_class_index(a.W)]) : 1;
+    const int sp = tiled ? std::max(1, h.n_split[das_class_index(a.W, h.p.acq_kind == RCBF_HERCULES_2D)]) : 1;
     info->n_split = (uint32_t)sp;
     info->das_launches = sp > 1 ? 2u : 1u;
     info->decode_launches = h.p.hadamard_order ? (h.p.decoded_dtype == RCBF_CF32 ? 2u : 1u) : 0u;

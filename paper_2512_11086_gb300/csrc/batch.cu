@@ -71,6 +71,8 @@ int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t
         if (h.p.interp != RCBF_LINEAR) return set_error(RCBF_EUNSUPPORTED, at + "batch frames use linear interpolation");
         if (h.p.iq_freq > 0.0 || h.p.demod_decimation)
             return set_error(RCBF_EUNSUPPORTED, at + "batch frames are RF frames without demodulation");
+        if (h.p.acq_kind == RCBF_HERCULES_2D)
+            return set_error(RCBF_EUNSUPPORTED, at + "batch frames use separable (row-column) delays");
         if (h.das.bu != bu) return set_error(RCBF_EINVAL, at + "all plans of a batch need the same tile extent along u");
         if (!decoded[f] || !images[f] || (h.p.hadamard_order && (!rf || !rf[f])))
             return set_error(RCBF_EINVAL, at + "NULL buffer");

@@ -13,17 +13,34 @@
 
 namespace rcbf {
 
-template <int VU, bool CPLX> int configure_das_vu(int ws, bool cubic, bool iq, int* per_sm);
-template <int VU, bool CPLX> int launch_das_vu(const DasArgs& a, int ws, bool apod, bool cubic, bool iq, cudaStream_t s);
+template <int VU, bool CPLX, bool D2> int configure_das_vu(int ws, bool cubic, bool iq, int* per_sm);
+template <int VU, bool CPLX, bool D2>
+int launch_das_vu(const DasArgs& a, int ws, bool apod, bool cubic, bool iq, cudaStream_t s);
 
 namespace {
 template <int VU>
-int configure_vu(int ws, bool cplx, bool cubic, bool iq, int* per_sm) {
-    return cplx ? configure_das_vu<VU, true>(ws, cubic, iq, per_sm) : configure_das_vu<VU, false>(ws, cubic, iq, per_sm);
+int configure_vu(int ws, bool cplx, bool cubic, bool iq, bool d2, int* per_sm) {
+    if (d2) {
+        if constexpr (VU == 1)
+            return cplx ? configure_das_vu<1, true, true>(ws, cubic, iq, per_sm)
+                        : configure_das_vu<1, false, true>(ws, cubic, iq, per_sm);
+        else
+            return set_error(RCBF_EUNSUPPORTED, "das: the 2D aperture tiles hold one voxel per thread along u");
+    }
+    return cplx ? configure_das_vu<VU, true, false>(ws, cubic, iq, per_sm)
+                : configure_das_vu<VU, false, false>(ws, cubic, iq, per_sm);
 }
 template <int VU>
-int launch_vu(const DasArgs& a, int ws, bool cplx, bool apod, bool cubic, bool iq, cudaStream_t s) {
-    return cplx ? launch_das_vu<VU, true>(a, ws, apod, cubic, iq, s) : launch_das_vu<VU, false>(a, ws, apod, cubic, iq, s);
+int launch_vu(const DasArgs& a, int ws, bool cplx, bool apod, bool cubic, bool iq, bool d2, cudaStream_t s) {
+    if (d2) {
+        if constexpr (VU == 1)
+            return cplx ? launch_das_vu<1, true, true>(a, ws, apod, cubic, iq, s)
+                        : launch_das_vu<1, false, true>(a, ws, apod, cubic, iq, s);
+        else
+            return set_error(RCBF_EUNSUPPORTED, "das: the 2D aperture tiles hold one voxel per thread along u");
+    }
+    return cplx ? launch_das_vu<VU, true, false>(a, ws, apod, cubic, iq, s)
+                : launch_das_vu<VU, false, false>(a, ws, apod, cubic, iq, s);
 }
 }  // namespace
 
@@ -279,9 +296,24 @@ int das_prepare_tile(const PlanHost& h, double c, int bu, int bv, int bw, double
     a->c = c;
     a->fs_over_c = h.p.fs / c;
     a->t0fs = h.p.t0 * h.p.fs;
-    const double R = (r_alpha_m + r_beta_m) * a->fs_over_c;
-    a->lo = (int)std::floor(-R) - 1;
-    a->W = (int)std::floor(4.0 + 2.0 * R + 0.01) + 1;
+    if (h.p.acq_kind == RCBF_HERCULES_2D) {
+        // 2D receive aperture: the receive path varies over the tile by at
+        // most the diagonal D of its bounding box, the transmit wave's path by
+        // at most r_alpha (its largest spread over a tile's box, in metres);
+        // the kernel places each window from box bounds (no common offset lo)
+        double e2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            const double ext = std::fabs(a->Gu[d]) * (bu - 1) + std::fabs(a->Gv[d]) * (bv - 1) + std::fabs(a->Gw[d]) * (bw - 1);
+            e2 += ext * ext;
+        }
+        const double X = (std::sqrt(e2) + r_alpha_m) * a->fs_over_c;
+        a->lo = 0;
+        a->W = (int)std::floor(4.0 + X + 0.02) + 1;
+    } else {
+        const double R = (r_alpha_m + r_beta_m) * a->fs_over_c;
+        a->lo = (int)std::floor(-R) - 1;
+        a->W = (int)std::floor(4.0 + 2.0 * R + 0.01) + 1;
+    }
     a->H = a->W / 2;
     a->raw_samples = ((a->W + 8 + 7) / 8) * 8;
     // alpha and beta are clamped to reference +- reach in the kernel; the
@@ -289,6 +321,7 @@ int das_prepare_tile(const PlanHost& h, double c, int bu, int bv, int bw, double
     // interval index lands in [0, W-1] whatever the input (NaN included)
     a->reach_a = (float)(r_alpha_m * a->fs_over_c + 0.004);
     a->reach_b = (float)(r_beta_m * a->fs_over_c + 0.004);
+    if (h.p.acq_kind == RCBF_HERCULES_2D) a->reach_a = 0.004f;   // slack of the kernel's box bounds
     if (a->interp == RCBF_CUBIC) {
         // the 4-point stencil of interval n reaches one sample before the
         // window start and two after its interval: copies start one sample
@@ -301,7 +334,7 @@ int das_prepare_tile(const PlanHost& h, double c, int bu, int bv, int bw, double
     }
     if (h.force_plain) {
         if (why) *why = h.p.acq_kind == RCBF_HERCULES_2D
-                            ? "das: a 2D receive aperture (non-separable delays) runs the plain form"
+                            ? "das: a 2D receive aperture with an F# window or a tile wider than 32 voxels runs the plain form"
                             : "das: the virtual-line-source focal depth lies inside the image (delays jump there)";
         return RCBF_EUNSUPPORTED;
     }
@@ -312,14 +345,16 @@ int das_prepare_tile(const PlanHost& h, double c, int bu, int bv, int bw, double
     return RCBF_OK;
 }
 
-static int stride_class(int W) { return W <= 48 ? 48 : W <= 64 ? 64 : W <= 96 ? 96 : 128; }
+// window class of W intervals (the 2D receive aperture starts at 64)
+static int stride_class(int W, bool d2) { return W <= 48 && !d2 ? 48 : W <= 64 ? 64 : W <= 96 ? 96 : 128; }
 static int class_index(int ws) { return ws == 48 ? 0 : ws == 64 ? 1 : ws == 96 ? 2 : 3; }
 
-int das_class_index(int W) { return class_index(stride_class(W)); }
+int das_class_index(int W, bool d2) { return class_index(stride_class(W, d2)); }
 
 int launch_das(const PlanHost& h, const DasArgs& a_in, cudaStream_t s) {
     DasArgs a = a_in;
-    const int ws = stride_class(a.W);
+    const bool d2 = a.acq_kind == RCBF_HERCULES_2D;
+    const int ws = stride_class(a.W, d2);
     const bool cplx = a.dtype == RCBF_CF32;
     const bool apod = a.apod != nullptr || a.f_number > 0.f;
     const bool cubic = a.interp == RCBF_CUBIC;
@@ -329,9 +364,9 @@ int launch_das(const PlanHost& h, const DasArgs& a_in, cudaStream_t s) {
     a.partial_stride = a.image_plane * (cplx ? 2 : 1);
     int rc;
     switch (h.vu) {
-        case 1: rc = launch_vu<1>(a, ws, cplx, apod, cubic, iq, s); break;
-        case 2: rc = launch_vu<2>(a, ws, cplx, apod, cubic, iq, s); break;
-        default: rc = launch_vu<4>(a, ws, cplx, apod, cubic, iq, s); break;
+        case 1: rc = launch_vu<1>(a, ws, cplx, apod, cubic, iq, d2, s); break;
+        case 2: rc = launch_vu<2>(a, ws, cplx, apod, cubic, iq, d2, s); break;
+        default: rc = launch_vu<4>(a, ws, cplx, apod, cubic, iq, d2, s); break;
     }
     if (rc != RCBF_OK || a.n_split == 1) return rc;
     const long long n = a.partial_stride;
@@ -346,18 +381,20 @@ int configure_das(PlanHost& h) {
     const bool cplx = h.p.decoded_dtype == RCBF_CF32;
     const bool cubic = h.p.interp == RCBF_CUBIC;
     const bool iq = cplx && h.p.iq_freq > 0.0;
+    const bool d2 = h.p.acq_kind == RCBF_HERCULES_2D;
+    if (d2 && h.force_plain) return RCBF_OK;
     for (int c = 0; c < 4; ++c) {
         const int ws = c == 0 ? 48 : c == 1 ? 64 : c == 2 ? 96 : 128;
         int rc, n = 0;
-        if (cubic && cplx && ws == 128) {          // runs the plain form
+        if ((cubic && cplx && ws == 128) || (d2 && ws == 48)) {   // plain form / 64 class
             h.das_blocks_per_sm[c] = 0;
             h.n_split[c] = 1;
             continue;
         }
         switch (h.vu) {
-            case 1: rc = configure_vu<1>(ws, cplx, cubic, iq, &n); break;
-            case 2: rc = configure_vu<2>(ws, cplx, cubic, iq, &n); break;
-            default: rc = configure_vu<4>(ws, cplx, cubic, iq, &n); break;
+            case 1: rc = configure_vu<1>(ws, cplx, cubic, iq, d2, &n); break;
+            case 2: rc = configure_vu<2>(ws, cplx, cubic, iq, d2, &n); break;
+            default: rc = configure_vu<4>(ws, cplx, cubic, iq, d2, &n); break;
         }
         if (rc != RCBF_OK) return rc;
         h.das_blocks_per_sm[c] = n;

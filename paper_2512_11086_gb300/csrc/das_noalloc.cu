@@ -85,7 +85,7 @@ extern "C" int rcbf_das_noalloc(const rcbf_params* params, const void* decoded, 
     const bool tiled = h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok && fits;
     if (tiled) {
         if ((rc = configure_das(h)) != RCBF_OK) return rc;
-        const int split = std::max(1, h.n_split[das_class_index(a.W)]);
+        const int split = std::max(1, h.n_split[das_class_index(a.W, h.p.acq_kind == RCBF_HERCULES_2D)]);
         const size_t planes = h.p.decoded_dtype == RCBF_CF32 ? 2 : 1;
         const size_t need = split > 1 ? (size_t)split * planes * (size_t)a.image_plane : 0;
         if (need > kNoAllocScratchFloats - kNoAllocHeaderFloats)

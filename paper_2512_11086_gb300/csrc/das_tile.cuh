@@ -32,6 +32,17 @@
 // frac(that + r u) (u the window-relative position), and the rotation is one
 // sincos and a complex product.
 //
+// 2D receive aperture (D2, HERCULES read as a 2D array): the receive path of
+// row i and column j is d = sqrt(P_i + Q_j), P_i = (lat_tx - e_i)^2 + z^2 and
+// Q_j = (lat_rx - e_j)^2, so the tables keep P per (tile row, transmit) and Q
+// per (voxel, channel) where the separable form keeps alpha and beta, and a
+// sum costs P + Q, one approximate square root and one FMA more.
+// Each (i, j) window starts below the smallest delay that the tile's bounding
+// box admits (the box minima of P and Q and of the transmit wave's path: a
+// plane wave's path is linear, a diverging wave's convex, so both have exact
+// box bounds); P, Q and the transmit path are clamped to their box bounds per
+// voxel, so every index lands inside the window.
+//
 // Windows. Every (i, j) trace is read only inside the window
 // [K_i + K_j + lo, K_i + K_j + lo + W] that the tile can reach (W from the
 // tile radius, a 1-Lipschitz bound of the distances). The 1-D TMA bulk engine
@@ -65,7 +76,7 @@ __device__ __forceinline__ void static_for(F&& f) {
     }
 }
 
-template <int VU, int WS, bool CPLX, bool CUBIC = false>
+template <int VU, int WS, bool CPLX, bool CUBIC = false, bool D2 = false>
 struct DasCfg {
     static constexpr int VR = 4 / VU;              // tile rows per thread
     static constexpr int ROWS = 8 * VR;            // tile rows (one warp covers VR rows)
@@ -91,7 +102,8 @@ struct DasCfg {
     static constexpr int OFF_ALPHA = OFF_RX + kMaxChannels * 16;       // float[NB][CI][ROWS]
     static constexpr int OFF_WOFF = OFF_ALPHA + NB * ALPHA_N * 4;      // int[2][NWIN]
     static constexpr int OFF_WPH = OFF_WOFF + 2 * NWIN * 4;            // float[NB][NWIN]: IQ window phases
-    static constexpr int OFF_BAR = ((OFF_WPH + NB * NWIN * 4 + 7) / 8) * 8;   // uint64[10]
+    static constexpr int OFF_WS0 = OFF_WPH + NB * NWIN * 4;            // float[NB][NWIN]: 2D window starts
+    static constexpr int OFF_BAR = ((OFF_WS0 + (D2 ? NB * NWIN * 4 : 0) + 7) / 8) * 8;   // uint64[10]
     static constexpr int OFF_ABORT = OFF_BAR + 80;                     // int: a bounded wait expired
     static constexpr int SMEM = OFF_ABORT + 16;
     static_assert(ALPHA_N <= kDasThreads, "one thread per transmit term");
@@ -250,10 +262,11 @@ __device__ __forceinline__ void das_pipe_init(unsigned char* bar_base, volatile 
 
 // One work unit. Returns false when a bounded wait expired (the CTA must
 // stop; the caller records the status).
-template <int VU, int WS, bool CPLX, bool APOD, bool CUBIC = false, bool IQ = false>
+template <int VU, int WS, bool CPLX, bool APOD, bool CUBIC = false, bool IQ = false, bool D2 = false>
 __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned char* smem, DasPipe& pipe) {
-    using C = DasCfg<VU, WS, CPLX, CUBIC>;
+    using C = DasCfg<VU, WS, CPLX, CUBIC, D2>;
     static_assert(!IQ || CPLX, "IQ beamforming reads two planes");
+    float* s_ws0 = reinterpret_cast<float*>(smem + C::OFF_WS0);
     float* s_wph = reinterpret_cast<float*>(smem + C::OFF_WPH);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float4* s_tx = reinterpret_cast<float4*>(smem + C::OFF_TX);
@@ -285,7 +298,60 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     const double zr = a.q0[2] + a.Gu[2] * cu + a.Gv[2] * cv + a.Gw[2] * cw;
     const double lat_tx_ref = a.tx_axis ? qy : qx, lat_rx_ref = a.rx_axis ? qy : qx;
     const int j_lo = jc0 * C::CJ, n_rx = js * C::CJ;
+    // 2D: the transmit wave's reference path splits into Kt + Eref (integer
+    // and fractional samples); windows are placed relative to Kt. [elo, ehi]:
+    // the path's bounds over the tile's bounding box (samples, relative to Kt,
+    // with a slack for the FP32 evaluation per voxel)
+    auto half_ext = [&](int d) {
+        return 0.5 * (fabs(a.Gu[d]) * (C::BU - 1) + fabs(a.Gv[d]) * (a.bv - 1) + fabs(a.Gw[d]) * (a.bw - 1));
+    };
+    int Kt = 0;
+    float Eref = 0.f, elo = 0.f, ehi = 0.f;
+    if constexpr (D2) {
+        double dw, dlo, dhi;
+        if (a.tx_wave == RCBF_TX_PLANE) {
+            const float2 sc = a.tx_dir[0];
+            dw = zr * (double)sc.y + lat_tx_ref * (double)sc.x;
+            const double hw = fabs((double)sc.y) * half_ext(2) + fabs((double)sc.x) * half_ext(a.tx_axis);
+            dlo = dw - hw;
+            dhi = dw + hw;
+        } else {
+            // source at (0, 0, f): nearest point of the box and farthest corner
+            const double zf = zr - a.tx_focus, hx = half_ext(0), hy = half_ext(1), hz = half_ext(2);
+            const double nx = fmax(fabs(qx) - hx, 0.0), ny = fmax(fabs(qy) - hy, 0.0), nz = fmax(fabs(zf) - hz, 0.0);
+            const double fx = fabs(qx) + hx, fy = fabs(qy) + hy, fz = fabs(zf) + hz;
+            dw = sqrt(qx * qx + qy * qy + zf * zf) + a.tx_focus;
+            dlo = sqrt(nx * nx + ny * ny + nz * nz) + a.tx_focus;
+            dhi = sqrt(fx * fx + fy * fy + fz * fz) + a.tx_focus;
+        }
+        const double A = dw * a.fs_over_c - a.t0fs;
+        const double K = floor(A);
+        Kt = (int)K;
+        Eref = (float)(A - K);
+        elo = (float)(dlo * a.fs_over_c - a.t0fs - K) - a.reach_a;
+        ehi = (float)(dhi * a.fs_over_c - a.t0fs - K) + a.reach_a;
+    }
     __syncthreads();   // the previous unit of this CTA no longer reads the tables
+    if constexpr (D2) {
+        // squared-distance bounds over the tile's bounding box (half extents
+        // along each array axis): transmit rows (L, P_min, P_max), receive
+        // columns (L, Q_min, Q_max), L the reference lateral offset
+        auto sq_lo = [](double x, double h) { const double m = fabs(x) - h; return m > 0.0 ? m * m : 0.0; };
+        auto sq_hi = [](double x, double h) { const double m = fabs(x) + h; return m * m; };
+        const double ht = half_ext(a.tx_axis), hr = half_ext(a.rx_axis), hz = half_ext(2);
+        const double z2lo = sq_lo(zr, hz), z2hi = sq_hi(zr, hz);
+        for (int e = tid; e < a.n_tx + n_rx; e += kDasThreads) {
+            if (e < a.n_tx) {
+                const double L = lat_tx_ref - (a.tx_e0 + e * a.tx_pitch);
+                // the floor keeps every P + Q positive (a finite reciprocal root)
+                s_tx[e] = make_float4((float)L, (float)fmax(sq_lo(L, ht) + z2lo, 1e-14), (float)(sq_hi(L, ht) + z2hi), 0.f);
+            } else {
+                const int j = j_lo + e - a.n_tx;
+                const double L = lat_rx_ref - (a.rx_e0 + j * a.rx_pitch);
+                s_rx[j] = make_float4((float)L, (float)sq_lo(L, hr), (float)sq_hi(L, hr), 0.f);
+            }
+        }
+    } else
     for (int e = tid; e < a.n_tx + n_rx; e += kDasThreads) {
         if (e < a.n_tx) {
             float tx0, tx1;
@@ -324,6 +390,12 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
         dlr = gur * du + gvr * dv + gwr * dw;
         dz = guz * du + gvz * dv + gwz * dw;
     };
+    // 2D: first window sample of (i, j) relative to Kt, one below the
+    // smallest delay of the box (FP32, the same in every thread)
+    auto win_start = [&](int i, int j) -> int {
+        const float lowd = sqrtf(s_tx[i].y + s_rx[j].y);
+        return (int)floorf(fmaf(lowd, fsc, elo)) - 1;
+    };
     __syncthreads();   // reference tables ready
 
     volatile int* abort = reinterpret_cast<volatile int*>(smem + C::OFF_ABORT);
@@ -349,7 +421,8 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
         const int ii = win / C::CJ, jj = win % C::CJ;
         const int i = (s % n_ic) * C::CI + ii, j = (jc0 + s / n_ic) * C::CJ + jj;
         // first staged sample (cubic: one before the window, for the stencil)
-        const int S0 = __float_as_int(s_tx[i].w) + __float_as_int(s_rx[j].w) + a.lo - (CUBIC ? 1 : 0);
+        const int S0 = (D2 ? Kt + win_start(i, j) : __float_as_int(s_tx[i].w) + __float_as_int(s_rx[j].w) + a.lo) -
+                       (CUBIC ? 1 : 0);
         const int A = S0 & ~7;
         if (plane == 0) s_woff[b * C::NWIN + win] = S0 - A;
         const int lo_s = max(A, 0);
@@ -395,15 +468,24 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             rewrite_windows<int, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
         else
             rewrite_windows<float, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
-        if (IQ && tid < C::NWIN) {
-            // phase (in cycles) of the window's reference position: the sample
-            // at u = 0 is S0 + 0.5 + H for linear pieces; cubic positions
-            // already include 0.5 + H
+        if ((IQ || D2) && tid < C::NWIN) {
             const int win = tid;
             const int i = (s % n_ic) * C::CI + win / C::CJ, j = (jc0 + s / n_ic) * C::CJ + win % C::CJ;
-            const int S0 = __float_as_int(s_tx[i].w) + __float_as_int(s_rx[j].w) + a.lo;
-            const double x = a.iq_ratio * ((double)S0 + (CUBIC ? 0.0 : 0.5 + (double)a.H));
-            s_wph[pb * C::NWIN + win] = (float)(x - floor(x));
+            int S0;
+            if constexpr (D2) {
+                const int w0 = win_start(i, j);
+                s_ws0[pb * C::NWIN + win] = -(float)w0;
+                S0 = Kt + w0;
+            } else {
+                S0 = __float_as_int(s_tx[i].w) + __float_as_int(s_rx[j].w) + a.lo;
+            }
+            if (IQ) {
+                // phase (in cycles) of the window's reference position: the
+                // sample at u = 0 is S0 + 0.5 + H for linear pieces; cubic
+                // positions already include 0.5 + H
+                const double x = a.iq_ratio * ((double)S0 + (CUBIC ? 0.0 : 0.5 + (double)a.H));
+                s_wph[pb * C::NWIN + win] = (float)(x - floor(x));
+            }
         }
         const int ae = (tid + kDasThreads - (s * C::ALPHA_N + kDasThreads / 2) % kDasThreads) % kDasThreads;
         if (ae < C::ALPHA_N) {
@@ -414,8 +496,14 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             const float dL = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]) * dv + (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]) * dw;
             const float dz = (float)a.Gv[2] * dv + (float)a.Gw[2] * dw;
             const float4 tx = s_tx[(s % n_ic) * C::CI + ii];
-            const float al = tx_offset(a.tx_wave, tx, dL, dz, Zf, Zfoc, fsc);
-            s_alpha[pb * C::ALPHA_N + ii * C::ROWS + row] = fminf(fmaxf(al, tx.z - a.reach_a), tx.z + a.reach_a);
+            if constexpr (D2) {
+                // P = (lat_tx - e_i)^2 + z^2 of the row, clamped to its box bounds
+                const float Lt = tx.x + dL, Zv = Zf + dz;
+                s_alpha[pb * C::ALPHA_N + ii * C::ROWS + row] = fminf(fmaxf(fmaf(Lt, Lt, Zv * Zv), tx.y), tx.z);
+            } else {
+                const float al = tx_offset(a.tx_wave, tx, dL, dz, Zf, Zfoc, fsc);
+                s_alpha[pb * C::ALPHA_N + ii * C::ROWS + row] = fminf(fmaxf(al, tx.z - a.reach_a), tx.z + a.reach_a);
+            }
         }
         mbar_arrive(bar0 + 8 * (kRawEmpty + b));
         mbar_arrive(bar0 + 8 * (kPieceFull + pb));
@@ -432,6 +520,45 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     const f2x magic2 = pk(magic, magic);
     constexpr int SHIFT = C::SHIFT;
     const float iqr = (float)a.iq_ratio;
+    const f2x fsc2 = pk(fsc, fsc);
+    // 2D: per voxel the transmit wave's path in samples relative to Kt
+    // (cancellation-free offset from the reference, clamped to its reach),
+    // with the linear pieces' centring folded in
+    f2x E2[2] = {0ull, 0ull};
+    if constexpr (D2) {
+        const float gut = (float)(a.tx_axis ? a.Gu[1] : a.Gu[0]);
+        const float gvt = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]);
+        const float gwt = (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]);
+        const float shift = CUBIC ? 0.0f : hp;
+        float ev[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float dlr, dz;
+            voxel_offsets(k, dlr, dz);
+            const int ku = k % VU, kr = k / VU;
+            const int row = warp * C::VR + kr;
+            const float du = (float)(lane + 32 * ku) - 0.5f * (C::BU - 1);
+            const float dv = (float)(row % a.bv) - 0.5f * (a.bv - 1);
+            const float dw = (float)(row / a.bv) - 0.5f * (a.bw - 1);
+            const float dlt = gut * du + gvt * dv + gwt * dw;
+            float de;
+            if (a.tx_wave == RCBF_TX_PLANE) {
+                const float2 sc = a.tx_dir[0];
+                de = fmaf(dz, sc.y, dlt * sc.x) * fsc;
+            } else {
+                // point source at (0, 0, f) of the array frame
+                const float X = (float)lat_rx_ref, Y = (float)lat_tx_ref, Zq = (float)(zr - a.tx_focus);
+                const float Xv = X + dlr, Yv = Y + dlt, Zv = Zq + dz;
+                const float dv3 = sqrtf(Xv * Xv + Yv * Yv + Zv * Zv);
+                const float dr3 = sqrtf(X * X + Y * Y + Zq * Zq);
+                const float num = dlr * (2.0f * X + dlr) + dlt * (2.0f * Y + dlt) + dz * (2.0f * Zq + dz);
+                de = __fdividef(num, dv3 + dr3) * fsc;
+            }
+            ev[k] = fminf(fmaxf(Eref + de, elo), ehi) - shift;
+        }
+        E2[0] = pk(ev[0], ev[1]);
+        E2[1] = pk(ev[2], ev[3]);
+    }
 
     // ---- prologue: stages 0 and 1 in flight, stage 0 rewritten
     bool ok = issue(0);
@@ -458,6 +585,13 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
                     float bt[2], aw[2];
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
+                        if constexpr (D2) {
+                            // Q = (lat_rx - e_j)^2, clamped to its box bounds (no F# window)
+                            const float Lv = rx.x + dlr[h];
+                            bt[h] = fminf(fmaxf(Lv * Lv, rx.y), rx.z);
+                            aw[h] = wj;
+                            continue;
+                        }
                         const float Lv = rx.x + dlr[h], Zv = Zf + dz[h];
                         const float d = sqrtf(Lv * Lv + Zv * Zv);
                         const float num = dlr[h] * (2.0f * rx.x + dlr[h]) + dz[h] * (2.0f * Zf + dz[h]);
@@ -489,6 +623,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
                 constexpr int jj = decltype(jjc)::value;
                 constexpr int OFF = jj * WS * C::PAIR_BYTES;
                 const float phw = IQ ? s_wph[pb * C::NWIN + ii * C::CJ + jj] : 0.0f;
+                const float ws0 = D2 ? s_ws0[pb * C::NWIN + ii * C::CJ + jj] : 0.0f;
                 // e^{j 2 pi (phw + r u)} applied to (vr, vi)
                 auto iq_rotate = [&](float uu, float& vr, float& vi) {
                     const float x = fmaf(iqr, uu, phw);
@@ -500,7 +635,20 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
                 };
 #pragma unroll
                 for (int kp = 0; kp < 2; ++kp) {
-                    const f2x u2 = add2(al2[kp], beta2[kp][jj]);
+                    f2x u2;
+                    if constexpr (D2) {
+                        // window position: sqrt(P + Q) fs/c + E - S0 (the square root
+                        // by the approximate PTX instruction: one special-function
+                        // operation, no multiply; measured faster than x rsqrt(x))
+                        const f2x x2 = add2(al2[kp], beta2[kp][jj]);
+                        float xa, xb, sa, sb;
+                        upk(x2, xa, xb);
+                        asm("sqrt.approx.f32 %0, %1;" : "=f"(sa) : "f"(xa));
+                        asm("sqrt.approx.f32 %0, %1;" : "=f"(sb) : "f"(xb));
+                        u2 = fma2(pk(sa, sb), fsc2, add2(E2[kp], pk(ws0, ws0)));
+                    } else {
+                        u2 = add2(al2[kp], beta2[kp][jj]);
+                    }
                     const f2x t2 = add2(u2, magic2);
                     float u[2], t[2];
                     upk(u2, u[0], u[1]);

@@ -2,6 +2,6 @@
 #include "das_kernels.cuh"
 
 namespace rcbf {
-template int configure_das_vu<1, true>(int, bool, bool, int*);
-template int launch_das_vu<1, true>(const DasArgs&, int, bool, bool, bool, cudaStream_t);
+template int configure_das_vu<1, true, false>(int, bool, bool, int*);
+template int launch_das_vu<1, true, false>(const DasArgs&, int, bool, bool, bool, cudaStream_t);
 }  // namespace rcbf

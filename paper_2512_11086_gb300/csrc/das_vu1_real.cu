@@ -2,6 +2,6 @@
 #include "das_kernels.cuh"
 
 namespace rcbf {
-template int configure_das_vu<1, false>(int, bool, bool, int*);
-template int launch_das_vu<1, false>(const DasArgs&, int, bool, bool, bool, cudaStream_t);
+template int configure_das_vu<1, false, false>(int, bool, bool, int*);
+template int launch_das_vu<1, false, false>(const DasArgs&, int, bool, bool, bool, cudaStream_t);
 }  // namespace rcbf

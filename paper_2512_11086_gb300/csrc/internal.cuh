@@ -89,7 +89,7 @@ struct DecodeArgs {
 struct PlanHost {
     rcbf_params p;
     DasArgs das;            // geometry part filled at plan time
-    double r_alpha_m;       // tile radius in the (lateral_tx, z) plane [m]
+    double r_alpha_m;       // tile radius in the (lateral_tx, z) plane [m] (2D aperture: the transmit path's largest spread over a tile's box)
     double r_beta_m;        // tile radius in the (lateral_rx, z) plane [m]
     int vu;                 // voxels per thread along u (1, 2, 4)
     bool swap_uv;           // u = y
@@ -107,6 +107,8 @@ struct PlanHost {
     size_t partial_floats;
     int16_t* d_taps;        // device demodulation FIR taps (demod_decimation > 0)
     float2* d_tx_dir;       // device plane-wave directions (tx_wave == RCBF_TX_PLANE)
+    bool has_tx_angle0;     // tx_angle0 holds the first plane-wave angle (the params' pointer is not kept)
+    double tx_angle0;
     bool force_plain;       // the geometry admits no tile windows (a VLS focal plane inside the image)
     // adjoint tile with lanes over z: 32 voxels along u by bwd_bv x bwd_bw
     // rows (bwd_bv = 0: no such tile keeps the window within 128 samples)
@@ -148,7 +150,7 @@ int launch_das_plain(const PlanHost& h, const DasArgs& a, cudaStream_t s);
 // the adjoint tile (lanes over z; a.bu must be 32)
 int launch_das_backward(const PlanHost& h, const DasArgs& a, int mode, cudaStream_t s);
 int configure_decode(PlanHost& h);
-int das_class_index(int W);
+int das_class_index(int W, bool d2);
 int configure_das(PlanHost& h);
 
 // ------------------------------------------------------------ PTX helpers

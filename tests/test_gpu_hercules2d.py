@@ -1,15 +1,20 @@
 """HERCULES with its 2D receive aperture (non-separable delays) on the GPU
-against the FP64 oracle: volumes and cross-planes, plane and diverging
-transmit waves, linear and cubic interpolation, real and complex data with
-an F# window and weights, IQ beamforming, 3D focusing of a point scatterer,
-and the entry points that are built for separable delays only."""
+against the FP64 oracle, in the tiled form (box-bounded windows, sqrt(P + Q)
+per sum) and the plain form: volumes and cross-planes, plane and diverging
+transmit waves, linear and cubic interpolation, FP32 / FP16 / int32 storage,
+real and complex data with weights and IQ beamforming, an F# window (plain
+form), ragged tiles and record edges, the full-size volume on sampled voxels,
+3D focusing of a point scatterer, and the entry points that are built for
+separable delays only."""
+import dataclasses
+
 import numpy as np
 import pytest
 
 import oracle
 import synth
 from synth import MM, HERCULES_2D
-from tests._frames import rel_l2
+from tests._frames import rel_l2, sample_voxels
 
 pytestmark = pytest.mark.gpu
 
@@ -44,24 +49,101 @@ def _run(g, decoded, dtype="f32", variant=rc.DAS_PLAIN, interp="linear", apod=No
     if dtype == "cf32":
         dec = torch.from_numpy(np.stack([decoded.real, decoded.imag]).astype(np.float32)).cuda()
     else:
-        dec = torch.from_numpy(decoded.astype(np.float32)).cuda()
+        tdt = {"f32": torch.float32, "f16": torch.float16, "i32": torch.int32}[dtype]
+        dec = torch.from_numpy(np.asarray(decoded)).to(tdt).cuda()
     w = None if apod is None else torch.from_numpy(apod.astype(np.float32)).cuda()
     img = plan.das(dec, apod=w).cpu().numpy().astype(np.float64)
     return (img[0] + 1j * img[1] if dtype == "cf32" else img), plan.info()
 
 
+@pytest.mark.parametrize("variant", [rc.DAS_TILED, rc.DAS_PLAIN])
 @pytest.mark.parametrize("wave", ["plane", "point"])
 @pytest.mark.parametrize("interp", ["linear", "cubic"])
-@pytest.mark.parametrize("dims", [(24, 20, 40), (48, 1, 64), (1, 40, 64)])
-def test_2d_aperture_matches_oracle(wave, interp, dims):
+@pytest.mark.parametrize("dims", [(24, 20, 40), (48, 1, 160), (1, 40, 64)])
+def test_2d_aperture_matches_oracle(wave, interp, dims, variant):
     g = _geom(wave, dims=dims)
     fr = synth.make_frame(g, seed=51, n_scatterers=4, box_x=(-1 * MM, 1 * MM), box_y=(-1 * MM, 1 * MM),
                           box_z=(5 * MM, 13 * MM), noise_frac=0.0)
     want = oracle.das(g, fr.decoded.astype(np.float64), interp=interp)
-    got, info = _run(g, fr.decoded, variant=rc.DAS_TILED, interp=interp)      # runs the plain form
-    assert not info["tiled"]
+    got, info = _run(g, fr.decoded, variant=variant, interp=interp)
+    assert info["tiled"] == (variant == rc.DAS_TILED)
     err = rel_l2(got, want)
-    print("2D aperture %s %s %s: rel-L2 %.3e" % (wave, interp, dims, err))
+    print("2D aperture %s %s %s v%d (window %d): rel-L2 %.3e" % (wave, interp, dims, variant, info["window"], err))
+    assert err <= TOL
+
+
+def test_2d_coarse_grid_runs_the_plain_form():
+    # a 32 x 32-voxel x-z tile of this grid reaches more than 128 samples
+    g = _geom("plane", dims=(48, 1, 64))
+    fr = synth.make_frame(g, seed=56, n_scatterers=3, box_x=(-1 * MM, 1 * MM), box_y=(0.0, 0.0),
+                          box_z=(5 * MM, 13 * MM), noise_frac=0.0)
+    got, info = _run(g, fr.decoded, variant=rc.DAS_TILED)
+    assert not info["tiled"] and info["window"] > 128
+    assert rel_l2(got, oracle.das(g, fr.decoded.astype(np.float64))) <= TOL
+
+
+@pytest.mark.parametrize("wave", ["plane", "point"])
+def test_tiled_2d_storage_types(wave):
+    g = _geom(wave)
+    fr = synth.make_frame(g, seed=54, n_scatterers=5, box_x=(-1 * MM, 1 * MM), box_y=(-1 * MM, 1 * MM),
+                          box_z=(5 * MM, 13 * MM), noise_frac=0.0)
+    x = fr.decoded.astype(np.float64)
+    h = x.astype(np.float16)
+    got, info = _run(g, h, dtype="f16", variant=rc.DAS_TILED)
+    assert info["tiled"]
+    assert rel_l2(got, oracle.das(g, h.astype(np.float64))) <= TOL
+    q = np.round(x * 64).astype(np.int32)           # int32 storage is the decoded sum D, scaled by 1/n_tx
+    got, _ = _run(g, q, dtype="i32", variant=rc.DAS_TILED)
+    assert rel_l2(got, oracle.das(g, q.astype(np.float64) / g.n_tx)) <= TOL
+
+
+@pytest.mark.parametrize("wave", ["plane", "point"])
+@pytest.mark.parametrize("interp", ["linear", "cubic"])
+def test_tiled_2d_complex_weights_and_iq(wave, interp):
+    # a grid fine enough for windows of at most 64 samples (complex cubic
+    # pieces have no larger tiled class)
+    g = _geom(wave, dims=(48, 40, 80))
+    fr = synth.make_frame(g, seed=55, n_scatterers=4, analytic=True, noise_frac=0.0, box_x=(-1 * MM, 1 * MM),
+                          box_y=(-1 * MM, 1 * MM), box_z=(5 * MM, 13 * MM))
+    r = fr.decoded.astype(np.complex128)
+    w = np.random.default_rng(6).uniform(0.5, 1.5, g.n_ch)
+    got, info = _run(g, fr.decoded, dtype="cf32", variant=rc.DAS_TILED, interp=interp, apod=w)
+    print("2D complex %s %s: tiled %s window %d" % (wave, interp, info["tiled"], info["window"]))
+    assert info["tiled"]
+    assert rel_l2(got, oracle.das(g, r, w=w, interp=interp)) <= TOL
+    g.iq_freq = 2.5e6
+    got, info = _run(g, fr.decoded, dtype="cf32", variant=rc.DAS_TILED, interp=interp)
+    assert info["tiled"]
+    assert rel_l2(got, oracle.das(g, r, interp=interp)) <= TOL
+
+
+def test_tiled_2d_ragged_tiles_and_record_edges():
+    # delays run off both ends of a short record; grid sizes are not
+    # multiples of the tile extents; a steered plane wave
+    g = synth.Geometry(n_tx=16, n_ch=16, n_samples=384, acq_kind=HERCULES_2D, out_dims=(37, 13, 77), t0=3e-6,
+                       out_min=(-1.8 * MM, -1.1 * MM, 1 * MM), out_max=(1.8 * MM, 1.1 * MM, 12 * MM))
+    g.tx_wave, g.tx_angles = "plane", (-0.2,)
+    r = np.random.default_rng(18).normal(size=(16, 16, 384))
+    for interp in ("linear", "cubic"):
+        got, info = _run(g, r.astype(np.float32), variant=rc.DAS_TILED, interp=interp)
+        assert info["tiled"]
+        err = rel_l2(got, oracle.das(g, r, interp=interp))
+        print("2D edges %s: rel-L2 %.3e" % (interp, err))
+        assert err <= TOL
+
+
+def test_tiled_2d_full_volume_sampled():
+    # the benchmark's workload and launch configuration: 128 rows x 128
+    # columns x 2048 samples decoded to FP16, one plane wave, 128 x 128 x 256
+    g = dataclasses.replace(synth.hercules_volume_geometry(), acq_kind=HERCULES_2D, hadamard_order=0)
+    g.tx_wave, g.tx_angles = "plane", (0.0,)
+    h = np.random.default_rng(7).normal(size=(g.n_tx, g.n_ch, g.n_samples)).astype(np.float16)
+    got, info = _run(g, h, dtype="f16", variant=rc.DAS_TILED)
+    assert info["tiled"]
+    vox = sample_voxels(g.out_dims, 1200, seed=3)
+    want = oracle.das(g, h.astype(np.float64), voxels=vox)
+    err = rel_l2(got.ravel()[vox], want)
+    print("2D full volume: tile %s window %d rel-L2 %.3e" % (info["tile"], info["window"], err))
     assert err <= TOL
 
 
@@ -83,7 +165,8 @@ def test_complex_fnumber_weights_and_iq(wave):
                           box_y=(-1 * MM, 1 * MM), box_z=(5 * MM, 13 * MM))
     r = fr.decoded.astype(np.complex128)
     w = np.random.default_rng(5).uniform(0.5, 1.5, g.n_ch)
-    got, _ = _run(g, fr.decoded, dtype="cf32", apod=w, f_number=0.8)
+    got, info = _run(g, fr.decoded, dtype="cf32", variant=rc.DAS_TILED, apod=w, f_number=0.8)
+    assert not info["tiled"]                        # the radial F# window runs the plain form
     assert rel_l2(got, oracle.das(g, r, w=w, f_number=0.8)) <= TOL
     g.iq_freq = 2.5e6                               # IQ beamforming of the same samples
     got, _ = _run(g, fr.decoded, dtype="cf32")
