@@ -612,10 +612,11 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
         // ---- the sum: 4 voxels x CI transmits x CJ channels from buffer pb
         const uint32_t pbase = pairs_u32 + pb * C::PAIR_BUF - (0x4B000000u << SHIFT);
         const float* alb = s_alpha + pb * C::ALPHA_N + warp * C::VR;
-        // two transmits per iteration for real linear pieces (more independent
-        // loads in flight; measured +2.7 % on the batched B-scan); the wider
-        // forms stay at one (register budget)
-#pragma unroll(CPLX || CUBIC ? 1 : 2)
+        // real linear pieces: two transmits per iteration, four in the
+        // 48-interval class (more independent loads in flight; measured on the
+        // batched B-scan +2.7 % and +1.3 %; four cost the 96 class 4-7 %); the
+        // wider forms stay at one (register budget)
+#pragma unroll(CPLX || CUBIC ? 1 : WS <= 48 ? 4 : 2)
         for (int ii = 0; ii < C::CI; ++ii) {
             float al[C::VR];
 #pragma unroll
