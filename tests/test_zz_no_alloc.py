@@ -56,3 +56,23 @@ def test_noalloc_matches_planned_das_on_two_calls(name):
         err = rel_l2(got, want)
         print("%s c=%g: rel-L2 vs rcbf_das %.2e" % (name, c, err))
         assert err <= 1e-4
+
+
+def test_noalloc_2d_aperture_diverging_wave():
+    # HERCULES read as a 2D receive aperture with a diverging wave (a plane
+    # wave needs the plan's device direction table): the tiled 2D form from
+    # the parameter block alone, equal to the planned call and to the oracle
+    g = synth.Geometry(n_tx=16, n_ch=16, n_samples=1024, acq_kind=synth.HERCULES_2D, out_dims=(48, 40, 80),
+                       out_min=(-1.5e-3, -1.2e-3, 4e-3), out_max=(1.5e-3, 1.2e-3, 14e-3))
+    g.tx_wave, g.tx_focus = "point", -6e-3
+    fr = synth.make_frame(g, seed=57, n_scatterers=4, box_x=(-1e-3, 1e-3), box_y=(-1e-3, 1e-3),
+                          box_z=(5e-3, 13e-3), noise_frac=0.0)
+    params = rc.make_params(g, decoded_dtype="f32")
+    plan = rc.Plan(rc.make_params(g, decoded_dtype="f32"))
+    assert plan.info()["tiled"]
+    d = torch.from_numpy(fr.decoded.astype(np.float32)).cuda()
+    out = torch.empty(plan.image_shape, dtype=torch.float32, device="cuda")
+    got = _noalloc(params, d, out)
+    want = plan.das(d).cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+    assert rel_l2(got, oracle.das(g, fr.decoded.astype(np.float64))) <= 1e-4
