@@ -587,6 +587,15 @@ def main():
     achieved = ops_per_sum * B * sums / (t_batch * 1e-3) / 1e12
     dec_bytes = g.n_tx * g.n_ch * g.n_samples * (2 + 2)       # int16 in + FP16 out
     info = tuned.info()
+    # the same launch against HBM: compulsory bytes per frame if nothing stayed
+    # on chip (RF read, FP16 decoded written and read back once, image written),
+    # and the window bytes the DAS copies from L2 per frame (every tile stages
+    # raw_samples FP16 samples of every (transmit, channel) trace)
+    n_tiles = -(-g.out_dims[0] // tile[0]) * -(-g.out_dims[1] // tile[1]) * -(-g.out_dims[2] // tile[2])
+    raw_samples = ((info["window"] + 8 + 7) // 8) * 8
+    frame_bytes = g.n_tx * g.n_ch * g.n_samples * (2 + 2 + 2) + g.n_vox * 4
+    window_bytes = n_tiles * g.n_tx * g.n_ch * raw_samples * 2
+    traffic = recorded_traffic("batch_kernel", B)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -610,10 +619,18 @@ def main():
         "plain_fp32": {"value": plain_value, "unit": UNIT, "ms_per_frame": plain_ms,
                        "speedup_of_tuned": value / ws / plain_value},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TOP/s",
-                     "frac": achieved / alu_peak, "traffic": recorded_traffic("batch_kernel", B),
+                     "frac": achieved / alu_peak, "traffic": traffic,
                      "kernel": "batch_kernel",
                      "peak_src": "%d SMs x 128 FP32 lanes x %.0f MHz" % (sms, peaks["sm_max_mhz"]),
                      "ops_per_sum": ops_per_sum},
+        "roofline_memory": {"bound": "hbm", "achieved": B * frame_bytes / (t_batch * 1e-3) / 1e9,
+                            "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                            "frac": B * frame_bytes / (t_batch * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                            "traffic": traffic,
+                            "traffic_GBps": None if traffic is None else traffic / (t_batch * 1e-3) / 1e9,
+                            "l2_window_GBps": B * window_bytes / (t_batch * 1e-3) / 1e9,
+                            "kernel": "batch_kernel", "peak_src": peaks["src"],
+                            "bytes_per_frame": frame_bytes},
         "roofline_decode": {"bound": "hbm", "achieved": dec_bytes / (t_dec * 1e-3) / 1e9,
                             "peak": peaks["hbm_gbs"], "unit": "GB/s",
                             "frac": dec_bytes / (t_dec * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": None,

@@ -190,3 +190,20 @@ def test_separable_only_entry_points_reject_2d_aperture():
     with pytest.raises(rc.RcbfError) as e:
         rc.Plan(rc.make_params(bad, decoded_dtype="f32"))
     assert e.value.code == rc.EINVAL
+
+
+@pytest.mark.parametrize("wave", ["plane", "point"])
+def test_tiled_2d_speed_of_sound_override(wave):
+    # the window and the box bounds follow the call's speed of sound
+    g = _geom(wave, dims=(48, 40, 80))
+    fr = synth.make_frame(g, seed=58, n_scatterers=4, box_x=(-1 * MM, 1 * MM), box_y=(-1 * MM, 1 * MM),
+                          box_z=(5 * MM, 13 * MM), noise_frac=0.0)
+    plan = rc.Plan(rc.make_params(g, decoded_dtype="f32"))
+    assert plan.info()["tiled"]
+    d = torch.from_numpy(fr.decoded.astype(np.float32)).cuda()
+    for c in (1420.0, 1610.0):
+        got = plan.das(d, c=c).cpu().numpy().astype(np.float64)
+        want = oracle.das(dataclasses.replace(g, c=c), fr.decoded.astype(np.float64))
+        err = rel_l2(got, want)
+        print("2D %s c=%g: rel-L2 %.3e" % (wave, c, err))
+        assert err <= TOL
