@@ -43,15 +43,16 @@ namespace {
 
 constexpr int kBwdCI = 4;          // transmits per backward stage
 constexpr int kBwdCJ = 4;          // channels per backward stage
-constexpr int kBwdWS = 128;        // window intervals (every W <= 128)
-constexpr int kBwdGroups = (7 + kBwdWS + 1 + 3) / 4;   // 4-sample groups a window's cells can touch
 
 // ZL: lanes on tile rows (the z-major row index), each thread four
 // consecutive voxels along u. Along z the delay grows by a sizeable fraction
 // of a sample per voxel, so the 32 lanes of a warp rarely meet on one sample
 // and the shared atomics rarely serialise; with lanes along u (ZL false) the
 // lanes near a receive element's axis share a sample.
-template <int VU, bool CPLX>
+// WS: window intervals of the class (every W <= WS). Three accumulator sets
+// (stages s-1, s and s+1 in flight: flushed, summed, cleared) and two raw
+// window buffers and alpha tables.
+template <int VU, bool CPLX, int WS>
 struct BwdCfg {
     static constexpr int VR = 4 / VU;
     static constexpr int ROWS = 8 * VR;
@@ -59,31 +60,33 @@ struct BwdCfg {
     static constexpr int NWIN = kBwdCI * kBwdCJ;
     static constexpr int PLANES = CPLX ? 2 : 1;
     static constexpr int COPIES = NWIN * PLANES;
-    static constexpr int RAWS = kBwdWS + 8;
+    static constexpr int RAWS = WS + 8;
     static constexpr int RAW_WIN_BYTES = RAWS * 4 * PLANES;
-    static constexpr int GW = kBwdWS + 2;            // accumulator intervals per window plane (stride)
+    static constexpr int GW = WS + 2;                // accumulator intervals per window plane (stride)
+    static constexpr int GROUPS = (7 + WS + 1 + 3) / 4;   // 4-sample groups a window's cells can touch
     static constexpr int ACC_INTS = NWIN * PLANES * GW;   // one accumulator (G0 or G1)
+    static constexpr int ACC_BUF = 2 * ACC_INTS;          // G0 and G1 of one stage
     static constexpr int OFF_RAW = 0;
-    static constexpr int OFF_GRAD = OFF_RAW + 2 * NWIN * RAW_WIN_BYTES;   // int G0[ACC_INTS], G1[ACC_INTS]
-    static constexpr int OFF_TX = OFF_GRAD + 2 * ACC_INTS * 4;
+    static constexpr int OFF_GRAD = OFF_RAW + 2 * NWIN * RAW_WIN_BYTES;   // int [3][G0, G1]
+    static constexpr int OFF_TX = OFF_GRAD + 3 * ACC_BUF * 4;
     static constexpr int OFF_RX = OFF_TX + kMaxOrder * 16;
-    static constexpr int OFF_ALPHA = OFF_RX + kMaxChannels * 16;
-    static constexpr int OFF_WIN = OFF_ALPHA + kBwdCI * ROWS * 4;      // int S0[2][NWIN], int off[2][NWIN]
+    static constexpr int OFF_ALPHA = OFF_RX + kMaxChannels * 16;       // float[2][CI][ROWS]
+    static constexpr int OFF_WIN = OFF_ALPHA + 2 * kBwdCI * ROWS * 4;  // int S0[2][NWIN], int off[2][NWIN]
     static constexpr int OFF_GW = OFF_WIN + 4 * NWIN * 4;              // float[kMaxChannels]
     static constexpr int OFF_RED = OFF_GW + kMaxChannels * 4;          // float[8]
     static constexpr int OFF_MAX = OFF_RED + 32;                       // float[8]: per-warp max|G|
     static constexpr int OFF_BAR = OFF_MAX + 32;                       // uint64[2]
     static constexpr int SMEM = OFF_BAR + 16;
     static_assert(OFF_RAW % 128 == 0 && OFF_GRAD % 16 == 0 && ACC_INTS % 4 == 0 && OFF_TX % 16 == 0 &&
-                  OFF_BAR % 8 == 0, "alignment");
+                  OFF_BAR % 8 == 0 && (ACC_BUF * 4) % 16 == 0, "alignment");
 };
 
 // FN: receive F# window active (a per-voxel weight W_j(v)); VEC_RED: dL/dr
 // is 16-byte aligned, so window cells go out as four-float reductions.
-template <int VU, bool CPLX, bool ZL, bool FN, bool VEC_RED>
+template <int VU, bool CPLX, bool ZL, bool FN, bool VEC_RED, int WS>
 __global__ void __launch_bounds__(kDasThreads, 2)
 das_bwd_kernel(DasArgs a) {
-    using C = BwdCfg<VU, CPLX>;
+    using C = BwdCfg<VU, CPLX, WS>;
     static_assert(!ZL || VU == 1, "lanes on rows need 32 rows of 32 voxels");
     // tile row -> (v, w): z-fastest when lanes run over rows
     auto row_v = [&](int row) { return ZL ? row / a.bw : row % a.bv; };
@@ -107,7 +110,7 @@ das_bwd_kernel(DasArgs a) {
         mbar_init(bar0 + 8, C::COPIES);
         fence_mbar_init();
     }
-    for (int q = tid; q < 2 * C::ACC_INTS; q += kDasThreads) gwin[q] = 0;
+    for (int q = tid; q < 3 * C::ACC_BUF; q += kDasThreads) gwin[q] = 0;
     for (int q = tid; q < kMaxChannels; q += kDasThreads) s_gw[q] = 0.f;
 
     // ---- unit -> (tile, channel split)
@@ -197,6 +200,8 @@ das_bwd_kernel(DasArgs a) {
     }
 
     const int es = 4;
+    // stage s: raw buffer s & 1 (its window starts in s_S0 / s_off), alpha
+    // table s & 1, accumulator s % 3
     auto issue = [&](int s) {
         if (tid >= C::COPIES) return;
         const int b = s & 1;
@@ -222,9 +227,20 @@ das_bwd_kernel(DasArgs a) {
             bulk_g2s(smem_u32(dst + pre), src, (uint32_t)body, bar0 + 8 * b);
         }
     };
+    // transmit terms of stage s for every tile row
+    auto make_alpha = [&](int s) {
+        if (tid >= kBwdCI * C::ROWS) return;
+        const int ii = tid / C::ROWS, row = tid % C::ROWS;
+        const float dv = (float)row_v(row) - 0.5f * (a.bv - 1);
+        const float dw = (float)row_w(row) - 0.5f * (a.bw - 1);
+        const float dL = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]) * dv + (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]) * dw;
+        const float dzz = (float)a.Gv[2] * dv + (float)a.Gw[2] * dw;
+        const float4 tx = s_tx[(s % n_ic) * kBwdCI + ii];
+        const float al = tx_offset(a.tx_wave, tx, dL, dzz, Zf, Zfoc, fsc);
+        s_alpha[(s & 1) * kBwdCI * C::ROWS + ii * C::ROWS + row] = fminf(fmaxf(al, tx.z - a.reach_a), tx.z + a.reach_a);
+    };
 
-    issue(0);
-    if (NS > 1) issue(1);
+    make_alpha(0);
     __syncthreads();
 
     const float hp = 0.5f + (float)a.H;
@@ -233,224 +249,230 @@ das_bwd_kernel(DasArgs a) {
     float betah[4][kBwdCJ], win_w[FN ? 4 : 1][kBwdCJ], wj[kBwdCJ], pw[kBwdCJ];
     float gc = 0.f;                         // dL/dc partial (times -c, scaled)
     bool ok = true;
-    uint32_t phase = 0;
+    uint32_t phase = 0;                     // parity of each raw buffer's next phase
+    constexpr uint32_t kG1 = 4u * C::ACC_INTS;                  // G1 after G0
+    constexpr uint32_t kIm = 4u * C::NWIN * C::GW;              // plane 1 after plane 0
 
-    for (int s = 0; s < NS; ++s) {
-        const int ic = s % n_ic, jc = jc0 + s / n_ic;
-        const int b = s & 1;
-        if (ic == 0) {
+    // Iteration s: copy the windows of stage s; flush stage s-1 (its windows
+    // landed during the previous iteration); accumulate stage s; compute the
+    // transmit terms of stage s+1 and clear the accumulator of stage s+1
+    // (last flushed in the previous iteration). One barrier per iteration
+    // orders every hand-over: accumulator s is complete before its flush in
+    // iteration s+1 and cleared in iteration s+2 before stage s+3 uses it.
+    for (int s = 0; s <= NS; ++s) {
+        if (s < NS) issue(s);
+        if (s > 0) {
+            // ---- flush stage t = s - 1: accumulators -> dL/dr = w_j c, dL/dw_j
+            // and dL/dc partials. Cells go out in groups of four samples
+            // starting at a multiple of 4 (window starts are A + off with A a
+            // multiple of 8; traces are multiples of 8 long, so a group lies
+            // wholly inside or wholly outside its trace).
+            const int t = s - 1, tb = t & 1;
+            const int ic = t % n_ic, jc = jc0 + t / n_ic;
+            ok = mbar_wait_parity(bar0 + 8 * tb, (phase >> tb) & 1u) && ok;
+            phase ^= 1u << tb;
+            const int* acc = gwin + (t % 3) * C::ACC_BUF;
+            for (int q = tid; q < C::NWIN * C::PLANES * C::GROUPS; q += kDasThreads) {
+                const int g = q % C::GROUPS, wp = q / C::GROUPS;
+                const int win = wp % C::NWIN, plane = wp / C::NWIN;
+                const int off = s_off[tb * C::NWIN + win];
+                const int n0 = 4 * g - off;
+                if (n0 > a.W) continue;
+                const int* G0 = acc + (plane * C::NWIN + win) * C::GW;
+                const int* G1 = G0 + C::ACC_INTS;
+                // intervals n0-1 .. n0+3 (valid ones are 0 .. W-1)
+                int g0[4], g1[5];
 #pragma unroll
-            for (int jj = 0; jj < kBwdCJ; ++jj) {
-                wj[jj] = a.apod ? __ldg(a.apod + jc * kBwdCJ + jj) : 1.0f;
-                pw[jj] = 0.f;
+                for (int e = 0; e < 5; ++e) {
+                    const int n = n0 - 1 + e;
+                    const bool in = n >= 0 && n < a.W;
+                    g1[e] = in ? G1[n] : 0;
+                    if (e > 0) g0[e - 1] = in ? G0[n] : 0;
+                }
+                if ((g0[0] | g0[1] | g0[2] | g0[3] | g1[0] | g1[1] | g1[2] | g1[3] | g1[4]) == 0) continue;
+                // raw sample of cell n is at window index off + n = 4g + e
+                const float* rw = reinterpret_cast<const float*>(raw + (tb * C::NWIN + win) * C::RAW_WIN_BYTES +
+                                                                 plane * C::RAWS * 4) + 4 * g;
+                const float4 r4 = *reinterpret_cast<const float4*>(rw);
+                const float r5 = (n0 + 3 < a.W) ? rw[4] : 0.f;     // right end of interval n0+3
+                const float rr[5] = {r4.x, r4.y, r4.z, r4.w, r5};
+                const float cwin = (float)s_S0[tb * C::NWIN + win] + (float)a.t0fs + (float)n0;
+                float c4[4], pr = 0.f, pc = 0.f;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    c4[e] = (float)((long long)g0[e] - (long long)g1[e + 1] + (long long)g1[e]);
+                    pr = fmaf(rr[e], c4[e], pr);
+                    // interval n0+e: slope times position-weighted sum
+                    pc = fmaf(rr[e + 1] - rr[e], fmaf((float)e + cwin, (float)g0[e], (float)g1[e + 1]), pc);
+                }
+                const int jj = win % kBwdCJ;
+                float w_sel = 1.f;
+#pragma unroll
+                for (int u = 0; u < kBwdCJ; ++u) {
+                    if (u == jj) {
+                        pw[u] += pr;
+                        w_sel = wj[u];
+                    }
+                }
+                gc = fmaf(w_sel, pc, gc);
+                const int S = s_S0[tb * C::NWIN + win] - off + 4 * g;
+                if (S < 0 || S >= a.n_s || !a.grad_rf) continue;
+                const int ii = win / kBwdCJ;
+                const int i = ic * kBwdCI + ii, j = jc * kBwdCJ + jj;
+                float* dst = a.grad_rf + (long long)plane * a.plane_stride + ((long long)i * a.n_ch + j) * a.n_s + S;
+                const float m = w_sel * inv_scale;
+                if (VEC_RED) {
+                    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};"
+                                 :: "l"(dst), "f"(c4[0] * m), "f"(c4[1] * m), "f"(c4[2] * m), "f"(c4[3] * m)
+                                 : "memory");
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (c4[e] != 0.f) atomicAdd(dst + e, c4[e] * m);
+                }
             }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float Zv = Zf + dz[k];
+            if (ic == n_ic - 1) {
+                // this channel chunk is complete: dL/dw_j partials
 #pragma unroll
                 for (int jj = 0; jj < kBwdCJ; ++jj) {
-                    const float4 rx = s_rx[jc * kBwdCJ + jj];
-                    const float Lv = rx.x + dlr[k];
-                    const float d = sqrtf(Lv * Lv + Zv * Zv);
-                    const float num = dlr[k] * (2.0f * rx.x + dlr[k]) + dz[k] * (2.0f * Zf + dz[k]);
-                    const float bt = rx.z + __fdividef(num, d + rx.y) * fsc;
-                    betah[k][jj] = fminf(fmaxf(bt, rx.z - a.reach_b), rx.z + a.reach_b) + hp;
-                    if (FN) win_w[FN ? k : 0][jj] = hann_weight(a.f_number, Lv, Zv);
+                    float v = pw[jj];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0 && v != 0.f) atomicAdd(s_gw + jc * kBwdCJ + jj, v * inv_scale);
                 }
             }
         }
-        // ---- wait for this stage's windows
-        ok = mbar_wait_parity(bar0 + 8 * b, (phase >> b) & 1u) && ok;
-        phase ^= 1u << b;
-        if (tid < kBwdCI * C::ROWS) {
-            const int ii = tid / C::ROWS, row = tid % C::ROWS;
-            const float dv = (float)row_v(row) - 0.5f * (a.bv - 1);
-            const float dw = (float)row_w(row) - 0.5f * (a.bw - 1);
-            const float dL = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]) * dv + (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]) * dw;
-            const float dzz = (float)a.Gv[2] * dv + (float)a.Gw[2] * dw;
-            const float4 tx = s_tx[ic * kBwdCI + ii];
-            const float al = tx_offset(a.tx_wave, tx, dL, dzz, Zf, Zfoc, fsc);
-            s_alpha[ii * C::ROWS + row] = fminf(fmaxf(al, tx.z - a.reach_a), tx.z + a.reach_a);
+        if (s < NS) {
+            const int ic = s % n_ic, jc = jc0 + s / n_ic;
+            if (ic == 0) {
+#pragma unroll
+                for (int jj = 0; jj < kBwdCJ; ++jj) {
+                    wj[jj] = a.apod ? __ldg(a.apod + jc * kBwdCJ + jj) : 1.0f;
+                    pw[jj] = 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float Zv = Zf + dz[k];
+#pragma unroll
+                    for (int jj = 0; jj < kBwdCJ; ++jj) {
+                        const float4 rx = s_rx[jc * kBwdCJ + jj];
+                        const float Lv = rx.x + dlr[k];
+                        const float d = sqrtf(Lv * Lv + Zv * Zv);
+                        const float num = dlr[k] * (2.0f * rx.x + dlr[k]) + dz[k] * (2.0f * Zf + dz[k]);
+                        const float bt = rx.z + __fdividef(num, d + rx.y) * fsc;
+                        betah[k][jj] = fminf(fmaxf(bt, rx.z - a.reach_b), rx.z + a.reach_b) + hp;
+                        if (FN) win_w[FN ? k : 0][jj] = hann_weight(a.f_number, Lv, Zv);
+                    }
+                }
+            }
+
+            // ---- interval sums G0, G1 of every window of stage s. With uh =
+            // u + 0.5 + H (u the window-relative delay), the interval is
+            // n = round(uh - 0.5) and the fraction f = uh - n: t = uh + 2^23 - 0.5
+            // holds n in its low mantissa bits.
+            const uint32_t abase = smem_u32(gwin + (s % 3) * C::ACC_BUF) - (0x4B000000u << 2);
+            const float* alp = s_alpha + (s & 1) * kBwdCI * C::ROWS;
+#pragma unroll 1
+            for (int ii = 0; ii < kBwdCI; ++ii) {
+                const float al_row = ZL ? alp[ii * C::ROWS + lane] : 0.f;
+#pragma unroll
+                for (int jj = 0; jj < kBwdCJ; ++jj) {
+                    const int win = ii * kBwdCJ + jj;
+                    const uint32_t wb0 = abase + 4u * (uint32_t)(win * C::GW);      // G0, plane 0
+                    // the four voxels' intervals (t holds the interval in its low bits)
+                    uint32_t tb[4];
+                    float fr[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float al = ZL ? al_row : alp[ii * C::ROWS + warp * C::VR + k / VU];
+                        const float uh = al + betah[k][jj];
+                        const float t = uh + 8388607.5f;
+                        tb[k] = __float_as_uint(t);
+                        fr[k] = uh - (t - 8388608.0f);
+                    }
+                    // With lanes over z a thread's four voxels are consecutive along
+                    // u. Where the delay changes slowly along u they fall into at
+                    // most two adjacent intervals in every lane: then per plane the
+                    // interval sums go out as two or four reductions, not eight.
+                    uint32_t span = 2;
+                    uint32_t tmin = 0;
+                    if (ZL) {
+                        tmin = min(min(tb[0], tb[1]), min(tb[2], tb[3]));
+                        span = __reduce_max_sync(0xffffffffu, max(max(tb[0], tb[1]), max(tb[2], tb[3])) - tmin);
+                    }
+                    if (ZL && span <= 1) {
+                        const uint32_t s0 = (tmin << 2) + wb0;
+#pragma unroll
+                        for (int p = 0; p < (CPLX ? 2 : 1); ++p) {
+                            int qs = 0, a1 = 0, g1 = 0, b1 = 0;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                float g = p ? gs_im[k] : gs_re[k];
+                                int q = p ? q_im[k] : q_re[k];
+                                if (FN) {
+                                    g *= win_w[FN ? k : 0][jj];
+                                    q = (int)(__float_as_uint(g + kQ) - kQbits);
+                                }
+                                const int q1 = (int)(__float_as_uint(fmaf(g, fr[k], kQ)) - kQbits);
+                                const int d = (int)(tb[k] - tmin);                  // 0 or 1
+                                qs += q;
+                                a1 += d * q;
+                                g1 += q1;
+                                b1 += d * q1;
+                            }
+                            const uint32_t sp0 = s0 + (p ? kIm : 0u);
+                            asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0), "r"(qs - a1) : "memory");
+                            asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0 + kG1), "r"(g1 - b1) : "memory");
+                            if (span == 1) {
+                                asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0 + 4u), "r"(a1) : "memory");
+                                asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0 + 4u + kG1), "r"(b1) : "memory");
+                            }
+                        }
+                        continue;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float f = fr[k];
+                        const uint32_t g0 = (tb[k] << 2) + wb0;
+                        float gr = gs_re[k];
+                        int qr = q_re[k];
+                        if (FN) {
+                            gr *= win_w[FN ? k : 0][jj];
+                            qr = (int)(__float_as_uint(gr + kQ) - kQbits);
+                        }
+                        const int q1 = (int)(__float_as_uint(fmaf(gr, f, kQ)) - kQbits);
+                        asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(g0), "r"(qr) : "memory");
+                        asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(g0 + kG1), "r"(q1) : "memory");
+                        if (CPLX) {
+                            float gi = gs_im[k];
+                            int qi = q_im[k];
+                            if (FN) {
+                                gi *= win_w[FN ? k : 0][jj];
+                                qi = (int)(__float_as_uint(gi + kQ) - kQbits);
+                            }
+                            const int qi1 = (int)(__float_as_uint(fmaf(gi, f, kQ)) - kQbits);
+                            asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(g0 + kIm), "r"(qi) : "memory");
+                            asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(g0 + kIm + kG1), "r"(qi1) : "memory");
+                        }
+                    }
+                }
+            }
+            if (s + 1 < NS) make_alpha(s + 1);
+        }
+        // clear the accumulator of stage s+1 (it held stage s-2, flushed in
+        // the previous iteration)
+        {
+            int4* clr = reinterpret_cast<int4*>(gwin + ((s + 1) % 3) * C::ACC_BUF);
+            for (int q = tid; q < C::ACC_BUF / 4; q += kDasThreads) clr[q] = make_int4(0, 0, 0, 0);
         }
         if (__syncthreads_or(!ok)) {
-            if (s + 1 < NS) mbar_wait_parity(bar0 + 8 * (b ^ 1), (phase >> (b ^ 1)) & 1u);
+            // a bounded wait expired: give the copies still in flight (stages
+            // s and, if its wait failed, s-1) a bounded chance to land, then stop
+            if (s < NS) mbar_wait_parity(bar0 + 8 * (s & 1), (phase >> (s & 1)) & 1u);
+            if (s > 0) mbar_wait_parity(bar0 + 8 * ((s - 1) & 1), ((phase >> ((s - 1) & 1)) & 1u) ^ 1u);
             if (tid == 0) atomicOr(a.status, kStatusWaitExpired);
             return;
         }
-
-        // ---- interval sums G0, G1 of every window. With uh = u + 0.5 + H (u
-        // the window-relative delay), the interval is n = round(uh - 0.5) and
-        // the fraction f = uh - n: t = uh + 2^23 - 0.5 holds n in its low
-        // mantissa bits.
-        const uint32_t abase = smem_u32(gwin) - (0x4B000000u << 2);
-#pragma unroll 1
-        for (int ii = 0; ii < kBwdCI; ++ii) {
-            const float al_row = ZL ? s_alpha[ii * C::ROWS + lane] : 0.f;
-#pragma unroll
-            for (int jj = 0; jj < kBwdCJ; ++jj) {
-                const int win = ii * kBwdCJ + jj;
-                const uint32_t wb0 = abase + 4u * (uint32_t)(win * C::GW);      // G0, plane 0
-                // the four voxels' intervals (t holds the interval in its low bits)
-                uint32_t tb[4];
-                float fr[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float al = ZL ? al_row : s_alpha[ii * C::ROWS + warp * C::VR + k / VU];
-                    const float uh = al + betah[k][jj];
-                    const float t = uh + 8388607.5f;
-                    tb[k] = __float_as_uint(t);
-                    fr[k] = uh - (t - 8388608.0f);
-                }
-                constexpr uint32_t kG1 = 4u * C::ACC_INTS;                  // G1 after G0
-                constexpr uint32_t kIm = 4u * C::NWIN * C::GW;              // plane 1 after plane 0
-                // With lanes over z a thread's four voxels are consecutive along
-                // u. Where the delay changes slowly along u they fall into at
-                // most two adjacent intervals in every lane: then per plane the
-                // interval sums go out as two or four reductions, not eight.
-                uint32_t span = 2;
-                uint32_t tmin = 0;
-                if (ZL) {
-                    tmin = min(min(tb[0], tb[1]), min(tb[2], tb[3]));
-                    span = __reduce_max_sync(0xffffffffu, max(max(tb[0], tb[1]), max(tb[2], tb[3])) - tmin);
-                }
-                if (ZL && span <= 1) {
-                    const uint32_t s0 = (tmin << 2) + wb0;
-#pragma unroll
-                    for (int p = 0; p < (CPLX ? 2 : 1); ++p) {
-                        int qs = 0, a1 = 0, g1 = 0, b1 = 0;
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            float g = p ? gs_im[k] : gs_re[k];
-                            int q = p ? q_im[k] : q_re[k];
-                            if (FN) {
-                                g *= win_w[FN ? k : 0][jj];
-                                q = (int)(__float_as_uint(g + kQ) - kQbits);
-                            }
-                            const int q1 = (int)(__float_as_uint(fmaf(g, fr[k], kQ)) - kQbits);
-                            const int d = (int)(tb[k] - tmin);                  // 0 or 1
-                            qs += q;
-                            a1 += d * q;
-                            g1 += q1;
-                            b1 += d * q1;
-                        }
-                        const uint32_t sp0 = s0 + (p ? kIm : 0u);
-                        asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0), "r"(qs - a1) : "memory");
-                        asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0 + kG1), "r"(g1 - b1) : "memory");
-                        if (span == 1) {
-                            asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0 + 4u), "r"(a1) : "memory");
-                            asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0 + 4u + kG1), "r"(b1) : "memory");
-                        }
-                    }
-                    continue;
-                }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float f = fr[k];
-                    const uint32_t g0 = (tb[k] << 2) + wb0;
-                    float gr = gs_re[k];
-                    int qr = q_re[k];
-                    if (FN) {
-                        gr *= win_w[FN ? k : 0][jj];
-                        qr = (int)(__float_as_uint(gr + kQ) - kQbits);
-                    }
-                    const int q1 = (int)(__float_as_uint(fmaf(gr, f, kQ)) - kQbits);
-                    asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(g0), "r"(qr) : "memory");
-                    asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(g0 + kG1), "r"(q1) : "memory");
-                    if (CPLX) {
-                        float gi = gs_im[k];
-                        int qi = q_im[k];
-                        if (FN) {
-                            gi *= win_w[FN ? k : 0][jj];
-                            qi = (int)(__float_as_uint(gi + kQ) - kQbits);
-                        }
-                        const int qi1 = (int)(__float_as_uint(fmaf(gi, f, kQ)) - kQbits);
-                        asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(g0 + kIm), "r"(qi) : "memory");
-                        asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(g0 + kIm + kG1), "r"(qi1) : "memory");
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        // ---- accumulators -> dL/dr = w_j c, dL/dw_j and dL/dc partials. Cells go
-        // out in groups of four samples starting at a multiple of 4 (window
-        // starts are A + off with A a multiple of 8; traces are multiples of 8
-        // long, so a group lies wholly inside or wholly outside its trace).
-        for (int q = tid; q < C::NWIN * C::PLANES * kBwdGroups; q += kDasThreads) {
-            const int g = q % kBwdGroups, wp = q / kBwdGroups;
-            const int win = wp % C::NWIN, plane = wp / C::NWIN;
-            const int off = s_off[b * C::NWIN + win];
-            const int n0 = 4 * g - off;
-            if (n0 > a.W) continue;
-            const int* G0 = gwin + (plane * C::NWIN + win) * C::GW;
-            const int* G1 = G0 + C::ACC_INTS;
-            // intervals n0-1 .. n0+3 (valid ones are 0 .. W-1)
-            int g0[4], g1[5];
-#pragma unroll
-            for (int e = 0; e < 5; ++e) {
-                const int n = n0 - 1 + e;
-                const bool in = n >= 0 && n < a.W;
-                g1[e] = in ? G1[n] : 0;
-                if (e > 0) g0[e - 1] = in ? G0[n] : 0;
-            }
-            if ((g0[0] | g0[1] | g0[2] | g0[3] | g1[0] | g1[1] | g1[2] | g1[3] | g1[4]) == 0) continue;
-            // raw sample of cell n is at window index off + n = 4g + e
-            const float* rw = reinterpret_cast<const float*>(raw + (b * C::NWIN + win) * C::RAW_WIN_BYTES +
-                                                             plane * C::RAWS * 4) + 4 * g;
-            const float4 r4 = *reinterpret_cast<const float4*>(rw);
-            const float r5 = (n0 + 3 < a.W) ? rw[4] : 0.f;     // right end of interval n0+3
-            const float rr[5] = {r4.x, r4.y, r4.z, r4.w, r5};
-            const float cwin = (float)s_S0[b * C::NWIN + win] + (float)a.t0fs + (float)n0;
-            float c4[4], pr = 0.f, pc = 0.f;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                c4[e] = (float)((long long)g0[e] - (long long)g1[e + 1] + (long long)g1[e]);
-                pr = fmaf(rr[e], c4[e], pr);
-                // interval n0+e: slope times position-weighted sum
-                pc = fmaf(rr[e + 1] - rr[e], fmaf((float)e + cwin, (float)g0[e], (float)g1[e + 1]), pc);
-            }
-            const int jj = win % kBwdCJ;
-            float w_sel = 1.f;
-#pragma unroll
-            for (int t = 0; t < kBwdCJ; ++t) {
-                if (t == jj) {
-                    pw[t] += pr;
-                    w_sel = wj[t];
-                }
-            }
-            gc = fmaf(w_sel, pc, gc);
-            const int S = s_S0[b * C::NWIN + win] - off + 4 * g;
-            if (S < 0 || S >= a.n_s || !a.grad_rf) continue;
-            const int ii = win / kBwdCJ;
-            const int i = ic * kBwdCI + ii, j = jc * kBwdCJ + jj;
-            float* dst = a.grad_rf + (long long)plane * a.plane_stride + ((long long)i * a.n_ch + j) * a.n_s + S;
-            const float m = w_sel * inv_scale;
-            if (VEC_RED) {
-                asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};"
-                             :: "l"(dst), "f"(c4[0] * m), "f"(c4[1] * m), "f"(c4[2] * m), "f"(c4[3] * m)
-                             : "memory");
-            } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (c4[e] != 0.f) atomicAdd(dst + e, c4[e] * m);
-            }
-        }
-        if (ic == n_ic - 1) {
-            // this channel chunk is complete: dL/dc and dL/dw_j partials
-#pragma unroll
-            for (int jj = 0; jj < kBwdCJ; ++jj) {
-                float v = pw[jj];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0 && v != 0.f) atomicAdd(s_gw + jc * kBwdCJ + jj, v * inv_scale);
-            }
-        }
-        __syncthreads();
-        // clear the accumulators (read above, written again after the next
-        // stage's barrier); the window starts of stage s are no longer read:
-        // refill its raw buffer
-        for (int q = tid; q < 2 * C::ACC_INTS / 4; q += kDasThreads)
-            reinterpret_cast<int4*>(gwin)[q] = make_int4(0, 0, 0, 0);
-        if (s + 2 < NS) issue(s + 2);
     }
 
     // ---- dL/dc and dL/dw partials of this unit
@@ -527,10 +549,10 @@ das_bwd_plain_kernel(DasArgs a) {
     }
 }
 
-template <int VU, bool CPLX, bool ZL, bool FN, bool VEC_RED>
+template <int VU, bool CPLX, bool ZL, bool FN, bool VEC_RED, int WS>
 int launch_bwd_tiled_v(const PlanHost& h, DasArgs a, cudaStream_t s) {
-    using C = BwdCfg<VU, CPLX>;
-    auto k = das_bwd_kernel<VU, CPLX, ZL, FN, VEC_RED>;
+    using C = BwdCfg<VU, CPLX, WS>;
+    auto k = das_bwd_kernel<VU, CPLX, ZL, FN, VEC_RED, WS>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess)
         return check_launch("das_backward: set shared memory");
     // channel split: the smallest power of two (dividing the channel chunks)
@@ -556,14 +578,24 @@ int launch_bwd_tiled_v(const PlanHost& h, DasArgs a, cudaStream_t s) {
     return check_launch("das_bwd_kernel");
 }
 
-template <int VU, bool CPLX, bool ZL>
-int launch_bwd_tiled(const PlanHost& h, const DasArgs& a, cudaStream_t s) {
+template <int VU, bool CPLX, bool ZL, int WS>
+int launch_bwd_tiled_ws(const PlanHost& h, const DasArgs& a, cudaStream_t s) {
     const bool fn = a.f_number > 0.f;
     const bool vec = (reinterpret_cast<uintptr_t>(a.grad_rf) & 15u) == 0;
-    if (fn) return vec ? launch_bwd_tiled_v<VU, CPLX, ZL, true, true>(h, a, s)
-                       : launch_bwd_tiled_v<VU, CPLX, ZL, true, false>(h, a, s);
-    return vec ? launch_bwd_tiled_v<VU, CPLX, ZL, false, true>(h, a, s)
-               : launch_bwd_tiled_v<VU, CPLX, ZL, false, false>(h, a, s);
+    if (fn) return vec ? launch_bwd_tiled_v<VU, CPLX, ZL, true, true, WS>(h, a, s)
+                       : launch_bwd_tiled_v<VU, CPLX, ZL, true, false, WS>(h, a, s);
+    return vec ? launch_bwd_tiled_v<VU, CPLX, ZL, false, true, WS>(h, a, s)
+               : launch_bwd_tiled_v<VU, CPLX, ZL, false, false, WS>(h, a, s);
+}
+
+// Windows of up to 96 intervals keep two CTAs per SM (the 96 class, built for
+// the lanes-over-z tile of the autofocus path); larger ones use the 128 class.
+template <int VU, bool CPLX, bool ZL>
+int launch_bwd_tiled(const PlanHost& h, const DasArgs& a, cudaStream_t s) {
+    if constexpr (ZL) {
+        if (a.W <= 96) return launch_bwd_tiled_ws<VU, CPLX, ZL, 96>(h, a, s);
+    }
+    return launch_bwd_tiled_ws<VU, CPLX, ZL, 128>(h, a, s);
 }
 
 }  // namespace
