@@ -253,103 +253,19 @@ das_bwd_kernel(DasArgs a) {
     constexpr uint32_t kG1 = 4u * C::ACC_INTS;                  // G1 after G0
     constexpr uint32_t kIm = 4u * C::NWIN * C::GW;              // plane 1 after plane 0
 
-    // Iteration s: copy the windows of stage s; flush stage s-1 (its windows
-    // landed during the previous iteration); accumulate stage s; compute the
-    // transmit terms of stage s+1 and clear the accumulator of stage s+1
-    // (last flushed in the previous iteration). One barrier per iteration
-    // orders every hand-over: accumulator s is complete before its flush in
-    // iteration s+1 and cleared in iteration s+2 before stage s+3 uses it.
+    // Iteration s: copy the windows of stage s; accumulate stage s (the sums
+    // need the window starts only, not the samples); flush stage s-1 (its
+    // windows were copied a whole iteration earlier); compute the transmit
+    // terms of stage s+1 and clear the accumulator of stage s+1 (last flushed
+    // in the previous iteration). One barrier per iteration orders every
+    // hand-over: accumulator s is complete before its flush in iteration s+1
+    // and cleared in iteration s+2 before stage s+3 uses it. The channel
+    // weights and dL/dw partials follow the flushed stage's channel chunk.
     for (int s = 0; s <= NS; ++s) {
         if (s < NS) issue(s);
-        if (s > 0) {
-            // ---- flush stage t = s - 1: accumulators -> dL/dr = w_j c, dL/dw_j
-            // and dL/dc partials. Cells go out in groups of four samples
-            // starting at a multiple of 4 (window starts are A + off with A a
-            // multiple of 8; traces are multiples of 8 long, so a group lies
-            // wholly inside or wholly outside its trace).
-            const int t = s - 1, tb = t & 1;
-            const int ic = t % n_ic, jc = jc0 + t / n_ic;
-            ok = mbar_wait_parity(bar0 + 8 * tb, (phase >> tb) & 1u) && ok;
-            phase ^= 1u << tb;
-            const int* acc = gwin + (t % 3) * C::ACC_BUF;
-            for (int q = tid; q < C::NWIN * C::PLANES * C::GROUPS; q += kDasThreads) {
-                const int g = q % C::GROUPS, wp = q / C::GROUPS;
-                const int win = wp % C::NWIN, plane = wp / C::NWIN;
-                const int off = s_off[tb * C::NWIN + win];
-                const int n0 = 4 * g - off;
-                if (n0 > a.W) continue;
-                const int* G0 = acc + (plane * C::NWIN + win) * C::GW;
-                const int* G1 = G0 + C::ACC_INTS;
-                // intervals n0-1 .. n0+3 (valid ones are 0 .. W-1)
-                int g0[4], g1[5];
-#pragma unroll
-                for (int e = 0; e < 5; ++e) {
-                    const int n = n0 - 1 + e;
-                    const bool in = n >= 0 && n < a.W;
-                    g1[e] = in ? G1[n] : 0;
-                    if (e > 0) g0[e - 1] = in ? G0[n] : 0;
-                }
-                if ((g0[0] | g0[1] | g0[2] | g0[3] | g1[0] | g1[1] | g1[2] | g1[3] | g1[4]) == 0) continue;
-                // raw sample of cell n is at window index off + n = 4g + e
-                const float* rw = reinterpret_cast<const float*>(raw + (tb * C::NWIN + win) * C::RAW_WIN_BYTES +
-                                                                 plane * C::RAWS * 4) + 4 * g;
-                const float4 r4 = *reinterpret_cast<const float4*>(rw);
-                const float r5 = (n0 + 3 < a.W) ? rw[4] : 0.f;     // right end of interval n0+3
-                const float rr[5] = {r4.x, r4.y, r4.z, r4.w, r5};
-                const float cwin = (float)s_S0[tb * C::NWIN + win] + (float)a.t0fs + (float)n0;
-                float c4[4], pr = 0.f, pc = 0.f;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    c4[e] = (float)((long long)g0[e] - (long long)g1[e + 1] + (long long)g1[e]);
-                    pr = fmaf(rr[e], c4[e], pr);
-                    // interval n0+e: slope times position-weighted sum
-                    pc = fmaf(rr[e + 1] - rr[e], fmaf((float)e + cwin, (float)g0[e], (float)g1[e + 1]), pc);
-                }
-                const int jj = win % kBwdCJ;
-                float w_sel = 1.f;
-#pragma unroll
-                for (int u = 0; u < kBwdCJ; ++u) {
-                    if (u == jj) {
-                        pw[u] += pr;
-                        w_sel = wj[u];
-                    }
-                }
-                gc = fmaf(w_sel, pc, gc);
-                const int S = s_S0[tb * C::NWIN + win] - off + 4 * g;
-                if (S < 0 || S >= a.n_s || !a.grad_rf) continue;
-                const int ii = win / kBwdCJ;
-                const int i = ic * kBwdCI + ii, j = jc * kBwdCJ + jj;
-                float* dst = a.grad_rf + (long long)plane * a.plane_stride + ((long long)i * a.n_ch + j) * a.n_s + S;
-                const float m = w_sel * inv_scale;
-                if (VEC_RED) {
-                    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};"
-                                 :: "l"(dst), "f"(c4[0] * m), "f"(c4[1] * m), "f"(c4[2] * m), "f"(c4[3] * m)
-                                 : "memory");
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (c4[e] != 0.f) atomicAdd(dst + e, c4[e] * m);
-                }
-            }
-            if (ic == n_ic - 1) {
-                // this channel chunk is complete: dL/dw_j partials
-#pragma unroll
-                for (int jj = 0; jj < kBwdCJ; ++jj) {
-                    float v = pw[jj];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (lane == 0 && v != 0.f) atomicAdd(s_gw + jc * kBwdCJ + jj, v * inv_scale);
-                }
-            }
-        }
         if (s < NS) {
             const int ic = s % n_ic, jc = jc0 + s / n_ic;
             if (ic == 0) {
-#pragma unroll
-                for (int jj = 0; jj < kBwdCJ; ++jj) {
-                    wj[jj] = a.apod ? __ldg(a.apod + jc * kBwdCJ + jj) : 1.0f;
-                    pw[jj] = 0.f;
-                }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const float Zv = Zf + dz[k];
@@ -458,6 +374,94 @@ das_bwd_kernel(DasArgs a) {
                 }
             }
             if (s + 1 < NS) make_alpha(s + 1);
+        }
+        if (s > 0) {
+            // ---- flush stage t = s - 1: accumulators -> dL/dr = w_j c, dL/dw_j
+            // and dL/dc partials. Cells go out in groups of four samples
+            // starting at a multiple of 4 (window starts are A + off with A a
+            // multiple of 8; traces are multiples of 8 long, so a group lies
+            // wholly inside or wholly outside its trace).
+            const int t = s - 1, tb = t & 1;
+            const int ic = t % n_ic, jc = jc0 + t / n_ic;
+            ok = mbar_wait_parity(bar0 + 8 * tb, (phase >> tb) & 1u) && ok;
+            phase ^= 1u << tb;
+            const int* acc = gwin + (t % 3) * C::ACC_BUF;
+            if (ic == 0) {
+#pragma unroll
+                for (int jj = 0; jj < kBwdCJ; ++jj) {
+                    wj[jj] = a.apod ? __ldg(a.apod + jc * kBwdCJ + jj) : 1.0f;
+                    pw[jj] = 0.f;
+                }
+            }
+            for (int q = tid; q < C::NWIN * C::PLANES * C::GROUPS; q += kDasThreads) {
+                const int g = q % C::GROUPS, wp = q / C::GROUPS;
+                const int win = wp % C::NWIN, plane = wp / C::NWIN;
+                const int off = s_off[tb * C::NWIN + win];
+                const int n0 = 4 * g - off;
+                if (n0 > a.W) continue;
+                const int* G0 = acc + (plane * C::NWIN + win) * C::GW;
+                const int* G1 = G0 + C::ACC_INTS;
+                // intervals n0-1 .. n0+3 (valid ones are 0 .. W-1)
+                int g0[4], g1[5];
+#pragma unroll
+                for (int e = 0; e < 5; ++e) {
+                    const int n = n0 - 1 + e;
+                    const bool in = n >= 0 && n < a.W;
+                    g1[e] = in ? G1[n] : 0;
+                    if (e > 0) g0[e - 1] = in ? G0[n] : 0;
+                }
+                if ((g0[0] | g0[1] | g0[2] | g0[3] | g1[0] | g1[1] | g1[2] | g1[3] | g1[4]) == 0) continue;
+                // raw sample of cell n is at window index off + n = 4g + e
+                const float* rw = reinterpret_cast<const float*>(raw + (tb * C::NWIN + win) * C::RAW_WIN_BYTES +
+                                                                 plane * C::RAWS * 4) + 4 * g;
+                const float4 r4 = *reinterpret_cast<const float4*>(rw);
+                const float r5 = (n0 + 3 < a.W) ? rw[4] : 0.f;     // right end of interval n0+3
+                const float rr[5] = {r4.x, r4.y, r4.z, r4.w, r5};
+                const float cwin = (float)s_S0[tb * C::NWIN + win] + (float)a.t0fs + (float)n0;
+                float c4[4], pr = 0.f, pc = 0.f;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    c4[e] = (float)((long long)g0[e] - (long long)g1[e + 1] + (long long)g1[e]);
+                    pr = fmaf(rr[e], c4[e], pr);
+                    // interval n0+e: slope times position-weighted sum
+                    pc = fmaf(rr[e + 1] - rr[e], fmaf((float)e + cwin, (float)g0[e], (float)g1[e + 1]), pc);
+                }
+                const int jj = win % kBwdCJ;
+                float w_sel = 1.f;
+#pragma unroll
+                for (int u = 0; u < kBwdCJ; ++u) {
+                    if (u == jj) {
+                        pw[u] += pr;
+                        w_sel = wj[u];
+                    }
+                }
+                gc = fmaf(w_sel, pc, gc);
+                const int S = s_S0[tb * C::NWIN + win] - off + 4 * g;
+                if (S < 0 || S >= a.n_s || !a.grad_rf) continue;
+                const int ii = win / kBwdCJ;
+                const int i = ic * kBwdCI + ii, j = jc * kBwdCJ + jj;
+                float* dst = a.grad_rf + (long long)plane * a.plane_stride + ((long long)i * a.n_ch + j) * a.n_s + S;
+                const float m = w_sel * inv_scale;
+                if (VEC_RED) {
+                    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};"
+                                 :: "l"(dst), "f"(c4[0] * m), "f"(c4[1] * m), "f"(c4[2] * m), "f"(c4[3] * m)
+                                 : "memory");
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (c4[e] != 0.f) atomicAdd(dst + e, c4[e] * m);
+                }
+            }
+            if (ic == n_ic - 1) {
+                // this channel chunk is complete: dL/dw_j partials
+#pragma unroll
+                for (int jj = 0; jj < kBwdCJ; ++jj) {
+                    float v = pw[jj];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0 && v != 0.f) atomicAdd(s_gw + jc * kBwdCJ + jj, v * inv_scale);
+                }
+            }
         }
         // clear the accumulator of stage s+1 (it held stage s-2, flushed in
         // the previous iteration)
