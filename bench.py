@@ -596,6 +596,10 @@ def main():
     frame_bytes = g.n_tx * g.n_ch * g.n_samples * (2 + 2 + 2) + g.n_vox * 4
     window_bytes = n_tiles * g.n_tx * g.n_ch * raw_samples * 2
     traffic = recorded_traffic("batch_kernel", B)
+    # on-chip ceilings measured on this GPU (microbenchmarks at the DAS
+    # kernel's occupancy): one 8-byte line piece per sum from shared memory
+    ceil = rc.measure_ceilings()
+    das_alone = sums / (t_das * 1e-3)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -631,6 +635,16 @@ def main():
                             "l2_window_GBps": B * window_bytes / (t_batch * 1e-3) / 1e9,
                             "kernel": "batch_kernel", "peak_src": peaks["src"],
                             "bytes_per_frame": frame_bytes},
+        "ceilings": {"lds64_TBps": ceil["lds64_bytes_per_s"] / 1e12,
+                     "ffma_TOPs": ceil["ffma_lane_ops_per_s"] / 1e12,
+                     "ffma2_TOPs": ceil["ffma2_lane_ops_per_s"] / 1e12,
+                     "red_shared_G_per_s": ceil["red_shared_per_s"] / 1e9,
+                     "sm_mhz": ceil["sm_clock_hz"] / 1e6,
+                     "lds_sums_per_s_ceiling": ceil["lds64_bytes_per_s"] / 8.0,
+                     "frac_lds_batched": B * sums / (t_batch * 1e-3) * 8.0 / ceil["lds64_bytes_per_s"],
+                     "frac_lds_das_alone": das_alone * 8.0 / ceil["lds64_bytes_per_s"],
+                     "frac_ffma_batched": achieved * 1e12 / ceil["ffma_lane_ops_per_s"],
+                     "source": "rcbf_measure_ceilings (this GPU, 2 CTAs x 256 threads per SM)"},
         "roofline_decode": {"bound": "hbm", "achieved": dec_bytes / (t_dec * 1e-3) / 1e9,
                             "peak": peaks["hbm_gbs"], "unit": "GB/s",
                             "frac": dec_bytes / (t_dec * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": None,

@@ -400,6 +400,33 @@ void rcbf_pipeline_destroy(rcbf_pipeline_t pipeline);
 int rcbf_das_noalloc(const rcbf_params* params, const void* decoded, const float* apod, float c,
                      float* image, void* stream);
 
+/* rcbf_measure_ceilings — on-chip ceilings of the current device, measured
+ * by microbenchmark kernels run at the tiled DAS kernel's occupancy (two CTAs
+ * of 256 threads per SM, one per resident slot): the denominators of the DAS
+ * roofline, which is bound on chip, not by HBM (the paper's own optimisation
+ * section discusses the DAS as the stage with the most operations, without a
+ * roofline). Fields:
+ *   lds64_bytes_per_s    conflict-free 8-byte shared-memory loads (one line
+ *                        piece (c_n, slope_n) per DAS sum);
+ *   ffma_lane_ops_per_s  scalar FP32 FMAs, lanes x instructions per second;
+ *   ffma2_lane_ops_per_s packed f32x2 FMAs, two lane operations each;
+ *   red_shared_per_s     warp-wide shared integer reductions (red.shared.add.s32)
+ *                        to 32 distinct addresses, warp instructions per second;
+ *   sm_clock_hz          SM clock during the loads: clock64 cycles over
+ *                        global-timer time in one thread (0 if the timer
+ *                        did not advance).
+ * Runs four short kernels (a few ms each, bounded loops, no waits) on `stream`
+ * and synchronises it. Errors: RCBF_EINVAL (NULL out), RCBF_ECUDA. */
+typedef struct rcbf_ceilings {
+    double lds64_bytes_per_s;
+    double ffma_lane_ops_per_s;
+    double ffma2_lane_ops_per_s;
+    double red_shared_per_s;
+    double sm_clock_hz;
+} rcbf_ceilings;
+
+int rcbf_measure_ceilings(rcbf_ceilings* out, void* stream);
+
 /* rcbf_last_error — message for the last failure on this thread ("" if none). */
 const char* rcbf_last_error(void);
 

@@ -80,6 +80,12 @@ class PlanInfo(ctypes.Structure):
 
 # symbol -> (restype, argtypes); every function rcbf.h declares
 _P = ctypes.c_void_p
+class Ceilings(ctypes.Structure):
+    _fields_ = [("lds64_bytes_per_s", ctypes.c_double), ("ffma_lane_ops_per_s", ctypes.c_double),
+                ("ffma2_lane_ops_per_s", ctypes.c_double), ("red_shared_per_s", ctypes.c_double),
+                ("sm_clock_hz", ctypes.c_double)]
+
+
 SIGNATURES = {
     "rcbf_plan": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(_P)]),
     "rcbf_destroy": (None, [_P]),
@@ -99,6 +105,7 @@ SIGNATURES = {
     "rcbf_batch_set_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int32]),
     "rcbf_batch_destroy": (None, [_P]),
     "rcbf_das_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _P, _P, ctypes.c_float, _P, _P]),
+    "rcbf_measure_ceilings": (ctypes.c_int, [ctypes.POINTER(Ceilings), _P]),
     "rcbf_last_error": (ctypes.c_char_p, []),
     "rcbf_version": (ctypes.c_char_p, []),
 }
@@ -388,6 +395,14 @@ class Batch:
 
 def version() -> str:
     return load_library().rcbf_version().decode()
+
+
+def measure_ceilings(stream=None) -> dict:
+    """On-chip ceilings of the current device measured by microbenchmark
+    kernels at the tiled DAS kernel's occupancy (rcbf_measure_ceilings)."""
+    out = Ceilings()
+    _check(load_library().rcbf_measure_ceilings(ctypes.byref(out), _stream(stream)))
+    return {name: getattr(out, name) for name, _ in Ceilings._fields_}
 
 
 def _make_das_function():

@@ -72,6 +72,24 @@ def test_plan_info_layout_matches_header(tmp_path):
     assert got == [ctypes.sizeof(I), I.workspace_bytes.offset, I.bwd_tile.offset, I.bwd_mode.offset]
 
 
+def test_ceilings_layout_matches_header(tmp_path):
+    src = tmp_path / "ceil.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "rcbf.h"\n'
+        "int main(void){printf(\"%zu %zu %zu\\n\", sizeof(rcbf_ceilings),"
+        " offsetof(rcbf_ceilings, red_shared_per_s), offsetof(rcbf_ceilings, sm_clock_hz)); return 0;}\n")
+    exe = tmp_path / "ceil"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    C = rc.Ceilings
+    assert got == [ctypes.sizeof(C), C.red_shared_per_s.offset, C.sm_clock_hz.offset]
+
+
+def test_measure_ceilings_rejects_null():
+    lib = rc.load_library()
+    assert lib.rcbf_measure_ceilings(None, None) == rc.EINVAL
+
+
 def _good_params():
     import synth
     return rc.make_params(synth.tiny_bscan_geometry(), decoded_dtype="f32")
