@@ -191,32 +191,45 @@ def run_reference(args):
         return
     import oracle
     import synth
-    frame = synth.full_bscan(seed=2)
+    # the default B-scan, or (for the oracle's own timing on the other
+    # configurations) the tiny B-scan, the HERCULES volume or the complex
+    # autofocus frame; each step times a bounded random voxel sample
+    workload = args.workload if args.workload in ("tiny", "volume", "autofocus") else "bscan"
+    frame = {"bscan": lambda: synth.full_bscan(seed=2), "tiny": lambda: synth.tiny_bscan(1),
+             "volume": lambda: synth.hercules_volume(3), "autofocus": lambda: synth.autofocus(5)}[workload]()
     g = frame.geometry
     oracle.build()
     cores = oracle.threads()
-    exact = _exact_decoded(frame)
+    if frame.rf is not None:
+        exact = _exact_decoded(frame)
+    else:
+        exact = frame.decoded.astype(np.complex128 if np.iscomplexobj(frame.decoded) else np.float64)
     rng = np.random.default_rng(1)
-    nv = 2048                                  # voxels per step (a bounded sample)
+    nv = min(2048, g.n_vox)                    # voxels per step (a bounded sample)
     phi = nv / g.n_vox
     ncol = int(round(phi * g.n_ch * g.n_samples))
     times = []
     for step in range(args.warmup + args.steps):
         vox = np.sort(rng.choice(g.n_vox, size=nv, replace=False)).astype(np.int64)
         t0 = time.perf_counter()
-        oracle.decode(frame.rf.reshape(g.n_tx, -1)[:, :ncol])
+        if frame.rf is not None:
+            oracle.decode(frame.rf.reshape(g.n_tx, -1)[:, :ncol])
         oracle.das(g, exact, voxels=vox)
         t1 = time.perf_counter()
         if step >= args.warmup:
             times.append(t1 - t0)
     per = float(np.mean(times))
     value = nv * g.n_tx * g.n_ch / per / 1e9
-    sample = "%d random voxels (%.5f of the frame) and the same fraction of decode columns per step" % (nv, phi)
+    sample = "%d random voxels (%.5f of the frame)%s per step" % (
+        nv, phi, " and the same fraction of decode columns" if frame.rf is not None else " (complex, two planes)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": sample},
+        "config": {"workload": WORKLOAD if workload == "bscan" else
+                   "FORCES tiny B-scan: 32 tx (H32) x 32 ch x 1024 int16 samples -> 128x128 FP32 image"
+                   if workload == "tiny" else OTHER_WORKLOADS[workload],
+                   "sample": sample},
         "frames_per_s": value * 1e9 / g.sums,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -382,9 +395,12 @@ def main():
     ap.add_argument("--batch", type=int, default=4, help="frames per step (one persistent launch)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="bscan", choices=["bscan"] + sorted(OTHER_WORKLOADS),
-                    help="bscan (the headline) or another configuration on its own line")
+    ap.add_argument("--workload", default="bscan", choices=["bscan", "tiny"] + sorted(OTHER_WORKLOADS),
+                    help="bscan (the headline) or another configuration on its own line "
+                         "(tiny: the 32-transmit B-scan, reference arm only)")
     args = ap.parse_args()
+    if args.workload == "tiny" and args.impl != "reference":
+        ap.error("--workload tiny times the oracle only (--impl reference)")
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
