@@ -534,6 +534,21 @@ def main():
     torch.cuda.synchronize()
     t_cubic = c0.elapsed_time(c1) / ub_steps
 
+    # ---- F# = 1 (the receive window of Eq. (2)-(3) active): sums/s counts
+    # every term of the sum ("effective" throughput) although channel chunks
+    # outside a tile's aperture are skipped
+    fn1 = rc.Plan(rc.make_params(g, decoded_dtype="f16", das_variant=rc.DAS_TILED, tile=tile, f_number=1.0))
+    for s in range(3):
+        fn1.das(dec16[s % B], out=imgs[0])
+    f0, f1 = _events(2)
+    torch.cuda.synchronize()
+    f0.record(stream)
+    for s in range(ub_steps):
+        fn1.das(dec16[s % B], out=imgs[0])
+    f1.record(stream)
+    torch.cuda.synchronize()
+    t_fn1 = f0.elapsed_time(f1) / ub_steps
+
     # ---- plain FP32 form on the same GPU (same frames, same timing)
     plain = rc.Plan(rc.make_params(g, decoded_dtype="f32", decode_variant=rc.DECODE_PLAIN,
                                    das_variant=rc.DAS_PLAIN))
@@ -633,6 +648,9 @@ def main():
                       "decode_f16_mma_alternative": t_dec_f16},
         "unbatched": {"value": sums / ((t_dec + t_das) * 1e-3) / 1e9, "unit": UNIT,
                       "das_only": sums / (t_das * 1e-3) / 1e9},
+        "f_number_1": {"value": sums / (t_fn1 * 1e-3) / 1e9, "unit": UNIT, "ms_per_frame": t_fn1,
+                       "form": "tiled DAS alone with F# = 1 (effective: every term counted; channel chunks "
+                               "outside a tile's aperture skipped)"},
         "cubic": {"value": sums / (t_cubic * 1e-3) / 1e9, "unit": UNIT, "ms_per_frame": t_cubic,
                   "tile": list(ctile), "window": cub.info()["window"],
                   "form": "tiled DAS alone, 4-point cubic Hermite, FP16 decoded frame"},

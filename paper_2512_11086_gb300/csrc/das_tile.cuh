@@ -76,7 +76,7 @@ __device__ __forceinline__ void static_for(F&& f) {
     }
 }
 
-template <int VU, int WS, bool CPLX, bool CUBIC = false, bool D2 = false>
+template <int VU, int WS, bool CPLX, bool CUBIC = false, bool D2 = false, bool APOD = false>
 struct DasCfg {
     static constexpr int VR = 4 / VU;              // tile rows per thread
     static constexpr int ROWS = 8 * VR;            // tile rows (one warp covers VR rows)
@@ -103,7 +103,8 @@ struct DasCfg {
     static constexpr int OFF_WOFF = OFF_ALPHA + NB * ALPHA_N * 4;      // int[2][NWIN]
     static constexpr int OFF_WPH = OFF_WOFF + 2 * NWIN * 4;            // float[NB][NWIN]: IQ window phases
     static constexpr int OFF_WS0 = OFF_WPH + NB * NWIN * 4;            // float[NB][NWIN]: 2D window starts
-    static constexpr int OFF_BAR = ((OFF_WS0 + (D2 ? NB * NWIN * 4 : 0) + 7) / 8) * 8;   // uint64[10]
+    static constexpr int OFF_ACT = OFF_WS0 + (D2 ? NB * NWIN * 4 : 0); // int[chunks + 1]: active channel chunks, count (APOD)
+    static constexpr int OFF_BAR = ((OFF_ACT + (APOD ? (kMaxChannels / CJ + 1) * 4 : 0) + 7) / 8) * 8;   // uint64[10]
     static constexpr int OFF_ABORT = OFF_BAR + 80;                     // int: a bounded wait expired
     static constexpr int SMEM = OFF_ABORT + 16;
     static_assert(ALPHA_N <= kDasThreads, "one thread per transmit term");
@@ -264,7 +265,7 @@ __device__ __forceinline__ void das_pipe_init(unsigned char* bar_base, volatile 
 // stop; the caller records the status).
 template <int VU, int WS, bool CPLX, bool APOD, bool CUBIC = false, bool IQ = false, bool D2 = false>
 __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned char* smem, DasPipe& pipe) {
-    using C = DasCfg<VU, WS, CPLX, CUBIC, D2>;
+    using C = DasCfg<VU, WS, CPLX, CUBIC, D2, APOD>;
     static_assert(!IQ || CPLX, "IQ beamforming reads two planes");
     float* s_ws0 = reinterpret_cast<float*>(smem + C::OFF_WS0);
     float* s_wph = reinterpret_cast<float*>(smem + C::OFF_WPH);
@@ -285,7 +286,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     const int n_ic = a.n_tx / C::CI;
     const int js = (a.n_ch / C::CJ) / a.n_split;     // channel chunks of this unit
     const int jc0 = split * js;
-    const int NS = n_ic * js;
+    int* s_act = reinterpret_cast<int*>(smem + C::OFF_ACT);
 
     // ---- tile position and FP64 reference delays
     const int tu = tile % a.tiles_u;
@@ -396,7 +397,39 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
         const float lowd = sqrtf(s_tx[i].y + s_rx[j].y);
         return (int)floorf(fmaf(lowd, fsc, elo)) - 1;
     };
-    __syncthreads();   // reference tables ready
+    // Channel chunks of this unit with a nonzero F# window somewhere in the
+    // tile (Eq. (2)-(3) skip test, on the tile's bounding box: a chunk is
+    // skipped only if F# |lat - e_j| >= |z| / 2 at every voxel for all its
+    // channels, so skipping changes nothing); all chunks without a window
+    if (APOD && a.f_number > 0.f) {
+        const double hr = 0.5 * (fabs(a.rx_axis ? a.Gu[1] : a.Gu[0]) * (C::BU - 1) +
+                                 fabs(a.rx_axis ? a.Gv[1] : a.Gv[0]) * (a.bv - 1) +
+                                 fabs(a.rx_axis ? a.Gw[1] : a.Gw[0]) * (a.bw - 1));
+        const double zmax = fabs(zr) + 0.5 * (fabs(a.Gu[2]) * (C::BU - 1) + fabs(a.Gv[2]) * (a.bv - 1) +
+                                              fabs(a.Gw[2]) * (a.bw - 1));
+        for (int c = tid; c < js; c += kDasThreads) {
+            int act = 0;
+            for (int jj = 0; jj < C::CJ; ++jj) {
+                const double L = lat_rx_ref - (a.rx_e0 + ((jc0 + c) * C::CJ + jj) * a.rx_pitch);
+                act |= (double)a.f_number * fmax(fabs(L) - hr, 0.0) < 0.5 * zmax + 1e-9;
+            }
+            s_act[c] = act;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int n = 0;
+            for (int c = 0; c < js; ++c)
+                if (s_act[c]) s_act[n++] = jc0 + c;
+            s_act[kMaxChannels / C::CJ] = n;
+        }
+    } else if (APOD && tid == 0) {
+        for (int c = 0; c < js; ++c) s_act[c] = jc0 + c;
+        s_act[kMaxChannels / C::CJ] = js;
+    }
+    __syncthreads();   // reference tables and the chunk list ready
+    // channel chunk of stage s (forms without weights never skip a chunk)
+    auto chunk_of = [&](int s) -> int { return APOD ? s_act[s / n_ic] : jc0 + s / n_ic; };
+    const int NS = n_ic * (APOD ? s_act[kMaxChannels / C::CJ] : js);
 
     volatile int* abort = reinterpret_cast<volatile int*>(smem + C::OFF_ABORT);
     auto wait = [&](int slot, uint32_t phase) -> bool {
@@ -419,7 +452,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
         const int win = CPLX ? (copy >> 1) : copy;
         const int plane = CPLX ? (copy & 1) : 0;
         const int ii = win / C::CJ, jj = win % C::CJ;
-        const int i = (s % n_ic) * C::CI + ii, j = (jc0 + s / n_ic) * C::CJ + jj;
+        const int i = (s % n_ic) * C::CI + ii, j = chunk_of(s) * C::CJ + jj;
         // first staged sample (cubic: one before the window, for the stencil)
         const int S0 = (D2 ? Kt + win_start(i, j) : __float_as_int(s_tx[i].w) + __float_as_int(s_rx[j].w) + a.lo) -
                        (CUBIC ? 1 : 0);
@@ -470,7 +503,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             rewrite_windows<float, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
         if ((IQ || D2) && tid < C::NWIN) {
             const int win = tid;
-            const int i = (s % n_ic) * C::CI + win / C::CJ, j = (jc0 + s / n_ic) * C::CJ + win % C::CJ;
+            const int i = (s % n_ic) * C::CI + win / C::CJ, j = chunk_of(s) * C::CJ + win % C::CJ;
             int S0;
             if constexpr (D2) {
                 const int w0 = win_start(i, j);
@@ -561,14 +594,17 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     }
 
     // ---- prologue: stages 0 and 1 in flight, stage 0 rewritten
-    bool ok = issue(0);
-    if (ok && NS > 1) ok = issue(1);
-    if (ok) ok = prepare(0);
+    bool ok = true;
+    if (!APOD || NS > 0) {          // a weighted unit may have no active chunk
+        ok = issue(0);
+        if (ok && NS > 1) ok = issue(1);
+        if (ok) ok = prepare(0);
+    }
     int issued = NS > 1 ? 1 : 0;      // last stage this thread's copies were requested for
     int landed = 0;                   // last stage whose raw windows this thread waited for
 
     for (int s = 0; ok && s < NS; ++s) {
-        const int ic = s % n_ic, jc = jc0 + s / n_ic;
+        const int ic = s % n_ic, jc = chunk_of(s);
         const int pb = piece_buf(s);
         if (ic == 0) {
             // per-voxel receive terms (and apodization) for this channel chunk
