@@ -93,7 +93,11 @@ enum rcbf_acq_kind {
                               (tx_wave RCBF_TX_PLANE with tx_angles[0], or RCBF_TX_POINT): index i is
                               the receive row at lateral e_i (tx_orientation's axis), j the column;
                               d_rx = sqrt((lat_rx - e_j)^2 + (lat_tx - e_i)^2 + z^2), not separable;
-                              the F# window uses the radial lateral distance. Plain DAS form. */
+                              the F# window uses the radial lateral distance. Tiled DAS form with
+                              windows from the tile's bounding box (one voxel per thread along u,
+                              tile 32 x bv x bw) when f_number == 0, the tile reaches at most 128
+                              samples and rows and columns lie along different axes; otherwise
+                              the plain form. */
 };
 
 enum rcbf_orientation {
@@ -273,7 +277,10 @@ int rcbf_decode(rcbf_plan_t plan, const int16_t* rf, void* decoded, void* stream
  * needs n_tx % 8 == 0 (4 for complex), n_ch % 8 == 0, an image axis parallel
  * to the transmit line elements, and voxel tiles that reach at most 128
  * samples of a trace (any grid finer than about a quarter of the pulse
- * length); a grid too coarse for that runs the plain form instead.
+ * length); a grid too coarse for that runs the plain form instead. With
+ * f_number > 0 the tiled form skips, per voxel tile, every chunk of 8
+ * channels whose window W is zero at all of the tile's voxels (the test of
+ * Eq. (2)-(3) on the tile's bounding box; the result is unchanged).
  * Errors: RCBF_EINVAL, RCBF_EUNSUPPORTED, RCBF_ECUDA. */
 int rcbf_das(rcbf_plan_t plan, const void* decoded, const float* apod, float c,
              float* image, void* stream);
