@@ -223,3 +223,24 @@ def test_point_scatterer_peak_matches_oracle():
     img = plan.das(plan.decode(torch.from_numpy(fr.rf).cuda())).cpu().numpy()
     iz, iy, ix = np.unravel_index(np.argmax(np.abs(img)), img.shape)
     assert (ix, iy, iz) == node
+
+
+@pytest.mark.parametrize("dtype,cubic", [("f32", False), ("f16", False), ("f32", True)])
+def test_f_number_chunk_skip_and_tiles_outside_every_aperture(dtype, cubic):
+    # lateral extent ±8 mm against a 3.2 mm array and F# = 3: tiles beyond
+    # about 3 mm from the array have no channel chunk inside their window
+    # (the unit sums nothing) and shallow tiles keep only a few chunks; the
+    # image must equal the oracle's, with exact zeros where every weight is 0
+    g = synth.Geometry(n_tx=32, n_ch=32, n_samples=1024, hadamard_order=0, out_dims=(256, 1, 160),
+                       out_min=(-8 * MM, 0.0, 2 * MM), out_max=(8 * MM, 0.0, 10 * MM))
+    if cubic:
+        g.interp = "cubic"
+    r = np.random.default_rng(19).normal(size=(32, 32, 1024))
+    w = np.random.default_rng(20).uniform(0.5, 1.5, 32)
+    data = r.astype(np.float16).astype(np.float64) if dtype == "f16" else r
+    want = oracle.das(g, data, w=w, f_number=3.0, interp="cubic" if cubic else "linear")
+    got = _gpu_image(g, data if dtype == "f32" else data.astype(np.float16), dtype=dtype, apod=w, f_number=3.0)
+    assert _report("F#3 wide grid %s cubic=%s" % (dtype, cubic), got, want) <= TOL
+    dead = want == 0.0
+    assert dead.sum() > 0.2 * dead.size                 # many voxels lie outside every aperture
+    assert np.all(got[dead] == 0.0)
