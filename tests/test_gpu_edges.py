@@ -120,3 +120,17 @@ def test_channel_shards_sum_to_the_frame():
     full = rc.Plan(rc.make_params(g, decoded_dtype="f32")).das(dec).cpu().numpy()
     assert rel_l2(total.cpu().numpy(), full) <= 1e-5
     assert rel_l2(total.cpu().numpy(), oracle.das(g, fr.decoded.astype(np.float64))) <= TOL
+
+
+def test_measured_ceilings_are_consistent_with_the_clock():
+    # the microbenchmarks behind the DAS roofline: per SM and clock, 8-byte
+    # shared loads deliver at most 128 B (one wavefront), FP32 FMA at most
+    # 128 lane operations, shared reductions at most one warp instruction
+    c = rc.measure_ceilings()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    per_clk = sms * c["sm_clock_hz"]
+    assert 1e8 < c["sm_clock_hz"] < 4e9
+    assert 0.5 * 128 <= c["lds64_bytes_per_s"] / per_clk <= 1.05 * 128
+    assert 0.5 * 128 <= c["ffma_lane_ops_per_s"] / per_clk <= 1.05 * 128
+    assert 0.5 * 128 <= c["ffma2_lane_ops_per_s"] / per_clk <= 1.05 * 128
+    assert 0.25 <= c["red_shared_per_s"] / per_clk <= 1.05
