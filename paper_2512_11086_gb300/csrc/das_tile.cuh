@@ -663,7 +663,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
                 constexpr int jj = decltype(jjc)::value;
                 constexpr int OFF = jj * WS * C::PAIR_BYTES;
                 const float phw = IQ ? s_wph[pb * C::NWIN + ii * C::CJ + jj] : 0.0f;
-                const float ws0 = D2 ? s_ws0[pb * C::NWIN + ii * C::CJ + jj] : 0.0f;
+                [[maybe_unused]] const float ws0 = D2 ? s_ws0[pb * C::NWIN + ii * C::CJ + jj] : 0.0f;
                 // e^{j 2 pi (phw + r u)} applied to (vr, vi)
                 auto iq_rotate = [&](float uu, float& vr, float& vi) {
                     const float x = fmaf(iqr, uu, phw);

@@ -344,7 +344,7 @@ int configure_decode(PlanHost& h) {
     if (h.p.hadamard_order == 0 || h.p.decode_variant == RCBF_DECODE_PLAIN) return RCBF_OK;
     const int n = (int)h.p.n_tx;
     const bool f16 = h.p.decode_variant == RCBF_DECODE_MMA_F16;
-    switch (h.p.decoded_dtype == RCBF_CF32 ? RCBF_F32 : h.p.decoded_dtype) {
+    switch (h.p.decoded_dtype == RCBF_CF32 ? (uint32_t)RCBF_F32 : h.p.decoded_dtype) {
         case RCBF_I32: return f16 ? configure_dt<RCBF_I32, true>(n, &h.decode_blocks_per_sm)
                                   : configure_dt<RCBF_I32, false>(n, &h.decode_blocks_per_sm);
         case RCBF_F32: return f16 ? configure_dt<RCBF_F32, true>(n, &h.decode_blocks_per_sm)
