@@ -237,8 +237,9 @@ void setup_geometry(PlanHost& h) {
     if (p.tx_wave == RCBF_TX_VLS) {
         // off the line's axis the virtual-line-source delay jumps by 2 |lat - e|
         // at the focal depth (converging above, diverging below), so tile
-        // windows from the 1-Lipschitz radius bound hold only when no voxel
-        // lies at that depth: a focal plane inside the image runs the plain form
+        // windows from the 1-Lipschitz radius bound hold only for tiles that do
+        // not reach that depth: with a focal plane inside the image the tiles
+        // across it run the plain form, the others the tiled form
         double zmin = 1e300, zmax = -1e300;
         for (int c = 0; c < 8; ++c) {
             const double ix = (c & 1) ? (double)(p.out_dims[0] - 1) : 0.0;
@@ -248,7 +249,7 @@ void setup_geometry(PlanHost& h) {
             zmin = std::fmin(zmin, z);
             zmax = std::fmax(zmax, z);
         }
-        h.force_plain = p.tx_focus >= zmin && p.tx_focus <= zmax;
+        h.vls_split = p.tx_focus >= zmin && p.tx_focus <= zmax;
     }
     const bool h2d = p.acq_kind == RCBF_HERCULES_2D;
     if (h2d) {
@@ -546,7 +547,7 @@ int rcbf_plan_query(rcbf_plan_t plan, rcbf_plan_info* info) {
     info->workspace_bytes = bytes;
     int mode = 0;
     DasArgs b = a;
-    if (h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok) {
+    if (h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok && !h.vls_split) {
         if (h.bwd_bv > 0 && das_prepare_tile(h, h.p.c, 32, h.bwd_bv, h.bwd_bw, h.bwd_r_alpha_m, h.bwd_r_beta_m, &b,
                                              &why) == RCBF_OK)
             mode = 2;
@@ -612,7 +613,13 @@ int rcbf_das(rcbf_plan_t plan, const void* decoded, const float* apod, float c, 
     a.apod = apod;
     a.image = image;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    return tiled && fits ? launch_das(h, a, s) : launch_das_plain(h, a, s);
+    if (!(tiled && fits)) return launch_das_plain(h, a, s);
+    if (!h.vls_split) return launch_das(h, a, s);
+    // VLS focal plane inside the image: the tiled form for every tile but
+    // those across the focal depth, then the plain form for exactly those
+    a.vls_split = 1;
+    const int rc = launch_das(h, a, s);
+    return rc != RCBF_OK ? rc : launch_das_plain(h, a, s);
 }
 
 int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, float c,
@@ -633,8 +640,9 @@ int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, 
     std::string why;
     // the adjoint's own tile (lanes over z) where its window fits at this
     // speed of sound, else the plan's tile, else the plain form
+    // (a VLS focal plane inside the image: the plain form throughout)
     int mode = 0;
-    if (h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok) {
+    if (h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok && !h.vls_split) {
         if (h.bwd_bv > 0 && das_prepare_tile(h, cc, 32, h.bwd_bv, h.bwd_bw, h.bwd_r_alpha_m, h.bwd_r_beta_m, &a,
                                              &why) == RCBF_OK)
             mode = 2;

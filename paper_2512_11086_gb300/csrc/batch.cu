@@ -73,6 +73,9 @@ int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t
             return set_error(RCBF_EUNSUPPORTED, at + "batch frames are RF frames without demodulation");
         if (h.p.acq_kind == RCBF_HERCULES_2D)
             return set_error(RCBF_EUNSUPPORTED, at + "batch frames use separable (row-column) delays");
+        if (h.vls_split)
+            return set_error(RCBF_EUNSUPPORTED, at + "a virtual-line-source focal plane inside the image needs "
+                                                     "the plain form for the tiles across it");
         if (h.das.bu != bu) return set_error(RCBF_EINVAL, at + "all plans of a batch need the same tile extent along u");
         if (!decoded[f] || !images[f] || (h.p.hadamard_order && (!rf || !rf[f])))
             return set_error(RCBF_EINVAL, at + "NULL buffer");

@@ -163,6 +163,8 @@ das_plain_kernel(DasArgs a) {
     const int iu = (int)(vox % a.n_u);
     const int iv = (int)((vox / a.n_u) % a.n_v);
     const int iw = (int)(vox / ((long long)a.n_u * a.n_v));
+    // split VLS image: only the voxels of tiles across the focal depth
+    if (a.vls_split && !tile_across_focus(a, iu / a.bu, iv / a.bv, iw / a.bw)) return;
     float q[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d)
@@ -333,9 +335,7 @@ int das_prepare_tile(const PlanHost& h, double c, int bu, int bv, int bw, double
         return RCBF_EUNSUPPORTED;
     }
     if (h.force_plain) {
-        if (why) *why = h.p.acq_kind == RCBF_HERCULES_2D
-                            ? "das: a 2D receive aperture with an F# window or a tile wider than 32 voxels runs the plain form"
-                            : "das: the virtual-line-source focal depth lies inside the image (delays jump there)";
+        if (why) *why = "das: a 2D receive aperture with an F# window or a tile wider than 32 voxels runs the plain form";
         return RCBF_EUNSUPPORTED;
     }
     if (a->interp == RCBF_CUBIC && a->dtype == RCBF_CF32 && a->W > 64) {

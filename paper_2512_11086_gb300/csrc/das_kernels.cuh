@@ -14,6 +14,14 @@ __global__ void __launch_bounds__(kDasThreads, 2)
 das_tiled_kernel(DasArgs a) {
     using C = DasCfg<VU, WS, CPLX, CUBIC, D2, APOD>;
     extern __shared__ __align__(128) unsigned char smem[];
+    if (a.vls_split) {
+        // a tile across a virtual-line-source focal depth is left to the
+        // plain kernel (uniform over the CTA: nothing set up yet)
+        const int n_tiles = a.tiles_u * a.tiles_v * a.tiles_w;
+        const int tile = (int)(blockIdx.x % (unsigned)n_tiles);
+        if (tile_across_focus(a, tile % a.tiles_u, (tile / a.tiles_u) % a.tiles_v, tile / (a.tiles_u * a.tiles_v)))
+            return;
+    }
     das_pipe_init<C::COPIES>(smem + C::OFF_BAR, reinterpret_cast<volatile int*>(smem + C::OFF_ABORT));
     DasPipe pipe{0u};   // stage counter of this CTA
     if (!das_unit<VU, WS, CPLX, APOD, CUBIC, IQ, D2>(a, blockIdx.x, smem, pipe) && threadIdx.x == 0)

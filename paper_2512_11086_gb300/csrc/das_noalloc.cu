@@ -109,5 +109,8 @@ extern "C" int rcbf_das_noalloc(const rcbf_params* params, const void* decoded, 
         return check_launch("rcbf_das_noalloc: clear status");
     if (!tiled) return launch_das_plain(h, a, s);
     h.d_partial = scratch + kNoAllocHeaderFloats;
-    return launch_das(h, a, s);
+    if (!h.vls_split) return launch_das(h, a, s);
+    a.vls_split = 1;                 // tiles across a VLS focal depth: the plain form
+    rc = launch_das(h, a, s);
+    return rc != RCBF_OK ? rc : launch_das_plain(h, a, s);
 }

@@ -47,6 +47,8 @@ struct DasArgs {
     const float2* tx_dir;  // plane waves: (sin a_i, cos a_i) per transmit (device)
     int tx_wave;           // rcbf_tx_wave
     int acq_kind;          // rcbf_acq_kind (RCBF_HERCULES_2D: non-separable receive)
+    int vls_split;         // 1: the tiled kernel skips tiles across the VLS focal depth and the plain
+                           // kernel computes only their voxels (tile_across_focus)
     float f_number;
     int interp;            // rcbf_interp
     int W;                 // pairs per window actually used (<= compiled stride)
@@ -109,7 +111,8 @@ struct PlanHost {
     float2* d_tx_dir;       // device plane-wave directions (tx_wave == RCBF_TX_PLANE)
     bool has_tx_angle0;     // tx_angle0 holds the first plane-wave angle (the params' pointer is not kept)
     double tx_angle0;
-    bool force_plain;       // the geometry admits no tile windows (a VLS focal plane inside the image)
+    bool force_plain;       // the geometry admits no tile windows (2D aperture forms the tiled form lacks)
+    bool vls_split;         // a VLS focal plane inside the image: tiles across it run the plain form
     // adjoint tile with lanes over z: 32 voxels along u by bwd_bv x bwd_bw
     // rows (bwd_bv = 0: no such tile keeps the window within 128 samples)
     int bwd_bv, bwd_bw;
@@ -189,9 +192,9 @@ __device__ __forceinline__ double tx_ref_distance(const DasArgs& a, int e, doubl
 __device__ __forceinline__ float tx_offset(int wave, float4 tx, float dL, float dZ, float Zf, float Zfoc, float fsc) {
     if (wave == RCBF_TX_PLANE) return tx.z + fmaf(dZ, tx.y, dL * tx.x) * fsc;
     if (wave == RCBF_TX_VLS) {
-        // tiles never straddle the focal depth (such images run the plain
-        // form), so the voxel is on the reference's side: the same
-        // cancellation-free difference, signed like the reference
+        // the tiled form never sees a tile across the focal depth (the plain
+        // kernel computes those), so the voxel is on the reference's side:
+        // the same cancellation-free difference, signed like the reference
         const float Lv = tx.x + dL, Zv = Zfoc + dZ;
         const float dv = sqrtf(Lv * Lv + Zv * Zv);
         const float num = dL * (2.0f * tx.x + dL) + dZ * (2.0f * Zfoc + dZ);
@@ -206,6 +209,17 @@ __device__ __forceinline__ float tx_offset(int wave, float4 tx, float dL, float 
 }
 
 // FP32 transmit path of transmit i to (lat_tx, z) (the plain forms).
+// Whether voxel tile (tu, tv, tw) reaches the virtual-line-source focal depth
+// (its bounding box in z contains tx_focus, boundary included): off axis the
+// VLS delay jumps there, so such a tile has no sample window and runs the
+// plain form. The tiled and the plain kernels evaluate the same expression.
+__device__ __forceinline__ bool tile_across_focus(const DasArgs& a, int tu, int tv, int tw) {
+    const double cu = tu * a.bu + 0.5 * (a.bu - 1), cv = tv * a.bv + 0.5 * (a.bv - 1), cw = tw * a.bw + 0.5 * (a.bw - 1);
+    const double zc = a.q0[2] + a.Gu[2] * cu + a.Gv[2] * cv + a.Gw[2] * cw;
+    const double hz = 0.5 * (fabs(a.Gu[2]) * (a.bu - 1) + fabs(a.Gv[2]) * (a.bv - 1) + fabs(a.Gw[2]) * (a.bw - 1));
+    return fabs(a.tx_focus - zc) <= hz + 1e-9;
+}
+
 __device__ __forceinline__ float tx_distance_f32(const DasArgs& a, int i, float lat_tx, float z) {
     if (a.tx_wave == RCBF_TX_PLANE) {
         const float2 sc = a.tx_dir[i];

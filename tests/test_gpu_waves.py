@@ -1,8 +1,9 @@
 """Plane-wave (TPW) and virtual-line-source (VLS) transmits on the GPU
 against the FP64 oracle: tiled and plain DAS (linear and cubic, real and
 complex with an F# window), the adjoint, and a batch of plane-wave frames; the
-VLS focus inside the image (the transmit delay changes sign of curvature
-within tiles), above it, and behind the array (a diverging wave)."""
+VLS focus inside the image (tiles across the focal depth run the plain form,
+the others the tiled one, with and without a channel split), above it, and
+behind the array (a diverging wave)."""
 import numpy as np
 import pytest
 
@@ -65,9 +66,9 @@ def test_transmit_wave_das_matches_oracle(wave, kw, variant, interp):
     print("%s %s v%d %s: tiled %s window %d rel-L2 %.3e" % (wave, kw, variant, interp, info["tiled"],
                                                              info["window"], err))
     # a virtual-line-source focus inside the image (8 mm) makes the transmit
-    # delay jump at the focal depth off axis: the library runs the plain form
-    focus_inside = wave == "vls" and g.out_min[2] <= kw["tx_focus"] <= g.out_max[2]
-    assert info["tiled"] == (variant == rc.DAS_TILED and not focus_inside)
+    # delay jump at the focal depth off axis: the tiles across it run the
+    # plain form, every other tile the tiled form
+    assert info["tiled"] == (variant == rc.DAS_TILED)
     assert err <= TOL
     # the image of the wave's own data focuses: its peak is within a few voxels of a scatterer
     pk = np.unravel_index(np.argmax(np.abs(got)), got.shape)
@@ -121,3 +122,34 @@ def test_batch_of_plane_wave_frames():
     want = oracle.das(g, h, voxels=vox)
     for k in range(2):
         assert rel_l2(img[k].cpu().numpy().ravel()[vox], want) <= TOL
+
+
+@pytest.mark.parametrize("focus_mm,dtype", [(8.0, "f32"), (11.0, "f16"), (3.0, "f32"), (18.0, "f32")])
+def test_vls_focal_plane_split_full_image(focus_mm, dtype):
+    # the focal depth inside the image, on a tile row boundary or at the
+    # image's top and bottom rows; FP16 storage; the split works for any
+    # channel split of the plan
+    g = _geom("vls", n_tx=32, tx_focus=focus_mm * MM)
+    g.n_ch = 64
+    fr = synth.make_frame(g, seed=46, n_scatterers=6, box_x=(-2.5 * MM, 2.5 * MM), box_z=(4 * MM, 17 * MM),
+                          noise_frac=0.0)
+    data = fr.decoded.astype(np.float16).astype(np.float64) if dtype == "f16" else fr.decoded.astype(np.float64)
+    want = oracle.das(g, data)
+    plan = rc.Plan(rc.make_params(g, decoded_dtype=dtype))
+    assert plan.info()["tiled"]
+    dec = torch.from_numpy(data.astype(np.float16 if dtype == "f16" else np.float32)).cuda()
+    got = plan.das(dec).cpu().numpy().astype(np.float64)
+    err = rel_l2(got, want)
+    print("VLS focus %.1f mm %s: split %d, rel-L2 %.3e" % (focus_mm, dtype, plan.info()["n_split"], err))
+    assert err <= TOL
+
+
+def test_batch_rejects_a_vls_focal_plane_inside_the_image():
+    g = _geom("vls", n_tx=32, hadamard_order=32, tx_focus=8 * MM)
+    plan = rc.Plan(rc.make_params(g, decoded_dtype="f16"))
+    rf = [torch.zeros(32, 32, 1024, dtype=torch.int16, device="cuda")]
+    dec = [torch.empty(32, 32, 1024, dtype=torch.float16, device="cuda")]
+    img = [torch.empty(plan.image_shape, device="cuda")]
+    with pytest.raises(rc.RcbfError) as e:
+        rc.Batch([plan], rf, dec, img)
+    assert e.value.code == rc.EUNSUPPORTED
