@@ -110,8 +110,9 @@ enum rcbf_tx_wave {
     RCBF_TX_PLANE = 1,  /* plane wave i: d_tx = z cos(a_i) + lat_tx sin(a_i) (crosses the array at t = 0) */
     RCBF_TX_VLS   = 2,  /* virtual line source above line i at depth f:
                            d_tx = f + sgn(z - f) sqrt((lat_tx - e_i)^2 + (z - f)^2), sgn(0) = +1.
-                           Off axis the delay jumps at z = f, so an image whose depth range
-                           contains f runs the plain DAS form. */
+                           Off axis the delay jumps at z = f: the voxel tiles whose depth
+                           range reaches f run the plain DAS form, all others the tiled one
+                           (rcbf_das_backward runs the plain form for such an image). */
     RCBF_TX_POINT = 3   /* RCBF_HERCULES_2D only: diverging wave from a virtual point at depth f < 0 on the
                            array axis: d_tx = sqrt(x^2 + y^2 + (z - f)^2) + f */
 };
