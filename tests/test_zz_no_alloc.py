@@ -76,3 +76,21 @@ def test_noalloc_2d_aperture_diverging_wave():
     want = plan.das(d).cpu().numpy()
     np.testing.assert_array_equal(got, want)
     assert rel_l2(got, oracle.das(g, fr.decoded.astype(np.float64))) <= 1e-4
+
+
+def test_noalloc_vls_focal_plane_inside_the_image():
+    # the split form (tiled tiles plus the plain pass over the tiles across
+    # the focal depth) from the parameter block alone, equal to the plan's
+    g = synth.Geometry(n_tx=32, n_ch=64, n_samples=1024, out_dims=(128, 1, 320),
+                       out_min=(-3e-3, 0.0, 3e-3), out_max=(3e-3, 0.0, 18e-3))
+    g.tx_wave, g.tx_focus = "vls", 9e-3
+    fr = synth.make_frame(g, seed=59, n_scatterers=5, box_x=(-2.5e-3, 2.5e-3), box_z=(4e-3, 17e-3),
+                          noise_frac=0.0)
+    params = rc.make_params(g, decoded_dtype="f32")
+    plan = rc.Plan(rc.make_params(g, decoded_dtype="f32"))
+    assert plan.info()["tiled"]
+    d = torch.from_numpy(fr.decoded.astype(np.float32)).cuda()
+    out = torch.empty(plan.image_shape, dtype=torch.float32, device="cuda")
+    got = _noalloc(params, d, out)
+    np.testing.assert_array_equal(got, plan.das(d).cpu().numpy())
+    assert rel_l2(got, oracle.das(g, fr.decoded.astype(np.float64))) <= 1e-4
