@@ -75,7 +75,8 @@ extern "C" {
 #define RCBF_EUNSUPPORTED  -2  /* dtype / mode / size combination not built */
 #define RCBF_ECUDA         -3  /* CUDA runtime or launch error (message in rcbf_last_error) */
 #define RCBF_ENOMEM        -4  /* device allocation failed */
-#define RCBF_ETIMEOUT      -5  /* a bounded device-side wait expired (batch only) */
+#define RCBF_ETIMEOUT      -5  /* a bounded device-side wait expired (rcbf_plan_status, rcbf_batch_status,
+                                  rcbf_pipeline_wait, rcbf_das_noalloc_status) */
 
 /* ---- enumerations -------------------------------------------------------- */
 enum rcbf_dtype {
@@ -191,8 +192,9 @@ typedef struct rcbf_params {
     double   tx_focus;          /* RCBF_TX_VLS: depth f of the virtual line sources [m] */
     const double* tx_angles;    /* RCBF_TX_PLANE: HOST pointer to n_tx steering angles [rad], |angle| < pi/2,
                                    copied by rcbf_plan */
-    /* Receive channels as a slice of a larger array (a channel-sharded frame: each GPU
-     * beamforms its slice and the partial images add, §8(e)-style one reduce-sum):
+    /* Receive channels as a slice of a larger array (a channel-sharded frame: Eq. (1) is a
+     * sum over channels, so each GPU beamforms its slice and one reduce-sum adds the
+     * partial images):
      * channel j of this plan is element rx_channel_offset + j of rx_channels_total.
      * 0 / 0 = the plan's channels are the whole array. */
     uint32_t rx_channel_offset;
@@ -282,6 +284,12 @@ int rcbf_decode(rcbf_plan_t plan, const int16_t* rf, void* decoded, void* stream
  * f_number > 0 the tiled form skips, per voxel tile, every chunk of 8
  * channels whose window W is zero at all of the tile's voxels (the test of
  * Eq. (2)-(3) on the tile's bounding box; the result is unchanged).
+ * Status: the tiled form's waits on its staged windows are bounded (one second
+ * by default, see rcbf_plan_set_wait); a wait that expires stops its voxel
+ * tile, leaving that part of the image unwritten, and records RCBF_ETIMEOUT in
+ * the plan's status word, which every rcbf_das and rcbf_das_backward call
+ * clears when it starts (one 4-byte memset on `stream`) and rcbf_plan_status
+ * reads. Calls on one plan in different streams share that word.
  * Errors: RCBF_EINVAL, RCBF_EUNSUPPORTED, RCBF_ECUDA. */
 int rcbf_das(rcbf_plan_t plan, const void* decoded, const float* apod, float c,
              float* image, void* stream);
@@ -306,11 +314,31 @@ int rcbf_das(rcbf_plan_t plan, const void* decoded, const float* apod, float c,
  * between runs. A 16-byte aligned grad_rf takes four-float reductions; any
  * 4-byte aligned one is accepted. rcbf_plan_query reports the tile used.
  * Built for RF data with linear interpolation: IQ or cubic plans return
- * RCBF_EUNSUPPORTED.
+ * RCBF_EUNSUPPORTED. Bounded waits and the status word as for rcbf_das: an
+ * expired wait leaves the gradients incomplete and rcbf_plan_status returns
+ * RCBF_ETIMEOUT.
  * Errors: RCBF_EINVAL, RCBF_EUNSUPPORTED (dtype), RCBF_ECUDA. */
 int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, float c,
                       const float* grad_image, float* grad_rf, float* grad_c,
                       float* grad_apod, void* stream);
+
+/* rcbf_plan_status — synchronise `stream` and return the status of the last
+ * rcbf_das or rcbf_das_backward call on the plan: RCBF_OK, or RCBF_ETIMEOUT
+ * when one of its bounded device-side waits expired (its output is then
+ * incomplete). The word is cleared by the next call, not by this one.
+ * Errors: RCBF_EINVAL (NULL plan), RCBF_ECUDA. */
+int rcbf_plan_status(rcbf_plan_t plan, void* stream);
+
+/* rcbf_plan_set_wait — bound of every device-side wait of the plan's tiled
+ * DAS and adjoint kernels (default one second; at most ten), and a test hook
+ * for failure detection: withhold = 1 makes every voxel tile of the tiled
+ * rcbf_das omit the request of its first window copy, so that the tile's
+ * first wait runs out, the kernel stops that tile and returns, and
+ * rcbf_plan_status reports RCBF_ETIMEOUT while the context stays usable;
+ * withhold = 0 restores normal operation. Batches created from the plan are
+ * not affected. Host only.
+ * Errors: RCBF_EINVAL (NULL plan, wait_ns == 0, withhold not 0 or 1). */
+int rcbf_plan_set_wait(rcbf_plan_t plan, uint64_t wait_ns, int32_t withhold);
 
 /* rcbf_batch_create — bind n_frames (plan, buffers) triples into one batch
  * that a single persistent kernel processes: for every frame with a
@@ -403,10 +431,22 @@ void rcbf_pipeline_destroy(rcbf_pipeline_t pipeline);
  * The first call on a device looks up that device's address of the array;
  * make it before any stream capture. All calls share the one array: calls
  * whose work overlaps on the GPU (other streams, other host threads) race on
- * it, so serialise them. Errors: as rcbf_plan and rcbf_das, and RCBF_EINVAL
- * when the partial images would exceed the 16 MiB array. */
+ * it, so serialise them. A bounded wait of the tiled kernel that expires is
+ * reported by rcbf_das_noalloc_status. Errors: as rcbf_plan and rcbf_das
+ * (RCBF_EUNSUPPORTED for a tiled form the geometry does not admit, and for
+ * plane waves, whose direction table needs a plan), and RCBF_EINVAL when the
+ * partial images would exceed the 16 MiB array. */
 int rcbf_das_noalloc(const rcbf_params* params, const void* decoded, const float* apod, float c,
                      float* image, void* stream);
+
+/* rcbf_das_noalloc_status — synchronise `stream` and return the status of the
+ * last rcbf_das_noalloc call on the current device: RCBF_OK, or RCBF_ETIMEOUT
+ * when a bounded wait of its tiled DAS expired (the image is then
+ * incomplete). The status word lives in the same static array as the scratch,
+ * so it is cleared by the next rcbf_das_noalloc call on the device and shared
+ * by every caller on it. Allocates nothing.
+ * Errors: RCBF_ECUDA. */
+int rcbf_das_noalloc_status(void* stream);
 
 /* rcbf_measure_ceilings — on-chip ceilings of the current device, measured
  * by microbenchmark kernels run at the tiled DAS kernel's occupancy (two CTAs

@@ -105,6 +105,9 @@ SIGNATURES = {
     "rcbf_batch_set_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int32]),
     "rcbf_batch_destroy": (None, [_P]),
     "rcbf_das_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _P, _P, ctypes.c_float, _P, _P]),
+    "rcbf_das_noalloc_status": (ctypes.c_int, [_P]),
+    "rcbf_plan_status": (ctypes.c_int, [_P, _P]),
+    "rcbf_plan_set_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int32]),
     "rcbf_measure_ceilings": (ctypes.c_int, [ctypes.POINTER(Ceilings), _P]),
     "rcbf_last_error": (ctypes.c_char_p, []),
     "rcbf_version": (ctypes.c_char_p, []),
@@ -249,6 +252,16 @@ class Plan:
                 "n_split": pi.n_split, "das_launches": pi.das_launches,
                 "decode_launches": pi.decode_launches, "workspace_bytes": pi.workspace_bytes,
                 "bwd_tile": tuple(pi.bwd_tile), "bwd_mode": pi.bwd_mode}
+
+    def status(self, stream=None) -> int:
+        """rcbf_plan_status: synchronise the stream and return OK or ETIMEOUT
+        for the last das / das_backward call (no exception)."""
+        return int(load_library().rcbf_plan_status(self.handle, _stream(stream)))
+
+    def set_wait(self, wait_ns: int, withhold: int = 0):
+        """rcbf_plan_set_wait: bound of the tiled kernels' waits; withhold = 1
+        is the test hook that makes every tiled DAS unit's first wait expire."""
+        _check(load_library().rcbf_plan_set_wait(self.handle, int(wait_ns), int(withhold)))
 
     def decoded_torch_dtype(self):
         import torch

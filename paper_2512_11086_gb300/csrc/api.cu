@@ -234,23 +234,6 @@ void setup_geometry(PlanHost& h) {
     for (int ax = 0; ax < 2 && ua < 0; ++ax) if (tx_invariant(ax) && p.out_dims[ax] > 1) ua = ax;
     for (int ax = 0; ax < 2 && ua < 0; ++ax) if (tx_invariant(ax)) ua = ax;
     h.tiled_ok = ua >= 0 && p.n_ch % kCJ == 0 && p.n_tx % (p.decoded_dtype == RCBF_CF32 ? 4 : kCI) == 0;
-    if (p.tx_wave == RCBF_TX_VLS) {
-        // off the line's axis the virtual-line-source delay jumps by 2 |lat - e|
-        // at the focal depth (converging above, diverging below), so tile
-        // windows from the 1-Lipschitz radius bound hold only for tiles that do
-        // not reach that depth: with a focal plane inside the image the tiles
-        // across it run the plain form, the others the tiled form
-        double zmin = 1e300, zmax = -1e300;
-        for (int c = 0; c < 8; ++c) {
-            const double ix = (c & 1) ? (double)(p.out_dims[0] - 1) : 0.0;
-            const double iy = (c & 2) ? (double)(p.out_dims[1] - 1) : 0.0;
-            const double iz = (c & 4) ? (double)(p.out_dims[2] - 1) : 0.0;
-            const double z = G[8] * ix + G[9] * iy + G[10] * iz + G[11];
-            zmin = std::fmin(zmin, z);
-            zmax = std::fmax(zmax, z);
-        }
-        h.vls_split = p.tx_focus >= zmin && p.tx_focus <= zmax;
-    }
     const bool h2d = p.acq_kind == RCBF_HERCULES_2D;
     if (h2d) {
         // the tiled 2D form takes no F# window (its weight is radial, per
@@ -299,6 +282,8 @@ void setup_geometry(PlanHost& h) {
     a.scale = p.decoded_dtype == RCBF_I32 ? 1.0f / (float)p.n_tx : 1.0f;
     a.plane_stride = (long long)p.n_tx * p.n_ch * p.n_samples;
     a.image_plane = (long long)p.out_dims[0] * p.out_dims[1] * p.out_dims[2];
+    a.wait_ns = kWaitNs;
+    a.withhold = 0;
 
     // ---- DAS tile: given, or the shape with the smallest window at the plan's c
     auto radius_sum = [&](int bu, int bv, int bw) {
@@ -413,6 +398,32 @@ void setup_geometry(PlanHost& h) {
         }
     }
 
+    if (p.tx_wave == RCBF_TX_VLS) {
+        // off the line's axis the virtual-line-source delay jumps by 2 |lat - e|
+        // at the focal depth (converging above, diverging below), so tile
+        // windows from the 1-Lipschitz radius bound hold only for tiles whose
+        // whole box (ragged tiles included: the reference sits at the centre
+        // of the full tile) lies on one side of it. The test is the kernels'
+        // own (tile_across_focus), over every tile of the forward and of the
+        // adjoint tiling.
+        auto any_across = [&](int bu, int bv, int bw) {
+            if (bv <= 0) return false;
+            const long long tu_n = (a.n_u + bu - 1) / bu, tv_n = (a.n_v + bv - 1) / bv, tw_n = (a.n_w + bw - 1) / bw;
+            const double hz = 0.5 * (std::fabs(a.Gu[2]) * (bu - 1) + std::fabs(a.Gv[2]) * (bv - 1) +
+                                     std::fabs(a.Gw[2]) * (bw - 1));
+            for (long long tw = 0; tw < tw_n; ++tw)
+                for (long long tv = 0; tv < tv_n; ++tv)
+                    for (long long tu = 0; tu < tu_n; ++tu) {
+                        const double cu = tu * bu + 0.5 * (bu - 1), cv = tv * bv + 0.5 * (bv - 1),
+                                     cw = tw * bw + 0.5 * (bw - 1);
+                        const double zc = a.q0[2] + a.Gu[2] * cu + a.Gv[2] * cv + a.Gw[2] * cw;
+                        if (std::fabs(p.tx_focus - zc) <= hz + 1e-9) return true;
+                    }
+            return false;
+        };
+        h.vls_split = any_across(a.bu, a.bv, a.bw);
+        h.vls_split_bwd = any_across(32, h.bwd_bv, h.bwd_bw);
+    }
 }
 
 }  // namespace
@@ -547,11 +558,11 @@ int rcbf_plan_query(rcbf_plan_t plan, rcbf_plan_info* info) {
     info->workspace_bytes = bytes;
     int mode = 0;
     DasArgs b = a;
-    if (h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok && !h.vls_split) {
-        if (h.bwd_bv > 0 && das_prepare_tile(h, h.p.c, 32, h.bwd_bv, h.bwd_bw, h.bwd_r_alpha_m, h.bwd_r_beta_m, &b,
-                                             &why) == RCBF_OK)
+    if (h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok) {
+        if (!h.vls_split_bwd && h.bwd_bv > 0 &&
+            das_prepare_tile(h, h.p.c, 32, h.bwd_bv, h.bwd_bw, h.bwd_r_alpha_m, h.bwd_r_beta_m, &b, &why) == RCBF_OK)
             mode = 2;
-        else if (fits)
+        else if (!h.vls_split && fits)
             mode = 1;
     }
     info->bwd_mode = (uint32_t)mode;
@@ -613,6 +624,8 @@ int rcbf_das(rcbf_plan_t plan, const void* decoded, const float* apod, float c, 
     a.apod = apod;
     a.image = image;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the status word reports this call (rcbf_plan_status)
+    if (cudaMemsetAsync(h.d_status, 0, sizeof(int), s) != cudaSuccess) return check_launch("rcbf_das: clear status");
     if (!(tiled && fits)) return launch_das_plain(h, a, s);
     if (!h.vls_split) return launch_das(h, a, s);
     // VLS focal plane inside the image: the tiled form for every tile but
@@ -642,11 +655,11 @@ int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, 
     // speed of sound, else the plan's tile, else the plain form
     // (a VLS focal plane inside the image: the plain form throughout)
     int mode = 0;
-    if (h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok && !h.vls_split) {
-        if (h.bwd_bv > 0 && das_prepare_tile(h, cc, 32, h.bwd_bv, h.bwd_bw, h.bwd_r_alpha_m, h.bwd_r_beta_m, &a,
-                                             &why) == RCBF_OK)
+    if (h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok) {
+        if (!h.vls_split_bwd && h.bwd_bv > 0 &&
+            das_prepare_tile(h, cc, 32, h.bwd_bv, h.bwd_bw, h.bwd_r_alpha_m, h.bwd_r_beta_m, &a, &why) == RCBF_OK)
             mode = 2;
-        else if (das_prepare(h, cc, &a, &why) == RCBF_OK)
+        else if (!h.vls_split && das_prepare(h, cc, &a, &why) == RCBF_OK)
             mode = 1;
     }
     if (mode == 0) das_prepare(h, cc, &a, &why);
@@ -658,6 +671,8 @@ int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, 
     a.grad_apod = grad_apod;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int planes = h.p.decoded_dtype == RCBF_CF32 ? 2 : 1;
+    if (cudaMemsetAsync(h.d_status, 0, sizeof(int), s) != cudaSuccess)
+        return check_launch("rcbf_das_backward: clear status");
     if (grad_rf && cudaMemsetAsync(grad_rf, 0, (size_t)a.plane_stride * planes * sizeof(float), s) != cudaSuccess)
         return check_launch("rcbf_das_backward: clear grad_rf");
     if (grad_c && cudaMemsetAsync(grad_c, 0, sizeof(float), s) != cudaSuccess)
@@ -667,5 +682,25 @@ int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, 
     return launch_das_backward(h, a, mode, s);
 }
 
+int rcbf_plan_status(rcbf_plan_t plan, void* stream) {
+    if (!plan) return set_error(RCBF_EINVAL, "rcbf_plan_status: plan is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return check_launch("rcbf_plan_status: synchronize");
+    int st = 0;
+    if (cudaMemcpy(&st, plan->h.d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return check_launch("rcbf_plan_status: read status");
+    if (st) return set_error(RCBF_ETIMEOUT, "rcbf_plan_status: a bounded device wait of the last rcbf_das / "
+                                            "rcbf_das_backward call expired; its output is incomplete");
+    return RCBF_OK;
+}
+
+int rcbf_plan_set_wait(rcbf_plan_t plan, uint64_t wait_ns, int32_t withhold) {
+    if (!plan) return set_error(RCBF_EINVAL, "rcbf_plan_set_wait: plan is NULL");
+    if (wait_ns == 0 || (withhold != 0 && withhold != 1))
+        return set_error(RCBF_EINVAL, "rcbf_plan_set_wait: wait_ns must be > 0 and withhold 0 or 1");
+    plan->h.das.wait_ns = (long long)std::min<uint64_t>(wait_ns, (uint64_t)10000000000ULL);
+    plan->h.das.withhold = withhold;
+    return RCBF_OK;
+}
 
 }  // extern "C"

@@ -91,6 +91,8 @@ int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t
         fr.das.apod = nullptr;
         fr.das.n_split = 1;
         fr.das.partial = nullptr;
+        fr.das.withhold = 0;            // the plan's DAS test hook does not apply to a batch
+        fr.das.wait_ns = kWaitNs;
         ws = std::max(ws, class_of(fr.das.W));
         fr.out_dtype = (int)h.p.decoded_dtype;
         fr.order = (int)h.p.n_tx;

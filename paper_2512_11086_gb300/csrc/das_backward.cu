@@ -383,7 +383,7 @@ das_bwd_kernel(DasArgs a) {
             // wholly inside or wholly outside its trace).
             const int t = s - 1, tb = t & 1;
             const int ic = t % n_ic, jc = jc0 + t / n_ic;
-            ok = mbar_wait_parity(bar0 + 8 * tb, (phase >> tb) & 1u) && ok;
+            ok = mbar_wait_parity(bar0 + 8 * tb, (phase >> tb) & 1u, a.wait_ns) && ok;
             phase ^= 1u << tb;
             const int* acc = gwin + (t % 3) * C::ACC_BUF;
             if (ic == 0) {
@@ -472,8 +472,8 @@ das_bwd_kernel(DasArgs a) {
         if (__syncthreads_or(!ok)) {
             // a bounded wait expired: give the copies still in flight (stages
             // s and, if its wait failed, s-1) a bounded chance to land, then stop
-            if (s < NS) mbar_wait_parity(bar0 + 8 * (s & 1), (phase >> (s & 1)) & 1u);
-            if (s > 0) mbar_wait_parity(bar0 + 8 * ((s - 1) & 1), ((phase >> ((s - 1) & 1)) & 1u) ^ 1u);
+            if (s < NS) mbar_wait_parity(bar0 + 8 * (s & 1), (phase >> (s & 1)) & 1u, a.wait_ns);
+            if (s > 0) mbar_wait_parity(bar0 + 8 * ((s - 1) & 1), ((phase >> ((s - 1) & 1)) & 1u) ^ 1u, a.wait_ns);
             if (tid == 0) atomicOr(a.status, kStatusWaitExpired);
             return;
         }

@@ -73,6 +73,9 @@ extern "C" int rcbf_das_noalloc(const rcbf_params* params, const void* decoded, 
     h.p.demod_taps = nullptr;
     h.p.tx_angles = nullptr;
     plan_geometry(h);
+    if (h.p.das_variant == RCBF_DAS_TILED && !h.tiled_ok)
+        return set_error(RCBF_EUNSUPPORTED, "rcbf_das_noalloc: the tiled form needs n_ch % 8 == 0, n_tx % 8 == 0 "
+                                            "(4 for complex) and an image axis parallel to the transmit elements");
     int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&h.n_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -82,7 +85,7 @@ extern "C" int rcbf_das_noalloc(const rcbf_params* params, const void* decoded, 
     DasArgs a;
     std::string why;
     const bool fits = das_prepare(h, cc, &a, &why) == RCBF_OK;
-    const bool tiled = h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok && fits;
+    const bool tiled = h.p.das_variant == RCBF_DAS_TILED && fits;
     if (tiled) {
         if ((rc = configure_das(h)) != RCBF_OK) return rc;
         const int split = std::max(1, h.n_split[das_class_index(a.W, h.p.acq_kind == RCBF_HERCULES_2D)]);
@@ -113,4 +116,18 @@ extern "C" int rcbf_das_noalloc(const rcbf_params* params, const void* decoded, 
     a.vls_split = 1;                 // tiles across a VLS focal depth: the plain form
     rc = launch_das(h, a, s);
     return rc != RCBF_OK ? rc : launch_das_plain(h, a, s);
+}
+
+extern "C" int rcbf_das_noalloc_status(void* stream) {
+    float* scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc != RCBF_OK) return rc;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return check_launch("rcbf_das_noalloc_status: synchronize");
+    int st = 0;
+    if (cudaMemcpy(&st, scratch, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return check_launch("rcbf_das_noalloc_status: read status");
+    if (st) return set_error(RCBF_ETIMEOUT, "rcbf_das_noalloc_status: a bounded device wait of the last "
+                                            "rcbf_das_noalloc call on this device expired; its image is incomplete");
+    return RCBF_OK;
 }

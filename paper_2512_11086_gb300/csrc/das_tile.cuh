@@ -433,7 +433,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
 
     volatile int* abort = reinterpret_cast<volatile int*>(smem + C::OFF_ABORT);
     auto wait = [&](int slot, uint32_t phase) -> bool {
-        return mbar_wait_or_abort(bar0 + 8 * slot, phase & 1u, abort);
+        return mbar_wait_or_abort(bar0 + 8 * slot, phase & 1u, abort, a.wait_ns);
     };
     auto raw_phase = [&](int s) -> uint32_t { return (pipe.base + (uint32_t)s) >> 1; };
     auto piece_phase = [&](int s) -> uint32_t { return (pipe.base + (uint32_t)s) / 3u; };
@@ -447,6 +447,9 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     auto issue = [&](int s) -> bool {
         const int copy = (tid + kDasThreads - (s * C::COPIES) % kDasThreads) % kDasThreads;
         if (copy >= C::COPIES) return true;
+        // test hook (rcbf_plan_set_wait): the first copy of the unit is never
+        // requested, so the unit's first wait on its windows runs out
+        if (a.withhold && s == 0 && copy == 0) return true;
         const int b = raw_buf(s);
         if (!wait(kRawEmpty + b, raw_phase(s))) return false;
         const int win = CPLX ? (copy >> 1) : copy;
@@ -766,7 +769,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
         // a bounded wait expired somewhere in the CTA: give the copies this
         // thread still expects a bounded chance to land, then stop
         for (int k = landed + 1; k <= issued; ++k)
-            mbar_wait_parity(bar0 + 8 * (kRawFull + raw_buf(k)), raw_phase(k) & 1u);
+            mbar_wait_parity(bar0 + 8 * (kRawFull + raw_buf(k)), raw_phase(k) & 1u, a.wait_ns);
         return false;
     }
     pipe.base += (uint32_t)NS;

@@ -20,7 +20,7 @@ constexpr int kCI = 8;                // transmits per staged chunk
 constexpr int kCJ = 8;                // channels per staged chunk
 constexpr int kDecodeThreads = 256;
 constexpr int kDecodeCols = 128;      // columns (channel x sample) per decode tile
-constexpr long long kWaitCycles = 2000000000LL;   // bounded mbarrier waits: about one second of SM clock
+constexpr long long kWaitNs = 1000000000LL;   // default bound of a device-side mbarrier wait: one second
 
 // Status bits written by kernels into a plan's device status word.
 constexpr int kStatusWaitExpired = 1;
@@ -67,6 +67,10 @@ struct DasArgs {
     float* image;
     long long image_plane; // floats between image planes (complex)
     int* status;
+    long long wait_ns;     // bound of each mbarrier wait of the tiled forms (global-timer ns)
+    int withhold;          // test hook: 1 = every tiled DAS unit omits its first window copy, so
+                           // its first wait expires (rcbf_plan_set_wait); 0 in normal use
+    int reserved_w;
     // adjoint outputs (backward only)
     const float* grad_image;
     float* grad_rf;
@@ -112,7 +116,8 @@ struct PlanHost {
     bool has_tx_angle0;     // tx_angle0 holds the first plane-wave angle (the params' pointer is not kept)
     double tx_angle0;
     bool force_plain;       // the geometry admits no tile windows (2D aperture forms the tiled form lacks)
-    bool vls_split;         // a VLS focal plane inside the image: tiles across it run the plain form
+    bool vls_split;         // a VLS focal plane crosses a DAS tile: the tiles across it run the plain form
+    bool vls_split_bwd;     // a VLS focal plane crosses a tile of the adjoint's own tiling
     // adjoint tile with lanes over z: 32 voxels along u by bwd_bv x bwd_bw
     // rows (bwd_bv = 0: no such tile keeps the window within 128 samples)
     int bwd_bv, bwd_bw;
@@ -251,11 +256,20 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" :: "r"(bar) : "memory");
 }
 
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Bounded wait on an mbarrier phase that also gives up when another thread
 // of the CTA has raised the abort flag; raises it itself when its own time
-// budget (about a second) runs out. Returns false on abort.
-__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort) {
-    const long long t0 = clock64();
+// budget (limit_ns of global-timer time, counted from the first failed poll
+// so that a wait that succeeds at once reads no timer) runs out. Returns
+// false on abort.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort,
+                                                   long long limit_ns = kWaitNs) {
+    unsigned long long t0 = 0;
     for (uint32_t it = 0;; ++it) {
         uint32_t done;
         asm volatile(
@@ -266,17 +280,19 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity
         if (done) return true;
         if ((it & 15u) == 15u) {
             if (*abort) return false;
-            if (clock64() - t0 > kWaitCycles) break;
+            const unsigned long long now = globaltimer_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > (unsigned long long)limit_ns) break;
         }
     }
     *abort = 1;
     return false;
 }
 
-// Bounded wait on an mbarrier phase; returns false after about a second.
-__device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity) {
+// Bounded wait on an mbarrier phase; returns false after limit_ns.
+__device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity, long long limit_ns = kWaitNs) {
     volatile int never = 0;
-    return mbar_wait_or_abort(bar, parity, &never);
+    return mbar_wait_or_abort(bar, parity, &never, limit_ns);
 }
 
 // 1-D bulk copy global -> shared (TMA engine), completion on an mbarrier.

@@ -151,5 +151,26 @@ def test_null_arguments_rejected(lib):
     lib.rcbf_batch_destroy(None)
 
 
+def test_status_entry_points_reject_null(lib):
+    assert lib.rcbf_plan_status(None, None) == rc.EINVAL
+    assert lib.rcbf_plan_set_wait(None, 1000, 0) == rc.EINVAL
+
+
+def test_noalloc_rejects_what_rcbf_das_rejects_before_any_cuda_call(lib):
+    # the tiled form on a geometry that does not admit it (12 channels: not a
+    # multiple of the 8-channel chunk) is RCBF_EUNSUPPORTED for both entry
+    # points; the check runs on the host, so no device is needed here
+    p = _good_params()
+    p.n_ch = 12
+    fake = ctypes.c_void_p(1 << 20)          # never dereferenced: rejected first
+    assert lib.rcbf_das_noalloc(ctypes.byref(p), fake, None, ctypes.c_float(0), fake, None) == rc.EUNSUPPORTED
+    assert b"tiled form" in lib.rcbf_last_error()
+    p = _good_params()
+    p.tx_wave = rc.TX_PLANE
+    ang = (ctypes.c_double * p.n_tx)(*([0.0] * p.n_tx))
+    p.tx_angles = ctypes.cast(ang, ctypes.c_void_p)
+    assert lib.rcbf_das_noalloc(ctypes.byref(p), fake, None, ctypes.c_float(0), fake, None) == rc.EUNSUPPORTED
+
+
 def test_version_string(lib):
     assert b"rcbf" in lib.rcbf_version()

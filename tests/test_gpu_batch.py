@@ -137,3 +137,47 @@ def test_batch_rejects_mixed_tile_extents():
     with pytest.raises(rc.RcbfError) as e:
         rc.Batch([p1, p2], [rf, rf], d, im)
     assert e.value.code == rc.EINVAL
+
+
+def test_batch_at_the_benchmark_configuration():
+    # the launch the benchmark times: four full B-scans (128 tx x 128 ch x
+    # 4096 samples -> 512 x 1024) in one persistent launch replayed from a
+    # CUDA graph, split-byte int8 decode to FP16, tiled DAS with the tuned
+    # tile. Frames alternate in sign so that each slot has its own data.
+    from paper_2512_11086_gb300 import tune
+    from tests._frames import frame
+    fr = frame("bscan")
+    g = fr.geometry
+    tile = tune.tune_tile(g, "f16")
+    plan = rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=rc.DECODE_MMA_I8,
+                                  das_variant=rc.DAS_TILED, tile=tile))
+    B = 4
+    signs = [1 if k % 2 == 0 else -1 for k in range(B)]
+    rf = [torch.from_numpy(np.ascontiguousarray(s * fr.rf)).cuda() for s in signs]
+    dec = [torch.empty(g.n_tx, g.n_ch, g.n_samples, dtype=torch.float16, device="cuda") for _ in range(B)]
+    img = [torch.empty(g.out_dims[2], g.out_dims[1], g.out_dims[0], device="cuda") for _ in range(B)]
+    batch = rc.Batch([plan] * B, rf, dec, img)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        batch.run(stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.run()
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    assert batch.status() == rc.OK
+    D = oracle.decode(fr.rf)
+    want16 = oracle.decoded_as(D, g.n_tx, "f16")
+    vox = sample_voxels(g.out_dims, 1500, seed=9)
+    want = oracle.das(g, want16.astype(np.float64), voxels=vox)
+    for k, sg in enumerate(signs):
+        # FP16 rounding to nearest-even is odd-symmetric: decode(-S) = -decode(S)
+        np.testing.assert_array_equal(dec[k].cpu().numpy().view(np.uint16), (sg * want16).view(np.uint16))
+        got = img[k].cpu().numpy().ravel()[vox]
+        err = rel_l2(got, sg * want)
+        print("benchmark batch slot %d (tile %s): rel-L2 %.2e" % (k, tile, err))
+        assert err <= 1e-4

@@ -125,7 +125,9 @@ def test_full_bscan_plain_form_sampled():
     vox = sample_voxels(g.out_dims, 1500, seed=3)
     want = oracle.das(g, exact, voxels=vox)
     got = _gpu_image(g, exact.astype(np.float32), variant=rc.DAS_PLAIN).ravel()[vox]
-    _report("bscan plain FP32", got, want)
+    # the plain FP32 form is the baseline the tuned form is measured against:
+    # it is held to the same bound
+    assert _report("bscan plain FP32", got, want) <= TOL
 
 
 def test_volume_sampled_voxels():

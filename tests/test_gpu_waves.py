@@ -153,3 +153,40 @@ def test_batch_rejects_a_vls_focal_plane_inside_the_image():
     with pytest.raises(rc.RcbfError) as e:
         rc.Batch([plan], rf, dec, img)
     assert e.value.code == rc.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("variant", ["das", "adjoint"])
+def test_vls_focus_inside_a_ragged_last_tile(variant):
+    # 291 depth rows with 16-row tiles: the last tile holds 3 real rows (17.4 to
+    # 17.5 mm) and its reference sits at its centre (17.775 mm). A focal depth
+    # of 17.6 mm lies below every real voxel but inside that tile's box, so the
+    # real voxels and the tile's reference are on opposite sides of the focus:
+    # that tile must run the plain form (its tiled windows would take the
+    # transmit delay with the reference's sign)
+    g = synth.Geometry(n_tx=16, n_ch=32, n_samples=1024, out_dims=(128, 1, 291),
+                       out_min=(-3 * MM, 0.0, 3 * MM), out_max=(3 * MM, 0.0, 17.5 * MM))
+    g.tx_wave, g.tx_focus = "vls", 17.6 * MM
+    fr = synth.make_frame(g, seed=48, n_scatterers=6, box_x=(-2.5 * MM, 2.5 * MM), box_z=(15 * MM, 17.5 * MM),
+                          noise_frac=0.0)
+    data = fr.decoded.astype(np.float64)
+    plan = rc.Plan(rc.make_params(g, decoded_dtype="f32", tile=(64, 1, 16)))
+    assert plan.info()["tiled"]
+    dec = torch.from_numpy(data.astype(np.float32)).cuda()
+    if variant == "das":
+        want = oracle.das(g, data)
+        got = plan.das(dec).cpu().numpy().astype(np.float64)
+        tail = rel_l2(got[-3:], want[-3:])
+        err = rel_l2(got, want)
+        print("VLS focus in the ragged last tile: rel-L2 %.3e (last 3 rows %.3e)" % (err, tail))
+        assert err <= TOL and tail <= TOL
+    else:
+        # the autofocus loss gradient G = dL/dI = -2 I; every adjoint tile that
+        # reaches the focal depth keeps the adjoint off its tiled forms
+        G = -2.0 * oracle.das(g, data)
+        gr, gc, gw = plan.das_backward(dec, torch.from_numpy(G.astype(np.float32)).cuda())
+        wr, wc, ww = oracle.das_grad(g, data, G)
+        err = rel_l2(gr.cpu().numpy(), wr)
+        print("VLS focus in the ragged last tile, adjoint: dR rel-L2 %.3e, dc %.6e vs %.6e" % (err, gc.item(), wc))
+        assert err <= 1e-4
+        assert abs(gc.item() - wc) <= 1e-2 * abs(wc)     # FP32 delays of the plain form
+        assert rel_l2(gw.cpu().numpy(), ww) <= 1e-4

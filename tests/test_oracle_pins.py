@@ -2,6 +2,7 @@
 itself: textbook Hadamard values and identities, hand-computed times of
 flight, closed forms of the DAS sum for constant and ramp data, symmetry,
 exact linearity, brute force, and the adjoint identity. CPU only."""
+import dataclasses
 import math
 import os
 
@@ -478,3 +479,119 @@ def test_complex_gradient_planes():
     np.testing.assert_allclose(grc.imag, gr_im, atol=1e-12)
     assert gcc == pytest.approx(gc_re + gc_im, rel=1e-12)
     np.testing.assert_allclose(gwc, gw_re + gw_im, rtol=1e-12)
+
+
+# ------------------------------------- world -> array and voxel affines
+
+CORNER = [[1.0, 0.0, 0.0, -1.0 * MM], [0.0, 1.0, 0.0, -1.0 * MM], [0.0, 0.0, 1.0, 0.0], [0.0, 0.0, 0.0, 1.0]]
+
+
+def test_corner_element_origin_hand_computed_delays():
+    # §METHODS "Data Processing": the world frame has its origin at the centre
+    # of the corner element; for 3 x 3 elements of 1 mm pitch the world ->
+    # array affine is a translation by (-1, -1, 0) mm. The ramp sits in one
+    # trace (i, j), so the image is that trace's delay; the inverse
+    # translation, or a transform applied array -> world, gives other values.
+    for i, j, x, y, z, expect in _golden_rows("corner_origin_tof.txt"):
+        g = Geometry(n_tx=3, n_ch=3, n_samples=1000, fs=10e6, c=1500.0, t0=0.0,
+                     tx_pitch=1 * MM, rx_pitch=1 * MM, tx_orientation=ROWS, rx_orientation=COLUMNS,
+                     out_dims=(1, 1, 1), out_min=(x * MM, y * MM, z * MM), out_max=(x * MM, y * MM, z * MM))
+        r = np.zeros((3, 3, g.n_samples))
+        r[int(i), int(j)] = np.arange(g.n_samples)
+        got = oracle.das(g, r, xdc_transform=CORNER).ravel()[0]
+        assert got == pytest.approx(expect, rel=0, abs=1e-9)
+        # without the transform the same world point is read in the centred
+        # frame: a different delay
+        assert abs(oracle.das(g, r).ravel()[0] - expect) > 1.0
+
+
+def _ray_affine(axis):
+    # index axis `axis` onto (3, 0, 4) mm * (k + 1): row-major, index -> world
+    M = np.zeros((4, 4))
+    M[0, axis], M[0, 3] = 3 * MM, 3 * MM
+    M[2, axis], M[2, 3] = 4 * MM, 4 * MM
+    M[3, 3] = 1.0
+    return M
+
+
+def test_voxel_affine_hand_computed_delays():
+    # Fig. "das_dispatch": a 4x4 voxel-index affine. Each index axis in turn
+    # walks the ray (3, 0, 4) mm (k + 1), where the delay is 60 (k + 1)
+    # samples; reading the matrix column-major (its transpose) or mapping the
+    # wrong index axis moves every voxel off the ray.
+    rows = _golden_rows("voxel_affine_tof.txt")
+    for axis in (0, 2):
+        dims = [1, 1, 1]
+        dims[axis] = 3
+        g = Geometry(n_tx=1, n_ch=1, n_samples=1000, fs=10e6, c=1500.0, t0=0.0,
+                     tx_orientation=ROWS, rx_orientation=COLUMNS, out_dims=tuple(dims),
+                     out_min=(0.0, 0.0, 0.0), out_max=(0.0, 0.0, 0.0))
+        ramp = np.arange(g.n_samples, dtype=np.float64).reshape(1, 1, -1)
+        got = oracle.das(g, ramp, voxel_transform=_ray_affine(axis)).ravel()
+        want = [e for a, k, e in rows if int(a) == axis]
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-9)
+        got_t = oracle.das(g, ramp, voxel_transform=_ray_affine(axis).T).ravel()
+        assert np.abs(got_t - want).max() > 1.0
+
+
+def test_voxel_affine_permuting_index_axes_matches_the_linspace_grid():
+    # an affine that sends index axis 0 to world z and index axis 2 to world
+    # x, on a grid whose x and z extents are swapped, reads the same world
+    # points as the inclusive linspace grid, transposed (voxel (ix, 0, iz) of
+    # the affine grid is voxel (iz, 0, ix) of the linspace grid)
+    rng = np.random.default_rng(21)
+    lin = Geometry(n_tx=4, n_ch=4, n_samples=256, fs=30e6, c=1540.0, out_dims=(5, 1, 7),
+                   out_min=(-1 * MM, 0.0, 2 * MM), out_max=(1 * MM, 0.0, 4 * MM), f_number=0.8)
+    r = rng.normal(size=(4, 4, 256))
+    want = oracle.das(lin, r)                      # [nz=7][1][nx=5]
+    M = np.zeros((4, 4))
+    M[2, 0] = (4 - 2) * MM / 6                     # index axis 0 (7 points) -> z
+    M[2, 3] = 2 * MM
+    M[0, 2] = (1 - -1) * MM / 4                    # index axis 2 (5 points) -> x
+    M[0, 3] = -1 * MM
+    M[3, 3] = 1.0
+    perm = dataclasses.replace(lin, out_dims=(7, 1, 5))
+    got = oracle.das(perm, r, voxel_transform=M)   # [nz=5][1][nx=7]
+    np.testing.assert_allclose(got[:, 0, :], want[:, 0, :].T, rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------- radial F# window of the 2D aperture
+
+def test_hercules_2d_window_is_radial():
+    # Eq. (2)-(3) on the 2D receive aperture: the voxel (3, 4, 12) mm lies at
+    # radial lateral distance 5 mm from the element (row y = 0, column x = 0).
+    # F# = 0.6: u = 0.6 * 5 / 12 = 1/4, W = cos^2(pi / 4) = 1/2 exactly
+    # (a window on the x offset alone gives cos^2(0.15 pi) = 0.794, on y
+    # alone cos^2(0.2 pi) = 0.655). F# = 1.2: u = 1/2, the support edge, W = 0.
+    g = _point_geom(3 * MM, 4 * MM, 12 * MM)
+    g.acq_kind = synth.HERCULES_2D
+    g.tx_wave, g.tx_angles = "plane", (0.0,)
+    one = np.ones((1, 1, g.n_samples))
+    g.f_number = 0.6
+    assert oracle.das(g, one).ravel()[0] == pytest.approx(0.5, abs=1e-12)
+    g.f_number = 1.2
+    assert oracle.das(g, one).ravel()[0] == 0.0
+    g.f_number = 1.19                              # just inside the support
+    u = 1.19 * 5 / 12
+    assert oracle.das(g, one).ravel()[0] == pytest.approx(math.cos(math.pi * u) ** 2, abs=1e-12)
+
+
+# ------------------------------------- IQ at a fractional delay
+
+def test_iq_beamforming_at_a_quarter_sample_delay():
+    # s = 60 + 1/4 (the 3-4-5 geometry with t0 = -0.025 us), f_d / f_s = 1/4,
+    # baseband samples b[n] = j^n (a linear phase of pi/2 per sample).
+    # Linear: (3/4) b[60] + (1/4) b[61] = 3/4 + j/4. Cubic (weights -9, 111,
+    # 29, -3 over 128 on samples 59..62): (9j + 111 + 29j + 3)/128 =
+    # (114 + 38j)/128. Both are then rotated by e^{j 2 pi s / 4} =
+    # e^{j 30.125 pi} = e^{j pi / 8}; a phase taken at floor(s) would rotate
+    # by e^{j 30 pi} = 1 instead.
+    g = _point_geom(3 * MM, 0.0, 4 * MM, t0=-0.025e-6)
+    g.iq_freq = 2.5e6
+    n = np.arange(g.n_samples)
+    b = (1j ** (n % 4)).reshape(1, 1, -1)
+    rot = complex(math.cos(math.pi / 8), math.sin(math.pi / 8))
+    got = oracle.das(g, b, interp="linear").ravel()[0]
+    assert abs(got - (0.75 + 0.25j) * rot) <= 1e-12
+    got = oracle.das(g, b, interp="cubic").ravel()[0]
+    assert abs(got - (114 + 38j) / 128 * rot) <= 1e-12

@@ -56,6 +56,27 @@ def test_noalloc_matches_planned_das_on_two_calls(name):
         err = rel_l2(got, want)
         print("%s c=%g: rel-L2 vs rcbf_das %.2e" % (name, c, err))
         assert err <= 1e-4
+        assert rc.load_library().rcbf_das_noalloc_status(
+            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == rc.OK
+
+
+def test_noalloc_call_allocates_no_device_memory():
+    # after one call (which looks up the device address of the static scratch),
+    # a further call changes neither torch's allocator nor the device's free
+    # memory: the entry point itself allocates nothing
+    fr = frame("bscan")
+    g = fr.geometry
+    params = rc.make_params(g, decoded_dtype="f16")
+    dec = torch.from_numpy((oracle.decode(fr.rf).astype(np.float64) / g.n_tx).astype(np.float16)).cuda()
+    out = torch.empty(g.out_dims[2], g.out_dims[1], g.out_dims[0], dtype=torch.float32, device="cuda")
+    first = _noalloc(params, dec, out).copy()
+    torch.cuda.synchronize()
+    alloc0, free0 = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
+    second = _noalloc(params, dec, out)
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.cuda.mem_get_info()[0] == free0
+    np.testing.assert_array_equal(second, first)
 
 
 def test_noalloc_2d_aperture_diverging_wave():
