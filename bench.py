@@ -144,15 +144,22 @@ def _dist():
     return rank, ws, local
 
 
-def cpu_baseline(frame, target_s: float = 15.0):
-    """The FP64 oracle as it stands, on a bounded sample of the frame: the
-    decode of a slice of columns and the DAS of a random voxel subset, both
-    the same fraction phi of the frame, sized to about target_s seconds.
+def cpu_baseline(frame, target_s: float = 15.0, gpu_image=None, gpu_decoded=None):
+    """The CPU leg: the FP64 oracle as it stands, timed on a bounded sample of
+    the frame (the decode of a slice of columns and the DAS of a random voxel
+    subset, both the same fraction phi of the frame, sized to about target_s
+    seconds), and, outside its timing, the parity stamp of the GPU's output:
+    the decoded frame compared bit for bit with the oracle's decode, and the
+    image at the sampled voxels against the oracle's DAS of the same
+    FP16-rounded decoded data (the DAS input of the tuned form), plus the
+    FP16 storage error against the exact decode on up to 2048 voxels.
     Returns (Gsums/s, details)."""
     import oracle
     g = frame.geometry
     cores = oracle.threads()
-    exact = _exact_decoded(frame)          # inputs of the DAS sample (not timed)
+    D = _exact_int(frame)                  # inputs of the DAS sample (not timed)
+    data16 = oracle.decoded_as(D, g.n_tx, "f16")
+    r16 = data16.astype(np.float64)
     rng = np.random.default_rng(0)
     flat = frame.rf.reshape(g.n_tx, -1)
     nv = 256
@@ -161,27 +168,58 @@ def cpu_baseline(frame, target_s: float = 15.0):
         ncol = max(8, int(round(nv / g.n_vox * flat.shape[1])))
         t0 = time.perf_counter()
         oracle.decode(flat[:, :ncol])
-        oracle.das(g, exact, voxels=vox)
+        want = oracle.das(g, r16, voxels=vox)
         t = time.perf_counter() - t0
         if t >= 0.5 * target_s or nv >= g.n_vox:
             break
         nv = min(g.n_vox, int(nv * max(2.0, target_s / max(t, 1e-3))))
     value = nv * g.n_tx * g.n_ch / t / 1e9
-    return value, {"cores": cores, "seconds": t,
-                   "sample": "%d of %d voxels (%.4f of the frame) plus the same fraction of the decode "
-                             "columns: %.1f s of oracle time" % (nv, g.n_vox, nv / g.n_vox, t)}
+    det = {"cores": cores, "seconds": t,
+           "sample": "%d of %d voxels (%.4f of the frame) plus the same fraction of the decode "
+                     "columns: %.1f s of oracle time" % (nv, g.n_vox, nv / g.n_vox, t)}
+    if gpu_image is not None:
+        got = np.asarray(gpu_image, dtype=np.float64).ravel()[vox]
+        sub = vox[:: max(1, vox.size // 2048)]
+        exact = oracle.das(g, D.astype(np.float64) / g.n_tx, voxels=sub)
+        det["parity"] = {
+            "das_rel_l2": rel_l2(got, want), "das_max_abs": float(np.max(np.abs(got - want))),
+            "peak": float(np.max(np.abs(want))), "voxels": int(vox.size), "tol": 1e-4,
+            "reference": "FP64 oracle DAS of the FP16-rounded exact decode (the DAS input of the timed form)",
+            "fp16_storage_rel_l2": rel_l2(np.asarray(gpu_image, dtype=np.float64).ravel()[sub], exact),
+            "decode_bit_exact": None if gpu_decoded is None else
+            bool(np.array_equal(np.asarray(gpu_decoded).view(np.uint16), data16.view(np.uint16))),
+        }
+    return value, det
+
+
+def rel_l2(got, want) -> float:
+    got = np.asarray(got)
+    want = np.asarray(want)
+    return float(np.linalg.norm((got - want).ravel()) / max(np.linalg.norm(want.ravel()), 1e-300))
 
 
 _EXACT = {}
 
 
-def _exact_decoded(frame):
+def _exact_int(frame):
+    """The oracle's exact integer decode of the frame (cached)."""
     key = id(frame)
     if key not in _EXACT:
         import oracle
-        D = oracle.decode(frame.rf)
-        _EXACT[key] = D.astype(np.float64) / frame.geometry.n_tx
+        _EXACT[key] = oracle.decode(frame.rf)
     return _EXACT[key]
+
+
+def _exact_decoded(frame):
+    return _exact_int(frame).astype(np.float64) / frame.geometry.n_tx
+
+
+def headline_config(B: int, ws: int) -> dict:
+    """The `config` of the headline line, shared by both arms."""
+    return {"workload": WORKLOAD, "frames_per_step": B, "global_batch": B * ws,
+            "l2": "inputs larger than L2: %d frames of 128 MB int16 RF + 128 MB FP16 decoded per step "
+                  "(129 MB L2)" % B,
+            "parallelism": "independent frames per GPU" if ws > 1 else "1 GPU"}
 
 
 def run_reference(args):
@@ -205,7 +243,7 @@ def run_reference(args):
     else:
         exact = frame.decoded.astype(np.complex128 if np.iscomplexobj(frame.decoded) else np.float64)
     rng = np.random.default_rng(1)
-    nv = min(2048, g.n_vox)                    # voxels per step (a bounded sample)
+    nv = min(32768, g.n_vox)                   # voxels per step (a bounded sample, ~0.3 s of oracle time)
     phi = nv / g.n_vox
     ncol = int(round(phi * g.n_ch * g.n_samples))
     times = []
@@ -222,14 +260,16 @@ def run_reference(args):
     value = nv * g.n_tx * g.n_ch / per / 1e9
     sample = "%d random voxels (%.5f of the frame)%s per step" % (
         nv, phi, " and the same fraction of decode columns" if frame.rf is not None else " (complex, two planes)")
+    if workload == "bscan":
+        config = headline_config(max(1, args.batch), ws)
+    else:
+        config = {"workload": "FORCES tiny B-scan: 32 tx (H32) x 32 ch x 1024 int16 samples -> 128x128 FP32 image"
+                  if workload == "tiny" else OTHER_WORKLOADS[workload]}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if workload == "bscan" else
-                   "FORCES tiny B-scan: 32 tx (H32) x 32 ch x 1024 int16 samples -> 128x128 FP32 image"
-                   if workload == "tiny" else OTHER_WORKLOADS[workload],
-                   "sample": sample},
+        "config": config,
         "frames_per_s": value * 1e9 / g.sums,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -250,56 +290,202 @@ OTHER_WORKLOADS = {
 }
 
 
-def run_other_workload(args):
-    """The volume, stream and autofocus configurations, timed like the
-    headline (CUDA events, warm-up, clocks) but reported on their own line."""
+def _alu_peak_tops(sms: int) -> float:
+    """FP32 lane-operations per second of the whole GPU at the maximum SM clock (T)."""
+    return sms * 128 * _peaks()["sm_max_mhz"] * 1e6 / 1e12
+
+
+def _time_steps(step, steps: int, warmup: int, stream):
+    """Warm-up, then CUDA-event time of `steps` calls of step() on `stream`,
+    with the clocks sampled during the timed region. Returns (ms/step, clocks)."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = _events(2)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, clocks.stop()
+
+
+def _graph_of(batch):
+    """A CUDA graph of one batch run (warm-up launch outside the capture)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        batch.run(stream=side)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.run()
+    return graph
+
+
+def measure_batched(name: str, args, parity: bool = True) -> dict:
+    """The HERCULES volume (4 volumes per step) or the 64-frame stream: one
+    persistent launch per step replayed from a CUDA graph, split-byte int8
+    decode to FP16 and tiled DAS, tiles from the autotuner. Parity stamp
+    (outside the timed region): decode bit-exact and sampled voxels against
+    the FP64 oracle of the same FP16 decoded data, for the first frame of
+    every frame class."""
     import torch
     import paper_2512_11086_gb300 as rc
-    from paper_2512_11086_gb300 import build as rbuild, tune
+    from paper_2512_11086_gb300 import tune
+    import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    out = {}
+    if name == "volume":
+        fr = synth.hercules_volume(3)
+        frames = [fr] * max(1, args.batch)
+        tiles = [tune.tune_tile(fr.geometry, "f16")] * len(frames)
+    else:
+        cache = {}
+        frames = []
+        for g, seed, box in synth.stream_geometries():
+            key = (g.n_tx, g.n_samples, g.out_dims, g.tx_orientation)
+            if key not in cache:                      # one synthetic content per frame class
+                cache[key] = synth.make_frame(g, seed, 16, **box)
+            frames.append(cache[key])
+        tiles = tune.tune_stream([f.geometry for f in frames], "f16")
+        out["content"] = "frames of one class share synthetic content (distinct buffers)"
+    plans, rf, dec, img = [], [], [], []
+    for fr, t in zip(frames, tiles):
+        g = fr.geometry
+        plans.append(rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=rc.DECODE_MMA_I8, tile=t)))
+        rf.append(torch.from_numpy(fr.rf).to(dev))
+        dec.append(torch.empty(g.n_tx, g.n_ch, g.n_samples, dtype=torch.float16, device=dev))
+        img.append(torch.empty(g.out_dims[2], g.out_dims[1], g.out_dims[0], device=dev))
+    batch = rc.Batch(plans, rf, dec, img)
+    graph = _graph_of(batch)
+    ms, clk = _time_steps(graph.replay, args.steps, args.warmup, stream)
+    if batch.status() != rc.OK:
+        raise RuntimeError("%s: batch status %d" % (name, batch.status()))
+    sums = sum(f.geometry.sums for f in frames)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    achieved = 5 * sums / (ms * 1e-3) / 1e12
+    out.update({"workload": OTHER_WORKLOADS[name], "value": sums / (ms * 1e-3) / 1e9, "unit": UNIT,
+                "ms_per_step": ms, "frames_per_step": len(frames),
+                ("volumes_per_s" if name == "volume" else "frames_per_s"): len(frames) * 1e3 / ms,
+                "tiles": sorted({tuple(t) for t in tiles}),
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": _alu_peak_tops(sms), "unit": "TOP/s",
+                             "frac": achieved / _alu_peak_tops(sms), "kernel": "batch_kernel",
+                             "ops_per_sum": 5, "traffic": None},
+                "clocks": clk})
+    if parity:
+        import oracle
+        checked, worst, exact_all = 0, 0.0, True
+        seen = set()
+        for k, fr in enumerate(frames):
+            if id(fr) in seen:
+                continue
+            seen.add(id(fr))
+            g = fr.geometry
+            want16 = oracle.decoded_as(oracle.decode(fr.rf), g.n_tx, "f16")
+            exact_all &= bool(np.array_equal(dec[k].cpu().numpy().view(np.uint16), want16.view(np.uint16)))
+            vox = np.sort(np.random.default_rng(k).choice(g.n_vox, size=min(512, g.n_vox), replace=False))
+            got = img[k].cpu().numpy().astype(np.float64).ravel()[vox]
+            worst = max(worst, rel_l2(got, oracle.das(g, want16.astype(np.float64), voxels=vox)))
+            checked += 1
+        out["parity"] = {"decode_bit_exact": exact_all, "das_rel_l2_max": worst, "tol": 1e-4,
+                         "frames_checked": checked, "voxels_per_frame": 512,
+                         "reference": "FP64 oracle: decode, then DAS of the FP16-rounded decode"}
+    return out
+
+
+def measure_autofocus(args, parity: bool = True) -> dict:
+    """Speed-of-sound autofocus step: complex forward DAS and its adjoint
+    (dRF, dc, dw) for L = -sum |I|^2. Parity stamp: the forward at sampled
+    voxels and dL/dc, dL/dw against the FP64 oracle (whose own image gives its
+    upstream gradient)."""
+    import torch
+    import paper_2512_11086_gb300 as rc
+    from paper_2512_11086_gb300 import tune
+    import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    fr = synth.autofocus(5)
+    g = fr.geometry
+    tile = tune.tune_tile(g, "cf32")
+    plan = rc.Plan(rc.make_params(g, decoded_dtype="cf32", tile=tile))
+    d = torch.from_numpy(np.stack([fr.decoded.real, fr.decoded.imag]).astype(np.float32)).to(dev)
+    w = torch.ones(g.n_ch, device=dev)
+    out = torch.empty((2,) + plan.image_shape, device=dev)
+    grad_rf = torch.empty_like(d)
+    res = {}
+
+    def forward():
+        plan.das(d, apod=w, c=1540.0, out=out)
+
+    # the adjoint is linear in its upstream gradient: the step passes G = I
+    # (no elementwise kernel between the two calls), and the gradients of
+    # L = -sum |I|^2 (G = -2 I) are -2 times its outputs
+    def step():
+        plan.das(d, apod=w, c=1540.0, out=out)
+        res["g"] = plan.das_backward(d, out, apod=w, c=1540.0, out_rf=grad_rf)
+
+    ms, clk = _time_steps(step, args.steps, args.warmup, stream)
+    fwd_ms, _ = _time_steps(forward, args.steps, 2, stream)
+    if plan.status() != rc.OK:
+        raise RuntimeError("autofocus: plan status %d" % plan.status())
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    achieved = 7 * g.sums / (fwd_ms * 1e-3) / 1e12
+    line = {"workload": OTHER_WORKLOADS["autofocus"], "value": g.sums / (ms * 1e-3) / 1e9, "unit": UNIT,
+            "ms_per_step": ms, "forward_ms": fwd_ms, "adjoint_ms": ms - fwd_ms,
+            "sums": "complex voxel x channel x transmit sums (two real planes each)",
+            "tile": list(tile), "adjoint_tile": list(plan.info()["bwd_tile"]),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": _alu_peak_tops(sms), "unit": "TOP/s",
+                         "frac": achieved / _alu_peak_tops(sms), "kernel": "das_tiled_kernel (forward, complex)",
+                         "ops_per_sum": 7, "traffic": None},
+            "clocks": clk}
+    if parity:
+        import oracle
+        step()
+        torch.cuda.synchronize()
+        im = out.cpu().numpy().astype(np.float64)
+        im = im[0] + 1j * im[1]
+        _, gc, gw = res["g"]
+        gc, gw = -2.0 * gc.item(), -2.0 * gw.cpu().numpy().astype(np.float64)
+        ref = fr.decoded.astype(np.complex128)
+        want_im = oracle.das(g, ref, c=1540.0)
+        _, want_c, want_w = oracle.das_grad(g, ref, -2.0 * want_im, c=1540.0, want_rf=False)
+        line["parity"] = {"das_rel_l2": rel_l2(im, want_im), "grad_c_rel": abs(gc - want_c) / abs(want_c),
+                          "grad_apod_rel_l2": rel_l2(gw, want_w), "tol": {"das": 1e-4, "grad": 1e-3},
+                          "reference": "FP64 oracle forward and gradients (L = -sum |I|^2) on the same complex RF"}
+    return line
+
+
+def run_other_workload(args):
+    """Another configuration on its own line, timed like the headline (CUDA
+    events, warm-up, clocks)."""
+    import torch
+    import paper_2512_11086_gb300 as rc
+    from paper_2512_11086_gb300 import build as rbuild
     import synth
     rbuild.build()
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
+    if args.workload in ("volume", "stream", "autofocus"):
+        rec = measure_autofocus(args) if args.workload == "autofocus" else measure_batched(args.workload, args)
+        value, ms, clk = rec.pop("value"), rec.pop("ms_per_step"), rec.pop("clocks")
+        rec.pop("unit")
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": rec.pop("workload")}, "clocks": clk}
+        line.update(rec)
+        print(json.dumps(line))
+        return
     extra = {}
-    if args.workload in ("volume", "stream"):
-        if args.workload == "volume":
-            fr = synth.hercules_volume(3)
-            frames = [fr] * max(1, args.batch)
-            tiles = [tune.tune_tile(fr.geometry, "f16")] * len(frames)
-            extra["frames_per_step"] = len(frames)
-        else:
-            geos = synth.stream_geometries()
-            cache = {}
-            frames = []
-            for g, seed, box in geos:
-                key = (g.n_tx, g.n_samples, g.out_dims, g.tx_orientation)
-                if key not in cache:                      # one synthetic content per frame class
-                    cache[key] = synth.make_frame(g, seed, 16, **box)
-                frames.append(cache[key])
-            tiles = tune.tune_stream([f.geometry for f in frames], "f16")
-            extra["frames_per_step"] = len(frames)
-            extra["content"] = "frames of one class share synthetic content (distinct buffers)"
-        plans, rf, dec, img = [], [], [], []
-        for fr, t in zip(frames, tiles):
-            g = fr.geometry
-            plans.append(rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=rc.DECODE_MMA_I8, tile=t)))
-            rf.append(torch.from_numpy(fr.rf).to(dev))
-            dec.append(torch.empty(g.n_tx, g.n_ch, g.n_samples, dtype=torch.float16, device=dev))
-            img.append(torch.empty(g.out_dims[2], g.out_dims[1], g.out_dims[0], device=dev))
-        batch = rc.Batch(plans, rf, dec, img)
-        side = torch.cuda.Stream()
-        side.wait_stream(stream)
-        with torch.cuda.stream(side):
-            batch.run(stream=side)
-        stream.wait_stream(side)
-        torch.cuda.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            batch.run()
-        step = graph.replay
-        sums = sum(f.geometry.sums for f in frames)
-        extra["tiles"] = sorted({tuple(t) for t in tiles})
-    elif args.workload == "hercules2d":
+    if args.workload == "hercules2d":
         g = dataclasses.replace(synth.hercules_volume_geometry(), acq_kind=synth.HERCULES_2D, hadamard_order=0,
                                 tx_wave="plane", tx_angles=(0.0,))
         plan = rc.Plan(rc.make_params(g, decoded_dtype="f16"))
@@ -312,7 +498,7 @@ def run_other_workload(args):
         sums = g.sums
         extra["plan"] = plan.info()
         extra["data"] = "seeded Gaussian decoded samples (timing only)"
-    elif args.workload == "iq":
+    else:
         fr = synth.full_bscan(2)
         g_raw = fr.geometry
         D, taps, shift = 4, synth.lowpass_taps(166, 0.12, shift=14), 14
@@ -346,40 +532,116 @@ def run_other_workload(args):
                              "iq_das_cubic": ev[2].elapsed_time(ev[3])}
         extra["sums"] = "complex voxel x channel x transmit sums of the IQ DAS"
         extra["plan"] = plan.info()
-    else:
-        fr = synth.autofocus(5)
-        g = fr.geometry
-        tile = tune.tune_tile(g, "cf32")
-        plan = rc.Plan(rc.make_params(g, decoded_dtype="cf32", tile=tile))
-        d = torch.from_numpy(np.stack([fr.decoded.real, fr.decoded.imag]).astype(np.float32)).to(dev)
-        w = torch.ones(g.n_ch, device=dev)
-        out = torch.empty((2,) + plan.image_shape, device=dev)
-
-        def step():
-            im = plan.das(d, apod=w, c=1540.0, out=out)
-            plan.das_backward(d, -2.0 * im, apod=w, c=1540.0)
-        sums = g.sums
-        extra["sums"] = "complex voxel x channel x transmit sums (two real planes each)"
-        extra["tiles"] = [list(tile)]
-        extra["adjoint_tile"] = list(plan.info()["bwd_tile"])
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    e0, e1 = _events(2)
-    clocks = ClockSampler(0)
-    clocks.start()
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms, clk = _time_steps(step, args.steps, args.warmup, stream)
     line = {"metric": METRIC, "value": sums / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict({"workload": OTHER_WORKLOADS[args.workload]}, **extra), "clocks": clk}
     print(json.dumps(line))
+
+
+def run_channel_shard(args):
+    """One B-scan per step split over the ranks by receive channel (Eq. (1) is
+    a sum over channels): rank r decodes and beamforms its contiguous slice
+    of channels with a plan over that slice of the array, and one NCCL
+    all-reduce sums the partial images (2 MB), the only exchange of the path.
+    Total work is fixed as N grows ("strong" scaling). At N = 1 it is the
+    unbatched decode + DAS of one frame."""
+    import torch
+    rank, ws, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2512_11086_gb300 import build as rbuild
+    if rank == 0:
+        rbuild.build()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    import paper_2512_11086_gb300 as rc
+    from paper_2512_11086_gb300 import shard, tune
+    import synth
+    frame = synth.full_bscan(seed=2)
+    g = frame.geometry
+    tile = tune.tune_tile(g, "f16")
+    off, cnt = shard.channel_slices(g.n_ch, ws)[rank]
+    plan = rc.Plan(shard.shard_params(g, rank, ws, decoded_dtype="f16", decode_variant=rc.DECODE_MMA_I8,
+                                      das_variant=rc.DAS_TILED, tile=tile))
+    host = torch.from_numpy(np.ascontiguousarray(frame.rf[:, off:off + cnt, :])).pin_memory()
+    rf = host.to(dev)
+    dec = torch.empty(g.n_tx, cnt, g.n_samples, dtype=torch.float16, device=dev)
+    img = torch.empty(plan.image_shape, dtype=torch.float32, device=dev)
+    img_host = torch.empty(plan.image_shape, dtype=torch.float32).pin_memory()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def step():
+        plan.decode(rf, out=dec)
+        plan.das(dec, out=img)
+        shard.reduce_image(img)
+
+    def e2e_step():
+        rf.copy_(host, non_blocking=True)
+        step()
+        if rank == 0:
+            img_host.copy_(img, non_blocking=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = _events(2)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    total_ms, _ = aggregate(e0.elapsed_time(e1), 0.0, device=dev)
+    ms = total_ms / args.steps
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    q0, q1 = _events(2)
+    q0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    q1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms, _ = aggregate(q0.elapsed_time(q1), 0.0, device=dev)
+    e2e_ms /= args.steps
+    if plan.status() != rc.OK:
+        raise RuntimeError("rank %d: plan status %d" % (rank, plan.status()))
+    line = {"metric": METRIC, "value": g.sums / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames_per_step": 1, "global_batch": 1,
+                       "parallelism": "receive channels split over %d GPU(s), partial images summed by one "
+                                      "all-reduce" % ws,
+                       "l2": "one 128 MB int16 frame per step (129 MB L2; decoded FP16 written and re-read)"},
+            "form": "per rank: split-byte int8 decode of its channel slice to FP16, tiled DAS of the slice, "
+                    "NCCL all-reduce of the partial image",
+            "tile": list(tile), "frames_per_s": 1e3 / ms,
+            "e2e": {"value": g.sums / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
+                    "h2d_bytes_per_step": int(frame.rf.nbytes), "d2h_bytes_per_step": int(img_host.numel() * 4),
+                    "ms_per_step": e2e_ms,
+                    "form": "each rank uploads its RF slice from pinned memory, rank 0 reads the image back"},
+            "gpu_launches": args.steps * (1 + plan.info()["das_launches"]),
+            "plan": plan.info(), "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 def _events(n):
@@ -394,7 +656,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--batch", type=int, default=4, help="frames per step (one persistent launch)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the CPU leg (the oracle's timing and the parity stamps)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the volume, stream and autofocus records of the default line")
+    ap.add_argument("--shard", default="frames", choices=["frames", "channels"],
+                    help="frames: each GPU beamforms its own frames (no collective); channels: one B-scan "
+                         "split over the GPUs by receive channel, partial images summed by one all-reduce")
     ap.add_argument("--workload", default="bscan", choices=["bscan", "tiny"] + sorted(OTHER_WORKLOADS),
                     help="bscan (the headline) or another configuration on its own line "
                          "(tiny: the 32-transmit B-scan, reference arm only)")
@@ -408,6 +676,9 @@ def main():
         return
     if args.workload != "bscan":
         run_other_workload(args)
+        return
+    if args.shard == "channels":
+        run_channel_shard(args)
         return
 
     import torch
@@ -486,6 +757,9 @@ def main():
     value = job_sums / (total_ms * 1e-3) / 1e9
     if batch.status() != rc.OK:
         raise RuntimeError("batch status %d after the timed steps" % batch.status())
+    # the last timed step's output, for the parity stamp of the CPU leg
+    last_image = imgs[B - 1].cpu().numpy()
+    last_decoded = dec16[B - 1].cpu().numpy()
 
     # ---- the same form unbatched: decode and DAS launched per frame
     ub_steps = max(3, min(args.steps, 10))
@@ -636,13 +910,10 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "frames_per_step": B, "global_batch": B * ws,
-                   "form": "batched persistent launch (CUDA graph): split-byte int8 mma.sync decode "
-                           "(exact) to FP16, tiled TMA-window DAS in FP32",
-                   "tile": list(tile),
-                   "l2": "inputs larger than L2: %d frames of %d MB int16 RF + %d MB FP16 decoded per step "
-                         "(129 MB L2)" % (B, rf_host.numel() * 2 >> 20, rf_host.numel() * 2 >> 20),
-                   "parallelism": "independent frames per GPU" if ws > 1 else "1 GPU"},
+        "config": headline_config(B, ws),
+        "form": "batched persistent launch (CUDA graph): split-byte int8 mma.sync decode (exact) to FP16, "
+                "tiled TMA-window DAS in FP32",
+        "tile": list(tile),
         "frames_per_s": B * ws * 1e3 / ms_step,
         "kernel_ms": {"batch_kernel_per_step": t_batch, "unbatched_decode": t_dec, "unbatched_das": t_das,
                       "decode_f16_mma_alternative": t_dec_f16},
@@ -691,10 +962,19 @@ def main():
         "plan": info,
         "clocks": clk,
     }
+    if rank == 0 and ws == 1 and not args.no_configs:
+        # the other configurations, each timed like the headline and stamped
+        # with its own parity check (outside its timed region)
+        line["configs"] = {
+            "volume": measure_batched("volume", args, parity=not args.no_cpu_baseline),
+            "stream": measure_batched("stream", args, parity=not args.no_cpu_baseline),
+            "autofocus": measure_autofocus(args, parity=not args.no_cpu_baseline),
+        }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        v, det = cpu_baseline(frame)
+        v, det = cpu_baseline(frame, gpu_image=last_image, gpu_decoded=last_decoded)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": det["cores"], "kind": "oracle",
                                 "sample": det["sample"]}
+        line["parity"] = det["parity"]
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:

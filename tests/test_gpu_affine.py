@@ -102,8 +102,8 @@ def test_axis_permuting_voxel_affine(variant):
 
 def test_rotated_array_runs_plain_form():
     # the array turned by 30 degrees about z: the transmit lateral coordinate
-    # changes along both image axes, so no lane axis exists and the library
-    # runs the plain form, still within the bound
+    # changes along both image axes, so no lane axis exists: the tiled form
+    # is refused (RCBF_EUNSUPPORTED) and the plain form holds the bound
     g = synth.Geometry(n_tx=16, n_ch=16, n_samples=768, out_dims=(24, 20, 48),
                        out_min=(-1 * MM, -1 * MM, 4 * MM), out_max=(1 * MM, 1 * MM, 8 * MM), f_number=0.7)
     a = math.radians(30.0)
@@ -112,7 +112,10 @@ def test_rotated_array_runs_plain_form():
     X[0, 3], X[1, 3] = 0.1 * MM, -0.2 * MM
     r = np.random.default_rng(43).normal(size=(16, 16, 768))
     want = oracle.das(g, r, xdc_transform=X)
-    got, info = _gpu(g, r, rc.DAS_TILED, xdc=X)
+    with pytest.raises(rc.RcbfError) as e:
+        _gpu(g, r, rc.DAS_TILED, xdc=X)
+    assert e.value.code == rc.EUNSUPPORTED
+    got, info = _gpu(g, r, rc.DAS_PLAIN, xdc=X)
     assert not info["tiled"]
     err = rel_l2(got, want)
     print("rotated array (plain form): rel-L2 %.3e" % err)
