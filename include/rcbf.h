@@ -126,8 +126,13 @@ enum rcbf_interp {
 enum rcbf_decode_variant {
     RCBF_DECODE_MMA_I8  = 0,  /* split-byte int8 tensor-core GEMM (mma.sync s8/u8), exact */
     RCBF_DECODE_PLAIN   = 1,  /* plain CUDA-core form: one thread per output, int32 sums */
-    RCBF_DECODE_MMA_F16 = 2   /* split-byte FP16 tensor-core GEMM (bytes and +-1 exact in
+    RCBF_DECODE_MMA_F16 = 2,  /* split-byte FP16 tensor-core GEMM (bytes and +-1 exact in
                                  FP16, FP32 accumulation exact below 2^24), exact */
+    RCBF_DECODE_TC      = 3   /* the split-byte FP16 GEMM on the 5th-generation tensor cores:
+                                 tcgen05.mma with accumulators in tensor memory, TMA tensor
+                                 loads of the int16 tiles and TMA stores of the output; exact;
+                                 n_tx in {32, 64, 128}. Inside a batch the frame is decoded by
+                                 the split-byte FP16 form of the persistent kernel. */
 };
 
 enum rcbf_das_variant {
@@ -260,8 +265,10 @@ int rcbf_demodulate(rcbf_plan_t plan, const int16_t* rf, int16_t* iq, void* stre
  *            RCBF_I32 = D exactly; RCBF_F32 = D / N exactly (|D| < 2^24 always
  *            holds for int16 input and N <= 256); RCBF_F16 = D / N rounded once.
  * Exact for every int16 input (integer arithmetic throughout).
- * n_samples must be a multiple of 8. Errors: RCBF_EINVAL (NULL, misaligned,
- * plan without Hadamard order), RCBF_EUNSUPPORTED (CF32 output), RCBF_ECUDA. */
+ * n_samples must be a multiple of 8. The RCBF_DECODE_TC form's waits are
+ * bounded like the tiled DAS's (rcbf_plan_set_wait) and an expiry is reported
+ * by rcbf_plan_status. Errors: RCBF_EINVAL (NULL, misaligned, plan without
+ * Hadamard order), RCBF_EUNSUPPORTED (CF32 output), RCBF_ECUDA. */
 int rcbf_decode(rcbf_plan_t plan, const int16_t* rf, void* decoded, void* stream);
 
 /* rcbf_das — delay-and-sum of Eq. (1) with a_tx = 1 and receive apodization
@@ -286,10 +293,8 @@ int rcbf_decode(rcbf_plan_t plan, const int16_t* rf, void* decoded, void* stream
  * Eq. (2)-(3) on the tile's bounding box; the result is unchanged).
  * Status: the tiled form's waits on its staged windows are bounded (one second
  * by default, see rcbf_plan_set_wait); a wait that expires stops its voxel
- * tile, leaving that part of the image unwritten, and records RCBF_ETIMEOUT in
- * the plan's status word, which every rcbf_das and rcbf_das_backward call
- * clears when it starts (one 4-byte memset on `stream`) and rcbf_plan_status
- * reads. Calls on one plan in different streams share that word.
+ * tile, leaving that part of the image unwritten, and records the expiry in
+ * the plan's status word, which rcbf_plan_status reads and clears.
  * Errors: RCBF_EINVAL, RCBF_EUNSUPPORTED, RCBF_ECUDA. */
 int rcbf_das(rcbf_plan_t plan, const void* decoded, const float* apod, float c,
              float* image, void* stream);
@@ -315,22 +320,26 @@ int rcbf_das(rcbf_plan_t plan, const void* decoded, const float* apod, float c,
  * 4-byte aligned one is accepted. rcbf_plan_query reports the tile used.
  * Built for RF data with linear interpolation: IQ or cubic plans return
  * RCBF_EUNSUPPORTED. Bounded waits and the status word as for rcbf_das: an
- * expired wait leaves the gradients incomplete and rcbf_plan_status returns
- * RCBF_ETIMEOUT.
+ * expired wait leaves the gradients incomplete and the next rcbf_plan_status
+ * returns RCBF_ETIMEOUT.
  * Errors: RCBF_EINVAL, RCBF_EUNSUPPORTED (dtype), RCBF_ECUDA. */
 int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, float c,
                       const float* grad_image, float* grad_rf, float* grad_c,
                       float* grad_apod, void* stream);
 
-/* rcbf_plan_status — synchronise `stream` and return the status of the last
- * rcbf_das or rcbf_das_backward call on the plan: RCBF_OK, or RCBF_ETIMEOUT
- * when one of its bounded device-side waits expired (its output is then
- * incomplete). The word is cleared by the next call, not by this one.
+/* rcbf_plan_status — synchronise `stream` and return the plan's status word:
+ * RCBF_OK, or RCBF_ETIMEOUT when a bounded device-side wait of one of the
+ * plan's kernels (tiled rcbf_das, rcbf_das_backward, the RCBF_DECODE_TC
+ * decode) expired since the previous rcbf_plan_status call; the output of that
+ * call is then incomplete. Reading clears the word (a synchronous 4-byte
+ * memset when it was set), so each expiry is reported once. The word is
+ * shared by all calls on the plan, whichever stream they use.
  * Errors: RCBF_EINVAL (NULL plan), RCBF_ECUDA. */
 int rcbf_plan_status(rcbf_plan_t plan, void* stream);
 
 /* rcbf_plan_set_wait — bound of every device-side wait of the plan's tiled
- * DAS and adjoint kernels (default one second; at most ten), and a test hook
+ * DAS, adjoint and RCBF_DECODE_TC kernels (default one second; at most ten),
+ * and a test hook
  * for failure detection: withhold = 1 makes every voxel tile of the tiled
  * rcbf_das omit the request of its first window copy, so that the tile's
  * first wait runs out, the kernel stops that tile and returns, and

@@ -30,7 +30,7 @@ TX_LINE, TX_PLANE, TX_VLS, TX_POINT = 0, 1, 2, 3
 _TX_WAVE_NAMES = {"line": TX_LINE, "plane": TX_PLANE, "vls": TX_VLS, "point": TX_POINT}
 HERCULES_2D = 2
 _INTERP_NAMES = {"linear": LINEAR, "cubic": CUBIC}
-DECODE_MMA_I8, DECODE_PLAIN, DECODE_MMA_F16 = 0, 1, 2
+DECODE_MMA_I8, DECODE_PLAIN, DECODE_MMA_F16, DECODE_TC = 0, 1, 2, 3
 DAS_TILED, DAS_PLAIN = 0, 1
 
 _DTYPE_NAMES = {"i32": I32, "f32": F32, "f16": F16, "cf32": CF32}

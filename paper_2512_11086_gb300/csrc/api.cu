@@ -138,7 +138,7 @@ int validate(const rcbf_params* p) {
     if (p->decoded_dtype != RCBF_I32 && p->decoded_dtype != RCBF_F32 && p->decoded_dtype != RCBF_F16 &&
         p->decoded_dtype != RCBF_CF32)
         return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: decoded_dtype must be RCBF_I32, RCBF_F32, RCBF_F16 or RCBF_CF32");
-    if (p->decode_variant > RCBF_DECODE_MMA_F16 || p->das_variant > RCBF_DAS_PLAIN)
+    if (p->decode_variant > RCBF_DECODE_TC || p->das_variant > RCBF_DAS_PLAIN)
         return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: unknown variant");
     if (p->hadamard_order) {
         if (p->hadamard_order != p->n_tx)
@@ -152,6 +152,8 @@ int validate(const rcbf_params* p) {
             return set_error(RCBF_EINVAL, "rcbf_plan: a Sylvester order must be a power of two");
         if (p->decode_variant != RCBF_DECODE_PLAIN && !(p->n_tx == 32 || p->n_tx == 64 || p->n_tx == 128 || p->n_tx == 256))
             return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: the tensor-core decode needs n_tx in {32, 64, 128, 256}");
+        if (p->decode_variant == RCBF_DECODE_TC && !(p->n_tx == 32 || p->n_tx == 64 || p->n_tx == 128))
+            return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: the tcgen05 decode needs n_tx in {32, 64, 128}");
         if (p->decode_variant == RCBF_DECODE_PLAIN && p->n_tx % 16)
             return set_error(RCBF_EUNSUPPORTED, "rcbf_plan: the plain decode needs n_tx a multiple of 16");
         if (p->decode_matrix)
@@ -624,8 +626,6 @@ int rcbf_das(rcbf_plan_t plan, const void* decoded, const float* apod, float c, 
     a.apod = apod;
     a.image = image;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // the status word reports this call (rcbf_plan_status)
-    if (cudaMemsetAsync(h.d_status, 0, sizeof(int), s) != cudaSuccess) return check_launch("rcbf_das: clear status");
     if (!(tiled && fits)) return launch_das_plain(h, a, s);
     if (!h.vls_split) return launch_das(h, a, s);
     // VLS focal plane inside the image: the tiled form for every tile but
@@ -671,8 +671,6 @@ int rcbf_das_backward(rcbf_plan_t plan, const void* decoded, const float* apod, 
     a.grad_apod = grad_apod;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int planes = h.p.decoded_dtype == RCBF_CF32 ? 2 : 1;
-    if (cudaMemsetAsync(h.d_status, 0, sizeof(int), s) != cudaSuccess)
-        return check_launch("rcbf_das_backward: clear status");
     if (grad_rf && cudaMemsetAsync(grad_rf, 0, (size_t)a.plane_stride * planes * sizeof(float), s) != cudaSuccess)
         return check_launch("rcbf_das_backward: clear grad_rf");
     if (grad_c && cudaMemsetAsync(grad_c, 0, sizeof(float), s) != cudaSuccess)
@@ -689,9 +687,10 @@ int rcbf_plan_status(rcbf_plan_t plan, void* stream) {
     int st = 0;
     if (cudaMemcpy(&st, plan->h.d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         return check_launch("rcbf_plan_status: read status");
-    if (st) return set_error(RCBF_ETIMEOUT, "rcbf_plan_status: a bounded device wait of the last rcbf_das / "
-                                            "rcbf_das_backward call expired; its output is incomplete");
-    return RCBF_OK;
+    if (!st) return RCBF_OK;
+    if (cudaMemset(plan->h.d_status, 0, sizeof(int)) != cudaSuccess) return check_launch("rcbf_plan_status: clear status");
+    return set_error(RCBF_ETIMEOUT, "rcbf_plan_status: a bounded device wait of the plan's kernels expired since the "
+                                    "last status read; that call's output is incomplete");
 }
 
 int rcbf_plan_set_wait(rcbf_plan_t plan, uint64_t wait_ns, int32_t withhold) {

@@ -98,7 +98,7 @@ int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t
         fr.order = (int)h.p.n_tx;
         if (h.p.hadamard_order) {
             fr.n_decode = (int)(((long long)h.p.n_ch * h.p.n_samples + kDecodeCols - 1) / kDecodeCols);
-            fr.decode_f16 = h.p.decode_variant == RCBF_DECODE_MMA_F16 ? 1 : 0;
+            fr.decode_f16 = (h.p.decode_variant == RCBF_DECODE_MMA_F16 || h.p.decode_variant == RCBF_DECODE_TC) ? 1 : 0;
             DecodeArgs& d = fr.dec;
             d.rf = rf[f];
             d.out = decoded[f];

@@ -324,6 +324,7 @@ int launch_decode(const PlanHost& h, const int16_t* rf, void* out, cudaStream_t 
     a.afrag16 = h.d_afrag16;
     a.hsum = h.d_hsum;
     const int v = (int)h.p.decode_variant;
+    if (v == RCBF_DECODE_TC) return launch_decode_tc(h, a.dtype, rf, out, s);
     switch (a.dtype) {
         case RCBF_I32: return v == RCBF_DECODE_PLAIN ? launch_plain<RCBF_I32>(a, s)
                             : v == RCBF_DECODE_MMA_F16 ? launch_mma_dt<RCBF_I32, true>(h, a, s)
@@ -342,6 +343,8 @@ int launch_decode(const PlanHost& h, const int16_t* rf, void* out, cudaStream_t 
 // persistent grid (CTAs per SM) for the plan's order and output type.
 int configure_decode(PlanHost& h) {
     if (h.p.hadamard_order == 0 || h.p.decode_variant == RCBF_DECODE_PLAIN) return RCBF_OK;
+    if (h.p.decode_variant == RCBF_DECODE_TC)
+        return configure_decode_tc(h, h.p.decoded_dtype == RCBF_CF32 ? (int)RCBF_F32 : (int)h.p.decoded_dtype);
     const int n = (int)h.p.n_tx;
     const bool f16 = h.p.decode_variant == RCBF_DECODE_MMA_F16;
     switch (h.p.decoded_dtype == RCBF_CF32 ? (uint32_t)RCBF_F32 : h.p.decoded_dtype) {

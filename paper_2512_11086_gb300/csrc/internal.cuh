@@ -149,6 +149,9 @@ int das_prepare_tile(const PlanHost& h, double c, int bu, int bv, int bw, double
 
 // Kernel launchers (one per translation unit).
 int launch_decode(const PlanHost& h, const int16_t* rf, void* out, cudaStream_t s);
+// The tcgen05 form of the decode (decode_tc.cu): launch, and plan-time set-up.
+int launch_decode_tc(const PlanHost& h, int dtype, const int16_t* rf, void* out, cudaStream_t s);
+int configure_decode_tc(const PlanHost& h, int dtype);
 // Device address of a batch's status word (batch.cu).
 int* batch_status_word(rcbf_batch_t batch);
 int launch_demodulate(const PlanHost& h, const int16_t* rf, int16_t* iq, cudaStream_t s);
