@@ -3,17 +3,19 @@
 Workload: the FORCES full-aperture B-scan (128 Hadamard-encoded transmits x
 128 channels x 4096 int16 samples, 512 x 1024 image, 8.59e9 voxel-channel-
 transmit sums per frame), synthetic point-scatterer data. One step = one
-batch of B frames (default 4) through the whole path in one persistent
-launch replayed from a CUDA graph: Hadamard decode (split-byte int8 tensor
-cores, FP16-stored output) and tiled DAS (FP32 accumulation), voxel tile
-from the autotuner.
+batch of B frames (default 4) through the whole path, replayed from one CUDA
+graph: the exact Hadamard decode of each frame on the tcgen05 tensor cores
+(FP16-stored output), then the tiled DAS (FP32 accumulation) of all frames in
+one persistent launch, voxel tile from the autotuner.
 
 Reported: value = whole-job DAS sums/s over the full step (decode included),
-frames/s, the same form unbatched (per-kernel CUDA-event times), the plain
-FP32 form on the same GPU, the roofline of the dominant kernel and of the
-decode, an end-to-end figure through the C ABI with host buffers, clocks
-during the timed region, and the FP64 CPU oracle timed on a bounded sample
-(N = 1, rank 0).
+frames/s, the same step with the split-byte int8 mma.sync decode inside the
+persistent kernel, the forms unbatched (per-kernel CUDA-event times), the
+plain FP32 form on the same GPU, the roofline of the dominant kernel and of
+the decode, an end-to-end figure through the C ABI with host buffers, clocks
+during the timed region, the volume / stream / autofocus configurations, and
+the CPU leg (N = 1, rank 0): the FP64 oracle timed on a bounded sample and the
+parity stamps of the timed outputs.
 
 --impl reference times the FP64 CPU oracle itself (the reference arm) on a
 bounded sample of the same workload.
@@ -330,9 +332,10 @@ def _graph_of(batch):
 
 
 def measure_batched(name: str, args, parity: bool = True) -> dict:
-    """The HERCULES volume (4 volumes per step) or the 64-frame stream: one
-    persistent launch per step replayed from a CUDA graph, split-byte int8
-    decode to FP16 and tiled DAS, tiles from the autotuner. Parity stamp
+    """The HERCULES volume (4 volumes per step) or the 64-frame stream, per
+    step one CUDA graph: the exact tcgen05 decode of each frame to FP16, then
+    the tiled DAS of all frames in one persistent launch, tiles from the
+    autotuner. The roofline fraction is that of the whole step. Parity stamp
     (outside the timed region): decode bit-exact and sampled voxels against
     the FP64 oracle of the same FP16 decoded data, for the first frame of
     every frame class."""
@@ -360,7 +363,7 @@ def measure_batched(name: str, args, parity: bool = True) -> dict:
     plans, rf, dec, img = [], [], [], []
     for fr, t in zip(frames, tiles):
         g = fr.geometry
-        plans.append(rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=rc.DECODE_MMA_I8, tile=t)))
+        plans.append(rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=rc.DECODE_TC, tile=t)))
         rf.append(torch.from_numpy(fr.rf).to(dev))
         dec.append(torch.empty(g.n_tx, g.n_ch, g.n_samples, dtype=torch.float16, device=dev))
         img.append(torch.empty(g.out_dims[2], g.out_dims[1], g.out_dims[0], device=dev))
@@ -564,7 +567,7 @@ def run_channel_shard(args):
     g = frame.geometry
     tile = tune.tune_tile(g, "f16")
     off, cnt = shard.channel_slices(g.n_ch, ws)[rank]
-    plan = rc.Plan(shard.shard_params(g, rank, ws, decoded_dtype="f16", decode_variant=rc.DECODE_MMA_I8,
+    plan = rc.Plan(shard.shard_params(g, rank, ws, decoded_dtype="f16", decode_variant=rc.DECODE_TC,
                                       das_variant=rc.DAS_TILED, tile=tile))
     host = torch.from_numpy(np.ascontiguousarray(frame.rf[:, off:off + cnt, :])).pin_memory()
     rf = host.to(dev)
@@ -628,7 +631,7 @@ def run_channel_shard(args):
                        "parallelism": "receive channels split over %d GPU(s), partial images summed by one "
                                       "all-reduce" % ws,
                        "l2": "one 128 MB int16 frame per step (129 MB L2; decoded FP16 written and re-read)"},
-            "form": "per rank: split-byte int8 decode of its channel slice to FP16, tiled DAS of the slice, "
+            "form": "per rank: tcgen05 decode of its channel slice to FP16, tiled DAS of the slice, "
                     "NCCL all-reduce of the partial image",
             "tile": list(tile), "frames_per_s": 1e3 / ms,
             "e2e": {"value": g.sums / (e2e_ms * 1e-3) / 1e9, "unit": UNIT,
@@ -642,6 +645,22 @@ def run_channel_shard(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _graph_ms(batch, steps: int, warmup: int, stream) -> float:
+    """CUDA-event time of one replay of a graph of batch.run() (after warm-up)."""
+    import torch
+    graph = _graph_of(batch)
+    for _ in range(warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = _events(2)
+    e0.record(stream)
+    for _ in range(steps):
+        graph.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
 
 
 def _events(n):
@@ -714,11 +733,12 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    # ---- the batched, precision-tuned form: B frames per step, split-byte int8
-    # tensor-core decode to FP16, tiled FP32 DAS, one persistent launch replayed
-    # from a CUDA graph; the voxel tile comes from the autotuner
+    # ---- the batched, precision-tuned form: B frames per step, the exact
+    # decode on the tcgen05 tensor cores to FP16 (one launch per frame), then
+    # the tiled FP32 DAS of all frames in one persistent launch, the whole step
+    # replayed from a CUDA graph; the voxel tile comes from the autotuner
     tile = tune.tune_tile(g, "f16")
-    tuned = rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=rc.DECODE_MMA_I8,
+    tuned = rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=rc.DECODE_TC,
                                    das_variant=rc.DAS_TILED, tile=tile))
     rf_host = torch.from_numpy(frame.rf)
     rf = [rf_host.to(dev) for _ in range(B)]
@@ -761,6 +781,22 @@ def main():
     last_image = imgs[B - 1].cpu().numpy()
     last_decoded = dec16[B - 1].cpu().numpy()
 
+    # ---- the persistent DAS kernel alone (the dominant kernel): the same batch
+    # over the decoded frames, without their decode
+    g_dec = dataclasses.replace(g, hadamard_order=0)
+    das_only = rc.Batch([rc.Plan(rc.make_params(g_dec, decoded_dtype="f16", das_variant=rc.DAS_TILED,
+                                                tile=tile))] * B, None, dec16, imgs)
+    t_batch_kernel = _graph_ms(das_only, args.steps, args.warmup, stream)
+
+    # ---- the same batch with the split-byte int8 mma.sync decode as work items
+    # of the persistent kernel (the int8 tensor-core form of the decode)
+    i8 = rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=rc.DECODE_MMA_I8,
+                                das_variant=rc.DAS_TILED, tile=tile))
+    batch_i8 = rc.Batch([i8] * B, rf, dec16, imgs)
+    t_batch_i8 = _graph_ms(batch_i8, args.steps, args.warmup, stream)
+    if batch_i8.status() != rc.OK or das_only.status() != rc.OK:
+        raise RuntimeError("batch status after the variant timings")
+
     # ---- the same form unbatched: decode and DAS launched per frame
     ub_steps = max(3, min(args.steps, 10))
     for s in range(3):
@@ -778,19 +814,21 @@ def main():
     t_dec = float(np.mean([e[0].elapsed_time(e[1]) for e in ue]))
     t_das = float(np.mean([e[1].elapsed_time(e[2]) for e in ue]))
 
-    # ---- the exact byte-split FP16 tensor-core decode, same output
-    f16dec = rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=rc.DECODE_MMA_F16,
-                                    das_variant=rc.DAS_TILED, tile=tile))
-    for s in range(3):
-        f16dec.decode(rf[s % B], out=dec16[s % B])
-    q0, q1 = _events(2)
-    torch.cuda.synchronize()
-    q0.record(stream)
-    for s in range(ub_steps):
-        f16dec.decode(rf[s % B], out=dec16[s % B])
-    q1.record(stream)
-    torch.cuda.synchronize()
-    t_dec_f16 = q0.elapsed_time(q1) / ub_steps
+    # ---- the other exact decode forms, same output: split-byte int8 and FP16 mma.sync
+    def decode_ms(plan):
+        for s in range(3):
+            plan.decode(rf[s % B], out=dec16[s % B])
+        q0, q1 = _events(2)
+        torch.cuda.synchronize()
+        q0.record(stream)
+        for s in range(ub_steps):
+            plan.decode(rf[s % B], out=dec16[s % B])
+        q1.record(stream)
+        torch.cuda.synchronize()
+        return q0.elapsed_time(q1) / ub_steps
+    t_dec_i8 = decode_ms(i8)
+    t_dec_f16 = decode_ms(rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=rc.DECODE_MMA_F16,
+                                                 das_variant=rc.DAS_TILED, tile=tile)))
 
     # ---- cubic Hermite interpolation (the paper's measured setting): the DAS
     # alone on the same FP16 decoded frame, its own tuned tile
@@ -889,7 +927,7 @@ def main():
     sms = props.multi_processor_count
     ops_per_sum = 5   # add (A_i + B_j), floor, fraction, interpolation FMA, accumulate
     alu_peak = sms * 128 * peaks["sm_max_mhz"] * 1e6 / 1e12   # FP32 lane-ops/s in T
-    achieved = ops_per_sum * B * sums / (t_batch * 1e-3) / 1e12
+    achieved = ops_per_sum * B * sums / (t_batch_kernel * 1e-3) / 1e12
     dec_bytes = g.n_tx * g.n_ch * g.n_samples * (2 + 2)       # int16 in + FP16 out
     info = tuned.info()
     # the same launch against HBM: compulsory bytes per frame if nothing stayed
@@ -901,6 +939,7 @@ def main():
     frame_bytes = g.n_tx * g.n_ch * g.n_samples * (2 + 2 + 2) + g.n_vox * 4
     window_bytes = n_tiles * g.n_tx * g.n_ch * raw_samples * 2
     traffic = recorded_traffic("batch_kernel", B)
+    traffic_dec = recorded_traffic("decode_tc_kernel", 1)
     # on-chip ceilings measured on this GPU (microbenchmarks at the DAS
     # kernel's occupancy): one 8-byte line piece per sum from shared memory
     ceil = rc.measure_ceilings()
@@ -911,12 +950,17 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": headline_config(B, ws),
-        "form": "batched persistent launch (CUDA graph): split-byte int8 mma.sync decode (exact) to FP16, "
-                "tiled TMA-window DAS in FP32",
+        "form": "per step (one CUDA graph): exact split-byte decode to FP16 on the tcgen05 tensor cores "
+                "(TMEM accumulators, TMA tiles), one launch per frame, then the tiled TMA-window FP32 DAS of "
+                "all frames in one persistent launch",
         "tile": list(tile),
         "frames_per_s": B * ws * 1e3 / ms_step,
-        "kernel_ms": {"batch_kernel_per_step": t_batch, "unbatched_decode": t_dec, "unbatched_das": t_das,
-                      "decode_f16_mma_alternative": t_dec_f16},
+        "kernel_ms": {"step": t_batch, "batch_kernel_das_only": t_batch_kernel,
+                      "unbatched_decode_tc": t_dec, "unbatched_das": t_das,
+                      "decode_i8_mma": t_dec_i8, "decode_f16_mma": t_dec_f16},
+        "batched_i8_decode": {"value": B * sums / (t_batch_i8 * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": t_batch_i8,
+                              "form": "the same step with the split-byte int8 mma.sync decode as work items of "
+                                      "the persistent kernel (one launch per step)"},
         "unbatched": {"value": sums / ((t_dec + t_das) * 1e-3) / 1e9, "unit": UNIT,
                       "das_only": sums / (t_das * 1e-3) / 1e9},
         "f_number_1": {"value": sums / (t_fn1 * 1e-3) / 1e9, "unit": UNIT, "ms_per_frame": t_fn1,
@@ -929,15 +973,15 @@ def main():
                        "speedup_of_tuned": value / ws / plain_value},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TOP/s",
                      "frac": achieved / alu_peak, "traffic": traffic,
-                     "kernel": "batch_kernel",
+                     "kernel": "batch_kernel (the persistent DAS launch of the step, timed alone)",
                      "peak_src": "%d SMs x 128 FP32 lanes x %.0f MHz" % (sms, peaks["sm_max_mhz"]),
                      "ops_per_sum": ops_per_sum},
-        "roofline_memory": {"bound": "hbm", "achieved": B * frame_bytes / (t_batch * 1e-3) / 1e9,
+        "roofline_memory": {"bound": "hbm", "achieved": B * frame_bytes / (t_batch_kernel * 1e-3) / 1e9,
                             "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                            "frac": B * frame_bytes / (t_batch * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                            "frac": B * frame_bytes / (t_batch_kernel * 1e-3) / 1e9 / peaks["hbm_gbs"],
                             "traffic": traffic,
-                            "traffic_GBps": None if traffic is None else traffic / (t_batch * 1e-3) / 1e9,
-                            "l2_window_GBps": B * window_bytes / (t_batch * 1e-3) / 1e9,
+                            "traffic_GBps": None if traffic is None else traffic / (t_batch_kernel * 1e-3) / 1e9,
+                            "l2_window_GBps": B * window_bytes / (t_batch_kernel * 1e-3) / 1e9,
                             "kernel": "batch_kernel", "peak_src": peaks["src"],
                             "bytes_per_frame": frame_bytes},
         "ceilings": {"lds64_TBps": ceil["lds64_bytes_per_s"] / 1e12,
@@ -946,19 +990,24 @@ def main():
                      "red_shared_G_per_s": ceil["red_shared_per_s"] / 1e9,
                      "sm_mhz": ceil["sm_clock_hz"] / 1e6,
                      "lds_sums_per_s_ceiling": ceil["lds64_bytes_per_s"] / 8.0,
-                     "frac_lds_batched": B * sums / (t_batch * 1e-3) * 8.0 / ceil["lds64_bytes_per_s"],
+                     "frac_lds_batched": B * sums / (t_batch_kernel * 1e-3) * 8.0 / ceil["lds64_bytes_per_s"],
                      "frac_lds_das_alone": das_alone * 8.0 / ceil["lds64_bytes_per_s"],
                      "frac_ffma_batched": achieved * 1e12 / ceil["ffma_lane_ops_per_s"],
                      "source": "rcbf_measure_ceilings (this GPU, 2 CTAs x 256 threads per SM)"},
         "roofline_decode": {"bound": "hbm", "achieved": dec_bytes / (t_dec * 1e-3) / 1e9,
                             "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                            "frac": dec_bytes / (t_dec * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
-                            "kernel": "decode_mma_kernel (unbatched)", "peak_src": peaks["src"]},
+                            "frac": dec_bytes / (t_dec * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": traffic_dec,
+                            "kernel": "decode_tc_kernel (tcgen05, unbatched)", "peak_src": peaks["src"],
+                            "bytes_per_launch": dec_bytes},
+        "roofline_decode_i8": {"bound": "tensor (int8 mma.sync rate)", "achieved_GBps": dec_bytes / (t_dec_i8 * 1e-3) / 1e9,
+                               "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                               "frac": dec_bytes / (t_dec_i8 * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                               "kernel": "decode_mma_kernel (split-byte int8 mma.sync, unbatched)"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(B * rf_host.numel() * 2),
                 "d2h_bytes_per_step": int(B * img_host[0][0].numel() * 4), "ms_per_step": e2e_ms,
                 "form": "rcbf_pipeline upload ring, 3 slots (host wall clock between full waits)",
                 "serial_ms_per_step": e2e_serial_ms},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (1 + B),
         "plan": info,
         "clocks": clk,
     }

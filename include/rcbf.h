@@ -131,8 +131,8 @@ enum rcbf_decode_variant {
     RCBF_DECODE_TC      = 3   /* the split-byte FP16 GEMM on the 5th-generation tensor cores:
                                  tcgen05.mma with accumulators in tensor memory, TMA tensor
                                  loads of the int16 tiles and TMA stores of the output; exact;
-                                 n_tx in {32, 64, 128}. Inside a batch the frame is decoded by
-                                 the split-byte FP16 form of the persistent kernel. */
+                                 n_tx in {32, 64, 128}. In a batch such a frame is decoded by its
+                                 own tcgen05 launch ahead of the persistent launch. */
 };
 
 enum rcbf_das_variant {
@@ -352,7 +352,9 @@ int rcbf_plan_set_wait(rcbf_plan_t plan, uint64_t wait_ns, int32_t withhold);
 /* rcbf_batch_create — bind n_frames (plan, buffers) triples into one batch
  * that a single persistent kernel processes: for every frame with a
  * Hadamard order, decode rf[f] into decoded[f] (with the plan's tensor-core
- * decode form), then DAS decoded[f] into images[f] (frames with
+ * decode form; an RCBF_DECODE_TC frame by its own tcgen05 launch, enqueued by
+ * rcbf_batch_run ahead of the persistent launch, the other forms as work
+ * items of the persistent kernel), then DAS decoded[f] into images[f] (frames with
  * hadamard_order == 0 skip the decode and read decoded[f] directly). Plans
  * may differ in transmit count, samples, grid and orientation; all must use
  * decoded_dtype RCBF_F32 or RCBF_F16, the tiled DAS with no F# window, and
@@ -370,7 +372,7 @@ int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames,
                       float* const* images, rcbf_batch_t* out_batch);
 
 /* rcbf_batch_run — enqueue the whole batch as one persistent launch (plus a
- * small reset kernel) on `stream`. Contains no host synchronisation and no
+ * counter reset, and one tcgen05 decode launch per RCBF_DECODE_TC frame) on `stream`. Contains no host synchronisation and no
  * allocation, so it can be captured in a CUDA graph. The persistent kernel's
  * waits on per-frame decode completion are bounded; on expiry it records
  * RCBF_ETIMEOUT in the batch's device status word (see rcbf_batch_status). */

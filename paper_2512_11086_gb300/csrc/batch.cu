@@ -28,6 +28,7 @@ struct rcbf_batch_s {
     int4* d_items = nullptr;
     rcbf::BatchFrame* d_frames = nullptr;
     int* d_counters = nullptr;
+    std::vector<rcbf::TcJob> tc_jobs;   // frames decoded by the tcgen05 kernel ahead of the persistent launch
 };
 
 using namespace rcbf;
@@ -57,6 +58,7 @@ int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t
         return set_error(RCBF_EINVAL, "rcbf_batch_create: NULL array or zero frames");
     const int bu = plans[0] ? plans[0]->h.das.bu : 0;
     std::vector<BatchFrame> frames(n_frames);
+    std::vector<TcJob> tc_jobs;
     int ws = 48;
     for (uint32_t f = 0; f < n_frames; ++f) {
         const rcbf_plan_t p = plans[f];
@@ -96,9 +98,16 @@ int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t
         ws = std::max(ws, class_of(fr.das.W));
         fr.out_dtype = (int)h.p.decoded_dtype;
         fr.order = (int)h.p.n_tx;
-        if (h.p.hadamard_order) {
+        if (h.p.hadamard_order && h.p.decode_variant == RCBF_DECODE_TC) {
+            // decoded by its own tcgen05 launch ahead of the persistent kernel
+            // (stream order makes its output visible to the frame's DAS items)
+            TcJob job;
+            if (decode_tc_prepare(h, (int)h.p.decoded_dtype, rf[f], decoded[f], &job) != RCBF_OK)
+                return set_error(RCBF_EUNSUPPORTED, at + rcbf_last_error());
+            tc_jobs.push_back(job);
+        } else if (h.p.hadamard_order) {
             fr.n_decode = (int)(((long long)h.p.n_ch * h.p.n_samples + kDecodeCols - 1) / kDecodeCols);
-            fr.decode_f16 = (h.p.decode_variant == RCBF_DECODE_MMA_F16 || h.p.decode_variant == RCBF_DECODE_TC) ? 1 : 0;
+            fr.decode_f16 = h.p.decode_variant == RCBF_DECODE_MMA_F16 ? 1 : 0;
             DecodeArgs& d = fr.dec;
             d.rf = rf[f];
             d.out = decoded[f];
@@ -131,6 +140,7 @@ int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t
     for (uint32_t f = 0; f < n_frames; ++f) frames[f].das.status = nullptr;   // set below
 
     rcbf_batch_s* b = new rcbf_batch_s();
+    b->tc_jobs = tc_jobs;
     b->n_frames = (int)n_frames;
     b->n_items = (int)items.size();
     b->vu = bu / 32;
@@ -164,6 +174,10 @@ int rcbf_batch_run(rcbf_batch_t batch, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(batch->d_counters, 0, (kBatchDone + batch->n_frames) * sizeof(int), s) != cudaSuccess)
         return check_launch("rcbf_batch_run: reset counters");
+    for (const TcJob& job : batch->tc_jobs) {
+        const int rc = decode_tc_run(job, batch->d_counters + kBatchStatus, batch->wait_ns, s);
+        if (rc != RCBF_OK) return rc;
+    }
     switch (batch->vu) {
         case 1: return batch_launch_vu<1>(batch->ws, batch->grid, batch->smem, batch->d_items, batch->n_items,
                                           batch->d_frames, batch->d_counters, batch->wait_ns, batch->withhold, s);

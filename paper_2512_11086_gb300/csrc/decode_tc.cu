@@ -441,25 +441,44 @@ int make_map(CUtensorMap* map, CUtensorMapDataType dt, int es, const void* base,
 }
 
 template <int N, int DT>
-int tc_launch(const PlanHost& h, const int16_t* rf, void* out, cudaStream_t s) {
+int tc_launch_job(const TcJob& job, int* status, long long wait_ns, cudaStream_t s) {
+    constexpr int ES = DT == RCBF_F16 ? 2 : 4;
+    decode_tc_kernel<N, DT><<<job.grid, kTcThreads, TcCfg<N, ES>::SMEM, s>>>(
+        job.in_map, job.out_map, job.hmat, job.hsum, job.n_cols, job.inv_n, status, wait_ns);
+    return check_launch("decode_tc_kernel");
+}
+
+template <int N, int DT>
+int tc_prepare(const PlanHost& h, const int16_t* rf, void* out, TcJob* job) {
     constexpr int ES = DT == RCBF_F16 ? 2 : 4;
     using C = TcCfg<N, ES>;
     const long long n_cols = (long long)h.p.n_ch * h.p.n_samples;
     if (n_cols > 2147483647LL - kTcCols)
         return set_error(RCBF_EUNSUPPORTED, "decode (tcgen05): n_ch * n_samples must stay below 2^31 (TMA coordinates)");
-    CUtensorMap in_map, out_map;
     // int16 samples moved as 16-bit words (TMA has no signed 16-bit type; only the bits matter)
-    int rc = make_map(&in_map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, rf, n_cols, N, kTcCols, N);
+    int rc = make_map(&job->in_map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, rf, n_cols, N, kTcCols, N);
     if (rc != RCBF_OK) return rc;
     const CUtensorMapDataType odt = DT == RCBF_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                   : DT == RCBF_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_INT32;
-    if ((rc = make_map(&out_map, odt, ES, out, n_cols, N, 128 / ES, C::ROWS)) != RCBF_OK) return rc;
+    if ((rc = make_map(&job->out_map, odt, ES, out, n_cols, N, 128 / ES, C::ROWS)) != RCBF_OK) return rc;
     const long long tiles = (n_cols + kTcCols - 1) / kTcCols;
     long long grid = h.n_sms > 0 ? h.n_sms : 1;
     if (grid > tiles) grid = tiles;
-    decode_tc_kernel<N, DT><<<(unsigned)grid, kTcThreads, C::SMEM, s>>>(
-        in_map, out_map, h.d_hmat, h.d_hsum, n_cols, 1.0f / (float)h.p.n_tx, h.d_status, h.das.wait_ns);
-    return check_launch("decode_tc_kernel");
+    job->hmat = h.d_hmat;
+    job->hsum = h.d_hsum;
+    job->n_cols = n_cols;
+    job->inv_n = 1.0f / (float)h.p.n_tx;
+    job->n = N;
+    job->dtype = DT;
+    job->grid = (unsigned)grid;
+    return RCBF_OK;
+}
+
+template <int N, int DT>
+int tc_launch(const PlanHost& h, const int16_t* rf, void* out, cudaStream_t s) {
+    TcJob job;
+    const int rc = tc_prepare<N, DT>(h, rf, out, &job);
+    return rc != RCBF_OK ? rc : tc_launch_job<N, DT>(job, h.d_status, h.das.wait_ns, s);
 }
 
 template <int N, int DT>
@@ -471,21 +490,32 @@ int tc_configure() {
     return RCBF_OK;
 }
 
+// op: 0 configure, 1 launch, 2 prepare a job, 3 run a job
 template <int DT>
-int tc_dispatch(const PlanHost& h, const int16_t* rf, void* out, cudaStream_t s, bool configure) {
-    switch (h.p.n_tx) {
-        case 32: return configure ? tc_configure<32, DT>() : tc_launch<32, DT>(h, rf, out, s);
-        case 64: return configure ? tc_configure<64, DT>() : tc_launch<64, DT>(h, rf, out, s);
-        case 128: return configure ? tc_configure<128, DT>() : tc_launch<128, DT>(h, rf, out, s);
+int tc_dispatch(int n, int op, const PlanHost* h, const int16_t* rf, void* out, cudaStream_t s, TcJob* job,
+                int* status, long long wait_ns) {
+#define RCBF_TC_OPS(NN)                                                                              \
+    switch (op) {                                                                                    \
+        case 0: return tc_configure<NN, DT>();                                                       \
+        case 1: return tc_launch<NN, DT>(*h, rf, out, s);                                            \
+        case 2: return tc_prepare<NN, DT>(*h, rf, out, job);                                         \
+        default: return tc_launch_job<NN, DT>(*job, status, wait_ns, s);                             \
+    }
+    switch (n) {
+        case 32: RCBF_TC_OPS(32)
+        case 64: RCBF_TC_OPS(64)
+        case 128: RCBF_TC_OPS(128)
         default: return set_error(RCBF_EUNSUPPORTED, "decode (tcgen05): n_tx must be 32, 64 or 128");
     }
+#undef RCBF_TC_OPS
 }
 
-int tc_by_dtype(const PlanHost& h, int dtype, const int16_t* rf, void* out, cudaStream_t s, bool configure) {
+int tc_by_dtype(int dtype, int n, int op, const PlanHost* h, const int16_t* rf, void* out, cudaStream_t s,
+                TcJob* job, int* status, long long wait_ns) {
     switch (dtype) {
-        case RCBF_I32: return tc_dispatch<RCBF_I32>(h, rf, out, s, configure);
-        case RCBF_F32: return tc_dispatch<RCBF_F32>(h, rf, out, s, configure);
-        case RCBF_F16: return tc_dispatch<RCBF_F16>(h, rf, out, s, configure);
+        case RCBF_I32: return tc_dispatch<RCBF_I32>(n, op, h, rf, out, s, job, status, wait_ns);
+        case RCBF_F32: return tc_dispatch<RCBF_F32>(n, op, h, rf, out, s, job, status, wait_ns);
+        case RCBF_F16: return tc_dispatch<RCBF_F16>(n, op, h, rf, out, s, job, status, wait_ns);
         default: return set_error(RCBF_EUNSUPPORTED, "decode (tcgen05): output dtype must be RCBF_I32, RCBF_F32 or RCBF_F16");
     }
 }
@@ -493,12 +523,20 @@ int tc_by_dtype(const PlanHost& h, int dtype, const int16_t* rf, void* out, cuda
 }  // namespace
 
 int launch_decode_tc(const PlanHost& h, int dtype, const int16_t* rf, void* out, cudaStream_t s) {
-    return tc_by_dtype(h, dtype, rf, out, s, false);
+    return tc_by_dtype(dtype, (int)h.p.n_tx, 1, &h, rf, out, s, nullptr, nullptr, 0);
 }
 
 int configure_decode_tc(const PlanHost& h, int dtype) {
     if (!encode_fn()) return set_error(RCBF_EUNSUPPORTED, "decode (tcgen05): no tensor-map encoder in the driver");
-    return tc_by_dtype(h, dtype, nullptr, nullptr, nullptr, true);
+    return tc_by_dtype(dtype, (int)h.p.n_tx, 0, &h, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
+}
+
+int decode_tc_prepare(const PlanHost& h, int dtype, const int16_t* rf, void* out, TcJob* job) {
+    return tc_by_dtype(dtype, (int)h.p.n_tx, 2, &h, rf, out, nullptr, job, nullptr, 0);
+}
+
+int decode_tc_run(const TcJob& job, int* status, long long wait_ns, cudaStream_t s) {
+    return tc_by_dtype(job.dtype, job.n, 3, nullptr, nullptr, nullptr, s, const_cast<TcJob*>(&job), status, wait_ns);
 }
 
 }  // namespace rcbf

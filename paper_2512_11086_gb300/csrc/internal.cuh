@@ -2,6 +2,7 @@
 // by the library's translation units (decode, DAS, adjoint, batch, API).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -152,6 +153,19 @@ int launch_decode(const PlanHost& h, const int16_t* rf, void* out, cudaStream_t 
 // The tcgen05 form of the decode (decode_tc.cu): launch, and plan-time set-up.
 int launch_decode_tc(const PlanHost& h, int dtype, const int16_t* rf, void* out, cudaStream_t s);
 int configure_decode_tc(const PlanHost& h, int dtype);
+// A tcgen05 decode bound to fixed buffers (the tensor maps encoded once), for
+// the batch: prepared at rcbf_batch_create, launched by every rcbf_batch_run.
+struct TcJob {
+    CUtensorMap in_map, out_map;
+    const int8_t* hmat;
+    const int* hsum;
+    long long n_cols;
+    float inv_n;
+    int n, dtype;
+    unsigned grid;
+};
+int decode_tc_prepare(const PlanHost& h, int dtype, const int16_t* rf, void* out, TcJob* job);
+int decode_tc_run(const TcJob& job, int* status, long long wait_ns, cudaStream_t s);
 // Device address of a batch's status word (batch.cu).
 int* batch_status_word(rcbf_batch_t batch);
 int launch_demodulate(const PlanHost& h, const int16_t* rf, int16_t* iq, cudaStream_t s);

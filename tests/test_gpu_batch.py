@@ -182,3 +182,57 @@ def test_batch_at_the_benchmark_configuration():
         err = rel_l2(got, sg * want)
         print("benchmark batch slot %d (tile %s): rel-L2 %.2e" % (k, tile, err))
         assert err <= 1e-4
+
+
+def test_batch_with_tcgen05_decode_frames():
+    # frames whose plans use the tcgen05 decode are decoded by their own
+    # launches ahead of the persistent kernel; mixed with an in-kernel
+    # (split-byte int8) frame, an unencoded frame, and replayed from a graph
+    frames = _stream_frames()
+    plans, rf, dec, img = [], [], [], []
+    for k, fr in enumerate(frames):
+        g = fr.geometry
+        variant = rc.DECODE_MMA_I8 if k == 1 else rc.DECODE_TC
+        plans.append(rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=variant, tile=(64, 1, 16))))
+        if fr.rf is not None:
+            rf.append(torch.from_numpy(fr.rf).cuda())
+            dec.append(torch.empty(g.n_tx, g.n_ch, g.n_samples, dtype=torch.float16, device="cuda"))
+        else:
+            rf.append(None)
+            dec.append(torch.from_numpy(fr.decoded).to(torch.float16).cuda())
+        img.append(torch.empty(g.out_dims[2], g.out_dims[1], g.out_dims[0], dtype=torch.float32, device="cuda"))
+    batch = rc.Batch(plans, rf, dec, img)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        batch.run(stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.run()
+    for k, fr in enumerate(frames):                       # new data in the bound buffers
+        if rf[k] is not None:
+            rf[k].copy_(torch.from_numpy(np.ascontiguousarray(-fr.rf)))
+    graph.replay()
+    torch.cuda.synchronize()
+    assert batch.status() == rc.OK
+    for k, fr in enumerate(frames):
+        g = fr.geometry
+        if fr.rf is not None:
+            want16 = oracle.decoded_as(oracle.decode(-fr.rf), g.n_tx, "f16")
+            np.testing.assert_array_equal(dec[k].cpu().numpy().view(np.uint16), want16.view(np.uint16))
+            data = want16.astype(np.float64)
+        else:
+            data = dec[k].cpu().numpy().astype(np.float64)
+        vox = sample_voxels(g.out_dims, 400, seed=20 + k)
+        err = rel_l2(img[k].cpu().numpy().ravel()[vox], oracle.das(g, data, voxels=vox))
+        print("tcgen05-decoded batch frame %d (%d tx): rel-L2 %.2e" % (k, g.n_tx, err))
+        assert err <= 1e-4
+    # the bounded per-frame wait still guards a tcgen05-decoded frame
+    batch.set_wait(2_000_000, withhold_frame=0)
+    batch.run()
+    assert batch.status() == rc.ETIMEOUT
+    batch.set_wait(1_000_000_000, withhold_frame=-1)
+    batch.run()
+    assert batch.status() == rc.OK
