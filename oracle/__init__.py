@@ -76,6 +76,7 @@ def _load():
             lib.oracle_das.argtypes = [P, P, I64, P, ctypes.c_double, I64, P, P]
             lib.oracle_das_grad.argtypes = [P, P, I64, P, ctypes.c_double, P, P, P, P]
             lib.oracle_demodulate.argtypes = [I64, I64, P, P, I64, I64, I64, I64, P]
+            lib.oracle_demodulate_complex.argtypes = [I64, I64, P, P, P, I64, I64, I64, I64, P]
             lib.oracle_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -210,16 +211,21 @@ def das_grad(g, rf: np.ndarray, G: np.ndarray, w: Optional[np.ndarray] = None,
 
 # ------------------------------------------------------------ demodulation
 
-def demodulate(rf: np.ndarray, taps: np.ndarray, shift: int, decimation: int) -> np.ndarray:
+def demodulate(rf: np.ndarray, taps: np.ndarray, shift: int, decimation: int,
+               taps_imag: Optional[np.ndarray] = None) -> np.ndarray:
     """Eq. (demodulation) at quadrature sampling (f_d = f_s / 4) with int16
-    taps, a rounding right shift and decimation, in exact integers.
+    taps (real, or complex with the imaginary parts in taps_imag), a rounding
+    right shift and decimation, in exact integers.
     rf: int16 [..., n_in] -> int16 [2, ..., n_in // decimation] (I, Q)."""
     rf = np.ascontiguousarray(rf, dtype=np.int16)
     h = np.ascontiguousarray(taps, dtype=np.int16)
+    hi = None if taps_imag is None else np.ascontiguousarray(taps_imag, dtype=np.int16)
+    if hi is not None and hi.size != h.size:
+        raise ValueError("taps_imag must have the length of taps")
     n_in = rf.shape[-1]
     n_out = n_in // int(decimation)
     n_traces = rf.size // n_in
     out = np.empty((2,) + rf.shape[:-1] + (n_out,), dtype=np.int16)
-    _load().oracle_demodulate(n_traces, n_in, _ptr(rf), _ptr(h), h.size, int(shift), int(decimation), n_out,
-                              _ptr(out))
+    _load().oracle_demodulate_complex(n_traces, n_in, _ptr(rf), _ptr(h), _ptr(hi), h.size, int(shift),
+                                      int(decimation), n_out, _ptr(out))
     return out

@@ -26,8 +26,8 @@
  *   oracle_demodulate  IQ[n] = LPF{s[n] e^{-j 2 pi f_d n / f_s}} (§OPTIMIZATIONS
  *                    "Filtering & Demodulation", Eq. (demodulation)) at
  *                    quadrature sampling f_s = 4 f_d, with an integer FIR
- *                    (int16 taps, a rounding right shift back to int16) and
- *                    decimation, in exact integer arithmetic.
+ *                    (int16 taps, real or complex, a rounding right shift back
+ *                    to int16) and decimation, in exact integer arithmetic.
  *   IQ beamforming   oracle_das with iq_freq = f_d > 0 reads the two planes as
  *                    the baseband signal and multiplies each interpolated
  *                    sample by e^{j 2 pi (f_d / f_s) s}, which restores the
@@ -367,12 +367,15 @@ static int64_t round_shift_even(int64_t x, int64_t shift) {
 /* Eq. (demodulation) at f_d = f_s / 4: e^{-j 2 pi n / 4} = cos(pi n / 2) - j sin(pi n / 2)
  * is 1, -j, -1, j for n mod 4 = 0, 1, 2, 3. The LPF is the causal FIR
  * y[n] = sum_k h[k] x[n - k] (x = 0 outside the record); decimation keeps
- * n = m D. Each output component is rounded (ties to even) after a right
- * shift and saturated to int16.
- * s: [n_traces][n_in] int16; h: [n_taps] int16; out: [2][n_traces][n_out]
- * (I plane, then Q plane), n_out * D <= n_in. */
-void oracle_demodulate(int64_t n_traces, int64_t n_in, const int16_t* s, const int16_t* h, int64_t n_taps,
-                       int64_t shift, int64_t decimation, int64_t n_out, int16_t* out) {
+ * n = m D. The taps may be complex, h[k] = h_re[k] + j h_im[k] (a baseband
+ * matched filter that also applies a phase correction); the product
+ * h[k] x[n - k] is the complex product. Each output component is rounded
+ * (ties to even) after a right shift and saturated to int16.
+ * s: [n_traces][n_in] int16; h_re, h_im: [n_taps] int16 (h_im NULL = real
+ * taps); out: [2][n_traces][n_out] (I plane, then Q plane), n_out * D <= n_in. */
+void oracle_demodulate_complex(int64_t n_traces, int64_t n_in, const int16_t* s, const int16_t* h_re,
+                               const int16_t* h_im, int64_t n_taps, int64_t shift, int64_t decimation,
+                               int64_t n_out, int16_t* out) {
 #pragma omp parallel for schedule(static)
     for (int64_t tr = 0; tr < n_traces; ++tr) {
         const int16_t* x = s + tr * n_in;
@@ -391,8 +394,10 @@ void oracle_demodulate(int64_t n_traces, int64_t n_in, const int16_t* s, const i
                     case 2: re = -v; break;
                     default: im = v; break;
                 }
-                acc_i += (int64_t)h[k] * re;
-                acc_q += (int64_t)h[k] * im;
+                const int64_t hr = h_re[k], hi = h_im ? h_im[k] : 0;
+                /* (hr + j hi)(re + j im) */
+                acc_i += hr * re - hi * im;
+                acc_q += hr * im + hi * re;
             }
             int64_t oi = round_shift_even(acc_i, shift), oq = round_shift_even(acc_q, shift);
             oi = oi > 32767 ? 32767 : oi < -32768 ? -32768 : oi;
@@ -401,4 +406,10 @@ void oracle_demodulate(int64_t n_traces, int64_t n_in, const int16_t* s, const i
             out[(n_traces + tr) * n_out + m] = (int16_t)oq;
         }
     }
+}
+
+/* The same with real taps. */
+void oracle_demodulate(int64_t n_traces, int64_t n_in, const int16_t* s, const int16_t* h, int64_t n_taps,
+                       int64_t shift, int64_t decimation, int64_t n_out, int16_t* out) {
+    oracle_demodulate_complex(n_traces, n_in, s, h, NULL, n_taps, shift, decimation, n_out, out);
 }

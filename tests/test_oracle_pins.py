@@ -595,3 +595,43 @@ def test_iq_beamforming_at_a_quarter_sample_delay():
     assert abs(got - (0.75 + 0.25j) * rot) <= 1e-12
     got = oracle.das(g, b, interp="cubic").ravel()[0]
     assert abs(got - (114 + 38j) / 128 * rot) <= 1e-12
+
+
+# ------------------------------------- complex matched-filter taps (Eq. demod)
+
+def test_demod_complex_impulse_response_by_hand():
+    # impulse A at raw index n0; the mixer e^{-j pi n0 / 2} gives A, -jA, -A, jA
+    # for n0 mod 4 = 0..3; the complex product with h = hr + j hi then gives
+    # (I, Q) = (hr A, hi A), (hi A, -hr A), (-hr A, -hi A), (-hi A, hr A)
+    hr = np.array([3, -7, 11, 2, -5, 9], dtype=np.int16)
+    hi = np.array([-4, 6, 1, -8, 10, -2], dtype=np.int16)
+    A = 5
+    want = {0: lambda r, i: (r * A, i * A), 1: lambda r, i: (i * A, -r * A),
+            2: lambda r, i: (-r * A, -i * A), 3: lambda r, i: (-i * A, r * A)}
+    for n0 in (12, 13, 14, 15):
+        s = np.zeros((1, 48), dtype=np.int16)
+        s[0, n0] = A
+        iq = oracle.demodulate(s, hr, shift=0, decimation=1, taps_imag=hi)
+        for m in range(48):
+            k = m - n0
+            wi, wq = want[n0 % 4](int(hr[k]), int(hi[k])) if 0 <= k < hr.size else (0, 0)
+            assert (iq[0, 0, m], iq[1, 0, m]) == (wi, wq), (n0, m)
+
+
+def test_demod_taps_times_j_rotate_the_output_by_a_quarter_turn():
+    # taps j h (hr = 0, hi = h) give j times the output of the real taps h:
+    # (I, Q) -> (-Q, I), exactly when nothing is rounded or saturated
+    # (|h| <= 10 over 31 taps and |s| <= 50 keep every sum below 2^15: no saturation)
+    rng = np.random.default_rng(23)
+    h = rng.integers(-10, 11, size=31).astype(np.int16)
+    s = rng.integers(-50, 51, size=(3, 400)).astype(np.int16)
+    real = oracle.demodulate(s, h, shift=0, decimation=4)
+    rot = oracle.demodulate(s, np.zeros_like(h), shift=0, decimation=4, taps_imag=h)
+    np.testing.assert_array_equal(rot[0], -real[1])
+    np.testing.assert_array_equal(rot[1], real[0])
+    # and a general complex tap set is the sum of its real and imaginary parts' outputs
+    h2 = rng.integers(-10, 11, size=31).astype(np.int16)
+    both = oracle.demodulate(s, h2, shift=0, decimation=4, taps_imag=h)
+    part = oracle.demodulate(s, h2, shift=0, decimation=4)
+    np.testing.assert_array_equal(both[0].astype(int), part[0].astype(int) - real[1].astype(int))
+    np.testing.assert_array_equal(both[1].astype(int), part[1].astype(int) + real[0].astype(int))
