@@ -204,6 +204,11 @@ typedef struct rcbf_params {
      * 0 / 0 = the plan's channels are the whole array. */
     uint32_t rx_channel_offset;
     uint32_t rx_channels_total;
+    /* Imaginary parts of complex demodulation taps h = demod_taps + j demod_taps_imag (a
+     * baseband matched filter that also applies a phase correction, §OPTIMIZATIONS
+     * "Filtering & Demodulation"): HOST pointer to demod_n_taps int16 values, copied by
+     * rcbf_plan; NULL = real taps. With complex taps sum |h_re| + sum |h_im| <= 65535. */
+    const int16_t* demod_taps_imag;
 } rcbf_params;
 
 typedef struct rcbf_plan_s*  rcbf_plan_t;
@@ -254,6 +259,27 @@ void rcbf_destroy(rcbf_plan_t plan);
  *   iq  device int16 [2][n_tx][n_ch][n_samples]: I plane, then Q plane
  * Errors: RCBF_EINVAL (NULL, misaligned, plan without demodulation), RCBF_ECUDA. */
 int rcbf_demodulate(rcbf_plan_t plan, const int16_t* rf, int16_t* iq, void* stream);
+
+/* rcbf_demod_decode — rcbf_demodulate followed by rcbf_decode in one kernel,
+ * the demodulation fused into the decode's load (§OPTIMIZATIONS "Filtering &
+ * Demodulation": the raw samples are filtered and decimated from shared
+ * memory before anything else; Eq. (demodulation); §OPTIMIZATIONS
+ * "Decoding"). Per channel and block of 64 demodulated samples, the raw
+ * window of every acquisition is staged once in shared memory, the FIR with
+ * the quadrature mixer (real or complex taps) gives the int16 I and Q samples
+ * with the same rounding and saturation as rcbf_demodulate, and the exact
+ * split-byte tensor-core decode turns them into both decoded planes; the
+ * demodulated planes never reach device memory. The result equals
+ * rcbf_demodulate then rcbf_decode bit for bit.
+ *   rf       device int16 [n_tx][n_ch][n_samples * D] (raw, Hadamard-encoded)
+ *   decoded  device float32 [2][n_tx][n_ch][n_samples]: D / N of the I plane,
+ *            then of the Q plane (RCBF_CF32)
+ * Needs a plan with demodulation, a Hadamard order, decoded_dtype RCBF_CF32,
+ * D = demod_decimation 4 or 8, n_tx in {32, 64, 128} and a raw window
+ * (64 D + 32 ceil(ceil(n_taps / 4) / 8) samples per acquisition) that fits
+ * shared memory. Errors: RCBF_EINVAL (NULL, misaligned), RCBF_EUNSUPPORTED
+ * (plan or sizes outside that set), RCBF_ECUDA. */
+int rcbf_demod_decode(rcbf_plan_t plan, const int16_t* rf, float* decoded, void* stream);
 
 /* rcbf_decode — D = H^T S over the transmit axis (§THEORY "Synthetic Aperture
  * Imaging": decoded data behaves as one transmit per element; §OPTIMIZATIONS

@@ -65,6 +65,7 @@ class Params(ctypes.Structure):
         ("tx_wave", ctypes.c_uint32), ("reserved3", ctypes.c_uint32),
         ("tx_focus", ctypes.c_double), ("tx_angles", ctypes.c_void_p),
         ("rx_channel_offset", ctypes.c_uint32), ("rx_channels_total", ctypes.c_uint32),
+        ("demod_taps_imag", ctypes.c_void_p),
     ]
 
 
@@ -91,6 +92,7 @@ SIGNATURES = {
     "rcbf_destroy": (None, [_P]),
     "rcbf_plan_query": (ctypes.c_int, [_P, ctypes.POINTER(PlanInfo)]),
     "rcbf_decode": (ctypes.c_int, [_P, _P, _P, _P]),
+    "rcbf_demod_decode": (ctypes.c_int, [_P, _P, _P, _P]),
     "rcbf_demodulate": (ctypes.c_int, [_P, _P, _P, _P]),
     "rcbf_das": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, _P, _P]),
     "rcbf_das_backward": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, _P, _P, _P, _P, _P]),
@@ -155,8 +157,9 @@ def make_params(g, decoded_dtype="f32", decode_variant=DECODE_MMA_I8, das_varian
     n_ch, n_samples, fs, c, t0, fc, pitches, orientations, hadamard_order,
     out_dims, out_min, out_max, f_number, optionally interp: 'linear' or
     'cubic', iq_freq; the arguments override them). demod = (decimation,
-    int16 taps, shift) adds the quadrature demodulation stage; the geometry
-    then describes the demodulated data (n_samples, fs, t0)."""
+    int16 taps, shift[, int16 imaginary taps]) adds the quadrature
+    demodulation stage (complex taps when the fourth item is given); the
+    geometry then describes the demodulated data (n_samples, fs, t0)."""
     p = Params()
     p.n_tx, p.n_ch, p.n_samples = int(g.n_tx), int(g.n_ch), int(g.n_samples)
     p.hadamard_order = int(getattr(g, "hadamard_order", 0))
@@ -189,11 +192,17 @@ def make_params(g, decoded_dtype="f32", decode_variant=DECODE_MMA_I8, das_varian
         p._angles = ang         # kept alive until rcbf_plan copies it
     if demod is not None:
         import numpy as np
-        dec, taps, shift = demod
+        dec, taps, shift = demod[:3]
         taps = np.ascontiguousarray(taps, dtype=np.int16)
         p.demod_decimation, p.demod_n_taps, p.demod_shift = int(dec), int(taps.size), int(shift)
         p.demod_taps = taps.ctypes.data
         p._taps = taps          # kept alive until rcbf_plan copies it
+        if len(demod) > 3 and demod[3] is not None:
+            taps_im = np.ascontiguousarray(demod[3], dtype=np.int16)
+            if taps_im.size != taps.size:
+                raise ValueError("the imaginary taps need the length of the real taps")
+            p.demod_taps_imag = taps_im.ctypes.data
+            p._taps_im = taps_im
     if xdc_transform is not None:
         for k, v in enumerate([float(x) for row in xdc_transform for x in row]):
             p.xdc_transform[k] = v
@@ -218,6 +227,7 @@ class Plan:
         _check(lib.rcbf_plan(ctypes.byref(params), ctypes.byref(h)))
         params.decode_matrix = None
         params.demod_taps = None
+        params.demod_taps_imag = None
         params.tx_angles = None
         self.handle = h
         self.params = params
@@ -274,6 +284,15 @@ class Plan:
         if out is None:
             out = torch.empty((2,) + self.rf_shape, dtype=torch.int16, device=rf.device)
         _check(load_library().rcbf_demodulate(self.handle, _ptr(rf), _ptr(out), _stream(stream)))
+        return out
+
+    def demod_decode(self, rf, out=None, stream=None):
+        """rcbf_demod_decode: raw int16 [n_tx][n_ch][n_s * D] -> decoded FP32 planes
+        [2][n_tx][n_ch][n_s] (demodulation fused into the decode)."""
+        import torch
+        if out is None:
+            out = torch.empty((2,) + self.rf_shape, dtype=torch.float32, device=rf.device)
+        _check(load_library().rcbf_demod_decode(self.handle, _ptr(rf), _ptr(out), _stream(stream)))
         return out
 
     def decode(self, rf, out=None, stream=None):

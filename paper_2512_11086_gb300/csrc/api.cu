@@ -168,8 +168,11 @@ int validate(const rcbf_params* p) {
         if (p->demod_shift < 0 || p->demod_shift > 30)
             return set_error(RCBF_EINVAL, "rcbf_plan: demod_shift must be in [0, 30]");
         long long l1 = 0;
-        for (uint32_t k = 0; k < p->demod_n_taps; ++k) l1 += std::llabs((long long)p->demod_taps[k]);
-        if (l1 > 65535) return set_error(RCBF_EINVAL, "rcbf_plan: sum |taps| must be <= 65535");
+        for (uint32_t k = 0; k < p->demod_n_taps; ++k) {
+            l1 += std::llabs((long long)p->demod_taps[k]);
+            if (p->demod_taps_imag) l1 += std::llabs((long long)p->demod_taps_imag[k]);
+        }
+        if (l1 > 65535) return set_error(RCBF_EINVAL, "rcbf_plan: sum |taps| (real and imaginary parts) must be <= 65535");
         if ((double)p->n_samples * p->demod_decimation > (double)(1u << 24))
             return set_error(RCBF_EINVAL, "rcbf_plan: raw trace too long");
     }
@@ -455,6 +458,7 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
     h.p = *params;
     h.p.decode_matrix = nullptr;   // the matrix is copied, never referenced later
     h.p.demod_taps = nullptr;      // so are the taps
+    h.p.demod_taps_imag = nullptr;
     h.p.tx_angles = nullptr;       // and the plane-wave angles
     h.has_tx_angle0 = params->tx_angles != nullptr;
     h.tx_angle0 = params->tx_angles ? params->tx_angles[0] : 0.0;
@@ -491,6 +495,11 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
         if (cudaMalloc(&h.d_taps, bytes) != cudaSuccess) return fail(RCBF_ENOMEM, "rcbf_plan: cudaMalloc taps");
         if (cudaMemcpy(h.d_taps, params->demod_taps, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
             return fail(RCBF_ECUDA, "rcbf_plan: copy taps");
+        if (params->demod_taps_imag) {
+            if (cudaMalloc(&h.d_taps_im, bytes) != cudaSuccess) return fail(RCBF_ENOMEM, "rcbf_plan: cudaMalloc taps");
+            if (cudaMemcpy(h.d_taps_im, params->demod_taps_imag, bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(RCBF_ECUDA, "rcbf_plan: copy taps");
+        }
     }
     if (p.hadamard_order) {
         const int n = (int)p.n_tx;
@@ -519,6 +528,11 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
                 return fail(RCBF_ECUDA, "rcbf_plan: copy sums");
         }
         if ((rc = configure_decode(h)) != RCBF_OK) { std::string m = g_last_error; rcbf_destroy(plan); return set_error(rc, m); }
+        if (p.demod_decimation && (rc = configure_demod_decode(h)) != RCBF_OK) {
+            std::string m = g_last_error;
+            rcbf_destroy(plan);
+            return set_error(rc, m);
+        }
     }
     if ((rc = configure_das(h)) != RCBF_OK) { std::string m = g_last_error; rcbf_destroy(plan); return set_error(rc, m); }
     {
@@ -556,7 +570,7 @@ int rcbf_plan_query(rcbf_plan_t plan, rcbf_plan_info* info) {
         bytes += n * n + n * sizeof(int);
         if (n % 32 == 0) bytes += 2 * (n / 16) * (n / 32) * 32 * 16 + (n / 16) * (n / 16) * 32 * 16 / 2;
     }
-    if (h.p.demod_decimation) bytes += (uint64_t)h.p.demod_n_taps * sizeof(int16_t);
+    if (h.p.demod_decimation) bytes += (uint64_t)h.p.demod_n_taps * sizeof(int16_t) * (h.d_taps_im ? 2 : 1);
     info->workspace_bytes = bytes;
     int mode = 0;
     DasArgs b = a;
@@ -584,6 +598,7 @@ void rcbf_destroy(rcbf_plan_t plan) {
     if (h.d_status) cudaFree(h.d_status);
     if (h.d_partial) cudaFree(h.d_partial);
     if (h.d_taps) cudaFree(h.d_taps);
+    if (h.d_taps_im) cudaFree(h.d_taps_im);
     if (h.d_tx_dir) cudaFree(h.d_tx_dir);
     delete plan;
 }
@@ -604,6 +619,17 @@ int rcbf_decode(rcbf_plan_t plan, const int16_t* rf, void* decoded, void* stream
     if (!rf || !decoded) return set_error(RCBF_EINVAL, "rcbf_decode: NULL buffer");
     if (!aligned16(rf) || !aligned16(decoded)) return set_error(RCBF_EINVAL, "rcbf_decode: buffers must be 16-byte aligned");
     return launch_decode(h, rf, decoded, static_cast<cudaStream_t>(stream));
+}
+
+int rcbf_demod_decode(rcbf_plan_t plan, const int16_t* rf, float* decoded, void* stream) {
+    if (!plan) return set_error(RCBF_EINVAL, "rcbf_demod_decode: plan is NULL");
+    const PlanHost& h = plan->h;
+    if (!rf || !decoded) return set_error(RCBF_EINVAL, "rcbf_demod_decode: NULL buffer");
+    if (!aligned16(rf) || !aligned16(decoded))
+        return set_error(RCBF_EINVAL, "rcbf_demod_decode: buffers must be 16-byte aligned");
+    std::string why;
+    if (!demod_decode_supported(h, &why)) return set_error(RCBF_EUNSUPPORTED, why);
+    return launch_demod_decode(h, rf, decoded, static_cast<cudaStream_t>(stream));
 }
 
 int rcbf_das(rcbf_plan_t plan, const void* decoded, const float* apod, float c, float* image, void* stream) {

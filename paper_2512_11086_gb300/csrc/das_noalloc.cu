@@ -71,6 +71,7 @@ extern "C" int rcbf_das_noalloc(const rcbf_params* params, const void* decoded, 
     h.p = *params;
     h.p.decode_matrix = nullptr;
     h.p.demod_taps = nullptr;
+    h.p.demod_taps_imag = nullptr;
     h.p.tx_angles = nullptr;
     plan_geometry(h);
     if (h.p.das_variant == RCBF_DAS_TILED && !h.tiled_ok)

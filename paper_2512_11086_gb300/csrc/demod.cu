@@ -10,7 +10,9 @@
 // (kDemodOut outputs need about kDemodOut * D + N_f samples, loaded and
 // converted once, zero outside the record: the paper's LDS reuse) and every
 // thread computes four outputs, sharing each tap load between them.
-// Accumulation is exact in 32 bits (sum |h| <= 65535 is checked at plan time).
+// Complex taps h + j hq (a matched filter with a phase correction) add the
+// sums of hq. Accumulation is exact in 32 bits (sum |h| + sum |hq| <= 65535 is
+// checked at plan time).
 #include "internal.cuh"
 
 namespace rcbf {
@@ -37,20 +39,26 @@ __device__ __forceinline__ int16_t round_shift_sat(int acc, int shift) {
 // a tap k = a D + b the 32 threads of a warp (consecutive outputs, inputs D
 // apart) read consecutive words of one row: no bank conflicts.
 // grid: (traces, segments of kDemodOut outputs)
+template <bool CPLX>
 __global__ void __launch_bounds__(kDemodThreads)
 demod_kernel(const int16_t* __restrict__ rf, int16_t* __restrict__ iq, const int16_t* __restrict__ taps,
-             int n_taps, int shift, int D, int Q, long long n_in, long long n_out, long long n_traces) {
+             const int16_t* __restrict__ taps_im, int n_taps, int shift, int D, int Q, long long n_in,
+             long long n_out, long long n_traces) {
     extern __shared__ int sm[];
     const int n_taps2 = (n_taps + 1) & ~1;                     // even, zero-padded
     const int PD = (n_taps2 - 1 + D - 1) / D;                  // rows of history before the first output
-    int* h = sm;                                               // [n_taps2]
-    int* e_ph = sm + n_taps2;                                  // [D][Q]
+    int* h = sm;                                               // [n_taps2] real parts
+    int* hq = sm + n_taps2;                                    // [n_taps2] imaginary parts (complex taps)
+    int* e_ph = sm + (CPLX ? 2 : 1) * n_taps2;                 // [D][Q]
     const long long tr = blockIdx.x;
     const long long m0 = (long long)blockIdx.y * kDemodOut;
     const long long base = (m0 - PD) * D;                      // input index of e[0]
     const int L = (kDemodOut + PD) * D;                        // staged samples, D * (rows used)
     const int16_t* x = rf + tr * n_in;
-    for (int k = threadIdx.x; k < n_taps2; k += kDemodThreads) h[k] = k < n_taps ? (int)taps[k] : 0;
+    for (int k = threadIdx.x; k < n_taps2; k += kDemodThreads) {
+        h[k] = k < n_taps ? (int)taps[k] : 0;
+        if (CPLX) hq[k] = k < n_taps ? (int)taps_im[k] : 0;
+    }
     for (int p = threadIdx.x; p < L; p += kDemodThreads) {
         const long long n = base + p;
         int v = 0;
@@ -64,26 +72,37 @@ demod_kernel(const int16_t* __restrict__ rf, int16_t* __restrict__ iq, const int
     __syncthreads();
     // output m (local index mi = m - m0) and tap k = a D + b read
     // e[(mi + PD) D - k] = e_ph[b ? D - b : 0][mi + PD - a - (b ? 1 : 0)]
-    int acc_even[kDemodPer], acc_odd[kDemodPer];
+    // sums over the even and the odd taps k, of the real parts h and (complex
+    // taps) of the imaginary parts hq
+    int acc_even[kDemodPer], acc_odd[kDemodPer], accq_even[kDemodPer], accq_odd[kDemodPer];
 #pragma unroll
-    for (int r = 0; r < kDemodPer; ++r) acc_even[r] = acc_odd[r] = 0;
+    for (int r = 0; r < kDemodPer; ++r) acc_even[r] = acc_odd[r] = accq_even[r] = accq_odd[r] = 0;
     const int astep = (D & 1) ? 2 : 1;                         // odd D: the parity of k alternates with a
     for (int b = 0; b < D; ++b) {
         const int* row = e_ph + (b ? D - b : 0) * Q + PD - (b ? 1 : 0) + threadIdx.x;
         for (int a0 = 0; a0 < astep; ++a0) {
-            int acc[kDemodPer];
+            int acc[kDemodPer], accq[kDemodPer];
 #pragma unroll
-            for (int r = 0; r < kDemodPer; ++r) acc[r] = 0;
+            for (int r = 0; r < kDemodPer; ++r) acc[r] = accq[r] = 0;
             for (int a = a0; a * D + b < n_taps2; a += astep) {
                 const int hk = h[a * D + b];
+                const int hqk = CPLX ? hq[a * D + b] : 0;
 #pragma unroll
-                for (int r = 0; r < kDemodPer; ++r) acc[r] += hk * row[kDemodThreads * r - a];
+                for (int r = 0; r < kDemodPer; ++r) {
+                    const int e = row[kDemodThreads * r - a];
+                    acc[r] += hk * e;
+                    if (CPLX) accq[r] += hqk * e;
+                }
             }
             const bool odd = ((a0 * D + b) & 1) != 0;         // parity of every k of this loop
 #pragma unroll
             for (int r = 0; r < kDemodPer; ++r) {
                 acc_even[r] += odd ? 0 : acc[r];
                 acc_odd[r] += odd ? acc[r] : 0;
+                if (CPLX) {
+                    accq_even[r] += odd ? 0 : accq[r];
+                    accq_odd[r] += odd ? accq[r] : 0;
+                }
             }
         }
     }
@@ -91,10 +110,14 @@ demod_kernel(const int16_t* __restrict__ rf, int16_t* __restrict__ iq, const int
     for (int r = 0; r < kDemodPer; ++r) {
         const long long m = m0 + threadIdx.x + kDemodThreads * r;
         if (m >= n_out) continue;
-        // n = m D: even n takes I from the even taps, odd n from the odd ones
+        // n = m D: a mixed sample n - k is real (re) for n - k even, imaginary
+        // (im) for odd; (h + j hq)(re + j im): I = sum h re - sum hq im,
+        // Q = sum h im + sum hq re
         const bool even = ((m * D) & 1) == 0;
-        const int ai = even ? acc_even[r] : acc_odd[r];
-        const int aq = even ? acc_odd[r] : acc_even[r];
+        const int re_h = even ? acc_even[r] : acc_odd[r], im_h = even ? acc_odd[r] : acc_even[r];
+        const int re_q = even ? accq_even[r] : accq_odd[r], im_q = even ? accq_odd[r] : accq_even[r];
+        const int ai = CPLX ? re_h - im_q : re_h;
+        const int aq = CPLX ? im_h + re_q : im_h;
         iq[tr * n_out + m] = round_shift_sat(ai, shift);
         iq[(n_traces + tr) * n_out + m] = round_shift_sat(aq, shift);
     }
@@ -109,12 +132,14 @@ int launch_demodulate(const PlanHost& h, const int16_t* rf, int16_t* iq, cudaStr
     const int n_taps2 = (n_taps + 1) & ~1;
     const int PD = (n_taps2 - 1 + D - 1) / D;
     const int Q = (kDemodOut + PD) | 1;          // row length (odd: rows start in different banks)
-    const size_t smem = (size_t)(n_taps2 + D * Q) * sizeof(int);
-    if (cudaFuncSetAttribute(demod_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    const bool cplx = h.d_taps_im != nullptr;
+    const size_t smem = (size_t)((cplx ? 2 : 1) * n_taps2 + D * Q) * sizeof(int);
+    auto k = cplx ? demod_kernel<true> : demod_kernel<false>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return check_launch("demodulate: set shared memory");
     dim3 grid((unsigned)n_traces, (unsigned)((n_out + kDemodOut - 1) / kDemodOut));
-    demod_kernel<<<grid, kDemodThreads, smem, s>>>(rf, iq, h.d_taps, n_taps, (int)h.p.demod_shift, D, Q, n_in,
-                                                    n_out, n_traces);
+    k<<<grid, kDemodThreads, smem, s>>>(rf, iq, h.d_taps, h.d_taps_im, n_taps, (int)h.p.demod_shift, D, Q, n_in,
+                                        n_out, n_traces);
     return check_launch("demod_kernel");
 }
 

@@ -113,6 +113,7 @@ struct PlanHost {
     float* d_partial;       // DAS partial images (channel split), plan-owned
     size_t partial_floats;
     int16_t* d_taps;        // device demodulation FIR taps (demod_decimation > 0)
+    int16_t* d_taps_im;     // their imaginary parts (complex taps), else nullptr
     float2* d_tx_dir;       // device plane-wave directions (tx_wave == RCBF_TX_PLANE)
     bool has_tx_angle0;     // tx_angle0 holds the first plane-wave angle (the params' pointer is not kept)
     double tx_angle0;
@@ -165,6 +166,10 @@ struct TcJob {
     unsigned grid;
 };
 int decode_tc_prepare(const PlanHost& h, int dtype, const int16_t* rf, void* out, TcJob* job);
+// Demodulation fused into the decode (demod_decode.cu).
+bool demod_decode_supported(const PlanHost& h, std::string* why);
+int configure_demod_decode(const PlanHost& h);
+int launch_demod_decode(const PlanHost& h, const int16_t* rf, float* out, cudaStream_t s);
 int decode_tc_run(const TcJob& job, int* status, long long wait_ns, cudaStream_t s);
 // Device address of a batch's status word (batch.cu).
 int* batch_status_word(rcbf_batch_t batch);
