@@ -288,7 +288,8 @@ OTHER_WORKLOADS = {
     "hercules2d": "HERCULES 2D receive aperture (non-separable delays, tiled form): decoded FP16 128 rows x 128 "
                   "columns x 2048 samples, one plane wave -> 128x128x256 FP32 voxels",
     "iq": "IQ pipeline: FORCES 128 tx x 128 ch x 4096 int16 at 4 f_d -> quadrature demodulation (166-tap "
-          "integer FIR, decimation 4) -> exact decode of both planes -> cubic IQ DAS to 512x1024 (complex)",
+          "integer FIR, decimation 4) fused with the exact decode of both planes -> cubic IQ DAS to 512x1024 "
+          "(complex)",
 }
 
 
@@ -466,6 +467,66 @@ def measure_autofocus(args, parity: bool = True) -> dict:
     return line
 
 
+def measure_iq(args, parity: bool = True) -> dict:
+    """The IQ pipeline on the B-scan acquisition (128 x 128 x 4096 int16 at
+    4 f_d): quadrature demodulation (166-tap FIR, D = 4) fused into the exact
+    decode of both planes (one launch), then the cubic IQ DAS. The stages are
+    also timed apart, beside the unfused demodulate + decode. Parity stamp: the
+    fused decoded planes bit for bit against oracle.demodulate then
+    oracle.decode, and the image at sampled voxels against the oracle's IQ DAS
+    of those planes."""
+    import torch
+    import paper_2512_11086_gb300 as rc
+    import synth
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    fr = synth.full_bscan(2)
+    g_raw = fr.geometry
+    D, taps, shift = 4, synth.lowpass_taps(166, 0.12, shift=14), 14
+    gd = (taps.size - 1) / 2
+    g = dataclasses.replace(g_raw, n_samples=g_raw.n_samples // D, fs=g_raw.fs / D,
+                            t0=g_raw.t0 - gd / g_raw.fs, iq_freq=g_raw.fs / 4, interp="cubic")
+    plan = rc.Plan(rc.make_params(g, decoded_dtype="cf32", demod=(D, taps, shift)))
+    rf = torch.from_numpy(fr.rf).to(dev)
+    iq = torch.empty((2,) + plan.rf_shape, dtype=torch.int16, device=dev)
+    dec = torch.empty((2,) + plan.rf_shape, dtype=torch.float32, device=dev)
+    out = torch.empty((2,) + plan.image_shape, device=dev)
+
+    def step():
+        plan.demod_decode(rf, out=dec)
+        plan.das(dec, out=out)
+
+    ms, clk = _time_steps(step, args.steps, args.warmup, stream)
+    stages = {"demod_decode_fused": lambda: plan.demod_decode(rf, out=dec),
+              "demodulate": lambda: plan.demodulate(rf, out=iq),
+              "decode_two_planes": lambda: plan.decode(iq, out=dec),
+              "iq_das_cubic": lambda: plan.das(dec, out=out)}
+    stage_ms = {k: _time_steps(f, max(3, min(args.steps, 10)), 2, stream)[0] for k, f in stages.items()}
+    rec = {"workload": OTHER_WORKLOADS["iq"], "value": g.sums / (ms * 1e-3) / 1e9, "unit": UNIT,
+           "ms_per_step": ms, "stage_ms": stage_ms,
+           "unfused_demod_plus_decode_ms": stage_ms["demodulate"] + stage_ms["decode_two_planes"],
+           "sums": "complex voxel x channel x transmit sums of the IQ DAS",
+           "form": "rcbf_demod_decode (demodulation fused into the decode's load) + cubic IQ DAS",
+           "plan": plan.info(), "clocks": clk}
+    if parity:
+        import oracle
+        plan.demod_decode(rf, out=dec)
+        torch.cuda.synchronize()
+        got = dec.cpu().numpy()
+        iq_o = oracle.demodulate(fr.rf, taps, shift, D)
+        want = np.stack([oracle.decoded_as(oracle.decode(iq_o[p]), g.n_tx, "f32") for p in range(2)])
+        plan.das(dec, out=out)
+        torch.cuda.synchronize()
+        img = out.cpu().numpy().astype(np.float64)
+        img = (img[0] + 1j * img[1]).ravel()
+        vox = np.sort(np.random.default_rng(3).choice(g.n_vox, size=512, replace=False))
+        ref = oracle.das(g, want[0].astype(np.float64) + 1j * want[1].astype(np.float64), voxels=vox)
+        rec["parity"] = {"demod_decode_bit_exact": bool(np.array_equal(got, want)),
+                         "iq_das_rel_l2": rel_l2(img[vox], ref), "tol": 1e-4, "voxels": int(vox.size),
+                         "reference": "oracle.demodulate then oracle.decode (bit for bit); FP64 IQ DAS"}
+    return rec
+
+
 def run_other_workload(args):
     """Another configuration on its own line, timed like the headline (CUDA
     events, warm-up, clocks)."""
@@ -476,8 +537,9 @@ def run_other_workload(args):
     rbuild.build()
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
-    if args.workload in ("volume", "stream", "autofocus"):
-        rec = measure_autofocus(args) if args.workload == "autofocus" else measure_batched(args.workload, args)
+    if args.workload in ("volume", "stream", "autofocus", "iq"):
+        rec = (measure_autofocus(args) if args.workload == "autofocus" else
+               measure_iq(args) if args.workload == "iq" else measure_batched(args.workload, args))
         value, ms, clk = rec.pop("value"), rec.pop("ms_per_step"), rec.pop("clocks")
         rec.pop("unit")
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -501,40 +563,6 @@ def run_other_workload(args):
         sums = g.sums
         extra["plan"] = plan.info()
         extra["data"] = "seeded Gaussian decoded samples (timing only)"
-    else:
-        fr = synth.full_bscan(2)
-        g_raw = fr.geometry
-        D, taps, shift = 4, synth.lowpass_taps(166, 0.12, shift=14), 14
-        gd = (taps.size - 1) / 2
-        g = dataclasses.replace(g_raw, n_samples=g_raw.n_samples // D, fs=g_raw.fs / D,
-                                t0=g_raw.t0 - gd / g_raw.fs, iq_freq=g_raw.fs / 4, interp="cubic")
-        plan = rc.Plan(rc.make_params(g, decoded_dtype="cf32", demod=(D, taps, shift)))
-        rf = torch.from_numpy(fr.rf).to(dev)
-        iq = torch.empty((2,) + plan.rf_shape, dtype=torch.int16, device=dev)
-        dec = torch.empty((2,) + plan.rf_shape, dtype=torch.float32, device=dev)
-        out = torch.empty((2,) + plan.image_shape, device=dev)
-
-        def step():
-            plan.demodulate(rf, out=iq)
-            plan.decode(iq, out=dec)
-            plan.das(dec, out=out)
-        sums = g.sums
-        for _ in range(3):
-            step()
-        ev = _events(4)
-        torch.cuda.synchronize()
-        ev[0].record(stream)
-        plan.demodulate(rf, out=iq)
-        ev[1].record(stream)
-        plan.decode(iq, out=dec)
-        ev[2].record(stream)
-        plan.das(dec, out=out)
-        ev[3].record(stream)
-        torch.cuda.synchronize()
-        extra["stage_ms"] = {"demodulate": ev[0].elapsed_time(ev[1]), "decode_two_planes": ev[1].elapsed_time(ev[2]),
-                             "iq_das_cubic": ev[2].elapsed_time(ev[3])}
-        extra["sums"] = "complex voxel x channel x transmit sums of the IQ DAS"
-        extra["plan"] = plan.info()
     ms, clk = _time_steps(step, args.steps, args.warmup, stream)
     line = {"metric": METRIC, "value": sums / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -1018,6 +1046,7 @@ def main():
             "volume": measure_batched("volume", args, parity=not args.no_cpu_baseline),
             "stream": measure_batched("stream", args, parity=not args.no_cpu_baseline),
             "autofocus": measure_autofocus(args, parity=not args.no_cpu_baseline),
+            "iq": measure_iq(args, parity=not args.no_cpu_baseline),
         }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, det = cpu_baseline(frame, gpu_image=last_image, gpu_decoded=last_decoded)

@@ -19,10 +19,10 @@
 // Per tile: (1) all threads stage the raw window x[k][c][m0 D - HALO ..
 // m0 D + 64 D) of every acquisition k in shared memory, polyphase and
 // transposed ([phase][q][k], k fastest), zero outside the record; (2) thread
-// (k, output group) computes its OPT outputs of row k by a register-blocked
+// (k, output group) computes its N / 8 outputs of row k by a register-blocked
 // convolution: for each tap class r = k mod 4 the taps a[4v + r] run over a
 // window of phase-(-r mod 4) samples held in registers, so one shared load
-// feeds up to 8 taps x OPT outputs; (3) the I and Q int16 outputs form one
+// feeds up to 8 taps x N / 8 outputs; (3) the I and Q int16 outputs form one
 // 128-column staged tile (I in columns 0-63, Q in 64-127) that the exact
 // split-byte FP16 tensor-core decode (as in decode_mma_f16_kernel) turns into
 // D / n for both planes, written as the two FP32 planes of RCBF_CF32.
@@ -32,7 +32,8 @@ namespace rcbf {
 
 namespace {
 
-constexpr int kFdThreads = 256;
+constexpr int kFdThreads = 512;
+constexpr int kFdDecodeWarps = 8;     // warps of the decode step (the mma.sync layout of 8 warps)
 constexpr int kFdOut = 64;            // demodulated samples per tile
 constexpr int kFdTapBlock = 8;        // taps of one class per register window
 
@@ -78,7 +79,7 @@ demod_decode_kernel(const int16_t* __restrict__ rf, float* __restrict__ out, con
                     const int16_t* __restrict__ taps_im, const uint32_t* __restrict__ afrag16,
                     const int* __restrict__ hsum, int n_taps, int shift, int D, int n_ch, int n_s, float inv_n) {
     using DC = DecodeCfg<N>;
-    constexpr int OPT = N / 4;                                 // outputs per thread and component
+    constexpr int OPT = kFdOut * N / kFdThreads;               // outputs per thread and component
     constexpr int GROUPS = kFdThreads / N;                     // output groups of a row
     static_assert(OPT * GROUPS == kFdOut, "tile split");
     extern __shared__ __align__(128) unsigned char smem[];
@@ -110,38 +111,59 @@ demod_decode_kernel(const int16_t* __restrict__ rf, float* __restrict__ out, con
     const int o0 = grp * OPT;
     const uint32_t sb = smem_u32(stage);
 
-    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int c = (int)(tile / n_blocks);
-        const int m0 = (int)(tile % n_blocks) * kFdOut;
-        const long long w0 = (long long)m0 * D - L.halo;       // raw index of window sample 0 (multiple of 8)
-        __syncthreads();                                       // previous tile's stage and raw buffers free
-        // ---- (1) raw window, polyphase and transposed: raw[(p * ql + q) * N + k] = x[w0 + 4q + p]
-        {
-            const int chunks = L.wl / 8;                       // 16-byte chunks per row
-            for (int t = tid; t < N * chunks; t += kFdThreads) {
-                const int k = t % N, ch = t / N;
-                const long long i0 = w0 + 8LL * ch;
-                const int16_t* src = rf + ((long long)k * n_ch + c) * n_in;
-                uint32_t wv[4] = {0u, 0u, 0u, 0u};
-                if (i0 >= 0 && i0 + 8 <= n_in) {
-                    const int4 v = __ldg(reinterpret_cast<const int4*>(src + i0));
-                    wv[0] = (uint32_t)v.x; wv[1] = (uint32_t)v.y; wv[2] = (uint32_t)v.z; wv[3] = (uint32_t)v.w;
-                } else {
+    // ---- (1) raw window of a tile, polyphase and transposed: raw[(p * ql + q) * N + k] =
+    // x[w0 + 4q + p], by threads tix of nthr. Each thread first loads up to 8 of its 16-byte
+    // chunks, then scatters them, so that its global loads are in flight together.
+    auto stage_raw = [&](long long tl, int tix, int nthr) {
+        const int c = (int)(tl / n_blocks);
+        const long long w0 = (long long)((int)(tl % n_blocks) * kFdOut) * D - L.halo;   // multiple of 8
+        const int chunks = L.wl / 8;                           // 16-byte chunks per row
+        const int total = N * chunks;
+        for (int t0 = 0; t0 < total; t0 += 8 * nthr) {
+            uint32_t wv[8][4];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const uint32_t u = (i0 + e >= 0 && i0 + e < n_in) ? (uint32_t)(uint16_t)src[i0 + e] : 0u;
-                        wv[e >> 1] |= u << (16 * (e & 1));
+            for (int u = 0; u < 8; ++u) {
+                const int t = t0 + tix + u * nthr;
+                wv[u][0] = wv[u][1] = wv[u][2] = wv[u][3] = 0u;
+                if (t < total) {
+                    const int k = t % N, ch = t / N;
+                    const long long i0 = w0 + 8LL * ch;
+                    const int16_t* src = rf + ((long long)k * n_ch + c) * n_in;
+                    if (i0 >= 0 && i0 + 8 <= n_in) {
+                        const int4 v = __ldg(reinterpret_cast<const int4*>(src + i0));
+                        wv[u][0] = (uint32_t)v.x; wv[u][1] = (uint32_t)v.y;
+                        wv[u][2] = (uint32_t)v.z; wv[u][3] = (uint32_t)v.w;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const uint32_t w = (i0 + e >= 0 && i0 + e < n_in) ? (uint32_t)(uint16_t)src[i0 + e] : 0u;
+                            wv[u][e >> 1] |= w << (16 * (e & 1));
+                        }
                     }
                 }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int t = t0 + tix + u * nthr;
+                if (t >= total) break;
+                const int k = t % N, ch = t / N;
                 // samples 8 ch + e -> phase e % 4, q = 2 ch + e / 4
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    const int16_t val = (int16_t)((wv[e >> 1] >> (16 * (e & 1))) & 0xFFFFu);
+                    const int16_t val = (int16_t)((wv[u][e >> 1] >> (16 * (e & 1))) & 0xFFFFu);
                     raw[((e & 3) * L.ql + 2 * ch + (e >> 2)) * N + k] = val;
                 }
             }
         }
-        __syncthreads();
+    };
+
+    // The decode of a tile reads only the staged tile, so while warps 0-7 decode tile t the
+    // other warps stage the raw window of the CTA's next tile.
+    if (blockIdx.x < n_tiles) stage_raw(blockIdx.x, tid, kFdThreads);
+    __syncthreads();
+    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int c = (int)(tile / n_blocks);
+        const int m0 = (int)(tile % n_blocks) * kFdOut;
         // ---- (2) FIR of row krow, outputs o0 .. o0 + OPT - 1 (tile-local), both components
         {
             int accI[OPT], accQ[OPT];
@@ -191,9 +213,12 @@ demod_decode_kernel(const int16_t* __restrict__ rf, float* __restrict__ out, con
                 srow[kFdOut + o0 + j] = valid ? fd_round_shift_sat(accQ[j], shift) : (int16_t)0;
             }
         }
-        __syncthreads();
+        __syncthreads();                                       // raw window consumed, staged tile ready
+        if (warp >= kFdDecodeWarps) {
+            const long long next = tile + gridDim.x;
+            if (next < n_tiles) stage_raw(next, tid - 32 * kFdDecodeWarps, kFdThreads - 32 * kFdDecodeWarps);
+        } else {
         // ---- (4) exact decode of the staged tile (split-byte FP16 mma.sync), two FP32 planes
-        {
             const int mg = warp % DC::MG, ng = warp / DC::MG;
             const int g = lane >> 2, t4 = lane & 3;
             constexpr int KF = N / 16;
@@ -256,6 +281,7 @@ demod_decode_kernel(const int16_t* __restrict__ rf, float* __restrict__ out, con
                 }
             }
         }
+        __syncthreads();                                       // staged tile decoded, next raw window staged
     }
 }
 
