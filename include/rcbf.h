@@ -376,15 +376,19 @@ int rcbf_plan_status(rcbf_plan_t plan, void* stream);
 int rcbf_plan_set_wait(rcbf_plan_t plan, uint64_t wait_ns, int32_t withhold);
 
 /* rcbf_batch_create — bind n_frames (plan, buffers) triples into one batch
- * that a single persistent kernel processes: for every frame with a
+ * that persistent kernels process: for every frame with a
  * Hadamard order, decode rf[f] into decoded[f] (with the plan's tensor-core
  * decode form; an RCBF_DECODE_TC frame by its own tcgen05 launch, enqueued by
- * rcbf_batch_run ahead of the persistent launch, the other forms as work
+ * rcbf_batch_run ahead of the persistent launches, the other forms as work
  * items of the persistent kernel), then DAS decoded[f] into images[f] (frames with
  * hadamard_order == 0 skip the decode and read decoded[f] directly). Plans
- * may differ in transmit count, samples, grid and orientation; all must use
- * decoded_dtype RCBF_F32 or RCBF_F16, the tiled DAS with no F# window, and
- * the same tile extent along u (tile[0]). Each frame is beamformed at its
+ * may differ in transmit count, samples, grid, orientation and tile; all
+ * must use decoded_dtype RCBF_F32 or RCBF_F16 and the tiled DAS with no F#
+ * window. Frames are grouped into phases by DAS window class (48, 64, 96 or
+ * 128 samples) and tile extent along u (tile[0]); each phase is one
+ * persistent launch, the later ones launched as programmatic dependents so
+ * that a phase's CTAs start on the SMs the previous phase frees at its tail
+ * (all frames of one class and tile extent: one launch). Each frame is beamformed at its
  * plan's speed of sound, without channel weights. The plans must outlive the
  * batch. Pointer arrays are HOST arrays of DEVICE pointers, copied; rf may be
  * NULL when no frame is encoded.
@@ -397,11 +401,12 @@ int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames,
                       const int16_t* const* rf, void* const* decoded,
                       float* const* images, rcbf_batch_t* out_batch);
 
-/* rcbf_batch_run — enqueue the whole batch as one persistent launch (plus a
- * counter reset, and one tcgen05 decode launch per RCBF_DECODE_TC frame) on `stream`. Contains no host synchronisation and no
- * allocation, so it can be captured in a CUDA graph. The persistent kernel's
- * waits on per-frame decode completion are bounded; on expiry it records
- * RCBF_ETIMEOUT in the batch's device status word (see rcbf_batch_status). */
+/* rcbf_batch_run — enqueue the whole batch on `stream`: a counter reset, one
+ * tcgen05 decode launch per RCBF_DECODE_TC frame, then one persistent launch
+ * per phase. Contains no host synchronisation and no allocation, so it can
+ * be captured in a CUDA graph. The persistent kernels' waits on per-frame
+ * decode completion are bounded; on expiry they record RCBF_ETIMEOUT in the
+ * batch's device status word (see rcbf_batch_status). */
 int rcbf_batch_run(rcbf_batch_t batch, void* stream);
 
 /* rcbf_batch_status — synchronise `stream` and return the device status word

@@ -386,7 +386,8 @@ class Pipeline:
 
 class Batch:
     """Owns an ``rcbf_batch_t``: frames bound to fixed device buffers, run as
-    one persistent launch (capturable in a CUDA graph)."""
+    one persistent launch per (window class, tile extent) phase (capturable
+    in a CUDA graph)."""
 
     def __init__(self, plans: Sequence[Plan], rf, decoded, images):
         lib = load_library()

@@ -12,17 +12,25 @@
 namespace rcbf {
 template <int VU> int batch_configure_vu(int ws, int* per_sm, size_t* smem);
 template <int VU> int batch_launch_vu(int ws, unsigned grid, size_t smem, const int4* items, int n_items,
-                                      const BatchFrame* frames, int* counters, long long wait_ns, int withhold,
-                                      cudaStream_t s);
+                                      const BatchFrame* frames, int* counters, int ticket_slot, long long wait_ns,
+                                      int withhold, bool dependent, cudaStream_t s);
+
+// one persistent launch: the frames of one (window class, tile extent) group
+struct BatchPhase {
+    int vu = 2;
+    int ws = 48;
+    int item0 = 0;           // first item of the phase in the batch's item list
+    int n_items = 0;
+    unsigned grid = 1;
+    size_t smem = 0;
+};
 }  // namespace rcbf
 
 struct rcbf_batch_s {
     int n_frames = 0;
     int n_items = 0;
-    int vu = 2;
-    int ws = 64;
-    unsigned grid = 1;
-    size_t smem = 0;
+    std::vector<rcbf::BatchPhase> phases;
+    long long n_counters = 0;            // status, per-frame decode counts, per-phase tickets, tile flags
     long long wait_ns = 1000000000LL;   // bounded wait of a DAS item on its frame's decode
     int withhold = -1;                  // test hook: a frame whose decode never completes
     int4* d_items = nullptr;
@@ -42,6 +50,10 @@ int batch_fail(rcbf_batch_s* b, int code, const std::string& msg) {
 
 int class_of(int W) { return W <= 48 ? 48 : W <= 64 ? 64 : W <= 96 ? 96 : 128; }
 
+// phases with fewer whole-tile units than this many waves of the grid split
+// every tile into two channel halves
+constexpr long long kSplitWaves = 24;
+
 }  // namespace
 
 namespace rcbf {
@@ -56,10 +68,9 @@ int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t
     *out_batch = nullptr;
     if (!plans || !decoded || !images || n_frames == 0)
         return set_error(RCBF_EINVAL, "rcbf_batch_create: NULL array or zero frames");
-    const int bu = plans[0] ? plans[0]->h.das.bu : 0;
     std::vector<BatchFrame> frames(n_frames);
     std::vector<TcJob> tc_jobs;
-    int ws = 48;
+    std::vector<int> frame_ws(n_frames), frame_vu(n_frames);
     for (uint32_t f = 0; f < n_frames; ++f) {
         const rcbf_plan_t p = plans[f];
         const std::string at = "rcbf_batch_create: frame " + std::to_string(f) + ": ";
@@ -78,7 +89,6 @@ int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t
         if (h.vls_split)
             return set_error(RCBF_EUNSUPPORTED, at + "a virtual-line-source focal plane inside the image needs "
                                                      "the plain form for the tiles across it");
-        if (h.das.bu != bu) return set_error(RCBF_EINVAL, at + "all plans of a batch need the same tile extent along u");
         if (!decoded[f] || !images[f] || (h.p.hadamard_order && (!rf || !rf[f])))
             return set_error(RCBF_EINVAL, at + "NULL buffer");
         if ((reinterpret_cast<uintptr_t>(decoded[f]) & 15u) || (reinterpret_cast<uintptr_t>(images[f]) & 3u) ||
@@ -95,7 +105,8 @@ int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t
         fr.das.partial = nullptr;
         fr.das.withhold = 0;            // the plan's DAS test hook does not apply to a batch
         fr.das.wait_ns = kWaitNs;
-        ws = std::max(ws, class_of(fr.das.W));
+        frame_ws[f] = class_of(fr.das.W);
+        frame_vu[f] = h.das.bu / 32;
         fr.out_dtype = (int)h.p.decoded_dtype;
         fr.order = (int)h.p.n_tx;
         if (h.p.hadamard_order && h.p.decode_variant == RCBF_DECODE_TC) {
@@ -122,49 +133,102 @@ int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t
             if (!h.d_afrag) return set_error(RCBF_EUNSUPPORTED, at + "the tensor-core decode needs n_tx in {32, 64, 128, 256}");
         }
     }
-    // item list: decode of frame f+1 ahead of the DAS of frame f
-    std::vector<int4> items;
-    auto push_decode = [&](int f) {
-        for (int t = 0; t < frames[f].n_decode; ++t) items.push_back(make_int4(kItemDecode, f, t, 0));
-    };
-    auto push_das = [&](int f) {
-        const DasArgs& a = frames[f].das;
-        const int units = a.tiles_u * a.tiles_v * a.tiles_w;
-        for (int u = 0; u < units; ++u) items.push_back(make_int4(kItemDas, f, u, 0));
-    };
-    push_decode(0);
+    // phases: frames grouped by (window class, tile extent along u), in order
+    // of first appearance; within a phase the frames keep their order and the
+    // decode of frame f+1 precedes the DAS of frame f
+    std::vector<std::pair<int, int>> keys;
+    std::vector<std::vector<int>> members;
     for (uint32_t f = 0; f < n_frames; ++f) {
-        if (f + 1 < n_frames) push_decode((int)f + 1);
-        push_das((int)f);
+        const std::pair<int, int> key(frame_ws[f], frame_vu[f]);
+        size_t p = 0;
+        while (p < keys.size() && keys[p] != key) ++p;
+        if (p == keys.size()) {
+            keys.push_back(key);
+            members.emplace_back();
+        }
+        members[p].push_back((int)f);
     }
-    for (uint32_t f = 0; f < n_frames; ++f) frames[f].das.status = nullptr;   // set below
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    std::vector<int4> items;
+    std::vector<BatchPhase> phases;
+    std::vector<long long> flag_off(n_frames, -1);      // tile flags of frames with a channel split
+    long long n_flags = 0;
+    for (size_t p = 0; p < keys.size(); ++p) {
+        BatchPhase ph;
+        ph.ws = keys[p].first;
+        ph.vu = keys[p].second;
+        int per_sm = 1, rc;
+        switch (ph.vu) {
+            case 1: rc = batch_configure_vu<1>(ph.ws, &per_sm, &ph.smem); break;
+            case 2: rc = batch_configure_vu<2>(ph.ws, &per_sm, &ph.smem); break;
+            default: rc = batch_configure_vu<4>(ph.ws, &per_sm, &ph.smem); break;
+        }
+        if (rc != RCBF_OK) return rc;
+        const std::vector<int>& fs = members[p];
+        const int slots = sms * per_sm;
+        // channel split of the phase's DAS units. Units of a whole tile leave
+        // the last wave of a short phase partly idle; halving them (two
+        // channel halves per tile, summed into the image in order) evens the
+        // tail, while every further split repeats the tile set-up and the
+        // pipeline fill. Measured on four B-scan frames (2048 tiles, 6.7 waves
+        // of 304 CTAs): whole tiles 9.67 ms, halves 9.49 ms, quarters 9.56 ms.
+        // Phases of many waves keep whole tiles.
+        long long tiles_all = 0;
+        bool halves = true;
+        for (int f : fs) {
+            const DasArgs& a = frames[f].das;
+            tiles_all += (long long)a.tiles_u * a.tiles_v * a.tiles_w;
+            halves = halves && (a.n_ch / 8) % 2 == 0;
+        }
+        const int split = (halves && tiles_all < kSplitWaves * (long long)slots) ? 2 : 1;
+        ph.item0 = (int)items.size();
+        auto push_decode = [&](int f) {
+            for (int t = 0; t < frames[f].n_decode; ++t) items.push_back(make_int4(kItemDecode, f, t, 0));
+        };
+        auto push_das = [&](int f) {
+            DasArgs& a = frames[f].das;
+            const int tiles = a.tiles_u * a.tiles_v * a.tiles_w;
+            a.n_split = split;
+            if (split > 1) {
+                flag_off[f] = n_flags;
+                n_flags += tiles;
+            }
+            // the splits of a tile take consecutive tickets
+            for (int t = 0; t < tiles; ++t)
+                for (int sp = 0; sp < split; ++sp) items.push_back(make_int4(kItemDas, f, sp * tiles + t, 0));
+        };
+        push_decode(fs[0]);
+        for (size_t k = 0; k < fs.size(); ++k) {
+            if (k + 1 < fs.size()) push_decode(fs[k + 1]);
+            push_das(fs[k]);
+        }
+        ph.n_items = (int)items.size() - ph.item0;
+        ph.grid = (unsigned)std::min<long long>((long long)slots, (long long)ph.n_items);
+        phases.push_back(ph);
+    }
+    const long long flags0 = kBatchDone + (long long)n_frames + (long long)phases.size();
+    const long long n_counters = flags0 + n_flags;
 
     rcbf_batch_s* b = new rcbf_batch_s();
     b->tc_jobs = tc_jobs;
     b->n_frames = (int)n_frames;
     b->n_items = (int)items.size();
-    b->vu = bu / 32;
-    b->ws = ws;
+    b->n_counters = n_counters;
     if (cudaMalloc(&b->d_items, items.size() * sizeof(int4)) != cudaSuccess ||
         cudaMalloc(&b->d_frames, frames.size() * sizeof(BatchFrame)) != cudaSuccess ||
-        cudaMalloc(&b->d_counters, (kBatchDone + n_frames) * sizeof(int)) != cudaSuccess)
+        cudaMalloc(&b->d_counters, n_counters * sizeof(int)) != cudaSuccess)
         return batch_fail(b, RCBF_ENOMEM, "rcbf_batch_create: cudaMalloc");
-    for (auto& fr : frames) fr.das.status = b->d_counters + kBatchStatus;
+    for (uint32_t f = 0; f < n_frames; ++f) {
+        frames[f].das.status = b->d_counters + kBatchStatus;
+        frames[f].das.tile_flags = flag_off[f] >= 0 ? b->d_counters + flags0 + flag_off[f] : nullptr;
+    }
     if (cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(b->d_frames, frames.data(), frames.size() * sizeof(BatchFrame), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(b->d_counters, 0, (kBatchDone + n_frames) * sizeof(int)) != cudaSuccess)
+        cudaMemset(b->d_counters, 0, n_counters * sizeof(int)) != cudaSuccess)
         return batch_fail(b, RCBF_ECUDA, "rcbf_batch_create: copy work list");
-    int per_sm = 1, rc;
-    switch (b->vu) {
-        case 1: rc = batch_configure_vu<1>(ws, &per_sm, &b->smem); break;
-        case 2: rc = batch_configure_vu<2>(ws, &per_sm, &b->smem); break;
-        default: rc = batch_configure_vu<4>(ws, &per_sm, &b->smem); break;
-    }
-    if (rc != RCBF_OK) { const std::string m = rcbf_last_error(); return batch_fail(b, rc, m); }
-    int dev = 0, sms = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    b->grid = (unsigned)std::min<long long>((long long)sms * per_sm, (long long)items.size());
+    b->phases = phases;
     *out_batch = b;
     return RCBF_OK;
 }
@@ -172,20 +236,32 @@ int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t
 int rcbf_batch_run(rcbf_batch_t batch, void* stream) {
     if (!batch) return set_error(RCBF_EINVAL, "rcbf_batch_run: batch is NULL");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cudaMemsetAsync(batch->d_counters, 0, (kBatchDone + batch->n_frames) * sizeof(int), s) != cudaSuccess)
+    if (cudaMemsetAsync(batch->d_counters, 0, batch->n_counters * sizeof(int), s) != cudaSuccess)
         return check_launch("rcbf_batch_run: reset counters");
     for (const TcJob& job : batch->tc_jobs) {
         const int rc = decode_tc_run(job, batch->d_counters + kBatchStatus, batch->wait_ns, s);
         if (rc != RCBF_OK) return rc;
     }
-    switch (batch->vu) {
-        case 1: return batch_launch_vu<1>(batch->ws, batch->grid, batch->smem, batch->d_items, batch->n_items,
-                                          batch->d_frames, batch->d_counters, batch->wait_ns, batch->withhold, s);
-        case 2: return batch_launch_vu<2>(batch->ws, batch->grid, batch->smem, batch->d_items, batch->n_items,
-                                          batch->d_frames, batch->d_counters, batch->wait_ns, batch->withhold, s);
-        default: return batch_launch_vu<4>(batch->ws, batch->grid, batch->smem, batch->d_items, batch->n_items,
-                                           batch->d_frames, batch->d_counters, batch->wait_ns, batch->withhold, s);
+    for (size_t p = 0; p < batch->phases.size(); ++p) {
+        const BatchPhase& ph = batch->phases[p];
+        const int4* items = batch->d_items + ph.item0;
+        const int slot = kBatchDone + batch->n_frames + (int)p;
+        const bool dependent = p > 0;
+        int rc;
+        switch (ph.vu) {
+            case 1: rc = batch_launch_vu<1>(ph.ws, ph.grid, ph.smem, items, ph.n_items, batch->d_frames,
+                                            batch->d_counters, slot, batch->wait_ns, batch->withhold, dependent, s);
+                break;
+            case 2: rc = batch_launch_vu<2>(ph.ws, ph.grid, ph.smem, items, ph.n_items, batch->d_frames,
+                                            batch->d_counters, slot, batch->wait_ns, batch->withhold, dependent, s);
+                break;
+            default: rc = batch_launch_vu<4>(ph.ws, ph.grid, ph.smem, items, ph.n_items, batch->d_frames,
+                                             batch->d_counters, slot, batch->wait_ns, batch->withhold, dependent, s);
+                break;
+        }
+        if (rc != RCBF_OK) return rc;
     }
+    return RCBF_OK;
 }
 
 int rcbf_batch_status(rcbf_batch_t batch, void* stream) {

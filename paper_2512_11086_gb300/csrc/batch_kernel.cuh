@@ -11,6 +11,15 @@
 // unless a frame's completion count is made unreachable on purpose (the
 // host-side test hook of rcbf_batch_set_wait), in which case the wait expires
 // and the status word records it.
+//
+// Frames are grouped into phases by DAS window class and tile extent (one
+// kernel instance each); every phase is one persistent launch with its own
+// ticket and its own item list (a frame's decode items sit in its phase).
+// Phases after the first are launched as programmatic dependents: every CTA
+// allows the next phase to launch as soon as it starts, so the next phase's
+// CTAs take the SM slots that this phase's CTAs free at its tail, and every
+// CTA waits for the previous phase's completion before it exits, so the
+// completion of the last phase implies that of all.
 #pragma once
 
 #include "das_tile.cuh"
@@ -31,7 +40,9 @@ static_assert(sizeof(DasArgs) % 8 == 0, "DasArgs is copied in 8-byte words");
 static_assert(alignof(BatchFrame) >= 16 && sizeof(BatchFrame) % 16 == 0, "frame descriptors stay 16-byte aligned");
 
 enum : int { kItemDecode = 0, kItemDas = 1 };
-enum : int { kBatchTicket = 0, kBatchStatus = 1, kBatchDone = 2 };   // counter slots
+// counter slots: the status word, one completion count per frame, then one
+// ticket per phase
+enum : int { kBatchStatus = 0, kBatchDone = 1 };
 
 template <int VU, int WS>
 struct BatchCfg {
@@ -73,16 +84,19 @@ __device__ __forceinline__ void batch_decode_dt(const BatchFrame& f, long long t
 template <int VU, int WS>
 __global__ void __launch_bounds__(kDasThreads, 2)
 batch_kernel(const int4* __restrict__ items, int n_items, const BatchFrame* __restrict__ frames,
-             int* counters, long long wait_ns, int withhold) {
+             int* counters, int ticket_slot, long long wait_ns, int withhold) {
     using C = BatchCfg<VU, WS>;
     using D = typename C::D;
     extern __shared__ __align__(128) unsigned char smem[];
     DasArgs* s_args = reinterpret_cast<DasArgs*>(smem + C::OFF_ARGS);
     __shared__ int s_item, s_ok;
+    // the next phase (independent frames) may launch now; its CTAs start as
+    // this phase's CTAs exit (no effect on a launch without dependents)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     das_pipe_init<D::COPIES>(smem + D::OFF_BAR, reinterpret_cast<volatile int*>(smem + D::OFF_ABORT));
     DasPipe pipe{0u};
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counters + kBatchTicket, 1);
+        if (threadIdx.x == 0) s_item = atomicAdd(counters + ticket_slot, 1);
         __syncthreads();
         const int t = s_item;
         if (t >= n_items) break;
@@ -130,6 +144,9 @@ batch_kernel(const int4* __restrict__ items, int n_items, const BatchFrame* __re
         }
         __syncthreads();   // s_item, s_args and the staging buffers are reused
     }
+    // completion of this phase implies completion of the previous one (a
+    // no-op for a launch that is not a programmatic dependent)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 template <int VU, int WS>
@@ -154,14 +171,39 @@ int batch_configure_vu(int ws, int* per_sm, size_t* smem) {
     return batch_configure<VU, 128>(per_sm, smem);
 }
 
+template <int VU, int WS>
+int batch_launch(unsigned grid, size_t smem, const int4* items, int n_items, const BatchFrame* frames, int* counters,
+                 int ticket_slot, long long wait_ns, int withhold, bool dependent, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kDasThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = dependent ? 1 : 0;
+    if (cudaLaunchKernelEx(&cfg, batch_kernel<VU, WS>, items, n_items, frames, counters, ticket_slot, wait_ns,
+                           withhold) != cudaSuccess)
+        return check_launch("batch_kernel launch");
+    return check_launch("batch_kernel");
+}
+
 template <int VU>
 int batch_launch_vu(int ws, unsigned grid, size_t smem, const int4* items, int n_items, const BatchFrame* frames,
-                    int* counters, long long wait_ns, int withhold, cudaStream_t s) {
-    if (ws == 48) batch_kernel<VU, 48><<<grid, kDasThreads, smem, s>>>(items, n_items, frames, counters, wait_ns, withhold);
-    else if (ws == 64) batch_kernel<VU, 64><<<grid, kDasThreads, smem, s>>>(items, n_items, frames, counters, wait_ns, withhold);
-    else if (ws == 96) batch_kernel<VU, 96><<<grid, kDasThreads, smem, s>>>(items, n_items, frames, counters, wait_ns, withhold);
-    else batch_kernel<VU, 128><<<grid, kDasThreads, smem, s>>>(items, n_items, frames, counters, wait_ns, withhold);
-    return check_launch("batch_kernel");
+                    int* counters, int ticket_slot, long long wait_ns, int withhold, bool dependent, cudaStream_t s) {
+    if (ws == 48)
+        return batch_launch<VU, 48>(grid, smem, items, n_items, frames, counters, ticket_slot, wait_ns, withhold,
+                                    dependent, s);
+    if (ws == 64)
+        return batch_launch<VU, 64>(grid, smem, items, n_items, frames, counters, ticket_slot, wait_ns, withhold,
+                                    dependent, s);
+    if (ws == 96)
+        return batch_launch<VU, 96>(grid, smem, items, n_items, frames, counters, ticket_slot, wait_ns, withhold,
+                                    dependent, s);
+    return batch_launch<VU, 128>(grid, smem, items, n_items, frames, counters, ticket_slot, wait_ns, withhold,
+                                 dependent, s);
 }
 
 }  // namespace rcbf

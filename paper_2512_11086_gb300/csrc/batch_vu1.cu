@@ -3,6 +3,6 @@
 
 namespace rcbf {
 template int batch_configure_vu<1>(int, int*, size_t*);
-template int batch_launch_vu<1>(int, unsigned, size_t, const int4*, int, const BatchFrame*, int*, long long, int,
-                                 cudaStream_t);
+template int batch_launch_vu<1>(int, unsigned, size_t, const int4*, int, const BatchFrame*, int*, int, long long,
+                                 int, bool, cudaStream_t);
 }  // namespace rcbf

@@ -6,7 +6,8 @@
 // walks its part of the (transmit, channel) plane in stages of CI x CJ
 // windows. A plan may split the channels of a tile over several units (to
 // fill every SM); each unit then writes a partial image and a reduce kernel
-// adds the partials in a fixed order.
+// adds the partials in a fixed order, or (the batch form) adds its sums into
+// the image itself once the previous split of its tile has (tile_flags).
 //
 // Delays. For the tile centre q_ref the FP64 reference distance of every
 // element is split into an integer sample K and a fractional remainder; a
@@ -774,11 +775,50 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     }
     pipe.base += (uint32_t)NS;
 
-    // ---- store the tile (or this unit's partial of it)
-    float* out = a.n_split > 1 ? a.partial + (long long)split * a.partial_stride : a.image;
     float acc[4];
     upk(acc2[0], acc[0], acc[1]);
     upk(acc2[1], acc[2], acc[3]);
+    if (a.tile_flags && a.n_split > 1) {
+        // ---- ordered accumulation of the channel splits of this tile: split
+        // s adds its sums to the image once splits 0 .. s-1 have (the wait is
+        // on a unit with a smaller ticket, which is running or done)
+        int* flag = a.tile_flags + tile;
+        int ok = 1;
+        if (split > 0 && tid == 0) {
+            const unsigned long long t0 = globaltimer_ns();
+            for (;;) {
+                int v;
+                asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+                if (v >= split) break;
+                if (globaltimer_ns() - t0 > (unsigned long long)a.wait_ns) { ok = 0; break; }
+                __nanosleep(100);
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(a.status, kStatusWaitExpired);
+            return false;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int ku = k % VU, kr = k / VU;
+            const int row = warp * C::VR + kr;
+            const int iu = u0 + lane + 32 * ku, iv = v0 + row % a.bv, iw = w0 + row / a.bv;
+            if (iu < a.n_u && iv < a.n_v && iw < a.n_w) {
+                const long long o = (long long)iw * a.out_sw + (long long)iv * a.out_sv + (long long)iu * a.out_su;
+                a.image[o] = split ? __ldcg(a.image + o) + acc[k] : acc[k];
+                if (CPLX) a.image[a.image_plane + o] = split ? __ldcg(a.image + a.image_plane + o) + acci[k] : acci[k];
+            }
+        }
+        __syncthreads();                       // every store of this split precedes the release
+        if (tid == 0) {
+            __threadfence();
+            asm volatile("st.release.gpu.global.s32 [%0], %1;" :: "l"(flag), "r"(split + 1) : "memory");
+        }
+        return true;
+    }
+
+    // ---- store the tile (or this unit's partial of it)
+    float* out = a.n_split > 1 ? a.partial + (long long)split * a.partial_stride : a.image;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int ku = k % VU, kr = k / VU;

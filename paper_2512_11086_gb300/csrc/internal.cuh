@@ -72,6 +72,11 @@ struct DasArgs {
     int withhold;          // test hook: 1 = every tiled DAS unit omits its first window copy, so
                            // its first wait expires (rcbf_plan_set_wait); 0 in normal use
     int reserved_w;
+    int* tile_flags;       // batch form of a channel split (n_split > 1): per tile, the number of
+                           // splits already added into the image; split s waits (bounded) until
+                           // it reads s, adds its sums into the image and publishes s + 1, so
+                           // the image is summed in split order with no partial buffers
+                           // (nullptr: partial images and a reduce kernel)
     // adjoint outputs (backward only)
     const float* grad_image;
     float* grad_rf;

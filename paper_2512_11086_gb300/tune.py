@@ -8,9 +8,9 @@ times every admissible shape with the library's own DAS on the GPU (CUDA
 events, after warm-up) and keeps the fastest. Results are cached in a JSON
 file keyed by the geometry, so a frame class is tuned once.
 
-Batches need one tile extent bu for all their frames; ``tune_stream`` picks
-the bu that minimises the summed time of the distinct frame classes and the
-best (bv, bw) of each class for it.
+A batch runs the frames of each window class and tile extent as their own
+persistent launch, so ``tune_stream`` gives every distinct frame class its own
+fastest tile.
 """
 from __future__ import annotations
 
@@ -122,9 +122,9 @@ def tune_tile(g, decoded_dtype: str = "f16", cache_path: Optional[str] = None, r
 
 def tune_stream(geometries: Sequence, decoded_dtype: str = "f16", cache_path: Optional[str] = None,
                 reps: int = 3) -> List[Tile]:
-    """Tiles for the frames of a batch: one common bu, the best (bv, bw) per
-    frame class for that bu, bu chosen to minimise the summed class time
-    weighted by how often each class occurs."""
+    """Tiles for the frames of a batch: the fastest tile of each frame class
+    (a batch runs the frames of each window class and tile extent along u as
+    their own persistent launch, so the classes need not share a tile)."""
     path = cache_path or default_cache_path()
     classes: Dict[str, Tuple[object, int]] = {}
     for g in geometries:
@@ -143,22 +143,10 @@ def tune_stream(geometries: Sequence, decoded_dtype: str = "f16", cache_path: Op
                 best = min(per_class[k], key=per_class[k].get)
                 cache[k] = {"best": list(best), "ms": {"%d,%d,%d" % t: v for t, v in per_class[k].items()}}
                 _store(path, cache)
-    best_bu, best_total = None, float("inf")
-    for bu in (32, 64, 128):
-        total = 0.0
-        for k, (g, count) in classes.items():
-            opts = [ms for t, ms in per_class[k].items() if t[0] == bu]
-            if not opts:
-                total = float("inf")
-                break
-            total += count * min(opts)
-        if total < best_total:
-            best_bu, best_total = bu, total
-    if best_bu is None:
-        raise RuntimeError("no common tile extent admits the tiled DAS for every frame")
     tiles = []
     for g in geometries:
-        k = geometry_key(g, decoded_dtype)
-        opts = {t: ms for t, ms in per_class[k].items() if t[0] == best_bu}
+        opts = per_class[geometry_key(g, decoded_dtype)]
+        if not opts:
+            raise RuntimeError("no tile admits the tiled DAS for a frame of the batch")
         tiles.append(min(opts, key=opts.get))
     return tiles

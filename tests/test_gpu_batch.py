@@ -127,16 +127,57 @@ def test_batch_bounded_wait_expires_and_context_survives(stream):
     assert rel_l2(img[k].cpu().numpy(), plans[k].das(dec[k]).cpu().numpy()) <= 1e-5
 
 
-def test_batch_rejects_mixed_tile_extents():
-    g1 = synth.tiny_bscan_geometry()
-    p1 = rc.Plan(rc.make_params(g1, decoded_dtype="f16", tile=(64, 1, 16)))
-    p2 = rc.Plan(rc.make_params(g1, decoded_dtype="f16", tile=(32, 1, 32)))
-    rf = torch.zeros(32, 32, 1024, dtype=torch.int16, device="cuda")
-    d = [torch.empty(32, 32, 1024, dtype=torch.float16, device="cuda") for _ in range(2)]
-    im = [torch.empty(128, 1, 128, device="cuda") for _ in range(2)]
-    with pytest.raises(rc.RcbfError) as e:
-        rc.Batch([p1, p2], [rf, rf], d, im)
-    assert e.value.code == rc.EINVAL
+def test_batch_phases_of_mixed_tiles_and_window_classes():
+    # frames with different tile extents along u and different window classes
+    # run as several persistent launches (phases), the later ones launched as
+    # programmatic dependents; interleaved in the frame list, captured in a
+    # graph and replayed: every frame equals its single-frame DAS
+    geos = synth.stream_geometries()
+    specs = [(0, (64, 1, 16)), (2, (32, 1, 32)), (1, (64, 1, 16)), (2, (128, 1, 8)), (0, (32, 1, 32)),
+             (33, (64, 1, 16))]
+    frames, plans, rf, dec, img = [], [], [], [], []
+    for idx, tile in specs:
+        g, seed, box = geos[idx]
+        fr = synth.make_frame(g, seed, 4, **box)
+        frames.append(fr)
+        variant = rc.DECODE_TC if len(plans) % 2 else rc.DECODE_MMA_I8
+        plans.append(rc.Plan(rc.make_params(g, decoded_dtype="f16", decode_variant=variant, tile=tile)))
+        rf.append(torch.from_numpy(fr.rf).cuda())
+        dec.append(torch.empty(g.n_tx, g.n_ch, g.n_samples, dtype=torch.float16, device="cuda"))
+        img.append(torch.empty(g.out_dims[2], g.out_dims[1], g.out_dims[0], device="cuda"))
+    cls = lambda w: 48 if w <= 48 else 64 if w <= 64 else 96 if w <= 96 else 128
+    phases = {(cls(p.info()["window"]), p.info()["tile"][0]) for p in plans}
+    assert len(phases) >= 3, phases
+    batch = rc.Batch(plans, rf, dec, img)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        batch.run(stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        batch.run()
+    for k in range(len(frames)):
+        img[k].zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert batch.status() == rc.OK
+    for k, fr in enumerate(frames):
+        g = fr.geometry
+        want16 = oracle.decoded_as(oracle.decode(fr.rf), g.n_tx, "f16")
+        np.testing.assert_array_equal(dec[k].cpu().numpy().view(np.uint16), want16.view(np.uint16))
+        single = plans[k].das(dec[k]).cpu().numpy()
+        assert rel_l2(img[k].cpu().numpy(), single) <= 1e-5, k
+        vox = sample_voxels(g.out_dims, 300, seed=k)
+        assert rel_l2(img[k].cpu().numpy().ravel()[vox], oracle.das(g, want16.astype(np.float64), voxels=vox)) <= 1e-4
+    # a withheld frame in a later phase times out; the other phases finish
+    batch.set_wait(2_000_000, withhold_frame=1)
+    batch.run()
+    assert batch.status() == rc.ETIMEOUT
+    batch.set_wait(1_000_000_000, withhold_frame=-1)
+    batch.run()
+    assert batch.status() == rc.OK
 
 
 def test_batch_at_the_benchmark_configuration():
