@@ -198,6 +198,10 @@ das_bwd_kernel(DasArgs a) {
             q_im[k] = (int)(__float_as_uint(gs_im[k] + kQ) - kQbits);
         }
     }
+    const f2x gs2_re[2] = {pk(gs_re[0], gs_re[1]), pk(gs_re[2], gs_re[3])};
+    const f2x gs2_im[2] = {pk(gs_im[0], gs_im[1]), pk(gs_im[2], gs_im[3])};
+    const int qsum_re = q_re[0] + q_re[1] + q_re[2] + q_re[3];
+    const int qsum_im = q_im[0] + q_im[1] + q_im[2] + q_im[3];
 
     const int es = 4;
     // stage s: raw buffer s & 1 (its window starts in s_S0 / s_off), alpha
@@ -229,8 +233,10 @@ das_bwd_kernel(DasArgs a) {
     };
     // transmit terms of stage s for every tile row
     auto make_alpha = [&](int s) {
-        if (tid >= kBwdCI * C::ROWS) return;
-        const int ii = tid / C::ROWS, row = tid % C::ROWS;
+        // the last warps (warp 0 issues the copies)
+        const int at = tid - (kDasThreads - kBwdCI * C::ROWS);
+        if (at < 0) return;
+        const int ii = at / C::ROWS, row = at % C::ROWS;
         const float dv = (float)row_v(row) - 0.5f * (a.bv - 1);
         const float dw = (float)row_w(row) - 0.5f * (a.bw - 1);
         const float dL = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]) * dv + (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]) * dw;
@@ -246,7 +252,9 @@ das_bwd_kernel(DasArgs a) {
     const float hp = 0.5f + (float)a.H;
     // per channel of the chunk: w_j and the dL/dw_j partial; per (voxel,
     // channel): beta + 0.5 + H and (F# window) W_j(v)
-    float betah[4][kBwdCJ], win_w[FN ? 4 : 1][kBwdCJ], wj[kBwdCJ], pw[kBwdCJ];
+    // receive terms of voxel pairs (k, k+1) packed in f32x2 registers
+    f2x betah2[2][kBwdCJ];
+    float win_w[FN ? 4 : 1][kBwdCJ], wj[kBwdCJ], pw[kBwdCJ];
     float gc = 0.f;                         // dL/dc partial (times -c, scaled)
     bool ok = true;
     uint32_t phase = 0;                     // parity of each raw buffer's next phase
@@ -267,18 +275,21 @@ das_bwd_kernel(DasArgs a) {
             const int ic = s % n_ic, jc = jc0 + s / n_ic;
             if (ic == 0) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float Zv = Zf + dz[k];
+                for (int jj = 0; jj < kBwdCJ; ++jj) {
+                    const float4 rx = s_rx[jc * kBwdCJ + jj];
+                    float bt[4];
 #pragma unroll
-                    for (int jj = 0; jj < kBwdCJ; ++jj) {
-                        const float4 rx = s_rx[jc * kBwdCJ + jj];
+                    for (int k = 0; k < 4; ++k) {
+                        const float Zv = Zf + dz[k];
                         const float Lv = rx.x + dlr[k];
                         const float d = sqrtf(Lv * Lv + Zv * Zv);
                         const float num = dlr[k] * (2.0f * rx.x + dlr[k]) + dz[k] * (2.0f * Zf + dz[k]);
-                        const float bt = rx.z + __fdividef(num, d + rx.y) * fsc;
-                        betah[k][jj] = fminf(fmaxf(bt, rx.z - a.reach_b), rx.z + a.reach_b) + hp;
+                        const float b0 = rx.z + __fdividef(num, d + rx.y) * fsc;
+                        bt[k] = fminf(fmaxf(b0, rx.z - a.reach_b), rx.z + a.reach_b) + hp;
                         if (FN) win_w[FN ? k : 0][jj] = hann_weight(a.f_number, Lv, Zv);
                     }
+                    betah2[0][jj] = pk(bt[0], bt[1]);
+                    betah2[1][jj] = pk(bt[2], bt[3]);
                 }
             }
 
@@ -295,16 +306,38 @@ das_bwd_kernel(DasArgs a) {
                 for (int jj = 0; jj < kBwdCJ; ++jj) {
                     const int win = ii * kBwdCJ + jj;
                     const uint32_t wb0 = abase + 4u * (uint32_t)(win * C::GW);      // G0, plane 0
-                    // the four voxels' intervals (t holds the interval in its low bits)
+                    // the four voxels' intervals (t holds the interval in its low
+                    // bits) and fractions, voxel pairs in f32x2 registers
                     uint32_t tb[4];
                     float fr[4];
+                    f2x fr2[2];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const float al = ZL ? al_row : alp[ii * C::ROWS + warp * C::VR + k / VU];
-                        const float uh = al + betah[k][jj];
-                        const float t = uh + 8388607.5f;
-                        tb[k] = __float_as_uint(t);
-                        fr[k] = uh - (t - 8388608.0f);
+                    for (int kp = 0; kp < 2; ++kp) {
+                        const float a0 = ZL ? al_row : alp[ii * C::ROWS + warp * C::VR + (2 * kp) / VU];
+                        const float a1v = ZL ? al_row : alp[ii * C::ROWS + warp * C::VR + (2 * kp + 1) / VU];
+                        const f2x uh2 = add2(pk(a0, a1v), betah2[kp][jj]);
+                        const f2x t2 = add2(uh2, pk(8388607.5f, 8388607.5f));
+                        fr2[kp] = fma2(add2(t2, pk(-8388608.0f, -8388608.0f)), pk(-1.0f, -1.0f), uh2);
+                        float t0, t1;
+                        upk(t2, t0, t1);
+                        tb[2 * kp] = __float_as_uint(t0);
+                        tb[2 * kp + 1] = __float_as_uint(t1);
+                        upk(fr2[kp], fr[2 * kp], fr[2 * kp + 1]);
+                    }
+                    // fixed-point G1 terms round(g f): the float bits of g f + 1.5 * 2^23
+                    // (without an F# window g is the voxel's scaled gradient)
+                    uint32_t bq[2][4];
+                    if constexpr (!FN) {
+#pragma unroll
+                        for (int p = 0; p < (CPLX ? 2 : 1); ++p) {
+#pragma unroll
+                            for (int kp = 0; kp < 2; ++kp) {
+                                float x0, x1;
+                                upk(fma2(p ? gs2_im[kp] : gs2_re[kp], fr2[kp], pk(kQ, kQ)), x0, x1);
+                                bq[p][2 * kp] = __float_as_uint(x0);
+                                bq[p][2 * kp + 1] = __float_as_uint(x1);
+                            }
+                        }
                     }
                     // With lanes over z a thread's four voxels are consecutive along
                     // u. Where the delay changes slowly along u they fall into at
@@ -318,57 +351,68 @@ das_bwd_kernel(DasArgs a) {
                     }
                     if (ZL && span <= 1) {
                         const uint32_t s0 = (tmin << 2) + wb0;
+                        uint32_t d[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) d[k] = tb[k] - tmin;             // 0 or 1
+                        const uint32_t dsum = d[0] + d[1] + d[2] + d[3];
 #pragma unroll
                         for (int p = 0; p < (CPLX ? 2 : 1); ++p) {
-                            int qs = 0, a1 = 0, g1 = 0, b1 = 0;
+                            uint32_t lo0, hi0, lo1, hi1;
+                            if constexpr (!FN) {
+                                // sums over the voxels of the upper interval (d = 1) and of
+                                // all four, in wrapping 32-bit arithmetic (the true values fit)
+                                const int* q = p ? q_im : q_re;
+                                hi0 = d[0] * (uint32_t)q[0] + d[1] * (uint32_t)q[1] + d[2] * (uint32_t)q[2] +
+                                      d[3] * (uint32_t)q[3];
+                                lo0 = (uint32_t)(p ? qsum_im : qsum_re) - hi0;
+                                const uint32_t hb = d[0] * bq[p][0] + d[1] * bq[p][1] + d[2] * bq[p][2] + d[3] * bq[p][3];
+                                const uint32_t sb = bq[p][0] + bq[p][1] + bq[p][2] + bq[p][3];
+                                hi1 = hb - dsum * kQbits;
+                                lo1 = sb - hb - (4u - dsum) * kQbits;
+                            } else {
+                                int qs = 0, a1 = 0, g1 = 0, b1 = 0;
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                float g = p ? gs_im[k] : gs_re[k];
-                                int q = p ? q_im[k] : q_re[k];
-                                if (FN) {
-                                    g *= win_w[FN ? k : 0][jj];
-                                    q = (int)(__float_as_uint(g + kQ) - kQbits);
+                                for (int k = 0; k < 4; ++k) {
+                                    const float g = (p ? gs_im[k] : gs_re[k]) * win_w[FN ? k : 0][jj];
+                                    const int qk = (int)(__float_as_uint(g + kQ) - kQbits);
+                                    const int q1 = (int)(__float_as_uint(fmaf(g, fr[k], kQ)) - kQbits);
+                                    qs += qk;
+                                    a1 += (int)d[k] * qk;
+                                    g1 += q1;
+                                    b1 += (int)d[k] * q1;
                                 }
-                                const int q1 = (int)(__float_as_uint(fmaf(g, fr[k], kQ)) - kQbits);
-                                const int d = (int)(tb[k] - tmin);                  // 0 or 1
-                                qs += q;
-                                a1 += d * q;
-                                g1 += q1;
-                                b1 += d * q1;
+                                lo0 = (uint32_t)(qs - a1);
+                                hi0 = (uint32_t)a1;
+                                lo1 = (uint32_t)(g1 - b1);
+                                hi1 = (uint32_t)b1;
                             }
                             const uint32_t sp0 = s0 + (p ? kIm : 0u);
-                            asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0), "r"(qs - a1) : "memory");
-                            asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0 + kG1), "r"(g1 - b1) : "memory");
+                            asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0), "r"(lo0) : "memory");
+                            asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0 + kG1), "r"(lo1) : "memory");
                             if (span == 1) {
-                                asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0 + 4u), "r"(a1) : "memory");
-                                asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0 + 4u + kG1), "r"(b1) : "memory");
+                                asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0 + 4u), "r"(hi0) : "memory");
+                                asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(sp0 + 4u + kG1), "r"(hi1) : "memory");
                             }
                         }
                         continue;
                     }
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const float f = fr[k];
                         const uint32_t g0 = (tb[k] << 2) + wb0;
-                        float gr = gs_re[k];
-                        int qr = q_re[k];
-                        if (FN) {
-                            gr *= win_w[FN ? k : 0][jj];
-                            qr = (int)(__float_as_uint(gr + kQ) - kQbits);
-                        }
-                        const int q1 = (int)(__float_as_uint(fmaf(gr, f, kQ)) - kQbits);
-                        asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(g0), "r"(qr) : "memory");
-                        asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(g0 + kG1), "r"(q1) : "memory");
-                        if (CPLX) {
-                            float gi = gs_im[k];
-                            int qi = q_im[k];
-                            if (FN) {
-                                gi *= win_w[FN ? k : 0][jj];
-                                qi = (int)(__float_as_uint(gi + kQ) - kQbits);
+#pragma unroll
+                        for (int p = 0; p < (CPLX ? 2 : 1); ++p) {
+                            int qk, q1;
+                            if constexpr (!FN) {
+                                qk = p ? q_im[k] : q_re[k];
+                                q1 = (int)(bq[p][k] - kQbits);
+                            } else {
+                                const float g = (p ? gs_im[k] : gs_re[k]) * win_w[FN ? k : 0][jj];
+                                qk = (int)(__float_as_uint(g + kQ) - kQbits);
+                                q1 = (int)(__float_as_uint(fmaf(g, fr[k], kQ)) - kQbits);
                             }
-                            const int qi1 = (int)(__float_as_uint(fmaf(gi, f, kQ)) - kQbits);
-                            asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(g0 + kIm), "r"(qi) : "memory");
-                            asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(g0 + kIm + kG1), "r"(qi1) : "memory");
+                            const uint32_t gp = g0 + (p ? kIm : 0u);
+                            asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(gp), "r"(qk) : "memory");
+                            asm volatile("red.shared.add.s32 [%0], %1;" :: "r"(gp + kG1), "r"(q1) : "memory");
                         }
                     }
                 }
@@ -393,7 +437,10 @@ das_bwd_kernel(DasArgs a) {
                     pw[jj] = 0.f;
                 }
             }
-            for (int q = tid; q < C::NWIN * C::PLANES * C::GROUPS; q += kDasThreads) {
+            // the items beyond a whole number per thread go to warps 1 and 2,
+            // which neither issue copies nor compute transmit terms
+            const int ft = (tid + kDasThreads - 32) % kDasThreads;
+            for (int q = ft; q < C::NWIN * C::PLANES * C::GROUPS; q += kDasThreads) {
                 const int g = q % C::GROUPS, wp = q / C::GROUPS;
                 const int win = wp % C::NWIN, plane = wp / C::NWIN;
                 const int off = s_off[tb * C::NWIN + win];
@@ -467,7 +514,8 @@ das_bwd_kernel(DasArgs a) {
         // the previous iteration)
         {
             int4* clr = reinterpret_cast<int4*>(gwin + ((s + 1) % 3) * C::ACC_BUF);
-            for (int q = tid; q < C::ACC_BUF / 4; q += kDasThreads) clr[q] = make_int4(0, 0, 0, 0);
+            const int ct = (tid + kDasThreads - 96) % kDasThreads;     // the remainder to warp 3
+            for (int q = ct; q < C::ACC_BUF / 4; q += kDasThreads) clr[q] = make_int4(0, 0, 0, 0);
         }
         if (__syncthreads_or(!ok)) {
             // a bounded wait expired: give the copies still in flight (stages

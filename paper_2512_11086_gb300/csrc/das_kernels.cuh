@@ -12,7 +12,7 @@ namespace rcbf {
 template <int VU, int WS, bool CPLX, bool APOD, bool CUBIC, bool IQ, bool D2>
 __global__ void __launch_bounds__(kDasThreads, 2)
 das_tiled_kernel(DasArgs a) {
-    using C = DasCfg<VU, WS, CPLX, CUBIC, D2, APOD>;
+    using C = DasCfg<VU, WS, CPLX, CUBIC, D2, APOD, IQ>;
     extern __shared__ __align__(128) unsigned char smem[];
     if (a.vls_split) {
         // a tile across a virtual-line-source focal depth is left to the
@@ -30,7 +30,7 @@ das_tiled_kernel(DasArgs a) {
 
 template <int VU, int WS, bool CPLX, bool APOD, bool CUBIC, bool IQ, bool D2>
 int das_cfg_one(int* per_sm) {
-    using C = DasCfg<VU, WS, CPLX, CUBIC, D2, APOD>;
+    using C = DasCfg<VU, WS, CPLX, CUBIC, D2, APOD, IQ>;
     auto k = das_tiled_kernel<VU, WS, CPLX, APOD, CUBIC, IQ, D2>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess)
         return check_launch("das: set shared memory");
@@ -81,7 +81,7 @@ int launch_das_vu(const DasArgs& a, int ws, bool apod, bool cubic, bool iq, cuda
     constexpr bool cplx = CPLX_T;
     const unsigned grid = (unsigned)a.tiles_u * a.tiles_v * a.tiles_w * a.n_split;
 #define RCBF_LAUNCH(WSV, CP, AP, CU, Q)                                                                               \
-    das_tiled_kernel<VU, WSV, CP, AP, CU, Q, D2><<<grid, kDasThreads, DasCfg<VU, WSV, CP, CU, D2, AP>::SMEM, s>>>(a); \
+    das_tiled_kernel<VU, WSV, CP, AP, CU, Q, D2><<<grid, kDasThreads, DasCfg<VU, WSV, CP, CU, D2, AP, Q>::SMEM, s>>>(a); \
     return check_launch("das_tiled_kernel");
 #define RCBF_AP(WSV, CP, CU, Q) \
     if (apod) { RCBF_LAUNCH(WSV, CP, true, CU, Q) } else { RCBF_LAUNCH(WSV, CP, false, CU, Q) }

@@ -77,7 +77,7 @@ __device__ __forceinline__ void static_for(F&& f) {
     }
 }
 
-template <int VU, int WS, bool CPLX, bool CUBIC = false, bool D2 = false, bool APOD = false>
+template <int VU, int WS, bool CPLX, bool CUBIC = false, bool D2 = false, bool APOD = false, bool IQ = false>
 struct DasCfg {
     static constexpr int VR = 4 / VU;              // tile rows per thread
     static constexpr int ROWS = 8 * VR;            // tile rows (one warp covers VR rows)
@@ -102,10 +102,15 @@ struct DasCfg {
     static constexpr int OFF_RX = OFF_TX + kMaxOrder * 16;             // float4[kMaxChannels]
     static constexpr int OFF_ALPHA = OFF_RX + kMaxChannels * 16;       // float[NB][CI][ROWS]
     static constexpr int OFF_WOFF = OFF_ALPHA + NB * ALPHA_N * 4;      // int[2][NWIN]
-    static constexpr int OFF_WPH = OFF_WOFF + 2 * NWIN * 4;            // float[NB][NWIN]: IQ window phases
-    static constexpr int OFF_WS0 = OFF_WPH + NB * NWIN * 4;            // float[NB][NWIN]: 2D window starts
+    static constexpr int OFF_WPH = OFF_WOFF + 2 * NWIN * 4;            // float[NB][NWIN]: 2D IQ window phases
+    static constexpr int OFF_WS0 = OFF_WPH + (IQ && D2 ? NB * NWIN * 4 : 0);   // float[NB][NWIN]: 2D window starts
     static constexpr int OFF_ACT = OFF_WS0 + (D2 ? NB * NWIN * 4 : 0); // int[chunks + 1]: active channel chunks, count (APOD)
-    static constexpr int OFF_BAR = ((OFF_ACT + (APOD ? (kMaxChannels / CJ + 1) * 4 : 0) + 7) / 8) * 8;   // uint64[10]
+    // IQ: carrier phases (cycles) of the transmit and receive parts of every
+    // window start
+    static constexpr int OFF_TXPH = ((OFF_ACT + (APOD ? (kMaxChannels / CJ + 1) * 4 : 0) + 7) / 8) * 8;  // float[kMaxOrder]
+    static constexpr bool IQ_SEP = IQ && !D2;    // separable delays: the rotation factorises
+    static constexpr int OFF_RXPH = OFF_TXPH + (IQ_SEP ? kMaxOrder * 4 : 0);                          // float[kMaxChannels]
+    static constexpr int OFF_BAR = OFF_RXPH + (IQ_SEP ? kMaxChannels * 4 : 0);                        // uint64[10]
     static constexpr int OFF_ABORT = OFF_BAR + 80;                     // int: a bounded wait expired
     static constexpr int SMEM = OFF_ABORT + 16;
     static_assert(ALPHA_N <= kDasThreads, "one thread per transmit term");
@@ -169,22 +174,24 @@ template <class T, bool CPLX, int WS, int NWIN, int RAWS, int RAW_WIN_BYTES>
 __device__ __forceinline__ void rewrite_windows(const unsigned char* rawb, const int* woff,
                                                 unsigned char* pairs, int W, float hp, float scale,
                                                 int warp, int lane) {
+    const float hn0 = hp - (float)(2 * lane);          // hp - n of this lane's first interval
     for (int win = warp; win < NWIN; win += kDasThreads / 32) {
         const int off = woff[win];
         const T* r = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES) + off;
         const T* ri = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES + RAWS * 4) + off;
-        for (int n = 2 * lane; n < W; n += 64) {
+        float hn = hn0;
+        for (int n = 2 * lane; n < W; n += 64, hn -= 64.0f) {
             const float r0 = to_f32<T>(r[n], scale), r1 = to_f32<T>(r[n + 1], scale);
             const float r2 = to_f32<T>(r[n + 2], scale);
             const float s0 = r1 - r0, s1 = r2 - r1;
-            const float c0 = fmaf(hp - (float)n, s0, r0), c1 = fmaf(hp - (float)(n + 1), s1, r1);
+            const float c0 = fmaf(hn, s0, r0), c1 = fmaf(hn - 1.0f, s1, r1);
             if (CPLX) {
                 const float i0 = to_f32<T>(ri[n], scale), i1 = to_f32<T>(ri[n + 1], scale);
                 const float i2 = to_f32<T>(ri[n + 2], scale);
                 const float t0 = i1 - i0, t1 = i2 - i1;
                 float4* p = reinterpret_cast<float4*>(pairs + (size_t)(win * WS + n) * 16);
-                p[0] = make_float4(c0, s0, fmaf(hp - (float)n, t0, i0), t0);
-                p[1] = make_float4(c1, s1, fmaf(hp - (float)(n + 1), t1, i1), t1);
+                p[0] = make_float4(c0, s0, fmaf(hn, t0, i0), t0);
+                p[1] = make_float4(c1, s1, fmaf(hn - 1.0f, t1, i1), t1);
             } else {
                 *reinterpret_cast<float4*>(pairs + (size_t)(win * WS + n) * 8) = make_float4(c0, s0, c1, s1);
             }
@@ -266,9 +273,11 @@ __device__ __forceinline__ void das_pipe_init(unsigned char* bar_base, volatile 
 // stop; the caller records the status).
 template <int VU, int WS, bool CPLX, bool APOD, bool CUBIC = false, bool IQ = false, bool D2 = false>
 __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned char* smem, DasPipe& pipe) {
-    using C = DasCfg<VU, WS, CPLX, CUBIC, D2, APOD>;
+    using C = DasCfg<VU, WS, CPLX, CUBIC, D2, APOD, IQ>;
     static_assert(!IQ || CPLX, "IQ beamforming reads two planes");
     float* s_ws0 = reinterpret_cast<float*>(smem + C::OFF_WS0);
+    float* s_txph = reinterpret_cast<float*>(smem + C::OFF_TXPH);
+    float* s_rxph = reinterpret_cast<float*>(smem + C::OFF_RXPH);
     float* s_wph = reinterpret_cast<float*>(smem + C::OFF_WPH);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float4* s_tx = reinterpret_cast<float4*>(smem + C::OFF_TX);
@@ -364,6 +373,13 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             // rounding trick and the window centring folded in
             const float rho = (float)(A - K - (double)a.lo - 0.5 - (double)a.H);
             s_tx[e] = make_float4(tx0, tx1, rho, __int_as_float((int)K));
+            if (C::IQ_SEP) {
+                // carrier phase of the transmit part of every window start of
+                // this transmit: S0 = K_i + K_j + lo, at u = 0 the sample
+                // S0 + 0.5 + H for linear pieces (cubic positions include it)
+                const double x = a.iq_ratio * (K + (double)a.lo + (CUBIC ? 0.0 : 0.5 + (double)a.H));
+                s_txph[e] = (float)(x - floor(x));
+            }
         } else {
             const int j = j_lo + e - a.n_tx;
             const double L = lat_rx_ref - (a.rx_e0 + j * a.rx_pitch);
@@ -371,6 +387,10 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             const double B = d * a.fs_over_c;
             const double K = floor(B);
             s_rx[j] = make_float4((float)L, (float)d, (float)(B - K), __int_as_float((int)K));
+            if (C::IQ_SEP) {
+                const double x = a.iq_ratio * K;
+                s_rxph[j] = (float)(x - floor(x));
+            }
         }
     }
 
@@ -505,22 +525,17 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             rewrite_windows<int, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
         else
             rewrite_windows<float, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
-        if ((IQ || D2) && tid < C::NWIN) {
+        if (D2 && tid < C::NWIN) {
             const int win = tid;
             const int i = (s % n_ic) * C::CI + win / C::CJ, j = chunk_of(s) * C::CJ + win % C::CJ;
-            int S0;
-            if constexpr (D2) {
-                const int w0 = win_start(i, j);
-                s_ws0[pb * C::NWIN + win] = -(float)w0;
-                S0 = Kt + w0;
-            } else {
-                S0 = __float_as_int(s_tx[i].w) + __float_as_int(s_rx[j].w) + a.lo;
-            }
+            const int w0 = win_start(i, j);
+            s_ws0[pb * C::NWIN + win] = -(float)w0;
             if (IQ) {
-                // phase (in cycles) of the window's reference position: the
-                // sample at u = 0 is S0 + 0.5 + H for linear pieces; cubic
-                // positions already include 0.5 + H
-                const double x = a.iq_ratio * ((double)S0 + (CUBIC ? 0.0 : 0.5 + (double)a.H));
+                // the delay is not separable here: the carrier phase (cycles) of
+                // the window's reference position, rotated per term (the sample
+                // at u = 0 is Kt + w0 + 0.5 + H for linear pieces; cubic
+                // positions already include 0.5 + H)
+                const double x = a.iq_ratio * ((double)(Kt + w0) + (CUBIC ? 0.0 : 0.5 + (double)a.H));
                 s_wph[pb * C::NWIN + win] = (float)(x - floor(x));
             }
         }
@@ -551,6 +566,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     // weights and accumulators
     f2x acc2[2] = {0ull, 0ull};
     float acci[4] = {0.f, 0.f, 0.f, 0.f};
+    [[maybe_unused]] float iq_re[4] = {0.f, 0.f, 0.f, 0.f}, iq_im[4] = {0.f, 0.f, 0.f, 0.f};   // IQ sums
     f2x beta2[2][C::CJ];
     f2x apw2[2][C::CJ];
     const float magic = CUBIC ? 8388607.5f : 8388608.0f + (float)a.H;     // 2^23 + H (cubic: on u + 0.5 + H)
@@ -656,6 +672,104 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
         // 48-interval class (more independent loads in flight; measured on the
         // batched B-scan +2.7 % and +1.3 %; four cost the 96 class 4-7 %); the
         // wider forms stay at one (register budget)
+        if constexpr (C::IQ_SEP) {
+            // IQ beamforming: the carrier phase of a term splits into a
+            // transmit part P_i(row) = txph_i + r alpha_i(row) and a receive
+            // part Q_j(voxel) = rxph_j + r beta_j(voxel), so the rotation
+            // e^{j 2 pi (P + Q)} is the product of a factor per (row,
+            // transmit) and a factor per (voxel, channel), the latter computed
+            // once per stage and used for G transmits: the terms of a transmit
+            // are summed rotated by the receive factor, and the sum is rotated
+            // by the transmit factor
+            constexpr int G = C::CI < 2 ? C::CI : 2;
+            const int j0 = chunk_of(s) * C::CJ, i0 = (s % n_ic) * C::CI;
+#pragma unroll 1
+            for (int ig = 0; ig < C::CI; ig += G) {
+                f2x alg[G][2];
+                float ec[G][C::VR], es[G][C::VR];          // transmit factors of this thread's rows
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    float al[C::VR];
+                    const float txph = s_txph[i0 + ig + g];
+#pragma unroll
+                    for (int kr = 0; kr < C::VR; ++kr) {
+                        al[kr] = alb[(ig + g) * C::ROWS + kr];
+                        const float x = fmaf(iqr, al[kr], txph);
+                        __sincosf(6.28318530717958648f * (x - rintf(x)), &es[g][kr], &ec[g][kr]);
+                    }
+                    alg[g][0] = pk(al[0 / VU], al[1 / VU]);
+                    alg[g][1] = pk(al[2 / VU], al[3 / VU]);
+                }
+                float sr[G][4], si[G][4];
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) sr[g][k] = si[g][k] = 0.f;
+                static_for<0, C::CJ>([&](auto jjc) {
+                    constexpr int jj = decltype(jjc)::value;
+                    constexpr int OFF = jj * WS * C::PAIR_BYTES;
+                    // receive factors e^{j 2 pi Q} of the four voxels (times the weights)
+                    const float qj = s_rxph[j0 + jj];
+                    float bt[4], fc[4], fs[4];
+                    upk(beta2[0][jj], bt[0], bt[1]);
+                    upk(beta2[1][jj], bt[2], bt[3]);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float x = fmaf(iqr, bt[k], qj);
+                        __sincosf(6.28318530717958648f * (x - rintf(x)), &fs[k], &fc[k]);
+                    }
+                    if (APOD) {
+                        float w[4];
+                        upk(apw2[0][jj], w[0], w[1]);
+                        upk(apw2[1][jj], w[2], w[3]);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            fc[k] *= w[k];
+                            fs[k] *= w[k];
+                        }
+                    }
+#pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        const uint32_t pb_g = pbase + (ig + g) * (C::CJ * WS * C::PAIR_BYTES);
+#pragma unroll
+                        for (int kp = 0; kp < 2; ++kp) {
+                            const f2x u2 = add2(alg[g][kp], beta2[kp][jj]);
+                            const f2x t2 = add2(u2, magic2);
+                            float u[2], t[2], f[2];
+                            upk(u2, u[0], u[1]);
+                            upk(t2, t[0], t[1]);
+                            if (CUBIC) upk(fma2(add2(t2, pk(-8388608.0f, -8388608.0f)), pk(-1.0f, -1.0f), u2), f[0], f[1]);
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const int k = 2 * kp + h;
+                                const uint32_t addr = (__float_as_uint(t[h]) << SHIFT) + pb_g;
+                                float vr, vi;
+                                if (CUBIC) {
+                                    const float4 p = lds_f4<OFF>(addr);
+                                    const float4 q = lds_f4<OFF + 16>(addr);
+                                    vr = fmaf(fmaf(fmaf(p.w, f[h], p.z), f[h], p.y), f[h], p.x);
+                                    vi = fmaf(fmaf(fmaf(q.w, f[h], q.z), f[h], q.y), f[h], q.x);
+                                } else {
+                                    const float4 p = lds_f4<OFF>(addr);
+                                    vr = fmaf(u[h], p.y, p.x);
+                                    vi = fmaf(u[h], p.w, p.z);
+                                }
+                                sr[g][k] = fmaf(vr, fc[k], fmaf(-vi, fs[k], sr[g][k]));
+                                si[g][k] = fmaf(vr, fs[k], fmaf(vi, fc[k], si[g][k]));
+                            }
+                        }
+                    }
+                });
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float c = ec[g][k / VU], sn = es[g][k / VU];
+                        iq_re[k] = fmaf(c, sr[g][k], fmaf(-sn, si[g][k], iq_re[k]));
+                        iq_im[k] = fmaf(c, si[g][k], fmaf(sn, sr[g][k], iq_im[k]));
+                    }
+            }
+        } else {
 #pragma unroll(CPLX || CUBIC ? 1 : WS <= 48 ? 4 : 2)
         for (int ii = 0; ii < C::CI; ++ii) {
             float al[C::VR];
@@ -666,10 +780,10 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             static_for<0, C::CJ>([&](auto jjc) {
                 constexpr int jj = decltype(jjc)::value;
                 constexpr int OFF = jj * WS * C::PAIR_BYTES;
-                const float phw = IQ ? s_wph[pb * C::NWIN + ii * C::CJ + jj] : 0.0f;
                 [[maybe_unused]] const float ws0 = D2 ? s_ws0[pb * C::NWIN + ii * C::CJ + jj] : 0.0f;
-                // e^{j 2 pi (phw + r u)} applied to (vr, vi)
-                auto iq_rotate = [&](float uu, float& vr, float& vi) {
+                [[maybe_unused]] const float phw = (IQ && D2) ? s_wph[pb * C::NWIN + ii * C::CJ + jj] : 0.0f;
+                // 2D IQ: e^{j 2 pi (phw + r u)} applied to (vr, vi)
+                [[maybe_unused]] auto iq_rotate = [&](float uu, float& vr, float& vi) {
                     const float x = fmaf(iqr, uu, phw);
                     float sn, cs;
                     __sincosf(6.28318530717958648f * (x - rintf(x)), &sn, &cs);
@@ -713,7 +827,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
                                 vi[h] = fmaf(fmaf(fmaf(q.w, f[h], q.z), f[h], q.y), f[h], q.x);
                             }
                         }
-                        if (IQ) {
+                        if constexpr (IQ && D2) {
 #pragma unroll
                             for (int h = 0; h < 2; ++h) iq_rotate(u[h], vr[h], vi[h]);
                         }
@@ -742,7 +856,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
                             const uint32_t addr = (__float_as_uint(t[h]) << SHIFT) + pb_ii;
                             const float4 p = lds_f4<OFF>(addr);
                             float vr = fmaf(u[h], p.y, p.x), vi = fmaf(u[h], p.w, p.z);
-                            if (IQ) iq_rotate(u[h], vr, vi);
+                            if constexpr (IQ && D2) iq_rotate(u[h], vr, vi);
                             float ar, ai;
                             upk(acc2[kp], ar, ai);
                             float wr = 1.f, wi = 1.f;
@@ -764,6 +878,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
                 }
             });
         }
+        }
         mbar_arrive(bar0 + 8 * (kPieceEmpty + pb));
     }
     if (!ok) {
@@ -775,6 +890,12 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     }
     pipe.base += (uint32_t)NS;
 
+    if constexpr (C::IQ_SEP) {
+        acc2[0] = pk(iq_re[0], iq_re[1]);
+        acc2[1] = pk(iq_re[2], iq_re[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acci[k] = iq_im[k];
+    }
     float acc[4];
     upk(acc2[0], acc[0], acc[1]);
     upk(acc2[1], acc[2], acc[3]);

@@ -113,6 +113,28 @@ def test_iq_beamforming_matches_oracle(interp, variant):
     assert rel_l2(oracle.das(g, x, iq_freq=0.0, interp=interp), want) > 0.1
 
 
+@pytest.mark.parametrize("interp", ["linear", "cubic"])
+@pytest.mark.parametrize("tile", [(32, 1, 32), (64, 1, 16), (128, 1, 8)])
+def test_iq_general_ratio_weights_and_tiles(interp, tile):
+    # a demodulation frequency that is not the sampling rate (the carrier
+    # phase of every window start matters: r = f_d / f_s = 0.3), the F#
+    # window with per-channel weights, and every voxels-per-thread class of
+    # the tiled IQ form
+    g = _geom(32, 32, 1024, fs=7.5e6, iq_freq=0.3 * 7.5e6, out_dims=(128, 1, 320),
+              out_min=(-3 * MM, 0.0, 4 * MM), out_max=(3 * MM, 0.0, 22 * MM), f_number=1.0)
+    _, x = _iq_case()
+    w = np.random.default_rng(5).uniform(0.5, 1.5, size=g.n_ch)
+    plan = rc.Plan(rc.make_params(g, decoded_dtype="cf32", das_variant=rc.DAS_TILED, interp=interp, tile=tile))
+    dec = torch.from_numpy(np.stack([x.real, x.imag]).astype(np.float32)).cuda()
+    img = plan.das(dec, apod=torch.from_numpy(w.astype(np.float32)).cuda()).cpu().numpy().astype(np.float64)
+    got = img[0] + 1j * img[1]
+    want = oracle.das(g, x.astype(np.complex64).astype(np.complex128), w=w, interp=interp)
+    err = rel_l2(got, want)
+    print("IQ r=0.3 %s tile %s: rel-L2 %.3e" % (interp, tile, err))
+    assert plan.info()["tiled"]
+    assert err <= TOL
+
+
 def _chain(g_raw, D, taps, frame_seed, n_scatterers, point=None):
     """Encoded RF at 4 f_d -> (plan of the demodulated data, raw int16 RF)."""
     kw = {} if point is None else dict(box_x=(point[0], point[0]), box_z=(point[2], point[2]))
