@@ -566,6 +566,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     // weights and accumulators
     f2x acc2[2] = {0ull, 0ull};
     float acci[4] = {0.f, 0.f, 0.f, 0.f};
+    f2x acci2[2] = {0ull, 0ull};      // complex: imaginary sums of the voxel pairs
     [[maybe_unused]] float iq_re[4] = {0.f, 0.f, 0.f, 0.f}, iq_im[4] = {0.f, 0.f, 0.f, 0.f};   // IQ sums
     f2x beta2[2][C::CJ];
     f2x apw2[2][C::CJ];
@@ -832,41 +833,26 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
                             for (int h = 0; h < 2; ++h) iq_rotate(u[h], vr[h], vi[h]);
                         }
                         if (CPLX) {
-#pragma unroll
-                            for (int h = 0; h < 2; ++h) {
-                                const int k = 2 * kp + h;
-                                float ar, ai;
-                                upk(acc2[kp], ar, ai);
-                                float wr = 1.f, wi = 1.f;
-                                if (APOD) upk(apw2[kp][jj], wr, wi);
-                                const float w = h == 0 ? wr : wi;
-                                if (h == 0) ar = APOD ? fmaf(w, vr[h], ar) : ar + vr[h];
-                                else ai = APOD ? fmaf(w, vr[h], ai) : ai + vr[h];
-                                acc2[kp] = pk(ar, ai);
-                                acci[k] = APOD ? fmaf(w, vi[h], acci[k]) : acci[k] + vi[h];
-                            }
+                            const f2x vr2 = pk(vr[0], vr[1]), vi2 = pk(vi[0], vi[1]);
+                            acc2[kp] = APOD ? fma2(apw2[kp][jj], vr2, acc2[kp]) : add2(acc2[kp], vr2);
+                            acci2[kp] = APOD ? fma2(apw2[kp][jj], vi2, acci2[kp]) : add2(acci2[kp], vi2);
                         } else {
                             const f2x v2 = pk(vr[0], vr[1]);
                             acc2[kp] = APOD ? fma2(apw2[kp][jj], v2, acc2[kp]) : add2(acc2[kp], v2);
                         }
                     } else if (CPLX) {
+                        float vr[2], vi[2];
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
-                            const int k = 2 * kp + h;
                             const uint32_t addr = (__float_as_uint(t[h]) << SHIFT) + pb_ii;
                             const float4 p = lds_f4<OFF>(addr);
-                            float vr = fmaf(u[h], p.y, p.x), vi = fmaf(u[h], p.w, p.z);
-                            if constexpr (IQ && D2) iq_rotate(u[h], vr, vi);
-                            float ar, ai;
-                            upk(acc2[kp], ar, ai);
-                            float wr = 1.f, wi = 1.f;
-                            if (APOD) upk(apw2[kp][jj], wr, wi);
-                            const float w = h == 0 ? wr : wi;
-                            if (h == 0) ar = APOD ? fmaf(w, vr, ar) : ar + vr;
-                            else ai = APOD ? fmaf(w, vr, ai) : ai + vr;
-                            acc2[kp] = pk(ar, ai);
-                            acci[k] = APOD ? fmaf(w, vi, acci[k]) : acci[k] + vi;
+                            vr[h] = fmaf(u[h], p.y, p.x);
+                            vi[h] = fmaf(u[h], p.w, p.z);
+                            if constexpr (IQ && D2) iq_rotate(u[h], vr[h], vi[h]);
                         }
+                        const f2x vr2 = pk(vr[0], vr[1]), vi2 = pk(vi[0], vi[1]);
+                        acc2[kp] = APOD ? fma2(apw2[kp][jj], vr2, acc2[kp]) : add2(acc2[kp], vr2);
+                        acci2[kp] = APOD ? fma2(apw2[kp][jj], vi2, acci2[kp]) : add2(acci2[kp], vi2);
                     } else {
                         const uint32_t ad0 = (__float_as_uint(t[0]) << SHIFT) + pb_ii;
                         const uint32_t ad1 = (__float_as_uint(t[1]) << SHIFT) + pb_ii;
@@ -890,6 +876,10 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     }
     pipe.base += (uint32_t)NS;
 
+    if constexpr (CPLX && !C::IQ_SEP) {
+        upk(acci2[0], acci[0], acci[1]);
+        upk(acci2[1], acci[2], acci[3]);
+    }
     if constexpr (C::IQ_SEP) {
         acc2[0] = pk(iq_re[0], iq_re[1]);
         acc2[1] = pk(iq_re[2], iq_re[3]);
