@@ -32,7 +32,8 @@
 // the tile (W_j <= 1 and 0 <= f <= 1): an accumulator collects at most one
 // term per voxel of the 1024-voxel tile, so it cannot overflow, and a term is
 // rounded to 2^-e <= 2^-19 max|G| (a relative 2e-6 of the largest term of the
-// tile). c[n] is formed in 64-bit integers.
+// tile). c[n] = G0[n] - G1[n] + G1[n-1] is a sum of at most 1024 such terms
+// with weights in [0, 1], so it is formed exactly in 32-bit integers.
 #include <algorithm>
 
 #include "das_tile.cuh"
@@ -254,6 +255,7 @@ das_bwd_kernel(DasArgs a) {
     // channel): beta + 0.5 + H and (F# window) W_j(v)
     // receive terms of voxel pairs (k, k+1) packed in f32x2 registers
     f2x betah2[2][kBwdCJ];
+    uint32_t merge_ok = 0;                  // bit jj: channel jj's receive terms lie within one sample
     float win_w[FN ? 4 : 1][kBwdCJ], wj[kBwdCJ], pw[kBwdCJ];
     float gc = 0.f;                         // dL/dc partial (times -c, scaled)
     bool ok = true;
@@ -290,6 +292,16 @@ das_bwd_kernel(DasArgs a) {
                     }
                     betah2[0][jj] = pk(bt[0], bt[1]);
                     betah2[1][jj] = pk(bt[2], bt[3]);
+                    if (ZL) {
+                        // the thread's four voxels differ only in their receive terms:
+                        // if these lie within one sample in every lane, so do the
+                        // delays of every transmit, and the voxels span at most two
+                        // adjacent intervals (no per-window test needed)
+                        const float spread = fmaxf(fmaxf(bt[0], bt[1]), fmaxf(bt[2], bt[3])) -
+                                             fminf(fminf(bt[0], bt[1]), fminf(bt[2], bt[3]));
+                        const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(spread));
+                        merge_ok = (merge_ok & ~(1u << jj)) | (__uint_as_float(m) < 1.0f ? 1u << jj : 0u);
+                    }
                 }
             }
 
@@ -347,7 +359,8 @@ das_bwd_kernel(DasArgs a) {
                     uint32_t tmin = 0;
                     if (ZL) {
                         tmin = min(min(tb[0], tb[1]), min(tb[2], tb[3]));
-                        span = __reduce_max_sync(0xffffffffu, max(max(tb[0], tb[1]), max(tb[2], tb[3])) - tmin);
+                        span = (merge_ok >> jj) & 1u ? 1u
+                             : __reduce_max_sync(0xffffffffu, max(max(tb[0], tb[1]), max(tb[2], tb[3])) - tmin);
                     }
                     if (ZL && span <= 1) {
                         const uint32_t s0 = (tmin << 2) + wb0;
@@ -468,7 +481,9 @@ das_bwd_kernel(DasArgs a) {
                 float c4[4], pr = 0.f, pc = 0.f;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    c4[e] = (float)((long long)g0[e] - (long long)g1[e + 1] + (long long)g1[e]);
+                    // exact in wrapping 32-bit arithmetic: |c| < 1024 * 2^20 (every term of
+                    // the tile is below 2^20 and weighs at most one)
+                    c4[e] = (float)(int)((uint32_t)g0[e] - (uint32_t)g1[e + 1] + (uint32_t)g1[e]);
                     pr = fmaf(rr[e], c4[e], pr);
                     // interval n0+e: slope times position-weighted sum
                     pc = fmaf(rr[e + 1] - rr[e], fmaf((float)e + cwin, (float)g0[e], (float)g1[e + 1]), pc);
