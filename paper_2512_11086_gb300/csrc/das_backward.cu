@@ -90,8 +90,9 @@ das_bwd_kernel(DasArgs a) {
     using C = BwdCfg<VU, CPLX, WS>;
     static_assert(!ZL || VU == 1, "lanes on rows need 32 rows of 32 voxels");
     // tile row -> (v, w): z-fastest when lanes run over rows
-    auto row_v = [&](int row) { return ZL ? row / a.bw : row % a.bv; };
-    auto row_w = [&](int row) { return ZL ? row % a.bw : row / a.bv; };
+    const StageDiv rdiv(ZL ? a.bw : a.bv);
+    auto row_v = [&](int row) { return ZL ? rdiv.div(row) : rdiv.mod(row); };
+    auto row_w = [&](int row) { return ZL ? rdiv.mod(row) : rdiv.div(row); };
     extern __shared__ __align__(128) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float4* s_tx = reinterpret_cast<float4*>(smem + C::OFF_TX);
@@ -119,6 +120,7 @@ das_bwd_kernel(DasArgs a) {
     const int tile = blockIdx.x % n_tiles;
     const int split = blockIdx.x / n_tiles;
     const int n_ic = a.n_tx / kBwdCI;
+    const StageDiv sdiv(n_ic);               // stage -> (transmit group, channel chunk)
     const int js = (a.n_ch / kBwdCJ) / a.n_split;
     const int jc0 = split * js;
     const int NS = n_ic * js;
@@ -213,7 +215,7 @@ das_bwd_kernel(DasArgs a) {
         const int win = CPLX ? (tid >> 1) : tid;
         const int plane = CPLX ? (tid & 1) : 0;
         const int ii = win / kBwdCJ, jj = win % kBwdCJ;
-        const int i = (s % n_ic) * kBwdCI + ii, j = (jc0 + s / n_ic) * kBwdCJ + jj;
+        const int i = sdiv.mod(s) * kBwdCI + ii, j = (jc0 + sdiv.div(s)) * kBwdCJ + jj;
         const int S0 = __float_as_int(s_tx[i].w) + __float_as_int(s_rx[j].w) + a.lo;
         const int A = S0 & ~7;
         if (plane == 0) { s_off[b * C::NWIN + win] = S0 - A; s_S0[b * C::NWIN + win] = S0; }
@@ -233,6 +235,8 @@ das_bwd_kernel(DasArgs a) {
         }
     };
     // transmit terms of stage s for every tile row
+    const float gvt_row = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]), gwt_row = (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]);
+    const float gvz_row = (float)a.Gv[2], gwz_row = (float)a.Gw[2];
     auto make_alpha = [&](int s) {
         // the last warps (warp 0 issues the copies)
         const int at = tid - (kDasThreads - kBwdCI * C::ROWS);
@@ -240,9 +244,9 @@ das_bwd_kernel(DasArgs a) {
         const int ii = at / C::ROWS, row = at % C::ROWS;
         const float dv = (float)row_v(row) - 0.5f * (a.bv - 1);
         const float dw = (float)row_w(row) - 0.5f * (a.bw - 1);
-        const float dL = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]) * dv + (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]) * dw;
-        const float dzz = (float)a.Gv[2] * dv + (float)a.Gw[2] * dw;
-        const float4 tx = s_tx[(s % n_ic) * kBwdCI + ii];
+        const float dL = gvt_row * dv + gwt_row * dw;
+        const float dzz = gvz_row * dv + gwz_row * dw;
+        const float4 tx = s_tx[sdiv.mod(s) * kBwdCI + ii];
         const float al = tx_offset(a.tx_wave, tx, dL, dzz, Zf, Zfoc, fsc);
         s_alpha[(s & 1) * kBwdCI * C::ROWS + ii * C::ROWS + row] = fminf(fmaxf(al, tx.z - a.reach_a), tx.z + a.reach_a);
     };
@@ -274,7 +278,7 @@ das_bwd_kernel(DasArgs a) {
     for (int s = 0; s <= NS; ++s) {
         if (s < NS) issue(s);
         if (s < NS) {
-            const int ic = s % n_ic, jc = jc0 + s / n_ic;
+            const int ic = sdiv.mod(s), jc = jc0 + sdiv.div(s);
             if (ic == 0) {
 #pragma unroll
                 for (int jj = 0; jj < kBwdCJ; ++jj) {
@@ -439,7 +443,7 @@ das_bwd_kernel(DasArgs a) {
             // multiple of 8; traces are multiples of 8 long, so a group lies
             // wholly inside or wholly outside its trace).
             const int t = s - 1, tb = t & 1;
-            const int ic = t % n_ic, jc = jc0 + t / n_ic;
+            const int ic = sdiv.mod(t), jc = jc0 + sdiv.div(t);
             ok = mbar_wait_parity(bar0 + 8 * tb, (phase >> tb) & 1u, a.wait_ns) && ok;
             phase ^= 1u << tb;
             const int* acc = gwin + (t % 3) * C::ACC_BUF;

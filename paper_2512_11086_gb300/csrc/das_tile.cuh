@@ -251,6 +251,18 @@ struct DasPipe {
     uint32_t base;
 };
 
+// Division by a small runtime count (transmit groups per channel chunk, tile
+// rows per depth row): floor(s / n) = umulhi(s, ceil(2^32 / n)), exact
+// whenever s n < 2^32 (the indices stay below 2^16, n below 2^10).
+struct StageDiv {
+    int n;
+    uint32_t mul;
+    __device__ __forceinline__ explicit StageDiv(int n_)
+        : n(n_), mul(n_ > 1 ? (uint32_t)((0x100000000ull + (unsigned)n_ - 1u) / (unsigned)n_) : 0u) {}
+    __device__ __forceinline__ int div(int s) const { return n > 1 ? (int)__umulhi((uint32_t)s, mul) : s; }
+    __device__ __forceinline__ int mod(int s) const { return s - div(s) * n; }
+};
+
 // Initialise the CTA's mbarriers (thread 0) and pre-complete the first phase
 // of every "empty" barrier so that the first fill of each buffer needs no
 // special case. Ends with a CTA barrier.
@@ -294,6 +306,8 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     const int tile = unit % n_tiles;
     const int split = unit / n_tiles;
     const int n_ic = a.n_tx / C::CI;
+    const StageDiv sdiv(n_ic);        // stage -> (transmit group, channel chunk) without a division
+    const StageDiv bvdiv(a.bv);       // tile row -> (v, w) offsets
     const int js = (a.n_ch / C::CJ) / a.n_split;     // channel chunks of this unit
     const int jc0 = split * js;
     int* s_act = reinterpret_cast<int*>(smem + C::OFF_ACT);
@@ -403,12 +417,14 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     const float gvr = (float)(a.rx_axis ? a.Gv[1] : a.Gv[0]);
     const float gwr = (float)(a.rx_axis ? a.Gw[1] : a.Gw[0]);
     const float guz = (float)a.Gu[2], gvz = (float)a.Gv[2], gwz = (float)a.Gw[2];
+    // transmit-lateral steps of the tile rows (converted once, not per stage)
+    const float gvt_row = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]), gwt_row = (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]);
     auto voxel_offsets = [&](int k, float& dlr, float& dz) {
         const int ku = k % VU, kr = k / VU;
         const int row = warp * C::VR + kr;
         const float du = (float)(lane + 32 * ku) - 0.5f * (C::BU - 1);
-        const float dv = (float)(row % a.bv) - 0.5f * (a.bv - 1);
-        const float dw = (float)(row / a.bv) - 0.5f * (a.bw - 1);
+        const float dv = (float)bvdiv.mod(row) - 0.5f * (a.bv - 1);
+        const float dw = (float)bvdiv.div(row) - 0.5f * (a.bw - 1);
         dlr = gur * du + gvr * dv + gwr * dw;
         dz = guz * du + gvz * dv + gwz * dw;
     };
@@ -449,7 +465,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     }
     __syncthreads();   // reference tables and the chunk list ready
     // channel chunk of stage s (forms without weights never skip a chunk)
-    auto chunk_of = [&](int s) -> int { return APOD ? s_act[s / n_ic] : jc0 + s / n_ic; };
+    auto chunk_of = [&](int s) -> int { return APOD ? s_act[sdiv.div(s)] : jc0 + sdiv.div(s); };
     const int NS = n_ic * (APOD ? s_act[kMaxChannels / C::CJ] : js);
 
     volatile int* abort = reinterpret_cast<volatile int*>(smem + C::OFF_ABORT);
@@ -476,7 +492,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
         const int win = CPLX ? (copy >> 1) : copy;
         const int plane = CPLX ? (copy & 1) : 0;
         const int ii = win / C::CJ, jj = win % C::CJ;
-        const int i = (s % n_ic) * C::CI + ii, j = chunk_of(s) * C::CJ + jj;
+        const int i = sdiv.mod(s) * C::CI + ii, j = chunk_of(s) * C::CJ + jj;
         // first staged sample (cubic: one before the window, for the stencil)
         const int S0 = (D2 ? Kt + win_start(i, j) : __float_as_int(s_tx[i].w) + __float_as_int(s_rx[j].w) + a.lo) -
                        (CUBIC ? 1 : 0);
@@ -527,7 +543,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             rewrite_windows<float, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
         if (D2 && tid < C::NWIN) {
             const int win = tid;
-            const int i = (s % n_ic) * C::CI + win / C::CJ, j = chunk_of(s) * C::CJ + win % C::CJ;
+            const int i = sdiv.mod(s) * C::CI + win / C::CJ, j = chunk_of(s) * C::CJ + win % C::CJ;
             const int w0 = win_start(i, j);
             s_ws0[pb * C::NWIN + win] = -(float)w0;
             if (IQ) {
@@ -543,11 +559,11 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
         if (ae < C::ALPHA_N) {
             // transmit terms of this stage for every tile row (alpha depends on the row only)
             const int ii = ae / C::ROWS, row = ae % C::ROWS;
-            const float dv = (float)(row % a.bv) - 0.5f * (a.bv - 1);
-            const float dw = (float)(row / a.bv) - 0.5f * (a.bw - 1);
-            const float dL = (float)(a.tx_axis ? a.Gv[1] : a.Gv[0]) * dv + (float)(a.tx_axis ? a.Gw[1] : a.Gw[0]) * dw;
-            const float dz = (float)a.Gv[2] * dv + (float)a.Gw[2] * dw;
-            const float4 tx = s_tx[(s % n_ic) * C::CI + ii];
+            const float dv = (float)bvdiv.mod(row) - 0.5f * (a.bv - 1);
+            const float dw = (float)bvdiv.div(row) - 0.5f * (a.bw - 1);
+            const float dL = gvt_row * dv + gwt_row * dw;
+            const float dz = gvz * dv + gwz * dw;
+            const float4 tx = s_tx[sdiv.mod(s) * C::CI + ii];
             if constexpr (D2) {
                 // P = (lat_tx - e_i)^2 + z^2 of the row, clamped to its box bounds
                 const float Lt = tx.x + dL, Zv = Zf + dz;
@@ -592,8 +608,8 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             const int ku = k % VU, kr = k / VU;
             const int row = warp * C::VR + kr;
             const float du = (float)(lane + 32 * ku) - 0.5f * (C::BU - 1);
-            const float dv = (float)(row % a.bv) - 0.5f * (a.bv - 1);
-            const float dw = (float)(row / a.bv) - 0.5f * (a.bw - 1);
+            const float dv = (float)bvdiv.mod(row) - 0.5f * (a.bv - 1);
+            const float dw = (float)bvdiv.div(row) - 0.5f * (a.bw - 1);
             const float dlt = gut * du + gvt * dv + gwt * dw;
             float de;
             if (a.tx_wave == RCBF_TX_PLANE) {
@@ -625,7 +641,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     int landed = 0;                   // last stage whose raw windows this thread waited for
 
     for (int s = 0; ok && s < NS; ++s) {
-        const int ic = s % n_ic, jc = chunk_of(s);
+        const int ic = sdiv.mod(s), jc = chunk_of(s);
         const int pb = piece_buf(s);
         if (ic == 0) {
             // per-voxel receive terms (and apodization) for this channel chunk
@@ -683,7 +699,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
             // are summed rotated by the receive factor, and the sum is rotated
             // by the transmit factor
             constexpr int G = C::CI < 2 ? C::CI : 2;
-            const int j0 = chunk_of(s) * C::CJ, i0 = (s % n_ic) * C::CI;
+            const int j0 = chunk_of(s) * C::CJ, i0 = sdiv.mod(s) * C::CI;
 #pragma unroll 1
             for (int ig = 0; ig < C::CI; ig += G) {
                 f2x alg[G][2];
@@ -913,7 +929,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
         for (int k = 0; k < 4; ++k) {
             const int ku = k % VU, kr = k / VU;
             const int row = warp * C::VR + kr;
-            const int iu = u0 + lane + 32 * ku, iv = v0 + row % a.bv, iw = w0 + row / a.bv;
+            const int iu = u0 + lane + 32 * ku, iv = v0 + bvdiv.mod(row), iw = w0 + bvdiv.div(row);
             if (iu < a.n_u && iv < a.n_v && iw < a.n_w) {
                 const long long o = (long long)iw * a.out_sw + (long long)iv * a.out_sv + (long long)iu * a.out_su;
                 a.image[o] = split ? __ldcg(a.image + o) + acc[k] : acc[k];
@@ -934,7 +950,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     for (int k = 0; k < 4; ++k) {
         const int ku = k % VU, kr = k / VU;
         const int row = warp * C::VR + kr;
-        const int iu = u0 + lane + 32 * ku, iv = v0 + row % a.bv, iw = w0 + row / a.bv;
+        const int iu = u0 + lane + 32 * ku, iv = v0 + bvdiv.mod(row), iw = w0 + bvdiv.div(row);
         if (iu < a.n_u && iv < a.n_v && iw < a.n_w) {
             const long long o = (long long)iw * a.out_sw + (long long)iv * a.out_sv + (long long)iu * a.out_su;
             out[o] = acc[k];
