@@ -67,6 +67,27 @@ std::vector<uint32_t> build_afrag(const std::vector<int8_t>& H, int n) {
 
 // A = H^T fragments of mma.m16n8k16 (row-major A, FP16 +-1): register r of
 // lane (g, t) holds rows g (+8 for r odd) and k pair 2t, 2t+1 (+8 for r >= 2).
+// A = H^T as the tcgen05 decode's shared-memory operand: FP16 +-1, K-major,
+// 128-byte swizzled. Per K atom of 64 acquisitions (atoms = max(1, n / 64)),
+// row i of 128 (rows >= n zero) holds eight 16-byte chunks c of the
+// acquisitions k = 64 atom + 8 c + 0..7; chunk c of row i sits at
+// 1024 (i / 8) + 128 (i % 8) + 16 (c xor (i % 8)) within the 16 KB atom.
+std::vector<uint16_t> build_a_tc(const std::vector<int8_t>& H, int n) {
+    const int atoms = n > 64 ? n / 64 : 1;
+    std::vector<uint16_t> a((size_t)atoms * 128 * 64, 0);
+    for (int atom = 0; atom < atoms; ++atom)
+        for (int i = 0; i < 128; ++i)
+            for (int c = 0; c < 8; ++c)
+                for (int e = 0; e < 8; ++e) {
+                    const int k = atom * 64 + c * 8 + e;
+                    if (i >= n || k >= n) continue;
+                    const size_t off = (size_t)atom * 16384 + (size_t)(i >> 3) * 1024 + (size_t)(i & 7) * 128 +
+                                       (size_t)((c ^ (i & 7)) << 4);
+                    a[off / 2 + e] = H[(size_t)k * n + i] > 0 ? 0x3C00u : 0xBC00u;
+                }
+    return a;
+}
+
 std::vector<uint32_t> build_afrag16(const std::vector<int8_t>& H, int n) {
     const int MT = n / 16, KC = n / 16;
     std::vector<uint32_t> out((size_t)MT * KC * 32 * 4);
@@ -526,6 +547,12 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
             if (cudaMalloc(&h.d_hsum, hs.size() * 4) != cudaSuccess) return fail(RCBF_ENOMEM, "rcbf_plan: cudaMalloc sums");
             if (cudaMemcpy(h.d_hsum, hs.data(), hs.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
                 return fail(RCBF_ECUDA, "rcbf_plan: copy sums");
+            if (n <= 128) {
+                const std::vector<uint16_t> at = build_a_tc(H, n);
+                if (cudaMalloc(&h.d_atc, at.size() * 2) != cudaSuccess) return fail(RCBF_ENOMEM, "rcbf_plan: cudaMalloc A");
+                if (cudaMemcpy(h.d_atc, at.data(), at.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess)
+                    return fail(RCBF_ECUDA, "rcbf_plan: copy A");
+            }
         }
         if ((rc = configure_decode(h)) != RCBF_OK) { std::string m = g_last_error; rcbf_destroy(plan); return set_error(rc, m); }
         if (p.demod_decimation && (rc = configure_demod_decode(h)) != RCBF_OK) {
@@ -595,6 +622,7 @@ void rcbf_destroy(rcbf_plan_t plan) {
     if (h.d_hmat) cudaFree(h.d_hmat);
     if (h.d_afrag16) cudaFree(h.d_afrag16);
     if (h.d_hsum) cudaFree(h.d_hsum);
+    if (h.d_atc) cudaFree(h.d_atc);
     if (h.d_status) cudaFree(h.d_status);
     if (h.d_partial) cudaFree(h.d_partial);
     if (h.d_taps) cudaFree(h.d_taps);

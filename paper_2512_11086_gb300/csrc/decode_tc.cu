@@ -72,8 +72,8 @@ struct TcCfg {
     static constexpr int OFF_B = OFF_RAW + RS * TILE_BYTES;        // 2 x (lo, hi) FP16 operand tiles
     static constexpr int OFF_STAGING = OFF_B + 2 * 2 * TILE_BYTES; // 2 output staging tiles
     static constexpr int OFF_BAR = OFF_STAGING + 2 * STAGING;
-    // raw_full[RS], raw_empty[RS], b_full[2], b_empty[2], accf[2], acce[2]
-    static constexpr int NBAR = 2 * RS + 8;
+    // raw_full[RS], raw_empty[RS], b_full[2], b_empty[2], accf[2], acce[2], a_full
+    static constexpr int NBAR = 2 * RS + 9;
     static constexpr int OFF_MISC = OFF_BAR + 8 * NBAR;     // tmem address, abort flag
     // + alignment slack of the dynamic base; at least 120 KB so that one CTA
     // holds an SM (two would not fit) and the tensor-memory allocation of a
@@ -172,7 +172,7 @@ __device__ __forceinline__ float decoded_value(float hi, float lo, float c1) {
 template <int N, int DT>
 __global__ void __launch_bounds__(kTcThreads, 1)
 decode_tc_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_out,
-                 const int8_t* __restrict__ hmat, const int* __restrict__ hsum, long long n_cols, float inv_n,
+                 const uint16_t* __restrict__ atc, const int* __restrict__ hsum, long long n_cols, float inv_n,
                  int* status, long long wait_ns) {
     constexpr int ES = DT == RCBF_F16 ? 2 : 4;
     using C = TcCfg<N, ES>;
@@ -190,6 +190,7 @@ decode_tc_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_consta
     auto b_empty = [&](int b) { return bar0 + 8u * (2 * RS + 2 + b); };
     auto accf_bar = [&](int a) { return bar0 + 8u * (2 * RS + 4 + a); };
     auto acce_bar = [&](int a) { return bar0 + 8u * (2 * RS + 6 + a); };
+    const uint32_t a_full = bar0 + 8u * (2 * RS + 8);
     uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + C::OFF_MISC);
     volatile int* abort = reinterpret_cast<volatile int*>(smem + C::OFF_MISC + 4);
     auto raw_buf = [&](int s) { return sbase + C::OFF_RAW + (uint32_t)(s * C::TILE_BYTES); };
@@ -198,7 +199,9 @@ decode_tc_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_consta
     const long long n_tiles = (n_cols + kTcCols - 1) / kTcCols;
     const int my_tiles = blockIdx.x < n_tiles ? (int)((n_tiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
 
-    // ---- set-up: barriers, A = H^T (FP16 +-1, K-major, 128-byte swizzle, rows >= n zero), tensor memory
+    // ---- set-up: barriers; A = H^T (FP16 +-1, K-major, 128-byte swizzle, rows >= n
+    // zero), prepared with the plan, arrives by one bulk copy while the
+    // tensor memory is allocated; tensor memory
     if (tid == 0) {
         for (int s = 0; s < RS; ++s) {
             mbar_init(raw_full(s), 1);
@@ -210,31 +213,14 @@ decode_tc_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_consta
             mbar_init(accf_bar(b), 1);
             mbar_init(acce_bar(b), kTcEpiThreads);
         }
+        mbar_init(a_full, 1);
         *abort = 0;
         fence_mbar_init();
         asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&map_in)) : "memory");
         asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&map_out)) : "memory");
+        mbar_arrive_expect_tx(a_full, (uint32_t)C::A_BYTES);
+        bulk_g2s(sbase + C::OFF_A, atc, (uint32_t)C::A_BYTES, a_full);
     }
-    for (int q = tid; q < C::KATOMS * 128 * 8; q += kTcThreads) {
-        // 16-byte chunk q: K atom q / 1024, row i, logical chunk c (8 k values)
-        const int atom = q >> 10, i = (q >> 3) & 127, c = q & 7;
-        uint32_t w[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            uint32_t word = 0;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k = atom * 64 + c * 8 + 2 * e + h;
-                uint32_t bits = 0;
-                if (i < N && k < N) bits = hmat[k * N + i] > 0 ? 0x3C00u : 0xBC00u;
-                word |= bits << (16 * h);
-            }
-            w[e] = word;
-        }
-        const uint32_t off = C::OFF_A + atom * 16384 + (i >> 3) * 1024 + (i & 7) * 128 + ((c ^ (i & 7)) << 4);
-        *reinterpret_cast<uint4*>(smem + off) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
-    fence_proxy_async_smem();
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(s_tmem)), "r"(kTcTmemCols) : "memory");
@@ -274,6 +260,7 @@ decode_tc_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_consta
             const uint32_t idesc = (1u << 4) | (1u << 16) | ((uint32_t)(2 * kTcCols >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
             const uint32_t a_base = sbase + C::OFF_A;
             int committed = 0;
+            ok = wait(a_full, 0);
             for (int j = 0; j < my_tiles && ok; ++j) {
                 const int b = j & 1;
                 if (!(ok = wait(b_full(b), j / 2))) break;
@@ -401,6 +388,8 @@ decode_tc_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_consta
         *abort = 1;
         if (lane == 0) atomicOr(status, kStatusWaitExpired);
     }
+    // the copy of A lands before the CTA may exit (it normally did long ago)
+    if (tid == 0) mbar_wait_parity(a_full, 0, wait_ns);
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
@@ -444,7 +433,7 @@ template <int N, int DT>
 int tc_launch_job(const TcJob& job, int* status, long long wait_ns, cudaStream_t s) {
     constexpr int ES = DT == RCBF_F16 ? 2 : 4;
     decode_tc_kernel<N, DT><<<job.grid, kTcThreads, TcCfg<N, ES>::SMEM, s>>>(
-        job.in_map, job.out_map, job.hmat, job.hsum, job.n_cols, job.inv_n, status, wait_ns);
+        job.in_map, job.out_map, job.atc, job.hsum, job.n_cols, job.inv_n, status, wait_ns);
     return check_launch("decode_tc_kernel");
 }
 
@@ -464,7 +453,8 @@ int tc_prepare(const PlanHost& h, const int16_t* rf, void* out, TcJob* job) {
     const long long tiles = (n_cols + kTcCols - 1) / kTcCols;
     long long grid = h.n_sms > 0 ? h.n_sms : 1;
     if (grid > tiles) grid = tiles;
-    job->hmat = h.d_hmat;
+    if (!h.d_atc) return set_error(RCBF_EUNSUPPORTED, "decode (tcgen05): the plan holds no A operand image (order above 128)");
+    job->atc = h.d_atc;
     job->hsum = h.d_hsum;
     job->n_cols = n_cols;
     job->inv_n = 1.0f / (float)h.p.n_tx;

@@ -110,6 +110,8 @@ struct PlanHost {
     int8_t* d_hmat;         // device H (plain decode)
     uint32_t* d_afrag16;    // device A fragments, FP16 form
     int* d_hsum;            // device column sums of H
+    uint16_t* d_atc;        // device A = H^T operand image of the tcgen05 decode (FP16 +-1, K-major,
+                            // 128-byte swizzled, rows >= n zero), copied whole into shared memory
     int* d_status;          // device status word
     int n_sms;              // SMs of the plan's device
     int decode_blocks_per_sm;
@@ -163,7 +165,7 @@ int configure_decode_tc(const PlanHost& h, int dtype);
 // the batch: prepared at rcbf_batch_create, launched by every rcbf_batch_run.
 struct TcJob {
     CUtensorMap in_map, out_map;
-    const int8_t* hmat;
+    const uint16_t* atc;
     const int* hsum;
     long long n_cols;
     float inv_n;
