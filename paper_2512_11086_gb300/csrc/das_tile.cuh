@@ -199,6 +199,36 @@ __device__ __forceinline__ void rewrite_windows(const unsigned char* rawb, const
     }
 }
 
+// Real raw windows of one stage -> line pieces, a half-warp per window: lane
+// l of the half-warp rewrites the K = WS / 16 intervals K l .. K l + K - 1
+// from K + 1 raw samples, so a warp covers two windows per pass with fewer
+// instructions per window than one interval pair per lane. Intervals past
+// the window's W are written too (from staged samples inside the buffer) and
+// never read.
+template <class T, int WS, int NWIN, int RAW_WIN_BYTES>
+__device__ __forceinline__ void rewrite_windows_real(const unsigned char* rawb, const int* woff,
+                                                     unsigned char* pairs, int W, float hp, float scale,
+                                                     int warp, int lane) {
+    constexpr int K = WS / 16;
+    static_assert(K * 16 == WS && NWIN % 2 == 0, "a half-warp per window");
+    const int half = lane >> 4, n0 = K * (lane & 15);
+    const float hn0 = hp - (float)n0;                   // hp - n of this lane's first interval
+    for (int w2 = warp; w2 < NWIN / 2; w2 += kDasThreads / 32) {
+        const int win = 2 * w2 + half;
+        if (n0 >= W) continue;
+        const T* r = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES) + woff[win] + n0;
+        float rv[K + 1];
+#pragma unroll
+        for (int e = 0; e <= K; ++e) rv[e] = to_f32<T>(r[e], scale);
+        float2* p = reinterpret_cast<float2*>(pairs + (size_t)(win * WS + n0) * 8);
+#pragma unroll
+        for (int e = 0; e < K; ++e) {
+            const float sl = rv[e + 1] - rv[e];
+            p[e] = make_float2(fmaf(hn0 - (float)e, sl, rv[e]), sl);
+        }
+    }
+}
+
 // Raw windows of one stage -> cubic Hermite pieces (coefficients of the
 // interval's cubic in its local fraction). The copy starts one sample before
 // the window, so interval n reads raw samples n .. n+3 (after the offset).
@@ -535,6 +565,13 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
                 rewrite_windows_cubic<int, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, a.scale, warp, lane);
             else
                 rewrite_windows_cubic<float, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, a.scale, warp, lane);
+        } else if (!CPLX) {
+            if (a.dtype == RCBF_F16)
+                rewrite_windows_real<__half, WS, C::NWIN, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
+            else if (a.dtype == RCBF_I32)
+                rewrite_windows_real<int, WS, C::NWIN, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
+            else
+                rewrite_windows_real<float, WS, C::NWIN, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
         } else if (a.dtype == RCBF_F16)
             rewrite_windows<__half, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
         else if (a.dtype == RCBF_I32)
