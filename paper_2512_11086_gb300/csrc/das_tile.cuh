@@ -167,48 +167,16 @@ template <> __device__ __forceinline__ float to_f32<float>(float v, float) { ret
 template <> __device__ __forceinline__ float to_f32<__half>(__half v, float) { return __half2float(v); }
 template <> __device__ __forceinline__ float to_f32<int>(int v, float scale) { return (float)v * scale; }
 
-// Raw windows of one stage -> line pieces. Lane l of a warp rewrites the
-// intervals 2l and 2l+1 (three raw samples, one 16-byte store), so a warp
-// covers 64 intervals per pass.
+// Raw windows of one stage -> line pieces, a half-warp per window: lane l of
+// the half-warp rewrites the K = WS / 16 intervals K l .. K l + K - 1 from
+// K + 1 staged samples (per plane), so a warp covers two windows per pass
+// with fewer instructions per window than one interval pair per lane.
+// Intervals past the window's W are written too (from staged samples inside
+// the buffer) and never read.
 template <class T, bool CPLX, int WS, int NWIN, int RAWS, int RAW_WIN_BYTES>
-__device__ __forceinline__ void rewrite_windows(const unsigned char* rawb, const int* woff,
-                                                unsigned char* pairs, int W, float hp, float scale,
-                                                int warp, int lane) {
-    const float hn0 = hp - (float)(2 * lane);          // hp - n of this lane's first interval
-    for (int win = warp; win < NWIN; win += kDasThreads / 32) {
-        const int off = woff[win];
-        const T* r = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES) + off;
-        const T* ri = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES + RAWS * 4) + off;
-        float hn = hn0;
-        for (int n = 2 * lane; n < W; n += 64, hn -= 64.0f) {
-            const float r0 = to_f32<T>(r[n], scale), r1 = to_f32<T>(r[n + 1], scale);
-            const float r2 = to_f32<T>(r[n + 2], scale);
-            const float s0 = r1 - r0, s1 = r2 - r1;
-            const float c0 = fmaf(hn, s0, r0), c1 = fmaf(hn - 1.0f, s1, r1);
-            if (CPLX) {
-                const float i0 = to_f32<T>(ri[n], scale), i1 = to_f32<T>(ri[n + 1], scale);
-                const float i2 = to_f32<T>(ri[n + 2], scale);
-                const float t0 = i1 - i0, t1 = i2 - i1;
-                float4* p = reinterpret_cast<float4*>(pairs + (size_t)(win * WS + n) * 16);
-                p[0] = make_float4(c0, s0, fmaf(hn, t0, i0), t0);
-                p[1] = make_float4(c1, s1, fmaf(hn - 1.0f, t1, i1), t1);
-            } else {
-                *reinterpret_cast<float4*>(pairs + (size_t)(win * WS + n) * 8) = make_float4(c0, s0, c1, s1);
-            }
-        }
-    }
-}
-
-// Real raw windows of one stage -> line pieces, a half-warp per window: lane
-// l of the half-warp rewrites the K = WS / 16 intervals K l .. K l + K - 1
-// from K + 1 raw samples, so a warp covers two windows per pass with fewer
-// instructions per window than one interval pair per lane. Intervals past
-// the window's W are written too (from staged samples inside the buffer) and
-// never read.
-template <class T, int WS, int NWIN, int RAW_WIN_BYTES>
-__device__ __forceinline__ void rewrite_windows_real(const unsigned char* rawb, const int* woff,
-                                                     unsigned char* pairs, int W, float hp, float scale,
-                                                     int warp, int lane) {
+__device__ __forceinline__ void rewrite_windows_hw(const unsigned char* rawb, const int* woff,
+                                                   unsigned char* pairs, int W, float hp, float scale,
+                                                   int warp, int lane) {
     constexpr int K = WS / 16;
     static_assert(K * 16 == WS && NWIN % 2 == 0, "a half-warp per window");
     const int half = lane >> 4, n0 = K * (lane & 15);
@@ -216,53 +184,74 @@ __device__ __forceinline__ void rewrite_windows_real(const unsigned char* rawb, 
     for (int w2 = warp; w2 < NWIN / 2; w2 += kDasThreads / 32) {
         const int win = 2 * w2 + half;
         if (n0 >= W) continue;
-        const T* r = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES) + woff[win] + n0;
+        const int off = woff[win] + n0;
+        const T* r = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES) + off;
         float rv[K + 1];
 #pragma unroll
         for (int e = 0; e <= K; ++e) rv[e] = to_f32<T>(r[e], scale);
-        float2* p = reinterpret_cast<float2*>(pairs + (size_t)(win * WS + n0) * 8);
+        if constexpr (CPLX) {
+            const T* ri = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES + RAWS * 4) + off;
+            float iv[K + 1];
 #pragma unroll
-        for (int e = 0; e < K; ++e) {
-            const float sl = rv[e + 1] - rv[e];
-            p[e] = make_float2(fmaf(hn0 - (float)e, sl, rv[e]), sl);
+            for (int e = 0; e <= K; ++e) iv[e] = to_f32<T>(ri[e], scale);
+            float4* p = reinterpret_cast<float4*>(pairs + (size_t)(win * WS + n0) * 16);
+#pragma unroll
+            for (int e = 0; e < K; ++e) {
+                const float sr = rv[e + 1] - rv[e], si = iv[e + 1] - iv[e];
+                const float h = hn0 - (float)e;
+                p[e] = make_float4(fmaf(h, sr, rv[e]), sr, fmaf(h, si, iv[e]), si);
+            }
+        } else {
+            float2* p = reinterpret_cast<float2*>(pairs + (size_t)(win * WS + n0) * 8);
+#pragma unroll
+            for (int e = 0; e < K; ++e) {
+                const float sl = rv[e + 1] - rv[e];
+                p[e] = make_float2(fmaf(hn0 - (float)e, sl, rv[e]), sl);
+            }
         }
     }
 }
 
-// Raw windows of one stage -> cubic Hermite pieces (coefficients of the
-// interval's cubic in its local fraction). The copy starts one sample before
-// the window, so interval n reads raw samples n .. n+3 (after the offset).
-// Lane l rewrites the intervals 2l and 2l+1 from five raw samples.
+// The same for cubic Hermite pieces: the copy starts one sample before the
+// window, so interval n reads staged samples n .. n+3 (after the offset) and
+// K intervals read K + 3 samples per plane. Complex 96-interval windows take
+// a whole warp (K = 3), which keeps the staged samples of a lane in registers.
 template <class T, bool CPLX, int WS, int NWIN, int RAWS, int RAW_WIN_BYTES>
-__device__ __forceinline__ void rewrite_windows_cubic(const unsigned char* rawb, const int* woff,
-                                                      unsigned char* pairs, int W, float scale,
-                                                      int warp, int lane) {
+__device__ __forceinline__ void rewrite_windows_cubic_hw(const unsigned char* rawb, const int* woff,
+                                                         unsigned char* pairs, int W, float scale,
+                                                         int warp, int lane) {
+    constexpr int LPW = (CPLX && WS == 96) ? 32 : 16;    // lanes per window
+    constexpr int K = WS / LPW;
+    constexpr int WPP = 32 / LPW;                         // windows per warp pass
+    static_assert(K * LPW == WS && NWIN % WPP == 0, "whole windows per warp pass");
     auto coeffs = [](float p0, float p1, float p2, float p3) {
         const float m1 = 0.5f * (p2 - p0), m2 = 0.5f * (p3 - p1);
         const float d = p2 - p1;
         return make_float4(p1, m1, fmaf(3.0f, d, -(2.0f * m1 + m2)), fmaf(-2.0f, d, m1 + m2));
     };
-    for (int win = warp; win < NWIN; win += kDasThreads / 32) {
-        const int off = woff[win];
+    const int half = lane / LPW, n0 = K * (lane % LPW);
+    for (int w2 = warp; w2 < NWIN / WPP; w2 += kDasThreads / 32) {
+        const int win = WPP * w2 + half;
+        if (n0 >= W) continue;
+        const int off = woff[win] + n0;
         const T* r = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES) + off;
-        const T* ri = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES + RAWS * 4) + off;
-        for (int n = 2 * lane; n < W; n += 64) {
-            float q[5];
+        float q[K + 3];
 #pragma unroll
-            for (int e = 0; e < 5; ++e) q[e] = to_f32<T>(r[n + e], scale);
-            float4* p = reinterpret_cast<float4*>(pairs + (size_t)(win * WS + n) * (CPLX ? 32 : 16));
-            if (CPLX) {
-                float qi[5];
+        for (int e = 0; e < K + 3; ++e) q[e] = to_f32<T>(r[e], scale);
+        float4* p = reinterpret_cast<float4*>(pairs + (size_t)(win * WS + n0) * (CPLX ? 32 : 16));
+        if constexpr (CPLX) {
+            const T* ri = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES + RAWS * 4) + off;
+            float qi[K + 3];
 #pragma unroll
-                for (int e = 0; e < 5; ++e) qi[e] = to_f32<T>(ri[n + e], scale);
-                p[0] = coeffs(q[0], q[1], q[2], q[3]);
-                p[1] = coeffs(qi[0], qi[1], qi[2], qi[3]);
-                p[2] = coeffs(q[1], q[2], q[3], q[4]);
-                p[3] = coeffs(qi[1], qi[2], qi[3], qi[4]);
-            } else {
-                p[0] = coeffs(q[0], q[1], q[2], q[3]);
-                p[1] = coeffs(q[1], q[2], q[3], q[4]);
+            for (int e = 0; e < K + 3; ++e) qi[e] = to_f32<T>(ri[e], scale);
+#pragma unroll
+            for (int e = 0; e < K; ++e) {
+                p[2 * e] = coeffs(q[e], q[e + 1], q[e + 2], q[e + 3]);
+                p[2 * e + 1] = coeffs(qi[e], qi[e + 1], qi[e + 2], qi[e + 3]);
             }
+        } else {
+#pragma unroll
+            for (int e = 0; e < K; ++e) p[e] = coeffs(q[e], q[e + 1], q[e + 2], q[e + 3]);
         }
     }
 }
@@ -560,24 +549,17 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
         const int* woff = s_woff + b * C::NWIN;
         if (CUBIC) {
             if (a.dtype == RCBF_F16)
-                rewrite_windows_cubic<__half, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, a.scale, warp, lane);
+                rewrite_windows_cubic_hw<__half, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, a.scale, warp, lane);
             else if (a.dtype == RCBF_I32)
-                rewrite_windows_cubic<int, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, a.scale, warp, lane);
+                rewrite_windows_cubic_hw<int, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, a.scale, warp, lane);
             else
-                rewrite_windows_cubic<float, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, a.scale, warp, lane);
-        } else if (!CPLX) {
-            if (a.dtype == RCBF_F16)
-                rewrite_windows_real<__half, WS, C::NWIN, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
-            else if (a.dtype == RCBF_I32)
-                rewrite_windows_real<int, WS, C::NWIN, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
-            else
-                rewrite_windows_real<float, WS, C::NWIN, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
+                rewrite_windows_cubic_hw<float, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, a.scale, warp, lane);
         } else if (a.dtype == RCBF_F16)
-            rewrite_windows<__half, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
+            rewrite_windows_hw<__half, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
         else if (a.dtype == RCBF_I32)
-            rewrite_windows<int, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
+            rewrite_windows_hw<int, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
         else
-            rewrite_windows<float, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
+            rewrite_windows_hw<float, CPLX, WS, C::NWIN, C::RAWS, C::RAW_WIN_BYTES>(rawb, woff, pairs, a.W, hp, a.scale, warp, lane);
         if (D2 && tid < C::NWIN) {
             const int win = tid;
             const int i = sdiv.mod(s) * C::CI + win / C::CJ, j = chunk_of(s) * C::CJ + win % C::CJ;
