@@ -220,6 +220,13 @@ decode_tc_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_consta
         asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&map_out)) : "memory");
         mbar_arrive_expect_tx(a_full, (uint32_t)C::A_BYTES);
         bulk_g2s(sbase + C::OFF_A, atc, (uint32_t)C::A_BYTES, a_full);
+        // the first raw tiles are requested before the tensor memory is
+        // allocated: their latency overlaps the rest of the set-up
+        for (int j = 0; j < RS && j < my_tiles; ++j) {
+            const long long tile = blockIdx.x + (long long)j * gridDim.x;
+            mbar_arrive_expect_tx(raw_full(j), (uint32_t)C::TILE_BYTES);
+            tma_load_2d(raw_buf(j), &map_in, (int)(tile * kTcCols), 0, raw_full(j));
+        }
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -239,10 +246,10 @@ decode_tc_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_consta
     if (warp == 0) {
         // ---- TMA producer: raw tiles run up to RS ahead of the converters
         if (lane == 0) {
-            int issued = 0;
-            for (int j = 0; j < my_tiles && ok; ++j) {
+            int issued = my_tiles < RS ? my_tiles : RS;     // requested during the set-up
+            for (int j = issued; j < my_tiles && ok; ++j) {
                 const int s = j % RS;
-                if (j >= RS && !(ok = wait(raw_empty(s), j / RS - 1))) break;
+                if (!(ok = wait(raw_empty(s), j / RS - 1))) break;
                 const long long tile = blockIdx.x + (long long)j * gridDim.x;
                 mbar_arrive_expect_tx(raw_full(s), (uint32_t)C::TILE_BYTES);
                 tma_load_2d(raw_buf(s), &map_in, (int)(tile * kTcCols), 0, raw_full(s));
