@@ -1004,7 +1004,9 @@ def main():
                      "frac": achieved / alu_peak, "traffic": traffic,
                      "kernel": "batch_kernel (the persistent DAS launch of the step, timed alone)",
                      "peak_src": "%d SMs x 128 FP32 lanes x %.0f MHz" % (sms, peaks["sm_max_mhz"]),
-                     "ops_per_sum": ops_per_sum},
+                     "ops_per_sum": ops_per_sum,
+                     "binding": "shared-memory data path: one 8-byte line piece per sum (16 sums per clock per "
+                                "SM); the fraction of that measured ceiling is ceilings.frac_lds_batched"},
         "roofline_memory": {"bound": "hbm", "achieved": B * frame_bytes / (t_batch_kernel * 1e-3) / 1e9,
                             "peak": peaks["hbm_gbs"], "unit": "GB/s",
                             "frac": B * frame_bytes / (t_batch_kernel * 1e-3) / 1e9 / peaks["hbm_gbs"],
