@@ -34,7 +34,10 @@ def _frames():
 @pytest.mark.parametrize("pinned", [True, False])
 def test_pipeline_steps_match_single_frames(pinned):
     frames = _frames()
-    plans = [rc.Plan(rc.make_params(f.geometry, decoded_dtype="f16", tile=(64, 1, 16))) for f in frames]
+    # different tile extents: the batch of every slot runs two phases (the
+    # second a programmatic dependent), captured in the slot's graph
+    plans = [rc.Plan(rc.make_params(f.geometry, decoded_dtype="f16", tile=t))
+             for f, t in zip(frames, [(64, 1, 16), (32, 1, 32)])]
     pipe = rc.Pipeline(plans, n_slots=3)
     steps = 7                               # every slot is reused at least twice
     inputs, images = [], []
