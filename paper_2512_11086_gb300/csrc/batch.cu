@@ -10,8 +10,8 @@
 #include "batch_kernel.cuh"
 
 namespace rcbf {
-template <int VU> int batch_configure_vu(int ws, int* per_sm, size_t* smem);
-template <int VU> int batch_launch_vu(int ws, unsigned grid, size_t smem, const int4* items, int n_items,
+template <int VU> int batch_configure_vu(int ws, bool dec, int* per_sm, size_t* smem);
+template <int VU> int batch_launch_vu(int ws, bool dec, unsigned grid, size_t smem, const int4* items, int n_items,
                                       const BatchFrame* frames, int* counters, int ticket_slot, long long wait_ns,
                                       int withhold, bool dependent, cudaStream_t s);
 
@@ -19,6 +19,7 @@ template <int VU> int batch_launch_vu(int ws, unsigned grid, size_t smem, const 
 struct BatchPhase {
     int vu = 2;
     int ws = 48;
+    bool dec = false;        // the phase holds decode items
     int item0 = 0;           // first item of the phase in the batch's item list
     int n_items = 0;
     unsigned grid = 1;
@@ -50,9 +51,14 @@ int batch_fail(rcbf_batch_s* b, int code, const std::string& msg) {
 
 int class_of(int W) { return W <= 48 ? 48 : W <= 64 ? 64 : W <= 96 ? 96 : 128; }
 
-// phases with fewer whole-tile units than this many waves of the grid split
-// every tile into two channel halves
-constexpr long long kSplitWaves = 24;
+// tail of a phase: the last kTailQuarters / 4 waves of the grid (tiles in
+// ticket order) are split into up to kTailParts ordered channel parts.
+// Measured on four B-scan frames (2048 tiles, 6.7 waves of 304 CTAs): every
+// tile in halves 8.65 ms per step, whole tiles 8.92 ms; whole tiles with a
+// tail of 1/2, 3/4, 1, 3/2 or 2 waves in halves 8.534, 8.534, 8.546, 8.551,
+// 8.583 ms; 1/2 or 3/4 of a wave in quarters 8.590, 8.598 ms.
+constexpr long long kTailQuarters = 3;
+constexpr int kTailParts = 2;
 
 }  // namespace
 
@@ -159,30 +165,30 @@ int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t
         BatchPhase ph;
         ph.ws = keys[p].first;
         ph.vu = keys[p].second;
+        const std::vector<int>& fs = members[p];
+        for (int f : fs) ph.dec = ph.dec || frames[f].n_decode > 0;
         int per_sm = 1, rc;
         switch (ph.vu) {
-            case 1: rc = batch_configure_vu<1>(ph.ws, &per_sm, &ph.smem); break;
-            case 2: rc = batch_configure_vu<2>(ph.ws, &per_sm, &ph.smem); break;
-            default: rc = batch_configure_vu<4>(ph.ws, &per_sm, &ph.smem); break;
+            case 1: rc = batch_configure_vu<1>(ph.ws, ph.dec, &per_sm, &ph.smem); break;
+            case 2: rc = batch_configure_vu<2>(ph.ws, ph.dec, &per_sm, &ph.smem); break;
+            default: rc = batch_configure_vu<4>(ph.ws, ph.dec, &per_sm, &ph.smem); break;
         }
         if (rc != RCBF_OK) return rc;
-        const std::vector<int>& fs = members[p];
         const int slots = sms * per_sm;
-        // channel split of the phase's DAS units. Units of a whole tile leave
-        // the last wave of a short phase partly idle; halving them (two
-        // channel halves per tile, summed into the image in order) evens the
-        // tail, while every further split repeats the tile set-up and the
-        // pipeline fill. Measured on four B-scan frames (2048 tiles, 6.7 waves
-        // of 304 CTAs): whole tiles 9.67 ms, halves 9.49 ms, quarters 9.56 ms.
-        // Phases of many waves keep whole tiles.
+        // channel split of the phase's DAS units. Whole tiles carry the bulk
+        // of a phase (every split repeats the tile set-up and the pipeline
+        // fill), but a wave of whole tiles leaves part of the grid idle at the
+        // end of the phase. So the last tiles in ticket order are split into
+        // ordered channel parts (summed into the image in part order): the
+        // CTAs that run out of whole tiles first pick up the parts, and the
+        // phase ends within about one part's time.
         long long tiles_all = 0;
-        bool halves = true;
         for (int f : fs) {
             const DasArgs& a = frames[f].das;
             tiles_all += (long long)a.tiles_u * a.tiles_v * a.tiles_w;
-            halves = halves && (a.n_ch / 8) % 2 == 0;
         }
-        const int split = (halves && tiles_all < kSplitWaves * (long long)slots) ? 2 : 1;
+        const long long tail = std::min(tiles_all, kTailQuarters * slots / 4);
+        long long tile_seq = 0;               // tiles of the phase before the current one
         ph.item0 = (int)items.size();
         auto push_decode = [&](int f) {
             for (int t = 0; t < frames[f].n_decode; ++t) items.push_back(make_int4(kItemDecode, f, t, 0));
@@ -190,14 +196,19 @@ int rcbf_batch_create(const rcbf_plan_t* plans, uint32_t n_frames, const int16_t
         auto push_das = [&](int f) {
             DasArgs& a = frames[f].das;
             const int tiles = a.tiles_u * a.tiles_v * a.tiles_w;
-            a.n_split = split;
-            if (split > 1) {
-                flag_off[f] = n_flags;
-                n_flags += tiles;
+            const int chunks = a.n_ch / 8;
+            int parts = 1;
+            while (parts * 2 <= kTailParts && chunks % (parts * 2) == 0) parts *= 2;
+            a.n_split = 1;
+            for (int t = 0; t < tiles; ++t, ++tile_seq) {
+                const int q = tile_seq >= tiles_all - tail ? parts : 1;
+                if (q > 1 && flag_off[f] < 0) {
+                    flag_off[f] = n_flags;
+                    n_flags += tiles;
+                }
+                // the parts of a tile take consecutive tickets
+                for (int sp = 0; sp < q; ++sp) items.push_back(make_int4(kItemDas, f, sp * tiles + t, q));
             }
-            // the splits of a tile take consecutive tickets
-            for (int t = 0; t < tiles; ++t)
-                for (int sp = 0; sp < split; ++sp) items.push_back(make_int4(kItemDas, f, sp * tiles + t, 0));
         };
         push_decode(fs[0]);
         for (size_t k = 0; k < fs.size(); ++k) {
@@ -249,13 +260,13 @@ int rcbf_batch_run(rcbf_batch_t batch, void* stream) {
         const bool dependent = p > 0;
         int rc;
         switch (ph.vu) {
-            case 1: rc = batch_launch_vu<1>(ph.ws, ph.grid, ph.smem, items, ph.n_items, batch->d_frames,
+            case 1: rc = batch_launch_vu<1>(ph.ws, ph.dec, ph.grid, ph.smem, items, ph.n_items, batch->d_frames,
                                             batch->d_counters, slot, batch->wait_ns, batch->withhold, dependent, s);
                 break;
-            case 2: rc = batch_launch_vu<2>(ph.ws, ph.grid, ph.smem, items, ph.n_items, batch->d_frames,
+            case 2: rc = batch_launch_vu<2>(ph.ws, ph.dec, ph.grid, ph.smem, items, ph.n_items, batch->d_frames,
                                             batch->d_counters, slot, batch->wait_ns, batch->withhold, dependent, s);
                 break;
-            default: rc = batch_launch_vu<4>(ph.ws, ph.grid, ph.smem, items, ph.n_items, batch->d_frames,
+            default: rc = batch_launch_vu<4>(ph.ws, ph.dec, ph.grid, ph.smem, items, ph.n_items, batch->d_frames,
                                              batch->d_counters, slot, batch->wait_ns, batch->withhold, dependent, s);
                 break;
         }

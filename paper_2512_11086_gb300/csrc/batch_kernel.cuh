@@ -3,7 +3,8 @@
 // §OPTIMIZATIONS "Data Transfer": frames kept in flight).
 //
 // Work items are decode tiles (128 columns of one frame) and DAS units (one
-// voxel tile of one frame). Resident CTAs take items in list order through an
+// voxel tile of one frame, or at a phase's tail one ordered channel part of
+// a tile). Resident CTAs take items in list order through an
 // atomic ticket. The host orders the list so that the decode of frame f+1
 // precedes the DAS of frame f, and a DAS item waits (bounded by a time limit)
 // until every decode item of its frame has completed. Every item it waits for
@@ -44,13 +45,13 @@ enum : int { kItemDecode = 0, kItemDas = 1 };
 // ticket per phase
 enum : int { kBatchStatus = 0, kBatchDone = 1 };
 
-template <int VU, int WS>
+template <int VU, int WS, bool DEC>
 struct BatchCfg {
     using D = DasCfg<VU, WS, false>;
     static constexpr int OFF_ARGS = ((D::SMEM + 15) / 16) * 16;
     static constexpr int SMEM_DAS = OFF_ARGS + (int)((sizeof(DasArgs) + 15) / 16) * 16;
     static constexpr int SMEM_DEC = DecodeCfg<256>::STAGE_BYTES;     // one staged tile of the largest order
-    static constexpr int SMEM = SMEM_DAS > SMEM_DEC ? SMEM_DAS : SMEM_DEC;
+    static constexpr int SMEM = (DEC && SMEM_DEC > SMEM_DAS) ? SMEM_DEC : SMEM_DAS;
     static_assert(SMEM_DEC <= D::OFF_BAR, "a decode tile must not overlap the DAS mbarriers");
 };
 
@@ -81,11 +82,13 @@ __device__ __forceinline__ void batch_decode_dt(const BatchFrame& f, long long t
     }
 }
 
-template <int VU, int WS>
+// DEC: the item list may hold decode items (a phase without them runs an
+// instance without the decode code)
+template <int VU, int WS, bool DEC>
 __global__ void __launch_bounds__(kDasThreads, 2)
 batch_kernel(const int4* __restrict__ items, int n_items, const BatchFrame* __restrict__ frames,
              int* counters, int ticket_slot, long long wait_ns, int withhold) {
-    using C = BatchCfg<VU, WS>;
+    using C = BatchCfg<VU, WS, DEC>;
     using D = typename C::D;
     extern __shared__ __align__(128) unsigned char smem[];
     DasArgs* s_args = reinterpret_cast<DasArgs*>(smem + C::OFF_ARGS);
@@ -102,7 +105,7 @@ batch_kernel(const int4* __restrict__ items, int n_items, const BatchFrame* __re
         if (t >= n_items) break;
         const int4 it = items[t];
         const BatchFrame& fr = frames[it.y];
-        if (it.x == kItemDecode) {
+        if (DEC && it.x == kItemDecode) {
             if (fr.out_dtype == RCBF_F16) batch_decode_dt<RCBF_F16>(fr, it.z, smem);
             else batch_decode_dt<RCBF_F32>(fr, it.z, smem);
             if (threadIdx.x == 0) {
@@ -135,7 +138,7 @@ batch_kernel(const int4* __restrict__ items, int n_items, const BatchFrame* __re
                 for (int q = threadIdx.x; q < (int)(sizeof(DasArgs) / 8); q += kDasThreads) dst[q] = src[q];
                 asm volatile("fence.proxy.async.global;" ::: "memory");
                 __syncthreads();
-                const bool ok = das_unit<VU, WS, false, false>(*s_args, it.z, smem, pipe);
+                const bool ok = das_unit<VU, WS, false, false>(*s_args, it.z, it.w, smem, pipe);
                 if (__syncthreads_or(!ok)) {
                     if (threadIdx.x == 0) atomicOr(counters + kBatchStatus, kStatusWaitExpired);
                     break;
@@ -149,10 +152,10 @@ batch_kernel(const int4* __restrict__ items, int n_items, const BatchFrame* __re
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-template <int VU, int WS>
+template <int VU, int WS, bool DEC>
 int batch_configure(int* per_sm, size_t* smem) {
-    using C = BatchCfg<VU, WS>;
-    auto k = batch_kernel<VU, WS>;
+    using C = BatchCfg<VU, WS, DEC>;
+    auto k = batch_kernel<VU, WS, DEC>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess)
         return check_launch("batch: set shared memory");
     int n = 0;
@@ -163,15 +166,20 @@ int batch_configure(int* per_sm, size_t* smem) {
     return RCBF_OK;
 }
 
-template <int VU>
-int batch_configure_vu(int ws, int* per_sm, size_t* smem) {
-    if (ws == 48) return batch_configure<VU, 48>(per_sm, smem);
-    if (ws == 64) return batch_configure<VU, 64>(per_sm, smem);
-    if (ws == 96) return batch_configure<VU, 96>(per_sm, smem);
-    return batch_configure<VU, 128>(per_sm, smem);
+template <int VU, int WS>
+int batch_configure_ws(bool dec, int* per_sm, size_t* smem) {
+    return dec ? batch_configure<VU, WS, true>(per_sm, smem) : batch_configure<VU, WS, false>(per_sm, smem);
 }
 
-template <int VU, int WS>
+template <int VU>
+int batch_configure_vu(int ws, bool dec, int* per_sm, size_t* smem) {
+    if (ws == 48) return batch_configure_ws<VU, 48>(dec, per_sm, smem);
+    if (ws == 64) return batch_configure_ws<VU, 64>(dec, per_sm, smem);
+    if (ws == 96) return batch_configure_ws<VU, 96>(dec, per_sm, smem);
+    return batch_configure_ws<VU, 128>(dec, per_sm, smem);
+}
+
+template <int VU, int WS, bool DEC>
 int batch_launch(unsigned grid, size_t smem, const int4* items, int n_items, const BatchFrame* frames, int* counters,
                  int ticket_slot, long long wait_ns, int withhold, bool dependent, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
@@ -184,26 +192,36 @@ int batch_launch(unsigned grid, size_t smem, const int4* items, int n_items, con
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = dependent ? 1 : 0;
-    if (cudaLaunchKernelEx(&cfg, batch_kernel<VU, WS>, items, n_items, frames, counters, ticket_slot, wait_ns,
+    if (cudaLaunchKernelEx(&cfg, batch_kernel<VU, WS, DEC>, items, n_items, frames, counters, ticket_slot, wait_ns,
                            withhold) != cudaSuccess)
         return check_launch("batch_kernel launch");
     return check_launch("batch_kernel");
 }
 
-template <int VU>
-int batch_launch_vu(int ws, unsigned grid, size_t smem, const int4* items, int n_items, const BatchFrame* frames,
+template <int VU, int WS>
+int batch_launch_ws(bool dec, unsigned grid, size_t smem, const int4* items, int n_items, const BatchFrame* frames,
                     int* counters, int ticket_slot, long long wait_ns, int withhold, bool dependent, cudaStream_t s) {
+    return dec ? batch_launch<VU, WS, true>(grid, smem, items, n_items, frames, counters, ticket_slot, wait_ns,
+                                            withhold, dependent, s)
+               : batch_launch<VU, WS, false>(grid, smem, items, n_items, frames, counters, ticket_slot, wait_ns,
+                                             withhold, dependent, s);
+}
+
+template <int VU>
+int batch_launch_vu(int ws, bool dec, unsigned grid, size_t smem, const int4* items, int n_items,
+                    const BatchFrame* frames, int* counters, int ticket_slot, long long wait_ns, int withhold,
+                    bool dependent, cudaStream_t s) {
     if (ws == 48)
-        return batch_launch<VU, 48>(grid, smem, items, n_items, frames, counters, ticket_slot, wait_ns, withhold,
-                                    dependent, s);
+        return batch_launch_ws<VU, 48>(dec, grid, smem, items, n_items, frames, counters, ticket_slot, wait_ns,
+                                       withhold, dependent, s);
     if (ws == 64)
-        return batch_launch<VU, 64>(grid, smem, items, n_items, frames, counters, ticket_slot, wait_ns, withhold,
-                                    dependent, s);
+        return batch_launch_ws<VU, 64>(dec, grid, smem, items, n_items, frames, counters, ticket_slot, wait_ns,
+                                       withhold, dependent, s);
     if (ws == 96)
-        return batch_launch<VU, 96>(grid, smem, items, n_items, frames, counters, ticket_slot, wait_ns, withhold,
-                                    dependent, s);
-    return batch_launch<VU, 128>(grid, smem, items, n_items, frames, counters, ticket_slot, wait_ns, withhold,
-                                 dependent, s);
+        return batch_launch_ws<VU, 96>(dec, grid, smem, items, n_items, frames, counters, ticket_slot, wait_ns,
+                                       withhold, dependent, s);
+    return batch_launch_ws<VU, 128>(dec, grid, smem, items, n_items, frames, counters, ticket_slot, wait_ns,
+                                    withhold, dependent, s);
 }
 
 }  // namespace rcbf

@@ -2,7 +2,7 @@
 #include "batch_kernel.cuh"
 
 namespace rcbf {
-template int batch_configure_vu<2>(int, int*, size_t*);
-template int batch_launch_vu<2>(int, unsigned, size_t, const int4*, int, const BatchFrame*, int*, int, long long,
+template int batch_configure_vu<2>(int, bool, int*, size_t*);
+template int batch_launch_vu<2>(int, bool, unsigned, size_t, const int4*, int, const BatchFrame*, int*, int, long long,
                                  int, bool, cudaStream_t);
 }  // namespace rcbf

@@ -24,7 +24,7 @@ das_tiled_kernel(DasArgs a) {
     }
     das_pipe_init<C::COPIES>(smem + C::OFF_BAR, reinterpret_cast<volatile int*>(smem + C::OFF_ABORT));
     DasPipe pipe{0u};   // stage counter of this CTA
-    if (!das_unit<VU, WS, CPLX, APOD, CUBIC, IQ, D2>(a, blockIdx.x, smem, pipe) && threadIdx.x == 0)
+    if (!das_unit<VU, WS, CPLX, APOD, CUBIC, IQ, D2>(a, blockIdx.x, a.n_split, smem, pipe) && threadIdx.x == 0)
         atomicOr(a.status, kStatusWaitExpired);
 }
 

@@ -300,10 +300,12 @@ __device__ __forceinline__ void das_pipe_init(unsigned char* bar_base, volatile 
     for (int k = 0; k < 3; ++k) mbar_arrive(bar0 + 8 * (kPieceEmpty + k));
 }
 
-// One work unit. Returns false when a bounded wait expired (the CTA must
-// stop; the caller records the status).
+// One work unit: channel part unit / tiles of tile unit % tiles, the tile's
+// channels split into n_split parts. Returns false when a bounded wait
+// expired (the CTA must stop; the caller records the status).
 template <int VU, int WS, bool CPLX, bool APOD, bool CUBIC = false, bool IQ = false, bool D2 = false>
-__device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned char* smem, DasPipe& pipe) {
+__device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, int n_split, unsigned char* smem,
+                                         DasPipe& pipe) {
     using C = DasCfg<VU, WS, CPLX, CUBIC, D2, APOD, IQ>;
     static_assert(!IQ || CPLX, "IQ beamforming reads two planes");
     float* s_ws0 = reinterpret_cast<float*>(smem + C::OFF_WS0);
@@ -327,7 +329,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     const int n_ic = a.n_tx / C::CI;
     const StageDiv sdiv(n_ic);        // stage -> (transmit group, channel chunk) without a division
     const StageDiv bvdiv(a.bv);       // tile row -> (v, w) offsets
-    const int js = (a.n_ch / C::CJ) / a.n_split;     // channel chunks of this unit
+    const int js = (a.n_ch / C::CJ) / n_split;       // channel chunks of this unit
     const int jc0 = split * js;
     int* s_act = reinterpret_cast<int*>(smem + C::OFF_ACT);
 
@@ -924,7 +926,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     float acc[4];
     upk(acc2[0], acc[0], acc[1]);
     upk(acc2[1], acc[2], acc[3]);
-    if (a.tile_flags && a.n_split > 1) {
+    if (a.tile_flags && n_split > 1) {
         // ---- ordered accumulation of the channel splits of this tile: split
         // s adds its sums to the image once splits 0 .. s-1 have (the wait is
         // on a unit with a smaller ticket, which is running or done)
@@ -964,7 +966,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, unsigned ch
     }
 
     // ---- store the tile (or this unit's partial of it)
-    float* out = a.n_split > 1 ? a.partial + (long long)split * a.partial_stride : a.image;
+    float* out = n_split > 1 ? a.partial + (long long)split * a.partial_stride : a.image;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int ku = k % VU, kr = k / VU;

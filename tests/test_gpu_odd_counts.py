@@ -1,8 +1,9 @@
 """Transmit and channel counts that are not powers of two on the GPU: the
 tiled DAS walks its (transmit group, channel chunk) stages with a division of
 the stage index by the number of transmit groups (3, 5 or 6 here), the
-adjoint likewise (its own group sizes), and the batched stream splits a tile
-into ordered channel halves only when the channel chunks divide evenly. Each
+adjoint likewise (its own group sizes), and the batched stream splits the
+tiles of a phase's tail into ordered channel halves only when the channel
+chunks divide evenly. Each
 result is checked against the FP64 oracle."""
 import numpy as np
 import pytest
