@@ -167,46 +167,86 @@ template <> __device__ __forceinline__ float to_f32<float>(float v, float) { ret
 template <> __device__ __forceinline__ float to_f32<__half>(__half v, float) { return __half2float(v); }
 template <> __device__ __forceinline__ float to_f32<int>(int v, float scale) { return (float)v * scale; }
 
-// Raw windows of one stage -> line pieces, a half-warp per window: lane l of
-// the half-warp rewrites the K = WS / 16 intervals K l .. K l + K - 1 from
-// K + 1 staged samples (per plane), so a warp covers two windows per pass
-// with fewer instructions per window than one interval pair per lane.
-// Intervals past the window's W are written too (from staged samples inside
-// the buffer) and never read.
+// Raw windows of one stage -> line pieces, a half-warp per window (a warp
+// covers two windows per pass), K = WS / 16 intervals per lane. In the
+// 48-interval class lane l takes intervals l, l + 16, l + 32: each load of
+// the half-warp reads 16 consecutive staged samples, so a warp's load touches
+// 16-18 words (one shared wavefront; 4-frame B-scan batch +1.1 %). The
+// longer classes take K consecutive intervals K l .. K l + K - 1 per lane from
+// K + 1 staged samples (fewer loads and conversions; the strided form cost
+// the 96-interval volume and the mixed stream 2-3 %). Intervals past the
+// window's W are written too (from staged samples inside the buffer) and
+// never read.
 template <class T, bool CPLX, int WS, int NWIN, int RAWS, int RAW_WIN_BYTES>
 __device__ __forceinline__ void rewrite_windows_hw(const unsigned char* rawb, const int* woff,
                                                    unsigned char* pairs, int W, float hp, float scale,
                                                    int warp, int lane) {
     constexpr int K = WS / 16;
     static_assert(K * 16 == WS && NWIN % 2 == 0, "a half-warp per window");
-    const int half = lane >> 4, n0 = K * (lane & 15);
-    const float hn0 = hp - (float)n0;                   // hp - n of this lane's first interval
-    for (int w2 = warp; w2 < NWIN / 2; w2 += kDasThreads / 32) {
-        const int win = 2 * w2 + half;
-        if (n0 >= W) continue;
-        const int off = woff[win] + n0;
-        const T* r = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES) + off;
-        float rv[K + 1];
-#pragma unroll
-        for (int e = 0; e <= K; ++e) rv[e] = to_f32<T>(r[e], scale);
-        if constexpr (CPLX) {
-            const T* ri = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES + RAWS * 4) + off;
-            float iv[K + 1];
-#pragma unroll
-            for (int e = 0; e <= K; ++e) iv[e] = to_f32<T>(ri[e], scale);
-            float4* p = reinterpret_cast<float4*>(pairs + (size_t)(win * WS + n0) * 16);
+    const int half = lane >> 4, l = lane & 15;
+    if constexpr (WS == 48) {
+        for (int w2 = warp; w2 < NWIN / 2; w2 += kDasThreads / 32) {
+            const int win = 2 * w2 + half;
+            const T* r = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES) + woff[win] + l;
+            [[maybe_unused]] const T* ri =
+                reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES + RAWS * 4) + woff[win] + l;
+            // every load first (all inside the staged buffer), then the pieces
+            T x0[K], x1[K];
+            [[maybe_unused]] T y0[K], y1[K];
 #pragma unroll
             for (int e = 0; e < K; ++e) {
-                const float sr = rv[e + 1] - rv[e], si = iv[e + 1] - iv[e];
-                const float h = hn0 - (float)e;
-                p[e] = make_float4(fmaf(h, sr, rv[e]), sr, fmaf(h, si, iv[e]), si);
+                x0[e] = r[16 * e];
+                x1[e] = r[16 * e + 1];
+                if constexpr (CPLX) {
+                    y0[e] = ri[16 * e];
+                    y1[e] = ri[16 * e + 1];
+                }
             }
-        } else {
-            float2* p = reinterpret_cast<float2*>(pairs + (size_t)(win * WS + n0) * 8);
 #pragma unroll
             for (int e = 0; e < K; ++e) {
-                const float sl = rv[e + 1] - rv[e];
-                p[e] = make_float2(fmaf(hn0 - (float)e, sl, rv[e]), sl);
+                if (16 * e >= W) break;                       // uniform: W is the stage's window length
+                const int n = l + 16 * e;
+                const float a0 = to_f32<T>(x0[e], scale), sl = to_f32<T>(x1[e], scale) - a0;
+                const float h = hp - (float)n;
+                if constexpr (CPLX) {
+                    const float b0 = to_f32<T>(y0[e], scale), si = to_f32<T>(y1[e], scale) - b0;
+                    reinterpret_cast<float4*>(pairs + (size_t)win * WS * 16)[n] =
+                        make_float4(fmaf(h, sl, a0), sl, fmaf(h, si, b0), si);
+                } else {
+                    reinterpret_cast<float2*>(pairs + (size_t)win * WS * 8)[n] = make_float2(fmaf(h, sl, a0), sl);
+                }
+            }
+        }
+    } else {
+        const int n0 = K * l;
+        const float hn0 = hp - (float)n0;                   // hp - n of this lane's first interval
+        for (int w2 = warp; w2 < NWIN / 2; w2 += kDasThreads / 32) {
+            const int win = 2 * w2 + half;
+            if (n0 >= W) continue;
+            const int off = woff[win] + n0;
+            const T* r = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES) + off;
+            float rv[K + 1];
+#pragma unroll
+            for (int e = 0; e <= K; ++e) rv[e] = to_f32<T>(r[e], scale);
+            if constexpr (CPLX) {
+                const T* ri = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES + RAWS * 4) + off;
+                float iv[K + 1];
+#pragma unroll
+                for (int e = 0; e <= K; ++e) iv[e] = to_f32<T>(ri[e], scale);
+                float4* p = reinterpret_cast<float4*>(pairs + (size_t)(win * WS + n0) * 16);
+#pragma unroll
+                for (int e = 0; e < K; ++e) {
+                    const float sr = rv[e + 1] - rv[e], si = iv[e + 1] - iv[e];
+                    const float h = hn0 - (float)e;
+                    p[e] = make_float4(fmaf(h, sr, rv[e]), sr, fmaf(h, si, iv[e]), si);
+                }
+            } else {
+                float2* p = reinterpret_cast<float2*>(pairs + (size_t)(win * WS + n0) * 8);
+#pragma unroll
+                for (int e = 0; e < K; ++e) {
+                    const float sl = rv[e + 1] - rv[e];
+                    p[e] = make_float2(fmaf(hn0 - (float)e, sl, rv[e]), sl);
+                }
             }
         }
     }
