@@ -96,6 +96,11 @@ struct DasCfg {
     static constexpr int RAW_WIN_BYTES = RAWS * 4 * (CPLX ? 2 : 1);
     static constexpr int PAIR_BUF = NWIN * WS * PAIR_BYTES;
     static constexpr int ALPHA_N = CI * ROWS;      // transmit terms per stage
+    // transmit terms ordered by warp (VR rows), then transmit, then row, so a
+    // warp reads the CI x VR terms of its rows from consecutive words
+    static __device__ __forceinline__ int alpha_index(int ii, int row) {
+        return (row / VR) * (CI * VR) + ii * VR + row % VR;
+    }
     static constexpr int OFF_PAIRS = 0;                                // NB line-piece buffers
     static constexpr int OFF_RAW = OFF_PAIRS + NB * PAIR_BUF;          // 2 raw window buffers
     static constexpr int OFF_TX = OFF_RAW + 2 * NWIN * RAW_WIN_BYTES;  // float4[kMaxOrder]
@@ -628,10 +633,10 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, int n_split
             if constexpr (D2) {
                 // P = (lat_tx - e_i)^2 + z^2 of the row, clamped to its box bounds
                 const float Lt = tx.x + dL, Zv = Zf + dz;
-                s_alpha[pb * C::ALPHA_N + ii * C::ROWS + row] = fminf(fmaxf(fmaf(Lt, Lt, Zv * Zv), tx.y), tx.z);
+                s_alpha[pb * C::ALPHA_N + C::alpha_index(ii, row)] = fminf(fmaxf(fmaf(Lt, Lt, Zv * Zv), tx.y), tx.z);
             } else {
                 const float al = tx_offset(a.tx_wave, tx, dL, dz, Zf, Zfoc, fsc);
-                s_alpha[pb * C::ALPHA_N + ii * C::ROWS + row] = fminf(fmaxf(al, tx.z - a.reach_a), tx.z + a.reach_a);
+                s_alpha[pb * C::ALPHA_N + C::alpha_index(ii, row)] = fminf(fmaxf(al, tx.z - a.reach_a), tx.z + a.reach_a);
             }
         }
         mbar_arrive(bar0 + 8 * (kRawEmpty + b));
@@ -745,7 +750,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, int n_split
 
         // ---- the sum: 4 voxels x CI transmits x CJ channels from buffer pb
         const uint32_t pbase = pairs_u32 + pb * C::PAIR_BUF - (0x4B000000u << SHIFT);
-        const float* alb = s_alpha + pb * C::ALPHA_N + warp * C::VR;
+        const float* alb = s_alpha + pb * C::ALPHA_N + warp * (C::CI * C::VR);   // this warp's rows, all transmits
         // real linear pieces: two transmits per iteration, four in the
         // 48-interval class (more independent loads in flight; measured on the
         // batched B-scan +2.7 % and +1.3 %; four cost the 96 class 4-7 %); the
@@ -771,7 +776,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, int n_split
                     const float txph = s_txph[i0 + ig + g];
 #pragma unroll
                     for (int kr = 0; kr < C::VR; ++kr) {
-                        al[kr] = alb[(ig + g) * C::ROWS + kr];
+                        al[kr] = alb[(ig + g) * C::VR + kr];
                         const float x = fmaf(iqr, al[kr], txph);
                         __sincosf(6.28318530717958648f * (x - rintf(x)), &es[g][kr], &ec[g][kr]);
                     }
@@ -852,7 +857,7 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, int n_split
         for (int ii = 0; ii < C::CI; ++ii) {
             float al[C::VR];
 #pragma unroll
-            for (int kr = 0; kr < C::VR; ++kr) al[kr] = alb[ii * C::ROWS + kr];
+            for (int kr = 0; kr < C::VR; ++kr) al[kr] = alb[ii * C::VR + kr];
             const f2x al2[2] = {pk(al[0 / VU], al[1 / VU]), pk(al[2 / VU], al[3 / VU])};
             const uint32_t pb_ii = pbase + ii * (C::CJ * WS * C::PAIR_BYTES);
             static_for<0, C::CJ>([&](auto jjc) {
