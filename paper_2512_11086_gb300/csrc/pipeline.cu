@@ -8,8 +8,9 @@
 //   d2h stream:     wait(computed) ; copy images ; record done
 // Three streams, so the uploads of step s+1 run while step s computes and the
 // read-back of step s-1 drains. The host waits for a slot's previous step only
-// when it reuses the slot, and then folds that step's batch status into the
-// pipeline's sticky status.
+// when it reuses the slot, and then folds that step's batch status (copied
+// to pinned host memory behind the images, so no synchronous copy is needed)
+// into the pipeline's sticky status.
 #include <string>
 #include <vector>
 
@@ -26,6 +27,7 @@ struct Slot {
     rcbf_batch_t batch = nullptr;
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t copied = nullptr, computed = nullptr, done = nullptr;
+    int* h_status = nullptr;        // pinned: the batch status word of the slot's last step
     bool busy = false;
 };
 
@@ -45,11 +47,9 @@ struct rcbf_pipeline_s {
 
 namespace {
 
+// the slot's done event has completed: its status copy has landed
 int fold_status(rcbf_pipeline_s* p, Slot& s) {
-    int st = 0;
-    if (cudaMemcpy(&st, batch_status_word(s.batch), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
-        return check_launch("rcbf_pipeline: read batch status");
-    p->status |= st;
+    p->status |= *reinterpret_cast<volatile int*>(s.h_status);
     s.busy = false;
     return RCBF_OK;
 }
@@ -118,6 +118,9 @@ int rcbf_pipeline_create(const rcbf_plan_t* plans, uint32_t n_frames, uint32_t n
             cudaEventCreateWithFlags(&s.computed, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess)
             return pipeline_fail(p, RCBF_ECUDA, "rcbf_pipeline_create: events");
+        if (cudaHostAlloc(reinterpret_cast<void**>(&s.h_status), sizeof(int), cudaHostAllocDefault) != cudaSuccess)
+            return pipeline_fail(p, RCBF_ENOMEM, "rcbf_pipeline_create: pinned status word");
+        *s.h_status = 0;
         // capture the batch launch (a counter reset and one persistent kernel)
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(p->compute, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
@@ -161,7 +164,10 @@ int rcbf_pipeline_submit(rcbf_pipeline_t p, const void* const* host_inputs, floa
     for (size_t f = 0; f < n; ++f)
         if (cudaMemcpyAsync(host_images[f], s.img[f], p->img_bytes[f], cudaMemcpyDeviceToHost, p->d2h) != cudaSuccess)
             return check_launch("rcbf_pipeline_submit: read-back");
-    if (cudaEventRecord(s.done, p->d2h) != cudaSuccess) return check_launch("rcbf_pipeline_submit: record");
+    if (cudaMemcpyAsync(s.h_status, batch_status_word(s.batch), sizeof(int), cudaMemcpyDeviceToHost, p->d2h) !=
+            cudaSuccess ||
+        cudaEventRecord(s.done, p->d2h) != cudaSuccess)
+        return check_launch("rcbf_pipeline_submit: record");
     s.busy = true;
     p->next = (p->next + 1) % (int)p->slots.size();
     return RCBF_OK;
@@ -196,6 +202,7 @@ void rcbf_pipeline_destroy(rcbf_pipeline_t p) {
         if (s.copied) cudaEventDestroy(s.copied);
         if (s.computed) cudaEventDestroy(s.computed);
         if (s.done) cudaEventDestroy(s.done);
+        if (s.h_status) cudaFreeHost(s.h_status);
     }
     if (p->h2d) cudaStreamDestroy(p->h2d);
     if (p->compute) cudaStreamDestroy(p->compute);
