@@ -86,7 +86,7 @@ struct BwdCfg {
 // is 16-byte aligned, so window cells go out as four-float reductions.
 template <int VU, bool CPLX, bool ZL, bool FN, bool VEC_RED, int WS>
 __global__ void __launch_bounds__(kDasThreads, 2)
-das_bwd_kernel(DasArgs a) {
+das_bwd_kernel(DasArgs a, int tail_units, int tail_parts) {
     using C = BwdCfg<VU, CPLX, WS>;
     static_assert(!ZL || VU == 1, "lanes on rows need 32 rows of 32 voxels");
     // tile row -> (v, w): z-fastest when lanes run over rows
@@ -115,14 +115,22 @@ das_bwd_kernel(DasArgs a) {
     for (int q = tid; q < 3 * C::ACC_BUF; q += kDasThreads) gwin[q] = 0;
     for (int q = tid; q < kMaxChannels; q += kDasThreads) s_gw[q] = 0.f;
 
-    // ---- unit -> (tile, channel split)
+    // ---- unit -> (tile, channel split). The last tail_units (tile, split)
+    // units run as tail_parts blocks of an equal part of the split's channel
+    // chunks each, the blocks scheduled last, so the grid's last wave ends
+    // within about one part's time (the partial sums go to dL/dr by atomics
+    // either way)
     const int n_tiles = a.tiles_u * a.tiles_v * a.tiles_w;
-    const int tile = blockIdx.x % n_tiles;
-    const int split = blockIdx.x / n_tiles;
+    const int n_bulk = n_tiles * a.n_split - tail_units;
+    const int b = (int)blockIdx.x;
+    const int unit = b < n_bulk ? b : n_bulk + (b - n_bulk) / tail_parts;
+    const int tile = unit % n_tiles;
+    const int split = unit / n_tiles;
     const int n_ic = a.n_tx / kBwdCI;
     const StageDiv sdiv(n_ic);               // stage -> (transmit group, channel chunk)
-    const int js = (a.n_ch / kBwdCJ) / a.n_split;
-    const int jc0 = split * js;
+    const int js_full = (a.n_ch / kBwdCJ) / a.n_split;
+    const int js = b < n_bulk ? js_full : js_full / tail_parts;
+    const int jc0 = split * js_full + (b < n_bulk ? 0 : ((b - n_bulk) % tail_parts) * js);
     const int NS = n_ic * js;
 
     const int tu = tile % a.tiles_u, tv = (tile / a.tiles_u) % a.tiles_v, tw = tile / (a.tiles_u * a.tiles_v);
@@ -620,14 +628,23 @@ das_bwd_plain_kernel(DasArgs a) {
     }
 }
 
+// channel split and tail: units of a tile and a power-of-two part of its
+// channel chunks, at least kBwdMinWaves waves of them, the last 3/4 wave of
+// units split into up to kBwdTailParts blocks each. Measured on the autofocus
+// workload (128 tiles, 32 chunks, 304 CTA slots): 16 splits without a tail
+// 2.508 ms; 16 splits, the last 3/4 or 1 wave halved 2.447, 2.442 ms; 8
+// splits, the last 3/4 wave in quarters 2.436 ms; 8 splits with a halved
+// wave 2.506 ms; 4 splits with a wave in quarters 2.495 ms.
+constexpr long long kBwdMinWaves = 3;
+constexpr int kBwdTailParts = 4;
+constexpr long long kBwdTailQuarters = 3;
+
 template <int VU, bool CPLX, bool ZL, bool FN, bool VEC_RED, int WS>
 int launch_bwd_tiled_v(const PlanHost& h, DasArgs a, cudaStream_t s) {
     using C = BwdCfg<VU, CPLX, WS>;
     auto k = das_bwd_kernel<VU, CPLX, ZL, FN, VEC_RED, WS>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess)
         return check_launch("das_backward: set shared memory");
-    // channel split: the smallest power of two (dividing the channel chunks)
-    // whose work units fill the resident CTA slots to >= 95 %
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kDasThreads, C::SMEM) != cudaSuccess || per_sm < 1)
         per_sm = 1;
@@ -635,17 +652,15 @@ int launch_bwd_tiled_v(const PlanHost& h, DasArgs a, cudaStream_t s) {
     const long long slots = (long long)h.n_sms * per_sm;
     const int chunks = a.n_ch / kBwdCJ;
     int sp = 1;
-    double best_eff = 0.0;
-    for (int c = 1; c <= chunks && c <= 32; c *= 2) {
-        if (chunks % c) break;
-        const long long units = tiles * c;
-        const double eff = (double)units / (double)(((units + slots - 1) / slots) * slots);
-        if (eff > best_eff + 1e-9) { best_eff = eff; sp = c; }
-        if (eff >= 0.95) break;
-    }
+    while (tiles * sp < kBwdMinWaves * slots && sp * 2 <= chunks && chunks % (sp * 2) == 0 && sp < 32) sp *= 2;
     a.n_split = sp;
-    const unsigned grid = (unsigned)(tiles * sp);
-    k<<<grid, kDasThreads, C::SMEM, s>>>(a);
+    // tail: the last units split into parts (when a unit's chunks divide)
+    const long long units = tiles * sp;
+    int parts = 1;
+    while (parts * 2 <= kBwdTailParts && (chunks / sp) % (parts * 2) == 0) parts *= 2;
+    const int tail = parts > 1 ? (int)std::min(units, kBwdTailQuarters * slots / 4) : 0;
+    const unsigned grid = (unsigned)(units + (long long)tail * (parts - 1));
+    k<<<grid, kDasThreads, C::SMEM, s>>>(a, tail, parts);
     return check_launch("das_bwd_kernel");
 }
 
