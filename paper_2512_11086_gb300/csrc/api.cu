@@ -563,7 +563,7 @@ int rcbf_plan(const rcbf_params* params, rcbf_plan_t* out_plan) {
     }
     if ((rc = configure_das(h)) != RCBF_OK) { std::string m = g_last_error; rcbf_destroy(plan); return set_error(rc, m); }
     {
-        const int sp = std::max(std::max(h.n_split[0], h.n_split[1]), std::max(h.n_split[2], h.n_split[3]));
+        const int sp = std::max(std::max(das_slices(h, 0), das_slices(h, 1)), std::max(das_slices(h, 2), das_slices(h, 3)));
         if (sp > 1) {
             h.partial_floats = (size_t)sp * a.image_plane * (p.decoded_dtype == RCBF_CF32 ? 2 : 1);
             if (cudaMalloc(&h.d_partial, h.partial_floats * sizeof(float)) != cudaSuccess)
@@ -587,9 +587,10 @@ int rcbf_plan_query(rcbf_plan_t plan, rcbf_plan_info* info) {
     const bool tiled = h.p.das_variant == RCBF_DAS_TILED && h.tiled_ok && fits;
     info->tiled = tiled ? 1u : 0u;
     info->window = (uint32_t)a.W;
-    const int sp = tiled ? std::max(1, h.n_split[das_class_index(a.W, h.p.acq_kind == RCBF_HERCULES_2D)]) : 1;
+    const int cls = das_class_index(a.W, h.p.acq_kind == RCBF_HERCULES_2D);
+    const int sp = tiled ? std::max(1, h.n_split[cls]) : 1;
     info->n_split = (uint32_t)sp;
-    info->das_launches = sp > 1 ? 2u : 1u;
+    info->das_launches = tiled && das_slices(h, cls) > 1 ? 2u : 1u;
     info->decode_launches = h.p.hadamard_order ? (h.p.decoded_dtype == RCBF_CF32 ? 2u : 1u) : 0u;
     uint64_t bytes = sizeof(int) + h.partial_floats * sizeof(float);
     if (h.p.hadamard_order) {

@@ -15,7 +15,8 @@ namespace rcbf {
 
 template <int VU, bool CPLX, bool D2> int configure_das_vu(int ws, bool cubic, bool iq, int* per_sm);
 template <int VU, bool CPLX, bool D2>
-int launch_das_vu(const DasArgs& a, int ws, bool apod, bool cubic, bool iq, cudaStream_t s);
+int launch_das_vu(const DasArgs& a, int ws, bool apod, bool cubic, bool iq, int tail_units, int tail_parts,
+                  cudaStream_t s);
 
 namespace {
 template <int VU>
@@ -31,16 +32,17 @@ int configure_vu(int ws, bool cplx, bool cubic, bool iq, bool d2, int* per_sm) {
                 : configure_das_vu<VU, false, false>(ws, cubic, iq, per_sm);
 }
 template <int VU>
-int launch_vu(const DasArgs& a, int ws, bool cplx, bool apod, bool cubic, bool iq, bool d2, cudaStream_t s) {
+int launch_vu(const DasArgs& a, int ws, bool cplx, bool apod, bool cubic, bool iq, bool d2, int tu, int tp,
+              cudaStream_t s) {
     if (d2) {
         if constexpr (VU == 1)
-            return cplx ? launch_das_vu<1, true, true>(a, ws, apod, cubic, iq, s)
-                        : launch_das_vu<1, false, true>(a, ws, apod, cubic, iq, s);
+            return cplx ? launch_das_vu<1, true, true>(a, ws, apod, cubic, iq, tu, tp, s)
+                        : launch_das_vu<1, false, true>(a, ws, apod, cubic, iq, tu, tp, s);
         else
             return set_error(RCBF_EUNSUPPORTED, "das: the 2D aperture tiles hold one voxel per thread along u");
     }
-    return cplx ? launch_das_vu<VU, true, false>(a, ws, apod, cubic, iq, s)
-                : launch_das_vu<VU, false, false>(a, ws, apod, cubic, iq, s);
+    return cplx ? launch_das_vu<VU, true, false>(a, ws, apod, cubic, iq, tu, tp, s)
+                : launch_das_vu<VU, false, false>(a, ws, apod, cubic, iq, tu, tp, s);
 }
 }  // namespace
 
@@ -351,6 +353,11 @@ static int class_index(int ws) { return ws == 48 ? 0 : ws == 64 ? 1 : ws == 96 ?
 
 int das_class_index(int W, bool d2) { return class_index(stride_class(W, d2)); }
 
+int das_slices(const PlanHost& h, int c) {
+    const int sp = std::max(1, h.n_split[c]);
+    return h.tail_parts[c] > 1 && h.tail_units[c] > 0 ? sp * h.tail_parts[c] : sp;
+}
+
 int launch_das(const PlanHost& h, const DasArgs& a_in, cudaStream_t s) {
     DasArgs a = a_in;
     const bool d2 = a.acq_kind == RCBF_HERCULES_2D;
@@ -359,20 +366,28 @@ int launch_das(const PlanHost& h, const DasArgs& a_in, cudaStream_t s) {
     const bool apod = a.apod != nullptr || a.f_number > 0.f;
     const bool cubic = a.interp == RCBF_CUBIC;
     const bool iq = cplx && a.iq_ratio > 0.0;
-    a.n_split = std::max(1, h.n_split[class_index(ws)]);
+    const int c = class_index(ws);
+    a.n_split = std::max(1, h.n_split[c]);
+    const int tp = std::max(1, h.tail_parts[c]), tu = tp > 1 ? h.tail_units[c] : 0;
+    const int slices = das_slices(h, c);
     a.partial = h.d_partial;
     a.partial_stride = a.image_plane * (cplx ? 2 : 1);
+    // the partial images of tail parts p >= 1 hold only the tail tiles' sums
+    if (slices > a.n_split &&
+        cudaMemsetAsync(a.partial + (long long)a.n_split * a.partial_stride, 0,
+                        (size_t)(slices - a.n_split) * a.partial_stride * sizeof(float), s) != cudaSuccess)
+        return check_launch("das: clear the tail partial images");
     int rc;
     switch (h.vu) {
-        case 1: rc = launch_vu<1>(a, ws, cplx, apod, cubic, iq, d2, s); break;
-        case 2: rc = launch_vu<2>(a, ws, cplx, apod, cubic, iq, d2, s); break;
-        default: rc = launch_vu<4>(a, ws, cplx, apod, cubic, iq, d2, s); break;
+        case 1: rc = launch_vu<1>(a, ws, cplx, apod, cubic, iq, d2, tu, tp, s); break;
+        case 2: rc = launch_vu<2>(a, ws, cplx, apod, cubic, iq, d2, tu, tp, s); break;
+        default: rc = launch_vu<4>(a, ws, cplx, apod, cubic, iq, d2, tu, tp, s); break;
     }
-    if (rc != RCBF_OK || a.n_split == 1) return rc;
+    if (rc != RCBF_OK || slices == 1) return rc;
     const long long n = a.partial_stride;
     long long blocks = (n + 255) / 256;
     if (blocks > (long long)h.n_sms * 8) blocks = (long long)h.n_sms * 8;
-    das_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(a.partial, a.image, n, a.partial_stride, a.n_split);
+    das_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(a.partial, a.image, n, a.partial_stride, slices);
     return check_launch("das_reduce_kernel");
 }
 
@@ -389,6 +404,8 @@ int configure_das(PlanHost& h) {
         if ((cubic && cplx && ws == 128) || (d2 && ws == 48)) {   // plain form / 64 class
             h.das_blocks_per_sm[c] = 0;
             h.n_split[c] = 1;
+            h.tail_parts[c] = 1;
+            h.tail_units[c] = 0;
             continue;
         }
         switch (h.vu) {
@@ -399,21 +416,20 @@ int configure_das(PlanHost& h) {
         if (rc != RCBF_OK) return rc;
         h.das_blocks_per_sm[c] = n;
         // channel split: the smallest power of two (dividing the channel
-        // chunks) whose work units fill the resident CTA slots to >= 95 %
+        // chunks, at most 16) whose units make three waves of the resident
+        // CTA slots; then the last 3/4 wave of units in up to four channel
+        // parts each (scheduled last), so the grid ends within about one
+        // part's time
         const long long tiles = (long long)h.das.tiles_u * h.das.tiles_v * h.das.tiles_w;
         const long long slots = (long long)h.n_sms * (n > 0 ? n : 1);
         const int chunks = (int)h.p.n_ch / kCJ;
-        int best = 1;
-        double best_eff = 0;
-        for (int sp = 1; sp <= chunks && sp <= 16; sp *= 2) {
-            if (chunks % sp) break;
-            const long long units = tiles * sp;
-            const long long waves = (units + slots - 1) / slots;
-            const double eff = (double)units / (double)(waves * slots);
-            if (eff > best_eff + 1e-9) { best_eff = eff; best = sp; }
-            if (eff >= 0.95) break;
-        }
-        h.n_split[c] = best;
+        int sp = 1;
+        while (tiles * sp < 3 * slots && sp * 2 <= chunks && chunks % (sp * 2) == 0 && sp < 16) sp *= 2;
+        int parts = 1;
+        while (parts * 2 <= 4 && (chunks / sp) % (parts * 2) == 0) parts *= 2;
+        h.n_split[c] = sp;
+        h.tail_parts[c] = parts;
+        h.tail_units[c] = parts > 1 ? (int)std::min(tiles * sp, 3 * slots / 4) : 0;
     }
     return RCBF_OK;
 }

@@ -4,5 +4,6 @@
 
 namespace rcbf {
 template int configure_das_vu<1, true, true>(int, bool, bool, int*);
-template int launch_das_vu<1, true, true>(const DasArgs&, int, bool, bool, bool, cudaStream_t);
+template int launch_das_vu<1, true, true>(const DasArgs&, int, bool, bool, bool, int, int,
+                                          cudaStream_t);
 }  // namespace rcbf

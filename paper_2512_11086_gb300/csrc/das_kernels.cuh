@@ -9,22 +9,39 @@
 
 namespace rcbf {
 
+// Block b < tiles * n_split - tail_units: unit b (tile b % tiles, channel
+// split b / tiles), written to partial image b / tiles. The last tail_units
+// units run as tail_parts blocks each, the blocks scheduled last: part p of
+// unit (tile t, split s) takes the p-th part of the split's channel chunks
+// and writes partial image s (p = 0) or n_split + s (tail_parts - 1) + p - 1,
+// images that the launcher clears for the tiles without such parts. With one
+// split and no tail the unit writes the image itself.
 template <int VU, int WS, bool CPLX, bool APOD, bool CUBIC, bool IQ, bool D2>
 __global__ void __launch_bounds__(kDasThreads, 2)
-das_tiled_kernel(DasArgs a) {
+das_tiled_kernel(DasArgs a, int tail_units, int tail_parts) {
     using C = DasCfg<VU, WS, CPLX, CUBIC, D2, APOD, IQ>;
     extern __shared__ __align__(128) unsigned char smem[];
+    const int n_tiles = a.tiles_u * a.tiles_v * a.tiles_w;
+    const int n_bulk = n_tiles * a.n_split - tail_units;
+    const int b = (int)blockIdx.x;
+    int unit = b, n_split = a.n_split, slice = a.n_split > 1 || tail_units > 0 ? b / n_tiles : -1;
+    if (b >= n_bulk) {
+        const int u = n_bulk + (b - n_bulk) / tail_parts, p = (b - n_bulk) % tail_parts;
+        const int s = u / n_tiles;
+        unit = (s * tail_parts + p) * n_tiles + u % n_tiles;
+        n_split = a.n_split * tail_parts;
+        slice = p == 0 ? s : a.n_split + s * (tail_parts - 1) + p - 1;
+    }
     if (a.vls_split) {
         // a tile across a virtual-line-source focal depth is left to the
         // plain kernel (uniform over the CTA: nothing set up yet)
-        const int n_tiles = a.tiles_u * a.tiles_v * a.tiles_w;
-        const int tile = (int)(blockIdx.x % (unsigned)n_tiles);
+        const int tile = unit % n_tiles;
         if (tile_across_focus(a, tile % a.tiles_u, (tile / a.tiles_u) % a.tiles_v, tile / (a.tiles_u * a.tiles_v)))
             return;
     }
     das_pipe_init<C::COPIES>(smem + C::OFF_BAR, reinterpret_cast<volatile int*>(smem + C::OFF_ABORT));
     DasPipe pipe{0u};   // stage counter of this CTA
-    if (!das_unit<VU, WS, CPLX, APOD, CUBIC, IQ, D2>(a, blockIdx.x, a.n_split, smem, pipe) && threadIdx.x == 0)
+    if (!das_unit<VU, WS, CPLX, APOD, CUBIC, IQ, D2>(a, unit, n_split, smem, pipe, slice) && threadIdx.x == 0)
         atomicOr(a.status, kStatusWaitExpired);
 }
 
@@ -77,11 +94,13 @@ int configure_das_vu(int ws, bool cubic, bool iq, int* per_sm) {
 }
 
 template <int VU, bool CPLX_T, bool D2 = false>
-int launch_das_vu(const DasArgs& a, int ws, bool apod, bool cubic, bool iq, cudaStream_t s) {
+int launch_das_vu(const DasArgs& a, int ws, bool apod, bool cubic, bool iq, int tail_units, int tail_parts,
+                  cudaStream_t s) {
     constexpr bool cplx = CPLX_T;
-    const unsigned grid = (unsigned)a.tiles_u * a.tiles_v * a.tiles_w * a.n_split;
+    const unsigned grid = (unsigned)a.tiles_u * a.tiles_v * a.tiles_w * a.n_split + tail_units * (tail_parts - 1);
 #define RCBF_LAUNCH(WSV, CP, AP, CU, Q)                                                                               \
-    das_tiled_kernel<VU, WSV, CP, AP, CU, Q, D2><<<grid, kDasThreads, DasCfg<VU, WSV, CP, CU, D2, AP, Q>::SMEM, s>>>(a); \
+    das_tiled_kernel<VU, WSV, CP, AP, CU, Q, D2><<<grid, kDasThreads, DasCfg<VU, WSV, CP, CU, D2, AP, Q>::SMEM, s>>>( \
+        a, tail_units, tail_parts);                                                                                   \
     return check_launch("das_tiled_kernel");
 #define RCBF_AP(WSV, CP, CU, Q) \
     if (apod) { RCBF_LAUNCH(WSV, CP, true, CU, Q) } else { RCBF_LAUNCH(WSV, CP, false, CU, Q) }

@@ -89,8 +89,14 @@ extern "C" int rcbf_das_noalloc(const rcbf_params* params, const void* decoded, 
     const bool tiled = h.p.das_variant == RCBF_DAS_TILED && fits;
     if (tiled) {
         if ((rc = configure_das(h)) != RCBF_OK) return rc;
-        const int split = std::max(1, h.n_split[das_class_index(a.W, h.p.acq_kind == RCBF_HERCULES_2D)]);
+        const int cls = das_class_index(a.W, h.p.acq_kind == RCBF_HERCULES_2D);
         const size_t planes = h.p.decoded_dtype == RCBF_CF32 ? 2 : 1;
+        // the tail parts' extra partial images only where the scratch holds them
+        if ((size_t)das_slices(h, cls) * planes * (size_t)a.image_plane > kNoAllocScratchFloats - kNoAllocHeaderFloats) {
+            h.tail_parts[cls] = 1;
+            h.tail_units[cls] = 0;
+        }
+        const int split = das_slices(h, cls);
         const size_t need = split > 1 ? (size_t)split * planes * (size_t)a.image_plane : 0;
         if (need > kNoAllocScratchFloats - kNoAllocHeaderFloats)
             return set_error(RCBF_EINVAL, "rcbf_das_noalloc: the channel-split partial images need " +

@@ -346,11 +346,13 @@ __device__ __forceinline__ void das_pipe_init(unsigned char* bar_base, volatile 
 }
 
 // One work unit: channel part unit / tiles of tile unit % tiles, the tile's
-// channels split into n_split parts. Returns false when a bounded wait
-// expired (the CTA must stop; the caller records the status).
+// channels split into n_split parts, written to partial image `slice` (-1:
+// the image itself when n_split is 1, else partial image unit / tiles).
+// Returns false when a bounded wait expired (the CTA must stop; the caller
+// records the status).
 template <int VU, int WS, bool CPLX, bool APOD, bool CUBIC = false, bool IQ = false, bool D2 = false>
 __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, int n_split, unsigned char* smem,
-                                         DasPipe& pipe) {
+                                         DasPipe& pipe, int slice = -1) {
     using C = DasCfg<VU, WS, CPLX, CUBIC, D2, APOD, IQ>;
     static_assert(!IQ || CPLX, "IQ beamforming reads two planes");
     float* s_ws0 = reinterpret_cast<float*>(smem + C::OFF_WS0);
@@ -1011,7 +1013,8 @@ __device__ __forceinline__ bool das_unit(const DasArgs& a, int unit, int n_split
     }
 
     // ---- store the tile (or this unit's partial of it)
-    float* out = n_split > 1 ? a.partial + (long long)split * a.partial_stride : a.image;
+    float* out = slice >= 0 ? a.partial + (long long)slice * a.partial_stride
+               : n_split > 1 ? a.partial + (long long)split * a.partial_stride : a.image;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int ku = k % VU, kr = k / VU;

@@ -3,5 +3,6 @@
 
 namespace rcbf {
 template int configure_das_vu<2, false, false>(int, bool, bool, int*);
-template int launch_das_vu<2, false, false>(const DasArgs&, int, bool, bool, bool, cudaStream_t);
+template int launch_das_vu<2, false, false>(const DasArgs&, int, bool, bool, bool, int, int,
+                                          cudaStream_t);
 }  // namespace rcbf

@@ -117,6 +117,8 @@ struct PlanHost {
     int decode_blocks_per_sm;
     int das_blocks_per_sm[4];   // by window stride class (48, 64, 96, 128)
     int n_split[4];         // channel split by window stride class
+    int tail_parts[4];      // parts of each of the last tail_units units (1: none)
+    int tail_units[4];      // units at the end of the grid run as tail_parts blocks each
     float* d_partial;       // DAS partial images (channel split), plan-owned
     size_t partial_floats;
     int16_t* d_taps;        // device demodulation FIR taps (demod_decimation > 0)
@@ -189,6 +191,7 @@ int launch_das_backward(const PlanHost& h, const DasArgs& a, int mode, cudaStrea
 int configure_decode(PlanHost& h);
 int das_class_index(int W, bool d2);
 int configure_das(PlanHost& h);
+int das_slices(const PlanHost& h, int c);   // partial images of window class c (1: none)
 
 // ------------------------------------------------------------ PTX helpers
 // ---- transmit waves (line element, plane wave, virtual line source): the
