@@ -118,6 +118,21 @@ def test_full_bscan_sampled_voxels_f16_storage():
     _report("bscan f16 vs exact decode (storage error, stated)", got, oracle.das(g, exact, voxels=vox))
 
 
+def test_full_bscan_f_number_and_weights_sampled():
+    # the full frame runs its channel split with a tail of channel parts in
+    # partial images of their own (512 tiles: 2 splits, the last 3/4 wave in
+    # quarters); with the F# window and channel weights the units also skip
+    # the chunks outside their aperture
+    fr = frame("bscan")
+    g = fr.geometry
+    _, exact = _decoded_exact(fr)
+    w = np.random.default_rng(8).uniform(0.5, 1.5, g.n_ch)
+    vox = sample_voxels(g.out_dims, 2000, seed=5)
+    want = oracle.das(g, exact, w=w, f_number=1.0, voxels=vox)
+    got = _gpu_image(g, exact.astype(np.float32), apod=w, f_number=1.0).ravel()[vox]
+    assert _report("bscan F#1 + w", got, want) <= TOL
+
+
 def test_full_bscan_plain_form_sampled():
     fr = frame("bscan")
     g = fr.geometry
