@@ -231,8 +231,27 @@ __device__ __forceinline__ void rewrite_windows_hw(const unsigned char* rawb, co
             const int off = woff[win] + n0;
             const T* r = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES) + off;
             float rv[K + 1];
+            if constexpr (std::is_same<T, __half>::value && !CPLX) {
+                // FP16 samples by 32-bit loads: the K + 2 samples from the even
+                // sample at or before the first, pairs realigned by a byte
+                // permute when the first is odd (K even: K / 2 + 1 words)
+                constexpr int NW = K / 2 + 1;
+                const uint32_t* rw = reinterpret_cast<const uint32_t*>(rawb + win * RAW_WIN_BYTES) + (off >> 1);
+                uint32_t wv[NW + 1];
 #pragma unroll
-            for (int e = 0; e <= K; ++e) rv[e] = to_f32<T>(r[e], scale);
+                for (int q = 0; q < NW; ++q) wv[q] = rw[q];
+                wv[NW] = 0u;
+                const uint32_t sel = (off & 1) ? 0x5432u : 0x3210u;
+#pragma unroll
+                for (int q = 0; q < NW; ++q) {
+                    const uint32_t pr = __byte_perm(wv[q], wv[q + 1], sel);
+                    rv[2 * q] = __half2float(__ushort_as_half((unsigned short)(pr & 0xffffu)));
+                    if (2 * q + 1 <= K) rv[2 * q + 1] = __half2float(__ushort_as_half((unsigned short)(pr >> 16)));
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e <= K; ++e) rv[e] = to_f32<T>(r[e], scale);
+            }
             if constexpr (CPLX) {
                 const T* ri = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES + RAWS * 4) + off;
                 float iv[K + 1];
