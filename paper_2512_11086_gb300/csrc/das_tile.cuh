@@ -174,14 +174,16 @@ template <> __device__ __forceinline__ float to_f32<int>(int v, float scale) { r
 
 // Raw windows of one stage -> line pieces, a half-warp per window (a warp
 // covers two windows per pass), K = WS / 16 intervals per lane. In the
-// 48-interval class lane l takes intervals l, l + 16, l + 32: each load of
-// the half-warp reads 16 consecutive staged samples, so a warp's load touches
-// 16-18 words (one shared wavefront; 4-frame B-scan batch +1.1 %). The
-// longer classes take K consecutive intervals K l .. K l + K - 1 per lane from
-// K + 1 staged samples (fewer loads and conversions; the strided form cost
-// the 96-interval volume and the mixed stream 2-3 %). Intervals past the
-// window's W are written too (from staged samples inside the buffer) and
-// never read.
+// 48-interval class, and for complex pieces in every class, lane l takes
+// intervals l, l + 16, l + 32, ..: each load of the half-warp reads 16
+// consecutive staged samples, so a warp's load touches 16-18 words (one
+// shared wavefront; 4-frame B-scan batch +1.1 %), and a half-warp's 16-byte
+// complex pieces go to 256 consecutive bytes (K consecutive pieces per lane
+// put lanes 4 apart on the same banks: two-way conflicts). The longer real
+// classes take K consecutive intervals K l .. K l + K - 1 per lane from K + 1
+// staged samples (fewer loads and conversions; the strided form cost the
+// 96-interval volume and the mixed stream 2-3 %). Intervals past the window's
+// W are written too (from staged samples inside the buffer) and never read.
 template <class T, bool CPLX, int WS, int NWIN, int RAWS, int RAW_WIN_BYTES>
 __device__ __forceinline__ void rewrite_windows_hw(const unsigned char* rawb, const int* woff,
                                                    unsigned char* pairs, int W, float hp, float scale,
@@ -189,7 +191,7 @@ __device__ __forceinline__ void rewrite_windows_hw(const unsigned char* rawb, co
     constexpr int K = WS / 16;
     static_assert(K * 16 == WS && NWIN % 2 == 0, "a half-warp per window");
     const int half = lane >> 4, l = lane & 15;
-    if constexpr (WS == 48) {
+    if constexpr (WS == 48 || CPLX) {
         for (int w2 = warp; w2 < NWIN / 2; w2 += kDasThreads / 32) {
             const int win = 2 * w2 + half;
             const T* r = reinterpret_cast<const T*>(rawb + win * RAW_WIN_BYTES) + woff[win] + l;
