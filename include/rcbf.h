@@ -231,7 +231,8 @@ typedef struct rcbf_plan_info {
     uint32_t tile[3];          /* DAS voxel tile (bu, bv, bw) */
     uint32_t tiled;            /* 1 if rcbf_das runs the tiled form at params.c, 0 if the plain form */
     uint32_t window;           /* samples per (transmit, channel) window of a tile at params.c */
-    uint32_t n_split;          /* channels of a tile split over this many work units (1 = none) */
+    uint32_t n_split;          /* channels of a tile split over this many work units (1 = none); the
+                                  units of the grid's last 3/4 wave run in up to four channel parts */
     uint32_t das_launches;     /* kernels one rcbf_das call enqueues at params.c */
     uint32_t decode_launches;  /* kernels one rcbf_decode call enqueues (0 without Hadamard order) */
     uint64_t workspace_bytes;  /* device memory the plan owns */
