@@ -115,3 +115,21 @@ def test_noalloc_vls_focal_plane_inside_the_image():
     got = _noalloc(params, d, out)
     np.testing.assert_array_equal(got, plan.das(d).cpu().numpy())
     assert rel_l2(got, oracle.das(g, fr.decoded.astype(np.float64))) <= 1e-4
+
+
+def test_noalloc_keeps_the_channel_parts_of_the_grid_tail():
+    # a frame whose tail parts' partial images fit the static scratch (512 x
+    # 256 image in 128 tiles: 8 channel splits, the last 3/4 wave of units in
+    # halves, 16 partial images of 0.5 MB): the same units and partial images
+    # as the planned call, so the two images are equal bit for bit
+    g = synth.Geometry(n_tx=128, n_ch=128, n_samples=2048, out_dims=(512, 1, 256),
+                       out_min=(-6.4e-3, 0.0, 3e-3), out_max=(6.4e-3, 0.0, 15e-3))
+    params = rc.make_params(g, decoded_dtype="f32", tile=(64, 1, 16))
+    plan = rc.Plan(rc.make_params(g, decoded_dtype="f32", tile=(64, 1, 16)))
+    info = plan.info()
+    assert info["tiled"] and info["n_split"] == 8 and info["das_launches"] == 2
+    gen = torch.Generator(device="cuda").manual_seed(61)
+    d = torch.randn(g.n_tx, g.n_ch, g.n_samples, device="cuda", generator=gen)
+    out = torch.empty(plan.image_shape, dtype=torch.float32, device="cuda")
+    got = _noalloc(params, d, out)
+    np.testing.assert_array_equal(got, plan.das(d).cpu().numpy())
