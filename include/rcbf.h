@@ -461,8 +461,8 @@ void rcbf_pipeline_destroy(rcbf_pipeline_t pipeline);
 
 /* rcbf_das_noalloc — rcbf_das without a plan, for callers that must not
  * allocate device memory: code that owns every device allocation through its
- * own pool, real-time loops that forbid allocation after start-up, or a
- * stream capture that may not allocate. rcbf_plan allocates (decode tables,
+ * own pool, or real-time loops that forbid allocation after start-up.
+ * rcbf_plan allocates (decode tables,
  * a status word, the channel-split partial images), so those callers cannot
  * make a plan. This entry point takes the parameter block itself, validates
  * and sets up the geometry on the host, and calls no cudaMalloc, cudaFree or
@@ -471,8 +471,8 @@ void rcbf_pipeline_destroy(rcbf_pipeline_t pipeline);
  * file-scope device array of 16 MiB, which every GPU that loads the library
  * holds until the process exits. There is no counterpart in the paper.
  *   params, decoded, apod, c, image, stream: as for rcbf_plan + rcbf_das.
- * The first call on a device looks up that device's address of the array;
- * make it before any stream capture. All calls share the one array: calls
+ * The first call on a device looks up that device's address of the array
+ * (once per device, on the host). All calls share the one array: calls
  * whose work overlaps on the GPU (other streams, other host threads) race on
  * it, so serialise them. A bounded wait of the tiled kernel that expires is
  * reported by rcbf_das_noalloc_status. Errors: as rcbf_plan and rcbf_das

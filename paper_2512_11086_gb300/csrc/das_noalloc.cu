@@ -2,9 +2,9 @@
 // memory.
 //
 // Who needs this: code that runs where cudaMalloc / cudaFree are off limits —
-// for example inside a CUDA-graph capture that must not allocate, under a
-// host framework that owns every device allocation through its own pool, or
-// in a real-time acquisition loop that forbids allocation after start-up.
+// for example under a host framework that owns every device allocation
+// through its own pool, or in a real-time acquisition loop that forbids
+// allocation after start-up.
 // rcbf_plan allocates (decode tables, the status word and the partial images
 // of the channel-split DAS), so such callers cannot use it. rcbf_das_noalloc
 // takes the parameter block directly and runs the same DAS kernels; the one

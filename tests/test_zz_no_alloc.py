@@ -1,6 +1,6 @@
 """rcbf_das_noalloc: the delay-and-sum entry point for callers that must not
 allocate device memory (allocation owned by a host framework's pool, real-time
-loops, stream captures that may not allocate). It takes the parameter block
+loops). It takes the parameter block
 instead of a plan and keeps its scratch (the channel-split partial images) in
 a fixed 16 MiB device array of the library. Its images must equal those of the
 planned rcbf_das on the same inputs, call after call."""
