@@ -229,6 +229,10 @@ def test_autofocus_speed_of_sound_gradient():
 
     gc, gw = adjoint(c0)
     im64 = oracle.das(g, r, c=c0)
+    # the complex forward itself (full frame: a channel split with a tail of
+    # channel parts in partial images of their own)
+    im = plan.das(dec, c=c0).cpu().numpy().astype(np.float64)
+    assert rel_l2(im[0] + 1j * im[1], im64) <= 1e-4
     _, gc64, gw64 = oracle.das_grad(g, r, -2.0 * im64, c=c0, want_rf=False)
     h = 1e-3 * c0
     fd = (loss_gpu(c0 + h) - loss_gpu(c0 - h)) / (2 * h)
